@@ -1,0 +1,165 @@
+/*
+ * tnsk.h -- C ABI of libtnsk: GB300 (sm_103a) sketching estimators for tensor
+ * network contraction, after "Approximating Tensor Network Contraction with
+ * Sketches" (Heddes, Nunes, Givargis, Nicolau; arXiv 2603.07387).
+ *
+ * Problem (Sec. 1, Def. "Tensor contraction", Def. "Tensor product", Def. "TNC"):
+ * tensors X_1..X_p, a set E of mode pairs (u, v) with u != v and n_u = n_v, modes
+ * numbered globally across X_1 x ... x X_p in order (0-based here, 1-based in the
+ * paper). tc(X, E)(i_K') = sum_{i_K} X(i) prod_{(u,v) in E} [i_u = i_v], where K'
+ * are the open (uncontracted) modes. The library returns a randomised estimate
+ * (Def. "ATNC": error relative to ||X||_F = prod_k ||X_k||_F):
+ *   TNSK_GENERAL  method 1, any network incl. cyclic ones (Sec. 4.2, Eq. 1, Alg. 1),
+ *                 complement count sketches, FFT-domain composition;
+ *   TNSK_ACYCLIC  method 2, acyclic full networks (Sec. 4.4, Eq. 2, Alg. 2, 4, 5),
+ *                 recursive sketches evaluated leaves to root.
+ * Repetitions are combined by the median of group means (Theorem 1, median trick);
+ * open output entries follow Corollary "full-to-partial-tc".
+ *
+ * Conventions for every call:
+ *  - Tensor data, outputs and per-rep buffers are DEVICE pointers on the ctx's
+ *    device; sizes and descriptors are host memory read during the call only.
+ *  - Tensors are row-major (the paper's vec(): last mode fastest, Sec. 2).
+ *  - Calls enqueue work on the ctx stream and return before it completes. The
+ *    caller keeps inputs alive and outputs untouched until the stream reaches
+ *    the work (e.g. tnsk_sync). Errors the host can see are returned at once;
+ *    device-side errors (exhausted waits, failed bounds checks) are recorded in
+ *    the ctx and returned by tnsk_sync or the next call.
+ *  - The caller owns every buffer it passes. The library allocates only its own
+ *    scratch (cached in the ctx, freed by tnsk_destroy) and keeps no caller
+ *    pointer after the work that uses it completes.
+ *  - One ctx per host thread; a ctx is not thread safe.
+ *  - Limits: m a power of two, 1 <= m <= 65536; tensor order <= 12; reps <= 65536.
+ * Hash contract (the paper fixes only 2-wise bins and 4-wise signs, Sec. 2.1):
+ * SplitMix64-keyed Carter-Wegman polynomials over P = 2^61 - 1, specified in
+ * the comment of tnsk_count_sketch below.
+ */
+#ifndef TNSK_H
+#define TNSK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TNSK_OK = 0,
+    TNSK_ERR_INVALID = -1,      /* malformed network or parameters */
+    TNSK_ERR_CYCLIC = -2,       /* TNSK_ACYCLIC on a network with a cycle */
+    TNSK_ERR_UNSUPPORTED = -3,  /* valid, but outside this build's limits */
+    TNSK_ERR_CUDA = -4,         /* a CUDA runtime call failed */
+    TNSK_ERR_OOM = -5,          /* scratch allocation failed */
+    TNSK_ERR_TIMEOUT = -6,      /* a device-side bounded wait gave up */
+    TNSK_ERR_UNREACHABLE = -7   /* no parameters meet the requested error */
+} tnsk_status;
+
+typedef enum { TNSK_F64 = 0, TNSK_F32 = 1, TNSK_BF16 = 2 } tnsk_dtype;
+typedef enum { TNSK_GENERAL = 1, TNSK_ACYCLIC = 2 } tnsk_method;
+/* Arithmetic of the sketches and transforms. FP32: sketches, FFTs and products in
+ * FP32 (per-tensor power-of-two scaling), per-rep estimates and combination in
+ * FP64. FP64: everything in FP64 (for high-dynamic-range sketches). */
+typedef enum { TNSK_PREC_FP32 = 0, TNSK_PREC_FP64 = 2 } tnsk_precision;
+
+typedef struct tnsk_ctx tnsk_ctx;
+
+typedef struct {
+    int32_t order;          /* q_k >= 0 (0 = scalar) */
+    const int64_t* dims;    /* [order] host */
+    const void* data;       /* device, row-major, numel = prod dims */
+    tnsk_dtype dtype;
+} tnsk_tensor;
+
+typedef struct {
+    int32_t p;              /* number of tensors, >= 1 */
+    const tnsk_tensor* X;   /* [p] host */
+    int32_t t;              /* |E| */
+    const int32_t* edges;   /* [2t] host: pairs (u, v) of global mode ids; the
+                               first mode u gets the count sketch C, v its
+                               complement C' (Sec. 4.2) */
+    int32_t n_open;         /* |K'| */
+    const int32_t* open;    /* [n_open] host: permutation of K' giving the output
+                               mode order; output is row-major over it */
+} tnsk_network;
+
+typedef struct {
+    int64_t m;              /* sketch size */
+    int32_t reps;           /* independent repetitions R */
+    int32_t groups;         /* median of `groups` group means; 1 = plain mean */
+    uint64_t seed;          /* hash seed */
+    tnsk_method method;
+    int32_t root;           /* method 2 root tensor; -1 = the tensor with the
+                               fewest entries (lowest index on ties) */
+    tnsk_precision prec;
+} tnsk_params;
+
+/* Create a context on `device` whose work goes to `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream). */
+tnsk_status tnsk_create(tnsk_ctx** ctx, int device, void* cuda_stream);
+/* Wait for the ctx's work, free its scratch and the ctx. */
+tnsk_status tnsk_destroy(tnsk_ctx* ctx);
+/* Rebind the ctx to another stream of the same device. */
+tnsk_status tnsk_set_stream(tnsk_ctx* ctx, void* cuda_stream);
+
+/* Count sketch table of the hash contract (Sec. 2.1, Def. "Count sketch") for
+ * repetition `rep` and table id `tid`:
+ *   sm(x)    SplitMix64 output for state x; K = sm(sm(sm(seed) ^ rep) ^ tid);
+ *   c(r,j) = sm(K ^ (8r + j)) folded into [0, P), P = 2^61 - 1;
+ *   bins[i]  = ((c(0,1) i + c(0,0)) mod P) mod m                  (2-wise)
+ *   signs[i] = +1 if (c(1,3) i^3 + c(1,2) i^2 + c(1,1) i + c(1,0)) mod P is even,
+ *              -1 otherwise                                       (4-wise)
+ * Table ids: method 1 edge e: (1<<56)|e; method 2 edge e: (2<<56)|e; method 2
+ * padding slot j of tensor k: (3<<56)|(k<<24)|j; method 2 tensor sketch T_{2^l,j}
+ * side s of tensor k: (4<<56)|(k<<24)|(l<<16)|(j<<1)|s.
+ * bins: device int32[n]; signs: device int8[n]. */
+tnsk_status tnsk_count_sketch(tnsk_ctx* ctx, uint64_t seed, uint64_t rep, uint64_t tid, int64_t n,
+                              int64_t m, int32_t* bins, int8_t* signs);
+
+/* Method-1 sketches x_k = T_k vec(X_k) of every tensor (Eq. 1; Alg. 1 "x_k <- T_k
+ * vec(X_k)"; hash form of Alg. 3) for reps 0..R-1 of params. Output x: device,
+ * float (FP32) or double (FP64) by params->prec, laid out [R][sum_k O_k m] with
+ * tensor k's block [O_k][m] (O_k = product of its open dims, row-major in the
+ * tensor's mode order), blocks in tensor order. */
+tnsk_status tnsk_m1_sketch(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, void* x);
+
+/* Estimate tc(X, E): out = device double[prod of open dims] (1 entry if full);
+ * per_rep = device double[R][prod open dims] or NULL. */
+tnsk_status tnsk_estimate(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, double* out,
+                          double* per_rep);
+
+/* B networks in one batch (one launch sequence for all). params[b], outs[b],
+ * per_reps[b] (may be NULL, or hold NULL entries) as in tnsk_estimate. */
+tnsk_status tnsk_estimate_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
+                                double* const* outs, double* const* per_reps);
+
+/* Per-kernel timing. While enabled, every kernel launch of the ctx is bracketed
+ * by CUDA events recorded on the ctx stream. tnsk_profile_read waits for the
+ * stream, writes the summed device time (ms) and the launch count of each kernel
+ * kind (arrays of TNSK_KERNEL_KINDS entries, indexed by tnsk_kernel_kind) and
+ * clears the records. Timing adds no synchronisation to the launch sequence. */
+typedef enum {
+    TNSK_K_TABLES = 0,      /* hash tables of all reps (a1) */
+    TNSK_K_M1_SCATTER = 1,  /* method 1 signed scatter-add (a2) */
+    TNSK_K_M1_SPECTRUM = 2, /* method 1 FFT, Hadamard product, bin sum (a3, a4) */
+    TNSK_K_M2_LEAF = 3,     /* method 2 leaf count sketches (a5) */
+    TNSK_K_M2_COMPOSE = 4,  /* method 2 Q_k composition (a6) */
+    TNSK_K_M2_VBUILD = 5,   /* method 2 recursive-sketch columns (a7) */
+    TNSK_K_M2_GEMM = 6,     /* method 2 sketched matrix-vector products (a7) */
+    TNSK_K_M2_ROOT = 7,     /* method 2 root inner products (a8) */
+    TNSK_K_COMBINE = 8,     /* median of group means (a9) */
+    TNSK_KERNEL_KINDS = 9
+} tnsk_kernel_kind;
+tnsk_status tnsk_profile(tnsk_ctx* ctx, int32_t enable);
+tnsk_status tnsk_profile_read(tnsk_ctx* ctx, double* ms, int64_t* launches);
+
+/* Wait for the ctx's stream; returns the first deferred device error, if any. */
+tnsk_status tnsk_sync(tnsk_ctx* ctx);
+
+const char* tnsk_status_string(tnsk_status s);
+/* Text of the last error on this ctx ("" if none). */
+const char* tnsk_last_error(tnsk_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNSK_H */

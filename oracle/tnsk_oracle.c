@@ -438,7 +438,6 @@ typedef struct {
     netinfo in;
     tnode* node;
     int64_t m;
-    int abs_mode;
     /* tables of the current rep */
     const int64_t* ebins;   /* [L] edge count sketches C_{k,l} */
     const int8_t* esigns;
@@ -488,10 +487,10 @@ static void rsh(const m2ctx* cx, int32_t k, const int64_t* slot_idx, int64_t* b,
             int32_t e = nd->child_edge[j];
             int64_t pos = cx->in.eoff[e] + slot_idx[j];
             b[j] = cx->ebins[pos];
-            if (!cx->abs_mode) sigma *= cx->esigns[pos];
+            sigma *= cx->esigns[pos];
         } else {
             b[j] = cx->pad_bin[k][j];
-            if (!cx->abs_mode) sigma *= cx->pad_sign[k][j];
+            sigma *= cx->pad_sign[k][j];
         }
     }
     for (int32_t l = nd->qt; l >= 2; l >>= 1) {
@@ -500,7 +499,7 @@ static void rsh(const m2ctx* cx, int32_t k, const int64_t* slot_idx, int64_t* b,
             const int64_t* hb = cx->t_bin[k] + t_off(nd->qt, l, j, 1, m);
             const int8_t* sa = cx->t_sign[k] + t_off(nd->qt, l, j, 0, m);
             const int8_t* sb = cx->t_sign[k] + t_off(nd->qt, l, j, 1, m);
-            if (!cx->abs_mode) sigma *= sa[b[2 * j]] * sb[b[2 * j + 1]];
+            sigma *= sa[b[2 * j]] * sb[b[2 * j + 1]];
             b[j] = (ha[b[2 * j]] + hb[b[2 * j + 1]]) % m;
         }
     }
@@ -533,12 +532,11 @@ static double* sketched_matvec(const m2ctx* cx, int32_t l, const double* z) {
         int64_t ipar = idx[nd->parent_mode];
         int64_t pos = cx->in.eoff[nd->parent_edge] + ipar;
         int64_t j = cx->ebins[pos];
-        int64_t s = cx->abs_mode ? 1 : cx->esigns[pos];
+        int64_t s = cx->esigns[pos];
         slot_values(cx, l, idx, sidx);
         int64_t sigma, bb;
         rsh(cx, l, sidx, b, &sigma, &bb);
         double v = net->data[l][f];
-        if (cx->abs_mode) v = fabs(v);
         y[j] += v * z[bb] * (double)sigma * (double)s;
     }
     free(idx);
@@ -556,7 +554,7 @@ static double* tensor_sketch_pair(const m2ctx* cx, const int64_t* ha, const int8
     for (int64_t a = 0; a < m; ++a) {
         if (u[a] == 0.0) continue;
         for (int64_t c = 0; c < m; ++c) {
-            double sg = cx->abs_mode ? 1.0 : (double)(sa[a] * sb[c]);
+            double sg = (double)(sa[a] * sb[c]);
             out[(ha[a] + hb[c]) % m] += sg * u[a] * v[c];
         }
     }
@@ -583,7 +581,7 @@ static double* neighbors_sketch(const m2ctx* cx, int32_t k) {
             free(rl);
         } else {
             x[j] = (double*)calloc((size_t)m, sizeof(double));
-            x[j][cx->pad_bin[k][j]] = cx->abs_mode ? 1.0 : (double)cx->pad_sign[k][j];
+            x[j][cx->pad_bin[k][j]] = (double)cx->pad_sign[k][j];
         }
     }
     /* Q_k = Q_2 Q_4 ... Q_qt: apply level qt first, then qt/2, ..., 2 */
@@ -723,8 +721,7 @@ int orc_m2_estimate(const orc_net* net, int32_t root, int64_t m, int32_t R, uint
                                          cx.t_sign[k] + o);
                     }
         }
-        for (int pass = 0; pass < (s_out ? 2 : 1); ++pass) {
-            cx.abs_mode = pass;
+        {
             /* x_o = R_o vec(X_o): scatter every component of the root by Alg. 4 */
             const tnode* nd = &cx.node[root];
             int32_t qo = net->order[root];
@@ -738,18 +735,20 @@ int orc_m2_estimate(const orc_net* net, int32_t root, int64_t m, int32_t R, uint
                 int64_t sigma, bb;
                 rsh(&cx, root, sidx, b, &sigma, &bb);
                 double v = net->data[root][f];
-                if (cx.abs_mode) v = fabs(v);
                 xo[bb] += (double)sigma * v;
             }
             /* r_o = NeighborsSketch(o); y = x_o^T r_o */
             double* ro = neighbors_sketch(&cx, root);
             int64_t len = nd->c == 0 ? 1 : m;
-            double y = 0;
-            for (int64_t j = 0; j < len; ++j) y += xo[j] * ro[j];
-            if (pass == 0)
-                y_out[r] = y;
-            else
-                s_out[r] = y;
+            double y = 0, nx = 0, nr = 0;
+            for (int64_t j = 0; j < len; ++j) {
+                y += xo[j] * ro[j];
+                nx += xo[j] * xo[j];
+                nr += ro[j] * ro[j];
+            }
+            y_out[r] = y;
+            /* scale for tolerances: |y| <= ||x_o|| ||r_o|| (Cauchy-Schwarz) */
+            if (s_out) s_out[r] = sqrt(nx) * sqrt(nr);
             free(ro);
             free(xo);
             free(idx);

@@ -81,7 +81,8 @@ int orc_m1_estimate(const orc_net* net, int64_t m, int32_t R, const int64_t* bin
 
 /* Method 2 (Alg. 2 with Alg. 4 and Alg. 5) for an acyclic full network rooted at
  * `root`. Edge count sketches may be overridden ([R][L], same layout as method 1).
- * s_out = the same recursion on |X| with every sign +1 (a scale for tolerances). */
+ * s_out = ||x_o||_2 ||r_o||_2, the Cauchy-Schwarz bound of y = x_o^T r_o (Alg. 2
+ * last line), used as the scale of rounding tolerances. */
 int orc_m2_estimate(const orc_net* net, int32_t root, int64_t m, int32_t R, uint64_t seed,
                     const int64_t* edge_bins, const int8_t* edge_signs,
                     double* y_out, double* s_out);

@@ -1,0 +1,364 @@
+// api.cu -- host side of the libtnsk C ABI: validation of the network and the
+// parameters (Def. "Tensor contraction": u != v, n_u = n_v), planning of the
+// launches, scratch management and error reporting. Every arithmetic step of
+// the estimators runs in the kernels; the host only lays out descriptors.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "method2.cuh"
+#include "plan.cuh"
+
+using namespace tnsk;
+
+struct tnsk_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    tnsk_status deferred = TNSK_OK;
+    // scratch arena, grown on demand, reused by every call (stream ordered)
+    unsigned char* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    // twiddles tw[k] = exp(-2 pi i k/m), k < m/2, for m = 2^l, l = 0..16
+    void* tw32[17] = {};
+    void* tw64[17] = {};
+    const void** d_tw32 = nullptr;  // device arrays of the pointers above
+    const void** d_tw64 = nullptr;
+    int* d_err = nullptr;  // device error word
+    Profiler prof;
+};
+
+namespace {
+
+tnsk_status fail(tnsk_ctx* ctx, tnsk_status st, const std::string& msg) {
+    if (ctx) ctx->last_error = msg;
+    return st;
+}
+
+tnsk_status cuda_fail(tnsk_ctx* ctx, cudaError_t e, const char* where) {
+    return fail(ctx, TNSK_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define TNSK_CUDA(call)                                       \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+tnsk_status ensure_scratch(tnsk_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->scratch_bytes) return TNSK_OK;
+    size_t want = std::max(bytes, ctx->scratch_bytes + ctx->scratch_bytes / 2);
+    want = (want + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
+    if (ctx->scratch) {
+        // earlier work on the stream may still read the old arena
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+        cudaFree(ctx->scratch);
+        ctx->scratch = nullptr;
+        ctx->scratch_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc((void**)&ctx->scratch, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, TNSK_ERR_OOM, "scratch allocation of " + std::to_string(want) + " bytes failed");
+    }
+    ctx->scratch_bytes = want;
+    return TNSK_OK;
+}
+
+tnsk_status ensure_twiddles(tnsk_ctx* ctx) {
+    if (ctx->d_tw32) return TNSK_OK;
+    size_t total32 = 0, total64 = 0;
+    for (int l = 0; l <= 16; ++l) {
+        size_t M = l > 0 ? ((size_t)1 << (l - 1)) : 1;
+        total32 += M * sizeof(float) * 2;
+        total64 += M * sizeof(double) * 2;
+    }
+    std::vector<float> h32;
+    std::vector<double> h64;
+    h32.reserve(total32 / 4);
+    h64.reserve(total64 / 8);
+    std::vector<size_t> off32, off64;
+    for (int l = 0; l <= 16; ++l) {
+        size_t m = (size_t)1 << l;
+        size_t M = l > 0 ? m / 2 : 1;
+        off32.push_back(h32.size());
+        off64.push_back(h64.size());
+        for (size_t k = 0; k < M; ++k) {
+            // exact argument reduction by symmetry keeps the table within an ulp
+            double a = -2.0 * M_PI * (double)k / (double)m;
+            double c = std::cos(a), s = std::sin(a);
+            h32.push_back((float)c);
+            h32.push_back((float)s);
+            h64.push_back(c);
+            h64.push_back(s);
+        }
+    }
+    void* d32 = nullptr;
+    void* d64 = nullptr;
+    TNSK_CUDA(cudaMalloc(&d32, h32.size() * sizeof(float)));
+    TNSK_CUDA(cudaMalloc(&d64, h64.size() * sizeof(double)));
+    TNSK_CUDA(cudaMemcpy(d32, h32.data(), h32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    TNSK_CUDA(cudaMemcpy(d64, h64.data(), h64.size() * sizeof(double), cudaMemcpyHostToDevice));
+    const void* p32[17];
+    const void* p64[17];
+    for (int l = 0; l <= 16; ++l) {
+        ctx->tw32[l] = (float*)d32 + off32[l];
+        ctx->tw64[l] = (double*)d64 + off64[l];
+        p32[l] = ctx->tw32[l];
+        p64[l] = ctx->tw64[l];
+    }
+    TNSK_CUDA(cudaMalloc((void**)&ctx->d_tw32, sizeof(p32)));
+    TNSK_CUDA(cudaMalloc((void**)&ctx->d_tw64, sizeof(p64)));
+    TNSK_CUDA(cudaMemcpy(ctx->d_tw32, p32, sizeof(p32), cudaMemcpyHostToDevice));
+    TNSK_CUDA(cudaMemcpy(ctx->d_tw64, p64, sizeof(p64), cudaMemcpyHostToDevice));
+    return TNSK_OK;
+}
+
+tnsk_status check_ctx(tnsk_ctx* ctx) {
+    if (!ctx) return TNSK_ERR_INVALID;
+    if (ctx->deferred != TNSK_OK) {
+        tnsk_status s = ctx->deferred;
+        ctx->deferred = TNSK_OK;
+        return s;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    return TNSK_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Arena: carve typed regions out of the ctx scratch, then upload host staging.
+// ---------------------------------------------------------------------------
+namespace tnsk {
+
+size_t Arena::take(size_t bytes, size_t align) {
+    size_t at = (used + align - 1) / align * align;
+    used = at + bytes;
+    return at;
+}
+
+}  // namespace tnsk
+
+extern "C" {
+
+tnsk_status tnsk_create(tnsk_ctx** out, int device, void* cuda_stream) {
+    if (!out) return TNSK_ERR_INVALID;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return TNSK_ERR_CUDA;
+    }
+    tnsk_ctx* ctx = new tnsk_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    if (cudaSetDevice(device) != cudaSuccess || cudaMalloc((void**)&ctx->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return TNSK_ERR_CUDA;
+    }
+    if (ensure_twiddles(ctx) != TNSK_OK) {
+        delete ctx;
+        return TNSK_ERR_CUDA;
+    }
+    *out = ctx;
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_destroy(tnsk_ctx* ctx) {
+    if (!ctx) return TNSK_ERR_INVALID;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->tw32[0]) cudaFree(ctx->tw32[0]);
+    if (ctx->tw64[0]) cudaFree(ctx->tw64[0]);
+    if (ctx->d_tw32) cudaFree(ctx->d_tw32);
+    if (ctx->d_tw64) cudaFree(ctx->d_tw64);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    delete ctx;
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_set_stream(tnsk_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return TNSK_ERR_INVALID;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_sync(tnsk_ctx* ctx) {
+    if (!ctx) return TNSK_ERR_INVALID;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    int err = 0;
+    e = cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy(err)");
+    if (err != DEVERR_NONE) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        if (err == DEVERR_TIMEOUT) return fail(ctx, TNSK_ERR_TIMEOUT, "a device-side wait gave up");
+        return fail(ctx, TNSK_ERR_INVALID, "a device-side bounds check failed");
+    }
+    if (ctx->deferred != TNSK_OK) {
+        tnsk_status s = ctx->deferred;
+        ctx->deferred = TNSK_OK;
+        return s;
+    }
+    return TNSK_OK;
+}
+
+const char* tnsk_status_string(tnsk_status s) {
+    switch (s) {
+        case TNSK_OK: return "TNSK_OK";
+        case TNSK_ERR_INVALID: return "TNSK_ERR_INVALID";
+        case TNSK_ERR_CYCLIC: return "TNSK_ERR_CYCLIC";
+        case TNSK_ERR_UNSUPPORTED: return "TNSK_ERR_UNSUPPORTED";
+        case TNSK_ERR_CUDA: return "TNSK_ERR_CUDA";
+        case TNSK_ERR_OOM: return "TNSK_ERR_OOM";
+        case TNSK_ERR_TIMEOUT: return "TNSK_ERR_TIMEOUT";
+        case TNSK_ERR_UNREACHABLE: return "TNSK_ERR_UNREACHABLE";
+    }
+    return "TNSK_UNKNOWN";
+}
+
+const char* tnsk_last_error(tnsk_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+tnsk_status tnsk_count_sketch(tnsk_ctx* ctx, uint64_t seed, uint64_t rep, uint64_t tid, int64_t n, int64_t m,
+                              int32_t* bins, int8_t* signs) {
+    tnsk_status st = check_ctx(ctx);
+    if (st != TNSK_OK) return st;
+    if (n < 0 || m < 1 || m > TNSK_MAX_M || (m & (m - 1)) || (n > 0 && (!bins || !signs)))
+        return fail(ctx, TNSK_ERR_INVALID, "count_sketch: need n >= 0, m a power of two <= 65536, buffers");
+    TNSK_CUDA(launch_count_sketch(seed, rep, tid, n, m, bins, signs, ctx->stream));
+    return TNSK_OK;
+}
+
+// Batch driver shared by tnsk_estimate, tnsk_estimate_batch and tnsk_m1_sketch.
+static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
+                             double* const* outs, double* const* per_reps, void* sketch_out) {
+    tnsk_status st = check_ctx(ctx);
+    if (st != TNSK_OK) return st;
+    if (B < 0 || (B > 0 && (!nets || !params))) return fail(ctx, TNSK_ERR_INVALID, "null batch arguments");
+    if (B == 0) return TNSK_OK;
+    std::vector<NetInfo> infos(B);
+    for (int b = 0; b < B; ++b) {
+        std::string why;
+        st = validate(nets[b], params[b], infos[b], why);
+        if (st != TNSK_OK) return fail(ctx, st, "network " + std::to_string(b) + ": " + why);
+        if (!sketch_out && (!outs || !outs[b])) return fail(ctx, TNSK_ERR_INVALID, "null output buffer");
+    }
+    // precision of the whole batch: one kind per launch sequence
+    const bool fp64 = params[0].prec == TNSK_PREC_FP64;
+    for (int b = 1; b < B; ++b)
+        if ((params[b].prec == TNSK_PREC_FP64) != fp64)
+            return fail(ctx, TNSK_ERR_UNSUPPORTED, "mixed precisions in one batch");
+
+    BatchPlan plan;
+    st = plan_batch(infos, nets, params, outs, per_reps, fp64, sketch_out != nullptr, plan, ctx->last_error);
+    if (st != TNSK_OK) return st;
+    st = ensure_scratch(ctx, plan.arena.used);
+    if (st != TNSK_OK) return st;
+    unsigned char* base = ctx->scratch;
+    cudaStream_t s = ctx->stream;
+    // descriptors (pageable host staging: the copy is complete on return)
+    if (!plan.host_desc.empty())
+        TNSK_CUDA(cudaMemcpyAsync(base + plan.desc_off, plan.host_desc.data(), plan.host_desc.size(),
+                                  cudaMemcpyHostToDevice, s));
+    if (plan.zero_bytes) TNSK_CUDA(cudaMemsetAsync(base + plan.zero_off, 0, plan.zero_bytes, s));
+    if (sketch_out && plan.sketch_user_bytes) TNSK_CUDA(cudaMemsetAsync(sketch_out, 0, plan.sketch_user_bytes, s));
+    Profiler& pf = ctx->prof;
+    if (plan.n_reqs) {
+        pf.begin(TNSK_K_TABLES, s);
+        TNSK_CUDA(launch_draw_tables((const TabReq*)(base + plan.reqs_off), plan.n_reqs, plan.n_table_words,
+                                     (uint32_t*)(base + plan.tabs_off), s));
+        pf.end(s);
+    }
+    if (plan.m1.n_nets) {
+        void* xs = sketch_out ? sketch_out : (void*)(base + plan.m1.xs_off);
+        pf.begin(TNSK_K_M1_SCATTER, s);
+        TNSK_CUDA(launch_m1_scatter((const M1Tensor*)(base + plan.m1.tens_off), (const M1Net*)(base + plan.m1.nets_off),
+                                    (const M1Work*)(base + plan.m1.work_off), plan.m1.n_work,
+                                    (const uint32_t*)(base + plan.tabs_off), xs, fp64, plan.m1.scatter_smem,
+                                    plan.m1.idx32, s));
+        pf.end(s);
+        if (!sketch_out) {
+            pf.begin(TNSK_K_M1_SPECTRUM, s);
+            TNSK_CUDA(launch_m1_spectrum((const M1Tensor*)(base + plan.m1.tens_off),
+                                         (const M1Net*)(base + plan.m1.nets_off),
+                                         (const OpenMode*)(base + plan.m1.opens_off),
+                                         (const int2*)(base + plan.m1.items_off), plan.m1.n_items, xs,
+                                         fp64 ? (const void* const*)ctx->d_tw64 : (const void* const*)ctx->d_tw32,
+                                         base + plan.m1.spec_off, (int*)(base + plan.m1.sexp_off),
+                                         (double*)(base + plan.yrep_off), fp64, plan.m1.max_log2m, s));
+            pf.end(s);
+        }
+    }
+    if (plan.m2.n_nets && !sketch_out) {
+        st = run_method2(plan, base, fp64, fp64 ? (const void* const*)ctx->d_tw64 : (const void* const*)ctx->d_tw32,
+                         s, pf, ctx->last_error);
+        if (st != TNSK_OK) return st;
+    }
+    if (!sketch_out && plan.n_comb) {
+        pf.begin(TNSK_K_COMBINE, s);
+        TNSK_CUDA(launch_combine((const CombineItem*)(base + plan.comb_off), plan.n_comb,
+                                 (const double*)(base + plan.yrep_off), s));
+        pf.end(s);
+    }
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_profile(tnsk_ctx* ctx, int32_t enable) {
+    if (!ctx) return TNSK_ERR_INVALID;
+    ctx->prof.on = enable != 0;
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_profile_read(tnsk_ctx* ctx, double* ms, int64_t* launches) {
+    if (!ctx || !ms || !launches) return TNSK_ERR_INVALID;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    for (int k = 0; k < TNSK_KERNEL_KINDS; ++k) {
+        ms[k] = 0;
+        launches[k] = 0;
+    }
+    for (auto& r : ctx->prof.recs) {
+        float t = 0;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess && r.kind >= 0 && r.kind < TNSK_KERNEL_KINDS) {
+            ms[r.kind] += t;
+            launches[r.kind] += 1;
+        }
+        ctx->prof.pool.push_back(r.a);
+        ctx->prof.pool.push_back(r.b);
+    }
+    ctx->prof.recs.clear();
+    cudaGetLastError();
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_estimate(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, double* out,
+                          double* per_rep) {
+    if (!ctx || !net || !params) return TNSK_ERR_INVALID;
+    return run_batch(ctx, 1, net, params, &out, &per_rep, nullptr);
+}
+
+tnsk_status tnsk_estimate_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
+                                double* const* outs, double* const* per_reps) {
+    if (!ctx) return TNSK_ERR_INVALID;
+    return run_batch(ctx, B, nets, params, outs, per_reps, nullptr);
+}
+
+tnsk_status tnsk_m1_sketch(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, void* x) {
+    if (!ctx || !net || !params) return TNSK_ERR_INVALID;
+    if (params->method != TNSK_GENERAL) return fail(ctx, TNSK_ERR_INVALID, "m1_sketch needs TNSK_GENERAL");
+    if (!x) return fail(ctx, TNSK_ERR_INVALID, "null sketch buffer");
+    return run_batch(ctx, 1, net, params, nullptr, nullptr, x);
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// fft.cuh -- block-cooperative shared-memory FFTs used by both estimators.
+//
+// A real sketch x of length m = 2M is transformed as M complex values
+// z[n] = x[2n] + i x[2n+1] by an in-place radix-2 decimation-in-frequency FFT
+// (output in bit-reversed order), then unpacked to the half spectrum
+// X[k], k = 0..M, of the unnormalised DFT F_{jk} = exp(-2 pi i jk/m) (Sec. 2).
+// The estimators only need products of spectra at equal frequencies and their
+// sum, so the bit-reversed order is never undone for them.
+#pragma once
+
+#include "common.cuh"
+
+namespace tnsk {
+
+template <typename T>
+__device__ __forceinline__ Cplx<T> cmul(Cplx<T> a, Cplx<T> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ Cplx<T> cadd(Cplx<T> a, Cplx<T> b) {
+    return {a.x + b.x, a.y + b.y};
+}
+template <typename T>
+__device__ __forceinline__ Cplx<T> csub(Cplx<T> a, Cplx<T> b) {
+    return {a.x - b.x, a.y - b.y};
+}
+template <typename T>
+__device__ __forceinline__ Cplx<T> cconj(Cplx<T> a) {
+    return {a.x, -a.y};
+}
+
+__device__ __forceinline__ int bitrev(int k, int log2M) {
+    return log2M == 0 ? 0 : (int)(__brev((unsigned)k) >> (32 - log2M));
+}
+
+// In-place DIF FFT of nb consecutive length-M complex arrays in shared memory.
+// tw[k] = exp(-2 pi i k / (2M)), k < M (the twiddles of the real length-2M
+// transform; W_M^j = tw[2j]). Natural order in, bit-reversed order out.
+// Must be called by all threads of the block; ends with __syncthreads().
+template <typename T>
+__device__ void block_fft_dif(Cplx<T>* z, int nb, int log2M, const Cplx<T>* __restrict__ tw) {
+    const int M = 1 << log2M;
+    if (log2M == 0) {
+        __syncthreads();
+        return;
+    }
+    const int lhb = log2M - 1;  // log2 of butterflies per array
+    const int total = nb << lhb;
+    for (int s = 0; s < log2M; ++s) {
+        const int lhalf = log2M - s - 1;
+        const int half = 1 << lhalf;
+        const int tstride = 1 << (s + 1);
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            const int b = t >> lhb;
+            const int u = t & ((1 << lhb) - 1);
+            const int grp = u >> lhalf;
+            const int j = u & (half - 1);
+            const int i0 = (b << log2M) + (grp << (lhalf + 1)) + j;
+            const int i1 = i0 + half;
+            Cplx<T> a = z[i0], c = z[i1];
+            z[i0] = cadd(a, c);
+            Cplx<T> w = tw[j * tstride];
+            z[i1] = cmul(csub(a, c), w);
+        }
+        __syncthreads();
+    }
+    (void)M;
+}
+
+// Half-spectrum bin k (0..M) of the real sequence whose packed transform Z sits
+// bit-reversed in z (one array of length M).
+template <typename T>
+__device__ __forceinline__ Cplx<T> unpack_bin(const Cplx<T>* z, int k, int log2M, const Cplx<T>* __restrict__ tw) {
+    const int M = 1 << log2M;
+    Cplx<T> zk = z[bitrev(k & (M - 1), log2M)];
+    Cplx<T> zc = cconj(z[bitrev((M - k) & (M - 1), log2M)]);
+    Cplx<T> e = {(zk.x + zc.x) * T(0.5), (zk.y + zc.y) * T(0.5)};
+    Cplx<T> d = csub(zk, zc);
+    Cplx<T> o = {d.y * T(0.5), -d.x * T(0.5)};  // (Zk - conj Z_{M-k}) / (2i)
+    Cplx<T> w = (k < M) ? tw[k] : Cplx<T>{T(-1), T(0)};
+    return cadd(e, cmul(w, o));
+}
+
+}  // namespace tnsk

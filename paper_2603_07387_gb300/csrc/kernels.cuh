@@ -1,0 +1,71 @@
+// kernels.cuh -- launchers of the libtnsk kernels (host-callable).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace tnsk {
+
+// Optional per-launch CUDA-event timing (tnsk_profile). begin/end bracket one
+// launch on the stream; events come from a reusable pool.
+struct Profiler {
+    bool on = false;
+    struct Rec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void begin(int kind, cudaStream_t s) {
+        if (!on) return;
+        Rec r{kind, get(), get()};
+        cudaEventRecord(r.a, s);
+        recs.push_back(r);
+    }
+    void end(cudaStream_t s) {
+        if (!on || recs.empty()) return;
+        cudaEventRecord(recs.back().b, s);
+    }
+    ~Profiler() {
+        for (auto& r : recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+struct CombineItem {  // one output entry of one network
+    int64_t y_off;    // per-rep estimates [R][O]
+    int64_t O;
+    int64_t o;
+    int32_t R;
+    int32_t groups;
+    double* out;
+    double* per_rep;  // optional [R][O]
+};
+
+cudaError_t launch_draw_tables(const TabReq* d_reqs, int nreq, int64_t total, uint32_t* d_out, cudaStream_t s);
+cudaError_t launch_count_sketch(uint64_t seed, uint64_t rep, uint64_t tid, int64_t n, int64_t m, int32_t* bins,
+                                int8_t* signs, cudaStream_t s);
+cudaError_t launch_m1_scatter(const M1Tensor* d_tens, const M1Net* d_nets, const M1Work* d_work, int n_work,
+                              const uint32_t* d_tabs, void* d_xs, bool fp64, size_t smem, bool idx32,
+                              cudaStream_t s);
+cudaError_t launch_m1_spectrum(const M1Tensor* d_tens, const M1Net* d_nets, const OpenMode* d_opens,
+                               const int2* d_items, int n_items, const void* d_xs, const void* const* d_tws,
+                               void* d_spec, int* d_sexp, double* d_yrep, bool fp64, int max_log2m,
+                               cudaStream_t s);
+cudaError_t launch_combine(const CombineItem* d_items, int n_items, const double* d_yrep, cudaStream_t s);
+
+}  // namespace tnsk

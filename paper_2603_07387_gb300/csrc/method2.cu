@@ -1,0 +1,382 @@
+// method2.cu -- method 2 of the paper (Sec. 4.4): recursive sketches on the
+// rooted tree, evaluated leaves to root (Alg. 2), with the sign and row of a
+// recursive-sketch column from Alg. 4 and the fused sketch / matrix-vector
+// product of Alg. 5 batched over repetitions.
+//
+//   a5  m2_leaf_kernel     x_l = C_{k,l} vec(X_l) for the leaves
+//   a6  m2_compose_kernel  r_k = Q_k((x) x_l): per level l = qt..2 and pair j,
+//                          T_{l,j}(u (x) v) = F^{-1}(F C_a u o F C_b v) (Def.
+//                          "Tensor sketch" of order 2) by shared-memory FFTs
+//   a7  m2_vbuild_kernel   V(col, r) = sigma_r(col) r_k[r][b_r(col)] (Alg. 4)
+//       m2_gemm_kernel     x_k[r] += C_{par,k} (mat(X_k) V)[:, r]  (Alg. 5 for all
+//                          reps at once: each entry of X_k is read once per
+//                          batch of 64 reps)
+//   a8  m2_root_kernel     y_r = sum_i X_o(i) sigma_r(i) r_o[r][b_r(i)] = x_o^T r_o
+#include "fft.cuh"
+#include "kernels.cuh"
+#include "method2.cuh"
+#include "plan.cuh"
+
+namespace tnsk {
+
+// Sign and row of the recursive sketch R_k for one column (Alg. 4). `slot[j]`
+// holds the packed base word of slot j (child count sketch C_{k,l} at the
+// child-mode index, or the padding slot's word at index 0); levels l = qt..2
+// combine pairs by TensorSketchHash (Alg. 3) with T_{l,j}.
+__device__ __forceinline__ void rsh_reduce(uint32_t (&b)[TNSK_MAX_SLOTS], uint32_t& neg, int qt,
+                                           const uint32_t* __restrict__ ttab, int64_t m, uint32_t mask) {
+#pragma unroll
+    for (int lv = TNSK_MAX_SLOTS; lv >= 2; lv >>= 1) {
+        if (lv <= qt) {
+            const int64_t before = qt - lv;  // pairs stored before level lv
+#pragma unroll
+            for (int j = 0; j < lv / 2; ++j) {
+                const uint32_t* ta = ttab + ((before + j) * 2 + 0) * m;
+                const uint32_t* tb = ttab + ((before + j) * 2 + 1) * m;
+                uint32_t wa = ta[b[2 * j]];
+                uint32_t wb = tb[b[2 * j + 1]];
+                neg ^= wa ^ wb;
+                b[j] = (wa + wb) & mask;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a5: leaves
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) m2_leaf_kernel(const M2Node* __restrict__ nodes, const M2Net* __restrict__ nets,
+                                                      const M2Item* __restrict__ items,
+                                                      const uint32_t* __restrict__ tabs, T* __restrict__ ws) {
+    const M2Item it = items[blockIdx.x];
+    const M2Node& nd = nodes[it.node];
+    const M2Net& N = nets[nd.net];
+    const int R = N.R;
+    const uint32_t mask = (uint32_t)(N.m - 1);
+    const int64_t cnt = (it.end - it.begin) * R;
+    for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const int64_t i = it.begin + q / R;
+        const int r = (int)(q % R);
+        const T v = load_as<T>(nd.data, nd.dtype, i);
+        const uint32_t w = tabs[N.tab_off + (int64_t)r * N.Lrep + nd.ptab + i];
+        atomicAdd(&ws[nd.x_off + (int64_t)r * N.m + (w & mask)], (w & TNSK_SIGN_BIT) ? -v : v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a6: Q_k composition
+// ---------------------------------------------------------------------------
+// One CTA per (node, rep). Shared memory: cu [M], cv [M], Y [M+1] complex.
+template <typename T>
+__global__ void __launch_bounds__(256) m2_compose_kernel(const M2Node* __restrict__ nodes,
+                                                         const M2Net* __restrict__ nets,
+                                                         const M2Item* __restrict__ items,
+                                                         const uint32_t* __restrict__ tabs, T* __restrict__ ws,
+                                                         const Cplx<T>* const* __restrict__ tws) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const M2Item it = items[blockIdx.x];
+    const M2Node& nd = nodes[it.node];
+    const M2Net& N = nets[nd.net];
+    const int r = it.a;
+    const int64_t m = N.m;
+    const uint32_t mask = (uint32_t)(m - 1);
+    const int log2m = N.log2m;
+    const int log2M = log2m > 0 ? log2m - 1 : 0;
+    const int M = 1 << log2M;
+    const Cplx<T>* tw = tws[log2m];
+    const uint32_t* tabr = tabs + N.tab_off + (int64_t)r * N.Lrep;
+    const int qt = nd.qt;
+    Cplx<T>* cu = reinterpret_cast<Cplx<T>*>(smem_raw);
+    Cplx<T>* cv = cu + M;
+    Cplx<T>* Y = cv + M;
+    T* ru = reinterpret_cast<T*>(cu);  // real views (length 2M = m, or 1 when m = 1)
+    T* rv = reinterpret_cast<T*>(cv);
+    T* rbuf = ws + nd.r_off + (int64_t)r * (qt - 1) * m;
+    for (int lv = qt; lv >= 2; lv >>= 1) {
+        for (int j = 0; j < lv / 2; ++j) {
+            const uint32_t* ta = tabr + nd.t_tab + ((int64_t)(qt - lv + j) * 2 + 0) * m;
+            const uint32_t* tb = tabr + nd.t_tab + ((int64_t)(qt - lv + j) * 2 + 1) * m;
+            for (int64_t i = threadIdx.x; i < 2 * (int64_t)M; i += blockDim.x) {
+                ru[i] = T(0);
+                rv[i] = T(0);
+            }
+            __syncthreads();
+            // count-sketch both inputs by the sides of T_{lv,j}
+            for (int side = 0; side < 2; ++side) {
+                const int s = 2 * j + side;
+                const uint32_t* th = side ? tb : ta;
+                T* dst = side ? rv : ru;
+                if (lv == qt && s >= nd.c) {
+                    // padding slot: C_pad e_1 is a signed one-hot vector
+                    if (threadIdx.x == 0) {
+                        uint32_t pw = tabr[nd.pad_tab + s];
+                        uint32_t w = th[pw & mask];
+                        T val = ((pw ^ w) & TNSK_SIGN_BIT) ? T(-1) : T(1);
+                        atomicAdd(&dst[w & mask], val);
+                    }
+                } else {
+                    const T* src = lv == qt ? ws + nd.child_x[s] + (int64_t)r * m
+                                            : rbuf + (int64_t)(qt - 2 * lv + s) * m;
+                    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+                        T v = src[i];
+                        if (v != T(0)) {
+                            uint32_t w = th[i];
+                            atomicAdd(&dst[w & mask], (w & TNSK_SIGN_BIT) ? -v : v);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            T* out = rbuf + (int64_t)(qt - lv + j) * m;
+            if (m == 1) {
+                if (threadIdx.x == 0) out[0] = ru[0] * rv[0];
+                __syncthreads();
+                continue;
+            }
+            block_fft_dif(cu, 2, log2M, tw);  // cu and cv are adjacent
+            for (int k = threadIdx.x; k <= M; k += blockDim.x)
+                Y[k] = cmul(unpack_bin(cu, k, log2M, tw), unpack_bin(cv, k, log2M, tw));
+            __syncthreads();
+            // inverse real transform: Z[k] = E[k] + i O[k] with E = (Y[k] + conj Y[M-k]) / 2,
+            // O = (Y[k] - conj Y[M-k]) conj(W^k) / 2; z = F_M^{-1} Z = conj(F_M conj Z) / M
+            for (int k = threadIdx.x; k < M; k += blockDim.x) {
+                Cplx<T> a = Y[k], c = cconj(Y[M - k]);
+                Cplx<T> e = {(a.x + c.x) * T(0.5), (a.y + c.y) * T(0.5)};
+                Cplx<T> o = cmul(csub(a, c), cconj(tw[k]));
+                o.x *= T(0.5);
+                o.y *= T(0.5);
+                Cplx<T> z = {e.x - o.y, e.y + o.x};  // E + i O
+                cu[k] = cconj(z);
+            }
+            __syncthreads();
+            block_fft_dif(cu, 1, log2M, tw);
+            const T invM = T(1) / T(M);
+            for (int n = threadIdx.x; n < M; n += blockDim.x) {
+                Cplx<T> z = cconj(cu[bitrev(n, log2M)]);
+                out[2 * n] = z.x * invM;
+                out[2 * n + 1] = z.y * invM;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a7: V = sigma_r(col) r_k[r][b_r(col)], and the batched sketched matvec
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict__ nodes,
+                                                        const M2Net* __restrict__ nets,
+                                                        const M2Item* __restrict__ items,
+                                                        const uint32_t* __restrict__ tabs, T* __restrict__ ws) {
+    const M2Item it = items[blockIdx.x];
+    const M2Node& nd = nodes[it.node];
+    const M2Net& N = nets[nd.net];
+    const int R = N.R;
+    const int64_t m = N.m;
+    const uint32_t mask = (uint32_t)(m - 1);
+    const int order = nd.order, pmode = nd.pmode, c = nd.c, qt = nd.qt;
+    const int64_t cnt = (it.end - it.begin) * R;
+    for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const int64_t col = it.begin + q / R;
+        const int r = (int)(q % R);
+        const uint32_t* tabr = tabs + N.tab_off + (int64_t)r * N.Lrep;
+        uint32_t b[TNSK_MAX_SLOTS];
+        uint32_t neg = 0;
+        int64_t rem = col;
+#pragma unroll
+        for (int d = TNSK_MAX_ORDER - 1; d >= 0; --d) {
+            if (d < order && d != pmode) {
+                const int64_t n = nd.dims[d];
+                const int64_t qd = rem / n;
+                const int64_t i = rem - qd * n;
+                rem = qd;
+                // children are the non-parent modes in mode order
+                if (pmode >= 0 && d > pmode) {  // then d >= 1: slot d - 1
+                    const int dd = d > 0 ? d - 1 : 0;
+                    uint32_t w = tabr[nd.ctab[dd] + i];
+                    neg ^= w;
+                    b[dd] = w & mask;
+                } else {
+                    uint32_t w = tabr[nd.ctab[d] + i];
+                    neg ^= w;
+                    b[d] = w & mask;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < TNSK_MAX_SLOTS; ++j)
+            if (j >= c && j < qt) {
+                uint32_t w = tabr[nd.pad_tab + j];
+                neg ^= w;
+                b[j] = w & mask;
+            }
+        rsh_reduce(b, neg, qt, tabr + nd.t_tab, m, mask);
+        const T z = ws[nd.src_off + (int64_t)r * nd.src_stride + b[0]];
+        ws[nd.v_off + col * R + r] = (neg & TNSK_SIGN_BIT) ? -z : z;
+    }
+}
+
+// W = mat(X_k)[rows, :] V[:, reps] for a 64 x 64 tile, then x_k[r][h(i)] += s(i) W[i][r]
+// with (h, s) the count sketch C_{par,k} of the parent edge (Alg. 5 scatter).
+template <typename T>
+__global__ void __launch_bounds__(256) m2_gemm_kernel(const M2Node* __restrict__ nodes, const M2Net* __restrict__ nets,
+                                                      const M2Item* __restrict__ items,
+                                                      const uint32_t* __restrict__ tabs, T* __restrict__ ws) {
+    __shared__ __align__(16) T Xs[32][64 + 4];
+    __shared__ __align__(16) T Vs[32][64 + 4];
+    const M2Item it = items[blockIdx.x];
+    const M2Node& nd = nodes[it.node];
+    const M2Net& N = nets[nd.net];
+    const int R = N.R;
+    const int64_t m = N.m;
+    const uint32_t mask = (uint32_t)(m - 1);
+    const int64_t row0 = (int64_t)it.a * 64;
+    const int rep0 = it.b * 64;
+    const int64_t npar = nd.npar, cols = nd.cols, Bc = nd.Bc;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    const T* V = ws + nd.v_off;
+    for (int64_t k0 = 0; k0 < cols; k0 += 32) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = threadIdx.x + 256 * q;
+            const int row = e >> 5, kk = e & 31;
+            const int64_t gr = row0 + row, gc = k0 + kk;
+            T v = T(0);
+            if (gr < npar && gc < cols) {
+                int64_t flat;
+                if (nd.A == 1)
+                    flat = gr * Bc + gc;
+                else {
+                    const int64_t a = gc / Bc;
+                    flat = (a * npar + gr) * Bc + (gc - a * Bc);
+                }
+                v = load_as<T>(nd.data, nd.dtype, flat);
+            }
+            Xs[kk][row] = v;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = threadIdx.x + 256 * q;
+            const int kk = e >> 6, rr = e & 63;
+            const int64_t gc = k0 + kk;
+            Vs[kk][rr] = (gc < cols && rep0 + rr < R) ? V[gc * R + rep0 + rr] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+            T a[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = Xs[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Vs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bv[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t row = row0 + ty * 4 + i;
+        if (row >= npar) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int rep = rep0 + tx * 4 + j;
+            if (rep >= R) continue;
+            const uint32_t w = tabs[N.tab_off + (int64_t)rep * N.Lrep + nd.ptab + row];
+            const T val = acc[i][j];
+            atomicAdd(&ws[nd.x_off + (int64_t)rep * m + (w & mask)], (w & TNSK_SIGN_BIT) ? -val : val);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a8: root, y_r = sum_col X_o[col] V[col][r]
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) m2_root_kernel(const M2Node* __restrict__ nodes, const M2Net* __restrict__ nets,
+                                                      const M2Item* __restrict__ items, const T* __restrict__ ws,
+                                                      double* __restrict__ yrep) {
+    __shared__ double part[4][64];
+    const M2Item it = items[blockIdx.x];
+    const M2Node& nd = nodes[it.node];
+    const M2Net& N = nets[nd.net];
+    const int R = N.R;
+    const int lane = threadIdx.x & 63, slice = threadIdx.x >> 6;
+    const T* V = nd.v_off >= 0 ? ws + nd.v_off : nullptr;
+    for (int r0 = 0; r0 < R; r0 += 64) {
+        const int r = r0 + lane;
+        double acc = 0;
+        if (r < R)
+            for (int64_t col = it.begin + slice; col < it.end; col += 4) {
+                const T x = load_as<T>(nd.data, nd.dtype, col);
+                acc += (double)(V ? x * V[col * R + r] : x);
+            }
+        part[slice][lane] = acc;
+        __syncthreads();
+        if (slice == 0 && r < R)
+            atomicAdd(&yrep[N.y_off + r], part[0][lane] + part[1][lane] + part[2][lane] + part[3][lane]);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host driver: heights 0..H, kinds in order leaf, compose, vbuild, gemm, root
+// ---------------------------------------------------------------------------
+template <typename T>
+static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void* const* d_tws, cudaStream_t s,
+                            Profiler& prof) {
+    static const int kKind[M2_NKINDS] = {TNSK_K_M2_LEAF, TNSK_K_M2_COMPOSE, TNSK_K_M2_VBUILD, TNSK_K_M2_GEMM,
+                                         TNSK_K_M2_ROOT};
+    const M2Node* nodes = (const M2Node*)(base + P.m2.nodes_off);
+    const M2Net* nets = (const M2Net*)(base + P.m2.nets_off);
+    const M2Item* items = (const M2Item*)(base + P.m2.items_off);
+    const uint32_t* tabs = (const uint32_t*)(base + P.tabs_off);
+    T* ws = (T*)(base + P.m2.ws_off);
+    double* yrep = (double*)(base + P.yrep_off);
+    const int M = P.m2.max_log2m > 0 ? 1 << (P.m2.max_log2m - 1) : 1;
+    const size_t csmem = (size_t)(3 * M + 1) * sizeof(Cplx<T>);
+    cudaFuncSetAttribute(m2_compose_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
+    for (int h = 0; h <= P.m2.max_height; ++h) {
+        for (int kind = 0; kind < M2_NKINDS; ++kind) {
+            const int n = P.m2.count[h * M2_NKINDS + kind];
+            if (n == 0) continue;
+            const M2Item* its = items + P.m2.first[h * M2_NKINDS + kind];
+            prof.begin(kKind[kind], s);
+            switch (kind) {
+                case M2_LEAF: m2_leaf_kernel<T><<<n, 256, 0, s>>>(nodes, nets, its, tabs, ws); break;
+                case M2_COMPOSE:
+                    m2_compose_kernel<T><<<n, 256, csmem, s>>>(nodes, nets, its, tabs, ws,
+                                                                (const Cplx<T>* const*)d_tws);
+                    break;
+                case M2_VBUILD: m2_vbuild_kernel<T><<<n, 256, 0, s>>>(nodes, nets, its, tabs, ws); break;
+                case M2_GEMM: m2_gemm_kernel<T><<<n, 256, 0, s>>>(nodes, nets, its, tabs, ws); break;
+                case M2_ROOT: m2_root_kernel<T><<<n, 256, 0, s>>>(nodes, nets, its, ws, yrep); break;
+            }
+            prof.end(s);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+tnsk_status run_method2(const BatchPlan& plan, unsigned char* base, bool fp64, const void* const* d_tws,
+                        cudaStream_t s, Profiler& prof, std::string& err) {
+    cudaError_t e = fp64 ? run_m2_t<double>(plan, base, d_tws, s, prof) : run_m2_t<float>(plan, base, d_tws, s, prof);
+    if (e != cudaSuccess) {
+        err = std::string("method 2 launch: ") + cudaGetErrorString(e);
+        return TNSK_ERR_CUDA;
+    }
+    return TNSK_OK;
+}
+
+}  // namespace tnsk

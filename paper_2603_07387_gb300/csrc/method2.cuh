@@ -1,0 +1,93 @@
+// method2.cuh -- descriptors of method 2 (Sec. 4.4, Eq. 2, Alg. 2, 4, 5).
+//
+// The rooted tree is evaluated by height (leaves first). Per repetition r every
+// non-root tensor k produces x_k = C_{par,k} mat(X_k) R_k^T r_k (an m-vector;
+// Alg. 5), every tensor with children produces r_k = Q_k((x) x_l) (Alg. 2
+// NeighborsSketch), and the root gives y_r = x_o^T r_o = sum_i X_o(i) sigma(i)
+// r_o[b(i)] with (sigma, b) of R_o from Alg. 4.
+//
+// GPU layout (per batch, in the scratch arena):
+//   tables   per network and rep: [edge tables C_{k,l} (sum n_e words)]
+//            [padding-slot words (sum_k qt_k)] [T_{l,j} tables (2(qt_k-1) m words per k)]
+//   x        per non-root node: [R][m] accumulators (zeroed per call)
+//   r        per node with >= 2 children: [R][(qt-1) m] level outputs; the last
+//            m-vector of each rep is r_k
+//   V        per node with children: [cols][R]: V(col, r) = sigma_r(col) r_k[r][b_r(col)],
+//            so that x_k = scatter_C( mat(X_k) V ) is a matrix product batched over reps
+//   y        per root: [R] FP64 accumulators
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace tnsk {
+
+#define TNSK_MAX_SLOTS 16  // slots of a recursive sketch: children padded to a power of two
+
+struct M2Node {
+    const void* data;
+    int64_t numel;
+    int64_t A;        // X viewed as [A][npar][Bc]: modes before / the parent mode / after
+    int64_t npar;     // parent-mode dim (1 for the root)
+    int64_t Bc;
+    int64_t cols;     // A * Bc: product of the child-mode dims
+    int64_t ptab;     // parent edge table offset in a rep's table block (-1: root)
+    int64_t ctab[TNSK_MAX_ORDER];  // child slot j: its edge table offset
+    int64_t pad_tab;  // offset of this node's padding words (slot j at pad_tab + j)
+    int64_t t_tab;    // offset of this node's T tables
+    int64_t x_off;    // [R][m] sketch accumulators of this (non-root) node, -1 for the root
+    int64_t r_off;    // [R][(qt-1) m] composition outputs (qt >= 2), else -1
+    int64_t src_off;  // r_k used by V: r_off + (qt-2) m for qt >= 2, the child's x_off for qt = 1
+    int64_t src_stride;  // distance between reps in the r_k source
+    int64_t v_off;    // [cols][R] V matrix (nodes with children)
+    int64_t child_x[TNSK_MAX_SLOTS];  // slot j < c: the child's x_off
+    int32_t dims[TNSK_MAX_ORDER];
+    int32_t cmode[TNSK_MAX_ORDER];    // slot j < c: this node's mode toward child j
+    int32_t dtype;
+    int32_t order;
+    int32_t pmode;    // parent mode (-1 root)
+    int32_t c;        // children
+    int32_t qt;       // slots (0 for a leaf)
+    int32_t net;      // method-2 network index
+    int32_t is_root;
+    int32_t pad_;
+};
+
+struct M2Net {
+    int64_t m;
+    int64_t Lrep;     // table words per rep
+    int64_t tab_off;  // table block of rep 0
+    int64_t y_off;    // per-rep estimates [R] (FP64), inside the shared [R][O] buffer
+    int32_t log2m;
+    int32_t R;
+};
+
+// Work items (node index into the batch's node array + a chunk of its work).
+struct M2Item {
+    int32_t node;
+    int32_t a;        // first rep (compose) or row tile (gemm) or chunk index
+    int32_t b;        // rep tile (gemm)
+    int32_t pad_;
+    int64_t begin, end;  // element range (leaf / vbuild / root chunks)
+};
+
+enum M2Kind { M2_LEAF = 0, M2_COMPOSE = 1, M2_VBUILD = 2, M2_GEMM = 3, M2_ROOT = 4, M2_NKINDS = 5 };
+
+struct M2Plan {
+    int n_nets = 0;
+    size_t nodes_off = 0, nets_off = 0, items_off = 0;
+    size_t ws_off = 0;  // x / r / V / y workspace base (all offsets above are relative to it)
+    int max_height = -1;
+    int max_log2m = 0;
+    // per height, per kind: [first, count) into the item array
+    std::vector<int> first, count;  // size (max_height+1) * M2_NKINDS
+};
+
+struct BatchPlan;
+struct Profiler;
+tnsk_status run_method2(const BatchPlan& plan, unsigned char* base, bool fp64, const void* const* d_tws,
+                        cudaStream_t s, Profiler& prof, std::string& err);
+
+}  // namespace tnsk

@@ -1,0 +1,708 @@
+// plan.cu -- validation of a network against the statement of the problem
+// (Sec. 1 Def. "Tensor contraction": u != v and n_u = n_v for every (u, v) in E;
+// Sec. 4.1 WLOG 1: a mode is part of at most one contraction) and the layout of
+// one batch's descriptors and scratch.
+#include <algorithm>
+#include <cstring>
+#include <limits>
+
+#include "plan.cuh"
+
+namespace tnsk {
+
+namespace {
+
+constexpr int64_t kMaxNumel = (int64_t)1 << 40;
+constexpr size_t kScatterSmemBudget = 96 * 1024;
+
+int max_log2m_for(bool fp64) { return fp64 ? 13 : 14; }
+
+template <class T>
+size_t stage(std::vector<unsigned char>& buf, const std::vector<T>& v) {
+    size_t at = (buf.size() + 255) & ~(size_t)255;
+    buf.resize(at + v.size() * sizeof(T));
+    if (!v.empty()) std::memcpy(buf.data() + at, v.data(), v.size() * sizeof(T));
+    return at;
+}
+
+int ilog2(int64_t x) {
+    int l = 0;
+    while (((int64_t)1 << l) < x) ++l;
+    return l;
+}
+
+// Offset (in words) of T_{l,j} side s inside a node's T block; levels are
+// stored from l = qt down to 2, level l holding l/2 pairs.
+int64_t ts_offset(int qt, int l, int j, int s, int64_t m) {
+    int64_t before = 0;
+    for (int ll = qt; ll > l; ll >>= 1) before += ll / 2;
+    return ((before + j) * 2 + s) * m;
+}
+
+}  // namespace
+
+tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I, std::string& why) {
+    if (net.p < 1 || !net.X) {
+        why = "need p >= 1 tensors";
+        return TNSK_ERR_INVALID;
+    }
+    const bool fp64 = prm.prec == TNSK_PREC_FP64;
+    if (prm.prec != TNSK_PREC_FP32 && prm.prec != TNSK_PREC_FP64) {
+        why = "unknown precision";
+        return TNSK_ERR_INVALID;
+    }
+    if (prm.method != TNSK_GENERAL && prm.method != TNSK_ACYCLIC) {
+        why = "unknown method";
+        return TNSK_ERR_INVALID;
+    }
+    if (prm.m < 1 || (prm.m & (prm.m - 1))) {
+        why = "sketch size m must be a power of two >= 1";
+        return TNSK_ERR_UNSUPPORTED;
+    }
+    I.log2m = ilog2(prm.m);
+    if (I.log2m > max_log2m_for(fp64)) {
+        why = "sketch size m above this build's single-CTA FFT limit (2^14 FP32, 2^13 FP64)";
+        return TNSK_ERR_UNSUPPORTED;
+    }
+    if (prm.reps < 1 || prm.reps > 65536) {
+        why = "reps must be in [1, 65536]";
+        return TNSK_ERR_INVALID;
+    }
+    if (prm.groups < 1 || prm.groups > 64 || prm.reps % prm.groups != 0) {
+        why = "groups must divide reps and be in [1, 64]";
+        return TNSK_ERR_INVALID;
+    }
+    I.p = net.p;
+    I.mode_off.assign(I.p + 1, 0);
+    for (int k = 0; k < I.p; ++k) {
+        const tnsk_tensor& X = net.X[k];
+        if (X.order < 0) {
+            why = "negative order";
+            return TNSK_ERR_INVALID;
+        }
+        if (X.order > TNSK_MAX_ORDER) {
+            why = "tensor order above 12";
+            return TNSK_ERR_UNSUPPORTED;
+        }
+        if (X.order > 0 && !X.dims) {
+            why = "null dims";
+            return TNSK_ERR_INVALID;
+        }
+        if (X.dtype != TNSK_F64 && X.dtype != TNSK_F32 && X.dtype != TNSK_BF16) {
+            why = "unknown dtype";
+            return TNSK_ERR_INVALID;
+        }
+        I.mode_off[k + 1] = I.mode_off[k] + X.order;
+    }
+    I.q = I.mode_off[I.p];
+    I.dims.resize(I.q);
+    I.tensor_of.resize(I.q);
+    I.numel.assign(I.p, 1);
+    I.idx32 = true;
+    for (int k = 0; k < I.p; ++k) {
+        const tnsk_tensor& X = net.X[k];
+        int64_t n = 1;
+        for (int d = 0; d < X.order; ++d) {
+            int64_t v = X.dims[d];
+            if (v < 0) {
+                why = "negative dim";
+                return TNSK_ERR_INVALID;
+            }
+            if (v > std::numeric_limits<int32_t>::max()) {
+                why = "dim above 2^31 - 1";
+                return TNSK_ERR_UNSUPPORTED;
+            }
+            I.dims[I.mode_off[k] + d] = v;
+            I.tensor_of[I.mode_off[k] + d] = k;
+            if (v == 0)
+                n = 0;
+            else if (n > 0) {
+                if (n > kMaxNumel / v) {
+                    why = "tensor above 2^40 entries";
+                    return TNSK_ERR_UNSUPPORTED;
+                }
+                n *= v;
+            }
+        }
+        I.numel[k] = n;
+        if (n > 0 && !X.data) {
+            why = "null data for a non-empty tensor";
+            return TNSK_ERR_INVALID;
+        }
+        if (n >= ((int64_t)1 << 32)) I.idx32 = false;
+    }
+    I.t = net.t;
+    if (I.t < 0 || (I.t > 0 && !net.edges)) {
+        why = "bad contraction list";
+        return TNSK_ERR_INVALID;
+    }
+    I.edge_of.assign(I.q, -1);
+    I.side_of.assign(I.q, 0);
+    I.open_pos.assign(I.q, -1);
+    I.eoff.assign(I.t + 1, 0);
+    for (int e = 0; e < I.t; ++e) {
+        int u = net.edges[2 * e], v = net.edges[2 * e + 1];
+        if (u < 0 || v < 0 || u >= I.q || v >= I.q || u == v) {
+            why = "contraction " + std::to_string(e) + " needs two distinct valid modes";
+            return TNSK_ERR_INVALID;
+        }
+        if (I.dims[u] != I.dims[v]) {
+            why = "contraction " + std::to_string(e) + " joins modes of different size";
+            return TNSK_ERR_INVALID;
+        }
+        if (I.edge_of[u] >= 0 || I.edge_of[v] >= 0) {
+            why = "a mode in two contractions (a hyperedge; WLOG 1 copies are not built in)";
+            return TNSK_ERR_UNSUPPORTED;
+        }
+        I.edge_of[u] = e;
+        I.side_of[u] = 0;
+        I.edge_of[v] = e;
+        I.side_of[v] = 1;
+        I.eoff[e + 1] = I.eoff[e] + I.dims[u];
+    }
+    I.L = I.eoff[I.t];
+    int n_free = 0;
+    for (int g = 0; g < I.q; ++g)
+        if (I.edge_of[g] < 0) ++n_free;
+    if (net.n_open != n_free || (n_free > 0 && !net.open)) {
+        why = "open list must be a permutation of the uncontracted modes";
+        return TNSK_ERR_INVALID;
+    }
+    I.O = 1;
+    for (int j = 0; j < net.n_open; ++j) {
+        int g = net.open[j];
+        if (g < 0 || g >= I.q || I.edge_of[g] >= 0 || I.open_pos[g] >= 0) {
+            why = "open list must be a permutation of the uncontracted modes";
+            return TNSK_ERR_INVALID;
+        }
+        I.open_pos[g] = j;
+        if (I.dims[g] > 0 && I.O > kMaxNumel / I.dims[g]) {
+            why = "output above 2^40 entries";
+            return TNSK_ERR_UNSUPPORTED;
+        }
+        I.O *= I.dims[g];
+    }
+    I.open_tot.assign(I.p, 1);
+    int n_ot = 0;
+    for (int k = 0; k < I.p; ++k) {
+        int64_t o = 1;
+        for (int g = I.mode_off[k]; g < I.mode_off[k + 1]; ++g)
+            if (I.edge_of[g] < 0) o *= I.dims[g];
+        I.open_tot[k] = o;
+        if (o > 1) ++n_ot;
+    }
+    if (prm.method == TNSK_GENERAL) {
+        if (n_ot > TNSK_MAX_OPEN_TENSORS) {
+            why = "open legs on more than 4 tensors";
+            return TNSK_ERR_UNSUPPORTED;
+        }
+        return TNSK_OK;
+    }
+    // ---- method 2: acyclic, connected, full (Sec. 4.4) ----
+    if (net.n_open != 0) {
+        why = "the acyclic method takes full networks (no open legs) in this build";
+        return TNSK_ERR_UNSUPPORTED;
+    }
+    for (int e = 0; e < I.t; ++e)
+        if (I.tensor_of[net.edges[2 * e]] == I.tensor_of[net.edges[2 * e + 1]]) {
+            why = "a contraction inside one tensor is a cycle for the acyclic method";
+            return TNSK_ERR_CYCLIC;
+        }
+    if (I.t > I.p - 1) {
+        why = "more contractions than a tree has: the network has a cycle";
+        return TNSK_ERR_CYCLIC;
+    }
+    if (I.t < I.p - 1) {
+        why = "the network is not connected";
+        return TNSK_ERR_UNSUPPORTED;
+    }
+    if (prm.root >= I.p || prm.root < -1) {
+        why = "root out of range";
+        return TNSK_ERR_INVALID;
+    }
+    int root = prm.root;
+    if (root < 0) {
+        root = 0;
+        for (int k = 1; k < I.p; ++k)
+            if (I.numel[k] < I.numel[root]) root = k;
+    }
+    I.root = root;
+    I.parent.assign(I.p, -1);
+    I.parent_mode.assign(I.p, -1);
+    I.parent_edge.assign(I.p, -1);
+    I.child.assign(I.p, {});
+    I.child_mode.assign(I.p, {});
+    I.child_edge.assign(I.p, {});
+    std::vector<int> seen(I.p, 0), order;
+    order.push_back(root);
+    seen[root] = 1;
+    for (size_t h = 0; h < order.size(); ++h) {
+        int k = order[h];
+        for (int g = I.mode_off[k]; g < I.mode_off[k + 1]; ++g) {
+            int e = I.edge_of[g];
+            if (e == I.parent_edge[k]) continue;
+            int other = net.edges[2 * e] == g ? net.edges[2 * e + 1] : net.edges[2 * e];
+            int l = I.tensor_of[other];
+            if (seen[l]) {
+                why = "two contractions between one pair of tensors (merge them, WLOG 3)";
+                return TNSK_ERR_CYCLIC;
+            }
+            seen[l] = 1;
+            I.child[k].push_back(l);
+            I.child_mode[k].push_back(g - I.mode_off[k]);
+            I.child_edge[k].push_back(e);
+            I.parent[l] = k;
+            I.parent_edge[l] = e;
+            I.parent_mode[l] = other - I.mode_off[l];
+            order.push_back(l);
+        }
+    }
+    if ((int)order.size() != I.p) {
+        why = "the network is not connected";
+        return TNSK_ERR_UNSUPPORTED;
+    }
+    I.height.assign(I.p, 0);
+    for (int h = (int)order.size() - 1; h >= 0; --h) {
+        int k = order[h];
+        if ((int)I.child[k].size() > TNSK_MAX_SLOTS) {
+            why = "a tensor with more than 16 children";
+            return TNSK_ERR_UNSUPPORTED;
+        }
+        for (int l : I.child[k]) I.height[k] = std::max(I.height[k], I.height[l] + 1);
+    }
+    I.max_height = I.height[root];
+    return TNSK_OK;
+}
+
+tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* nets, const tnsk_params* params,
+                       double* const* outs, double* const* per_reps, bool fp64, bool sketch_only, BatchPlan& P,
+                       std::string& err) {
+    const int B = (int)infos.size();
+    const size_t acc = fp64 ? sizeof(double) : sizeof(float);
+    std::vector<TabReq> reqs;
+    std::vector<M1Tensor> m1t;
+    std::vector<M1Net> m1n;
+    std::vector<M1Work> m1w;
+    std::vector<OpenMode> opens;
+    std::vector<int2> m1items;
+    std::vector<CombineItem> comb;
+    std::vector<M2Node> m2nodes;
+    std::vector<M2Net> m2n;
+    int64_t tab_words = 0, yrep_n = 0, xs_n = 0, spec_n = 0, sexp_n = 0;
+    int64_t ws_x = 0, ws_r = 0, ws_v = 0;  // method-2 workspace parts (elements)
+    size_t scatter_smem = 16;
+    int max_log2m1 = 0, max_log2m2 = 0;
+    bool idx32 = true;
+    struct PendingItem {
+        int h, kind;
+        M2Item it;
+    };
+    std::vector<PendingItem> pend;
+    // method-2 node-local offsets are finalised after the x / r / V totals are known
+    struct M2Fix {
+        size_t node;
+        int64_t x, r, v, src;
+        int src_kind;  // 0 none, 1 r part, 2 x part
+        int64_t child_x[TNSK_MAX_SLOTS];
+    };
+    std::vector<M2Fix> fixes;
+
+    for (int b = 0; b < B; ++b) {
+        const NetInfo& I = infos[b];
+        const tnsk_network& N = nets[b];
+        const tnsk_params& pr = params[b];
+        const int64_t m = pr.m;
+        const uint32_t mask = (uint32_t)(m - 1);
+        const int R = pr.reps;
+        idx32 = idx32 && I.idx32;
+        if (pr.method == TNSK_GENERAL) {
+            M1Net nb{};
+            nb.m = m;
+            nb.log2m = I.log2m;
+            nb.R = R;
+            nb.groups = pr.groups;
+            nb.L = I.L;
+            nb.tab_off = tab_words;
+            nb.O = I.O;
+            nb.y_off = yrep_n;
+            nb.t0 = (int)m1t.size();
+            nb.p = I.p;
+            nb.open0 = (int)opens.size();
+            nb.n_open = N.n_open;
+            nb.out = outs ? outs[b] : nullptr;
+            nb.per_rep = per_reps ? per_reps[b] : nullptr;
+            max_log2m1 = std::max(max_log2m1, I.log2m);
+            const int64_t K = m == 1 ? 1 : m / 2 + 1;
+            int64_t xacc = 0, sacc = 0, eacc = 0;
+            std::vector<int> slot_of(I.p, -1);
+            for (int k = 0; k < I.p; ++k) {
+                M1Tensor T{};
+                T.data = N.X[k].data;
+                T.numel = I.numel[k];
+                T.O = I.open_tot[k];
+                T.xoff = xacc;
+                xacc += T.O * m;
+                if (T.O > 1) {
+                    slot_of[k] = nb.n_ot;
+                    nb.ot[nb.n_ot++] = (int)m1t.size();
+                    T.soff = sacc;
+                    T.eoff = eacc;
+                    sacc += T.O * K;
+                    eacc += T.O;
+                } else {
+                    T.soff = -1;
+                    T.eoff = -1;
+                }
+                T.dtype = N.X[k].dtype;
+                T.order = N.X[k].order;
+                T.net = (int)m1n.size();
+                int64_t ost = 1;
+                for (int d = T.order - 1; d >= 0; --d) {
+                    int g = I.mode_off[k] + d;
+                    T.dims[d] = (int32_t)I.dims[g];
+                    if (I.edge_of[g] >= 0) {
+                        T.tab[d] = (int32_t)I.eoff[I.edge_of[g]];
+                        T.comp[d] = I.side_of[g];
+                        T.ostride[d] = 0;
+                        T.n_ctr++;
+                    } else {
+                        T.tab[d] = -1;
+                        T.comp[d] = 0;
+                        T.ostride[d] = ost;
+                        ost *= I.dims[g];
+                    }
+                }
+                m1t.push_back(T);
+            }
+            nb.X = xacc;
+            nb.x_off = sketch_only ? 0 : xs_n;
+            nb.spec_per_rep = sacc;
+            nb.spec_off = spec_n;
+            nb.exp_per_rep = eacc;
+            nb.exp_off = sexp_n;
+            // output modes: row-major over the open list
+            int64_t ostr = 1;
+            std::vector<OpenMode> om(N.n_open);
+            for (int j = N.n_open - 1; j >= 0; --j) {
+                int g = N.open[j];
+                int k = I.tensor_of[g];
+                int64_t ts = 1;
+                for (int g2 = g + 1; g2 < I.mode_off[k + 1]; ++g2)
+                    if (I.edge_of[g2] < 0) ts *= I.dims[g2];
+                om[j].ostride = ostr;
+                om[j].tstride = ts;
+                om[j].dim = (int32_t)I.dims[g];
+                om[j].slot = slot_of[k];
+                ostr *= I.dims[g];
+            }
+            opens.insert(opens.end(), om.begin(), om.end());
+            // tables: one count sketch per contraction and rep (Alg. 1 first loop)
+            for (int e = 0; e < I.t; ++e) {
+                TabReq q{};
+                q.seed = pr.seed;
+                q.tid = tid_m1_edge(e);
+                q.n = I.eoff[e + 1] - I.eoff[e];
+                q.out_off = tab_words + I.eoff[e];
+                q.rep_stride = I.L;
+                q.R = R;
+                q.mask = mask;
+                if (q.n > 0) reqs.push_back(q);
+            }
+            tab_words += (int64_t)R * I.L;
+            // scatter work: chunks of each tensor x batches of reps
+            for (int k = 0; k < I.p; ++k) {
+                const M1Tensor& T = m1t[nb.t0 + k];
+                if (T.numel == 0 || T.O == 0) continue;
+                int64_t TT = 0;
+                for (int d = 0; d < T.order; ++d)
+                    if (T.tab[d] >= 0) TT += T.dims[d];
+                const size_t tab_b = (size_t)TT * 4;
+                const size_t bin_b = (size_t)T.O * m * acc;
+                int64_t nrep_priv = (int64_t)(kScatterSmemBudget / (tab_b + bin_b + 16));
+                bool priv = nrep_priv >= 1 && T.numel * 4 >= T.O * m;
+                int nrep;
+                if (priv)
+                    nrep = (int)std::min<int64_t>({(int64_t)R, nrep_priv, 32});
+                else
+                    nrep = (int)std::min<int64_t>({(int64_t)R, std::max<int64_t>(1, (int64_t)(kScatterSmemBudget / (tab_b + 16))), 16});
+                if (!priv && tab_b > kScatterSmemBudget) {
+                    err = "tensor " + std::to_string(k) + ": hash tables exceed shared memory";
+                    return TNSK_ERR_UNSUPPORTED;
+                }
+                const int64_t CH = priv ? std::max<int64_t>(8192, 2 * T.O * m) : 8192;
+                size_t sm = ((size_t)nrep * tab_b + 15) / 16 * 16 + (priv ? (size_t)nrep * bin_b : 0);
+                scatter_smem = std::max(scatter_smem, sm);
+                for (int r0 = 0; r0 < R; r0 += nrep)
+                    for (int64_t b0 = 0; b0 < T.numel; b0 += CH) {
+                        M1Work w{};
+                        w.begin = b0;
+                        w.end = std::min(T.numel, b0 + CH);
+                        w.tensor = nb.t0 + k;
+                        w.rep0 = r0;
+                        w.nrep = std::min(nrep, R - r0);
+                        w.priv = priv ? 1 : 0;
+                        m1w.push_back(w);
+                    }
+            }
+            if (!sketch_only && I.O > 0)
+                for (int r = 0; r < R; ++r) m1items.push_back(make_int2((int)m1n.size(), r));
+            if (sketch_only) P.sketch_user_bytes = (size_t)R * xacc * acc;
+            xs_n += sketch_only ? 0 : (int64_t)R * xacc;
+            spec_n += (int64_t)R * sacc;
+            sexp_n += (int64_t)R * eacc;
+            for (int64_t o = 0; o < I.O; ++o) {
+                CombineItem c{};
+                c.y_off = yrep_n;
+                c.O = I.O;
+                c.o = o;
+                c.R = R;
+                c.groups = pr.groups;
+                c.out = nb.out;
+                c.per_rep = nb.per_rep;
+                comb.push_back(c);
+            }
+            yrep_n += (int64_t)R * I.O;
+            m1n.push_back(nb);
+            continue;
+        }
+        // ---------------- method 2 ----------------
+        M2Net nb{};
+        nb.m = m;
+        nb.log2m = I.log2m;
+        nb.R = R;
+        nb.tab_off = tab_words;
+        nb.y_off = yrep_n;
+        max_log2m2 = std::max(max_log2m2, I.log2m);
+        const int net_id = (int)m2n.size();
+        const size_t node0 = m2nodes.size();
+        std::vector<int> qt(I.p, 0);
+        int64_t Lrep = I.L;
+        std::vector<int64_t> pad_tab(I.p), t_tab(I.p);
+        for (int k = 0; k < I.p; ++k) {
+            int c = (int)I.child[k].size();
+            while (qt[k] < c) qt[k] = qt[k] ? qt[k] * 2 : 1;
+            pad_tab[k] = Lrep;
+            Lrep += qt[k];
+        }
+        for (int k = 0; k < I.p; ++k) {
+            t_tab[k] = Lrep;
+            if (qt[k] >= 2) Lrep += 2 * (int64_t)(qt[k] - 1) * m;
+        }
+        nb.Lrep = Lrep;
+        // tables: C_{k,l} per edge, padding slots, T_{l,j} (Alg. 2 "independent recursive sketch")
+        for (int e = 0; e < I.t; ++e) {
+            TabReq q{};
+            q.seed = pr.seed;
+            q.tid = tid_m2_edge(e);
+            q.n = I.eoff[e + 1] - I.eoff[e];
+            q.out_off = tab_words + I.eoff[e];
+            q.rep_stride = Lrep;
+            q.R = R;
+            q.mask = mask;
+            if (q.n > 0) reqs.push_back(q);
+        }
+        for (int k = 0; k < I.p; ++k) {
+            int c = (int)I.child[k].size();
+            for (int j = c; j < qt[k]; ++j) {
+                TabReq q{};
+                q.seed = pr.seed;
+                q.tid = tid_m2_pad(k, j);
+                q.n = 1;
+                q.out_off = tab_words + pad_tab[k] + j;
+                q.rep_stride = Lrep;
+                q.R = R;
+                q.mask = mask;
+                reqs.push_back(q);
+            }
+            for (int l = qt[k]; l >= 2; l >>= 1)
+                for (int j = 0; j < l / 2; ++j)
+                    for (int s = 0; s < 2; ++s) {
+                        TabReq q{};
+                        q.seed = pr.seed;
+                        q.tid = tid_m2_ts(k, ilog2(l), j, s);
+                        q.n = m;
+                        q.out_off = tab_words + t_tab[k] + ts_offset(qt[k], l, j, s, m);
+                        q.rep_stride = Lrep;
+                        q.R = R;
+                        q.mask = mask;
+                        reqs.push_back(q);
+                    }
+        }
+        tab_words += (int64_t)R * Lrep;
+        // nodes
+        std::vector<int64_t> xo(I.p, -1);
+        for (int k = 0; k < I.p; ++k) {
+            if (k == I.root) continue;
+            xo[k] = ws_x;
+            ws_x += (int64_t)R * m;
+        }
+        for (int k = 0; k < I.p; ++k) {
+            const tnsk_tensor& X = N.X[k];
+            M2Node nd{};
+            nd.data = X.data;
+            nd.numel = I.numel[k];
+            nd.dtype = X.dtype;
+            nd.order = X.order;
+            nd.net = net_id;
+            nd.is_root = k == I.root;
+            nd.pmode = I.parent_mode[k];
+            for (int d = 0; d < X.order; ++d) nd.dims[d] = (int32_t)I.dims[I.mode_off[k] + d];
+            if (nd.is_root) {
+                nd.A = 1;
+                nd.npar = 1;
+                nd.Bc = nd.numel;
+            } else {
+                nd.A = 1;
+                nd.Bc = 1;
+                for (int d = 0; d < nd.pmode; ++d) nd.A *= nd.dims[d];
+                for (int d = nd.pmode + 1; d < X.order; ++d) nd.Bc *= nd.dims[d];
+                nd.npar = nd.dims[nd.pmode];
+            }
+            nd.cols = nd.A * nd.Bc;
+            nd.ptab = nd.is_root ? -1 : I.eoff[I.parent_edge[k]];
+            nd.c = (int)I.child[k].size();
+            nd.qt = qt[k];
+            for (int j = 0; j < nd.c; ++j) {
+                nd.cmode[j] = I.child_mode[k][j];
+                nd.ctab[j] = I.eoff[I.child_edge[k][j]];
+            }
+            nd.pad_tab = pad_tab[k];
+            nd.t_tab = t_tab[k];
+            M2Fix fx{};
+            fx.node = m2nodes.size();
+            fx.x = xo[k];
+            fx.r = -1;
+            fx.v = -1;
+            fx.src_kind = 0;
+            for (int j = 0; j < nd.c; ++j) fx.child_x[j] = xo[I.child[k][j]];
+            if (nd.qt >= 2) {
+                fx.r = ws_r;
+                ws_r += (int64_t)R * (nd.qt - 1) * m;
+                fx.src = fx.r + (int64_t)(nd.qt - 2) * m;
+                fx.src_kind = 1;
+                nd.src_stride = (int64_t)(nd.qt - 1) * m;
+            } else if (nd.qt == 1) {
+                fx.src = xo[I.child[k][0]];
+                fx.src_kind = 2;
+                nd.src_stride = m;
+            }
+            if (nd.c >= 1) {
+                fx.v = ws_v;
+                ws_v += nd.cols * (int64_t)R;
+            }
+            fixes.push_back(fx);
+            m2nodes.push_back(nd);
+            // work items at this node's height
+            const int h = I.height[k];
+            const int node_idx = (int)(node0 + k);
+            if (nd.c == 0 && !nd.is_root) {
+                for (int64_t b0 = 0; b0 < nd.numel; b0 += 2048) {
+                    M2Item it{node_idx, 0, 0, 0, b0, std::min(nd.numel, b0 + 2048)};
+                    pend.push_back({h, M2_LEAF, it});
+                }
+            }
+            if (nd.qt >= 2)
+                for (int r = 0; r < R; ++r) pend.push_back({h, M2_COMPOSE, M2Item{node_idx, r, 0, 0, 0, 0}});
+            if (nd.c >= 1)
+                for (int64_t b0 = 0; b0 < nd.cols; b0 += 128) {
+                    M2Item it{node_idx, 0, 0, 0, b0, std::min(nd.cols, b0 + 128)};
+                    pend.push_back({h, M2_VBUILD, it});
+                }
+            if (nd.c >= 1 && !nd.is_root && nd.numel > 0)
+                for (int64_t rt = 0; rt * 64 < nd.npar; ++rt)
+                    for (int64_t ct = 0; ct * 64 < R; ++ct)
+                        pend.push_back({h, M2_GEMM, M2Item{node_idx, (int)rt, (int)ct, 0, 0, 0}});
+            if (nd.is_root)
+                for (int64_t b0 = 0; b0 < std::max<int64_t>(nd.cols, 1); b0 += 4096) {
+                    M2Item it{node_idx, 0, 0, 0, b0, std::min(nd.cols, b0 + 4096)};
+                    pend.push_back({h, M2_ROOT, it});
+                }
+        }
+        P.m2.max_height = std::max(P.m2.max_height, I.max_height);
+        CombineItem c{};
+        c.y_off = yrep_n;
+        c.O = 1;
+        c.o = 0;
+        c.R = R;
+        c.groups = pr.groups;
+        c.out = outs ? outs[b] : nullptr;
+        c.per_rep = per_reps ? per_reps[b] : nullptr;
+        comb.push_back(c);
+        yrep_n += R;
+        m2n.push_back(nb);
+    }
+
+    // ---- method-2 workspace offsets: ws = [x | r | V] (elements of the accumulator type)
+    for (const M2Fix& fx : fixes) {
+        M2Node& nd = m2nodes[fx.node];
+        nd.x_off = fx.x;
+        nd.r_off = fx.r >= 0 ? ws_x + fx.r : -1;
+        nd.v_off = fx.v >= 0 ? ws_x + ws_r + fx.v : -1;
+        nd.src_off = fx.src_kind == 1 ? ws_x + fx.src : (fx.src_kind == 2 ? fx.src : -1);
+        for (int j = 0; j < nd.c; ++j) nd.child_x[j] = fx.child_x[j];
+    }
+    // ---- method-2 item order: by height, then kind
+    std::vector<M2Item> m2items;
+    if (!m2n.empty()) {
+        const int H = P.m2.max_height + 1;
+        P.m2.first.assign(H * M2_NKINDS, 0);
+        P.m2.count.assign(H * M2_NKINDS, 0);
+        std::stable_sort(pend.begin(), pend.end(), [](const PendingItem& a, const PendingItem& b) {
+            return a.h != b.h ? a.h < b.h : a.kind < b.kind;
+        });
+        for (size_t i = 0; i < pend.size(); ++i) {
+            int slot = pend[i].h * M2_NKINDS + pend[i].kind;
+            if (P.m2.count[slot] == 0) P.m2.first[slot] = (int)i;
+            P.m2.count[slot]++;
+            m2items.push_back(pend[i].it);
+        }
+    }
+    P.m2.n_nets = (int)m2n.size();
+    P.m2.max_log2m = max_log2m2;
+
+    // ---- table request prefix offsets
+    int64_t first = 0;
+    for (TabReq& q : reqs) {
+        q.first = first;
+        first += q.n * q.R;
+    }
+    P.n_reqs = (int)reqs.size();
+    P.n_table_words = first;
+
+    // ---- stage descriptors
+    std::vector<unsigned char>& H = P.host_desc;
+    size_t o_reqs = stage(H, reqs), o_m1t = stage(H, m1t), o_m1n = stage(H, m1n), o_m1w = stage(H, m1w);
+    size_t o_open = stage(H, opens), o_items = stage(H, m1items), o_comb = stage(H, comb);
+    size_t o_m2nodes = stage(H, m2nodes), o_m2n = stage(H, m2n), o_m2items = stage(H, m2items);
+    P.desc_off = P.arena.take(H.size());
+    P.reqs_off = P.desc_off + o_reqs;
+    P.m1.tens_off = P.desc_off + o_m1t;
+    P.m1.nets_off = P.desc_off + o_m1n;
+    P.m1.work_off = P.desc_off + o_m1w;
+    P.m1.opens_off = P.desc_off + o_open;
+    P.m1.items_off = P.desc_off + o_items;
+    P.comb_off = P.desc_off + o_comb;
+    P.m2.nodes_off = P.desc_off + o_m2nodes;
+    P.m2.nets_off = P.desc_off + o_m2n;
+    P.m2.items_off = P.desc_off + o_m2items;
+    // ---- zeroed region: per-rep estimates, method-1 sketches, method-2 x accumulators
+    P.zero_off = P.arena.take(0);
+    P.yrep_off = P.arena.take((size_t)yrep_n * sizeof(double));
+    P.m1.xs_off = P.arena.take((size_t)xs_n * acc);
+    P.m2.ws_off = P.arena.take((size_t)(ws_x + ws_r + ws_v) * acc);
+    P.zero_bytes = P.m2.ws_off + (size_t)ws_x * acc - P.zero_off;
+    // ---- the rest
+    P.tabs_off = P.arena.take((size_t)tab_words * sizeof(uint32_t));
+    P.m1.spec_off = P.arena.take((size_t)spec_n * 2 * acc);
+    P.m1.sexp_off = P.arena.take((size_t)sexp_n * sizeof(int));
+    P.m1.n_nets = (int)m1n.size();
+    P.m1.n_work = (int)m1w.size();
+    P.m1.n_items = (int)m1items.size();
+    P.m1.scatter_smem = scatter_smem;
+    P.m1.idx32 = idx32;
+    P.m1.max_log2m = max_log2m1;
+    P.n_comb = (int)comb.size();
+    return TNSK_OK;
+}
+
+}  // namespace tnsk

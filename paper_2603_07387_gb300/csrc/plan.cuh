@@ -1,0 +1,72 @@
+// plan.cuh -- host-side network validation and launch planning.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "method2.cuh"
+
+namespace tnsk {
+
+// A validated network (Def. "Tensor contraction", Def. "TNC"), 0-based modes.
+struct NetInfo {
+    int p = 0, q = 0, t = 0;
+    std::vector<int> mode_off;      // [p+1]
+    std::vector<int64_t> dims;      // [q]
+    std::vector<int> tensor_of;     // [q]
+    std::vector<int> edge_of;       // [q] edge or -1 (open)
+    std::vector<int> side_of;       // [q] 0: first mode u (C), 1: second mode v (C')
+    std::vector<int> open_pos;      // [q] position in the open list or -1
+    std::vector<int64_t> numel;     // [p]
+    std::vector<int64_t> open_tot;  // [p] O_k
+    std::vector<int64_t> eoff;      // [t+1] edge table offsets
+    int64_t L = 0;                  // sum of edge dims
+    int64_t O = 1;                  // output entries
+    int log2m = 0;
+    bool idx32 = true;
+    // method 2: rooted tree (children in mode order, footnote to Gamma(k))
+    int root = -1;
+    std::vector<int> parent, parent_mode, parent_edge, height;
+    std::vector<std::vector<int>> child, child_mode, child_edge;
+    int max_height = 0;
+};
+
+struct Arena {
+    size_t used = 0;
+    size_t take(size_t bytes, size_t align = 256);
+};
+
+struct M1Plan {
+    int n_nets = 0;
+    size_t tens_off = 0, nets_off = 0, work_off = 0, opens_off = 0, items_off = 0;
+    size_t xs_off = 0, spec_off = 0, sexp_off = 0;
+    int n_work = 0, n_items = 0;
+    size_t scatter_smem = 0;
+    bool idx32 = true;
+    int max_log2m = 0;
+};
+
+struct BatchPlan {
+    Arena arena;
+    std::vector<unsigned char> host_desc;
+    size_t desc_off = 0;
+    size_t zero_off = 0, zero_bytes = 0;
+    size_t sketch_user_bytes = 0;
+    size_t reqs_off = 0;
+    int n_reqs = 0;
+    int64_t n_table_words = 0;
+    size_t tabs_off = 0;
+    size_t yrep_off = 0;
+    size_t comb_off = 0;
+    int n_comb = 0;
+    M1Plan m1;
+    M2Plan m2;
+};
+
+tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& info, std::string& why);
+tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* nets, const tnsk_params* params,
+                       double* const* outs, double* const* per_reps, bool fp64, bool sketch_only, BatchPlan& plan,
+                       std::string& err);
+
+}  // namespace tnsk

@@ -1,0 +1,267 @@
+"""ctypes binding of libtnsk (include/tnsk.h). Argument marshalling only.
+
+Every step of the estimators runs in the CUDA kernels of libtnsk.so; this module
+turns Python lists and torch CUDA tensors into the C structs and raises on a
+non-OK status. It fails loudly when libtnsk.so has not been built: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+from typing import Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libtnsk.so")
+
+TNSK_OK = 0
+STATUS = {
+    0: "TNSK_OK",
+    -1: "TNSK_ERR_INVALID",
+    -2: "TNSK_ERR_CYCLIC",
+    -3: "TNSK_ERR_UNSUPPORTED",
+    -4: "TNSK_ERR_CUDA",
+    -5: "TNSK_ERR_OOM",
+    -6: "TNSK_ERR_TIMEOUT",
+    -7: "TNSK_ERR_UNREACHABLE",
+}
+F64, F32, BF16 = 0, 1, 2
+GENERAL, ACYCLIC = 1, 2
+KERNEL_KINDS = ("tables", "m1_scatter", "m1_spectrum", "m2_leaf", "m2_compose", "m2_vbuild", "m2_gemm",
+                "m2_root", "combine")
+PREC_FP32, PREC_FP64 = 0, 2
+
+# exported symbols declared in include/tnsk.h
+SYMBOLS = (
+    "tnsk_create",
+    "tnsk_destroy",
+    "tnsk_set_stream",
+    "tnsk_count_sketch",
+    "tnsk_m1_sketch",
+    "tnsk_estimate",
+    "tnsk_estimate_batch",
+    "tnsk_profile",
+    "tnsk_profile_read",
+    "tnsk_sync",
+    "tnsk_status_string",
+    "tnsk_last_error",
+)
+
+
+class TnskError(RuntimeError):
+    def __init__(self, status: int, message: str = ""):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Tensor(ctypes.Structure):
+    _fields_ = [
+        ("order", ctypes.c_int32),
+        ("dims", ctypes.POINTER(ctypes.c_int64)),
+        ("data", ctypes.c_void_p),
+        ("dtype", ctypes.c_int32),
+    ]
+
+
+class _Network(ctypes.Structure):
+    _fields_ = [
+        ("p", ctypes.c_int32),
+        ("X", ctypes.POINTER(_Tensor)),
+        ("t", ctypes.c_int32),
+        ("edges", ctypes.POINTER(ctypes.c_int32)),
+        ("n_open", ctypes.c_int32),
+        ("open", ctypes.POINTER(ctypes.c_int32)),
+    ]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int64),
+        ("reps", ctypes.c_int32),
+        ("groups", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("method", ctypes.c_int32),
+        ("root", ctypes.c_int32),
+        ("prec", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libtnsk.so; raises if it is missing (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtnsk.so not found at {path}: build it with __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    L.tnsk_create.restype = i32
+    L.tnsk_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp]
+    L.tnsk_destroy.restype = i32
+    L.tnsk_destroy.argtypes = [vp]
+    L.tnsk_set_stream.restype = i32
+    L.tnsk_set_stream.argtypes = [vp, vp]
+    L.tnsk_count_sketch.restype = i32
+    L.tnsk_count_sketch.argtypes = [vp, u64, u64, u64, i64, i64, vp, vp]
+    L.tnsk_m1_sketch.restype = i32
+    L.tnsk_m1_sketch.argtypes = [vp, ctypes.POINTER(_Network), ctypes.POINTER(_Params), vp]
+    L.tnsk_estimate.restype = i32
+    L.tnsk_estimate.argtypes = [vp, ctypes.POINTER(_Network), ctypes.POINTER(_Params), vp, vp]
+    L.tnsk_estimate_batch.restype = i32
+    L.tnsk_estimate_batch.argtypes = [vp, i32, ctypes.POINTER(_Network), ctypes.POINTER(_Params),
+                                      ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.tnsk_profile.restype = i32
+    L.tnsk_profile.argtypes = [vp, i32]
+    L.tnsk_profile_read.restype = i32
+    L.tnsk_profile_read.argtypes = [vp, vp, vp]
+    L.tnsk_sync.restype = i32
+    L.tnsk_sync.argtypes = [vp]
+    L.tnsk_status_string.restype = ctypes.c_char_p
+    L.tnsk_status_string.argtypes = [i32]
+    L.tnsk_last_error.restype = ctypes.c_char_p
+    L.tnsk_last_error.argtypes = [vp]
+    _lib = L
+    return L
+
+
+@dataclass
+class Network:
+    """Tensors (torch CUDA tensors, row-major/contiguous), contractions E as pairs of
+    global 0-based mode ids, and the output order of the open modes."""
+
+    tensors: Sequence
+    edges: Sequence[tuple[int, int]]
+    open: Sequence[int] = ()
+
+
+@dataclass
+class Params:
+    m: int
+    reps: int
+    groups: int = 1
+    seed: int = 0
+    method: int = GENERAL
+    root: int = -1
+    prec: int = PREC_FP32
+
+
+def _dtype_code(t):
+    import torch
+
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.bfloat16:
+        return BF16
+    raise TypeError(f"unsupported tensor dtype {t.dtype}")
+
+
+class _NetHolder:
+    """Owns the ctypes arrays behind one tnsk_network."""
+
+    def __init__(self, net: Network):
+        self.dims = []
+        tens = (_Tensor * max(1, len(net.tensors)))()
+        for k, x in enumerate(net.tensors):
+            if x.numel() > 0 and not x.is_contiguous():
+                raise ValueError(f"tensor {k} must be contiguous (row-major)")
+            d = (ctypes.c_int64 * max(1, x.dim()))(*x.shape)
+            self.dims.append(d)
+            tens[k].order = x.dim()
+            tens[k].dims = ctypes.cast(d, ctypes.POINTER(ctypes.c_int64))
+            tens[k].data = x.data_ptr() if x.numel() > 0 else None
+            tens[k].dtype = _dtype_code(x)
+        self.tens = tens
+        flat = [int(m) for e in net.edges for m in e]
+        self.edges = (ctypes.c_int32 * max(1, len(flat)))(*flat)
+        self.open = (ctypes.c_int32 * max(1, len(net.open)))(*[int(g) for g in net.open])
+        self.c = _Network(
+            len(net.tensors),
+            ctypes.cast(tens, ctypes.POINTER(_Tensor)),
+            len(net.edges),
+            ctypes.cast(self.edges, ctypes.POINTER(ctypes.c_int32)),
+            len(net.open),
+            ctypes.cast(self.open, ctypes.POINTER(ctypes.c_int32)),
+        )
+        self.keep = list(net.tensors)
+
+
+def _params(p: Params) -> _Params:
+    return _Params(int(p.m), int(p.reps), int(p.groups), int(p.seed) & ((1 << 64) - 1), int(p.method),
+                   int(p.root), int(p.prec))
+
+
+class Context:
+    """A libtnsk context bound to one device and one CUDA stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        sp = None if stream is None else ctypes.c_void_p(int(stream))
+        st = self.lib.tnsk_create(ctypes.byref(h), int(device), sp)
+        if st != TNSK_OK:
+            raise TnskError(st, "tnsk_create failed")
+        self.h = h
+
+    def _check(self, st):
+        if st != TNSK_OK:
+            raise TnskError(st, self.lib.tnsk_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tnsk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._check(self.lib.tnsk_set_stream(self.h, ctypes.c_void_p(int(stream)) if stream else None))
+
+    def count_sketch(self, seed: int, rep: int, tid: int, n: int, m: int, bins, signs):
+        self._check(self.lib.tnsk_count_sketch(self.h, seed & ((1 << 64) - 1), rep, tid, n, m,
+                                               bins.data_ptr() if n else None, signs.data_ptr() if n else None))
+
+    def m1_sketch(self, net: Network, params: Params, x):
+        nh = _NetHolder(net)
+        pr = _params(params)
+        self._check(self.lib.tnsk_m1_sketch(self.h, ctypes.byref(nh.c), ctypes.byref(pr), x.data_ptr()))
+
+    def estimate(self, net: Network, params: Params, out, per_rep=None):
+        nh = _NetHolder(net)
+        pr = _params(params)
+        self._check(self.lib.tnsk_estimate(self.h, ctypes.byref(nh.c), ctypes.byref(pr), out.data_ptr(),
+                                           per_rep.data_ptr() if per_rep is not None else None))
+
+    def estimate_batch(self, nets: Sequence[Network], params: Sequence[Params], outs, per_reps=None):
+        B = len(nets)
+        holders = [_NetHolder(n) for n in nets]
+        carr = (_Network * max(1, B))(*[h.c for h in holders])
+        parr = (_Params * max(1, B))(*[_params(p) for p in params])
+        oarr = (ctypes.c_void_p * max(1, B))(*[o.data_ptr() for o in outs])
+        rarr = None
+        if per_reps is not None:
+            rarr = (ctypes.c_void_p * max(1, B))(*[(r.data_ptr() if r is not None else None) for r in per_reps])
+        self._check(self.lib.tnsk_estimate_batch(self.h, B, carr, parr, oarr, rarr))
+        return holders  # callers may keep them alive until the stream completes
+
+    def profile(self, enable: bool = True):
+        self._check(self.lib.tnsk_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel kind: (total ms, launches)} since the last read (waits for the stream)."""
+        ms = (ctypes.c_double * len(KERNEL_KINDS))()
+        n = (ctypes.c_int64 * len(KERNEL_KINDS))()
+        self._check(self.lib.tnsk_profile_read(self.h, ms, n))
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def sync(self):
+        self._check(self.lib.tnsk_sync(self.h))

@@ -1,0 +1,221 @@
+"""GPU parity: libtnsk (through the C ABI) against the FP64 oracle, same seeds.
+
+Rows covered: a1 tables (bit-exact), a2 method-1 sketches (per bin), a3+a4
+method-1 estimates (per rep), a5-a8 method-2 estimates (per rep), a9 combination.
+Tolerance: |gpu - oracle| <= tol * S with S the oracle's cancellation-aware scale
+(tol 1e-5 for the FP32 path, 1e-10 for the FP64 path)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_07387_gb300 import tnsk
+from paper_2603_07387_gb300 import workloads as W
+
+from gpu_common import TOL, assert_parity, gpu_estimate, gpu_network, oracle_estimate, rounded
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = tnsk.Context(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    c.close()
+
+
+# ---------------------------------------------------------------- a1 tables
+@pytest.mark.parametrize("seed,rep,tid,n,m", [
+    (0, 0, 1 << 56, 1000, 1024), (0x7E57, 7, (4 << 56) | (3 << 24) | (2 << 16) | 5, 4096, 4096),
+    (2**64 - 1, 65535, (2 << 56) | 9, 33, 1), (5, 1, (3 << 56) | 1, 100_000, 65536), (1, 2, 3, 0, 8)])
+def test_count_sketch_bit_exact(ctx, seed, rep, tid, n, m):
+    bins = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
+    signs = torch.zeros(max(n, 1), dtype=torch.int8, device="cuda")
+    ctx.count_sketch(seed, rep, tid, n, m, bins, signs)
+    ctx.sync()
+    ob, os_ = oracle.count_sketch(seed, rep, tid, n, m)
+    assert np.array_equal(bins.cpu().numpy()[:n], ob)
+    assert np.array_equal(signs.cpu().numpy()[:n], os_)
+
+
+# ---------------------------------------------------------------- a2 sketches
+def _small_specs():
+    rng = np.random.default_rng(11)
+    specs = [W.triangle(5, seed=1)]
+    specs.append(W.NetSpec([rng.standard_normal((3, 4, 2)), rng.standard_normal((4, 5)), rng.standard_normal((5, 3))],
+                           [(1, 3), (4, 5), (6, 0)], [2], "open1"))
+    specs.append(W.NetSpec([rng.standard_normal((3, 2, 3)), rng.standard_normal(2)], [(0, 2), (1, 3)], [],
+                           "selftrace"))
+    specs.append(W.random_network(np.random.default_rng(3), p_range=(4, 6), dim_range=(2, 5), open_dim_range=(2, 3)))
+    specs.append(W.grid(2, 3, 3, seed=4))
+    return specs
+
+
+@pytest.mark.parametrize("prec,m", [(tnsk.PREC_FP64, 8), (tnsk.PREC_FP64, 1), (tnsk.PREC_FP32, 64),
+                                    (tnsk.PREC_FP32, 2), (tnsk.PREC_FP32, 1024)])
+def test_method1_sketch_per_bin(ctx, prec, m):
+    R, seed = 5, 0x7E57
+    for spec in _small_specs():
+        tdt = torch.float64 if prec == tnsk.PREC_FP64 else torch.float32
+        net = gpu_network(spec, tdt)
+        X = rounded(spec, tdt)
+        bins, signs = oracle.m1_tables(X, spec.edges, spec.open, seed=seed, reps=R, m=m)
+        want = oracle.m1_sketch(X, spec.edges, spec.open, m, bins, signs)
+        scale = oracle.m1_sketch(X, spec.edges, spec.open, m, bins, signs, abs_mode=True)
+        x = torch.zeros(want.shape, dtype=tdt, device="cuda")
+        ctx.m1_sketch(net, tnsk.Params(m=m, reps=R, seed=seed, prec=prec), x)
+        ctx.sync()
+        got = x.double().cpu().numpy()
+        tol = 1e-12 if prec == tnsk.PREC_FP64 else 1e-6
+        assert np.all(np.abs(got - want) <= tol * np.maximum(scale, 1e-300)), spec.name
+
+
+# ---------------------------------------------------------------- a3 + a4 method 1
+@pytest.mark.parametrize("prec", [tnsk.PREC_FP32, tnsk.PREC_FP64])
+@pytest.mark.parametrize("m", [1, 2, 16, 256, 4096])
+def test_method1_estimate_small(ctx, prec, m):
+    tdt = torch.float64 if prec == tnsk.PREC_FP64 else torch.float32
+    for spec in _small_specs():
+        p = tnsk.Params(m=m, reps=6, groups=3, seed=99, prec=prec)
+        out, per = gpu_estimate(ctx, spec, p, tdt)
+        y, s = oracle_estimate(spec, p, tdt)
+        assert_parity(per, y, s, TOL[prec], f"{spec.name} m={m}")
+        assert np.allclose(out, oracle.combine(per, 3), rtol=1e-14, atol=0)
+
+
+def test_method1_triangle_full_size(ctx):
+    """tr(ABC) of three 64x64 FP64 N(0,1) matrices, m = 256, 16 reps."""
+    spec = W.triangle(64)
+    for prec in (tnsk.PREC_FP32, tnsk.PREC_FP64):
+        p = tnsk.Params(m=256, reps=16, seed=W.HASH_SEED, prec=prec)
+        out, per = gpu_estimate(ctx, spec, p, torch.float64)
+        y, s = oracle_estimate(spec, p, torch.float64)
+        assert_parity(per, y, s, TOL[prec], "triangle64")
+
+
+def test_method1_tt_ladder_full_size(ctx):
+    A, B = W.tt_cores()
+    spec = W.tt_ladder(A, B)
+    p = tnsk.Params(m=1024, reps=64, seed=W.HASH_SEED)
+    out, per = gpu_estimate(ctx, spec, p, torch.float32)
+    y, s = oracle_estimate(spec, p, torch.float32)
+    assert_parity(per, y, s, TOL[p.prec], "tt_ladder")
+
+
+def test_method1_grid_bf16_inputs(ctx):
+    spec = W.grid(3, 3, 4, seed=7)
+    p = tnsk.Params(m=512, reps=8, seed=3)
+    out, per = gpu_estimate(ctx, spec, p, torch.bfloat16)
+    y, s = oracle_estimate(spec, p, torch.bfloat16)  # oracle on the bf16-rounded inputs
+    assert_parity(per, y, s, TOL[p.prec], "grid bf16")
+
+
+def test_method1_open_legs_many_shapes(ctx):
+    rng = np.random.default_rng(21)
+    for _ in range(6):
+        spec = W.random_network(rng, p_range=(4, 7), dim_range=(2, 6), open_dim_range=(2, 5))
+        p = tnsk.Params(m=128, reps=4, seed=int(rng.integers(1 << 30)))
+        out, per = gpu_estimate(ctx, spec, p, torch.float32)
+        y, s = oracle_estimate(spec, p, torch.float32)
+        assert_parity(per, y, s, TOL[p.prec], "random open")
+
+
+# ---------------------------------------------------------------- a5-a8 method 2
+def _trees():
+    rng = np.random.default_rng(5)
+    specs = [W.random_tree(rng, p, dim_range=(2, 7), max_children=mc) for p, mc in
+             [(2, 1), (3, 2), (6, 3), (9, 5), (12, 2)]]
+    A, B = W.tt_cores(sites=5, bond=4, phys=3, seed=2)
+    specs.append(W.tt_chain(A, B))
+    return specs
+
+
+@pytest.mark.parametrize("prec", [tnsk.PREC_FP32, tnsk.PREC_FP64])
+@pytest.mark.parametrize("m", [1, 2, 32, 1024])
+def test_method2_estimate_small(ctx, prec, m):
+    tdt = torch.float64 if prec == tnsk.PREC_FP64 else torch.float32
+    for spec in _trees():
+        for root in (-1, 0, spec.p - 1):
+            p = tnsk.Params(m=m, reps=5, seed=17, method=tnsk.ACYCLIC, root=root, prec=prec)
+            out, per = gpu_estimate(ctx, spec, p, tdt)
+            y, s = oracle_estimate(spec, p, tdt)
+            assert_parity(per, y, s, TOL[prec], f"{spec.name} m={m} root={root}")
+
+
+def test_method2_tt_chain_full_size(ctx):
+    A, B = W.tt_cores()
+    spec = W.tt_chain(A, B)
+    p = tnsk.Params(m=1024, reps=64, seed=W.HASH_SEED, method=tnsk.ACYCLIC)
+    out, per = gpu_estimate(ctx, spec, p, torch.float32)
+    y, s = oracle_estimate(spec, p, torch.float32)
+    assert_parity(per, y, s, TOL[p.prec], "tt_chain")
+
+
+# ---------------------------------------------------------------- batch, combine, errors
+def test_batch_matches_oracle_per_network(ctx):
+    rng = np.random.default_rng(8)
+    specs = [W.random_network(rng, p_range=(4, 6), dim_range=(2, 5), open_dim_range=(2, 4)) for _ in range(5)]
+    specs += _trees()[:3]
+    params = []
+    for i, s in enumerate(specs):
+        method = tnsk.ACYCLIC if s.name.startswith("tree") else tnsk.GENERAL
+        params.append(tnsk.Params(m=64 * (1 + i % 3), reps=4, groups=2, seed=1000 + i, method=method))
+    nets = [gpu_network(s, torch.float32) for s in specs]
+    outs, pers = [], []
+    for s, p in zip(specs, params):
+        dims = [d for x in s.tensors for d in np.shape(x)]
+        O = int(np.prod([dims[g] for g in s.open])) if s.open else 1
+        outs.append(torch.zeros(max(O, 1), dtype=torch.float64, device="cuda"))
+        pers.append(torch.zeros((p.reps, max(O, 1)), dtype=torch.float64, device="cuda"))
+    ctx.estimate_batch(nets, params, outs, pers)
+    ctx.sync()
+    for s, p, o, pr in zip(specs, params, outs, pers):
+        y, sc = oracle_estimate(s, p, torch.float32)
+        assert_parity(pr.cpu().numpy()[:, :y.shape[1]], y, sc, TOL[p.prec], s.name)
+        assert np.allclose(o.cpu().numpy()[:y.shape[1]], oracle.combine(pr.cpu().numpy()[:, :y.shape[1]], 2),
+                           rtol=1e-14, atol=0)
+
+
+def test_degenerate_inputs(ctx):
+    # scalars, an empty contracted mode, an empty open mode, a single self-contraction
+    cases = [
+        W.NetSpec([np.array(3.0), np.array(-2.0)], [], [], "scalars"),
+        W.NetSpec([np.zeros((0, 3)), np.zeros((0,))], [(0, 2)], [1], "empty-contracted"),
+        W.NetSpec([np.ones((2, 0)), np.ones(2)], [(0, 2)], [1], "empty-open"),
+        W.NetSpec([np.arange(16.0).reshape(4, 4)], [(0, 1)], [], "trace"),
+    ]
+    for spec in cases:
+        p = tnsk.Params(m=8, reps=3, seed=4)
+        out, per = gpu_estimate(ctx, spec, p, torch.float32)
+        y, s = oracle_estimate(spec, p, torch.float32)
+        if y.size:
+            assert_parity(per, y, s, TOL[p.prec], spec.name)
+    p2 = tnsk.Params(m=8, reps=2, seed=4, method=tnsk.ACYCLIC)
+    out, per = gpu_estimate(ctx, W.NetSpec([np.array(4.0)], [], [], "scalar"), p2, torch.float32)
+    assert np.allclose(per, 4.0)
+
+
+def test_errors_are_reported(ctx):
+    A = [np.ones((3, 3)) for _ in range(3)]
+    tri = W.NetSpec(A, [(1, 2), (3, 4), (5, 0)], [])
+    net = gpu_network(tri, torch.float32)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(tnsk.TnskError) as e:
+        ctx.estimate(net, tnsk.Params(m=8, reps=2, method=tnsk.ACYCLIC), out)
+    assert e.value.status == -2
+    with pytest.raises(tnsk.TnskError) as e:
+        ctx.estimate(net, tnsk.Params(m=12, reps=2), out)
+    assert e.value.status == -3
+    with pytest.raises(tnsk.TnskError) as e:  # n_u != n_v
+        xy = [torch.ones(3, device="cuda"), torch.ones(4, device="cuda")]
+        ctx.estimate(tnsk.Network(xy, [(0, 1)], []), tnsk.Params(m=8, reps=2), out)
+    assert e.value.status == -1
+    with pytest.raises(tnsk.TnskError) as e:  # hyperedge: mode 1 in two contractions
+        ctx.estimate(tnsk.Network(net.tensors, [(1, 2), (1, 4), (3, 5)], [0]), tnsk.Params(m=8, reps=2), out)
+    assert e.value.status == -3
+    with pytest.raises(tnsk.TnskError) as e:  # groups must divide reps
+        ctx.estimate(net, tnsk.Params(m=8, reps=5, groups=2), out)
+    assert e.value.status == -1
+    ctx.sync()
