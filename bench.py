@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""bench.py -- estimates/s of the sketching estimators for tensor network contraction
+on GB300, through the C ABI of libtnsk.
+
+Workload (per GPU, per step): B = 64 pairs of tensor trains (8 sites, bond 32,
+physical 8, N(0, 1/sqrt(32)) entries, FP32). Every pair's inner product is
+estimated by both of the paper's methods at m = 1024 with 64 repetitions:
+  * method 2 (Sec. 4.4, acyclic) on the chain obtained by summing each site's
+    physical leg and merging its two bonds (8 tensors: 1024, 6 x 1024x1024, 1024);
+    this is the estimate that meets the 5% error target;
+  * method 1 (Sec. 4.2, any network) on the cyclic ladder (16 tensors, t = 22).
+One step = one tnsk_estimate_batch call over the 2B networks (all hot-path rows:
+tables, scatter, FFT/product, leaf/compose/V/GEMM/root, combine). `value` counts
+the B method-2 estimates per second; the method-1 estimates ride along in the
+same timed step.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 run under torchrun; each rank estimates its own B networks (weak
+scaling, no data-path collective) and rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "estimates/s at <=5% rel. err (chosen vs plain form, same GB300); HBM roofline %"
+UNIT = "estimates/s"
+M, REPS = 1024, 64
+# FP32 SIMT peak of GB300: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=64, help="tensor-train pairs per GPU per step")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def make_pairs(B, rank):
+    from paper_2603_07387_gb300 import workloads as W
+
+    pairs = []
+    for i in range(B):
+        A, Bc = W.tt_cores(seed=W.DATA_SEED + 100003 * rank + i)
+        pairs.append((W.tt_ladder(A, Bc), W.tt_chain(A, Bc)))
+    return pairs
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_uuid(dev):
+    import torch
+
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return dev
+
+
+# ---------------------------------------------------------------- exact values (for the error report)
+def exact_chain(chain_tensors_dev):
+    """tc of the chain (Def. "Tensor contraction"): v^T M_1 ... M_6 w in FP64 on the GPU."""
+    import torch
+
+    v = chain_tensors_dev[0].double()
+    for M_ in chain_tensors_dev[1:-1]:
+        v = v @ M_.double()
+    return float(v @ chain_tensors_dev[-1].double())
+
+
+def frob(ts):
+    return float(np.prod([float(t.double().norm()) for t in ts]))
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import torch
+
+    import __graft_entry__
+    from paper_2603_07387_gb300 import tnsk
+    from paper_2603_07387_gb300 import workloads as W
+
+    __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    B = args.batch
+    pairs = make_pairs(B, rank)
+    nets, params, host_bufs, dev_bufs = [], [], [], []
+    for ladder, chain in pairs:
+        for spec, method in ((ladder, tnsk.GENERAL), (chain, tnsk.ACYCLIC)):
+            ts = W.to_torch(spec, dev, torch.float32)
+            nets.append(tnsk.Network(ts, spec.edges, spec.open))
+            params.append(tnsk.Params(m=M, reps=REPS, seed=W.HASH_SEED, method=method))
+            dev_bufs.extend(ts)
+    outs = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in nets]
+    in_bytes = sum(t.numel() * t.element_size() for t in dev_bufs)
+    ctx = tnsk.Context(local, stream.cuda_stream)
+
+    def step():
+        ctx.estimate_batch(nets, params, outs)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    ctx.sync()
+    # ---------------- timed region (device time, CUDA events on the launching stream)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_uuid(local))
+    clocks.start()
+    time.sleep(0.3)
+    ctx.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    value = world * B / (ms / 1e3)
+
+    # ---------------- accuracy against the exact contraction (input-relative, Def. "ATNC")
+    est = [float(o.item()) for o in outs]
+    eps2, eps1 = [], []
+    for i in range(B):
+        chain_ts = nets[2 * i + 1].tensors
+        tc = exact_chain(chain_ts)
+        eps2.append((est[2 * i + 1] - tc) / frob(chain_ts))
+        eps1.append((est[2 * i] - tc) / frob(nets[2 * i].tensors))
+    err_m2 = float(np.sqrt(np.mean(np.square(eps2))))
+    err_m1 = float(np.sqrt(np.mean(np.square(eps1))))
+
+    # ---------------- roofline of the dominant kernel (largest share of device time)
+    total_ms = sum(v[0] for v in prof.values())
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    per_launch_ms = dom_ms / max(dom_n, 1)
+    gemm_flops = B * 6 * 2 * 1024 * 1024 * REPS  # 6 interior sites, 1024 x 1024, 64 reps
+    gemm_bytes = B * 6 * 1024 * 1024 * 4  # each interior matrix read once per 64-rep batch
+    traffic = read_traffic(dom)
+    if dom == "m2_gemm":
+        launches_per_step = dom_n / args.steps
+        achieved = gemm_flops / launches_per_step / (per_launch_ms / 1e3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 2), "peak": round(FP32_SIMT_PEAK_TFLOPS, 1),
+                "unit": "TFLOP/s", "frac": round(achieved / FP32_SIMT_PEAK_TFLOPS, 4),
+                "traffic": traffic,
+                "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived, not measured)",
+                "algorithmic_per_launch": {"flops": gemm_flops / launches_per_step,
+                                           "bytes": gemm_bytes / launches_per_step},
+                "hbm_view": {"achieved_gbs": round(gemm_bytes / launches_per_step / (per_launch_ms / 1e3) / 1e9, 1),
+                             "peak_gbs": hbm_peak()}}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": traffic}
+    roof["share"] = round(dom_ms / total_ms, 4) if total_ms else None
+
+    # ---------------- end to end through the public API, host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = [t.detach().cpu().pin_memory() for t in dev_bufs]
+        host_out = torch.zeros(len(outs), dtype=torch.float64).pin_memory()
+        out_cat = torch.zeros(len(outs), dtype=torch.float64, device=dev)
+
+        def e2e_step():
+            for h, d in zip(host, dev_bufs):
+                d.copy_(h, non_blocking=True)
+            ctx.estimate_batch(nets, params, outs)
+            torch.cat(outs, out=out_cat)
+            host_out.copy_(out_cat, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        k = max(1, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(k):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / k
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": round(world * B / (e2e_ms / 1e3), 2), "unit": UNIT, "ms_per_step": round(e2e_ms, 3),
+               "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": 8 * len(outs)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(pairs[0])
+    launches = int(sum(v[1] for v in prof.values()))
+    ctx.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "tt_pair_8x32x8 (configs[1]): per GPU per step 64 pairs of tensor trains; "
+                               "method 2 on the merged acyclic chain + method 1 on the cyclic ladder, "
+                               "m=1024, 64 reps, FP32",
+                   "networks_per_step": 2 * B, "estimate": "method-2 combined estimate of one pair",
+                   "m": M, "reps": REPS, "inputs_bytes_per_gpu": in_bytes,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+        "accuracy": {"method2_eps_rms": round(err_m2, 5), "method1_eps_rms": round(err_m1, 3),
+                     "eps": "|estimate - tc| / prod_k ||X_k||_F (Def. ATNC), RMS over the step's networks"},
+        "roofline": roof,
+        "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+def read_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary of `kernel`, or None when
+    the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{kernel}_tt_pair.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_2603_07387_gb300", "csrc", kv.get("source_file", "method2.cu"))
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if sha != kv.get("source_sha256"):
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- CPU baseline (oracle)
+def cpu_baseline(pair, budget_s: float = 12.0):
+    """The FP64 oracle, single-threaded, on a bounded sample of the workload: the first
+    pair, method 2 and method 1 with a few repetitions, scaled to one full estimate
+    (64 reps of each method)."""
+    import oracle
+
+    ladder, chain = pair
+    X2 = [np.asarray(x, dtype=np.float32).astype(np.float64) for x in chain.tensors]
+    X1 = [np.asarray(x, dtype=np.float32).astype(np.float64) for x in ladder.tensors]
+    root = int(np.argmin([x.size for x in X2]))
+    t0 = time.perf_counter()
+    oracle.m2_estimate(X2, chain.edges, m=M, reps=1, seed=1, root=root)
+    t_rep2 = time.perf_counter() - t0
+    r2 = int(max(1, min(REPS, budget_s / max(t_rep2, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.m2_estimate(X2, chain.edges, m=M, reps=r2, seed=1, root=root)
+    t2 = (time.perf_counter() - t0) / r2
+    t0 = time.perf_counter()
+    oracle.m1_estimate(X1, ladder.edges, [], m=M, reps=8, seed=1)
+    t1 = (time.perf_counter() - t0) / 8
+    per_estimate = REPS * (t1 + t2)
+    return {"value": round(1.0 / per_estimate, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 pair: method 2 with {r2} reps + method 1 with 8 reps, scaled to 64 reps each"}
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+
+    pairs = make_pairs(1, 0)
+    ladder, chain = pairs[0]
+    X2 = [np.asarray(x, dtype=np.float32).astype(np.float64) for x in chain.tensors]
+    X1 = [np.asarray(x, dtype=np.float32).astype(np.float64) for x in ladder.tensors]
+    root = int(np.argmin([x.size for x in X2]))
+
+    def step():  # one repetition of each method: 1/64 of one estimate
+        oracle.m2_estimate(X2, chain.edges, m=M, reps=1, seed=1, root=root)
+        oracle.m1_estimate(X1, ladder.edges, [], m=M, reps=1, seed=1)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    s_per_step = (time.perf_counter() - t0) / args.steps
+    value = 1.0 / (s_per_step * REPS)
+    sample = "1 pair per step, one repetition of each method (1/64 of one estimate), scaled to 64 reps"
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(s_per_step * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "tt_pair_8x32x8 (configs[1]): FP64 CPU oracle, same networks and parameters",
+                       "m": M, "reps": REPS},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -324,7 +324,8 @@ static void m1_sketch_one(const orc_net* net, const netinfo* in, int64_t m, cons
         }
         b %= m;
         double v = net->data[k][f];
-        if (abs_mode) v = fabs(v);
+        if (abs_mode == 1) v = fabs(v);
+        if (abs_mode == 2) v = v * v;
         xk[o * m + b] += (double)sigma * v;
     }
     free(idx);
@@ -352,7 +353,9 @@ int orc_m1_sketch(const orc_net* net, int64_t m, int32_t R, const int64_t* bins,
 
 /* Alg. 1: z = prod_k F x_k (Hadamard), y = (1/m) sum_j z_j. For an open output
  * entry o, each tensor contributes the spectrum of its sketch at its own part
- * of o. */
+ * of o. The scale s_out is the larger of (1/m) sum_j prod_k |F x_k(j)| and the
+ * root-sum-square of the terms of the expansion of y in the proof of Lemma
+ * "general-expectation-variance" (the same estimator on X_k^2 with unit signs). */
 int orc_m1_estimate(const orc_net* net, int64_t m, int32_t R, const int64_t* bins, const int8_t* signs,
                     double* y_out, double* s_out) {
     netinfo in;
@@ -366,6 +369,7 @@ int orc_m1_estimate(const orc_net* net, int64_t m, int32_t R, const int64_t* bin
     int64_t X = m1_x_per_rep(net, &in, m, xoff);
     double* x = (double*)malloc(sizeof(double) * (size_t)(X > 0 ? X : 1));
     cplx* xf = (cplx*)malloc(sizeof(cplx) * (size_t)(X > 0 ? X : 1));
+    cplx* xf2 = (cplx*)malloc(sizeof(cplx) * (size_t)(X > 0 ? X : 1)); /* squared terms */
     cplx* tmp = (cplx*)malloc(sizeof(cplx) * (size_t)m);
     int64_t* oidx = (int64_t*)malloc(sizeof(int64_t) * ((size_t)net->n_open + 1));
     int64_t* ok = (int64_t*)malloc(sizeof(int64_t) * (size_t)net->p);
@@ -375,6 +379,13 @@ int orc_m1_estimate(const orc_net* net, int64_t m, int32_t R, const int64_t* bin
             for (int64_t o = 0; o < in.n_opentot[k]; ++o) {
                 for (int64_t j = 0; j < m; ++j) tmp[j] = x[xoff[k] + o * m + j];
                 fft_c(tmp, m, xf + xoff[k] + o * m); /* F x_k */
+            }
+            if (s_out) {
+                m1_sketch_one(net, &in, m, bins + (int64_t)r * L, signs + (int64_t)r * L, 2, k, x + xoff[k]);
+                for (int64_t o = 0; o < in.n_opentot[k]; ++o) {
+                    for (int64_t j = 0; j < m; ++j) tmp[j] = x[xoff[k] + o * m + j];
+                    fft_c(tmp, m, xf2 + xoff[k] + o * m);
+                }
             }
         }
         for (int64_t o = 0; o < in.O; ++o) {
@@ -391,25 +402,31 @@ int orc_m1_estimate(const orc_net* net, int64_t m, int32_t R, const int64_t* bin
                     if (in.edge_of[g] < 0) a = a * net->dims[g] + oidx[in.open_pos[g]];
                 ok[k] = a;
             }
-            cplx acc = 0;
+            cplx acc = 0, acc2 = 0;
             double sacc = 0;
             for (int64_t j = 0; j < m; ++j) {
-                cplx z = 1;
+                cplx z = 1, z2 = 1;
                 double za = 1;
                 for (int32_t k = 0; k < net->p; ++k) {
                     cplx v = xf[xoff[k] + ok[k] * m + j];
                     z *= v;
                     za *= cabs(v);
+                    if (s_out) z2 *= xf2[xoff[k] + ok[k] * m + j];
                 }
                 acc += z;
+                acc2 += z2;
                 sacc += za;
             }
             y_out[(int64_t)r * in.O + o] = creal(acc) / (double)m;
-            if (s_out) s_out[(int64_t)r * in.O + o] = sacc / (double)m;
+            if (s_out) {
+                double rss = sqrt(fmax(creal(acc2) / (double)m, 0.0));
+                s_out[(int64_t)r * in.O + o] = fmax(sacc / (double)m, rss);
+            }
         }
     }
     free(x);
     free(xf);
+    free(xf2);
     free(tmp);
     free(oidx);
     free(ok);
@@ -438,6 +455,7 @@ typedef struct {
     netinfo in;
     tnode* node;
     int64_t m;
+    int sq_mode; /* 1: entries squared and every sign +1 (root-sum-square pass) */
     /* tables of the current rep */
     const int64_t* ebins;   /* [L] edge count sketches C_{k,l} */
     const int8_t* esigns;
@@ -487,10 +505,10 @@ static void rsh(const m2ctx* cx, int32_t k, const int64_t* slot_idx, int64_t* b,
             int32_t e = nd->child_edge[j];
             int64_t pos = cx->in.eoff[e] + slot_idx[j];
             b[j] = cx->ebins[pos];
-            sigma *= cx->esigns[pos];
+            if (!cx->sq_mode) sigma *= cx->esigns[pos];
         } else {
             b[j] = cx->pad_bin[k][j];
-            sigma *= cx->pad_sign[k][j];
+            if (!cx->sq_mode) sigma *= cx->pad_sign[k][j];
         }
     }
     for (int32_t l = nd->qt; l >= 2; l >>= 1) {
@@ -499,7 +517,7 @@ static void rsh(const m2ctx* cx, int32_t k, const int64_t* slot_idx, int64_t* b,
             const int64_t* hb = cx->t_bin[k] + t_off(nd->qt, l, j, 1, m);
             const int8_t* sa = cx->t_sign[k] + t_off(nd->qt, l, j, 0, m);
             const int8_t* sb = cx->t_sign[k] + t_off(nd->qt, l, j, 1, m);
-            sigma *= sa[b[2 * j]] * sb[b[2 * j + 1]];
+            if (!cx->sq_mode) sigma *= sa[b[2 * j]] * sb[b[2 * j + 1]];
             b[j] = (ha[b[2 * j]] + hb[b[2 * j + 1]]) % m;
         }
     }
@@ -532,11 +550,12 @@ static double* sketched_matvec(const m2ctx* cx, int32_t l, const double* z) {
         int64_t ipar = idx[nd->parent_mode];
         int64_t pos = cx->in.eoff[nd->parent_edge] + ipar;
         int64_t j = cx->ebins[pos];
-        int64_t s = cx->esigns[pos];
+        int64_t s = cx->sq_mode ? 1 : cx->esigns[pos];
         slot_values(cx, l, idx, sidx);
         int64_t sigma, bb;
         rsh(cx, l, sidx, b, &sigma, &bb);
         double v = net->data[l][f];
+        if (cx->sq_mode) v = v * v;
         y[j] += v * z[bb] * (double)sigma * (double)s;
     }
     free(idx);
@@ -554,7 +573,7 @@ static double* tensor_sketch_pair(const m2ctx* cx, const int64_t* ha, const int8
     for (int64_t a = 0; a < m; ++a) {
         if (u[a] == 0.0) continue;
         for (int64_t c = 0; c < m; ++c) {
-            double sg = (double)(sa[a] * sb[c]);
+            double sg = cx->sq_mode ? 1.0 : (double)(sa[a] * sb[c]);
             out[(ha[a] + hb[c]) % m] += sg * u[a] * v[c];
         }
     }
@@ -581,7 +600,7 @@ static double* neighbors_sketch(const m2ctx* cx, int32_t k) {
             free(rl);
         } else {
             x[j] = (double*)calloc((size_t)m, sizeof(double));
-            x[j][cx->pad_bin[k][j]] = (double)cx->pad_sign[k][j];
+            x[j][cx->pad_bin[k][j]] = cx->sq_mode ? 1.0 : (double)cx->pad_sign[k][j];
         }
     }
     /* Q_k = Q_2 Q_4 ... Q_qt: apply level qt first, then qt/2, ..., 2 */
@@ -721,7 +740,8 @@ int orc_m2_estimate(const orc_net* net, int32_t root, int64_t m, int32_t R, uint
                                          cx.t_sign[k] + o);
                     }
         }
-        {
+        for (int pass = 0; pass < (s_out ? 2 : 1); ++pass) {
+            cx.sq_mode = pass;
             /* x_o = R_o vec(X_o): scatter every component of the root by Alg. 4 */
             const tnode* nd = &cx.node[root];
             int32_t qo = net->order[root];
@@ -735,6 +755,7 @@ int orc_m2_estimate(const orc_net* net, int32_t root, int64_t m, int32_t R, uint
                 int64_t sigma, bb;
                 rsh(&cx, root, sidx, b, &sigma, &bb);
                 double v = net->data[root][f];
+                if (cx.sq_mode) v = v * v;
                 xo[bb] += (double)sigma * v;
             }
             /* r_o = NeighborsSketch(o); y = x_o^T r_o */
@@ -746,9 +767,13 @@ int orc_m2_estimate(const orc_net* net, int32_t root, int64_t m, int32_t R, uint
                 nx += xo[j] * xo[j];
                 nr += ro[j] * ro[j];
             }
-            y_out[r] = y;
-            /* scale for tolerances: |y| <= ||x_o|| ||r_o|| (Cauchy-Schwarz) */
-            if (s_out) s_out[r] = sqrt(nx) * sqrt(nr);
+            if (pass == 0) {
+                y_out[r] = y;
+                /* |y| <= ||x_o|| ||r_o|| (Cauchy-Schwarz) */
+                if (s_out) s_out[r] = sqrt(nx) * sqrt(nr);
+            } else { /* root-sum-square of the terms of the expansion of Eq. 2 */
+                s_out[r] = fmax(s_out[r], sqrt(fmax(y, 0.0)));
+            }
             free(ro);
             free(xo);
             free(idx);

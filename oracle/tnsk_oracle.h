@@ -75,14 +75,16 @@ int orc_m1_tables(const orc_net* net, uint64_t seed, int32_t R, int64_t m,
 int orc_m1_sketch(const orc_net* net, int64_t m, int32_t R, const int64_t* bins,
                   const int8_t* signs, int32_t abs_mode, double* x_out);
 /* Per-rep estimates y[r][o] (Alg. 1; open legs per Corollary "full-to-partial")
- * and the cancellation-aware scale s[r][o] = (1/m) sum_j prod_k |F x_k(j)|. */
+ * and the cancellation-aware scale s[r][o] = max((1/m) sum_j prod_k |F x_k(j)|,
+ * root-sum-square of the terms of y expanded over index combinations). */
 int orc_m1_estimate(const orc_net* net, int64_t m, int32_t R, const int64_t* bins,
                     const int8_t* signs, double* y_out, double* s_out);
 
 /* Method 2 (Alg. 2 with Alg. 4 and Alg. 5) for an acyclic full network rooted at
  * `root`. Edge count sketches may be overridden ([R][L], same layout as method 1).
- * s_out = ||x_o||_2 ||r_o||_2, the Cauchy-Schwarz bound of y = x_o^T r_o (Alg. 2
- * last line), used as the scale of rounding tolerances. */
+ * s_out = max(||x_o|| ||r_o||, the root-sum-square of the terms of y expanded
+ * over all index combinations (the same recursion on X_k^2 with every sign +1)),
+ * the scale of rounding tolerances. */
 int orc_m2_estimate(const orc_net* net, int32_t root, int64_t m, int32_t R, uint64_t seed,
                     const int64_t* edge_bins, const int8_t* edge_signs,
                     double* y_out, double* s_out);

@@ -161,7 +161,7 @@ def test_batch_matches_oracle_per_network(ctx):
     params = []
     for i, s in enumerate(specs):
         method = tnsk.ACYCLIC if s.name.startswith("tree") else tnsk.GENERAL
-        params.append(tnsk.Params(m=64 * (1 + i % 3), reps=4, groups=2, seed=1000 + i, method=method))
+        params.append(tnsk.Params(m=64 << (i % 3), reps=4, groups=2, seed=1000 + i, method=method))
     nets = [gpu_network(s, torch.float32) for s in specs]
     outs, pers = [], []
     for s, p in zip(specs, params):
