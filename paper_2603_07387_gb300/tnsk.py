@@ -41,6 +41,7 @@ SYMBOLS = (
     "tnsk_m1_sketch",
     "tnsk_estimate",
     "tnsk_estimate_batch",
+    "tnsk_estimate_static",
     "tnsk_profile",
     "tnsk_profile_read",
     "tnsk_sync",
@@ -114,6 +115,8 @@ def load_library(path: str = LIB_PATH):
     L.tnsk_estimate_batch.restype = i32
     L.tnsk_estimate_batch.argtypes = [vp, i32, ctypes.POINTER(_Network), ctypes.POINTER(_Params),
                                       ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.tnsk_estimate_static.restype = i32
+    L.tnsk_estimate_static.argtypes = [ctypes.POINTER(_Network), ctypes.POINTER(_Params), vp, vp, vp]
     L.tnsk_profile.restype = i32
     L.tnsk_profile.argtypes = [vp, i32]
     L.tnsk_profile_read.restype = i32
@@ -194,6 +197,19 @@ class _NetHolder:
 def _params(p: Params) -> _Params:
     return _Params(int(p.m), int(p.reps), int(p.groups), int(p.seed) & ((1 << 64) - 1), int(p.method),
                    int(p.root), int(p.prec))
+
+
+def estimate_static(net: Network, params: Params, out, per_rep=None, stream=None):
+    """tnsk_estimate_static: method-1 estimate with no device allocation (all scratch
+    in the library's fixed 16 MiB device array). Needs no Context."""
+    L = load_library()
+    nh = _NetHolder(net)
+    pr = _params(params)
+    st = L.tnsk_estimate_static(ctypes.byref(nh.c), ctypes.byref(pr), out.data_ptr(),
+                                per_rep.data_ptr() if per_rep is not None else None,
+                                ctypes.c_void_p(int(stream)) if stream else None)
+    if st != TNSK_OK:
+        raise TnskError(st, "tnsk_estimate_static")
 
 
 class Context:
