@@ -152,6 +152,20 @@ typedef enum {
 tnsk_status tnsk_profile(tnsk_ctx* ctx, int32_t enable);
 tnsk_status tnsk_profile_read(tnsk_ctx* ctx, double* ms, int64_t* launches);
 
+/* A batch planned once and run many times. tnsk_plan_create validates the B
+ * networks and lays out and uploads every launch descriptor into device memory
+ * owned by the plan (cudaMalloc); each tnsk_plan_run enqueues the whole launch
+ * sequence of tnsk_estimate_batch on the ctx stream, reading the tensors and
+ * writing outs / per_reps at the addresses given at creation (new data in the
+ * same buffers is picked up by the next run). The plan keeps those addresses:
+ * the buffers must stay allocated while it exists. tnsk_plan_destroy waits for
+ * the device and frees the plan. Arguments and errors as tnsk_estimate_batch. */
+typedef struct tnsk_plan tnsk_plan;
+tnsk_status tnsk_plan_create(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
+                             double* const* outs, double* const* per_reps, tnsk_plan** plan);
+tnsk_status tnsk_plan_run(tnsk_ctx* ctx, tnsk_plan* plan);
+tnsk_status tnsk_plan_destroy(tnsk_plan* plan);
+
 /* Method-1 estimate that allocates no device memory (the paper has no
  * counterpart; this is a deployment variant of tnsk_estimate).
  * For callers that cannot call cudaMalloc: code running inside a stream capture

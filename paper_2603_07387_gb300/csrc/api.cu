@@ -239,43 +239,38 @@ tnsk_status tnsk_count_sketch(tnsk_ctx* ctx, uint64_t seed, uint64_t rep, uint64
     return TNSK_OK;
 }
 
-// Batch driver shared by tnsk_estimate, tnsk_estimate_batch and tnsk_m1_sketch.
-static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
-                             double* const* outs, double* const* per_reps, void* sketch_out) {
-    tnsk_status st = check_ctx(ctx);
-    if (st != TNSK_OK) return st;
+// Host part of a batch: validation and layout of descriptors and scratch.
+static tnsk_status build_plan(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
+                              double* const* outs, double* const* per_reps, bool sketch_only, BatchPlan& plan,
+                              bool& fp64) {
     if (B < 0 || (B > 0 && (!nets || !params))) return fail(ctx, TNSK_ERR_INVALID, "null batch arguments");
-    if (B == 0) return TNSK_OK;
     std::vector<NetInfo> infos(B);
     for (int b = 0; b < B; ++b) {
         std::string why;
-        st = validate(nets[b], params[b], infos[b], why);
+        tnsk_status st = validate(nets[b], params[b], infos[b], why);
         if (st != TNSK_OK) return fail(ctx, st, "network " + std::to_string(b) + ": " + why);
-        if (!sketch_out && (!outs || !outs[b])) return fail(ctx, TNSK_ERR_INVALID, "null output buffer");
+        if (!sketch_only && (!outs || !outs[b])) return fail(ctx, TNSK_ERR_INVALID, "null output buffer");
     }
     // precision of the whole batch: one kind per launch sequence
-    const bool fp64 = params[0].prec == TNSK_PREC_FP64;
+    fp64 = B > 0 && params[0].prec == TNSK_PREC_FP64;
     for (int b = 1; b < B; ++b)
         if ((params[b].prec == TNSK_PREC_FP64) != fp64)
             return fail(ctx, TNSK_ERR_UNSUPPORTED, "mixed precisions in one batch");
+    return plan_batch(infos, nets, params, outs, per_reps, fp64, sketch_only, plan, ctx->last_error);
+}
 
-    BatchPlan plan;
-    st = plan_batch(infos, nets, params, outs, per_reps, fp64, sketch_out != nullptr, plan, ctx->last_error);
-    if (st != TNSK_OK) return st;
-    st = ensure_scratch(ctx, plan.arena.used);
-    if (st != TNSK_OK) return st;
-    unsigned char* base = ctx->scratch;
+// Device part: the launch sequence of a planned batch whose descriptors are
+// already at base + plan.desc_off.
+static tnsk_status launch_plan(tnsk_ctx* ctx, const BatchPlan& plan, unsigned char* base, bool fp64,
+                               void* sketch_out) {
     cudaStream_t s = ctx->stream;
-    // descriptors (pageable host staging: the copy is complete on return)
-    if (!plan.host_desc.empty())
-        TNSK_CUDA(cudaMemcpyAsync(base + plan.desc_off, plan.host_desc.data(), plan.host_desc.size(),
-                                  cudaMemcpyHostToDevice, s));
     if (plan.zero_bytes) TNSK_CUDA(cudaMemsetAsync(base + plan.zero_off, 0, plan.zero_bytes, s));
     if (sketch_out && plan.sketch_user_bytes) TNSK_CUDA(cudaMemsetAsync(sketch_out, 0, plan.sketch_user_bytes, s));
     Profiler& pf = ctx->prof;
     if (plan.n_reqs) {
         pf.begin(TNSK_K_TABLES, s);
         TNSK_CUDA(launch_draw_tables((const TabReq*)(base + plan.reqs_off), plan.n_reqs, plan.n_table_words,
+                                     plan.n_coef_rows, (HashCoef*)(base + plan.coef_off),
                                      (uint32_t*)(base + plan.tabs_off), s));
         pf.end(s);
     }
@@ -285,7 +280,7 @@ static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets,
         TNSK_CUDA(launch_m1_scatter((const M1Tensor*)(base + plan.m1.tens_off), (const M1Net*)(base + plan.m1.nets_off),
                                     (const M1Work*)(base + plan.m1.work_off), plan.m1.n_work,
                                     (const uint32_t*)(base + plan.tabs_off), xs, fp64, plan.m1.scatter_smem,
-                                    plan.m1.idx32, s));
+                                    plan.m1.max_order, s));
         pf.end(s);
         if (!sketch_out) {
             pf.begin(TNSK_K_M1_SPECTRUM, s);
@@ -300,8 +295,9 @@ static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets,
         }
     }
     if (plan.m2.n_nets && !sketch_out) {
-        st = run_method2(plan, base, fp64, fp64 ? (const void* const*)ctx->d_tw64 : (const void* const*)ctx->d_tw32,
-                         s, pf, ctx->last_error);
+        tnsk_status st =
+            run_method2(plan, base, fp64, fp64 ? (const void* const*)ctx->d_tw64 : (const void* const*)ctx->d_tw32,
+                        s, pf, ctx->last_error);
         if (st != TNSK_OK) return st;
     }
     if (!sketch_out && plan.n_comb) {
@@ -312,6 +308,32 @@ static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets,
     }
     return TNSK_OK;
 }
+
+// Batch driver shared by tnsk_estimate, tnsk_estimate_batch and tnsk_m1_sketch.
+static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
+                             double* const* outs, double* const* per_reps, void* sketch_out) {
+    tnsk_status st = check_ctx(ctx);
+    if (st != TNSK_OK) return st;
+    if (B == 0) return TNSK_OK;
+    BatchPlan plan;
+    bool fp64 = false;
+    st = build_plan(ctx, B, nets, params, outs, per_reps, sketch_out != nullptr, plan, fp64);
+    if (st != TNSK_OK) return st;
+    st = ensure_scratch(ctx, plan.arena.used);
+    if (st != TNSK_OK) return st;
+    // descriptors (pageable host staging: the copy is complete on return)
+    if (!plan.host_desc.empty())
+        TNSK_CUDA(cudaMemcpyAsync(ctx->scratch + plan.desc_off, plan.host_desc.data(), plan.host_desc.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+    return launch_plan(ctx, plan, ctx->scratch, fp64, sketch_out);
+}
+
+struct tnsk_plan {
+    BatchPlan plan;
+    bool fp64 = false;
+    int device = 0;
+    unsigned char* dev = nullptr;  // descriptors + scratch of this plan
+};
 
 tnsk_status tnsk_profile(tnsk_ctx* ctx, int32_t enable) {
     if (!ctx) return TNSK_ERR_INVALID;
@@ -339,6 +361,56 @@ tnsk_status tnsk_profile_read(tnsk_ctx* ctx, double* ms, int64_t* launches) {
     }
     ctx->prof.recs.clear();
     cudaGetLastError();
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_plan_create(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
+                             double* const* outs, double* const* per_reps, tnsk_plan** out) {
+    if (!out) return TNSK_ERR_INVALID;
+    *out = nullptr;
+    tnsk_status st = check_ctx(ctx);
+    if (st != TNSK_OK) return st;
+    tnsk_plan* p = new tnsk_plan();
+    p->device = ctx->device;
+    st = build_plan(ctx, B, nets, params, outs, per_reps, false, p->plan, p->fp64);
+    if (st != TNSK_OK) {
+        delete p;
+        return st;
+    }
+    if (cudaMalloc((void**)&p->dev, std::max<size_t>(p->plan.arena.used, 256)) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return fail(ctx, TNSK_ERR_OOM, "plan scratch allocation failed");
+    }
+    cudaError_t e = cudaSuccess;
+    if (!p->plan.host_desc.empty())
+        e = cudaMemcpy(p->dev + p->plan.desc_off, p->plan.host_desc.data(), p->plan.host_desc.size(),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p->dev);
+        delete p;
+        return cuda_fail(ctx, e, "cudaMemcpy(plan descriptors)");
+    }
+    p->plan.host_desc.clear();
+    p->plan.host_desc.shrink_to_fit();
+    *out = p;
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_plan_run(tnsk_ctx* ctx, tnsk_plan* plan) {
+    if (!plan) return TNSK_ERR_INVALID;
+    tnsk_status st = check_ctx(ctx);
+    if (st != TNSK_OK) return st;
+    if (ctx->device != plan->device) return fail(ctx, TNSK_ERR_INVALID, "plan made on another device");
+    return launch_plan(ctx, plan->plan, plan->dev, plan->fp64, nullptr);
+}
+
+tnsk_status tnsk_plan_destroy(tnsk_plan* plan) {
+    if (!plan) return TNSK_ERR_INVALID;
+    cudaSetDevice(plan->device);
+    cudaDeviceSynchronize();
+    cudaFree(plan->dev);
+    delete plan;
     return TNSK_OK;
 }
 

@@ -88,6 +88,7 @@ struct TabReq {
     int64_t out_off;    // packed-table offset of rep 0
     int64_t rep_stride; // distance between consecutive reps
     int64_t first;      // first flat entry of this request (prefix over R*n)
+    int64_t crow;       // first coefficient row of this request (prefix over R)
     int32_t R;
     uint32_t mask;      // m - 1
 };
@@ -161,7 +162,8 @@ struct M1Work {
     int32_t tensor;
     int32_t rep0;
     int32_t nrep;
-    int32_t priv;        // 1: shared-memory bins, 0: global atomics
+    int32_t priv;        // 0: global atomics; 1: shared-memory bins flushed by atomics;
+                         // 2: shared-memory bins of a whole tensor, flushed by stores
 };
 
 template <typename T>

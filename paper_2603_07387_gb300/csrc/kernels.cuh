@@ -56,11 +56,12 @@ struct CombineItem {  // one output entry of one network
     double* per_rep;  // optional [R][O]
 };
 
-cudaError_t launch_draw_tables(const TabReq* d_reqs, int nreq, int64_t total, uint32_t* d_out, cudaStream_t s);
+cudaError_t launch_draw_tables(const TabReq* d_reqs, int nreq, int64_t total, int64_t rows, HashCoef* d_coef,
+                               uint32_t* d_out, cudaStream_t s);
 cudaError_t launch_count_sketch(uint64_t seed, uint64_t rep, uint64_t tid, int64_t n, int64_t m, int32_t* bins,
                                 int8_t* signs, cudaStream_t s);
 cudaError_t launch_m1_scatter(const M1Tensor* d_tens, const M1Net* d_nets, const M1Work* d_work, int n_work,
-                              const uint32_t* d_tabs, void* d_xs, bool fp64, size_t smem, bool idx32,
+                              const uint32_t* d_tabs, void* d_xs, bool fp64, size_t smem, int max_order,
                               cudaStream_t s);
 cudaError_t launch_m1_spectrum(const M1Tensor* d_tens, const M1Net* d_nets, const OpenMode* d_opens,
                                const int2* d_items, int n_items, const void* d_xs, const void* const* d_tws,

@@ -9,6 +9,8 @@
 //   a4                      y_r = (1/m) sum_j prod_k (F x_k)(j) (Alg. 1 last line;
 //                           open output entries per Corollary "full-to-partial-tc")
 //   a9  combine_kernel      median of group means in FP64 (Theorem 1)
+#include <algorithm>
+
 #include "fft.cuh"
 #include "kernels.cuh"
 
@@ -19,7 +21,10 @@ namespace tnsk {
 // ---------------------------------------------------------------------------
 // Shared memory: [nrep][TT] packed table words (complement applied), then the
 // privatised bins [nrep][O][m] when w.priv. TT = sum of the contracted dims.
-template <typename AccT, typename IdxT>
+// Each thread walks entries f, f + S, f + 2S, ... (S = blockDim.x) keeping the
+// multi-index of f in registers and adding the mixed-radix digits of S with
+// carries, so no entry needs a division. MAXD bounds the tensor order.
+template <typename AccT, int MAXD>
 __global__ void __launch_bounds__(256) m1_scatter_kernel(const M1Tensor* __restrict__ tens,
                                                          const M1Net* __restrict__ nets,
                                                          const M1Work* __restrict__ work,
@@ -49,10 +54,10 @@ __global__ void __launch_bounds__(256) m1_scatter_kernel(const M1Tensor* __restr
     AccT* s_bin = reinterpret_cast<AccT*>(smem_raw + (((size_t)nrep * TT * 4 + 15) & ~(size_t)15));
 
     // tables of this tensor's contracted modes for the batch of reps
-    const int64_t tab_words = (int64_t)nrep * TT;
-    for (int64_t q = threadIdx.x; q < tab_words; q += blockDim.x) {
-        int r = (int)(q / TT);
-        int loc = (int)(q - (int64_t)r * TT);
+    const int tab_words = nrep * TT;  // fits shared memory
+    for (int q = threadIdx.x; q < tab_words; q += blockDim.x) {
+        int r = q / TT;
+        int loc = q - r * TT;
         int d = 0;
         for (int dd = 0; dd < order; ++dd)
             if (sT.tab[dd] >= 0 && loc >= sbase[dd] && loc < sbase[dd] + sT.dims[dd]) d = dd;
@@ -65,31 +70,46 @@ __global__ void __launch_bounds__(256) m1_scatter_kernel(const M1Tensor* __restr
     const int64_t nbins = (int64_t)nrep * O * m;
     if (w.priv)
         for (int64_t q = threadIdx.x; q < nbins; q += blockDim.x) s_bin[q] = AccT(0);
+
+    // block-uniform per-mode data in registers (modes >= order: dim 1, not contracted)
+    int dim[MAXD], base[MAXD], dig[MAXD], step[MAXD];
+    bool ctr[MAXD];
+    int64_t ostr[MAXD];
+    const bool has_open = O > 1;
+    {
+        int64_t f0 = w.begin + threadIdx.x;
+        int64_t sv = blockDim.x;
+#pragma unroll
+        for (int d = MAXD - 1; d >= 0; --d) {
+            const bool live = d < order;
+            dim[d] = live ? sT.dims[d] : 1;
+            base[d] = sbase[d < TNSK_MAX_ORDER ? d : 0];
+            ctr[d] = live && sT.tab[d] >= 0;
+            ostr[d] = live ? sT.ostride[d] : 0;
+            dig[d] = (int)(f0 % dim[d]);
+            f0 /= dim[d];
+            step[d] = (int)(sv % dim[d]);
+            sv /= dim[d];
+        }
+    }
     __syncthreads();
 
     AccT* gx = xs + N.x_off + sT.xoff;  // + (rep0 + r) * N.X + o * m + b
     for (int64_t f = w.begin + threadIdx.x; f < w.end; f += blockDim.x) {
         const AccT v = load_as<AccT>(sT.data, sT.dtype, f);
-        int32_t midx[TNSK_MAX_ORDER];
+        int off[MAXD];
         int64_t o = 0;
-        IdxT rem = (IdxT)f;
 #pragma unroll
-        for (int d = TNSK_MAX_ORDER - 1; d >= 0; --d) {
-            if (d < order) {
-                IdxT n = (IdxT)sT.dims[d];
-                IdxT qt = rem / n;
-                int i = (int)(rem - qt * n);
-                rem = qt;
-                midx[d] = sbase[d] + i;
-                o += (int64_t)i * sT.ostride[d];
-            }
+        for (int d = 0; d < MAXD; ++d) {
+            off[d] = base[d] + dig[d];
+            if (has_open) o += (int64_t)dig[d] * ostr[d];
         }
         for (int r = 0; r < nrep; ++r) {
-            uint32_t h = 0;
             const uint32_t* tr = s_tab + r * TT;
+            uint32_t h = 0;
 #pragma unroll
-            for (int d = 0; d < TNSK_MAX_ORDER; ++d)
-                if (d < order && sT.tab[d] >= 0) h += tr[midx[d]];
+            for (int d = 0; d < MAXD; ++d)
+                if (ctr[d]) h += tr[off[d]];
             const AccT sv = (h & TNSK_SIGN_BIT) ? -v : v;
             const uint32_t b = h & mask;
             if (w.priv)
@@ -97,73 +117,38 @@ __global__ void __launch_bounds__(256) m1_scatter_kernel(const M1Tensor* __restr
             else
                 atomicAdd(&gx[(int64_t)(w.rep0 + r) * N.X + o * m + b], sv);
         }
+        // advance the multi-index by blockDim.x (mixed-radix add with carries)
+        int carry = 0;
+#pragma unroll
+        for (int d = MAXD - 1; d >= 0; --d) {
+            int t = dig[d] + step[d] + carry;
+            carry = t >= dim[d];
+            dig[d] = carry ? t - dim[d] : t;
+        }
     }
     if (!w.priv) return;
     __syncthreads();
-    for (int64_t q = threadIdx.x; q < nbins; q += blockDim.x) {
+    // the bins of reps [rep0, rep0 + nrep) of this tensor are contiguous per rep
+    const int per = (int)(O * m);  // the bins fit shared memory
+    for (int q = threadIdx.x; q < (int)nbins; q += blockDim.x) {
         AccT val = s_bin[q];
-        if (val != AccT(0)) {
-            int64_t r = q / (O * m);
-            int64_t ob = q - r * (O * m);
-            atomicAdd(&gx[(int64_t)(w.rep0 + r) * N.X + ob], val);
-        }
+        int r = q / per;
+        int ob = q - r * per;
+        AccT* dst = &gx[(int64_t)(w.rep0 + r) * N.X + ob];
+        if (w.priv == 2)
+            *dst = val;  // this item owns these bins: no other CTA writes them
+        else if (val != AccT(0))
+            atomicAdd(dst, val);
     }
 }
 
 // ---------------------------------------------------------------------------
 // a3 + a4: spectra, Hadamard product, bin sum
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T block_max(T v, T* red) {
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, s));
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        v = lane < (int)(blockDim.x >> 5) ? red[lane] : T(0);
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, s));
-        if (lane == 0) red[0] = v;
-    }
-    __syncthreads();
-    T r = red[0];
-    __syncthreads();
-    return r;
-}
-
-// Loads sketch x (length m) as packed complex z[n] = x[2n] + i x[2n+1] (m >= 2) or
-// z[0] = x[0] (m = 1), FFTs it, and leaves its power-of-two exponent e (so that
-// 2^-e F x has entries of magnitude < 1) in *s_e. All threads must call.
-template <typename T>
-__device__ void load_fft_scale(const T* __restrict__ x, int64_t m, int log2m, Cplx<T>* z,
-                               const Cplx<T>* __restrict__ tw, T* red, int* s_e) {
-    const int log2M = log2m > 0 ? log2m - 1 : 0;
-    const int M = 1 << log2M;
-    if (m == 1) {
-        if (threadIdx.x == 0) z[0] = {x[0], T(0)};
-    } else {
-        for (int n = threadIdx.x; n < M; n += blockDim.x) z[n] = {x[2 * n], x[2 * n + 1]};
-    }
-    __syncthreads();
-    if (m > 1) block_fft_dif(z, 1, log2M, tw);
-    const int K = m == 1 ? 1 : M + 1;
-    T mx = T(0);
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        Cplx<T> X = m == 1 ? z[0] : unpack_bin(z, k, log2M, tw);
-        mx = fmax(mx, fmax(fabs(X.x), fabs(X.y)));
-    }
-    mx = block_max(mx, red);
-    if (threadIdx.x == 0) {
-        int e = 0;
-        if (mx > T(0)) frexp(mx, &e);
-        *s_e = e;
-    }
-    __syncthreads();
-}
-
-// One CTA per (network, rep). Shared memory: z [M] and P [M+1] complex (T).
+// One CTA per (network, rep). The sketches of the network (one per tensor, or
+// one per open index of a tensor with open legs) are transformed G at a time:
+// shared memory holds z [G][M] (packed complex sketches, FFT in place) and
+// P [M+1] (running Hadamard product of the folded spectra, scaled by 2^-E).
 template <typename T>
 __global__ void __launch_bounds__(256) m1_spectrum_kernel(const M1Tensor* __restrict__ tens,
                                                           const M1Net* __restrict__ nets,
@@ -171,10 +156,16 @@ __global__ void __launch_bounds__(256) m1_spectrum_kernel(const M1Tensor* __rest
                                                           const int2* __restrict__ items, const T* __restrict__ xs,
                                                           const Cplx<T>* const* __restrict__ tws,
                                                           Cplx<T>* __restrict__ spec, int* __restrict__ sexp,
-                                                          double* __restrict__ yrep) {
+                                                          double* __restrict__ yrep, int gmax) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T red[32];
-    __shared__ int s_e;
+    constexpr int kMaxG = 16;
+    __shared__ int s_k[kMaxG];       // tensor of each sketch in the group
+    __shared__ int64_t s_o[kMaxG];   // its open index
+    __shared__ int64_t s_x[kMaxG];   // offset of its sketch in the rep's sketch vector
+    __shared__ int64_t s_so[kMaxG];  // its open-spectrum offset, -1 when folded into P
+    __shared__ int64_t s_eo[kMaxG];  // its exponent slot
+    __shared__ unsigned long long s_max[kMaxG];  // bits of max |Re|,|Im| as a double (non-negative: ordered)
+    __shared__ int s_e[kMaxG];      // its power-of-two exponent
     __shared__ double dred[32];
     const int2 it = items[blockIdx.x];
     const M1Net& N = nets[it.x];
@@ -184,42 +175,91 @@ __global__ void __launch_bounds__(256) m1_spectrum_kernel(const M1Tensor* __rest
     const int log2M = log2m > 0 ? log2m - 1 : 0;
     const int M = 1 << log2M;
     const int K = m == 1 ? 1 : M + 1;
-    const Cplx<T>* tw = tws[log2m];
     Cplx<T>* z = reinterpret_cast<Cplx<T>*>(smem_raw);
-    Cplx<T>* P = z + M;
+    Cplx<T>* P = z + (size_t)gmax * M;
+    Cplx<T>* tw = P + M + 1;  // twiddles of this m, copied once
     const int64_t O = N.O;
     if (O == 0) return;
     for (int k = threadIdx.x; k < K; k += blockDim.x) P[k] = {T(1), T(0)};
+    {
+        const Cplx<T>* twg = tws[log2m];
+        for (int k = threadIdx.x; k < M; k += blockDim.x) tw[k] = twg[k];
+    }
     int E = 0;  // P holds 2^-E prod_k F x_k
     const T* xr = xs + N.x_off + (int64_t)r * N.X;
-    for (int k = 0; k < N.p; ++k) {
-        const M1Tensor& Tk = tens[N.t0 + k];
-        const bool folded = Tk.soff < 0;
-        const int64_t nsk = folded ? 1 : Tk.O;
-        for (int64_t o = 0; o < nsk; ++o) {
-            load_fft_scale(xr + Tk.xoff + o * m, m, log2m, z, tw, red, &s_e);
-            const int e = s_e;
-            const T sc = (T)ldexp(1.0, -e);
-            if (folded) {
-                for (int kk = threadIdx.x; kk < K; kk += blockDim.x) {
-                    Cplx<T> X = m == 1 ? z[0] : unpack_bin(z, kk, log2M, tw);
-                    X.x *= sc;
-                    X.y *= sc;
-                    P[kk] = cmul(P[kk], X);
-                }
-                E += e;
-            } else {
-                Cplx<T>* S = spec + N.spec_off + (int64_t)r * N.spec_per_rep + Tk.soff + o * K;
-                for (int kk = threadIdx.x; kk < K; kk += blockDim.x) {
-                    Cplx<T> X = m == 1 ? z[0] : unpack_bin(z, kk, log2M, tw);
-                    X.x *= sc;
-                    X.y *= sc;
-                    S[kk] = X;
-                }
-                if (threadIdx.x == 0) sexp[N.exp_off + (int64_t)r * N.exp_per_rep + Tk.eoff + o] = e;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int k_cur = 0;
+    int64_t o_cur = 0;
+    while (k_cur < N.p) {
+        // ---- the next group of up to gmax sketches (same walk in every thread)
+        int G = 0;
+        while (G < gmax && k_cur < N.p) {
+            const M1Tensor& Tk = tens[N.t0 + k_cur];
+            const int64_t nsk = Tk.soff < 0 ? 1 : Tk.O;
+            if (threadIdx.x == 0) {
+                s_k[G] = k_cur;
+                s_o[G] = o_cur;
+                s_x[G] = Tk.xoff + o_cur * m;
+                s_so[G] = Tk.soff < 0 ? -1 : Tk.soff + o_cur * K;
+                s_eo[G] = Tk.soff < 0 ? -1 : Tk.eoff + o_cur;
+                s_max[G] = 0;
             }
-            __syncthreads();
+            ++G;
+            if (++o_cur >= nsk) {
+                o_cur = 0;
+                ++k_cur;
+            }
         }
+        __syncthreads();
+        // ---- load as packed complex z[n] = x[2n] + i x[2n+1] (z[0] = x[0] when m = 1)
+        for (int idx = threadIdx.x; idx < G * M; idx += blockDim.x) {
+            const int g = idx >> log2M, n = idx & (M - 1);
+            const T* x = xr + s_x[g];
+            z[idx] = m == 1 ? Cplx<T>{x[0], T(0)} : Cplx<T>{x[2 * n], x[2 * n + 1]};
+        }
+        __syncthreads();
+        if (m > 1) block_fft_dif(z, G, log2M, tw);
+        // ---- per-sketch magnitude for the power-of-two scaling
+        for (int g = 0; g < G; ++g) {
+            T mx = T(0);
+            for (int kk = threadIdx.x; kk < K; kk += blockDim.x) {
+                Cplx<T> X = m == 1 ? z[g * M] : unpack_bin(z + g * M, kk, log2M, tw);
+                mx = fmax(mx, fmax(fabs(X.x), fabs(X.y)));
+            }
+#pragma unroll
+            for (int sft = 16; sft > 0; sft >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, sft));
+            if (lane == 0 && mx > T(0)) atomicMax(&s_max[g], (unsigned long long)__double_as_longlong((double)mx));
+        }
+        __syncthreads();
+        if (threadIdx.x < G) {
+            int e = 0;
+            const double mx = __longlong_as_double((long long)s_max[threadIdx.x]);
+            if (mx > 0.0) frexp(mx, &e);
+            s_e[threadIdx.x] = e;  // 2^-e F x has entries below 1 in magnitude
+        }
+        __syncthreads();
+        // ---- fold into P (tensors without open legs) or keep the open spectra
+        for (int kk = threadIdx.x; kk < K; kk += blockDim.x) {
+            Cplx<T> pk = P[kk];
+            for (int g = 0; g < G; ++g) {
+                Cplx<T> X = m == 1 ? z[g * M] : unpack_bin(z + g * M, kk, log2M, tw);
+                const T sc = (T)ldexp(1.0, -s_e[g]);
+                X.x *= sc;
+                X.y *= sc;
+                if (s_so[g] < 0)
+                    pk = cmul(pk, X);
+                else
+                    spec[N.spec_off + (int64_t)r * N.spec_per_rep + s_so[g] + kk] = X;
+            }
+            P[kk] = pk;
+        }
+        for (int g = 0; g < G; ++g) {
+            if (s_so[g] < 0)
+                E += s_e[g];
+            else if (threadIdx.x == 0)
+                sexp[N.exp_off + (int64_t)r * N.exp_per_rep + s_eo[g]] = s_e[g];
+        }
+        __syncthreads();
     }
     // y_r(o) = (1/m) sum_j prod_k (F x_k[o_k])(j); the full spectrum is Hermitian,
     // so sum_j = P[0] + P[M] + 2 Re sum_{0<k<M} P[k] (m >= 2).
@@ -231,19 +271,17 @@ __global__ void __launch_bounds__(256) m1_spectrum_kernel(const M1Tensor* __rest
             acc += wgt * (double)P[k].x;
         }
 #pragma unroll
-        for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int sft = 16; sft > 0; sft >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sft);
         if (lane == 0) dred[warp] = acc;
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += dred[q];
+            for (int q = 0; q < nw; ++q) t += dred[q];
             yr[0] = ldexp(t, E) / (double)m;
         }
         return;
     }
     // open outputs: one warp per output entry
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const Cplx<T>* Sb = spec + N.spec_off + (int64_t)r * N.spec_per_rep;
     const int* Eb = sexp + N.exp_off + (int64_t)r * N.exp_per_rep;
     for (int64_t o = warp; o < O; o += nw) {
@@ -252,32 +290,32 @@ __global__ void __launch_bounds__(256) m1_spectrum_kernel(const M1Tensor* __rest
             const OpenMode om = opens[N.open0 + j];
             int64_t digit = (o / om.ostride) % om.dim;
 #pragma unroll
-            for (int s = 0; s < TNSK_MAX_OPEN_TENSORS; ++s)
-                if (s == om.slot) oo[s] += digit * om.tstride;
+            for (int sl = 0; sl < TNSK_MAX_OPEN_TENSORS; ++sl)
+                if (sl == om.slot) oo[sl] += digit * om.tstride;
         }
         const Cplx<T>* sp[TNSK_MAX_OPEN_TENSORS];
         int Eo = E;
 #pragma unroll
-        for (int s = 0; s < TNSK_MAX_OPEN_TENSORS; ++s) {
-            if (s < N.n_ot) {
-                const M1Tensor& Tt = tens[N.ot[s]];
-                sp[s] = Sb + Tt.soff + oo[s] * K;
-                Eo += Eb[Tt.eoff + oo[s]];
+        for (int sl = 0; sl < TNSK_MAX_OPEN_TENSORS; ++sl) {
+            if (sl < N.n_ot) {
+                const M1Tensor& Tt = tens[N.ot[sl]];
+                sp[sl] = Sb + Tt.soff + oo[sl] * K;
+                Eo += Eb[Tt.eoff + oo[sl]];
             } else {
-                sp[s] = nullptr;
+                sp[sl] = nullptr;
             }
         }
         double acc = 0;
         for (int k = lane; k < K; k += 32) {
             Cplx<T> v = P[k];
 #pragma unroll
-            for (int s = 0; s < TNSK_MAX_OPEN_TENSORS; ++s)
-                if (s < N.n_ot) v = cmul(v, sp[s][k]);
+            for (int sl = 0; sl < TNSK_MAX_OPEN_TENSORS; ++sl)
+                if (sl < N.n_ot) v = cmul(v, sp[sl][k]);
             double wgt = (m == 1 || k == 0 || k == M) ? 1.0 : 2.0;
             acc += wgt * (double)v.x;
         }
 #pragma unroll
-        for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+        for (int sft = 16; sft > 0; sft >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sft);
         if (lane == 0) yr[o] = ldexp(acc, Eo) / (double)m;
     }
 }
@@ -312,28 +350,31 @@ __global__ void combine_kernel(const CombineItem* __restrict__ items, int n_item
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <typename AccT>
-cudaError_t launch_m1_scatter_t(const M1Tensor* d_tens, const M1Net* d_nets, const M1Work* d_work, int n_work,
-                                const uint32_t* d_tabs, AccT* d_xs, size_t smem, bool idx32, cudaStream_t s) {
-    if (n_work <= 0) return cudaSuccess;
-    if (idx32) {
-        auto k = m1_scatter_kernel<AccT, uint32_t>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<n_work, 256, smem, s>>>(d_tens, d_nets, d_work, d_tabs, d_xs);
-    } else {
-        auto k = m1_scatter_kernel<AccT, uint64_t>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<n_work, 256, smem, s>>>(d_tens, d_nets, d_work, d_tabs, d_xs);
-    }
+template <typename AccT, int MAXD>
+cudaError_t launch_scatter_d(const M1Tensor* d_tens, const M1Net* d_nets, const M1Work* d_work, int n_work,
+                             const uint32_t* d_tabs, AccT* d_xs, size_t smem, cudaStream_t s) {
+    auto k = m1_scatter_kernel<AccT, MAXD>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<n_work, 256, smem, s>>>(d_tens, d_nets, d_work, d_tabs, d_xs);
     return cudaGetLastError();
 }
 
+template <typename AccT>
+cudaError_t launch_m1_scatter_t(const M1Tensor* d_tens, const M1Net* d_nets, const M1Work* d_work, int n_work,
+                                const uint32_t* d_tabs, AccT* d_xs, size_t smem, int max_order, cudaStream_t s) {
+    if (n_work <= 0) return cudaSuccess;
+    if (max_order <= 2) return launch_scatter_d<AccT, 2>(d_tens, d_nets, d_work, n_work, d_tabs, d_xs, smem, s);
+    if (max_order <= 4) return launch_scatter_d<AccT, 4>(d_tens, d_nets, d_work, n_work, d_tabs, d_xs, smem, s);
+    if (max_order <= 6) return launch_scatter_d<AccT, 6>(d_tens, d_nets, d_work, n_work, d_tabs, d_xs, smem, s);
+    return launch_scatter_d<AccT, TNSK_MAX_ORDER>(d_tens, d_nets, d_work, n_work, d_tabs, d_xs, smem, s);
+}
+
 cudaError_t launch_m1_scatter(const M1Tensor* d_tens, const M1Net* d_nets, const M1Work* d_work, int n_work,
-                              const uint32_t* d_tabs, void* d_xs, bool fp64, size_t smem, bool idx32,
+                              const uint32_t* d_tabs, void* d_xs, bool fp64, size_t smem, int max_order,
                               cudaStream_t s) {
     if (fp64)
-        return launch_m1_scatter_t<double>(d_tens, d_nets, d_work, n_work, d_tabs, (double*)d_xs, smem, idx32, s);
-    return launch_m1_scatter_t<float>(d_tens, d_nets, d_work, n_work, d_tabs, (float*)d_xs, smem, idx32, s);
+        return launch_m1_scatter_t<double>(d_tens, d_nets, d_work, n_work, d_tabs, (double*)d_xs, smem, max_order, s);
+    return launch_m1_scatter_t<float>(d_tens, d_nets, d_work, n_work, d_tabs, (float*)d_xs, smem, max_order, s);
 }
 
 cudaError_t launch_m1_spectrum(const M1Tensor* d_tens, const M1Net* d_nets, const OpenMode* d_opens,
@@ -342,18 +383,20 @@ cudaError_t launch_m1_spectrum(const M1Tensor* d_tens, const M1Net* d_nets, cons
                                cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
     const int M = max_log2m > 0 ? 1 << (max_log2m - 1) : 1;
+    // sketches per FFT pass: up to 32 KiB of them, at most 8 (occupancy over batching)
+    const size_t csz = fp64 ? sizeof(Cplx<double>) : sizeof(Cplx<float>);
+    int gmax = (int)std::max<size_t>(1, std::min<size_t>(8, (32 * 1024) / (M * csz)));
+    size_t smem = ((size_t)gmax * M + M + 1 + M) * csz;
     if (fp64) {
-        size_t smem = (size_t)(2 * M + 1) * sizeof(Cplx<double>);
         auto k = m1_spectrum_kernel<double>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<n_items, 256, smem, s>>>(d_tens, d_nets, d_opens, d_items, (const double*)d_xs,
-                                     (const Cplx<double>* const*)d_tws, (Cplx<double>*)d_spec, d_sexp, d_yrep);
+                                     (const Cplx<double>* const*)d_tws, (Cplx<double>*)d_spec, d_sexp, d_yrep, gmax);
     } else {
-        size_t smem = (size_t)(2 * M + 1) * sizeof(Cplx<float>);
         auto k = m1_spectrum_kernel<float>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<n_items, 256, smem, s>>>(d_tens, d_nets, d_opens, d_items, (const float*)d_xs,
-                                     (const Cplx<float>* const*)d_tws, (Cplx<float>*)d_spec, d_sexp, d_yrep);
+                                     (const Cplx<float>* const*)d_tws, (Cplx<float>*)d_spec, d_sexp, d_yrep, gmax);
     }
     return cudaGetLastError();
 }

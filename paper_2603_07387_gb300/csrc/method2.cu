@@ -19,14 +19,15 @@
 
 namespace tnsk {
 
-// Sign and row of the recursive sketch R_k for one column (Alg. 4). `slot[j]`
-// holds the packed base word of slot j (child count sketch C_{k,l} at the
-// child-mode index, or the padding slot's word at index 0); levels l = qt..2
-// combine pairs by TensorSketchHash (Alg. 3) with T_{l,j}.
-__device__ __forceinline__ void rsh_reduce(uint32_t (&b)[TNSK_MAX_SLOTS], uint32_t& neg, int qt,
+// Sign and row of the recursive sketch R_k for one column (Alg. 4). b[j] holds
+// the bin of slot j (child count sketch C_{k,l} at the child-mode index, or the
+// padding slot's word at index 0); levels l = qt..2 combine pairs by
+// TensorSketchHash (Alg. 3) with T_{l,j}. QTMAX bounds qt at compile time.
+template <int QTMAX>
+__device__ __forceinline__ void rsh_reduce(uint32_t (&b)[QTMAX], uint32_t& neg, int qt,
                                            const uint32_t* __restrict__ ttab, int64_t m, uint32_t mask) {
 #pragma unroll
-    for (int lv = TNSK_MAX_SLOTS; lv >= 2; lv >>= 1) {
+    for (int lv = QTMAX; lv >= 2; lv >>= 1) {
         if (lv <= qt) {
             const int64_t before = qt - lv;  // pairs stored before level lv
 #pragma unroll
@@ -54,10 +55,11 @@ __global__ void __launch_bounds__(256) m2_leaf_kernel(const M2Node* __restrict__
     const M2Net& N = nets[nd.net];
     const int R = N.R;
     const uint32_t mask = (uint32_t)(N.m - 1);
-    const int64_t cnt = (it.end - it.begin) * R;
-    for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
-        const int64_t i = it.begin + q / R;
-        const int r = (int)(q % R);
+    const uint32_t cnt = (uint32_t)((it.end - it.begin) * R);  // <= 2048 * 65536
+    for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const uint32_t qi = q / (uint32_t)R;
+        const int64_t i = it.begin + qi;
+        const int r = (int)(q - qi * (uint32_t)R);
         const T v = load_as<T>(nd.data, nd.dtype, i);
         const uint32_t w = tabs[N.tab_off + (int64_t)r * N.Lrep + nd.ptab + i];
         atomicAdd(&ws[nd.x_off + (int64_t)r * N.m + (w & mask)], (w & TNSK_SIGN_BIT) ? -v : v);
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(256) m2_compose_kernel(const M2Node* __restric
 // ---------------------------------------------------------------------------
 // a7: V = sigma_r(col) r_k[r][b_r(col)], and the batched sketched matvec
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, typename IdxT, int QTMAX, int MAXD>
 __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict__ nodes,
                                                         const M2Net* __restrict__ nets,
                                                         const M2Item* __restrict__ items,
@@ -177,45 +179,72 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
     const int64_t m = N.m;
     const uint32_t mask = (uint32_t)(m - 1);
     const int order = nd.order, pmode = nd.pmode, c = nd.c, qt = nd.qt;
-    const int64_t cnt = (it.end - it.begin) * R;
-    for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
-        const int64_t col = it.begin + q / R;
-        const int r = (int)(q % R);
-        const uint32_t* tabr = tabs + N.tab_off + (int64_t)r * N.Lrep;
-        uint32_t b[TNSK_MAX_SLOTS];
-        uint32_t neg = 0;
-        int64_t rem = col;
+    // block-uniform per-mode data: dim and child-table offset of each mode
+    IdxT dim[MAXD];
+    int64_t ctab[MAXD];
 #pragma unroll
-        for (int d = TNSK_MAX_ORDER - 1; d >= 0; --d) {
+    for (int d = 0; d < MAXD; ++d) {
+        const bool child = d < order && d != pmode;
+        dim[d] = child ? (IdxT)nd.dims[d] : (IdxT)1;
+        const int slot = (pmode >= 0 && d > pmode) ? d - 1 : d;
+        ctab[d] = child ? nd.ctab[slot < TNSK_MAX_ORDER ? slot : 0] : 0;
+    }
+    const uint32_t len = (uint32_t)(it.end - it.begin);  // <= 128
+    const uint32_t cnt = len * (uint32_t)R;
+    for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const int r = (int)(q / len);
+        const int64_t col = it.begin + (q - (uint32_t)r * len);
+        const uint32_t* tabr = tabs + N.tab_off + (int64_t)r * N.Lrep;
+        uint32_t b[QTMAX];
+        uint32_t neg = 0;
+        IdxT rem = (IdxT)col;
+        // children are the non-parent modes in mode order: slot = d, or d - 1 after the parent
+#pragma unroll
+        for (int d = MAXD - 1; d >= 0; --d) {
             if (d < order && d != pmode) {
-                const int64_t n = nd.dims[d];
-                const int64_t qd = rem / n;
-                const int64_t i = rem - qd * n;
+                const IdxT qd = rem / dim[d];
+                const IdxT i = rem - qd * dim[d];
                 rem = qd;
-                // children are the non-parent modes in mode order
-                if (pmode >= 0 && d > pmode) {  // then d >= 1: slot d - 1
-                    const int dd = d > 0 ? d - 1 : 0;
-                    uint32_t w = tabr[nd.ctab[dd] + i];
-                    neg ^= w;
-                    b[dd] = w & mask;
+                const uint32_t w = tabr[ctab[d] + (int64_t)i];
+                neg ^= w;
+                if (pmode >= 0 && d > pmode) {
+                    if (d - 1 < QTMAX) b[d > 0 ? d - 1 : 0] = w & mask;
                 } else {
-                    uint32_t w = tabr[nd.ctab[d] + i];
-                    neg ^= w;
-                    b[d] = w & mask;
+                    if (d < QTMAX) b[d] = w & mask;
                 }
             }
         }
 #pragma unroll
-        for (int j = 0; j < TNSK_MAX_SLOTS; ++j)
+        for (int j = 0; j < QTMAX; ++j)
             if (j >= c && j < qt) {
                 uint32_t w = tabr[nd.pad_tab + j];
                 neg ^= w;
                 b[j] = w & mask;
             }
-        rsh_reduce(b, neg, qt, tabr + nd.t_tab, m, mask);
+        rsh_reduce<QTMAX>(b, neg, qt, tabr + nd.t_tab, m, mask);
         const T z = ws[nd.src_off + (int64_t)r * nd.src_stride + b[0]];
-        ws[nd.v_off + col * R + r] = (neg & TNSK_SIGN_BIT) ? -z : z;
+        ws[nd.v_off + (int64_t)r * nd.cols + col] = (neg & TNSK_SIGN_BIT) ? -z : z;
     }
+}
+
+template <typename T, typename IdxT, int QTMAX>
+static void launch_vbuild_q(int n, const M2Node* nodes, const M2Net* nets, const M2Item* its, const uint32_t* tabs,
+                            T* ws, int max_order, cudaStream_t s) {
+    if (max_order <= 4)
+        m2_vbuild_kernel<T, IdxT, QTMAX, 4><<<n, 256, 0, s>>>(nodes, nets, its, tabs, ws);
+    else
+        m2_vbuild_kernel<T, IdxT, QTMAX, TNSK_MAX_ORDER><<<n, 256, 0, s>>>(nodes, nets, its, tabs, ws);
+}
+
+template <typename T, typename IdxT>
+static void launch_vbuild(int n, const M2Node* nodes, const M2Net* nets, const M2Item* its, const uint32_t* tabs,
+                          T* ws, int max_qt, int max_order, cudaStream_t s) {
+    if (max_qt <= 1)
+        launch_vbuild_q<T, IdxT, 1>(n, nodes, nets, its, tabs, ws, max_order, s);
+    else if (max_qt <= 4)
+        launch_vbuild_q<T, IdxT, 4>(n, nodes, nets, its, tabs, ws, max_order, s);
+    else
+        launch_vbuild_q<T, IdxT, TNSK_MAX_SLOTS>(n, nodes, nets, its, tabs, ws, max_order, s);
 }
 
 // W = mat(X_k)[rows, :] V[:, reps] for a 64 x 64 tile, then x_k[r][h(i)] += s(i) W[i][r]
@@ -225,7 +254,7 @@ __global__ void __launch_bounds__(256) m2_gemm_kernel(const M2Node* __restrict__
                                                       const M2Item* __restrict__ items,
                                                       const uint32_t* __restrict__ tabs, T* __restrict__ ws) {
     __shared__ __align__(16) T Xs[32][64 + 4];
-    __shared__ __align__(16) T Vs[32][64 + 4];
+    __shared__ __align__(16) T Vs[32][64 + 1];
     const M2Item it = items[blockIdx.x];
     const M2Node& nd = nodes[it.node];
     const M2Net& N = nets[nd.net];
@@ -251,11 +280,11 @@ __global__ void __launch_bounds__(256) m2_gemm_kernel(const M2Node* __restrict__
             T v = T(0);
             if (gr < npar && gc < cols) {
                 int64_t flat;
-                if (nd.A == 1)
+                if (nd.A == 1) {
                     flat = gr * Bc + gc;
-                else {
-                    const int64_t a = gc / Bc;
-                    flat = (a * npar + gr) * Bc + (gc - a * Bc);
+                } else {
+                    const uint32_t a = (uint32_t)gc / (uint32_t)Bc;  // cols < 2^32 (checked by the planner)
+                    flat = ((int64_t)a * npar + gr) * Bc + (gc - (int64_t)a * Bc);
                 }
                 v = load_as<T>(nd.data, nd.dtype, flat);
             }
@@ -264,9 +293,9 @@ __global__ void __launch_bounds__(256) m2_gemm_kernel(const M2Node* __restrict__
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int e = threadIdx.x + 256 * q;
-            const int kk = e >> 6, rr = e & 63;
+            const int kk = e & 31, rr = e >> 5;
             const int64_t gc = k0 + kk;
-            Vs[kk][rr] = (gc < cols && rep0 + rr < R) ? V[gc * R + rep0 + rr] : T(0);
+            Vs[kk][rr] = (gc < cols && rep0 + rr < R) ? V[(int64_t)(rep0 + rr) * cols + gc] : T(0);
         }
         __syncthreads();
 #pragma unroll 8
@@ -299,32 +328,28 @@ __global__ void __launch_bounds__(256) m2_gemm_kernel(const M2Node* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// a8: root, y_r = sum_col X_o[col] V[col][r]
+// a8: root, y_r = sum_col X_o[col] V[r][col]
 // ---------------------------------------------------------------------------
+// One warp per rep at a time, lanes over the chunk's columns (coalesced X and V).
 template <typename T>
 __global__ void __launch_bounds__(256) m2_root_kernel(const M2Node* __restrict__ nodes, const M2Net* __restrict__ nets,
                                                       const M2Item* __restrict__ items, const T* __restrict__ ws,
                                                       double* __restrict__ yrep) {
-    __shared__ double part[4][64];
     const M2Item it = items[blockIdx.x];
     const M2Node& nd = nodes[it.node];
     const M2Net& N = nets[nd.net];
     const int R = N.R;
-    const int lane = threadIdx.x & 63, slice = threadIdx.x >> 6;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const T* V = nd.v_off >= 0 ? ws + nd.v_off : nullptr;
-    for (int r0 = 0; r0 < R; r0 += 64) {
-        const int r = r0 + lane;
+    for (int r = warp; r < R; r += nw) {
         double acc = 0;
-        if (r < R)
-            for (int64_t col = it.begin + slice; col < it.end; col += 4) {
-                const T x = load_as<T>(nd.data, nd.dtype, col);
-                acc += (double)(V ? x * V[col * R + r] : x);
-            }
-        part[slice][lane] = acc;
-        __syncthreads();
-        if (slice == 0 && r < R)
-            atomicAdd(&yrep[N.y_off + r], part[0][lane] + part[1][lane] + part[2][lane] + part[3][lane]);
-        __syncthreads();
+        for (int64_t col = it.begin + lane; col < it.end; col += 32) {
+            const T x = load_as<T>(nd.data, nd.dtype, col);
+            acc += (double)(V ? x * V[(int64_t)r * nd.cols + col] : x);
+        }
+#pragma unroll
+        for (int sft = 16; sft > 0; sft >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sft);
+        if (lane == 0) atomicAdd(&yrep[N.y_off + r], acc);
     }
 }
 
@@ -357,7 +382,12 @@ static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void*
                     m2_compose_kernel<T><<<n, 256, csmem, s>>>(nodes, nets, its, tabs, ws,
                                                                 (const Cplx<T>* const*)d_tws);
                     break;
-                case M2_VBUILD: m2_vbuild_kernel<T><<<n, 256, 0, s>>>(nodes, nets, its, tabs, ws); break;
+                case M2_VBUILD:
+                    if (P.m2.idx32)
+                        launch_vbuild<T, uint32_t>(n, nodes, nets, its, tabs, ws, P.m2.max_qt, P.m2.max_order, s);
+                    else
+                        launch_vbuild<T, uint64_t>(n, nodes, nets, its, tabs, ws, P.m2.max_qt, P.m2.max_order, s);
+                    break;
                 case M2_GEMM: m2_gemm_kernel<T><<<n, 256, 0, s>>>(nodes, nets, its, tabs, ws); break;
                 case M2_ROOT: m2_root_kernel<T><<<n, 256, 0, s>>>(nodes, nets, its, ws, yrep); break;
             }

@@ -12,7 +12,7 @@
 //   x        per non-root node: [R][m] accumulators (zeroed per call)
 //   r        per node with >= 2 children: [R][(qt-1) m] level outputs; the last
 //            m-vector of each rep is r_k
-//   V        per node with children: [cols][R]: V(col, r) = sigma_r(col) r_k[r][b_r(col)],
+//   V        per node with children: [R][cols]: V(col, r) = sigma_r(col) r_k[r][b_r(col)],
 //            so that x_k = scatter_C( mat(X_k) V ) is a matrix product batched over reps
 //   y        per root: [R] FP64 accumulators
 #pragma once
@@ -41,7 +41,7 @@ struct M2Node {
     int64_t r_off;    // [R][(qt-1) m] composition outputs (qt >= 2), else -1
     int64_t src_off;  // r_k used by V: r_off + (qt-2) m for qt >= 2, the child's x_off for qt = 1
     int64_t src_stride;  // distance between reps in the r_k source
-    int64_t v_off;    // [cols][R] V matrix (nodes with children)
+    int64_t v_off;    // [R][cols] V matrix (nodes with children)
     int64_t child_x[TNSK_MAX_SLOTS];  // slot j < c: the child's x_off
     int32_t dims[TNSK_MAX_ORDER];
     int32_t cmode[TNSK_MAX_ORDER];    // slot j < c: this node's mode toward child j
@@ -80,6 +80,9 @@ struct M2Plan {
     size_t nodes_off = 0, nets_off = 0, items_off = 0;
     size_t ws_off = 0;  // x / r / V / y workspace base (all offsets above are relative to it)
     int max_height = -1;
+    bool idx32 = true;  // every node has fewer than 2^32 columns
+    int max_qt = 0;     // largest slot count
+    int max_order = 0;  // largest tensor order
     int max_log2m = 0;
     // per height, per kind: [first, count) into the item array
     std::vector<int> first, count;  // size (max_height+1) * M2_NKINDS

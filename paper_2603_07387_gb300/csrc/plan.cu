@@ -291,8 +291,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     int64_t tab_words = 0, yrep_n = 0, xs_n = 0, spec_n = 0, sexp_n = 0;
     int64_t ws_x = 0, ws_r = 0, ws_v = 0;  // method-2 workspace parts (elements)
     size_t scatter_smem = 16;
-    int max_log2m1 = 0, max_log2m2 = 0;
-    bool idx32 = true;
+    int max_log2m1 = 0, max_log2m2 = 0, m1_max_order = 0;
     struct PendingItem {
         int h, kind;
         M2Item it;
@@ -314,7 +313,6 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
         const int64_t m = pr.m;
         const uint32_t mask = (uint32_t)(m - 1);
         const int R = pr.reps;
-        idx32 = idx32 && I.idx32;
         if (pr.method == TNSK_GENERAL) {
             M1Net nb{};
             nb.m = m;
@@ -355,6 +353,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 }
                 T.dtype = N.X[k].dtype;
                 T.order = N.X[k].order;
+                m1_max_order = std::max(m1_max_order, T.order);
                 T.net = (int)m1n.size();
                 int64_t ost = 1;
                 for (int d = T.order - 1; d >= 0; --d) {
@@ -440,7 +439,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                         w.tensor = nb.t0 + k;
                         w.rep0 = r0;
                         w.nrep = std::min(nrep, R - r0);
-                        w.priv = priv ? 1 : 0;
+                        w.priv = priv ? ((w.begin == 0 && w.end == T.numel) ? 2 : 1) : 0;
                         m1w.push_back(w);
                     }
             }
@@ -559,9 +558,18 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 nd.npar = nd.dims[nd.pmode];
             }
             nd.cols = nd.A * nd.Bc;
+            if (nd.cols >= ((int64_t)1 << 32)) {
+                if (nd.A > 1) {
+                    err = "tensor " + std::to_string(k) + ": 2^32 or more columns with the parent mode not first";
+                    return TNSK_ERR_UNSUPPORTED;
+                }
+                P.m2.idx32 = false;
+            }
             nd.ptab = nd.is_root ? -1 : I.eoff[I.parent_edge[k]];
             nd.c = (int)I.child[k].size();
             nd.qt = qt[k];
+            P.m2.max_qt = std::max(P.m2.max_qt, nd.qt);
+            P.m2.max_order = std::max(P.m2.max_order, nd.order);
             for (int j = 0; j < nd.c; ++j) {
                 nd.cmode[j] = I.child_mode[k][j];
                 nd.ctab[j] = I.eoff[I.child_edge[k][j]];
@@ -661,13 +669,16 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     P.m2.max_log2m = max_log2m2;
 
     // ---- table request prefix offsets
-    int64_t first = 0;
+    int64_t first = 0, crow = 0;
     for (TabReq& q : reqs) {
         q.first = first;
+        q.crow = crow;
         first += q.n * q.R;
+        crow += q.R;
     }
     P.n_reqs = (int)reqs.size();
     P.n_table_words = first;
+    P.n_coef_rows = crow;
 
     // ---- stage descriptors
     std::vector<unsigned char>& H = P.host_desc;
@@ -693,13 +704,14 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     P.zero_bytes = P.m2.ws_off + (size_t)ws_x * acc - P.zero_off;
     // ---- the rest
     P.tabs_off = P.arena.take((size_t)tab_words * sizeof(uint32_t));
+    P.coef_off = P.arena.take((size_t)P.n_coef_rows * sizeof(HashCoef));
     P.m1.spec_off = P.arena.take((size_t)spec_n * 2 * acc);
     P.m1.sexp_off = P.arena.take((size_t)sexp_n * sizeof(int));
     P.m1.n_nets = (int)m1n.size();
     P.m1.n_work = (int)m1w.size();
     P.m1.n_items = (int)m1items.size();
     P.m1.scatter_smem = scatter_smem;
-    P.m1.idx32 = idx32;
+    P.m1.max_order = m1_max_order;
     P.m1.max_log2m = max_log2m1;
     P.n_comb = (int)comb.size();
     return TNSK_OK;

@@ -43,7 +43,7 @@ struct M1Plan {
     size_t xs_off = 0, spec_off = 0, sexp_off = 0;
     int n_work = 0, n_items = 0;
     size_t scatter_smem = 0;
-    bool idx32 = true;
+    int max_order = 0;  // largest tensor order among method-1 tensors
     int max_log2m = 0;
 };
 
@@ -56,7 +56,9 @@ struct BatchPlan {
     size_t reqs_off = 0;
     int n_reqs = 0;
     int64_t n_table_words = 0;
+    int64_t n_coef_rows = 0;
     size_t tabs_off = 0;
+    size_t coef_off = 0;
     size_t yrep_off = 0;
     size_t comb_off = 0;
     int n_comb = 0;

@@ -42,6 +42,9 @@ SYMBOLS = (
     "tnsk_estimate",
     "tnsk_estimate_batch",
     "tnsk_estimate_static",
+    "tnsk_plan_create",
+    "tnsk_plan_run",
+    "tnsk_plan_destroy",
     "tnsk_profile",
     "tnsk_profile_read",
     "tnsk_sync",
@@ -117,6 +120,13 @@ def load_library(path: str = LIB_PATH):
                                       ctypes.POINTER(vp), ctypes.POINTER(vp)]
     L.tnsk_estimate_static.restype = i32
     L.tnsk_estimate_static.argtypes = [ctypes.POINTER(_Network), ctypes.POINTER(_Params), vp, vp, vp]
+    L.tnsk_plan_create.restype = i32
+    L.tnsk_plan_create.argtypes = [vp, i32, ctypes.POINTER(_Network), ctypes.POINTER(_Params), ctypes.POINTER(vp),
+                                   ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.tnsk_plan_run.restype = i32
+    L.tnsk_plan_run.argtypes = [vp, vp]
+    L.tnsk_plan_destroy.restype = i32
+    L.tnsk_plan_destroy.argtypes = [vp]
     L.tnsk_profile.restype = i32
     L.tnsk_profile.argtypes = [vp, i32]
     L.tnsk_profile_read.restype = i32
@@ -212,6 +222,29 @@ def estimate_static(net: Network, params: Params, out, per_rep=None, stream=None
         raise TnskError(st, "tnsk_estimate_static")
 
 
+class Plan:
+    """A planned batch (tnsk_plan): run() enqueues the whole batch on the ctx stream.
+    Keeps references to the tensors and outputs whose addresses it holds."""
+
+    def __init__(self, ctx, handle, tensors, outs, per_reps):
+        self.ctx, self.h = ctx, handle
+        self._keep = (tensors, outs, per_reps)
+
+    def run(self):
+        self.ctx._check(self.ctx.lib.tnsk_plan_run(self.ctx.h, self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.tnsk_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Context:
     """A libtnsk context bound to one device and one CUDA stream."""
 
@@ -268,6 +301,20 @@ class Context:
             rarr = (ctypes.c_void_p * max(1, B))(*[(r.data_ptr() if r is not None else None) for r in per_reps])
         self._check(self.lib.tnsk_estimate_batch(self.h, B, carr, parr, oarr, rarr))
         return holders  # callers may keep them alive until the stream completes
+
+    def plan(self, nets: Sequence[Network], params: Sequence[Params], outs, per_reps=None) -> "Plan":
+        """tnsk_plan_create: plan a batch once; run it with Plan.run()."""
+        B = len(nets)
+        holders = [_NetHolder(n) for n in nets]
+        carr = (_Network * max(1, B))(*[h.c for h in holders])
+        parr = (_Params * max(1, B))(*[_params(p) for p in params])
+        oarr = (ctypes.c_void_p * max(1, B))(*[o.data_ptr() for o in outs])
+        rarr = None
+        if per_reps is not None:
+            rarr = (ctypes.c_void_p * max(1, B))(*[(r.data_ptr() if r is not None else None) for r in per_reps])
+        h = ctypes.c_void_p()
+        self._check(self.lib.tnsk_plan_create(self.h, B, carr, parr, oarr, rarr, ctypes.byref(h)))
+        return Plan(self, h, [n.tensors for n in nets], list(outs), per_reps)
 
     def profile(self, enable: bool = True):
         self._check(self.lib.tnsk_profile(self.h, 1 if enable else 0))

@@ -178,6 +178,35 @@ def test_batch_matches_oracle_per_network(ctx):
                            rtol=1e-14, atol=0)
 
 
+def test_plan_runs_match_oracle_and_pick_up_new_data(ctx):
+    rng = np.random.default_rng(12)
+    specs = [W.random_network(rng, p_range=(4, 6), dim_range=(2, 5), open_dim_range=(2, 4)) for _ in range(3)]
+    specs += _trees()[3:5]
+    params = [tnsk.Params(m=128, reps=4, seed=50 + i,
+                          method=tnsk.ACYCLIC if s.name.startswith("tree") else tnsk.GENERAL)
+              for i, s in enumerate(specs)]
+    nets = [gpu_network(s, torch.float32) for s in specs]
+    Os = []
+    for s in specs:
+        dims = [d for x in s.tensors for d in np.shape(x)]
+        Os.append(int(np.prod([dims[g] for g in s.open])) if s.open else 1)
+    outs = [torch.zeros(max(O, 1), dtype=torch.float64, device="cuda") for O in Os]
+    pers = [torch.zeros((p.reps, max(O, 1)), dtype=torch.float64, device="cuda") for p, O in zip(params, Os)]
+    plan = ctx.plan(nets, params, outs, pers)
+    for run in range(2):
+        if run == 1:  # new values in the same buffers
+            for s, n in zip(specs, nets):
+                for k, t in enumerate(n.tensors):
+                    s.tensors[k] = 2.0 * s.tensors[k]
+                    t.copy_(torch.as_tensor(np.array(s.tensors[k], dtype=np.float64)).to(t.dtype))
+        plan.run()
+        ctx.sync()
+        for s, p, pr, O in zip(specs, params, pers, Os):
+            y, sc = oracle_estimate(s, p, torch.float32)
+            assert_parity(pr.cpu().numpy()[:, :O], y, sc, TOL[p.prec], f"plan run {run} {s.name}")
+    plan.close()
+
+
 def test_degenerate_inputs(ctx):
     # scalars, an empty contracted mode, an empty open mode, a single self-contraction
     cases = [
