@@ -147,7 +147,8 @@ typedef enum {
     TNSK_K_M2_GEMM = 6,     /* method 2 sketched matrix-vector products (a7) */
     TNSK_K_M2_ROOT = 7,     /* method 2 root inner products (a8) */
     TNSK_K_COMBINE = 8,     /* median of group means (a9) */
-    TNSK_KERNEL_KINDS = 9
+    TNSK_K_M2_SCATTER = 9,  /* method 2 count-sketch scatter of the product rows (a7) */
+    TNSK_KERNEL_KINDS = 10
 } tnsk_kernel_kind;
 tnsk_status tnsk_profile(tnsk_ctx* ctx, int32_t enable);
 tnsk_status tnsk_profile_read(tnsk_ctx* ctx, double* ms, int64_t* launches);

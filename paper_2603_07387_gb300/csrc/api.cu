@@ -297,7 +297,7 @@ static tnsk_status launch_plan(tnsk_ctx* ctx, const BatchPlan& plan, unsigned ch
     if (plan.m2.n_nets && !sketch_out) {
         tnsk_status st =
             run_method2(plan, base, fp64, fp64 ? (const void* const*)ctx->d_tw64 : (const void* const*)ctx->d_tw32,
-                        s, pf, ctx->last_error);
+                        s, pf, ctx->d_err, ctx->last_error);
         if (st != TNSK_OK) return st;
     }
     if (!sketch_out && plan.n_comb) {
@@ -320,6 +320,8 @@ static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets,
     st = build_plan(ctx, B, nets, params, outs, per_reps, sketch_out != nullptr, plan, fp64);
     if (st != TNSK_OK) return st;
     st = ensure_scratch(ctx, plan.arena.used);
+    if (st != TNSK_OK) return st;
+    st = finalize_plan(plan, ctx->scratch, ctx->last_error);
     if (st != TNSK_OK) return st;
     // descriptors (pageable host staging: the copy is complete on return)
     if (!plan.host_desc.empty())
@@ -381,6 +383,12 @@ tnsk_status tnsk_plan_create(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets,
         cudaGetLastError();
         delete p;
         return fail(ctx, TNSK_ERR_OOM, "plan scratch allocation failed");
+    }
+    st = finalize_plan(p->plan, p->dev, ctx->last_error);
+    if (st != TNSK_OK) {
+        cudaFree(p->dev);
+        delete p;
+        return st;
     }
     cudaError_t e = cudaSuccess;
     if (!p->plan.host_desc.empty())

@@ -1,0 +1,494 @@
+// m2_gemm_tc.cu -- row a7 of the hot path on the 5th-generation tensor cores.
+//
+// The sketched matrix-vector product of Alg. 5, for all repetitions at once,
+// is the dense product W = mat(X_k) V (V(col, r) = sigma_r(col) r_k[r][b_r(col)])
+// followed by the count-sketch scatter of W's rows into x_k. This kernel computes
+// a 128-row x 64-rep tile of W with tcgen05.mma (kind::tf32, FP32 accumulators in
+// tensor memory) and writes it as W^T (coalesced rows); m2_wscatter_kernel then
+// applies the count sketch of the parent edge with shared-memory bins.
+//
+// FP32 accuracy from TF32 tensor cores: every operand value v is split as
+// v = hi + lo with hi = tf32(v) (round to nearest) and lo = tf32(v - hi), and
+// W = Xhi Vhi + Xhi Vlo + Xlo Vhi (the dropped Xlo Vlo is below 2^-22 relative).
+//
+// General kernel (any dtype, any parent mode, any column count): per K-chunk of
+// 32 columns, X (128 x 32) and V^T (64 x 32) tiles are staged in shared memory
+// in the K-major, no-swizzle canonical layout: core matrices of 8 rows x 16
+// bytes; K-adjacent cores 128 B apart (leading byte offset), 8-row groups 1024 B
+// apart (stride byte offset). Two stages: threads load chunk c+1 into registers
+// while the tensor core works on chunk c; an mbarrier signalled by tcgen05.commit
+// frees a stage. The streaming kernel further below serves the common case.
+#include "common.cuh"
+#include "method2.cuh"
+
+namespace tnsk {
+namespace {
+
+constexpr int kTM = 128;  // rows of W per CTA (TMEM lanes)
+constexpr int kTN = 64;   // reps per CTA (TMEM columns)
+constexpr int kKC = 32;   // columns per chunk (4 MMAs of K = 8)
+constexpr int kStages = 2;
+constexpr int kABytes = kTM * kKC * 4;                   // 16 KiB
+constexpr int kBBytes = kTN * kKC * 4;                   // 8 KiB
+constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;   // hi + lo of both
+constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
+constexpr uint32_t kWaitLimit = 1u << 22;                // bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Byte offset of (row, k) in a K-major no-swizzle operand tile (k < 32).
+__device__ __forceinline__ int kmajor_offset(int row, int k) {
+    return (row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4;
+}
+
+// Shared-memory matrix descriptor: start, leading / stride byte offsets (>> 4),
+// descriptor version 1 at bit 46, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, N = 64, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTN >> 3) << 17) |
+                            ((uint32_t)(kTM >> 4) << 24);
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void store_split(unsigned char* hi, unsigned char* lo, int off, float4 v) {
+    uint32_t h0 = tf32_rna(v.x), h1 = tf32_rna(v.y), h2 = tf32_rna(v.z), h3 = tf32_rna(v.w);
+    uint32_t l0 = tf32_rna(v.x - __uint_as_float(h0)), l1 = tf32_rna(v.y - __uint_as_float(h1));
+    uint32_t l2 = tf32_rna(v.z - __uint_as_float(h2)), l3 = tf32_rna(v.w - __uint_as_float(h3));
+    *reinterpret_cast<uint4*>(hi + off) = make_uint4(h0, h1, h2, h3);
+    *reinterpret_cast<uint4*>(lo + off) = make_uint4(l0, l1, l2, l3);
+}
+
+}  // namespace
+
+// One CTA (128 threads) per item: (node, 128-row tile it.a, 64-rep tile it.b, K split
+// it.pad_ of it.begin).
+__global__ void __launch_bounds__(128, 2) m2_gemm_tc_kernel(const M2Node* __restrict__ nodes,
+                                                            const M2Net* __restrict__ nets,
+                                                            const M2Item* __restrict__ items,
+                                                            const uint32_t* __restrict__ tabs, float* __restrict__ ws,
+                                                            int* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t empty_bar[kStages];
+    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ uint32_t tmem_base;
+    unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const M2Item it = items[blockIdx.x];
+    const M2Node& nd = nodes[it.node];
+    const M2Net& N = nets[nd.net];
+    const int R = N.R;
+    const int64_t row0 = (int64_t)it.a * kTM;
+    const int rep0 = it.b * kTN;
+    const int64_t npar = nd.npar, cols = nd.cols, Bc = nd.Bc;
+    const float* V = ws + nd.v_off;
+    const bool fast_x = nd.dtype == TNSK_F32 && nd.A == 1 && (cols & 3) == 0 &&
+                        ((uintptr_t)nd.data & 15) == 0;
+    const bool fast_v = (cols & 3) == 0 && (((uintptr_t)V) & 15) == 0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(kTN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&empty_bar[s])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&done_bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    // thread -> 16-byte column group `sub` of rows rin + 8 (rhi + 2 j): the 8 threads of a
+    // quarter warp share a column group and cover the 8 rows of a core matrix, so
+    // their 16-byte stores land in 8 different bank groups
+    const int rin = tid & 7, sub = (tid >> 3) & 7, rhi = tid >> 6;
+    auto trow = [&](int j) { return rin + 8 * (rhi + 2 * j); };
+    float4 ra[8], rv[4];
+    auto load_chunk = [&](int64_t k0) {
+        const int64_t gc = k0 + sub * 4;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t gr = row0 + trow(j);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gr < npar) {
+                if (fast_x) {
+                    if (gc < cols) v = __ldg(reinterpret_cast<const float4*>((const float*)nd.data + gr * Bc + gc));
+                } else {
+                    float t[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int64_t cc = gc + q;
+                        t[q] = 0.f;
+                        if (cc < cols) {
+                            const int64_t a = cc / Bc;
+                            t[q] = load_as<float>(nd.data, nd.dtype, (a * npar + gr) * Bc + (cc - a * Bc));
+                        }
+                    }
+                    v = make_float4(t[0], t[1], t[2], t[3]);
+                }
+            }
+            ra[j] = v;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int rep = rep0 + trow(j);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rep < R) {
+                const float* src = V + (int64_t)rep * cols;
+                if (fast_v) {
+                    if (gc < cols) v = *reinterpret_cast<const float4*>(src + gc);
+                } else {
+                    v.x = gc + 0 < cols ? src[gc + 0] : 0.f;
+                    v.y = gc + 1 < cols ? src[gc + 1] : 0.f;
+                    v.z = gc + 2 < cols ? src[gc + 2] : 0.f;
+                    v.w = gc + 3 < cols ? src[gc + 3] : 0.f;
+                }
+            }
+            rv[j] = v;
+        }
+    };
+
+    // this item's share of the K chunks (split K: partial tiles meet in the atomic scatter)
+    const int total_chunks = (int)((cols + kKC - 1) / kKC);
+    const int cbeg = (int)(((int64_t)total_chunks * it.pad_) / it.begin);
+    const int cend = (int)(((int64_t)total_chunks * (it.pad_ + 1)) / it.begin);
+    const int nchunks = cend - cbeg;
+    bool ok = true;
+    if (nchunks > 0) load_chunk((int64_t)cbeg * kKC);
+    for (int c = 0; c < nchunks; ++c) {
+        const int s = c % kStages;
+        unsigned char* st = sm + s * kStageBytes;
+        unsigned char *a_hi = st, *a_lo = st + kABytes, *b_hi = st + 2 * kABytes, *b_lo = st + 2 * kABytes + kBBytes;
+        if (c >= kStages) ok = mbar_wait(smem_addr(&empty_bar[s]), (uint32_t)((c / kStages - 1) & 1)) && ok;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) store_split(a_hi, a_lo, kmajor_offset(trow(j), sub * 4), ra[j]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) store_split(b_hi, b_lo, kmajor_offset(trow(j), sub * 4), rv[j]);
+        if (c + 1 < nchunks) load_chunk((int64_t)(cbeg + c + 1) * kKC);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned char* aop[3] = {a_hi, a_hi, a_lo};
+            const unsigned char* bop[3] = {b_hi, b_lo, b_hi};
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int ks = 0; ks < kKC / 8; ++ks) {
+                    const uint64_t ad = smem_desc(smem_addr(aop[p]) + ks * 256, 128, 1024);
+                    const uint64_t bd = smem_desc(smem_addr(bop[p]) + ks * 256, 128, 1024);
+                    const uint32_t acc = (c > 0 || p > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_addr(&empty_bar[s])));
+            if (c == nchunks - 1)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_addr(&done_bar)));
+        }
+    }
+    if (nchunks > 0) ok = mbar_wait(smem_addr(&done_bar), 0u) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) {
+        if (lane == 0) atomicExch(err, DEVERR_TIMEOUT);
+    } else if (nchunks > 0) {
+        // epilogue: row = this thread's TMEM lane; x_k[r][h(row)] += s(row) W[row][r]
+        const int64_t row = row0 + warp * 32 + lane;
+#pragma unroll
+        for (int cc = 0; cc < kTN / 16; ++cc) {
+            uint32_t v[16];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 16);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < npar) {
+                // W^T[rep][row]: a warp writes 32 consecutive rows of one rep
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int rep = rep0 + cc * 16 + j;
+                    if (rep < R) {
+                        float* dst = &ws[nd.w_off + (int64_t)rep * npar + row];
+                        if (it.begin > 1)
+                            atomicAdd(dst, __uint_as_float(v[j]));  // K split: partial sums
+                        else
+                            *dst = __uint_as_float(v[j]);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTN));
+}
+
+// ---------------------------------------------------------------------------
+// Streaming variant for row-major FP32 tensors whose parent mode is the first
+// mode (mat(X_k) is the row-major matrix itself) and whose column count is a
+// multiple of 4. Warp-specialised; the tiles of X and V^T arrive by TMA (one
+// 2-D box per operand and chunk, described by tensor maps made at plan time) in
+// the 128-byte swizzled K-major layout, with zero fill outside the matrix.
+//   warp 0     producer: two cp.async.bulk.tensor loads per chunk into a
+//              5-deep ring (raw_full counts bytes)
+//   warps 1-4  converters: raw FP32 -> hi/lo TF32 at the same swizzled
+//              positions (row r's 16-byte chunk g sits at g ^ (r & 7)), then
+//              the epilogue
+//   warp 5     tensor memory allocation and MMA issue
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kRawStages = 5;
+constexpr int kOpStages = 2;
+constexpr int kRawA = kTM * 128;  // one chunk of X rows: 128 rows x 128 B
+constexpr int kRawB = kTN * 128;  // one chunk of V^T rows
+constexpr int kRawStage = kRawA + kRawB;
+constexpr int kStreamSmem = kRawStages * kRawStage + kOpStages * kStageBytes + 1024;
+
+__device__ __forceinline__ int sw128_offset(int row, int g) {
+    return (row >> 3) * 1024 + (row & 7) * 128 + ((g ^ (row & 7)) << 4);
+}
+
+// K-major, 128-byte swizzle: stride byte offset 1024 (8-row atoms), leading offset unused.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
+        "l"(tmap), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(192, 1) m2_gemm_tc_stream_kernel(const M2Node* __restrict__ nodes,
+                                                                   const M2Net* __restrict__ nets,
+                                                                   const M2Item* __restrict__ items,
+                                                                   const uint32_t* __restrict__ tabs,
+                                                                   float* __restrict__ ws,
+                                                                   const unsigned char* __restrict__ tmaps,
+                                                                   int* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t raw_full[kRawStages], raw_empty[kRawStages];
+    __shared__ __align__(8) uint64_t op_full[kOpStages], op_empty[kOpStages];
+    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ uint32_t tmem_base;
+    unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* raw = sm;
+    unsigned char* ops = sm + kRawStages * kRawStage;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const M2Item it = items[blockIdx.x];
+    const M2Node& nd = nodes[it.node];
+    const M2Net& N = nets[nd.net];
+    const int R = N.R;
+    const int64_t row0 = (int64_t)it.a * kTM;
+    const int rep0 = it.b * kTN;
+    const int64_t npar = nd.npar, cols = nd.cols;
+    const int total_chunks = (int)((cols + kKC - 1) / kKC);
+    const int cbeg = (int)(((int64_t)total_chunks * it.pad_) / it.begin);
+    const int cend = (int)(((int64_t)total_chunks * (it.pad_ + 1)) / it.begin);
+    const int nch = cend - cbeg;
+    const void* tmx = tmaps + (int64_t)nd.tm_x * 128;
+    const void* tmv = tmaps + (int64_t)nd.tm_v * 128;
+
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(kTN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kRawStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&raw_full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(&raw_empty[s])));
+        }
+        for (int s = 0; s < kOpStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(&op_full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&op_empty[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&done_bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    bool ok = true;
+
+    if (warp == 0) {
+        // ---------------- producer (one thread)
+        if (lane == 0) {
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmx) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmv) : "memory");
+            for (int c = 0; c < nch && ok; ++c) {
+                const int s = c % kRawStages;
+                if (c >= kRawStages)
+                    ok = mbar_wait(smem_addr(&raw_empty[s]), (uint32_t)((c / kRawStages - 1) & 1));
+                if (!ok) break;
+                const int k0 = (cbeg + c) * kKC;
+                unsigned char* ra = raw + s * kRawStage;
+                const uint32_t bar = smem_addr(&raw_full[s]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kRawStage)
+                             : "memory");
+                tma_load_2d(smem_addr(ra), tmx, k0, (int)row0, bar);
+                tma_load_2d(smem_addr(ra + kRawA), tmv, k0, rep0, bar);
+            }
+        }
+        __syncwarp();
+    } else if (warp <= 4) {
+        // ---------------- converters
+        const int ct = tid - 32;
+        for (int c = 0; c < nch && ok; ++c) {
+            const int s = c % kRawStages, o = c % kOpStages;
+            ok = mbar_wait(smem_addr(&raw_full[s]), (uint32_t)((c / kRawStages) & 1));
+            if (ok && c >= kOpStages) ok = mbar_wait(smem_addr(&op_empty[o]), (uint32_t)((c / kOpStages - 1) & 1));
+            if (!ok) break;
+            const unsigned char* ra = raw + s * kRawStage;
+            const unsigned char* rb = ra + kRawA;
+            unsigned char* st = ops + o * kStageBytes;
+            unsigned char *a_hi = st, *a_lo = st + kABytes, *b_hi = st + 2 * kABytes, *b_lo = st + 2 * kABytes + kBBytes;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = ct + 128 * q, off = sw128_offset(e >> 3, e & 7);
+                store_split(a_hi, a_lo, off, *reinterpret_cast<const float4*>(ra + off));
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = ct + 128 * q, off = sw128_offset(e >> 3, e & 7);
+                store_split(b_hi, b_lo, off, *reinterpret_cast<const float4*>(rb + off));
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(smem_addr(&op_full[o]));
+                mbar_arrive(smem_addr(&raw_empty[s]));
+            }
+        }
+    } else if (lane == 0) {
+        // ---------------- MMA issue (warp 5, one thread)
+        for (int c = 0; c < nch && ok; ++c) {
+            const int o = c % kOpStages;
+            ok = mbar_wait(smem_addr(&op_full[o]), (uint32_t)((c / kOpStages) & 1));
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned char* st = ops + o * kStageBytes;
+            const unsigned char* aop[3] = {st, st, st + kABytes};
+            const unsigned char* bop[3] = {st + 2 * kABytes, st + 2 * kABytes + kBBytes, st + 2 * kABytes};
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int ks = 0; ks < kKC / 8; ++ks) {
+                    const uint64_t ad = smem_desc_sw128(smem_addr(aop[p]) + ks * 32);
+                    const uint64_t bd = smem_desc_sw128(smem_addr(bop[p]) + ks * 32);
+                    const uint32_t acc = (c > 0 || p > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_addr(&op_empty[o])));
+            if (c == nch - 1)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_addr(&done_bar)));
+        }
+    }
+    if (!ok && (lane == 0)) atomicExch(err, DEVERR_TIMEOUT);
+
+    if (warp >= 1 && warp <= 4 && ok && nch > 0) {
+        // ---------------- epilogue: TMEM lanes 32 (warp % 4) .. + 31
+        const bool done = mbar_wait(smem_addr(&done_bar), 0u);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!done) {
+            if (lane == 0) atomicExch(err, DEVERR_TIMEOUT);
+        } else {
+            const int q4 = warp & 3;
+            const int64_t row = row0 + q4 * 32 + lane;
+#pragma unroll
+            for (int cc = 0; cc < kTN / 16; ++cc) {
+                uint32_t v[16];
+                const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(cc * 16);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < npar) {
+                    // W^T[rep][row]: a warp writes 32 consecutive rows of one rep
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int rep = rep0 + cc * 16 + j;
+                        if (rep < R) {
+                            float* dst = &ws[nd.w_off + (int64_t)rep * npar + row];
+                            if (it.begin > 1)
+                                atomicAdd(dst, __uint_as_float(v[j]));  // K split: partial sums
+                            else
+                                *dst = __uint_as_float(v[j]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTN));
+}
+
+cudaError_t launch_m2_gemm_tc(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items,
+                              const uint32_t* tabs, float* ws, const unsigned char* tmaps, int* err, bool stream,
+                              cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (stream) {
+        cudaFuncSetAttribute(m2_gemm_tc_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem);
+        m2_gemm_tc_stream_kernel<<<n, 192, kStreamSmem, s>>>(nodes, nets, items, tabs, ws, tmaps, err);
+    } else {
+        cudaFuncSetAttribute(m2_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        m2_gemm_tc_kernel<<<n, 128, kSmemBytes, s>>>(nodes, nets, items, tabs, ws, err);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tnsk

@@ -10,7 +10,8 @@
 //   a7  m2_vbuild_kernel   V(col, r) = sigma_r(col) r_k[r][b_r(col)] (Alg. 4)
 //       m2_gemm_kernel     x_k[r] += C_{par,k} (mat(X_k) V)[:, r]  (Alg. 5 for all
 //                          reps at once: each entry of X_k is read once per
-//                          batch of 64 reps)
+//                          batch of 64 reps); FP64 path. The FP32 path uses the
+//                          tensor-core kernel of m2_gemm_tc.cu.
 //   a8  m2_root_kernel     y_r = sum_i X_o(i) sigma_r(i) r_o[r][b_r(i)] = x_o^T r_o
 #include "fft.cuh"
 #include "kernels.cuh"
@@ -328,6 +329,41 @@ __global__ void __launch_bounds__(256) m2_gemm_kernel(const M2Node* __restrict__
 }
 
 // ---------------------------------------------------------------------------
+// a7 (tensor-core path): x_k[r][h_r(i)] += s_r(i) W^T[r][i], the count sketch of the
+// parent edge applied to the rows of W = mat(X_k) V. One CTA per (node, block of
+// reps), shared-memory bins, plain stores (x_k has no other producer).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) m2_wscatter_kernel(const M2Node* __restrict__ nodes,
+                                                          const M2Net* __restrict__ nets,
+                                                          const M2Item* __restrict__ items,
+                                                          const uint32_t* __restrict__ tabs, float* __restrict__ ws) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* bins = reinterpret_cast<float*>(smem_raw);
+    const M2Item it = items[blockIdx.x];
+    const M2Node& nd = nodes[it.node];
+    const M2Net& N = nets[nd.net];
+    const int64_t m = N.m;
+    const uint32_t mask = (uint32_t)(m - 1);
+    const int r0 = it.a, nr = it.b;
+    const int64_t npar = nd.npar;
+    for (int64_t q = threadIdx.x; q < (int64_t)nr * m; q += blockDim.x) bins[q] = 0.f;
+    __syncthreads();
+    for (int j = 0; j < nr; ++j) {
+        const int r = r0 + j;
+        const uint32_t* tw = tabs + N.tab_off + (int64_t)r * N.Lrep + nd.ptab;
+        const float* w = ws + nd.w_off + (int64_t)r * npar;
+        for (int64_t i = threadIdx.x; i < npar; i += blockDim.x) {
+            const uint32_t t = tw[i];
+            const float v = w[i];
+            atomicAdd(&bins[(int64_t)j * m + (t & mask)], (t & TNSK_SIGN_BIT) ? -v : v);
+        }
+    }
+    __syncthreads();
+    for (int64_t q = threadIdx.x; q < (int64_t)nr * m; q += blockDim.x)
+        ws[nd.x_off + (int64_t)r0 * m + q] = bins[q];
+}
+
+// ---------------------------------------------------------------------------
 // a8: root, y_r = sum_col X_o[col] V[r][col]
 // ---------------------------------------------------------------------------
 // One warp per rep at a time, lanes over the chunk's columns (coalesced X and V).
@@ -358,9 +394,9 @@ __global__ void __launch_bounds__(256) m2_root_kernel(const M2Node* __restrict__
 // ---------------------------------------------------------------------------
 template <typename T>
 static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void* const* d_tws, cudaStream_t s,
-                            Profiler& prof) {
+                            Profiler& prof, int* d_err) {
     static const int kKind[M2_NKINDS] = {TNSK_K_M2_LEAF, TNSK_K_M2_COMPOSE, TNSK_K_M2_VBUILD, TNSK_K_M2_GEMM,
-                                         TNSK_K_M2_ROOT};
+                                         TNSK_K_M2_GEMM, TNSK_K_M2_SCATTER, TNSK_K_M2_ROOT};
     const M2Node* nodes = (const M2Node*)(base + P.m2.nodes_off);
     const M2Net* nets = (const M2Net*)(base + P.m2.nets_off);
     const M2Item* items = (const M2Item*)(base + P.m2.items_off);
@@ -388,7 +424,20 @@ static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void*
                     else
                         launch_vbuild<T, uint64_t>(n, nodes, nets, its, tabs, ws, P.m2.max_qt, P.m2.max_order, s);
                     break;
-                case M2_GEMM: m2_gemm_kernel<T><<<n, 256, 0, s>>>(nodes, nets, its, tabs, ws); break;
+                case M2_GEMM:
+                case M2_GEMM_STREAM:
+                    if (sizeof(T) == 4)  // FP32: tensor cores (3-pass TF32 split)
+                        launch_m2_gemm_tc(n, nodes, nets, its, tabs, (float*)ws, base + P.m2.tmaps_off, d_err,
+                                          kind == M2_GEMM_STREAM, s);
+                    else
+                        m2_gemm_kernel<T><<<n, 256, 0, s>>>(nodes, nets, its, tabs, ws);
+                    break;
+                case M2_WSCATTER: {
+                    const size_t smem = P.m2.scatter_smem;
+                    cudaFuncSetAttribute(m2_wscatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    m2_wscatter_kernel<<<n, 256, smem, s>>>(nodes, nets, its, tabs, (float*)ws);
+                    break;
+                }
                 case M2_ROOT: m2_root_kernel<T><<<n, 256, 0, s>>>(nodes, nets, its, ws, yrep); break;
             }
             prof.end(s);
@@ -400,8 +449,9 @@ static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void*
 }
 
 tnsk_status run_method2(const BatchPlan& plan, unsigned char* base, bool fp64, const void* const* d_tws,
-                        cudaStream_t s, Profiler& prof, std::string& err) {
-    cudaError_t e = fp64 ? run_m2_t<double>(plan, base, d_tws, s, prof) : run_m2_t<float>(plan, base, d_tws, s, prof);
+                        cudaStream_t s, Profiler& prof, int* d_err, std::string& err) {
+    cudaError_t e = fp64 ? run_m2_t<double>(plan, base, d_tws, s, prof, d_err)
+                         : run_m2_t<float>(plan, base, d_tws, s, prof, d_err);
     if (e != cudaSuccess) {
         err = std::string("method 2 launch: ") + cudaGetErrorString(e);
         return TNSK_ERR_CUDA;

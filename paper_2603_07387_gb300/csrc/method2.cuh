@@ -14,6 +14,7 @@
 //            m-vector of each rep is r_k
 //   V        per node with children: [R][cols]: V(col, r) = sigma_r(col) r_k[r][b_r(col)],
 //            so that x_k = scatter_C( mat(X_k) V ) is a matrix product batched over reps
+//   W^T      FP32 tensor-core path: [R][npar] the product before the scatter (zeroed)
 //   y        per root: [R] FP64 accumulators
 #pragma once
 
@@ -42,6 +43,7 @@ struct M2Node {
     int64_t src_off;  // r_k used by V: r_off + (qt-2) m for qt >= 2, the child's x_off for qt = 1
     int64_t src_stride;  // distance between reps in the r_k source
     int64_t v_off;    // [R][cols] V matrix (nodes with children)
+    int64_t w_off;    // tensor-core path: [R][npar] product W^T = (mat(X_k) V)^T, -1 otherwise
     int64_t child_x[TNSK_MAX_SLOTS];  // slot j < c: the child's x_off
     int32_t dims[TNSK_MAX_ORDER];
     int32_t cmode[TNSK_MAX_ORDER];    // slot j < c: this node's mode toward child j
@@ -52,6 +54,8 @@ struct M2Node {
     int32_t qt;       // slots (0 for a leaf)
     int32_t net;      // method-2 network index
     int32_t is_root;
+    int32_t tm_x;     // streaming tensor-core path: tensor-map index of X and of V^T
+    int32_t tm_v;
     int32_t pad_;
 };
 
@@ -69,11 +73,24 @@ struct M2Item {
     int32_t node;
     int32_t a;        // first rep (compose) or row tile (gemm) or chunk index
     int32_t b;        // rep tile (gemm)
-    int32_t pad_;
-    int64_t begin, end;  // element range (leaf / vbuild / root chunks)
+    int32_t pad_;     // tensor-core gemm: index of this item's K split
+    int64_t begin, end;  // element range (leaf / vbuild / root chunks); tensor-core gemm:
+                         // begin = number of K splits
 };
 
-enum M2Kind { M2_LEAF = 0, M2_COMPOSE = 1, M2_VBUILD = 2, M2_GEMM = 3, M2_ROOT = 4, M2_NKINDS = 5 };
+// M2_GEMM_STREAM: tensor-core tiles of row-major FP32 tensors with contiguous
+// rows (parent mode first, 4 | cols, 16-byte aligned): streaming kernel.
+// M2_WSCATTER: x_k[r][h(i)] += s(i) W^T[r][i] for the tensor-core tiles.
+enum M2Kind {
+    M2_LEAF = 0,
+    M2_COMPOSE = 1,
+    M2_VBUILD = 2,
+    M2_GEMM = 3,
+    M2_GEMM_STREAM = 4,
+    M2_WSCATTER = 5,
+    M2_ROOT = 6,
+    M2_NKINDS = 7
+};
 
 struct M2Plan {
     int n_nets = 0;
@@ -83,6 +100,10 @@ struct M2Plan {
     bool idx32 = true;  // every node has fewer than 2^32 columns
     int max_qt = 0;     // largest slot count
     int max_order = 0;  // largest tensor order
+    size_t tmaps_off = 0;  // tensor maps (128 B each) in the descriptor block
+    size_t scatter_smem = 0;  // shared-memory bins of the largest row-scatter item
+    // tensor maps to encode once the device addresses are fixed: node, 0 = X / 1 = V^T
+    std::vector<std::pair<int, int>> tmap_jobs;
     int max_log2m = 0;
     // per height, per kind: [first, count) into the item array
     std::vector<int> first, count;  // size (max_height+1) * M2_NKINDS
@@ -91,6 +112,9 @@ struct M2Plan {
 struct BatchPlan;
 struct Profiler;
 tnsk_status run_method2(const BatchPlan& plan, unsigned char* base, bool fp64, const void* const* d_tws,
-                        cudaStream_t s, Profiler& prof, std::string& err);
+                        cudaStream_t s, Profiler& prof, int* d_err, std::string& err);
+cudaError_t launch_m2_gemm_tc(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items,
+                              const uint32_t* tabs, float* ws, const unsigned char* tmaps, int* err, bool stream,
+                              cudaStream_t s);
 
 }  // namespace tnsk

@@ -2,9 +2,12 @@
 // (Sec. 1 Def. "Tensor contraction": u != v and n_u = n_v for every (u, v) in E;
 // Sec. 4.1 WLOG 1: a mode is part of at most one contraction) and the layout of
 // one batch's descriptors and scratch.
+#include <cuda.h>
+
 #include <algorithm>
 #include <cstring>
 #include <limits>
+#include <mutex>
 
 #include "plan.cuh"
 
@@ -39,7 +42,65 @@ int64_t ts_offset(int qt, int l, int j, int s, int64_t m) {
     return ((before + j) * 2 + s) * m;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
 }  // namespace
+
+bool tensor_maps_available() { return encoder() != nullptr; }
+
+// Row-major FP32 matrix [rows][cols] (cols % 4 == 0, 16-byte aligned) as 2-D
+// TMA boxes of 32 columns x box_rows rows, 128-byte swizzle, zero fill outside.
+static bool encode_rowmajor(void* out, const void* base, int64_t rows, int64_t cols, int box_rows) {
+    EncodeTiledFn fn = encoder();
+    if (!fn) return false;
+    CUtensorMap tm;
+    cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t gstride[1] = {(cuuint64_t)cols * 4};
+    cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), gdim, gstride, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    std::memcpy(out, &tm, sizeof(tm));
+    return true;
+}
+
+tnsk_status finalize_plan(BatchPlan& P, unsigned char* base, std::string& err) {
+    if (P.m2.tmap_jobs.empty()) return TNSK_OK;
+    const M2Node* nodes = (const M2Node*)(P.host_desc.data() + (P.m2.nodes_off - P.desc_off));
+    const M2Net* nets = (const M2Net*)(P.host_desc.data() + (P.m2.nets_off - P.desc_off));
+    unsigned char* maps = P.host_desc.data() + (P.m2.tmaps_off - P.desc_off);
+    const float* ws = (const float*)(base + P.m2.ws_off);
+    for (size_t i = 0; i < P.m2.tmap_jobs.size(); ++i) {
+        const M2Node& nd = nodes[P.m2.tmap_jobs[i].first];
+        const bool is_v = P.m2.tmap_jobs[i].second == 1;
+        const bool ok = is_v ? encode_rowmajor(maps + i * 128, ws + nd.v_off, nets[nd.net].R, nd.cols, 64)
+                             : encode_rowmajor(maps + i * 128, nd.data, nd.npar, nd.cols, 128);
+        if (!ok) {
+            err = "tensor-map encoding failed";
+            return TNSK_ERR_CUDA;
+        }
+    }
+    return TNSK_OK;
+}
 
 tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I, std::string& why) {
     if (net.p < 1 || !net.X) {
@@ -289,7 +350,8 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     std::vector<M2Node> m2nodes;
     std::vector<M2Net> m2n;
     int64_t tab_words = 0, yrep_n = 0, xs_n = 0, spec_n = 0, sexp_n = 0;
-    int64_t ws_x = 0, ws_r = 0, ws_v = 0;  // method-2 workspace parts (elements)
+    int64_t ws_x = 0, ws_w = 0, ws_r = 0, ws_v = 0;  // method-2 workspace parts (elements)
+    const bool tma = tensor_maps_available();
     size_t scatter_smem = 16;
     int max_log2m1 = 0, max_log2m2 = 0, m1_max_order = 0;
     struct PendingItem {
@@ -300,7 +362,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     // method-2 node-local offsets are finalised after the x / r / V totals are known
     struct M2Fix {
         size_t node;
-        int64_t x, r, v, src;
+        int64_t x, w, r, v, src;
         int src_kind;  // 0 none, 1 r part, 2 x part
         int64_t child_x[TNSK_MAX_SLOTS];
     };
@@ -470,6 +532,9 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
         nb.log2m = I.log2m;
         nb.R = R;
         nb.tab_off = tab_words;
+        // reps per row-scatter CTA: bins of up to 48 KiB in shared memory
+        const int scatter_reps = (int)std::max<int64_t>(1, std::min<int64_t>(16, (48 * 1024) / (m * 4)));
+        P.m2.scatter_smem = std::max(P.m2.scatter_smem, (size_t)scatter_reps * (size_t)m * sizeof(float));
         nb.y_off = yrep_n;
         max_log2m2 = std::max(max_log2m2, I.log2m);
         const int net_id = (int)m2n.size();
@@ -529,11 +594,12 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
         }
         tab_words += (int64_t)R * Lrep;
         // nodes
+        auto up16 = [](int64_t v) { return (v + 15) & ~(int64_t)15; };
         std::vector<int64_t> xo(I.p, -1);
         for (int k = 0; k < I.p; ++k) {
             if (k == I.root) continue;
             xo[k] = ws_x;
-            ws_x += (int64_t)R * m;
+            ws_x = up16(ws_x + (int64_t)R * m);
         }
         for (int k = 0; k < I.p; ++k) {
             const tnsk_tensor& X = N.X[k];
@@ -576,6 +642,8 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
             }
             nd.pad_tab = pad_tab[k];
             nd.t_tab = t_tab[k];
+            nd.tm_x = -1;
+            nd.tm_v = -1;
             M2Fix fx{};
             fx.node = m2nodes.size();
             fx.x = xo[k];
@@ -585,7 +653,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
             for (int j = 0; j < nd.c; ++j) fx.child_x[j] = xo[I.child[k][j]];
             if (nd.qt >= 2) {
                 fx.r = ws_r;
-                ws_r += (int64_t)R * (nd.qt - 1) * m;
+                ws_r = up16(ws_r + (int64_t)R * (nd.qt - 1) * m);
                 fx.src = fx.r + (int64_t)(nd.qt - 2) * m;
                 fx.src_kind = 1;
                 nd.src_stride = (int64_t)(nd.qt - 1) * m;
@@ -596,7 +664,12 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
             }
             if (nd.c >= 1) {
                 fx.v = ws_v;
-                ws_v += nd.cols * (int64_t)R;
+                ws_v = up16(ws_v + nd.cols * (int64_t)R);
+            }
+            fx.w = -1;
+            if (!fp64 && nd.c >= 1 && !nd.is_root) {  // tensor-core product W^T
+                fx.w = ws_w;
+                ws_w = up16(ws_w + nd.npar * (int64_t)R);
             }
             fixes.push_back(fx);
             m2nodes.push_back(nd);
@@ -616,10 +689,31 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                     M2Item it{node_idx, 0, 0, 0, b0, std::min(nd.cols, b0 + 128)};
                     pend.push_back({h, M2_VBUILD, it});
                 }
-            if (nd.c >= 1 && !nd.is_root && nd.numel > 0)
-                for (int64_t rt = 0; rt * 64 < nd.npar; ++rt)
+            if (!fp64 && nd.c >= 1 && !nd.is_root) {
+                // count sketch of W's rows into x_k, after the tensor-core product
+                for (int r0 = 0; r0 < R; r0 += scatter_reps) {
+                    M2Item it{node_idx, r0, std::min(scatter_reps, R - r0), 0, 0, 0};
+                    pend.push_back({h, M2_WSCATTER, it});
+                }
+            }
+            if (nd.c >= 1 && !nd.is_root && nd.numel > 0) {
+                // row tiles: 128 rows for the tensor-core kernels (FP32), 64 for the FP64 one;
+                // the split of K (tensor-core kernels) is chosen once all tiles are known
+                const int64_t tile = fp64 ? 64 : 128;
+                const bool stream = !fp64 && tma && nd.dtype == TNSK_F32 && nd.A == 1 && (nd.cols % 4) == 0 &&
+                                    ((uintptr_t)nd.data % 16) == 0 && nd.npar < ((int64_t)1 << 31) &&
+                                    nd.cols < ((int64_t)1 << 31);
+                if (stream) {
+                    m2nodes.back().tm_x = (int32_t)P.m2.tmap_jobs.size();
+                    P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 0});
+                    m2nodes.back().tm_v = (int32_t)P.m2.tmap_jobs.size();
+                    P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 1});
+                }
+                for (int64_t rt = 0; rt * tile < nd.npar; ++rt)
                     for (int64_t ct = 0; ct * 64 < R; ++ct)
-                        pend.push_back({h, M2_GEMM, M2Item{node_idx, (int)rt, (int)ct, 0, 0, 0}});
+                        pend.push_back({h, stream ? M2_GEMM_STREAM : M2_GEMM,
+                                        M2Item{node_idx, (int)rt, (int)ct, 0, 1, 0}});
+            }
             if (nd.is_root)
                 for (int64_t b0 = 0; b0 < std::max<int64_t>(nd.cols, 1); b0 += 4096) {
                     M2Item it{node_idx, 0, 0, 0, b0, std::min(nd.cols, b0 + 4096)};
@@ -644,10 +738,38 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     for (const M2Fix& fx : fixes) {
         M2Node& nd = m2nodes[fx.node];
         nd.x_off = fx.x;
-        nd.r_off = fx.r >= 0 ? ws_x + fx.r : -1;
-        nd.v_off = fx.v >= 0 ? ws_x + ws_r + fx.v : -1;
-        nd.src_off = fx.src_kind == 1 ? ws_x + fx.src : (fx.src_kind == 2 ? fx.src : -1);
+        nd.w_off = fx.w >= 0 ? ws_x + fx.w : -1;
+        nd.r_off = fx.r >= 0 ? ws_x + ws_w + fx.r : -1;
+        nd.v_off = fx.v >= 0 ? ws_x + ws_w + ws_r + fx.v : -1;
+        nd.src_off = fx.src_kind == 1 ? ws_x + ws_w + fx.src : (fx.src_kind == 2 ? fx.src : -1);
         for (int j = 0; j < nd.c; ++j) nd.child_x[j] = fx.child_x[j];
+    }
+    // ---- split K of the tensor-core GEMM tiles: aim for >= 4 CTAs per SM per height,
+    // with >= 4 chunks of 32 columns per split
+    if (!fp64 && !pend.empty()) {
+        std::vector<int64_t> tiles(P.m2.max_height + 1, 0);
+        for (const PendingItem& q : pend)
+            if (q.kind == M2_GEMM || q.kind == M2_GEMM_STREAM) tiles[q.h]++;
+        std::vector<PendingItem> out;
+        out.reserve(pend.size());
+        for (const PendingItem& q : pend) {
+            if (q.kind != M2_GEMM && q.kind != M2_GEMM_STREAM) {
+                out.push_back(q);
+                continue;
+            }
+            const int64_t chunks = (m2nodes[q.it.node].cols + 31) / 32;
+            // streaming kernel: 1 CTA per SM, aim for 2 waves; general kernel: 2 per SM, 2 waves
+            const int64_t want = q.kind == M2_GEMM_STREAM ? 2 * 152 : 4 * 152;
+            int64_t split = (want + tiles[q.h] - 1) / tiles[q.h];
+            split = std::max<int64_t>(1, std::min<int64_t>(split, chunks / 4));
+            for (int64_t sidx = 0; sidx < split; ++sidx) {
+                PendingItem z = q;
+                z.it.begin = split;  // number of K splits
+                z.it.pad_ = (int)sidx;
+                out.push_back(z);
+            }
+        }
+        pend.swap(out);
     }
     // ---- method-2 item order: by height, then kind
     std::vector<M2Item> m2items;
@@ -685,6 +807,8 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     size_t o_reqs = stage(H, reqs), o_m1t = stage(H, m1t), o_m1n = stage(H, m1n), o_m1w = stage(H, m1w);
     size_t o_open = stage(H, opens), o_items = stage(H, m1items), o_comb = stage(H, comb);
     size_t o_m2nodes = stage(H, m2nodes), o_m2n = stage(H, m2n), o_m2items = stage(H, m2items);
+    std::vector<unsigned char> tmap_space(P.m2.tmap_jobs.size() * 128, 0);
+    size_t o_tmaps = stage(H, tmap_space);
     P.desc_off = P.arena.take(H.size());
     P.reqs_off = P.desc_off + o_reqs;
     P.m1.tens_off = P.desc_off + o_m1t;
@@ -696,12 +820,13 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     P.m2.nodes_off = P.desc_off + o_m2nodes;
     P.m2.nets_off = P.desc_off + o_m2n;
     P.m2.items_off = P.desc_off + o_m2items;
+    P.m2.tmaps_off = P.desc_off + o_tmaps;
     // ---- zeroed region: per-rep estimates, method-1 sketches, method-2 x accumulators
     P.zero_off = P.arena.take(0);
     P.yrep_off = P.arena.take((size_t)yrep_n * sizeof(double));
     P.m1.xs_off = P.arena.take((size_t)xs_n * acc);
-    P.m2.ws_off = P.arena.take((size_t)(ws_x + ws_r + ws_v) * acc);
-    P.zero_bytes = P.m2.ws_off + (size_t)ws_x * acc - P.zero_off;
+    P.m2.ws_off = P.arena.take((size_t)(ws_x + ws_w + ws_r + ws_v) * acc);
+    P.zero_bytes = P.m2.ws_off + (size_t)(ws_x + ws_w) * acc - P.zero_off;
     // ---- the rest
     P.tabs_off = P.arena.take((size_t)tab_words * sizeof(uint32_t));
     P.coef_off = P.arena.take((size_t)P.n_coef_rows * sizeof(HashCoef));

@@ -67,6 +67,11 @@ struct BatchPlan {
 };
 
 tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& info, std::string& why);
+// True when the driver's tensor-map encoder is available (streaming tensor-core path).
+bool tensor_maps_available();
+// Encodes the plan's tensor maps into its host descriptor block once the device
+// base address of the plan's scratch is fixed (before the descriptor upload).
+tnsk_status finalize_plan(BatchPlan& plan, unsigned char* base, std::string& err);
 tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* nets, const tnsk_params* params,
                        double* const* outs, double* const* per_reps, bool fp64, bool sketch_only, BatchPlan& plan,
                        std::string& err);

@@ -144,6 +144,21 @@ def test_method2_estimate_small(ctx, prec, m):
             assert_parity(per, y, s, TOL[prec], f"{spec.name} m={m} root={root}")
 
 
+@pytest.mark.parametrize("root,reps,dtype", [(0, 70, "float32"), (3, 64, "float32"), (0, 16, "bfloat16")])
+def test_method2_contraction_tile_edges(ctx, root, reps, dtype):
+    """Row counts off the 128-row tile, columns off the 32-column chunk, reps off the
+    64-rep tile, a parent mode that is not the first mode, BF16 inputs."""
+    rng = np.random.default_rng(40 + root)
+    X = [rng.standard_normal(300), rng.standard_normal((300, 200)), rng.standard_normal((170, 200)),
+         rng.standard_normal(170)]
+    spec = W.NetSpec(X, [(0, 1), (2, 4), (3, 5)], [], "chain-edges")
+    tdt = getattr(torch, dtype)
+    p = tnsk.Params(m=256, reps=reps, seed=9, method=tnsk.ACYCLIC, root=root)
+    out, per = gpu_estimate(ctx, spec, p, tdt)
+    y, s = oracle_estimate(spec, p, tdt)
+    assert_parity(per, y, s, TOL[p.prec], f"chain-edges root={root} reps={reps} {dtype}")
+
+
 def test_method2_tt_chain_full_size(ctx):
     A, B = W.tt_cores()
     spec = W.tt_chain(A, B)
