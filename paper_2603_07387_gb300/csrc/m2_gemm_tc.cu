@@ -102,10 +102,11 @@ __global__ void __launch_bounds__(128, 2) m2_gemm_tc_kernel(const M2Node* __rest
     const int64_t row0 = (int64_t)it.a * kTM;
     const int rep0 = it.b * kTN;
     const int64_t npar = nd.npar, cols = nd.cols, Bc = nd.Bc;
-    const float* V = ws + nd.v_off;
+    const float* V = ws + nd.v_off;                       // TF32 hi part of V^T
+    const float* Vlo = ws + nd.v_off + (int64_t)R * cols;  // its lo part
     const bool fast_x = nd.dtype == TNSK_F32 && nd.A == 1 && (cols & 3) == 0 &&
                         ((uintptr_t)nd.data & 15) == 0;
-    const bool fast_v = (cols & 3) == 0 && (((uintptr_t)V) & 15) == 0;
+    const bool fast_v = (cols & 3) == 0 && (((uintptr_t)V) & 15) == 0 && (((uintptr_t)Vlo) & 15) == 0;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(128, 2) m2_gemm_tc_kernel(const M2Node* __rest
     // their 16-byte stores land in 8 different bank groups
     const int rin = tid & 7, sub = (tid >> 3) & 7, rhi = tid >> 6;
     auto trow = [&](int j) { return rin + 8 * (rhi + 2 * j); };
-    float4 ra[8], rv[4];
+    float4 ra[8], rv[4], rvl[4];
     auto load_chunk = [&](int64_t k0) {
         const int64_t gc = k0 + sub * 4;
 #pragma unroll
@@ -157,19 +158,28 @@ __global__ void __launch_bounds__(128, 2) m2_gemm_tc_kernel(const M2Node* __rest
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int rep = rep0 + trow(j);
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f), vl = v;
             if (rep < R) {
                 const float* src = V + (int64_t)rep * cols;
+                const float* srl = Vlo + (int64_t)rep * cols;
                 if (fast_v) {
-                    if (gc < cols) v = *reinterpret_cast<const float4*>(src + gc);
+                    if (gc < cols) {
+                        v = *reinterpret_cast<const float4*>(src + gc);
+                        vl = *reinterpret_cast<const float4*>(srl + gc);
+                    }
                 } else {
                     v.x = gc + 0 < cols ? src[gc + 0] : 0.f;
                     v.y = gc + 1 < cols ? src[gc + 1] : 0.f;
                     v.z = gc + 2 < cols ? src[gc + 2] : 0.f;
                     v.w = gc + 3 < cols ? src[gc + 3] : 0.f;
+                    vl.x = gc + 0 < cols ? srl[gc + 0] : 0.f;
+                    vl.y = gc + 1 < cols ? srl[gc + 1] : 0.f;
+                    vl.z = gc + 2 < cols ? srl[gc + 2] : 0.f;
+                    vl.w = gc + 3 < cols ? srl[gc + 3] : 0.f;
                 }
             }
             rv[j] = v;
+            rvl[j] = vl;
         }
     };
 
@@ -188,7 +198,11 @@ __global__ void __launch_bounds__(128, 2) m2_gemm_tc_kernel(const M2Node* __rest
 #pragma unroll
         for (int j = 0; j < 8; ++j) store_split(a_hi, a_lo, kmajor_offset(trow(j), sub * 4), ra[j]);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) store_split(b_hi, b_lo, kmajor_offset(trow(j), sub * 4), rv[j]);
+        for (int j = 0; j < 4; ++j) {
+            const int off = kmajor_offset(trow(j), sub * 4);
+            *reinterpret_cast<float4*>(b_hi + off) = rv[j];
+            *reinterpret_cast<float4*>(b_lo + off) = rvl[j];
+        }
         if (c + 1 < nchunks) load_chunk((int64_t)(cbeg + c + 1) * kKC);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -258,28 +272,29 @@ __global__ void __launch_bounds__(128, 2) m2_gemm_tc_kernel(const M2Node* __rest
 // ---------------------------------------------------------------------------
 // Streaming variant for row-major FP32 tensors whose parent mode is the first
 // mode (mat(X_k) is the row-major matrix itself) and whose column count is a
-// multiple of 4. Warp-specialised; the tiles of X and V^T arrive by TMA (one
-// 2-D box per operand and chunk, described by tensor maps made at plan time) in
-// the 128-byte swizzled K-major layout, with zero fill outside the matrix.
-//   warp 0     producer: two cp.async.bulk.tensor loads per chunk into a
-//              5-deep ring (raw_full counts bytes)
-//   warps 1-4  converters: raw FP32 -> hi/lo TF32 at the same swizzled
-//              positions (row r's 16-byte chunk g sits at g ^ (r & 7)), then
-//              the epilogue
-//   warp 5     tensor memory allocation and MMA issue
+// multiple of 4. Warp-specialised; per K-chunk of 32 columns the tiles of X and
+// of the pre-split V^T (hi and lo TF32 parts, written by the V build) arrive by
+// TMA (2-D boxes from tensor maps made at plan time) in the 128-byte swizzled
+// K-major layout, with zero fill outside the matrices. X's hi / lo parts go to
+// tensor memory, so the MMA reads A from TMEM and only B from shared memory:
+//   warp 0     producer: three cp.async.bulk.tensor loads per chunk into a
+//              6-deep ring (raw_full counts bytes)
+//   warps 1-4  converters: one row of X per thread (its TMEM lane), raw FP32 ->
+//              hi / lo TF32 stored with tcgen05.st; then the epilogue
+//   warp 5     tensor memory allocation and MMA issue; tcgen05.commit frees the
+//              ring stage and the TMEM operand stage
+// Tensor memory: columns [0, 64) accumulator, [64 + 64 t, + 64) operand stage t
+// (hi in the first 32 columns, lo in the next 32).
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int kRawStages = 5;
-constexpr int kOpStages = 2;
-constexpr int kRawA = kTM * 128;  // one chunk of X rows: 128 rows x 128 B
-constexpr int kRawB = kTN * 128;  // one chunk of V^T rows
-constexpr int kRawStage = kRawA + kRawB;
-constexpr int kStreamSmem = kRawStages * kRawStage + kOpStages * kStageBytes + 1024;
-
-__device__ __forceinline__ int sw128_offset(int row, int g) {
-    return (row >> 3) * 1024 + (row & 7) * 128 + ((g ^ (row & 7)) << 4);
-}
+constexpr int kRawStages = 6;
+constexpr int kTmStages = 2;
+constexpr int kRawX = kTM * 128;   // 128 rows x 128 B
+constexpr int kRawV = kTN * 128;   // 64 rows x 128 B (one of hi / lo)
+constexpr int kRawStage = kRawX + 2 * kRawV;
+constexpr int kStreamSmem = kRawStages * kRawStage + 1024;
+constexpr uint32_t kTmemCols = 256;
 
 // K-major, 128-byte swizzle: stride byte offset 1024 (8-row atoms), leading offset unused.
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
@@ -299,23 +314,31 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int 
         : "memory");
 }
 
+__device__ __forceinline__ void tmem_store32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+        "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+        "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(192, 1) m2_gemm_tc_stream_kernel(const M2Node* __restrict__ nodes,
                                                                    const M2Net* __restrict__ nets,
                                                                    const M2Item* __restrict__ items,
-                                                                   const uint32_t* __restrict__ tabs,
                                                                    float* __restrict__ ws,
                                                                    const unsigned char* __restrict__ tmaps,
                                                                    int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t raw_full[kRawStages], raw_empty[kRawStages];
-    __shared__ __align__(8) uint64_t op_full[kOpStages], op_empty[kOpStages];
+    __shared__ __align__(8) uint64_t tm_full[kTmStages], tm_empty[kTmStages];
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t tmem_base;
-    unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* raw = sm;
-    unsigned char* ops = sm + kRawStages * kRawStage;
+    unsigned char* raw = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const M2Item it = items[blockIdx.x];
     const M2Node& nd = nodes[it.node];
@@ -329,21 +352,22 @@ __global__ void __launch_bounds__(192, 1) m2_gemm_tc_stream_kernel(const M2Node*
     const int cend = (int)(((int64_t)total_chunks * (it.pad_ + 1)) / it.begin);
     const int nch = cend - cbeg;
     const void* tmx = tmaps + (int64_t)nd.tm_x * 128;
-    const void* tmv = tmaps + (int64_t)nd.tm_v * 128;
+    const void* tmvh = tmaps + (int64_t)nd.tm_v * 128;
+    const void* tmvl = tmaps + (int64_t)(nd.tm_v + 1) * 128;
 
     if (warp == 5) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
-                     "r"(kTN));
+                     "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
         for (int s = 0; s < kRawStages; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&raw_full[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(&raw_empty[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&raw_empty[s])));
         }
-        for (int s = 0; s < kOpStages; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(&op_full[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&op_empty[s])));
+        for (int t = 0; t < kTmStages; ++t) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(&tm_full[t])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&tm_empty[t])));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&done_bar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -358,75 +382,81 @@ __global__ void __launch_bounds__(192, 1) m2_gemm_tc_stream_kernel(const M2Node*
         // ---------------- producer (one thread)
         if (lane == 0) {
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmx) : "memory");
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmv) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvh) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvl) : "memory");
             for (int c = 0; c < nch && ok; ++c) {
                 const int s = c % kRawStages;
                 if (c >= kRawStages)
                     ok = mbar_wait(smem_addr(&raw_empty[s]), (uint32_t)((c / kRawStages - 1) & 1));
                 if (!ok) break;
                 const int k0 = (cbeg + c) * kKC;
-                unsigned char* ra = raw + s * kRawStage;
+                unsigned char* st = raw + s * kRawStage;
                 const uint32_t bar = smem_addr(&raw_full[s]);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kRawStage)
                              : "memory");
-                tma_load_2d(smem_addr(ra), tmx, k0, (int)row0, bar);
-                tma_load_2d(smem_addr(ra + kRawA), tmv, k0, rep0, bar);
+                tma_load_2d(smem_addr(st), tmx, k0, (int)row0, bar);
+                tma_load_2d(smem_addr(st + kRawX), tmvh, k0, rep0, bar);
+                tma_load_2d(smem_addr(st + kRawX + kRawV), tmvl, k0, rep0, bar);
             }
         }
         __syncwarp();
     } else if (warp <= 4) {
-        // ---------------- converters
-        const int ct = tid - 32;
+        // ---------------- converters: thread = row q4 * 32 + lane of the tile (its TMEM lane)
+        const int q4 = warp & 3;
+        const int r = q4 * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
         for (int c = 0; c < nch && ok; ++c) {
-            const int s = c % kRawStages, o = c % kOpStages;
+            const int s = c % kRawStages, t = c % kTmStages;
             ok = mbar_wait(smem_addr(&raw_full[s]), (uint32_t)((c / kRawStages) & 1));
-            if (ok && c >= kOpStages) ok = mbar_wait(smem_addr(&op_empty[o]), (uint32_t)((c / kOpStages - 1) & 1));
+            if (ok && c >= kTmStages) ok = mbar_wait(smem_addr(&tm_empty[t]), (uint32_t)((c / kTmStages - 1) & 1));
             if (!ok) break;
-            const unsigned char* ra = raw + s * kRawStage;
-            const unsigned char* rb = ra + kRawA;
-            unsigned char* st = ops + o * kStageBytes;
-            unsigned char *a_hi = st, *a_lo = st + kABytes, *b_hi = st + 2 * kABytes, *b_lo = st + 2 * kABytes + kBBytes;
+            const unsigned char* rowp = raw + s * kRawStage + (r >> 3) * 1024 + (r & 7) * 128;
+            uint32_t hi[32], lo[32];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int e = ct + 128 * q, off = sw128_offset(e >> 3, e & 7);
-                store_split(a_hi, a_lo, off, *reinterpret_cast<const float4*>(ra + off));
-            }
+            for (int g = 0; g < 8; ++g) {
+                const float4 v = *reinterpret_cast<const float4*>(rowp + ((g ^ (r & 7)) << 4));
+                const float x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int e = ct + 128 * q, off = sw128_offset(e >> 3, e & 7);
-                store_split(b_hi, b_lo, off, *reinterpret_cast<const float4*>(rb + off));
+                for (int q = 0; q < 4; ++q) {
+                    hi[4 * g + q] = tf32_rna(x[q]);
+                    lo[4 * g + q] = tf32_rna(x[q] - __uint_as_float(hi[4 * g + q]));
+                }
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const uint32_t col = (uint32_t)(kTN + 64 * t);
+            tmem_store32(tmem + lane_base + col, hi);
+            tmem_store32(tmem + lane_base + col + 32, lo);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(smem_addr(&op_full[o]));
-                mbar_arrive(smem_addr(&raw_empty[s]));
-            }
+            if (lane == 0) mbar_arrive(smem_addr(&tm_full[t]));
         }
     } else if (lane == 0) {
         // ---------------- MMA issue (warp 5, one thread)
         for (int c = 0; c < nch && ok; ++c) {
-            const int o = c % kOpStages;
-            ok = mbar_wait(smem_addr(&op_full[o]), (uint32_t)((c / kOpStages) & 1));
+            const int s = c % kRawStages, t = c % kTmStages;
+            ok = mbar_wait(smem_addr(&tm_full[t]), (uint32_t)((c / kTmStages) & 1));
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned char* st = ops + o * kStageBytes;
-            const unsigned char* aop[3] = {st, st, st + kABytes};
-            const unsigned char* bop[3] = {st + 2 * kABytes, st + 2 * kABytes + kBBytes, st + 2 * kABytes};
+            const unsigned char* st = raw + s * kRawStage;
+            const uint32_t a_hi = tmem + (uint32_t)(kTN + 64 * t), a_lo = a_hi + 32;
+            const uint32_t aop[3] = {a_hi, a_hi, a_lo};
+            const unsigned char* bop[3] = {st + kRawX, st + kRawX + kRawV, st + kRawX};
 #pragma unroll
             for (int p = 0; p < 3; ++p)
 #pragma unroll
                 for (int ks = 0; ks < kKC / 8; ++ks) {
-                    const uint64_t ad = smem_desc_sw128(smem_addr(aop[p]) + ks * 32);
+                    const uint32_t at = aop[p] + ks * 8;
                     const uint64_t bd = smem_desc_sw128(smem_addr(bop[p]) + ks * 32);
                     const uint32_t acc = (c > 0 || p > 0 || ks > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, q;\n\t}" ::"r"(tmem),
+                        "r"(at), "l"(bd), "r"(kIdesc), "r"(acc));
                 }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_addr(&op_empty[o])));
+                smem_addr(&tm_empty[t])));
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_addr(&raw_empty[s])));
             if (c == nch - 1)
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     smem_addr(&done_bar)));
@@ -435,7 +465,7 @@ __global__ void __launch_bounds__(192, 1) m2_gemm_tc_stream_kernel(const M2Node*
     if (!ok && (lane == 0)) atomicExch(err, DEVERR_TIMEOUT);
 
     if (warp >= 1 && warp <= 4 && ok && nch > 0) {
-        // ---------------- epilogue: TMEM lanes 32 (warp % 4) .. + 31
+        // ---------------- epilogue: W^T[rep][row] from TMEM lanes 32 (warp % 4) .. + 31
         const bool done = mbar_wait(smem_addr(&done_bar), 0u);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!done) {
@@ -456,7 +486,6 @@ __global__ void __launch_bounds__(192, 1) m2_gemm_tc_stream_kernel(const M2Node*
                     : "r"(ta));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (row < npar) {
-                    // W^T[rep][row]: a warp writes 32 consecutive rows of one rep
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int rep = rep0 + cc * 16 + j;
@@ -474,7 +503,7 @@ __global__ void __launch_bounds__(192, 1) m2_gemm_tc_stream_kernel(const M2Node*
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTN));
+    if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 cudaError_t launch_m2_gemm_tc(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items,
@@ -483,7 +512,7 @@ cudaError_t launch_m2_gemm_tc(int n, const M2Node* nodes, const M2Net* nets, con
     if (n <= 0) return cudaSuccess;
     if (stream) {
         cudaFuncSetAttribute(m2_gemm_tc_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem);
-        m2_gemm_tc_stream_kernel<<<n, 192, kStreamSmem, s>>>(nodes, nets, items, tabs, ws, tmaps, err);
+        m2_gemm_tc_stream_kernel<<<n, 192, kStreamSmem, s>>>(nodes, nets, items, ws, tmaps, err);
     } else {
         cudaFuncSetAttribute(m2_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
         m2_gemm_tc_kernel<<<n, 128, kSmemBytes, s>>>(nodes, nets, items, tabs, ws, err);

@@ -224,7 +224,17 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
             }
         rsh_reduce<QTMAX>(b, neg, qt, tabr + nd.t_tab, m, mask);
         const T z = ws[nd.src_off + (int64_t)r * nd.src_stride + b[0]];
-        ws[nd.v_off + (int64_t)r * nd.cols + col] = (neg & TNSK_SIGN_BIT) ? -z : z;
+        const T v = (neg & TNSK_SIGN_BIT) ? -z : z;
+        if (sizeof(T) == 4 && !nd.is_root) {
+            // operand of the tensor-core product: TF32 hi part, then its lo part R*cols later
+            uint32_t hi, lo;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"((float)v));
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"((float)v - __uint_as_float(hi)));
+            ws[nd.v_off + (int64_t)r * nd.cols + col] = (T)__uint_as_float(hi);
+            ws[nd.v_off + ((int64_t)R + r) * nd.cols + col] = (T)__uint_as_float(lo);
+        } else {
+            ws[nd.v_off + (int64_t)r * nd.cols + col] = v;
+        }
     }
 }
 

@@ -42,7 +42,8 @@ struct M2Node {
     int64_t r_off;    // [R][(qt-1) m] composition outputs (qt >= 2), else -1
     int64_t src_off;  // r_k used by V: r_off + (qt-2) m for qt >= 2, the child's x_off for qt = 1
     int64_t src_stride;  // distance between reps in the r_k source
-    int64_t v_off;    // [R][cols] V matrix (nodes with children)
+    int64_t v_off;    // [R][cols] V matrix (nodes with children); FP32 non-root nodes hold the
+                      // TF32 hi part there and the lo part in the next [R][cols]
     int64_t w_off;    // tensor-core path: [R][npar] product W^T = (mat(X_k) V)^T, -1 otherwise
     int64_t child_x[TNSK_MAX_SLOTS];  // slot j < c: the child's x_off
     int32_t dims[TNSK_MAX_ORDER];
@@ -102,7 +103,7 @@ struct M2Plan {
     int max_order = 0;  // largest tensor order
     size_t tmaps_off = 0;  // tensor maps (128 B each) in the descriptor block
     size_t scatter_smem = 0;  // shared-memory bins of the largest row-scatter item
-    // tensor maps to encode once the device addresses are fixed: node, 0 = X / 1 = V^T
+    // tensor maps to encode once the device addresses are fixed: node, 0 = X / 1 = V^T hi / 2 = lo
     std::vector<std::pair<int, int>> tmap_jobs;
     int max_log2m = 0;
     // per height, per kind: [first, count) into the item array

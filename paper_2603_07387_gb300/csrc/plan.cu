@@ -91,9 +91,11 @@ tnsk_status finalize_plan(BatchPlan& P, unsigned char* base, std::string& err) {
     const float* ws = (const float*)(base + P.m2.ws_off);
     for (size_t i = 0; i < P.m2.tmap_jobs.size(); ++i) {
         const M2Node& nd = nodes[P.m2.tmap_jobs[i].first];
-        const bool is_v = P.m2.tmap_jobs[i].second == 1;
-        const bool ok = is_v ? encode_rowmajor(maps + i * 128, ws + nd.v_off, nets[nd.net].R, nd.cols, 64)
-                             : encode_rowmajor(maps + i * 128, nd.data, nd.npar, nd.cols, 128);
+        const int what = P.m2.tmap_jobs[i].second;  // 0: X, 1: V^T hi, 2: V^T lo
+        const int64_t R = nets[nd.net].R;
+        const bool ok = what == 0 ? encode_rowmajor(maps + i * 128, nd.data, nd.npar, nd.cols, 128)
+                                  : encode_rowmajor(maps + i * 128, ws + nd.v_off + (what - 1) * R * nd.cols, R,
+                                                    nd.cols, 64);
         if (!ok) {
             err = "tensor-map encoding failed";
             return TNSK_ERR_CUDA;
@@ -664,7 +666,8 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
             }
             if (nd.c >= 1) {
                 fx.v = ws_v;
-                ws_v = up16(ws_v + nd.cols * (int64_t)R);
+                const int64_t parts = (!fp64 && !nd.is_root) ? 2 : 1;  // TF32 hi / lo for the tensor cores
+                ws_v = up16(ws_v + parts * nd.cols * (int64_t)R);
             }
             fx.w = -1;
             if (!fp64 && nd.c >= 1 && !nd.is_root) {  // tensor-core product W^T
@@ -706,8 +709,9 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 if (stream) {
                     m2nodes.back().tm_x = (int32_t)P.m2.tmap_jobs.size();
                     P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 0});
-                    m2nodes.back().tm_v = (int32_t)P.m2.tmap_jobs.size();
+                    m2nodes.back().tm_v = (int32_t)P.m2.tmap_jobs.size();  // hi, then lo at tm_v + 1
                     P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 1});
+                    P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 2});
                 }
                 for (int64_t rt = 0; rt * tile < nd.npar; ++rt)
                     for (int64_t ct = 0; ct * 64 < R; ++ct)
