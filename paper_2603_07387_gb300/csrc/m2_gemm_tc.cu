@@ -36,12 +36,6 @@ constexpr uint32_t kWaitLimit = 1u << 22;                // bounded mbarrier wai
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
 // Byte offset of (row, k) in a K-major no-swizzle operand tile (k < 32).
 __device__ __forceinline__ int kmajor_offset(int row, int k) {
     return (row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4;
@@ -73,9 +67,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 }
 
 __device__ __forceinline__ void store_split(unsigned char* hi, unsigned char* lo, int off, float4 v) {
-    uint32_t h0 = tf32_rna(v.x), h1 = tf32_rna(v.y), h2 = tf32_rna(v.z), h3 = tf32_rna(v.w);
-    uint32_t l0 = tf32_rna(v.x - __uint_as_float(h0)), l1 = tf32_rna(v.y - __uint_as_float(h1));
-    uint32_t l2 = tf32_rna(v.z - __uint_as_float(h2)), l3 = tf32_rna(v.w - __uint_as_float(h3));
+    uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
+    tf32_split(v.x, h0, l0);
+    tf32_split(v.y, h1, l1);
+    tf32_split(v.z, h2, l2);
+    tf32_split(v.w, h3, l3);
     *reinterpret_cast<uint4*>(hi + off) = make_uint4(h0, h1, h2, h3);
     *reinterpret_cast<uint4*>(lo + off) = make_uint4(l0, l1, l2, l3);
 }
@@ -278,7 +274,8 @@ __global__ void __launch_bounds__(128, 2) m2_gemm_tc_kernel(const M2Node* __rest
 // K-major layout, with zero fill outside the matrices. X's hi / lo parts go to
 // tensor memory, so the MMA reads A from TMEM and only B from shared memory:
 //   warp 0     producer: three cp.async.bulk.tensor loads per chunk into a
-//              6-deep ring (raw_full counts bytes)
+//              3-deep ring (raw_full counts bytes); two CTAs share an SM, so
+//              one's prologue and epilogue overlap the other's streaming
 //   warps 1-4  converters: one row of X per thread (its TMEM lane), raw FP32 ->
 //              hi / lo TF32 stored with tcgen05.st; then the epilogue
 //   warp 5     tensor memory allocation and MMA issue; tcgen05.commit frees the
@@ -288,7 +285,7 @@ __global__ void __launch_bounds__(128, 2) m2_gemm_tc_kernel(const M2Node* __rest
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int kRawStages = 6;
+constexpr int kRawStages = 3;  // two CTAs per SM: 2 x 97 KiB of shared memory
 constexpr int kTmStages = 2;
 constexpr int kRawX = kTM * 128;   // 128 rows x 128 B
 constexpr int kRawV = kTN * 128;   // 64 rows x 128 B (one of hi / lo)
@@ -327,7 +324,7 @@ __device__ __forceinline__ void tmem_store32(uint32_t taddr, const uint32_t (&r)
 
 }  // namespace
 
-__global__ void __launch_bounds__(192, 1) m2_gemm_tc_stream_kernel(const M2Node* __restrict__ nodes,
+__global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node* __restrict__ nodes,
                                                                    const M2Net* __restrict__ nets,
                                                                    const M2Item* __restrict__ items,
                                                                    float* __restrict__ ws,
@@ -417,10 +414,7 @@ __global__ void __launch_bounds__(192, 1) m2_gemm_tc_stream_kernel(const M2Node*
                 const float4 v = *reinterpret_cast<const float4*>(rowp + ((g ^ (r & 7)) << 4));
                 const float x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    hi[4 * g + q] = tf32_rna(x[q]);
-                    lo[4 * g + q] = tf32_rna(x[q] - __uint_as_float(hi[4 * g + q]));
-                }
+                for (int q = 0; q < 4; ++q) tf32_split(x[q], hi[4 * g + q], lo[4 * g + q]);
             }
             const uint32_t col = (uint32_t)(kTN + 64 * t);
             tmem_store32(tmem + lane_base + col, hi);

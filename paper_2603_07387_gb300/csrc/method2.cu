@@ -228,8 +228,7 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
         if (sizeof(T) == 4 && !nd.is_root) {
             // operand of the tensor-core product: TF32 hi part, then its lo part R*cols later
             uint32_t hi, lo;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"((float)v));
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"((float)v - __uint_as_float(hi)));
+            tf32_split((float)v, hi, lo);
             ws[nd.v_off + (int64_t)r * nd.cols + col] = (T)__uint_as_float(hi);
             ws[nd.v_off + ((int64_t)R + r) * nd.cols + col] = (T)__uint_as_float(lo);
         } else {

@@ -25,6 +25,17 @@
 
 namespace tnsk {
 
+// Splits an FP32 value into two TF32 values with x = hi + lo up to the rounding
+// of lo: each part rounded to nearest, ties away from zero, by adding half a
+// TF32 unit in the last place to the bit pattern and clearing the 13 low bits
+// (a carry into the exponent is the correct rounding up). Integer operations
+// only, so the split of a streamed operand does not queue on the conversion
+// unit. x - hi is exact in FP32 (hi is within a factor of two of x).
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+    hi = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+    lo = (__float_as_uint(x - __uint_as_float(hi)) + 0x1000u) & 0xFFFFE000u;
+}
+
 #define TNSK_MAX_SLOTS 16  // slots of a recursive sketch: children padded to a power of two
 
 struct M2Node {

@@ -748,8 +748,10 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
         nd.src_off = fx.src_kind == 1 ? ws_x + ws_w + fx.src : (fx.src_kind == 2 ? fx.src : -1);
         for (int j = 0; j < nd.c; ++j) nd.child_x[j] = fx.child_x[j];
     }
-    // ---- split K of the tensor-core GEMM tiles: aim for >= 4 CTAs per SM per height,
-    // with >= 4 chunks of 32 columns per split
+    // ---- split K of the tensor-core GEMM tiles: both kernels run 2 CTAs per SM, so a
+    // height's tiles x splits CTAs run in waves of 304; pick the split that minimises
+    // waves x (chunks per split + a fixed cost of about 6 chunks per CTA), with at least
+    // 4 chunks of 32 columns per split
     if (!fp64 && !pend.empty()) {
         std::vector<int64_t> tiles(P.m2.max_height + 1, 0);
         for (const PendingItem& q : pend)
@@ -762,10 +764,13 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 continue;
             }
             const int64_t chunks = (m2nodes[q.it.node].cols + 31) / 32;
-            // streaming kernel: 1 CTA per SM, aim for 2 waves; general kernel: 2 per SM, 2 waves
-            const int64_t want = q.kind == M2_GEMM_STREAM ? 2 * 152 : 4 * 152;
-            int64_t split = (want + tiles[q.h] - 1) / tiles[q.h];
-            split = std::max<int64_t>(1, std::min<int64_t>(split, chunks / 4));
+            const int64_t slots = 2 * 152, fixed = 6;
+            int64_t split = 1, best = -1;
+            for (int64_t sp = 1; sp <= std::max<int64_t>(1, std::min<int64_t>(chunks / 4, 64)); ++sp) {
+                const int64_t waves = (tiles[q.h] * sp + slots - 1) / slots;
+                const int64_t cost = waves * ((chunks + sp - 1) / sp + fixed);
+                if (best < 0 || cost < best) best = cost, split = sp;
+            }
             for (int64_t sidx = 0; sidx < split; ++sidx) {
                 PendingItem z = q;
                 z.it.begin = split;  // number of K splits
