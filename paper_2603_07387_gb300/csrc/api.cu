@@ -284,13 +284,9 @@ static tnsk_status launch_plan(tnsk_ctx* ctx, const BatchPlan& plan, unsigned ch
         pf.end(s);
         if (!sketch_out) {
             pf.begin(TNSK_K_M1_SPECTRUM, s);
-            TNSK_CUDA(launch_m1_spectrum((const M1Tensor*)(base + plan.m1.tens_off),
-                                         (const M1Net*)(base + plan.m1.nets_off),
-                                         (const OpenMode*)(base + plan.m1.opens_off),
-                                         (const int2*)(base + plan.m1.items_off), plan.m1.n_items, xs,
-                                         fp64 ? (const void* const*)ctx->d_tw64 : (const void* const*)ctx->d_tw32,
-                                         base + plan.m1.spec_off, (int*)(base + plan.m1.sexp_off),
-                                         (double*)(base + plan.yrep_off), fp64, plan.m1.max_log2m, s));
+            TNSK_CUDA(launch_m1_spectra(plan, base, xs,
+                                        fp64 ? (const void* const*)ctx->d_tw64 : (const void* const*)ctx->d_tw32,
+                                        fp64, s));
             pf.end(s);
         }
     }

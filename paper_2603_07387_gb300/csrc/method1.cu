@@ -13,6 +13,7 @@
 
 #include "fft.cuh"
 #include "kernels.cuh"
+#include "plan.cuh"
 
 namespace tnsk {
 
@@ -399,6 +400,21 @@ cudaError_t launch_m1_spectrum(const M1Tensor* d_tens, const M1Net* d_nets, cons
                                      (const Cplx<float>* const*)d_tws, (Cplx<float>*)d_spec, d_sexp, d_yrep, gmax);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_m1_spectra(const BatchPlan& plan, unsigned char* base, const void* xs, const void* const* tws,
+                              bool fp64, cudaStream_t s) {
+    const M1Tensor* tens = (const M1Tensor*)(base + plan.m1.tens_off);
+    const M1Net* nets = (const M1Net*)(base + plan.m1.nets_off);
+    const int2* items = (const int2*)(base + plan.m1.items_off);
+    double* yrep = (double*)(base + plan.yrep_off);
+    cudaError_t e = launch_m1_spectrum(tens, nets, (const OpenMode*)(base + plan.m1.opens_off), items,
+                                       plan.m1.n_items, xs, tws, base + plan.m1.spec_off,
+                                       (int*)(base + plan.m1.sexp_off), yrep, fp64, plan.m1.max_log2m, s);
+    for (int sl = 0; sl < M1Plan::kWarpSlots && e == cudaSuccess; ++sl)
+        e = launch_m1_spectrum_warp(tens, nets, items + plan.m1.warp_first[sl], plan.m1.warp_count[sl], xs, tws, yrep,
+                                    6 + sl, s);
+    return e;
 }
 
 cudaError_t launch_combine(const CombineItem* d_items, int n_items, const double* d_yrep, cudaStream_t s) {

@@ -348,6 +348,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     std::vector<M1Work> m1w;
     std::vector<OpenMode> opens;
     std::vector<int2> m1items;
+    std::vector<int2> m1warp[M1Plan::kWarpSlots];
     std::vector<CombineItem> comb;
     std::vector<M2Node> m2nodes;
     std::vector<M2Net> m2n;
@@ -507,10 +508,15 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                         m1w.push_back(w);
                     }
             }
-            if (!sketch_only && I.O > 0)
-                for (int r = 0; r < R; ++r) m1items.push_back(make_int2((int)m1n.size(), r));
+            if (!sketch_only && I.O > 0) {
+                // FP32, no open legs, 2^6 <= m <= 2^10: the warp-per-item spectrum kernel
+                const bool warp_path = !fp64 && I.O == 1 && nb.n_ot == 0 && I.log2m >= 6 && I.log2m <= 10;
+                std::vector<int2>& dst = warp_path ? m1warp[I.log2m - 6] : m1items;
+                for (int r = 0; r < R; ++r) dst.push_back(make_int2((int)m1n.size(), r));
+            }
             if (sketch_only) P.sketch_user_bytes = (size_t)R * xacc * acc;
             xs_n += sketch_only ? 0 : (int64_t)R * xacc;
+            xs_n = (xs_n + 3) & ~(int64_t)3;  // every network's sketches start 16-byte aligned
             spec_n += (int64_t)R * sacc;
             sexp_n += (int64_t)R * eacc;
             for (int64_t o = 0; o < I.O; ++o) {
@@ -814,6 +820,12 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     // ---- stage descriptors
     std::vector<unsigned char>& H = P.host_desc;
     size_t o_reqs = stage(H, reqs), o_m1t = stage(H, m1t), o_m1n = stage(H, m1n), o_m1w = stage(H, m1w);
+    const int n_block_items = (int)m1items.size();
+    for (int sl = 0; sl < M1Plan::kWarpSlots; ++sl) {
+        P.m1.warp_first[sl] = (int)m1items.size();
+        P.m1.warp_count[sl] = (int)m1warp[sl].size();
+        m1items.insert(m1items.end(), m1warp[sl].begin(), m1warp[sl].end());
+    }
     size_t o_open = stage(H, opens), o_items = stage(H, m1items), o_comb = stage(H, comb);
     size_t o_m2nodes = stage(H, m2nodes), o_m2n = stage(H, m2n), o_m2items = stage(H, m2items);
     std::vector<unsigned char> tmap_space(P.m2.tmap_jobs.size() * 128, 0);
@@ -843,7 +855,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     P.m1.sexp_off = P.arena.take((size_t)sexp_n * sizeof(int));
     P.m1.n_nets = (int)m1n.size();
     P.m1.n_work = (int)m1w.size();
-    P.m1.n_items = (int)m1items.size();
+    P.m1.n_items = n_block_items;
     P.m1.scatter_smem = scatter_smem;
     P.m1.max_order = m1_max_order;
     P.m1.max_log2m = max_log2m1;

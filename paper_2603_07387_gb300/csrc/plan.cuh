@@ -45,6 +45,11 @@ struct M1Plan {
     size_t scatter_smem = 0;
     int max_order = 0;  // largest tensor order among method-1 tensors
     int max_log2m = 0;
+    // items of the warp-per-item spectrum kernel, by log2 m = 6 + slot, stored after
+    // the n_items items of the block kernel
+    static constexpr int kWarpSlots = 5;
+    int warp_first[kWarpSlots] = {0, 0, 0, 0, 0};
+    int warp_count[kWarpSlots] = {0, 0, 0, 0, 0};
 };
 
 struct BatchPlan {
@@ -65,6 +70,10 @@ struct BatchPlan {
     M1Plan m1;
     M2Plan m2;
 };
+
+// Launches the spectrum kernels of every method-1 item of the plan (rows a3 + a4).
+cudaError_t launch_m1_spectra(const BatchPlan& plan, unsigned char* base, const void* xs, const void* const* tws,
+                              bool fp64, cudaStream_t s);
 
 tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& info, std::string& why);
 // True when the driver's tensor-map encoder is available (streaming tensor-core path).

@@ -134,11 +134,7 @@ extern "C" tnsk_status tnsk_estimate_static(const tnsk_network* net, const tnsk_
                           (const M1Work*)(base + plan.m1.work_off), plan.m1.n_work,
                           (const uint32_t*)(base + plan.tabs_off), base + plan.m1.xs_off, false,
                           plan.m1.scatter_smem, plan.m1.max_order, s) != cudaSuccess ||
-        launch_m1_spectrum((const M1Tensor*)(base + plan.m1.tens_off), (const M1Net*)(base + plan.m1.nets_off),
-                           (const OpenMode*)(base + plan.m1.opens_off), (const int2*)(base + plan.m1.items_off),
-                           plan.m1.n_items, base + plan.m1.xs_off, tws, base + plan.m1.spec_off,
-                           (int*)(base + plan.m1.sexp_off), (double*)(base + plan.yrep_off), false,
-                           plan.m1.max_log2m, s) != cudaSuccess ||
+        launch_m1_spectra(plan, base, base + plan.m1.xs_off, (const void* const*)tws, false, s) != cudaSuccess ||
         launch_combine((const CombineItem*)(base + plan.comb_off), plan.n_comb, (const double*)(base + plan.yrep_off),
                        s) != cudaSuccess) {
         cudaGetLastError();

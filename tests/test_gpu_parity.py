@@ -122,6 +122,51 @@ def test_method1_open_legs_many_shapes(ctx):
         assert_parity(per, y, s, TOL[p.prec], "random open")
 
 
+def _closed_specs():
+    rng = np.random.default_rng(31)
+    specs = [W.triangle(7, seed=2), W.grid(3, 3, 3, seed=5),
+             W.NetSpec([rng.standard_normal((3, 2, 3)), rng.standard_normal(2)], [(0, 2), (1, 3)], [], "selftrace")]
+    specs += [W.random_network(rng, p_range=(4, 9), dim_range=(2, 6), max_open=0) for _ in range(3)]
+    return specs
+
+
+@pytest.mark.parametrize("m", [64, 128, 256, 512, 1024])
+def test_method1_warp_spectrum_every_size(ctx, m):
+    """FP32 networks without open legs and 64 <= m <= 1024 take the warp-per-(network, rep)
+    register FFT; every lane count per bin (J = m / 64) is covered."""
+    for spec in _closed_specs():
+        p = tnsk.Params(m=m, reps=5, seed=7 + m, prec=tnsk.PREC_FP32)
+        out, per = gpu_estimate(ctx, spec, p, torch.float32)
+        y, s = oracle_estimate(spec, p, torch.float32)
+        assert_parity(per, y, s, TOL[p.prec], f"{spec.name} m={m}")
+
+
+def test_method1_batch_mixes_spectrum_kernels(ctx):
+    """One batch with networks for the warp kernel at two sizes, the block kernel (open legs,
+    m above 1024, m below 64) and method 2, each against the oracle."""
+    rng = np.random.default_rng(33)
+    closed = _closed_specs()
+    opened = [W.random_network(rng, p_range=(4, 6), dim_range=(2, 5), open_dim_range=(2, 4)) for _ in range(2)]
+    specs = [closed[0], closed[1], opened[0], closed[3], opened[1], closed[4], closed[5], _trees()[2]]
+    ms = [64, 1024, 256, 2048, 1024, 32, 256, 128]
+    params = [tnsk.Params(m=m, reps=4 + (i % 3), seed=500 + i,
+                          method=tnsk.ACYCLIC if s.name.startswith("tree") else tnsk.GENERAL)
+              for i, (s, m) in enumerate(zip(specs, ms))]
+    nets = [gpu_network(s, torch.float32) for s in specs]
+    outs, pers, Os = [], [], []
+    for s, p in zip(specs, params):
+        dims = [d for x in s.tensors for d in np.shape(x)]
+        O = int(np.prod([dims[g] for g in s.open])) if s.open else 1
+        Os.append(O)
+        outs.append(torch.zeros(max(O, 1), dtype=torch.float64, device="cuda"))
+        pers.append(torch.zeros((p.reps, max(O, 1)), dtype=torch.float64, device="cuda"))
+    ctx.estimate_batch(nets, params, outs, pers)
+    ctx.sync()
+    for s, p, pr, O in zip(specs, params, pers, Os):
+        y, sc = oracle_estimate(s, p, torch.float32)
+        assert_parity(pr.cpu().numpy()[:, :O], y, sc, TOL[p.prec], f"{s.name} m={p.m}")
+
+
 # ---------------------------------------------------------------- a5-a8 method 2
 def _trees():
     rng = np.random.default_rng(5)
