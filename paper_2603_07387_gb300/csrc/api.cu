@@ -269,8 +269,7 @@ static tnsk_status launch_plan(tnsk_ctx* ctx, const BatchPlan& plan, unsigned ch
     Profiler& pf = ctx->prof;
     if (plan.n_reqs) {
         pf.begin(TNSK_K_TABLES, s);
-        TNSK_CUDA(launch_draw_tables((const TabReq*)(base + plan.reqs_off), plan.n_reqs, plan.n_table_words,
-                                     plan.n_coef_rows, (HashCoef*)(base + plan.coef_off),
+        TNSK_CUDA(launch_draw_tables((const TabReq*)(base + plan.reqs_off), plan.n_reqs, plan.n_table_rows,
                                      (uint32_t*)(base + plan.tabs_off), s));
         pf.end(s);
     }

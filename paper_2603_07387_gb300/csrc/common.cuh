@@ -58,6 +58,25 @@ __device__ __forceinline__ HashCoef hash_coef(uint64_t seed, uint64_t rep, uint6
     return h;
 }
 
+// (a * x) mod P for a < P and x < 2^32: with a = ah 2^32 + al,
+// a x = ah x 2^32 + al x, and ah x 2^32 = (ah x mod 2^29) 2^32 + (ah x >> 29) 2^61
+// with 2^61 = 1 (mod P); two 32 x 32 -> 64-bit products instead of a 64 x 64 one.
+__device__ __forceinline__ uint64_t mulmod61_u32(uint64_t a, uint32_t x) {
+    const uint64_t p1 = (uint64_t)(uint32_t)(a >> 32) * x;  // < 2^61
+    const uint64_t p0 = (uint64_t)(uint32_t)a * x;          // < 2^64
+    return fold61((p0 & kP61) + (p0 >> 61) + ((p1 & 0x1FFFFFFFull) << 32) + (p1 >> 29));
+}
+
+// hash_packed for an index below 2^32 (x = i < P needs no reduction).
+__device__ __forceinline__ uint32_t hash_packed_u32(const HashCoef& h, uint32_t x, uint32_t mask) {
+    const uint64_t b = fold61(mulmod61_u32(h.a1, x) + h.a0);
+    uint64_t g = h.c3;
+    g = fold61(mulmod61_u32(g, x) + h.c2);
+    g = fold61(mulmod61_u32(g, x) + h.c1);
+    g = fold61(mulmod61_u32(g, x) + h.c0);
+    return (uint32_t)(b & mask) | ((uint32_t)(g & 1) << TNSK_SIGN_SHIFT);
+}
+
 // Packed table word for index i: bin | (negative sign) << 24. m is a power of two.
 __device__ __forceinline__ uint32_t hash_packed(const HashCoef& h, uint64_t i, uint32_t mask) {
     uint64_t x = fold61(i);
@@ -87,8 +106,7 @@ struct TabReq {
     int64_t n;          // domain size
     int64_t out_off;    // packed-table offset of rep 0
     int64_t rep_stride; // distance between consecutive reps
-    int64_t first;      // first flat entry of this request (prefix over R*n)
-    int64_t crow;       // first coefficient row of this request (prefix over R)
+    int64_t crow;       // first table row of this request (prefix over R)
     int32_t R;
     uint32_t mask;      // m - 1
 };

@@ -56,8 +56,8 @@ struct CombineItem {  // one output entry of one network
     double* per_rep;  // optional [R][O]
 };
 
-cudaError_t launch_draw_tables(const TabReq* d_reqs, int nreq, int64_t total, int64_t rows, HashCoef* d_coef,
-                               uint32_t* d_out, cudaStream_t s);
+// One table row per (request, rep); rows = sum of the requests' R (crow prefix).
+cudaError_t launch_draw_tables(const TabReq* d_reqs, int nreq, int64_t rows, uint32_t* d_out, cudaStream_t s);
 cudaError_t launch_count_sketch(uint64_t seed, uint64_t rep, uint64_t tid, int64_t n, int64_t m, int32_t* bins,
                                 int8_t* signs, cudaStream_t s);
 cudaError_t launch_m1_scatter(const M1Tensor* d_tens, const M1Net* d_nets, const M1Work* d_work, int n_work,

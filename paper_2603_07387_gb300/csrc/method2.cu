@@ -51,19 +51,16 @@ template <typename T>
 __global__ void __launch_bounds__(256) m2_leaf_kernel(const M2Node* __restrict__ nodes, const M2Net* __restrict__ nets,
                                                       const M2Item* __restrict__ items,
                                                       const uint32_t* __restrict__ tabs, T* __restrict__ ws) {
-    const M2Item it = items[blockIdx.x];
+    const M2Item it = items[blockIdx.x];  // entries [begin, end), reps [a, a + b)
     const M2Node& nd = nodes[it.node];
     const M2Net& N = nets[nd.net];
-    const int R = N.R;
     const uint32_t mask = (uint32_t)(N.m - 1);
-    const uint32_t cnt = (uint32_t)((it.end - it.begin) * R);  // <= 2048 * 65536
-    for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) {
-        const uint32_t qi = q / (uint32_t)R;
-        const int64_t i = it.begin + qi;
-        const int r = (int)(q - qi * (uint32_t)R);
+    for (int64_t i = it.begin + threadIdx.x; i < it.end; i += blockDim.x) {
         const T v = load_as<T>(nd.data, nd.dtype, i);
-        const uint32_t w = tabs[N.tab_off + (int64_t)r * N.Lrep + nd.ptab + i];
-        atomicAdd(&ws[nd.x_off + (int64_t)r * N.m + (w & mask)], (w & TNSK_SIGN_BIT) ? -v : v);
+        for (int r = it.a; r < it.a + it.b; ++r) {
+            const uint32_t w = tabs[N.tab_off + (int64_t)r * N.Lrep + nd.ptab + i];
+            atomicAdd(&ws[nd.x_off + (int64_t)r * N.m + (w & mask)], (w & TNSK_SIGN_BIT) ? -v : v);
+        }
     }
 }
 
@@ -193,7 +190,7 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
     const uint32_t len = (uint32_t)(it.end - it.begin);  // <= 128
     const uint32_t cnt = len * (uint32_t)R;
     for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) {
-        const int r = (int)(q / len);
+        const int r = (int)(len == 128 ? q >> 7 : q / len);
         const int64_t col = it.begin + (q - (uint32_t)r * len);
         const uint32_t* tabr = tabs + N.tab_off + (int64_t)r * N.Lrep;
         uint32_t b[QTMAX];
@@ -380,13 +377,12 @@ template <typename T>
 __global__ void __launch_bounds__(256) m2_root_kernel(const M2Node* __restrict__ nodes, const M2Net* __restrict__ nets,
                                                       const M2Item* __restrict__ items, const T* __restrict__ ws,
                                                       double* __restrict__ yrep) {
-    const M2Item it = items[blockIdx.x];
+    const M2Item it = items[blockIdx.x];  // columns [begin, end), reps [a, a + b)
     const M2Node& nd = nodes[it.node];
     const M2Net& N = nets[nd.net];
-    const int R = N.R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const T* V = nd.v_off >= 0 ? ws + nd.v_off : nullptr;
-    for (int r = warp; r < R; r += nw) {
+    for (int r = it.a + warp; r < it.a + it.b; r += nw) {
         double acc = 0;
         for (int64_t col = it.begin + lane; col < it.end; col += 32) {
             const T x = load_as<T>(nd.data, nd.dtype, col);

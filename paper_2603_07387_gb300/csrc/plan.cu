@@ -540,8 +540,9 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
         nb.log2m = I.log2m;
         nb.R = R;
         nb.tab_off = tab_words;
-        // reps per row-scatter CTA: bins of up to 48 KiB in shared memory
-        const int scatter_reps = (int)std::max<int64_t>(1, std::min<int64_t>(16, (48 * 1024) / (m * 4)));
+        // reps per row-scatter CTA: at most 4 (enough CTAs to fill the GPU), bins of up
+        // to 48 KiB in shared memory
+        const int scatter_reps = (int)std::max<int64_t>(1, std::min<int64_t>(4, (48 * 1024) / (m * 4)));
         P.m2.scatter_smem = std::max(P.m2.scatter_smem, (size_t)scatter_reps * (size_t)m * sizeof(float));
         nb.y_off = yrep_n;
         max_log2m2 = std::max(max_log2m2, I.log2m);
@@ -685,11 +686,12 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
             // work items at this node's height
             const int h = I.height[k];
             const int node_idx = (int)(node0 + k);
-            if (nd.c == 0 && !nd.is_root) {
-                for (int64_t b0 = 0; b0 < nd.numel; b0 += 2048) {
-                    M2Item it{node_idx, 0, 0, 0, b0, std::min(nd.numel, b0 + 2048)};
-                    pend.push_back({h, M2_LEAF, it});
-                }
+            if (nd.c == 0 && !nd.is_root) {  // chunks of 2048 entries x blocks of 8 reps
+                for (int64_t b0 = 0; b0 < nd.numel; b0 += 2048)
+                    for (int r0 = 0; r0 < R; r0 += 8) {
+                        M2Item it{node_idx, r0, std::min(8, R - r0), 0, b0, std::min(nd.numel, b0 + 2048)};
+                        pend.push_back({h, M2_LEAF, it});
+                    }
             }
             if (nd.qt >= 2)
                 for (int r = 0; r < R; ++r) pend.push_back({h, M2_COMPOSE, M2Item{node_idx, r, 0, 0, 0, 0}});
@@ -724,11 +726,12 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                         pend.push_back({h, stream ? M2_GEMM_STREAM : M2_GEMM,
                                         M2Item{node_idx, (int)rt, (int)ct, 0, 1, 0}});
             }
-            if (nd.is_root)
-                for (int64_t b0 = 0; b0 < std::max<int64_t>(nd.cols, 1); b0 += 4096) {
-                    M2Item it{node_idx, 0, 0, 0, b0, std::min(nd.cols, b0 + 4096)};
-                    pend.push_back({h, M2_ROOT, it});
-                }
+            if (nd.is_root)  // chunks of 4096 columns x blocks of 8 reps (one warp each)
+                for (int64_t b0 = 0; b0 < std::max<int64_t>(nd.cols, 1); b0 += 4096)
+                    for (int r0 = 0; r0 < R; r0 += 8) {
+                        M2Item it{node_idx, r0, std::min(8, R - r0), 0, b0, std::min(nd.cols, b0 + 4096)};
+                        pend.push_back({h, M2_ROOT, it});
+                    }
         }
         P.m2.max_height = std::max(P.m2.max_height, I.max_height);
         CombineItem c{};
@@ -806,16 +809,13 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     P.m2.max_log2m = max_log2m2;
 
     // ---- table request prefix offsets
-    int64_t first = 0, crow = 0;
+    int64_t crow = 0;
     for (TabReq& q : reqs) {
-        q.first = first;
         q.crow = crow;
-        first += q.n * q.R;
         crow += q.R;
     }
     P.n_reqs = (int)reqs.size();
-    P.n_table_words = first;
-    P.n_coef_rows = crow;
+    P.n_table_rows = crow;
 
     // ---- stage descriptors
     std::vector<unsigned char>& H = P.host_desc;
@@ -850,7 +850,6 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     P.zero_bytes = P.m2.ws_off + (size_t)(ws_x + ws_w) * acc - P.zero_off;
     // ---- the rest
     P.tabs_off = P.arena.take((size_t)tab_words * sizeof(uint32_t));
-    P.coef_off = P.arena.take((size_t)P.n_coef_rows * sizeof(HashCoef));
     P.m1.spec_off = P.arena.take((size_t)spec_n * 2 * acc);
     P.m1.sexp_off = P.arena.take((size_t)sexp_n * sizeof(int));
     P.m1.n_nets = (int)m1n.size();

@@ -60,10 +60,8 @@ struct BatchPlan {
     size_t sketch_user_bytes = 0;
     size_t reqs_off = 0;
     int n_reqs = 0;
-    int64_t n_table_words = 0;
-    int64_t n_coef_rows = 0;
+    int64_t n_table_rows = 0;  // (request, rep) rows
     size_t tabs_off = 0;
-    size_t coef_off = 0;
     size_t yrep_off = 0;
     size_t comb_off = 0;
     int n_comb = 0;

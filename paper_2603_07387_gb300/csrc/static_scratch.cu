@@ -127,9 +127,8 @@ extern "C" tnsk_status tnsk_estimate_static(const tnsk_network* net, const tnsk_
     // sketches and per-rep estimates accumulate: they must start at zero
     if (plan.zero_bytes && cudaMemsetAsync(base + plan.zero_off, 0, plan.zero_bytes, s) != cudaSuccess)
         return TNSK_ERR_CUDA;
-    if (launch_draw_tables((const TabReq*)(base + plan.reqs_off), plan.n_reqs, plan.n_table_words,
-                           plan.n_coef_rows, (HashCoef*)(base + plan.coef_off), (uint32_t*)(base + plan.tabs_off),
-                           s) != cudaSuccess ||
+    if (launch_draw_tables((const TabReq*)(base + plan.reqs_off), plan.n_reqs, plan.n_table_rows,
+                           (uint32_t*)(base + plan.tabs_off), s) != cudaSuccess ||
         launch_m1_scatter((const M1Tensor*)(base + plan.m1.tens_off), (const M1Net*)(base + plan.m1.nets_off),
                           (const M1Work*)(base + plan.m1.work_off), plan.m1.n_work,
                           (const uint32_t*)(base + plan.tabs_off), base + plan.m1.xs_off, false,

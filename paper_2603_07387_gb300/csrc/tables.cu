@@ -19,35 +19,21 @@ __device__ __forceinline__ int find_req(const TabReq* __restrict__ reqs, int nre
     return lo;
 }
 
-// The polynomial coefficients of every (request, rep): the SplitMix64 key chain
-// runs once per table instead of once per word.
-__global__ void table_coef_kernel(const TabReq* __restrict__ reqs, int nreq, int64_t rows, HashCoef* __restrict__ coef) {
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < rows; g += (int64_t)gridDim.x * blockDim.x) {
-        const int q = find_req(reqs, nreq, g, [](const TabReq& r) { return r.crow; });
-        const TabReq& t = reqs[q];
-        coef[g] = hash_coef(t.seed, (uint64_t)(g - t.crow), t.tid);
-    }
-}
-
-// One thread per table word.
-__global__ void draw_tables_kernel(const TabReq* __restrict__ reqs, int nreq, int64_t total,
-                                   const HashCoef* __restrict__ coef, uint32_t* __restrict__ out) {
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int qi = find_req(reqs, nreq, g, [](const TabReq& r) { return r.first; });
-        const TabReq& q = reqs[qi];
-        const uint64_t local = (uint64_t)(g - q.first);
-        uint64_t rep, i;
-        if (local < (1ull << 32) && q.n < (1ll << 32)) {
-            const uint32_t r32 = (uint32_t)local / (uint32_t)q.n;
-            rep = r32;
-            i = (uint32_t)local - r32 * (uint32_t)q.n;
-        } else {
-            rep = local / (uint64_t)q.n;
-            i = local - rep * (uint64_t)q.n;
-        }
-        const HashCoef h = coef[q.crow + rep];
-        out[q.out_off + rep * q.rep_stride + i] = hash_packed(h, (uint64_t)i, q.mask);
+// One warp per table row (request, rep): the SplitMix64 key chain and the six
+// polynomial coefficients once per row, then the lanes over the row's indices
+// (coalesced stores). Warps stride over the rows of all requests.
+__global__ void __launch_bounds__(256) draw_tables_kernel(const TabReq* __restrict__ reqs, int nreq, int64_t rows,
+                                                          uint32_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += nwarps) {
+        const TabReq& q = reqs[find_req(reqs, nreq, row, [](const TabReq& r) { return r.crow; })];
+        const uint64_t rep = (uint64_t)(row - q.crow);
+        const HashCoef h = hash_coef(q.seed, rep, q.tid);
+        uint32_t* dst = out + q.out_off + (int64_t)rep * q.rep_stride;
+        const int64_t n32 = q.n < (1ll << 32) ? q.n : (1ll << 32);
+        for (int64_t i = lane; i < n32; i += 32) dst[i] = hash_packed_u32(h, (uint32_t)i, q.mask);
+        for (int64_t i = n32 + lane; i < q.n; i += 32) dst[i] = hash_packed(h, (uint64_t)i, q.mask);
     }
 }
 
@@ -61,15 +47,11 @@ __global__ void count_sketch_kernel(uint64_t seed, uint64_t rep, uint64_t tid, i
     }
 }
 
-cudaError_t launch_draw_tables(const TabReq* d_reqs, int nreq, int64_t total, int64_t rows, HashCoef* d_coef,
-                               uint32_t* d_out, cudaStream_t s) {
-    if (total <= 0 || nreq <= 0) return cudaSuccess;
-    int64_t cblocks = (rows + 127) / 128;
-    if (cblocks > 152 * 16) cblocks = 152 * 16;
-    table_coef_kernel<<<(unsigned)cblocks, 128, 0, s>>>(d_reqs, nreq, rows, d_coef);
-    int64_t blocks = (total + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    draw_tables_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_reqs, nreq, total, d_coef, d_out);
+cudaError_t launch_draw_tables(const TabReq* d_reqs, int nreq, int64_t rows, uint32_t* d_out, cudaStream_t s) {
+    if (rows <= 0 || nreq <= 0) return cudaSuccess;
+    int64_t blocks = (rows + 7) / 8;  // 8 warps per block, one row each per pass
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    draw_tables_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_reqs, nreq, rows, d_out);
     return cudaGetLastError();
 }
 
