@@ -67,6 +67,39 @@ __device__ void block_fft_dif(Cplx<T>* z, int nb, int log2M, const Cplx<T>* __re
     (void)M;
 }
 
+// The same DIF FFT on nb arrays interleaved element by element: element i of
+// array b sits at z[i * nb + b] (nb a power of two). Consecutive threads take the
+// same butterfly of consecutive arrays, so shared-memory accesses are
+// conflict-free; this is the layout of a block of columns of a row-major matrix.
+// Natural order in, bit-reversed order out. Ends with __syncthreads().
+template <typename T>
+__device__ void block_fft_dif_interleaved(Cplx<T>* z, int log2nb, int log2M, const Cplx<T>* __restrict__ tw) {
+    if (log2M == 0) {
+        __syncthreads();
+        return;
+    }
+    const int nb = 1 << log2nb;
+    const int total = 1 << (log2nb + log2M - 1);  // butterflies per stage
+    for (int s = 0; s < log2M; ++s) {
+        const int lhalf = log2M - s - 1;
+        const int half = 1 << lhalf;
+        const int tstride = 1 << (s + 1);
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            const int b = t & (nb - 1);
+            const int u = t >> log2nb;
+            const int grp = u >> lhalf;
+            const int j = u & (half - 1);
+            const int i0 = (grp << (lhalf + 1)) + j;
+            Cplx<T>* p0 = z + ((size_t)i0 << log2nb) + b;
+            Cplx<T>* p1 = p0 + ((size_t)half << log2nb);
+            const Cplx<T> a = *p0, c = *p1;
+            *p0 = cadd(a, c);
+            *p1 = cmul(csub(a, c), tw[j * tstride]);
+        }
+        __syncthreads();
+    }
+}
+
 // Half-spectrum bin k (0..M) of the real sequence whose packed transform Z sits
 // bit-reversed in z (one array of length M).
 template <typename T>

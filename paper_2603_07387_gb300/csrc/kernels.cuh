@@ -67,6 +67,11 @@ cudaError_t launch_m1_spectrum(const M1Tensor* d_tens, const M1Net* d_nets, cons
                                const int2* d_items, int n_items, const void* d_xs, const void* const* d_tws,
                                void* d_spec, int* d_sexp, double* d_yrep, bool fp64, int max_log2m,
                                cudaStream_t s);
+// m above one CTA's shared memory, no open legs: two-pass FFT per (net, rep, sketch)
+// into d_lspec, then the product and bin sum per (net, rep, bin block)
+cudaError_t launch_m1_large(const M1Tensor* d_tens, const M1Net* d_nets, const int4* d_fft_items, int n_fft,
+                            const int4* d_prod_items, int n_prod, const void* d_xs, const void* const* d_tws,
+                            void* d_lspec, double* d_yrep, bool fp64, cudaStream_t s);
 // FP32 networks without open legs, 2^6 <= m = 2^log2m <= 2^10: one warp per item
 cudaError_t launch_m1_spectrum_warp(const M1Tensor* d_tens, const M1Net* d_nets, const int2* d_items, int n_items,
                                     const void* d_xs, const void* const* d_tws, double* d_yrep, int log2m,

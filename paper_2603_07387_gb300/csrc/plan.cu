@@ -18,7 +18,10 @@ namespace {
 constexpr int64_t kMaxNumel = (int64_t)1 << 40;
 constexpr size_t kScatterSmemBudget = 96 * 1024;
 
+// Largest m whose FFT runs inside one CTA's shared memory (block kernels, method 2's
+// composition); method 1 goes further (2^16) with the two-pass large-m kernels.
 int max_log2m_for(bool fp64) { return fp64 ? 13 : 14; }
+constexpr int kMaxLog2mLarge = 16;
 
 template <class T>
 size_t stage(std::vector<unsigned char>& buf, const std::vector<T>& v) {
@@ -123,8 +126,9 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
         return TNSK_ERR_UNSUPPORTED;
     }
     I.log2m = ilog2(prm.m);
-    if (I.log2m > max_log2m_for(fp64)) {
-        why = "sketch size m above this build's single-CTA FFT limit (2^14 FP32, 2^13 FP64)";
+    if (I.log2m > (prm.method == TNSK_GENERAL ? kMaxLog2mLarge : max_log2m_for(fp64))) {
+        why = prm.method == TNSK_GENERAL ? "sketch size m above 2^16"
+                                         : "method 2: sketch size m above the single-CTA FFT limit (2^14 FP32, 2^13 FP64)";
         return TNSK_ERR_UNSUPPORTED;
     }
     if (prm.reps < 1 || prm.reps > 65536) {
@@ -352,7 +356,8 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     std::vector<CombineItem> comb;
     std::vector<M2Node> m2nodes;
     std::vector<M2Net> m2n;
-    int64_t tab_words = 0, yrep_n = 0, xs_n = 0, spec_n = 0, sexp_n = 0;
+    int64_t tab_words = 0, yrep_n = 0, xs_n = 0, spec_n = 0, sexp_n = 0, lspec_n = 0;
+    std::vector<int4> lfft, lprod;  // large-m method 1: (net, rep, sketch), (net, rep, first bin, bins)
     int64_t ws_x = 0, ws_w = 0, ws_r = 0, ws_v = 0;  // method-2 workspace parts (elements)
     const bool tma = tensor_maps_available();
     size_t scatter_smem = 16;
@@ -508,7 +513,21 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                         m1w.push_back(w);
                     }
             }
-            if (!sketch_only && I.O > 0) {
+            const bool large = I.log2m > max_log2m_for(fp64);
+            if (large && (nb.n_ot > 0 || I.O > 1)) {
+                err = "method 1 above m = 2^14 (FP32) / 2^13 (FP64) takes networks without open legs only";
+                return TNSK_ERR_UNSUPPORTED;
+            }
+            if (!sketch_only && I.O > 0 && large) {
+                // two-pass FFT per (rep, sketch) through a global spectrum scratch
+                nb.lspec_off = lspec_n;
+                lspec_n += (int64_t)R * I.p * m;
+                for (int r = 0; r < R; ++r) {
+                    for (int k = 0; k < I.p; ++k) lfft.push_back(make_int4((int)m1n.size(), r, k, 0));
+                    for (int64_t j0 = 0; j0 < m; j0 += 4096)
+                        lprod.push_back(make_int4((int)m1n.size(), r, (int)j0, (int)std::min<int64_t>(4096, m - j0)));
+                }
+            } else if (!sketch_only && I.O > 0) {
                 // FP32, no open legs, 2^6 <= m <= 2^10: the warp-per-item spectrum kernel
                 const bool warp_path = !fp64 && I.O == 1 && nb.n_ot == 0 && I.log2m >= 6 && I.log2m <= 10;
                 std::vector<int2>& dst = warp_path ? m1warp[I.log2m - 6] : m1items;
@@ -827,6 +846,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
         m1items.insert(m1items.end(), m1warp[sl].begin(), m1warp[sl].end());
     }
     size_t o_open = stage(H, opens), o_items = stage(H, m1items), o_comb = stage(H, comb);
+    size_t o_lfft = stage(H, lfft), o_lprod = stage(H, lprod);
     size_t o_m2nodes = stage(H, m2nodes), o_m2n = stage(H, m2n), o_m2items = stage(H, m2items);
     std::vector<unsigned char> tmap_space(P.m2.tmap_jobs.size() * 128, 0);
     size_t o_tmaps = stage(H, tmap_space);
@@ -837,6 +857,10 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     P.m1.work_off = P.desc_off + o_m1w;
     P.m1.opens_off = P.desc_off + o_open;
     P.m1.items_off = P.desc_off + o_items;
+    P.m1.lfft_off = P.desc_off + o_lfft;
+    P.m1.lprod_off = P.desc_off + o_lprod;
+    P.m1.n_lfft = (int)lfft.size();
+    P.m1.n_lprod = (int)lprod.size();
     P.comb_off = P.desc_off + o_comb;
     P.m2.nodes_off = P.desc_off + o_m2nodes;
     P.m2.nets_off = P.desc_off + o_m2n;
@@ -851,6 +875,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     // ---- the rest
     P.tabs_off = P.arena.take((size_t)tab_words * sizeof(uint32_t));
     P.m1.spec_off = P.arena.take((size_t)spec_n * 2 * acc);
+    P.m1.lspec_off = P.arena.take((size_t)lspec_n * 2 * acc);
     P.m1.sexp_off = P.arena.take((size_t)sexp_n * sizeof(int));
     P.m1.n_nets = (int)m1n.size();
     P.m1.n_work = (int)m1w.size();

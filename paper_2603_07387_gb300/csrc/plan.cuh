@@ -50,6 +50,9 @@ struct M1Plan {
     static constexpr int kWarpSlots = 5;
     int warp_first[kWarpSlots] = {0, 0, 0, 0, 0};
     int warp_count[kWarpSlots] = {0, 0, 0, 0, 0};
+    // large-m items (two-pass FFT, then the product over bin blocks) and their spectra
+    size_t lfft_off = 0, lprod_off = 0, lspec_off = 0;
+    int n_lfft = 0, n_lprod = 0;
 };
 
 struct BatchPlan {

@@ -167,6 +167,36 @@ def test_method1_batch_mixes_spectrum_kernels(ctx):
         assert_parity(pr.cpu().numpy()[:, :O], y, sc, TOL[p.prec], f"{s.name} m={p.m}")
 
 
+@pytest.mark.parametrize("prec", [tnsk.PREC_FP32, tnsk.PREC_FP64])
+@pytest.mark.parametrize("m", [1 << 14, 1 << 15, 1 << 16])
+def test_method1_large_m(ctx, prec, m):
+    """m above one CTA's shared memory (2^15, 2^16; 2^14 in FP64): two-pass FFT per sketch
+    and the product over bin blocks, against the oracle."""
+    tdt = torch.float64 if prec == tnsk.PREC_FP64 else torch.float32
+    specs = [W.grid(3, 3, 4, seed=9), W.triangle(9, seed=3), _closed_specs()[3]]
+    for spec in specs:
+        p = tnsk.Params(m=m, reps=3, seed=77, prec=prec)
+        out, per = gpu_estimate(ctx, spec, p, tdt)
+        y, s = oracle_estimate(spec, p, tdt)
+        assert_parity(per, y, s, TOL[prec], f"{spec.name} m={m}")
+
+
+def test_large_m_limits(ctx):
+    spec = _small_specs()[1]  # one open leg
+    assert spec.open
+    net = gpu_network(spec, torch.float32)
+    out = torch.zeros(64, dtype=torch.float64, device="cuda")
+    with pytest.raises(tnsk.TnskError) as e:  # open legs above the single-CTA FFT
+        ctx.estimate(net, tnsk.Params(m=1 << 15, reps=2), out)
+    assert e.value.status == -3
+    with pytest.raises(tnsk.TnskError) as e:  # above 2^16
+        ctx.estimate(gpu_network(W.triangle(4), torch.float32), tnsk.Params(m=1 << 17, reps=2), out)
+    assert e.value.status == -3
+    with pytest.raises(tnsk.TnskError) as e:  # method 2 stays within one CTA
+        ctx.estimate(gpu_network(_trees()[1], torch.float32), tnsk.Params(m=1 << 15, reps=2, method=tnsk.ACYCLIC), out)
+    assert e.value.status == -3
+
+
 # ---------------------------------------------------------------- a5-a8 method 2
 def _trees():
     rng = np.random.default_rng(5)
