@@ -91,6 +91,10 @@ typedef struct {
     int32_t root;           /* method 2 root tensor; -1 = the tensor with the
                                fewest entries (lowest index on ties) */
     tnsk_precision prec;
+    int32_t rep0;           /* index of the first repetition: the call draws the hash
+                               functions of reps rep0 .. rep0 + reps - 1, so shards of
+                               one estimate (e.g. on several GPUs) can be combined;
+                               0 for a whole estimate */
 } tnsk_params;
 
 /* Create a context on `device` whose work goes to `cuda_stream` (a cudaStream_t;
@@ -132,6 +136,15 @@ tnsk_status tnsk_estimate(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_par
 tnsk_status tnsk_estimate_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
                                 double* const* outs, double* const* per_reps);
 
+/* Row a9 on its own (Theorem 1's median trick): out[o] = the median of `groups`
+ * contiguous group means of per_rep[r][o] over r < R (groups = 1: the mean; an
+ * even count takes the mean of the two middle values), all in FP64. per_rep:
+ * device double[R][O] (e.g. per-rep estimates gathered from several GPUs that
+ * each ran a block of reps via tnsk_params.rep0); out: device double[O].
+ * Errors: TNSK_ERR_INVALID when R < 1, O < 0, groups outside [1, 64] or not
+ * dividing R, or a pointer is NULL while O > 0. */
+tnsk_status tnsk_combine(tnsk_ctx* ctx, int32_t R, int64_t O, const double* per_rep, int32_t groups, double* out);
+
 /* Per-kernel timing. While enabled, every kernel launch of the ctx is bracketed
  * by CUDA events recorded on the ctx stream. tnsk_profile_read waits for the
  * stream, writes the summed device time (ms) and the launch count of each kernel
@@ -164,6 +177,10 @@ tnsk_status tnsk_profile_read(tnsk_ctx* ctx, double* ms, int64_t* launches);
 typedef struct tnsk_plan tnsk_plan;
 tnsk_status tnsk_plan_create(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
                              double* const* outs, double* const* per_reps, tnsk_plan** plan);
+/* From its second run on, a plan's launch sequence is captured once into a CUDA
+ * graph and replayed with one graph launch, when the ctx stream is not the legacy
+ * default stream and profiling is off; otherwise (or if capture fails) the
+ * kernels are launched one by one. Results are the same either way. */
 tnsk_status tnsk_plan_run(tnsk_ctx* ctx, tnsk_plan* plan);
 tnsk_status tnsk_plan_destroy(tnsk_plan* plan);
 
@@ -187,6 +204,12 @@ tnsk_status tnsk_plan_destroy(tnsk_plan* plan);
  * same array, so calls whose GPU work overlaps race; order them on one stream. */
 tnsk_status tnsk_estimate_static(const tnsk_network* net, const tnsk_params* params, double* out, double* per_rep,
                                  void* cuda_stream);
+
+/* Measurement aid (not part of the method): the rate of FP32 shared-memory
+ * atomic adds to random bins (1024 bins x 8 per CTA, 256 threads, two CTAs per
+ * SM over all SMs), the ceiling of privatised scatter-add. Runs on the ctx
+ * stream, waits for it, and writes updates per second to *updates_per_s. */
+tnsk_status tnsk_probe_shared_atomics(tnsk_ctx* ctx, double* updates_per_s);
 
 /* Wait for the ctx's stream; returns the first deferred device error, if any. */
 tnsk_status tnsk_sync(tnsk_ctx* ctx);

@@ -330,6 +330,9 @@ struct tnsk_plan {
     bool fp64 = false;
     int device = 0;
     unsigned char* dev = nullptr;  // descriptors + scratch of this plan
+    int64_t runs = 0;
+    cudaGraphExec_t graph = nullptr;  // the launch sequence, captured on the second run
+    bool no_graph = false;            // capture failed or is not possible: launch directly
 };
 
 tnsk_status tnsk_profile(tnsk_ctx* ctx, int32_t enable) {
@@ -405,6 +408,34 @@ tnsk_status tnsk_plan_run(tnsk_ctx* ctx, tnsk_plan* plan) {
     tnsk_status st = check_ctx(ctx);
     if (st != TNSK_OK) return st;
     if (ctx->device != plan->device) return fail(ctx, TNSK_ERR_INVALID, "plan made on another device");
+    cudaStream_t s = ctx->stream;
+    // the first run launches directly (and sets every kernel attribute); later runs
+    // replay one CUDA graph of the same sequence (not on the legacy stream, whose
+    // work cannot be captured, and not while per-kernel timing is on)
+    if (plan->runs++ >= 1 && !ctx->prof.on && !plan->no_graph && s != nullptr) {
+        if (!plan->graph) {
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+            tnsk_status st = TNSK_ERR_CUDA;
+            if (e == cudaSuccess) {
+                st = launch_plan(ctx, plan->plan, plan->dev, plan->fp64, nullptr);
+                e = cudaStreamEndCapture(s, &g);
+            }
+            if (e == cudaSuccess && st == TNSK_OK && g) e = cudaGraphInstantiate(&plan->graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess || st != TNSK_OK || !plan->graph) {
+                cudaGetLastError();
+                plan->graph = nullptr;
+                plan->no_graph = true;
+                ctx->last_error.clear();
+            }
+        }
+        if (plan->graph) {
+            cudaError_t e = cudaGraphLaunch(plan->graph, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+            return TNSK_OK;
+        }
+    }
     return launch_plan(ctx, plan->plan, plan->dev, plan->fp64, nullptr);
 }
 
@@ -412,8 +443,45 @@ tnsk_status tnsk_plan_destroy(tnsk_plan* plan) {
     if (!plan) return TNSK_ERR_INVALID;
     cudaSetDevice(plan->device);
     cudaDeviceSynchronize();
+    if (plan->graph) cudaGraphExecDestroy(plan->graph);
     cudaFree(plan->dev);
     delete plan;
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_combine(tnsk_ctx* ctx, int32_t R, int64_t O, const double* per_rep, int32_t groups, double* out) {
+    tnsk_status st = check_ctx(ctx);
+    if (st != TNSK_OK) return st;
+    if (R < 1 || O < 0 || groups < 1 || groups > 64 || R % groups != 0)
+        return fail(ctx, TNSK_ERR_INVALID, "combine: need R >= 1, O >= 0, groups in [1, 64] dividing R");
+    if (O == 0) return TNSK_OK;
+    if (!per_rep || !out) return fail(ctx, TNSK_ERR_INVALID, "combine: NULL buffer");
+    std::vector<CombineItem> items((size_t)O);
+    for (int64_t o = 0; o < O; ++o) items[(size_t)o] = CombineItem{0, O, o, R, groups, out, nullptr};
+    const size_t bytes = items.size() * sizeof(CombineItem);
+    st = ensure_scratch(ctx, bytes);
+    if (st != TNSK_OK) return st;
+    // pageable host staging: the copy has read `items` when it returns
+    TNSK_CUDA(cudaMemcpyAsync(ctx->scratch, items.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->prof.begin(TNSK_K_COMBINE, ctx->stream);
+    TNSK_CUDA(launch_combine((const CombineItem*)ctx->scratch, (int)O, per_rep, ctx->stream));
+    ctx->prof.end(ctx->stream);
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_probe_shared_atomics(tnsk_ctx* ctx, double* updates_per_s) {
+    if (!updates_per_s) return TNSK_ERR_INVALID;
+    tnsk_status st = check_ctx(ctx);
+    if (st != TNSK_OK) return st;
+    float* sink = nullptr;
+    if (cudaMalloc((void**)&sink, sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, TNSK_ERR_OOM, "probe allocation failed");
+    }
+    cudaError_t e = run_probe_shared_atomics(sink, ctx->stream, updates_per_s);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(sink);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "shared-atomic probe");
     return TNSK_OK;
 }
 

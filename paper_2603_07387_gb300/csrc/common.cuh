@@ -107,6 +107,7 @@ struct TabReq {
     int64_t out_off;    // packed-table offset of rep 0
     int64_t rep_stride; // distance between consecutive reps
     int64_t crow;       // first table row of this request (prefix over R)
+    int64_t rep_base;   // repetition index of the request's first row (tnsk_params.rep0)
     int32_t R;
     uint32_t mask;      // m - 1
 };

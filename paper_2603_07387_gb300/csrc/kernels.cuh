@@ -77,5 +77,7 @@ cudaError_t launch_m1_spectrum_warp(const M1Tensor* d_tens, const M1Net* d_nets,
                                     const void* d_xs, const void* const* d_tws, double* d_yrep, int log2m,
                                     cudaStream_t s);
 cudaError_t launch_combine(const CombineItem* d_items, int n_items, const double* d_yrep, cudaStream_t s);
+// measurement aid: random-bin FP32 shared-memory atomic adds per second (waits for s)
+cudaError_t run_probe_shared_atomics(float* sink, cudaStream_t s, double* updates_per_s);
 
 }  // namespace tnsk

@@ -135,6 +135,10 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
         why = "reps must be in [1, 65536]";
         return TNSK_ERR_INVALID;
     }
+    if (prm.rep0 < 0) {
+        why = "rep0 must be >= 0";
+        return TNSK_ERR_INVALID;
+    }
     if (prm.groups < 1 || prm.groups > 64 || prm.reps % prm.groups != 0) {
         why = "groups must divide reps and be in [1, 64]";
         return TNSK_ERR_INVALID;
@@ -469,6 +473,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
             for (int e = 0; e < I.t; ++e) {
                 TabReq q{};
                 q.seed = pr.seed;
+                q.rep_base = pr.rep0;
                 q.tid = tid_m1_edge(e);
                 q.n = I.eoff[e + 1] - I.eoff[e];
                 q.out_off = tab_words + I.eoff[e];
@@ -585,6 +590,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
         for (int e = 0; e < I.t; ++e) {
             TabReq q{};
             q.seed = pr.seed;
+            q.rep_base = pr.rep0;
             q.tid = tid_m2_edge(e);
             q.n = I.eoff[e + 1] - I.eoff[e];
             q.out_off = tab_words + I.eoff[e];
@@ -598,6 +604,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
             for (int j = c; j < qt[k]; ++j) {
                 TabReq q{};
                 q.seed = pr.seed;
+                q.rep_base = pr.rep0;
                 q.tid = tid_m2_pad(k, j);
                 q.n = 1;
                 q.out_off = tab_words + pad_tab[k] + j;
@@ -611,6 +618,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                     for (int s = 0; s < 2; ++s) {
                         TabReq q{};
                         q.seed = pr.seed;
+                        q.rep_base = pr.rep0;
                         q.tid = tid_m2_ts(k, ilog2(l), j, s);
                         q.n = m;
                         q.out_off = tab_words + t_tab[k] + ts_offset(qt[k], l, j, s, m);

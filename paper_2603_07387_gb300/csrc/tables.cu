@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256) draw_tables_kernel(const TabReq* __restri
     for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += nwarps) {
         const TabReq& q = reqs[find_req(reqs, nreq, row, [](const TabReq& r) { return r.crow; })];
         const uint64_t rep = (uint64_t)(row - q.crow);
-        const HashCoef h = hash_coef(q.seed, rep, q.tid);
+        const HashCoef h = hash_coef(q.seed, (uint64_t)q.rep_base + rep, q.tid);
         uint32_t* dst = out + q.out_off + (int64_t)rep * q.rep_stride;
         const int64_t n32 = q.n < (1ll << 32) ? q.n : (1ll << 32);
         for (int64_t i = lane; i < n32; i += 32) dst[i] = hash_packed_u32(h, (uint32_t)i, q.mask);

@@ -48,6 +48,8 @@ SYMBOLS = (
     "tnsk_profile",
     "tnsk_profile_read",
     "tnsk_sync",
+    "tnsk_probe_shared_atomics",
+    "tnsk_combine",
     "tnsk_status_string",
     "tnsk_last_error",
 )
@@ -88,6 +90,7 @@ class _Params(ctypes.Structure):
         ("method", ctypes.c_int32),
         ("root", ctypes.c_int32),
         ("prec", ctypes.c_int32),
+        ("rep0", ctypes.c_int32),
     ]
 
 
@@ -133,6 +136,10 @@ def load_library(path: str = LIB_PATH):
     L.tnsk_profile_read.argtypes = [vp, vp, vp]
     L.tnsk_sync.restype = i32
     L.tnsk_sync.argtypes = [vp]
+    L.tnsk_combine.restype = i32
+    L.tnsk_combine.argtypes = [vp, i32, i64, vp, i32, vp]
+    L.tnsk_probe_shared_atomics.restype = i32
+    L.tnsk_probe_shared_atomics.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.tnsk_status_string.restype = ctypes.c_char_p
     L.tnsk_status_string.argtypes = [i32]
     L.tnsk_last_error.restype = ctypes.c_char_p
@@ -160,6 +167,7 @@ class Params:
     method: int = GENERAL
     root: int = -1
     prec: int = PREC_FP32
+    rep0: int = 0  # first repetition index (shards of one estimate)
 
 
 def _dtype_code(t):
@@ -206,7 +214,7 @@ class _NetHolder:
 
 def _params(p: Params) -> _Params:
     return _Params(int(p.m), int(p.reps), int(p.groups), int(p.seed) & ((1 << 64) - 1), int(p.method),
-                   int(p.root), int(p.prec))
+                   int(p.root), int(p.prec), int(p.rep0))
 
 
 def estimate_static(net: Network, params: Params, out, per_rep=None, stream=None):
@@ -325,6 +333,20 @@ class Context:
         n = (ctypes.c_int64 * len(KERNEL_KINDS))()
         self._check(self.lib.tnsk_profile_read(self.h, ms, n))
         return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def combine(self, per_rep, groups: int, out):
+        """tnsk_combine: out[o] = median of `groups` group means of per_rep[:, o] (FP64,
+        device tensors; per_rep is [R][O] contiguous, out holds O entries)."""
+        assert per_rep.is_cuda and out.is_cuda and per_rep.is_contiguous() and out.is_contiguous()
+        R = per_rep.shape[0]
+        O = per_rep.numel() // max(R, 1)
+        self._check(self.lib.tnsk_combine(self.h, R, O, per_rep.data_ptr(), groups, out.data_ptr()))
+
+    def probe_shared_atomics(self) -> float:
+        """Random-bin FP32 shared-memory atomic adds per second (a measurement aid)."""
+        r = ctypes.c_double(0.0)
+        self._check(self.lib.tnsk_probe_shared_atomics(self.h, ctypes.byref(r)))
+        return r.value
 
     def sync(self):
         self._check(self.lib.tnsk_sync(self.h))

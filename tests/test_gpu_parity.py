@@ -297,6 +297,80 @@ def test_plan_runs_match_oracle_and_pick_up_new_data(ctx):
     plan.close()
 
 
+def test_plan_graph_replay_matches_direct_runs():
+    """On a non-default stream a plan's runs from the second on replay one CUDA graph;
+    every run matches the oracle and picks up new input values."""
+    stream = torch.cuda.Stream()
+    c = tnsk.Context(0, stream.cuda_stream)
+    rng = np.random.default_rng(44)
+    specs = [_closed_specs()[1], W.random_network(rng, p_range=(4, 6), dim_range=(2, 5), open_dim_range=(2, 3)),
+             _trees()[3]]
+    params = [tnsk.Params(m=m, reps=4, seed=90 + i, method=tnsk.ACYCLIC if s.name.startswith("tree") else tnsk.GENERAL)
+              for i, (s, m) in enumerate(zip(specs, [256, 128, 64]))]
+    with torch.cuda.stream(stream):
+        nets = [gpu_network(s, torch.float32) for s in specs]
+        Os = []
+        for s in specs:
+            dims = [d for x in s.tensors for d in np.shape(x)]
+            Os.append(int(np.prod([dims[g] for g in s.open])) if s.open else 1)
+        outs = [torch.zeros(max(O, 1), dtype=torch.float64, device="cuda") for O in Os]
+        pers = [torch.zeros((p.reps, max(O, 1)), dtype=torch.float64, device="cuda") for p, O in zip(params, Os)]
+    stream.synchronize()
+    plan = c.plan(nets, params, outs, pers)
+    for run in range(4):
+        if run == 3:
+            for s, n in zip(specs, nets):
+                for k, t in enumerate(n.tensors):
+                    s.tensors[k] = -1.5 * s.tensors[k]
+                    t.copy_(torch.as_tensor(np.array(s.tensors[k], dtype=np.float64)).to(t.dtype))
+            torch.cuda.synchronize()
+        plan.run()
+        c.sync()
+        for s, p, pr, O in zip(specs, params, pers, Os):
+            y, sc = oracle_estimate(s, p, torch.float32)
+            assert_parity(pr.cpu().numpy()[:, :O], y, sc, TOL[p.prec], f"graph run {run} {s.name}")
+    plan.close()
+    c.close()
+
+
+def test_rep0_blocks_match_the_whole_estimate(ctx):
+    """tnsk_params.rep0: a call for reps [3, 7) gives reps 3..6 of the whole estimate."""
+    for spec, method in [(_closed_specs()[1], tnsk.GENERAL), (_trees()[2], tnsk.ACYCLIC)]:
+        whole = tnsk.Params(m=128, reps=8, seed=5, method=method)
+        _, per_all = gpu_estimate(ctx, spec, whole, torch.float32)
+        part = tnsk.Params(m=128, reps=4, seed=5, method=method, rep0=3)
+        _, per_part = gpu_estimate(ctx, spec, part, torch.float32)
+        y, sc = oracle_estimate(spec, whole, torch.float32)
+        assert_parity(per_part, y[3:7], sc[3:7], TOL[tnsk.PREC_FP32], f"rep0 {spec.name}")
+        assert_parity(per_all[3:7], y[3:7], sc[3:7], TOL[tnsk.PREC_FP32], f"whole {spec.name}")
+
+
+@pytest.mark.parametrize("R,O,groups", [(12, 3, 4), (7, 1, 7), (64, 5, 1), (10, 2, 2)])
+def test_combine_entry_point_matches_oracle(ctx, R, O, groups):
+    rng = np.random.default_rng(R * 100 + O)
+    per = rng.standard_normal((R, O))
+    per_d = torch.as_tensor(per, device="cuda")
+    out = torch.zeros(O, dtype=torch.float64, device="cuda")
+    ctx.combine(per_d, groups, out)
+    ctx.sync()
+    assert np.array_equal(out.cpu().numpy(), oracle.combine(per, groups))
+
+
+def test_estimate_sharded_on_one_rank_equals_estimate(ctx):
+    from paper_2603_07387_gb300.sharding import estimate_sharded
+
+    spec = _closed_specs()[0]
+    p = tnsk.Params(m=64, reps=6, groups=3, seed=12)
+    out, per = gpu_estimate(ctx, spec, p, torch.float32)
+    net = gpu_network(spec, torch.float32)
+    got = torch.zeros(1, dtype=torch.float64, device="cuda")
+    allreps = estimate_sharded(ctx, net, p, got)
+    ctx.sync()
+    y, sc = oracle_estimate(spec, p, torch.float32)  # FP32 atomics: summation order varies run to run
+    assert_parity(allreps.cpu().numpy(), y, sc, TOL[p.prec], "sharded")
+    assert np.array_equal(got.cpu().numpy(), oracle.combine(allreps.cpu().numpy(), 3))
+
+
 def test_degenerate_inputs(ctx):
     # scalars, an empty contracted mode, an empty open mode, a single self-contraction
     cases = [
