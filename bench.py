@@ -16,6 +16,10 @@ are done once, when the batch is planned. `value` counts
 the B method-2 estimates per second; the method-1 estimates ride along in the
 same timed step.
 
+The timed region replays the planned batch as one CUDA graph per step; the same
+steps run again right after with per-kernel CUDA events for the rooflines. A
+second, HBM-bound probe (tr(ABCD), 1 GiB) reports the method-1 scatter's GB/s.
+
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 run under torchrun; each rank estimates its own B networks (weak
 scaling, no data-path collective) and rank 0 prints the JSON line.
@@ -52,6 +56,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=64, help="tensor-train pairs per GPU per step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-hbm-probe", action="store_true")
     return ap.parse_args()
 
 
@@ -161,7 +166,10 @@ def run_ours(args, world, rank, local):
     __graft_entry__.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream(dev)
+    # a stream of our own (not the legacy default stream), so planned runs replay as
+    # one CUDA graph from the second run on
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     B = args.batch
     pairs = make_pairs(B, rank)
     # every input tensor is a 16-byte aligned view into one flat FP32 buffer, so a
@@ -206,17 +214,17 @@ def run_ours(args, world, rank, local):
     def step():
         plan.run()
 
-    for _ in range(max(args.warmup, 0)):
+    for _ in range(max(args.warmup, 2)):  # run 1 launches directly, run 2 captures the graph
         step()
     ctx.sync()
-    # ---------------- timed region (device time, CUDA events on the launching stream)
+    atomic_peak = ctx.probe_shared_atomics() if rank == 0 else None
+    # ---------------- timed region: device time, CUDA events on the launching stream
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(gpu_uuid(local))
     clocks.start()
     time.sleep(0.3)
-    ctx.profile(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -228,8 +236,6 @@ def run_ours(args, world, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    prof = ctx.profile_read()
-    ctx.profile(False)
     clk = clocks.stop()
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -237,6 +243,18 @@ def run_ours(args, world, rank, local):
         ms = float(t.item())
         torch.distributed.barrier()
     value = world * B / (ms / 1e3)
+    # ---------------- the same steps again with per-kernel CUDA events (kernels launched
+    # one by one, each bracketed by events on the ctx stream): the roofline's durations
+    ctx.profile(True)
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        step()
+    p1.record(stream)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ms_profiled = p0.elapsed_time(p1) / args.steps
 
     # ---------------- accuracy against the exact contraction (input-relative, Def. "ATNC")
     est = [float(o.item()) for o in outs]
@@ -252,29 +270,48 @@ def run_ours(args, world, rank, local):
     def rms(v):
         return float(np.sqrt(np.mean(np.square(v))))
 
-    # ---------------- roofline of the dominant kernel (largest share of device time)
+    # ---------------- rooflines: the dominant kernel (largest share of device time) first
     total_ms = sum(v[0] for v in prof.values())
-    dom = max(prof, key=lambda k: prof[k][0])
-    dom_ms, dom_n = prof[dom]
-    per_launch_ms = dom_ms / max(dom_n, 1)
-    gemm_flops = B * 6 * 2 * 1024 * 1024 * REPS  # 6 interior sites, 1024 x 1024, 64 reps
-    gemm_bytes = B * 6 * 1024 * 1024 * 4  # each interior matrix read once per 64-rep batch
-    traffic = read_traffic(dom)
-    if dom == "m2_gemm":
-        launches_per_step = dom_n / args.steps
-        achieved = gemm_flops / launches_per_step / (per_launch_ms / 1e3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 2), "peak": round(FP32_SIMT_PEAK_TFLOPS, 1),
-                "unit": "TFLOP/s", "frac": round(achieved / FP32_SIMT_PEAK_TFLOPS, 4),
-                "traffic": traffic,
-                "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived, not measured)",
-                "algorithmic_per_launch": {"flops": gemm_flops / launches_per_step,
-                                           "bytes": gemm_bytes / launches_per_step},
-                "hbm_view": {"achieved_gbs": round(gemm_bytes / launches_per_step / (per_launch_ms / 1e3) / 1e9, 1),
-                             "peak_gbs": hbm_peak()}}
-    else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": traffic}
-    roof["share"] = round(dom_ms / total_ms, 4) if total_ms else None
+    m1_entries = sum(int(np.prod(np.shape(x))) for sp in specs[0::2] for x in sp.tensors)  # ladders
+    units = {
+        # one launch per step: every entry of every ladder tensor, once per rep
+        "m1_scatter": {"bound": "alu", "per_launch": REPS * m1_entries, "unit": "Gupdates/s",
+                       "peak": atomic_peak / 1e9 if atomic_peak else None,
+                       "peak_source": "measured in this run: random-bin FP32 shared-memory atomic adds "
+                                      "(tnsk_probe_shared_atomics)",
+                       "what": "signed scatter-adds (updates) per launch = reps x entries"},
+        # one launch per height (6 per step): one 1024 x 1024 FP32 matrix per pair, read once
+        "m2_gemm": {"bound": "hbm", "per_launch": B * 1024 * 1024 * 4, "unit": "GB/s", "peak": hbm_peak(),
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
+                    "what": "bytes of X_k read per launch (each interior matrix once for all 64 reps)"},
+        # one launch per step: every ladder sketch (reps x 16 tensors x m FP32) read once
+        "m1_spectrum": {"bound": "hbm", "per_launch": B * REPS * 16 * M * 4, "unit": "GB/s", "peak": hbm_peak(),
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
+                        "what": "sketch bytes read per launch"},
+    }
+    rooflines = []
+    for kern in sorted(prof, key=lambda k: -prof[k][0]):
+        k_ms, k_n = prof[kern]
+        if k_n == 0:
+            continue
+        per_launch_ms = k_ms / k_n
+        d = units.get(kern)
+        r = {"kernel": kern, "share": round(k_ms / total_ms, 4) if total_ms else None,
+             "launch_ms": round(per_launch_ms, 5), "launches_per_step": k_n / args.steps}
+        if d:
+            scale = 1e9
+            achieved = d["per_launch"] / (per_launch_ms / 1e3) / scale
+            r.update({"bound": d["bound"], "achieved": round(achieved, 1), "peak": round(d["peak"], 1) if d["peak"] else None,
+                      "unit": d["unit"], "frac": round(achieved / d["peak"], 4) if d["peak"] else None,
+                      "algorithmic_per_launch": d["per_launch"], "what": d["what"], "peak_source": d["peak_source"]})
+        else:
+            r.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None})
+        r["traffic"] = read_traffic(kern)
+        rooflines.append(r)
+    roof = rooflines[0] if rooflines else None
+    if roof is not None:
+        roof["timing"] = ("CUDA events around each launch, over the same steps as the timed region run again "
+                          "right after it with the kernels launched one by one")
 
     # ---------------- end to end through the public API, host buffers
     # Every step: one pinned host -> device copy of all inputs (copy stream), the plan
@@ -319,7 +356,8 @@ def run_ours(args, world, rank, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(pairs[0])
-    launches = int(sum(v[1] for v in prof.values()))
+    launches = int(sum(v[1] for v in prof.values())) // max(args.steps, 1) * args.steps
+    probe = hbm_sketch_probe(ctx, dev) if (rank == 0 and not args.no_hbm_probe) else None
     for p_ in plans:
         p_.close()
     ctx.close()
@@ -340,6 +378,9 @@ def run_ours(args, world, rank, local):
                      "eps": "|estimate - tc| / prod_k ||X_k||_F (Def. ATNC); rel_err = |estimate - tc| / |tc|; "
                             "RMS over the step's networks"},
         "roofline": roof,
+        "roofline_others": rooflines[1:4],
+        "ms_per_step_profiled": round(ms_profiled, 4),
+        "hbm_sketch_probe": probe,
         "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
         "gpu_launches": launches,
         "host_ms_per_call": round(host_s * 1e3 / max(args.steps, 1), 3),
@@ -381,6 +422,46 @@ def read_traffic(kernel):
         return float(kv["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+# ---------------------------------------------------------------- sketching at an HBM-bound size
+def hbm_sketch_probe(ctx, dev):
+    """Row a2 where HBM is the bound: tr(ABCD) of four 8192 x 8192 FP32 N(0,1) matrices
+    (1 GiB, generated on the device) by method 1 at m = 4096. The scatter reads every
+    entry once per batch of reps; its algorithmic bytes per launch (1 GiB) over the
+    launch's CUDA-event duration, against the measured copy bandwidth, for calls of
+    1 and 8 reps."""
+    import torch
+
+    from paper_2603_07387_gb300 import tnsk
+
+    n = 8192
+    g = torch.Generator(device=dev)
+    g.manual_seed(20260307)
+    mats = [torch.randn((n, n), generator=g, device=dev, dtype=torch.float32) for _ in range(4)]
+    net = tnsk.Network(mats, [(1, 2), (3, 4), (5, 6), (7, 0)], [])
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    res = {"workload": "tr(ABCD), 4 x 8192^2 FP32 N(0,1) (1 GiB), method 1, m=4096",
+           "peak_gbs": hbm_peak(), "bytes_per_launch": 4 * n * n * 4}
+    for R in (1, 8):
+        plan = ctx.plan([net], [tnsk.Params(m=4096, reps=R, seed=0x7E57)], [out])
+        plan.run()
+        plan.run()
+        ctx.sync()
+        ctx.profile(True)
+        for _ in range(3):
+            plan.run()
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        sc_ms = prof["m1_scatter"][0] / max(prof["m1_scatter"][1], 1)
+        gbs = res["bytes_per_launch"] / (sc_ms / 1e3) / 1e9
+        res[f"reps_{R}"] = {"scatter_ms": round(sc_ms, 4), "achieved_gbs": round(gbs, 1),
+                            "frac": round(gbs / hbm_peak(), 4),
+                            "gupdates_per_s": round(R * 4 * n * n / (sc_ms / 1e3) / 1e9, 1)}
+        plan.close()
+    del mats
+    torch.cuda.empty_cache()
+    return res
 
 
 # ---------------------------------------------------------------- CPU baseline (oracle)

@@ -184,6 +184,9 @@ struct M1Work {
     int32_t nrep;
     int32_t priv;        // 0: global atomics; 1: shared-memory bins flushed by atomics;
                          // 2: shared-memory bins of a whole tensor, flushed by stores
+    int32_t gtab;        // 1: hash-table words read from global memory (large tables),
+                         // 0: staged in shared memory
+    int32_t pad_;
 };
 
 template <typename T>

@@ -10,6 +10,7 @@
 //                           open output entries per Corollary "full-to-partial-tc")
 //   a9  combine_kernel      median of group means in FP64 (Theorem 1)
 #include <algorithm>
+#include <type_traits>
 
 #include "fft.cuh"
 #include "kernels.cuh"
@@ -25,6 +26,9 @@ namespace tnsk {
 // Each thread walks entries f, f + S, f + 2S, ... (S = blockDim.x) keeping the
 // multi-index of f in registers and adding the mixed-radix digits of S with
 // carries, so no entry needs a division. MAXD bounds the tensor order.
+// Tensors whose tables are large (w.gtab) read the table words from global memory
+// instead (they stay in L2; within a warp the last mode's words are consecutive
+// and the other modes' are shared), leaving shared memory to the bins.
 template <typename AccT, int MAXD>
 __global__ void __launch_bounds__(256) m1_scatter_kernel(const M1Tensor* __restrict__ tens,
                                                          const M1Net* __restrict__ nets,
@@ -52,10 +56,13 @@ __global__ void __launch_bounds__(256) m1_scatter_kernel(const M1Tensor* __restr
     const int nrep = w.nrep;
     const int order = sT.order;
     uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem_raw);
-    AccT* s_bin = reinterpret_cast<AccT*>(smem_raw + (((size_t)nrep * TT * 4 + 15) & ~(size_t)15));
+    // bins after the staged tables (none in global-table mode): the plan sizes shared
+    // memory the same way
+    const size_t tab_bytes = w.gtab ? 0 : (((size_t)nrep * TT * 4 + 15) & ~(size_t)15);
+    AccT* s_bin = reinterpret_cast<AccT*>(smem_raw + tab_bytes);
 
     // tables of this tensor's contracted modes for the batch of reps
-    const int tab_words = nrep * TT;  // fits shared memory
+    const int tab_words = w.gtab ? 0 : nrep * TT;  // fits shared memory
     for (int q = threadIdx.x; q < tab_words; q += blockDim.x) {
         int r = q / TT;
         int loc = q - r * TT;
@@ -72,21 +79,28 @@ __global__ void __launch_bounds__(256) m1_scatter_kernel(const M1Tensor* __restr
     if (w.priv)
         for (int64_t q = threadIdx.x; q < nbins; q += blockDim.x) s_bin[q] = AccT(0);
 
-    // block-uniform per-mode data in registers (modes >= order: dim 1, not contracted)
+    // block-uniform per-mode data in registers. Slot s holds mode s - (MAXD - order): the
+    // padding slots (dim 1, not contracted) come first, so the last mode is slot MAXD - 1
     int dim[MAXD], base[MAXD], dig[MAXD], step[MAXD];
     bool ctr[MAXD];
     int64_t ostr[MAXD];
     const bool has_open = O > 1;
+    // four entries per thread and step: FP32 data, 16-byte aligned, last dim a multiple
+    // of 4 (so are the chunk bounds)
+    const bool vec4 = sT.dtype == TNSK_F32 && order >= 1 && (sT.dims[order - 1] & 3) == 0 &&
+                      ((uintptr_t)sT.data & 15) == 0 && (w.begin & 3) == 0 && (w.end & 3) == 0;
     {
-        int64_t f0 = w.begin + threadIdx.x;
-        int64_t sv = blockDim.x;
+        const int V = vec4 ? 4 : 1;
+        int64_t f0 = w.begin + (int64_t)V * threadIdx.x;
+        int64_t sv = (int64_t)V * blockDim.x;
 #pragma unroll
         for (int d = MAXD - 1; d >= 0; --d) {
-            const bool live = d < order;
-            dim[d] = live ? sT.dims[d] : 1;
-            base[d] = sbase[d < TNSK_MAX_ORDER ? d : 0];
-            ctr[d] = live && sT.tab[d] >= 0;
-            ostr[d] = live ? sT.ostride[d] : 0;
+            const int md = d - (MAXD - order);  // the tensor mode in slot d
+            const bool live = md >= 0;
+            dim[d] = live ? sT.dims[md] : 1;
+            base[d] = live ? sbase[md] : 0;
+            ctr[d] = live && sT.tab[md] >= 0;
+            ostr[d] = live ? sT.ostride[md] : 0;
             dig[d] = (int)(f0 % dim[d]);
             f0 /= dim[d];
             step[d] = (int)(sv % dim[d]);
@@ -96,36 +110,93 @@ __global__ void __launch_bounds__(256) m1_scatter_kernel(const M1Tensor* __restr
     __syncthreads();
 
     AccT* gx = xs + N.x_off + sT.xoff;  // + (rep0 + r) * N.X + o * m + b
-    for (int64_t f = w.begin + threadIdx.x; f < w.end; f += blockDim.x) {
-        const AccT v = load_as<AccT>(sT.data, sT.dtype, f);
-        int off[MAXD];
-        int64_t o = 0;
+    // global-table mode: mode d's words of rep r at gt + r * N.L + gofs[d] + index
+    const uint32_t* gt = tabs + N.tab_off + (int64_t)w.rep0 * N.L;
+    int32_t gofs[MAXD];
+    bool gcomp[MAXD];
 #pragma unroll
-        for (int d = 0; d < MAXD; ++d) {
-            off[d] = base[d] + dig[d];
-            if (has_open) o += (int64_t)dig[d] * ostr[d];
+    for (int d = 0; d < MAXD; ++d) {
+        const int md = d - (MAXD - order);
+        gofs[d] = ctr[d] ? sT.tab[md] : 0;
+        gcomp[d] = ctr[d] && sT.comp[md];
+    }
+    // one table word of mode d at index off (rep r): staged or global, complement applied
+    auto word_of = [&](auto global_tables, int r, int d, int off) -> uint32_t {
+        if (decltype(global_tables)::value) {
+            uint32_t wd = __ldg(gt + (int64_t)r * N.L + off);
+            if (gcomp[d]) wd = (((uint32_t)m - (wd & mask)) & mask) | (wd & TNSK_SIGN_BIT);
+            return wd;
         }
-        for (int r = 0; r < nrep; ++r) {
-            const uint32_t* tr = s_tab + r * TT;
-            uint32_t h = 0;
+        return s_tab[r * TT + off];
+    };
+    auto add = [&](int r, int64_t o, uint32_t h, AccT v) {
+        const AccT sv = (h & TNSK_SIGN_BIT) ? -v : v;
+        const uint32_t b = h & mask;
+        if (w.priv)
+            atomicAdd(&s_bin[((int64_t)r * O + o) * m + b], sv);
+        else
+            atomicAdd(&gx[(int64_t)(w.rep0 + r) * N.X + o * m + b], sv);
+    };
+    // entries f = begin + V * (tid + k * blockDim.x) .. + V - 1: with V = 4 the four share
+    // every digit but the last (the last mode's dim is a multiple of 4), come in one
+    // 16-byte load, and share the other modes' table words
+    auto entries = [&](auto global_tables, auto vec) {
+        constexpr bool kG = decltype(global_tables)::value;
+        constexpr int V = decltype(vec)::value;
+        constexpr int L = MAXD - 1;  // the tensor's last mode
+        for (int64_t f = w.begin + (int64_t)V * threadIdx.x; f < w.end; f += (int64_t)V * blockDim.x) {
+            AccT v[V];
+            if (V == 4) {
+                const float4 q = __ldg(reinterpret_cast<const float4*>((const float*)sT.data + f));
+                v[0] = (AccT)q.x;
+                v[V > 1 ? 1 : 0] = (AccT)q.y;
+                v[V > 2 ? 2 : 0] = (AccT)q.z;
+                v[V > 3 ? 3 : 0] = (AccT)q.w;
+            } else {
+                v[0] = load_as<AccT>(sT.data, sT.dtype, f);
+            }
+            int off[MAXD];
+            int64_t o = 0;
 #pragma unroll
-            for (int d = 0; d < MAXD; ++d)
-                if (ctr[d]) h += tr[off[d]];
-            const AccT sv = (h & TNSK_SIGN_BIT) ? -v : v;
-            const uint32_t b = h & mask;
-            if (w.priv)
-                atomicAdd(&s_bin[((int64_t)r * O + o) * m + b], sv);
-            else
-                atomicAdd(&gx[(int64_t)(w.rep0 + r) * N.X + o * m + b], sv);
-        }
-        // advance the multi-index by blockDim.x (mixed-radix add with carries)
-        int carry = 0;
+            for (int d = 0; d < MAXD; ++d) {
+                off[d] = (kG ? gofs[d] : base[d]) + dig[d];
+                if (has_open) o += (int64_t)dig[d] * ostr[d];
+            }
+            for (int r = 0; r < nrep; ++r) {
+                uint32_t h = 0;  // the modes other than the last (V = 4) or all modes (V = 1)
 #pragma unroll
-        for (int d = MAXD - 1; d >= 0; --d) {
-            int t = dig[d] + step[d] + carry;
-            carry = t >= dim[d];
-            dig[d] = carry ? t - dim[d] : t;
+                for (int d = 0; d < MAXD; ++d)
+                    if (ctr[d] && (V == 1 || d != L)) h += word_of(global_tables, r, d, off[d]);
+                if (V == 1) {
+                    add(r, o, h, v[0]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < V; ++j) {
+                        const uint32_t hj = h + (ctr[L] ? word_of(global_tables, r, L, off[L] + j) : 0u);
+                        add(r, has_open ? o + j * ostr[L] : o, hj, v[j]);
+                    }
+                }
+            }
+            // advance the multi-index by V * blockDim.x (mixed-radix add with carries)
+            int carry = 0;
+#pragma unroll
+            for (int d = MAXD - 1; d >= 0; --d) {
+                int t = dig[d] + step[d] + carry;
+                carry = t >= dim[d];
+                dig[d] = carry ? t - dim[d] : t;
+            }
         }
+    };
+    if (vec4) {
+        if (w.gtab)
+            entries(std::true_type{}, std::integral_constant<int, 4>{});
+        else
+            entries(std::false_type{}, std::integral_constant<int, 4>{});
+    } else {
+        if (w.gtab)
+            entries(std::true_type{}, std::integral_constant<int, 1>{});
+        else
+            entries(std::false_type{}, std::integral_constant<int, 1>{});
     }
     if (!w.priv) return;
     __syncthreads();

@@ -490,7 +490,9 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 int64_t TT = 0;
                 for (int d = 0; d < T.order; ++d)
                     if (T.tab[d] >= 0) TT += T.dims[d];
-                const size_t tab_b = (size_t)TT * 4;
+                // tables above 8 KiB per rep are read from global memory (L2)
+                const bool gtab = TT > 2048;
+                const size_t tab_b = gtab ? 0 : (size_t)TT * 4;
                 const size_t bin_b = (size_t)T.O * m * acc;
                 int64_t nrep_priv = (int64_t)(kScatterSmemBudget / (tab_b + bin_b + 16));
                 bool priv = nrep_priv >= 1 && T.numel * 4 >= T.O * m;
@@ -499,11 +501,9 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                     nrep = (int)std::min<int64_t>({(int64_t)R, nrep_priv, 32});
                 else
                     nrep = (int)std::min<int64_t>({(int64_t)R, std::max<int64_t>(1, (int64_t)(kScatterSmemBudget / (tab_b + 16))), 16});
-                if (!priv && tab_b > kScatterSmemBudget) {
-                    err = "tensor " + std::to_string(k) + ": hash tables exceed shared memory";
-                    return TNSK_ERR_UNSUPPORTED;
-                }
-                const int64_t CH = priv ? std::max<int64_t>(8192, 2 * T.O * m) : 8192;
+                // chunks: privatised bins are flushed once per chunk, so a chunk has at least
+                // 32x as many entries as bins (a few percent of flush per update)
+                const int64_t CH = priv ? std::max<int64_t>(8192, 32 * T.O * m) : (gtab ? 65536 : 8192);
                 size_t sm = ((size_t)nrep * tab_b + 15) / 16 * 16 + (priv ? (size_t)nrep * bin_b : 0);
                 scatter_smem = std::max(scatter_smem, sm);
                 for (int r0 = 0; r0 < R; r0 += nrep)
@@ -515,6 +515,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                         w.rep0 = r0;
                         w.nrep = std::min(nrep, R - r0);
                         w.priv = priv ? ((w.begin == 0 && w.end == T.numel) ? 2 : 1) : 0;
+                        w.gtab = gtab ? 1 : 0;
                         m1w.push_back(w);
                     }
             }

@@ -85,6 +85,23 @@ def test_method1_estimate_small(ctx, prec, m):
         assert np.allclose(out, oracle.combine(per, 3), rtol=1e-14, atol=0)
 
 
+@pytest.mark.parametrize("prec", [tnsk.PREC_FP32, tnsk.PREC_FP64])
+def test_method1_large_tables_from_global_memory(ctx, prec):
+    """Modes above 2048 indices: the scatter reads table words from global memory
+    (with the complement applied on the fly) and chunks are large; tr(ABC) with long
+    inner modes, and a chain with an open leg, against the oracle."""
+    rng = np.random.default_rng(17)
+    tdt = torch.float64 if prec == tnsk.PREC_FP64 else torch.float32
+    A, B, C = rng.standard_normal((3000, 5)), rng.standard_normal((5, 2100)), rng.standard_normal((2100, 3000))
+    tri = W.NetSpec([A, B, C], [(1, 2), (3, 4), (5, 0)], [], "long-modes")
+    chain = W.NetSpec([rng.standard_normal((2500, 3)), rng.standard_normal((2500, 4))], [(0, 2)], [1, 3], "open")
+    for spec, m in [(tri, 256), (tri, 4096), (chain, 64)]:
+        p = tnsk.Params(m=m, reps=9, seed=21, prec=prec)
+        out, per = gpu_estimate(ctx, spec, p, tdt)
+        y, s = oracle_estimate(spec, p, tdt)
+        assert_parity(per, y, s, TOL[prec], f"{spec.name} m={m}")
+
+
 def test_method1_triangle_full_size(ctx):
     """tr(ABC) of three 64x64 FP64 N(0,1) matrices, m = 256, 16 reps."""
     spec = W.triangle(64)
