@@ -206,8 +206,8 @@ tnsk_status tnsk_estimate_static(const tnsk_network* net, const tnsk_params* par
                                  void* cuda_stream);
 
 /* Measurement aid (not part of the method): the rate of FP32 shared-memory
- * atomic adds to random bins (1024 bins x 8 per CTA, 256 threads, two CTAs per
- * SM over all SMs), the ceiling of privatised scatter-add. Runs on the ctx
+ * atomic adds to random bins (1024 bins x 8 per CTA, 512 threads, four CTAs per
+ * SM over all SMs: full occupancy), the ceiling of privatised scatter-add. Runs on the ctx
  * stream, waits for it, and writes updates per second to *updates_per_s. */
 tnsk_status tnsk_probe_shared_atomics(tnsk_ctx* ctx, double* updates_per_s);
 

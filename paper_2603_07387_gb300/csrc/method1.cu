@@ -29,8 +29,11 @@ namespace tnsk {
 // Tensors whose tables are large (w.gtab) read the table words from global memory
 // instead (they stay in L2; within a warp the last mode's words are consecutive
 // and the other modes' are shared), leaving shared memory to the bins.
+// 512 threads: two CTAs (16 warps each) share an SM when the bins take ~96 KiB
+constexpr int kScatterThreads = 512;
+
 template <typename AccT, int MAXD>
-__global__ void __launch_bounds__(256) m1_scatter_kernel(const M1Tensor* __restrict__ tens,
+__global__ void __launch_bounds__(kScatterThreads) m1_scatter_kernel(const M1Tensor* __restrict__ tens,
                                                          const M1Net* __restrict__ nets,
                                                          const M1Work* __restrict__ work,
                                                          const uint32_t* __restrict__ tabs, AccT* __restrict__ xs) {
@@ -427,7 +430,7 @@ cudaError_t launch_scatter_d(const M1Tensor* d_tens, const M1Net* d_nets, const 
                              const uint32_t* d_tabs, AccT* d_xs, size_t smem, cudaStream_t s) {
     auto k = m1_scatter_kernel<AccT, MAXD>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<n_work, 256, smem, s>>>(d_tens, d_nets, d_work, d_tabs, d_xs);
+    k<<<n_work, kScatterThreads, smem, s>>>(d_tens, d_nets, d_work, d_tabs, d_xs);
     return cudaGetLastError();
 }
 

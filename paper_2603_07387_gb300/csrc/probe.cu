@@ -18,7 +18,7 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {  // a 32-bit integer fin
 }
 }  // namespace
 
-__global__ void __launch_bounds__(256, 2) probe_shared_atomics_kernel(float* sink) {
+__global__ void __launch_bounds__(512, 4) probe_shared_atomics_kernel(float* sink) {
     __shared__ float bins[kBins * kReps];
     for (int i = threadIdx.x; i < kBins * kReps; i += blockDim.x) bins[i] = 0.f;
     __syncthreads();
@@ -39,15 +39,15 @@ cudaError_t run_probe_shared_atomics(float* sink, cudaStream_t s, double* update
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int blocks = 2 * sms;
+    const int blocks = 4 * sms;  // 2048 threads per SM: full occupancy
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    probe_shared_atomics_kernel<<<blocks, 256, 0, s>>>(sink);  // warm-up
+    probe_shared_atomics_kernel<<<blocks, 512, 0, s>>>(sink);  // warm-up
     float best = 0.f;
     for (int rep = 0; rep < 5; ++rep) {
         cudaEventRecord(a, s);
-        for (int k = 0; k < 8; ++k) probe_shared_atomics_kernel<<<blocks, 256, 0, s>>>(sink);
+        for (int k = 0; k < 8; ++k) probe_shared_atomics_kernel<<<blocks, 512, 0, s>>>(sink);
         cudaEventRecord(b, s);
         cudaEventSynchronize(b);
         float ms = 0.f;
@@ -56,7 +56,7 @@ cudaError_t run_probe_shared_atomics(float* sink, cudaStream_t s, double* update
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    const double n = 8.0 * blocks * 256.0 * kIters * kReps;
+    const double n = 8.0 * blocks * 512.0 * kIters * kReps;
     *updates_per_s = best > 0.f ? n / (best * 1e-3) : 0.0;
     return cudaGetLastError();
 }
