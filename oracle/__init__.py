@@ -16,7 +16,7 @@ import subprocess
 
 import numpy as np
 
-from .exact import frobenius_product, tc_definition, tc_einsum, tc_reduced  # noqa: F401
+from .exact import frobenius_product, tc_definition, tc_einsum, tc_reduced, tc_sequential  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")

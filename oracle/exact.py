@@ -96,6 +96,34 @@ def tc_einsum(tensors, edges, open_modes):
     return np.asarray(np.einsum(*args, optimize="greedy"), dtype=np.float64)
 
 
+def tc_sequential(tensors, edges, open_modes):
+    """Def. "Tensor contraction" evaluated by absorbing the tensors one at a time, in
+    the given order, into a running tensor (float64); an index is summed as soon as
+    no later tensor carries it and it is not open. On a grid in row-major order the
+    running tensor holds at most one row of bonds."""
+    tensors = [np.asarray(x, dtype=np.float64) for x in tensors]
+    off, dims = _modes(tensors)
+    q = len(dims)
+    lab = list(range(q))  # unmatched modes keep their own label
+    for u, v in edges:
+        lab[v] = lab[u]
+    open_labels = [lab[g] for g in open_modes]
+    owner = [[lab[g] for g in range(off[k], off[k + 1])] for k in range(len(tensors))]
+    if not tensors:
+        return np.asarray(1.0)
+    run, run_lab = tensors[0], owner[0]
+    keep = lambda labels, k: [l for i, l in enumerate(labels) if l not in labels[:i] and
+                              (l in open_labels or any(l in owner[j] for j in range(k + 1, len(tensors))))]
+    out = keep(run_lab, 0)
+    run = np.einsum(run, run_lab, out)
+    run_lab = out
+    for k in range(1, len(tensors)):
+        out = keep(run_lab + owner[k], k)
+        run = np.einsum(run, run_lab, tensors[k], owner[k], out)
+        run_lab = out
+    return np.asarray(np.einsum(run, run_lab, open_labels), dtype=np.float64)
+
+
 def frobenius_product(tensors):
     """||X||_F of the tensor product = prod_k ||X_k||_F (proof of Theorem 1)."""
     return float(np.prod([np.linalg.norm(np.asarray(x, dtype=np.float64).ravel()) for x in tensors]))

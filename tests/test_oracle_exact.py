@@ -85,6 +85,24 @@ def test_three_exact_forms_agree_on_random_networks(seed):
     a = oracle.tc_definition(X, edges2, [0, 2])
     c = oracle.tc_einsum(X, edges2, [0, 2])
     assert np.allclose(a, c)
+    assert np.allclose(a, oracle.tc_sequential(X, edges2, [0, 2]))
+    assert np.allclose(oracle.tc_definition(X, edges, open_modes), oracle.tc_sequential(X, edges, open_modes))
+
+
+def test_sequential_contraction_on_grids_and_the_triangle():
+    from paper_2603_07387_gb300 import workloads as W
+
+    for L1, L2, b in [(1, 3, 3), (2, 2, 3), (2, 3, 2), (3, 3, 2)]:
+        g = W.grid(L1, L2, b, seed=L1 * 10 + L2)
+        want = oracle.tc_definition(g.tensors, g.edges, g.open) if L1 * L2 <= 6 else oracle.tc_einsum(
+            g.tensors, g.edges, g.open)
+        assert np.allclose(oracle.tc_sequential(g.tensors, g.edges, g.open), want, rtol=1e-12)
+    rng = np.random.default_rng(5)
+    A, B, C = rng.standard_normal((4, 5)), rng.standard_normal((5, 6)), rng.standard_normal((6, 4))
+    assert np.isclose(oracle.tc_sequential([A, B, C], [(1, 2), (3, 4), (5, 0)], []), np.trace(A @ B @ C))
+    # an open leg kept in the requested order
+    out = oracle.tc_sequential([A, B], [(1, 2)], [3, 0])
+    assert np.allclose(out, (A @ B).T)
 
 
 def test_frobenius_product():
