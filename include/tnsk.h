@@ -211,6 +211,55 @@ tnsk_status tnsk_estimate_static(const tnsk_network* net, const tnsk_params* par
  * stream, waits for it, and writes updates per second to *updates_per_s. */
 tnsk_status tnsk_probe_shared_atomics(tnsk_ctx* ctx, double* updates_per_s);
 
+/* ---- Learned sketch-size predictor (the paper has no counterpart: it sizes m
+ * by its variance bounds). A multilayer perceptron TNSK_MLP_FEATURES -> 128 ->
+ * 128 -> 128 -> 1, GELU (x Phi(x)) after each hidden layer, maps the features of
+ * a network at sketch size m and R reps (tnsk_features) to log10 of the relative
+ * error |y - tc| / |tc| of the method-1 estimate; trained by mean squared error
+ * and Adam (FP32) on samples the caller measures, evaluated in FP32 or with BF16
+ * operands (FP32 accumulation). Parameters: per layer W [n_out][n_in] row-major,
+ * then b [n_out], layers in order (tnsk_mlp_num_params floats); inputs are
+ * standardised per feature with mu, sigma (norm = mu[F] then sigma[F]) taken from
+ * the last training set. All X / y / grad pointers are device FP32, row-major
+ * [n][TNSK_MLP_FEATURES]. Calls run on the ctx stream; get, save, loss_grad and
+ * train return after the device work. */
+#define TNSK_MLP_FEATURES 9
+typedef struct tnsk_mlp tnsk_mlp;
+tnsk_status tnsk_mlp_num_params(int64_t* n);
+/* W ~ U(-a, a), a = sqrt(6 / n_in), b = 0 (seeded); identity standardisation. */
+tnsk_status tnsk_mlp_create(tnsk_ctx* ctx, uint64_t seed, tnsk_mlp** mlp);
+tnsk_status tnsk_mlp_destroy(tnsk_mlp* mlp);
+/* host copies: theta[tnsk_mlp_num_params], norm[2 * TNSK_MLP_FEATURES] */
+tnsk_status tnsk_mlp_get(tnsk_mlp* mlp, float* theta, float* norm);
+tnsk_status tnsk_mlp_set(tnsk_ctx* ctx, tnsk_mlp* mlp, const float* theta, const float* norm);
+/* Mean squared error of the n rows and its gradient (device, tnsk_mlp_num_params
+ * floats; may be NULL) at the current parameters; *loss on the host. n <= 2^24. */
+tnsk_status tnsk_mlp_loss_grad(tnsk_ctx* ctx, tnsk_mlp* mlp, const float* X, const float* y, int64_t n, float* grad,
+                               double* loss);
+/* Sets the standardisation from X, then `epochs` passes of Adam (lr, beta 0.9 /
+ * 0.999, eps 1e-8) over minibatches of `batch` rows in a seeded random order;
+ * *final_loss (may be NULL) = the mean squared error over all n rows after. */
+tnsk_status tnsk_mlp_train(tnsk_ctx* ctx, tnsk_mlp* mlp, const float* X, const float* y, int64_t n, int32_t epochs,
+                           int32_t batch, float lr, uint64_t seed, double* final_loss);
+/* y[i] = predicted log10 relative error of row i; bf16 != 0: BF16 operands. */
+tnsk_status tnsk_mlp_predict(tnsk_ctx* ctx, tnsk_mlp* mlp, const float* X, int64_t n, float* y, int32_t bf16);
+/* Binary file of this library ("TNSKMLP1", shape, norm, theta); load checks the shape. */
+tnsk_status tnsk_mlp_save(tnsk_mlp* mlp, const char* path);
+tnsk_status tnsk_mlp_load(tnsk_ctx* ctx, tnsk_mlp* mlp, const char* path);
+/* Features (host float[TNSK_MLP_FEATURES]) of a network at params->m and
+ * params->reps: p, t, cycle rank t - p + components, log2 of the largest and the
+ * mean log2 of the contraction dims, mean and standard deviation over tensors of
+ * ln ||X_k||_F (computed on the device), log2 m, log2 R. */
+tnsk_status tnsk_features(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, float* features);
+/* Sets inout->m to the smallest 2^6 .. 2^16 whose predicted relative error at
+ * inout->reps is <= target_err (*predicted_err, may be NULL, gets it). With
+ * mlp == NULL, or for TNSK_ACYCLIC, the paper's variance bound with delta = 0.1
+ * decides instead: m R >= 3^t / (eps^2 delta) (general) or 32 t / (eps^2 delta)
+ * (acyclic). TNSK_ERR_UNREACHABLE (inout unchanged, *predicted_err = the best
+ * candidate's) when no candidate meets the target. */
+tnsk_status tnsk_choose_params(tnsk_ctx* ctx, const tnsk_network* net, double target_err, tnsk_mlp* mlp,
+                               tnsk_params* inout, double* predicted_err);
+
 /* Wait for the ctx's stream; returns the first deferred device error, if any. */
 tnsk_status tnsk_sync(tnsk_ctx* ctx);
 

@@ -8,28 +8,12 @@
 #include <string>
 #include <vector>
 
+#include "ctx.cuh"
 #include "kernels.cuh"
 #include "method2.cuh"
 #include "plan.cuh"
 
 using namespace tnsk;
-
-struct tnsk_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    std::string last_error;
-    tnsk_status deferred = TNSK_OK;
-    // scratch arena, grown on demand, reused by every call (stream ordered)
-    unsigned char* scratch = nullptr;
-    size_t scratch_bytes = 0;
-    // twiddles tw[k] = exp(-2 pi i k/m), k < m/2, for m = 2^l, l = 0..16
-    void* tw32[17] = {};
-    void* tw64[17] = {};
-    const void** d_tw32 = nullptr;  // device arrays of the pointers above
-    const void** d_tw64 = nullptr;
-    int* d_err = nullptr;  // device error word
-    Profiler prof;
-};
 
 namespace {
 
@@ -131,6 +115,13 @@ tnsk_status check_ctx(tnsk_ctx* ctx) {
 }
 
 }  // namespace
+
+namespace tnsk {
+tnsk_status ctx_fail(tnsk_ctx* ctx, tnsk_status st, const std::string& msg) { return fail(ctx, st, msg); }
+tnsk_status ctx_cuda_fail(tnsk_ctx* ctx, cudaError_t e, const char* where) { return cuda_fail(ctx, e, where); }
+tnsk_status ctx_check(tnsk_ctx* ctx) { return check_ctx(ctx); }
+tnsk_status ctx_ensure_scratch(tnsk_ctx* ctx, size_t bytes) { return ensure_scratch(ctx, bytes); }
+}  // namespace tnsk
 
 // ---------------------------------------------------------------------------
 // Arena: carve typed regions out of the ctx scratch, then upload host staging.

@@ -1,0 +1,34 @@
+// ctx.cuh -- the library context (tnsk_ctx) and the host helpers every C-ABI
+// source uses: error recording, context checks, the shared scratch arena.
+#pragma once
+
+#include <string>
+
+#include "kernels.cuh"
+
+struct tnsk_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    tnsk_status deferred = TNSK_OK;
+    // scratch arena, grown on demand, reused by every call (stream ordered)
+    unsigned char* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    // twiddles tw[k] = exp(-2 pi i k/m), k < m/2, for m = 2^l, l = 0..16
+    void* tw32[17] = {};
+    void* tw64[17] = {};
+    const void** d_tw32 = nullptr;  // device arrays of the pointers above
+    const void** d_tw64 = nullptr;
+    int* d_err = nullptr;  // device error word
+    tnsk::Profiler prof;
+};
+
+namespace tnsk {
+// records msg as the ctx's last error and returns st
+tnsk_status ctx_fail(tnsk_ctx* ctx, tnsk_status st, const std::string& msg);
+tnsk_status ctx_cuda_fail(tnsk_ctx* ctx, cudaError_t e, const char* where);
+// non-null, no deferred device error, its device current
+tnsk_status ctx_check(tnsk_ctx* ctx);
+// the ctx scratch arena holds at least `bytes` (stream-ordered reuse)
+tnsk_status ctx_ensure_scratch(tnsk_ctx* ctx, size_t bytes);
+}  // namespace tnsk

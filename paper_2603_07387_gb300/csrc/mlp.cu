@@ -1,0 +1,692 @@
+// mlp.cu -- the learned sketch-size predictor: a multilayer perceptron
+// 9 -> 128 -> 128 -> 128 -> 1 (GELU after each hidden layer) that maps features of
+// a network and a sketch size to log10 of the estimator's relative error, trained
+// on the GPU by these kernels (mean squared error, Adam) and evaluated in FP32 or
+// with BF16 operands (FP32 accumulation). tnsk_choose_params uses it to pick the
+// smallest m whose predicted error meets a target, with the paper's variance bound
+// (Theorem "general" / "acyclic" bounds, m R >= 3^t / (eps^2 delta) resp.
+// 32 t / (eps^2 delta)) when no predictor is given.
+//
+// Parameters: for each layer W [n_out][n_in] row-major then b [n_out], layers in
+// order, one flat FP32 vector; inputs are standardised per feature, z = (x - mu) /
+// sigma, with mu and sigma taken from the training set.
+//
+// The products are at most [batch x 128] x [128 x 128]: launch-bound, not
+// throughput-bound, so they run as one small tiled SIMT kernel (32 x 32 output
+// tile, 256 threads, 2 x 2 outputs per thread) rather than on the tensor cores.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "kernels.cuh"
+#include "plan.cuh"
+
+namespace tnsk {
+namespace {
+
+constexpr int kFeatures = TNSK_MLP_FEATURES;
+constexpr int kHidden = 128;
+constexpr int kLayers = 4;
+constexpr int kDims[kLayers + 1] = {kFeatures, kHidden, kHidden, kHidden, 1};
+constexpr int kTile = 32;
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float x) {
+    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+__device__ __forceinline__ float round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+}  // namespace
+
+// C[M][N] (+)= sum_k A(m, k) B(k, n), then an epilogue. A(m, k) = A[m * lda + k], or
+// A[k * lda + m] when TA; B(k, n) = B[k * ldb + n], or B[n * ldb + k] when TB.
+// Epilogue: + bias[n] (if bias), pre = value (if pre), C = gelu(value) (if gelu).
+// BF16: A and B are rounded to bfloat16 as they are loaded (FP32 accumulation).
+template <bool TA, bool TB, bool BF16>
+__global__ void __launch_bounds__(256) mlp_gemm_kernel(int M, int N, int K, const float* __restrict__ A, int lda,
+                                                       const float* __restrict__ B, int ldb, float* __restrict__ C,
+                                                       int ldc, const float* __restrict__ bias, float* __restrict__ pre,
+                                                       int gelu) {
+    __shared__ float As[kTile][kTile + 1];  // [m][k]
+    __shared__ float Bs[kTile][kTile + 1];  // [k][n]
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * kTile, n0 = blockIdx.x * kTile;
+    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int k0 = 0; k0 < K; k0 += kTile) {
+        for (int q = threadIdx.x; q < kTile * kTile; q += blockDim.x) {
+            const int r = q / kTile, c = q % kTile;
+            {  // As[r = m][c = k]
+                const int mm = m0 + r, kk = k0 + c;
+                float v = 0.f;
+                if (mm < M && kk < K) v = TA ? A[(size_t)kk * lda + mm] : A[(size_t)mm * lda + kk];
+                As[r][c] = BF16 ? round_bf16(v) : v;
+            }
+            {  // Bs[r = k][c = n]
+                const int kk = k0 + r, nn = n0 + c;
+                float v = 0.f;
+                if (kk < K && nn < N) v = TB ? B[(size_t)nn * ldb + kk] : B[(size_t)kk * ldb + nn];
+                Bs[r][c] = BF16 ? round_bf16(v) : v;
+            }
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < kTile; ++k) {
+            const float a0 = As[ty][k], a1 = As[ty + 16][k];
+            const float b0 = Bs[k][tx], b1 = Bs[k][tx + 16];
+            acc[0][0] += a0 * b0;
+            acc[0][1] += a0 * b1;
+            acc[1][0] += a1 * b0;
+            acc[1][1] += a1 * b1;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int mm = m0 + ty + 16 * i, nn = n0 + tx + 16 * j;
+            if (mm >= M || nn >= N) continue;
+            float v = acc[i][j] + (bias ? bias[nn] : 0.f);
+            if (pre) pre[(size_t)mm * ldc + nn] = v;
+            C[(size_t)mm * ldc + nn] = gelu ? gelu_f(v) : v;
+        }
+}
+
+// z = (x - mu) / sigma per feature; rows picked by idx when idx != nullptr.
+__global__ void mlp_standardize_kernel(const float* __restrict__ X, const int64_t* __restrict__ idx, int64_t n,
+                                       const float* __restrict__ mu, const float* __restrict__ sigma,
+                                       float* __restrict__ Z) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n * kFeatures;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = q / kFeatures;
+        const int f = (int)(q - row * kFeatures);
+        const int64_t src = idx ? idx[row] : row;
+        Z[q] = (X[src * kFeatures + f] - mu[f]) / sigma[f];
+    }
+}
+
+// dout = 2 (out - y) / B for the picked rows; loss += sum (out - y)^2 / B.
+__global__ void mlp_mse_kernel(const float* __restrict__ out, const float* __restrict__ y,
+                               const int64_t* __restrict__ idx, int B, float* __restrict__ dout,
+                               double* __restrict__ loss) {
+    double part = 0.0;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+        const float d = out[b] - y[idx ? idx[b] : b];
+        dout[b] = 2.f * d / (float)B;
+        part += (double)d * d / B;
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(0xffffffffu, part, s);
+    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, part);
+}
+
+__global__ void mlp_gelu_bwd_kernel(float* __restrict__ d, const float* __restrict__ pre, int64_t n) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        d[q] *= gelu_grad_f(pre[q]);
+}
+
+// db[n] = sum_b d[b][n]
+__global__ void mlp_bias_grad_kernel(const float* __restrict__ d, int B, int N, float* __restrict__ db) {
+    const int nn = blockIdx.x * blockDim.x + threadIdx.x;
+    if (nn >= N) return;
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s += d[(size_t)b * N + nn];
+    db[nn] = s;
+}
+
+// Adam (Kingma & Ba), bias-corrected.
+__global__ void mlp_adam_kernel(float* __restrict__ theta, const float* __restrict__ g, float* __restrict__ m,
+                                float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                                float c2) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const float gq = g[q];
+        const float mq = b1 * m[q] + (1.f - b1) * gq;
+        const float vq = b2 * v[q] + (1.f - b2) * gq * gq;
+        m[q] = mq;
+        v[q] = vq;
+        theta[q] -= lr * (mq / c1) / (sqrtf(vq / c2) + eps);
+    }
+}
+
+// sum of squares of a tensor in FP64 (features: Frobenius norms)
+__global__ void sumsq_kernel(const void* __restrict__ data, int dtype, int64_t n, double* __restrict__ out) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = load_as<double>(data, dtype, i);
+        s += x * x;
+    }
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) s += __shfl_xor_sync(0xffffffffu, s, sh);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+}  // namespace tnsk
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+#include "ctx.cuh"
+
+using namespace tnsk;
+
+struct tnsk_mlp {
+    int device = 0;
+    int64_t n = 0;  // parameters
+    float* theta = nullptr;
+    float* grad = nullptr;
+    float* m1 = nullptr;  // Adam moments
+    float* m2 = nullptr;
+    float* norm = nullptr;  // device [2F]: mu, sigma
+    float h_norm[2 * kFeatures];
+    int64_t step = 0;
+    // activation buffers for `cap` rows
+    int64_t cap = 0;
+    float* Z = nullptr;
+    float* pre[kLayers] = {};
+    float* out[kLayers] = {};
+    float* d0 = nullptr;
+    float* d1 = nullptr;
+    double* loss = nullptr;
+};
+
+namespace {
+
+int64_t param_count() {
+    int64_t n = 0;
+    for (int l = 0; l < kLayers; ++l) n += (int64_t)kDims[l + 1] * kDims[l] + kDims[l + 1];
+    return n;
+}
+int64_t w_off(int l) {
+    int64_t o = 0;
+    for (int i = 0; i < l; ++i) o += (int64_t)kDims[i + 1] * kDims[i] + kDims[i + 1];
+    return o;
+}
+int64_t b_off(int l) { return w_off(l) + (int64_t)kDims[l + 1] * kDims[l]; }
+
+void free_acts(tnsk_mlp* p) {
+    cudaFree(p->Z);
+    for (int l = 0; l < kLayers; ++l) {
+        cudaFree(p->pre[l]);
+        cudaFree(p->out[l]);
+        p->pre[l] = p->out[l] = nullptr;
+    }
+    cudaFree(p->d0);
+    cudaFree(p->d1);
+    p->Z = p->d0 = p->d1 = nullptr;
+    p->cap = 0;
+}
+
+bool ensure_acts(tnsk_mlp* p, int64_t rows) {
+    if (rows <= p->cap) return true;
+    free_acts(p);
+    bool ok = cudaMalloc((void**)&p->Z, rows * kFeatures * sizeof(float)) == cudaSuccess;
+    for (int l = 0; l < kLayers; ++l) {
+        ok = ok && cudaMalloc((void**)&p->pre[l], rows * kDims[l + 1] * sizeof(float)) == cudaSuccess;
+        ok = ok && cudaMalloc((void**)&p->out[l], rows * kDims[l + 1] * sizeof(float)) == cudaSuccess;
+    }
+    ok = ok && cudaMalloc((void**)&p->d0, rows * kHidden * sizeof(float)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&p->d1, rows * kHidden * sizeof(float)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_acts(p);
+        return false;
+    }
+    p->cap = rows;
+    return true;
+}
+
+template <bool TA, bool TB, bool BF16>
+void gemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc, const float* bias,
+          float* pre, bool gelu, cudaStream_t s) {
+    dim3 grid((N + kTile - 1) / kTile, (M + kTile - 1) / kTile);
+    mlp_gemm_kernel<TA, TB, BF16><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, pre, gelu ? 1 : 0);
+}
+
+unsigned grid_for(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8); }
+
+// standardise rows (picked by idx) of X into p->Z and run the layers; the output
+// column is p->out[kLayers - 1]
+void forward(tnsk_mlp* p, const float* X, const int64_t* idx, int64_t B, bool bf16, cudaStream_t s) {
+    mlp_standardize_kernel<<<grid_for(B * kFeatures), 256, 0, s>>>(X, idx, B, p->norm, p->norm + kFeatures, p->Z);
+    const float* h = p->Z;
+    for (int l = 0; l < kLayers; ++l) {
+        const bool act = l < kLayers - 1;
+        if (bf16)
+            gemm<false, true, true>((int)B, kDims[l + 1], kDims[l], h, kDims[l], p->theta + w_off(l), kDims[l],
+                                    p->out[l], kDims[l + 1], p->theta + b_off(l), p->pre[l], act, s);
+        else
+            gemm<false, true, false>((int)B, kDims[l + 1], kDims[l], h, kDims[l], p->theta + w_off(l), kDims[l],
+                                     p->out[l], kDims[l + 1], p->theta + b_off(l), p->pre[l], act, s);
+        h = p->out[l];
+    }
+}
+
+// mean squared error of the last forward against y (rows idx) and its gradient
+// into p->grad; adds the loss to p->loss
+void backward(tnsk_mlp* p, const float* y, const int64_t* idx, int64_t B, cudaStream_t s) {
+    float* d = p->d0;
+    float* dn = p->d1;
+    mlp_mse_kernel<<<grid_for(B), 256, 0, s>>>(p->out[kLayers - 1], y, idx, (int)B, d, p->loss);
+    for (int l = kLayers - 1; l >= 0; --l) {
+        const int no = kDims[l + 1], ni = kDims[l];
+        const float* in = l > 0 ? p->out[l - 1] : p->Z;
+        // gW[o][i] = sum_b d[b][o] in[b][i]
+        gemm<true, false, false>(no, ni, (int)B, d, no, in, ni, p->grad + w_off(l), ni, nullptr, nullptr, false, s);
+        mlp_bias_grad_kernel<<<(no + 127) / 128, 128, 0, s>>>(d, (int)B, no, p->grad + b_off(l));
+        if (l > 0) {
+            // d_prev[b][i] = sum_o d[b][o] W[o][i], times gelu'(pre_prev)
+            gemm<false, false, false>((int)B, ni, no, d, no, p->theta + w_off(l), ni, dn, ni, nullptr, nullptr, false,
+                                      s);
+            mlp_gelu_bwd_kernel<<<grid_for(B * ni), 256, 0, s>>>(dn, p->pre[l - 1], B * ni);
+            std::swap(d, dn);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+tnsk_status tnsk_mlp_num_params(int64_t* n) {
+    if (!n) return TNSK_ERR_INVALID;
+    *n = param_count();
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_mlp_create(tnsk_ctx* ctx, uint64_t seed, tnsk_mlp** out) {
+    if (!out) return TNSK_ERR_INVALID;
+    *out = nullptr;
+    tnsk_status st = ctx_check(ctx);
+    if (st != TNSK_OK) return st;
+    tnsk_mlp* p = new tnsk_mlp();
+    p->device = ctx->device;
+    p->n = param_count();
+    const size_t bytes = (size_t)p->n * sizeof(float);
+    bool ok = cudaMalloc((void**)&p->theta, bytes) == cudaSuccess && cudaMalloc((void**)&p->grad, bytes) == cudaSuccess &&
+              cudaMalloc((void**)&p->m1, bytes) == cudaSuccess && cudaMalloc((void**)&p->m2, bytes) == cudaSuccess &&
+              cudaMalloc((void**)&p->norm, 2 * kFeatures * sizeof(float)) == cudaSuccess &&
+              cudaMalloc((void**)&p->loss, sizeof(double)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        tnsk_mlp_destroy(p);
+        return ctx_fail(ctx, TNSK_ERR_OOM, "predictor allocation failed");
+    }
+    // W ~ U(-a, a), a = sqrt(6 / n_in), b = 0; identity standardisation
+    std::mt19937_64 rng(seed);
+    std::vector<float> h((size_t)p->n, 0.f);
+    for (int l = 0; l < kLayers; ++l) {
+        std::uniform_real_distribution<double> u(-std::sqrt(6.0 / kDims[l]), std::sqrt(6.0 / kDims[l]));
+        for (int64_t q = 0; q < (int64_t)kDims[l + 1] * kDims[l]; ++q) h[(size_t)(w_off(l) + q)] = (float)u(rng);
+    }
+    for (int f = 0; f < kFeatures; ++f) {
+        p->h_norm[f] = 0.f;
+        p->h_norm[kFeatures + f] = 1.f;
+    }
+    cudaMemcpy(p->theta, h.data(), bytes, cudaMemcpyHostToDevice);
+    cudaMemcpy(p->norm, p->h_norm, sizeof(p->h_norm), cudaMemcpyHostToDevice);
+    cudaMemset(p->m1, 0, bytes);
+    cudaMemset(p->m2, 0, bytes);
+    if (cudaGetLastError() != cudaSuccess) {
+        tnsk_mlp_destroy(p);
+        return ctx_fail(ctx, TNSK_ERR_CUDA, "predictor initialisation failed");
+    }
+    *out = p;
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_mlp_destroy(tnsk_mlp* p) {
+    if (!p) return TNSK_ERR_INVALID;
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    free_acts(p);
+    cudaFree(p->theta);
+    cudaFree(p->grad);
+    cudaFree(p->m1);
+    cudaFree(p->m2);
+    cudaFree(p->norm);
+    cudaFree(p->loss);
+    delete p;
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_mlp_get(tnsk_mlp* p, float* theta, float* norm) {
+    if (!p || !theta || !norm) return TNSK_ERR_INVALID;
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    if (cudaMemcpy(theta, p->theta, (size_t)p->n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return TNSK_ERR_CUDA;
+    }
+    std::memcpy(norm, p->h_norm, sizeof(p->h_norm));
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_mlp_set(tnsk_ctx* ctx, tnsk_mlp* p, const float* theta, const float* norm) {
+    tnsk_status st = ctx_check(ctx);
+    if (st != TNSK_OK) return st;
+    if (!p || !theta || !norm) return ctx_fail(ctx, TNSK_ERR_INVALID, "mlp_set: NULL argument");
+    for (int f = 0; f < kFeatures; ++f)
+        if (!(norm[kFeatures + f] > 0.f)) return ctx_fail(ctx, TNSK_ERR_INVALID, "mlp_set: sigma must be > 0");
+    std::memcpy(p->h_norm, norm, sizeof(p->h_norm));
+    cudaStreamSynchronize(ctx->stream);
+    if (cudaMemcpy(p->theta, theta, (size_t)p->n * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->norm, p->h_norm, sizeof(p->h_norm), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return ctx_fail(ctx, TNSK_ERR_CUDA, "mlp_set: copy failed");
+    }
+    p->step = 0;
+    cudaMemset(p->m1, 0, (size_t)p->n * sizeof(float));
+    cudaMemset(p->m2, 0, (size_t)p->n * sizeof(float));
+    return TNSK_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+tnsk_status tnsk_mlp_loss_grad(tnsk_ctx* ctx, tnsk_mlp* p, const float* X, const float* y, int64_t n, float* grad,
+                               double* loss) {
+    tnsk_status st = ctx_check(ctx);
+    if (st != TNSK_OK) return st;
+    if (!p || !X || !y || n < 1 || n > (1 << 24)) return ctx_fail(ctx, TNSK_ERR_INVALID, "mlp_loss_grad: arguments");
+    if (!ensure_acts(p, n)) return ctx_fail(ctx, TNSK_ERR_OOM, "mlp_loss_grad: activations");
+    cudaStream_t s = ctx->stream;
+    cudaMemsetAsync(p->loss, 0, sizeof(double), s);
+    forward(p, X, nullptr, n, false, s);
+    backward(p, y, nullptr, n, s);
+    if (grad) cudaMemcpyAsync(grad, p->grad, (size_t)p->n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    double h = 0;
+    cudaMemcpyAsync(&h, p->loss, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "mlp_loss_grad");
+    if (loss) *loss = h;
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_mlp_train(tnsk_ctx* ctx, tnsk_mlp* p, const float* X, const float* y, int64_t n, int32_t epochs,
+                           int32_t batch, float lr, uint64_t seed, double* final_loss) {
+    tnsk_status st = ctx_check(ctx);
+    if (st != TNSK_OK) return st;
+    if (!p || !X || !y || n < 2 || n > (1 << 24) || epochs < 0 || batch < 1 || !(lr > 0.f))
+        return ctx_fail(ctx, TNSK_ERR_INVALID, "mlp_train: arguments");
+    cudaStream_t s = ctx->stream;
+    // standardisation from the training set (host, FP64)
+    std::vector<float> hx((size_t)n * kFeatures);
+    if (cudaMemcpy(hx.data(), X, hx.size() * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return ctx_fail(ctx, TNSK_ERR_CUDA, "mlp_train: reading X");
+    }
+    for (int f = 0; f < kFeatures; ++f) {
+        double m = 0, v = 0;
+        for (int64_t i = 0; i < n; ++i) m += hx[(size_t)(i * kFeatures + f)];
+        m /= (double)n;
+        for (int64_t i = 0; i < n; ++i) {
+            const double d = hx[(size_t)(i * kFeatures + f)] - m;
+            v += d * d;
+        }
+        const double sd = std::sqrt(v / (double)n);
+        p->h_norm[f] = (float)m;
+        p->h_norm[kFeatures + f] = sd > 1e-6 ? (float)sd : 1.f;
+    }
+    cudaMemcpy(p->norm, p->h_norm, sizeof(p->h_norm), cudaMemcpyHostToDevice);
+    const int64_t B = std::min<int64_t>(batch, n);
+    if (!ensure_acts(p, std::max<int64_t>(B, 1))) return ctx_fail(ctx, TNSK_ERR_OOM, "mlp_train: activations");
+    int64_t* d_idx = nullptr;
+    if (cudaMalloc((void**)&d_idx, (size_t)n * sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return ctx_fail(ctx, TNSK_ERR_OOM, "mlp_train: index buffer");
+    }
+    std::mt19937_64 rng(seed);
+    std::vector<int64_t> perm((size_t)n);
+    for (int64_t i = 0; i < n; ++i) perm[(size_t)i] = i;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int ep = 0; ep < epochs; ++ep) {
+        for (int64_t i = n - 1; i > 0; --i)  // Fisher-Yates, the same order on every platform
+            std::swap(perm[(size_t)i], perm[(size_t)(rng() % (uint64_t)(i + 1))]);
+        // the host vector is reused next epoch: copy synchronously with the stream
+        cudaMemcpyAsync(d_idx, perm.data(), (size_t)n * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+        for (int64_t b0 = 0; b0 < n; b0 += B) {
+            const int64_t nb = std::min<int64_t>(B, n - b0);
+            forward(p, X, d_idx + b0, nb, false, s);
+            backward(p, y, d_idx + b0, nb, s);
+            ++p->step;
+            const float c1 = 1.f - std::pow(b1, (float)p->step), c2 = 1.f - std::pow(b2, (float)p->step);
+            mlp_adam_kernel<<<grid_for(p->n), 256, 0, s>>>(p->theta, p->grad, p->m1, p->m2, p->n, lr, b1, b2, eps, c1,
+                                                           c2);
+        }
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaFree(d_idx);
+            return ctx_cuda_fail(ctx, e, "mlp_train");
+        }
+    }
+    cudaFree(d_idx);
+    if (final_loss) {  // mean squared error over the whole training set, in chunks
+        double tot = 0.0;
+        for (int64_t b0 = 0; b0 < n; b0 += B) {
+            const int64_t nb = std::min<int64_t>(B, n - b0);
+            cudaMemsetAsync(p->loss, 0, sizeof(double), s);
+            forward(p, X + b0 * kFeatures, nullptr, nb, false, s);
+            mlp_mse_kernel<<<grid_for(nb), 256, 0, s>>>(p->out[kLayers - 1], y + b0, nullptr, (int)nb, p->d0, p->loss);
+            double h = 0;
+            cudaMemcpyAsync(&h, p->loss, sizeof(double), cudaMemcpyDeviceToHost, s);
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "mlp_train: loss");
+            tot += h * (double)nb;
+        }
+        *final_loss = tot / (double)n;
+    }
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_mlp_predict(tnsk_ctx* ctx, tnsk_mlp* p, const float* X, int64_t n, float* y, int32_t bf16) {
+    tnsk_status st = ctx_check(ctx);
+    if (st != TNSK_OK) return st;
+    if (!p || (n > 0 && (!X || !y)) || n < 0) return ctx_fail(ctx, TNSK_ERR_INVALID, "mlp_predict: arguments");
+    const int64_t chunk = 65536;
+    if (!ensure_acts(p, std::min<int64_t>(std::max<int64_t>(n, 1), chunk)))
+        return ctx_fail(ctx, TNSK_ERR_OOM, "mlp_predict: activations");
+    cudaStream_t s = ctx->stream;
+    for (int64_t b0 = 0; b0 < n; b0 += chunk) {
+        const int64_t nb = std::min<int64_t>(chunk, n - b0);
+        forward(p, X + b0 * kFeatures, nullptr, nb, bf16 != 0, s);
+        cudaMemcpyAsync(y + b0, p->out[kLayers - 1], (size_t)nb * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "mlp_predict");
+    return TNSK_OK;
+}
+
+// file: "TNSKMLP1", int32 features, int32 hidden, int64 parameters, float mu[F],
+// float sigma[F], float theta[parameters] (little-endian, as written by this library)
+tnsk_status tnsk_mlp_save(tnsk_mlp* p, const char* path) {
+    if (!p || !path) return TNSK_ERR_INVALID;
+    std::vector<float> th((size_t)p->n);
+    float nm[2 * kFeatures];
+    tnsk_status st = tnsk_mlp_get(p, th.data(), nm);
+    if (st != TNSK_OK) return st;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return TNSK_ERR_INVALID;
+    const int32_t hdr[2] = {kFeatures, kHidden};
+    const int64_t n = p->n;
+    bool ok = std::fwrite("TNSKMLP1", 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              std::fwrite(&n, sizeof(n), 1, f) == 1 && std::fwrite(nm, sizeof(nm), 1, f) == 1 &&
+              std::fwrite(th.data(), sizeof(float), th.size(), f) == th.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? TNSK_OK : TNSK_ERR_INVALID;
+}
+
+tnsk_status tnsk_mlp_load(tnsk_ctx* ctx, tnsk_mlp* p, const char* path) {
+    tnsk_status st = ctx_check(ctx);
+    if (st != TNSK_OK) return st;
+    if (!p || !path) return ctx_fail(ctx, TNSK_ERR_INVALID, "mlp_load: NULL argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return ctx_fail(ctx, TNSK_ERR_INVALID, std::string("mlp_load: cannot open ") + path);
+    char magic[8];
+    int32_t hdr[2];
+    int64_t n = 0;
+    float nm[2 * kFeatures];
+    std::vector<float> th((size_t)p->n);
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "TNSKMLP1", 8) == 0 &&
+              std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == kFeatures && hdr[1] == kHidden &&
+              std::fread(&n, sizeof(n), 1, f) == 1 && n == p->n && std::fread(nm, sizeof(nm), 1, f) == 1 &&
+              std::fread(th.data(), sizeof(float), th.size(), f) == th.size();
+    std::fclose(f);
+    if (!ok) return ctx_fail(ctx, TNSK_ERR_INVALID, std::string("mlp_load: not a predictor file of this shape: ") + path);
+    return tnsk_mlp_set(ctx, p, th.data(), nm);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Features of a network at sketch size m and R reps (the predictor's inputs):
+// p, t, cycle rank t - p + components, log2 of the largest and mean log2 of the
+// contraction dims, mean and standard deviation of ln ||X_k||_F, log2 m, log2 R.
+tnsk_status network_features(tnsk_ctx* ctx, const tnsk_network& net, const tnsk_params& prm, NetInfo& I,
+                             float* feat) {
+    std::string why;
+    tnsk_params q = prm;
+    q.m = 1;  // the features take log2 m from prm; validation needs any valid m
+    tnsk_status st = validate(net, q, I, why);
+    if (st != TNSK_OK) return ctx_fail(ctx, st, why);
+    // connected components of the tensors joined by contractions
+    std::vector<int> parent(I.p);
+    for (int k = 0; k < I.p; ++k) parent[k] = k;
+    auto find = [&](int x) {
+        while (parent[x] != x) x = parent[x] = parent[parent[x]];
+        return x;
+    };
+    double lmax = 0.0, lsum = 0.0;
+    for (int e = 0; e < I.t; ++e) {
+        const int u = net.edges[2 * e], v = net.edges[2 * e + 1];
+        parent[find(I.tensor_of[u])] = find(I.tensor_of[v]);
+        const double l = std::log2((double)std::max<int64_t>(I.dims[u], 1));
+        lmax = std::max(lmax, l);
+        lsum += l;
+    }
+    int comps = 0;
+    for (int k = 0; k < I.p; ++k) comps += find(k) == k;
+    // Frobenius norms on the device (FP64 sums of squares)
+    double* d = nullptr;
+    if (cudaMalloc((void**)&d, std::max(I.p, 1) * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return ctx_fail(ctx, TNSK_ERR_OOM, "features: buffer");
+    }
+    cudaMemsetAsync(d, 0, std::max(I.p, 1) * sizeof(double), ctx->stream);
+    for (int k = 0; k < I.p; ++k)
+        if (I.numel[k] > 0)
+            sumsq_kernel<<<grid_for(I.numel[k]), 256, 0, ctx->stream>>>(net.X[k].data, net.X[k].dtype, I.numel[k],
+                                                                      d + k);
+    std::vector<double> ss(std::max(I.p, 1));
+    cudaMemcpyAsync(ss.data(), d, ss.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "features");
+    double mean = 0.0, var = 0.0;
+    std::vector<double> ln(I.p);
+    for (int k = 0; k < I.p; ++k) {
+        ln[k] = 0.5 * std::log(std::max(ss[k], 1e-300));
+        mean += ln[k];
+    }
+    mean /= std::max(I.p, 1);
+    for (int k = 0; k < I.p; ++k) var += (ln[k] - mean) * (ln[k] - mean);
+    var /= std::max(I.p, 1);
+    feat[0] = (float)I.p;
+    feat[1] = (float)I.t;
+    feat[2] = (float)(I.t - I.p + comps);
+    feat[3] = (float)lmax;
+    feat[4] = I.t > 0 ? (float)(lsum / I.t) : 0.f;
+    feat[5] = (float)mean;
+    feat[6] = (float)std::sqrt(var);
+    feat[7] = (float)std::log2((double)std::max<int64_t>(prm.m, 1));
+    feat[8] = (float)std::log2((double)std::max(prm.reps, 1));
+    return TNSK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tnsk_status tnsk_features(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, float* features) {
+    tnsk_status st = ctx_check(ctx);
+    if (st != TNSK_OK) return st;
+    if (!net || !params || !features) return ctx_fail(ctx, TNSK_ERR_INVALID, "features: NULL argument");
+    NetInfo I;
+    return network_features(ctx, *net, *params, I, features);
+}
+
+tnsk_status tnsk_choose_params(tnsk_ctx* ctx, const tnsk_network* net, double target_err, tnsk_mlp* mlp,
+                               tnsk_params* inout, double* predicted_err) {
+    tnsk_status st = ctx_check(ctx);
+    if (st != TNSK_OK) return st;
+    if (!net || !inout || !(target_err > 0.0)) return ctx_fail(ctx, TNSK_ERR_INVALID, "choose_params: arguments");
+    constexpr int kLo = 6, kHi = 16;  // candidate m = 2^6 .. 2^16
+    const double R = std::max(inout->reps, 1);
+    if (!mlp || inout->method != TNSK_GENERAL) {
+        // the variance bound with delta = 0.1: m R >= 3^t / (eps^2 delta) (general), 32 t / (eps^2 delta) (acyclic)
+        NetInfo I;
+        std::string why;
+        tnsk_params q = *inout;
+        q.m = 1;
+        st = validate(*net, q, I, why);
+        if (st != TNSK_OK) return ctx_fail(ctx, st, why);
+        const double delta = 0.1;
+        const double num = inout->method == TNSK_GENERAL ? std::pow(3.0, I.t) : 32.0 * I.t;
+        for (int l = kLo; l <= kHi; ++l) {
+            const double m = std::ldexp(1.0, l);
+            const double eps = std::sqrt(num / (m * R * delta));
+            if (eps <= target_err || l == kHi) {
+                if (predicted_err) *predicted_err = eps;
+                if (eps > target_err) return ctx_fail(ctx, TNSK_ERR_UNREACHABLE, "choose_params: bound not met at m = 2^16");
+                inout->m = (int64_t)1 << l;
+                return TNSK_OK;
+            }
+        }
+    }
+    float base[kFeatures];
+    NetInfo I;
+    st = network_features(ctx, *net, *inout, I, base);
+    if (st != TNSK_OK) return st;
+    const int nc = kHi - kLo + 1;
+    std::vector<float> hx((size_t)nc * kFeatures), hy(nc);
+    for (int c = 0; c < nc; ++c) {
+        std::memcpy(&hx[(size_t)c * kFeatures], base, sizeof(base));
+        hx[(size_t)c * kFeatures + 7] = (float)(kLo + c);
+    }
+    float* d = nullptr;
+    if (cudaMalloc((void**)&d, (hx.size() + hy.size()) * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return ctx_fail(ctx, TNSK_ERR_OOM, "choose_params: buffer");
+    }
+    cudaMemcpyAsync(d, hx.data(), hx.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+    st = tnsk_mlp_predict(ctx, mlp, d, nc, d + hx.size(), 1);
+    if (st == TNSK_OK) {
+        cudaMemcpyAsync(hy.data(), d + hx.size(), hy.size() * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = ctx_cuda_fail(ctx, e, "choose_params");
+    }
+    cudaFree(d);
+    if (st != TNSK_OK) return st;
+    // predicted log10 relative error per candidate: the smallest m that meets the target
+    double best = 1e300;
+    for (int c = 0; c < nc; ++c) {
+        const double err = std::pow(10.0, (double)hy[c]);
+        best = std::min(best, err);
+        if (err <= target_err) {
+            inout->m = (int64_t)1 << (kLo + c);
+            if (predicted_err) *predicted_err = err;
+            return TNSK_OK;
+        }
+    }
+    if (predicted_err) *predicted_err = best;
+    return ctx_fail(ctx, TNSK_ERR_UNREACHABLE, "choose_params: no m <= 2^16 meets the target");
+}
+
+}  // extern "C"

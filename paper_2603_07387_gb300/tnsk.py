@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libtnsk.so")
 
 TNSK_OK = 0
+ERR_UNREACHABLE = -7
 STATUS = {
     0: "TNSK_OK",
     -1: "TNSK_ERR_INVALID",
@@ -50,6 +51,18 @@ SYMBOLS = (
     "tnsk_sync",
     "tnsk_probe_shared_atomics",
     "tnsk_combine",
+    "tnsk_mlp_num_params",
+    "tnsk_mlp_create",
+    "tnsk_mlp_destroy",
+    "tnsk_mlp_get",
+    "tnsk_mlp_set",
+    "tnsk_mlp_loss_grad",
+    "tnsk_mlp_train",
+    "tnsk_mlp_predict",
+    "tnsk_mlp_save",
+    "tnsk_mlp_load",
+    "tnsk_features",
+    "tnsk_choose_params",
     "tnsk_status_string",
     "tnsk_last_error",
 )
@@ -136,6 +149,23 @@ def load_library(path: str = LIB_PATH):
     L.tnsk_profile_read.argtypes = [vp, vp, vp]
     L.tnsk_sync.restype = i32
     L.tnsk_sync.argtypes = [vp]
+    f32p, dp = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)
+    for name, args in [
+        ("tnsk_mlp_num_params", [ctypes.POINTER(i64)]),
+        ("tnsk_mlp_create", [vp, u64, ctypes.POINTER(vp)]),
+        ("tnsk_mlp_destroy", [vp]),
+        ("tnsk_mlp_get", [vp, f32p, f32p]),
+        ("tnsk_mlp_set", [vp, vp, f32p, f32p]),
+        ("tnsk_mlp_loss_grad", [vp, vp, vp, vp, i64, vp, dp]),
+        ("tnsk_mlp_train", [vp, vp, vp, vp, i64, i32, i32, ctypes.c_float, u64, dp]),
+        ("tnsk_mlp_predict", [vp, vp, vp, i64, vp, i32]),
+        ("tnsk_mlp_save", [vp, ctypes.c_char_p]),
+        ("tnsk_mlp_load", [vp, vp, ctypes.c_char_p]),
+        ("tnsk_features", [vp, ctypes.POINTER(_Network), ctypes.POINTER(_Params), f32p]),
+        ("tnsk_choose_params", [vp, ctypes.POINTER(_Network), ctypes.c_double, vp, ctypes.POINTER(_Params), dp]),
+    ]:
+        getattr(L, name).restype = i32
+        getattr(L, name).argtypes = args
     L.tnsk_combine.restype = i32
     L.tnsk_combine.argtypes = [vp, i32, i64, vp, i32, vp]
     L.tnsk_probe_shared_atomics.restype = i32
@@ -253,6 +283,80 @@ class Plan:
             pass
 
 
+MLP_FEATURES = 9
+
+
+class Mlp:
+    """The learned sketch-size predictor (tnsk_mlp_*); device tensors are FP32 torch
+    tensors, X of shape [n, MLP_FEATURES], y of shape [n]."""
+
+    def __init__(self, ctx: "Context", seed: int = 0):
+        self.ctx, self.lib = ctx, ctx.lib
+        h = ctypes.c_void_p()
+        ctx._check(self.lib.tnsk_mlp_create(ctx.h, int(seed) & ((1 << 64) - 1), ctypes.byref(h)))
+        self.h = h
+        n = ctypes.c_int64(0)
+        self.lib.tnsk_mlp_num_params(ctypes.byref(n))
+        self.n_params = n.value
+
+    def close(self):
+        if self.h is not None:
+            self.lib.tnsk_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get(self):
+        import numpy as np
+
+        th = np.zeros(self.n_params, dtype=np.float32)
+        nm = np.zeros(2 * MLP_FEATURES, dtype=np.float32)
+        st = self.lib.tnsk_mlp_get(self.h, th.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                   nm.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        if st != 0:
+            raise TnskError(st, "tnsk_mlp_get")
+        return th, nm
+
+    def set(self, theta, norm):
+        import numpy as np
+
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        nm = np.ascontiguousarray(norm, dtype=np.float32)
+        assert th.size == self.n_params and nm.size == 2 * MLP_FEATURES
+        self.ctx._check(self.lib.tnsk_mlp_set(self.ctx.h, self.h, th.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                              nm.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def loss_grad(self, X, y, grad=None) -> float:
+        loss = ctypes.c_double(0.0)
+        self.ctx._check(self.lib.tnsk_mlp_loss_grad(self.ctx.h, self.h, X.data_ptr(), y.data_ptr(), X.shape[0],
+                                                    grad.data_ptr() if grad is not None else None,
+                                                    ctypes.byref(loss)))
+        return loss.value
+
+    def train(self, X, y, epochs: int, batch: int = 256, lr: float = 1e-3, seed: int = 0) -> float:
+        loss = ctypes.c_double(0.0)
+        self.ctx._check(self.lib.tnsk_mlp_train(self.ctx.h, self.h, X.data_ptr(), y.data_ptr(), X.shape[0],
+                                                int(epochs), int(batch), float(lr), int(seed) & ((1 << 64) - 1),
+                                                ctypes.byref(loss)))
+        return loss.value
+
+    def predict(self, X, y, bf16: bool = True):
+        self.ctx._check(self.lib.tnsk_mlp_predict(self.ctx.h, self.h, X.data_ptr(), X.shape[0], y.data_ptr(),
+                                                  1 if bf16 else 0))
+
+    def save(self, path: str):
+        st = self.lib.tnsk_mlp_save(self.h, path.encode())
+        if st != 0:
+            raise TnskError(st, f"tnsk_mlp_save {path}")
+
+    def load(self, path: str):
+        self.ctx._check(self.lib.tnsk_mlp_load(self.ctx.h, self.h, path.encode()))
+
+
 class Context:
     """A libtnsk context bound to one device and one CUDA stream."""
 
@@ -341,6 +445,32 @@ class Context:
         R = per_rep.shape[0]
         O = per_rep.numel() // max(R, 1)
         self._check(self.lib.tnsk_combine(self.h, R, O, per_rep.data_ptr(), groups, out.data_ptr()))
+
+    def features(self, net: Network, params: Params):
+        """tnsk_features: the predictor's inputs for a network at params.m, params.reps."""
+        import numpy as np
+
+        nh = _NetHolder(net)
+        pr = _params(params)
+        f = (ctypes.c_float * MLP_FEATURES)()
+        self._check(self.lib.tnsk_features(self.h, ctypes.byref(nh.c), ctypes.byref(pr), f))
+        return np.array(f[:], dtype=np.float32)
+
+    def choose_params(self, net: Network, target_err: float, params: Params, mlp=None):
+        """tnsk_choose_params: (params with the chosen m, predicted error), or (None,
+        the best candidate's predicted error) when no m <= 2^16 meets the target
+        (TNSK_ERR_UNREACHABLE); other errors raise."""
+        import dataclasses
+
+        nh = _NetHolder(net)
+        pr = _params(params)
+        err = ctypes.c_double(0.0)
+        st = self.lib.tnsk_choose_params(self.h, ctypes.byref(nh.c), float(target_err),
+                                         mlp.h if mlp is not None else None, ctypes.byref(pr), ctypes.byref(err))
+        if st == ERR_UNREACHABLE:
+            return None, err.value
+        self._check(st)
+        return dataclasses.replace(params, m=int(pr.m)), err.value
 
     def probe_shared_atomics(self) -> float:
         """Random-bin FP32 shared-memory atomic adds per second (a measurement aid)."""
