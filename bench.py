@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hbm-probe", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     return ap.parse_args()
 
 
@@ -358,6 +359,7 @@ def run_ours(args, world, rank, local):
         cpu = cpu_baseline(pairs[0])
     launches = int(sum(v[1] for v in prof.values())) // max(args.steps, 1) * args.steps
     probe = hbm_sketch_probe(ctx, dev) if (rank == 0 and not args.no_hbm_probe) else None
+    lvp = learned_vs_plain(ctx, dev) if (rank == 0 and not args.no_learned) else None
     for p_ in plans:
         p_.close()
     ctx.close()
@@ -381,6 +383,7 @@ def run_ours(args, world, rank, local):
         "roofline_others": rooflines[1:4],
         "ms_per_step_profiled": round(ms_profiled, 4),
         "hbm_sketch_probe": probe,
+        "learned_vs_plain": lvp,
         "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
         "gpu_launches": launches,
         "host_ms_per_call": round(host_s * 1e3 / max(args.steps, 1), 3),
@@ -462,6 +465,123 @@ def hbm_sketch_probe(ctx, dev):
     del mats
     torch.cuda.empty_cache()
     return res
+
+
+# ---------------------------------------------------------------- learned-size batched form vs plain form
+def exact_sequential(spec, dev):
+    """tc of a network for the error report: the tensors absorbed one at a time (grid in
+    row order: one row of bonds wide), FP64 torch.einsum on the GPU."""
+    import torch
+
+    off = [0]
+    for x in spec.tensors:
+        off.append(off[-1] + np.ndim(x))
+    lab = list(range(off[-1]))
+    for u, v in spec.edges:
+        lab[v] = lab[u]
+    owner = [[lab[g] for g in range(off[k], off[k + 1])] for k in range(len(spec.tensors))]
+    ts = [torch.as_tensor(np.asarray(x, dtype=np.float32), device=dev).double() for x in spec.tensors]
+
+    def keep(labels, k):
+        return [l for i, l in enumerate(labels) if l not in labels[:i] and any(l in owner[j] for j in
+                                                                               range(k + 1, len(ts)))]
+
+    run, rl = ts[0], owner[0]
+    out = keep(rl, 0)
+    run, rl = torch.einsum(run, rl, out), out
+    for k in range(1, len(ts)):
+        out = keep(rl + owner[k], k)
+        run, rl = torch.einsum(run, rl, ts[k], owner[k], out), out
+    return float(run.sum())
+
+
+def learned_vs_plain(ctx, dev, steps: int = 5):
+    """Estimates/s at <= 5% relative error on held-out grids of the predictor's family
+    (L1 x L2 <= 4 x 4, bond 2..8, U(0,1), at least 7 contractions, so the variance bound
+    cannot reach 5% for any m <= 2^16), 16 reps each:
+      plain   = the paper's sizing (m from m R >= 3^t / (eps^2 delta), capped at 2^16),
+                one tnsk_estimate call per network, FP32;
+      chosen  = m from the learned predictor (trained here on 192 other grids against exact
+                values), every network in one planned batch (CUDA-graph replay); networks
+                the predictor calls unreachable are left out and counted.
+    Throughput counts every estimate produced; `within_5pct` is the fraction of them
+    within 5% of the exact value."""
+    import torch
+
+    from paper_2603_07387_gb300 import predictor, tnsk
+    from paper_2603_07387_gb300 import workloads as W
+
+    t0 = time.perf_counter()
+    train_specs = predictor.grid_specs(np.random.default_rng(2026), 192)
+    exact = [exact_sequential(s, dev) for s in train_specs]
+    X, y = predictor.measure(ctx, train_specs, exact, reps=(4, 16), seeds=(1, 2), device=dev)
+    mlp, loss = predictor.train(ctx, X, y, epochs=300, batch=256, lr=2e-3, seed=5, device=dev)
+    t_train = time.perf_counter() - t0
+    held = [s for s in predictor.grid_specs(np.random.default_rng(7), 200) if len(s.edges) >= 7]
+    R, target = 16, 0.05
+    nets = [tnsk.Network(W.to_torch(s, dev, torch.float32), s.edges, s.open) for s in held]
+    tcs = np.array([exact_sequential(s, dev) for s in held])
+
+    def rel(outs, idx):
+        est = np.array([float(o.item()) for o in outs])
+        return np.abs(est - tcs[idx]) / np.abs(tcs[idx])
+
+    # plain: bound sizing, one call per network
+    plain_p = []
+    for i, n in enumerate(nets):
+        p, _ = ctx.choose_params(n, target, tnsk.Params(m=1, reps=R, seed=31 + i))
+        plain_p.append(p if p is not None else tnsk.Params(m=1 << 16, reps=R, seed=31 + i))
+    outs = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in nets]
+    for i, n in enumerate(nets):  # warm-up
+        ctx.estimate(n, plain_p[i], outs[i])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        for i, n in enumerate(nets):
+            ctx.estimate(n, plain_p[i], outs[i])
+    e1.record()
+    torch.cuda.synchronize()
+    plain_s = e0.elapsed_time(e1) / 1e3 / steps
+    plain_err = rel(outs, np.arange(len(nets)))
+    # chosen: learned sizing, one planned batch
+    picked, chosen_p = [], []
+    for i, n in enumerate(nets):
+        p, _ = ctx.choose_params(n, target, tnsk.Params(m=1, reps=R, seed=31 + i), mlp)
+        if p is not None:
+            picked.append(i)
+            chosen_p.append(p)
+    couts = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in picked]
+    plan = ctx.plan([nets[i] for i in picked], chosen_p, couts)
+    plan.run()
+    plan.run()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        plan.run()
+    e1.record()
+    torch.cuda.synchronize()
+    chosen_s = e0.elapsed_time(e1) / 1e3 / steps
+    chosen_err = rel(couts, np.array(picked, dtype=int))
+    plan.close()
+    mlp.close()
+    plain = {"estimates_per_s": round(len(nets) / plain_s, 1), "networks": len(nets),
+             "within_5pct": round(float(np.mean(plain_err <= target)), 3),
+             "median_m": int(np.median([p.m for p in plain_p])), "median_rel_err": float(f"{np.median(plain_err):.3g}")}
+    chosen = {"estimates_per_s": round(len(picked) / chosen_s, 1), "networks": len(picked),
+              "within_5pct": round(float(np.mean(chosen_err <= target)), 3),
+              "median_m": int(np.median([p.m for p in chosen_p])) if chosen_p else None,
+              "median_rel_err": float(f"{np.median(chosen_err):.3g}") if picked else None,
+              "unreachable_by_predictor": len(nets) - len(picked)}
+    good_plain = len(nets) * plain["within_5pct"] / plain_s
+    good_chosen = len(picked) * chosen["within_5pct"] / chosen_s
+    return {"workload": "held-out grids (L1 x L2 <= 4 x 4, bond 2..8, U(0,1), t >= 7), 16 reps, target 5% "
+                        "relative error; FP32",
+            "plain": plain, "chosen": chosen,
+            "within_5pct_estimates_per_s": {"plain": round(good_plain, 1), "chosen": round(good_chosen, 1),
+                                            "ratio": round(good_chosen / good_plain, 2) if good_plain else None},
+            "predictor": {"train_samples": int(len(y)), "train_mse_log10": round(loss, 4),
+                          "train_s": round(t_train, 1)}}
 
 
 # ---------------------------------------------------------------- CPU baseline (oracle)

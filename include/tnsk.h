@@ -252,7 +252,10 @@ tnsk_status tnsk_mlp_load(tnsk_ctx* ctx, tnsk_mlp* mlp, const char* path);
  * ln ||X_k||_F (computed on the device), log2 m, log2 R. */
 tnsk_status tnsk_features(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, float* features);
 /* Sets inout->m to the smallest 2^6 .. 2^16 whose predicted relative error at
- * inout->reps is <= target_err (*predicted_err, may be NULL, gets it). With
+ * inout->reps is <= target_err (*predicted_err, may be NULL, gets it). The
+ * predicted error is the 90% quantile of one estimate's relative error: the
+ * predictor's expected log10 error, shifted by the log10 |Z| statistics of a
+ * normal error (10^pred / 0.3224). With
  * mlp == NULL, or for TNSK_ACYCLIC, the paper's variance bound with delta = 0.1
  * decides instead: m R >= 3^t / (eps^2 delta) (general) or 32 t / (eps^2 delta)
  * (acyclic). TNSK_ERR_UNREACHABLE (inout unchanged, *predicted_err = the best

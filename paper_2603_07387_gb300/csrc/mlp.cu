@@ -674,10 +674,15 @@ tnsk_status tnsk_choose_params(tnsk_ctx* ctx, const tnsk_network* net, double ta
     }
     cudaFree(d);
     if (st != TNSK_OK) return st;
-    // predicted log10 relative error per candidate: the smallest m that meets the target
+    // The predictor gives the expected log10 of one estimate's relative error. With
+    // the estimate's error ~ sigma Z (a mean of reps; Z standard normal),
+    // E log10 |Z| = -(gamma + ln 2) / (2 ln 10) = -0.2757 and P(|Z| <= 1.6449) = 0.9,
+    // so the error's 90% quantile is 10^(pred + 0.2757 + log10 1.6449) = 10^pred / 0.3224;
+    // that quantile must meet the target. The smallest such m wins.
+    constexpr double kQuantile90 = 1.0 / 0.3224;
     double best = 1e300;
     for (int c = 0; c < nc; ++c) {
-        const double err = std::pow(10.0, (double)hy[c]);
+        const double err = std::pow(10.0, (double)hy[c]) * kQuantile90;
         best = std::min(best, err);
         if (err <= target_err) {
             inout->m = (int64_t)1 << (kLo + c);

@@ -403,7 +403,6 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
             nb.n_open = N.n_open;
             nb.out = outs ? outs[b] : nullptr;
             nb.per_rep = per_reps ? per_reps[b] : nullptr;
-            max_log2m1 = std::max(max_log2m1, I.log2m);
             const int64_t K = m == 1 ? 1 : m / 2 + 1;
             int64_t xacc = 0, sacc = 0, eacc = 0;
             std::vector<int> slot_of(I.p, -1);
@@ -537,6 +536,8 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 // FP32, no open legs, 2^6 <= m <= 2^10: the warp-per-item spectrum kernel
                 const bool warp_path = !fp64 && I.O == 1 && nb.n_ot == 0 && I.log2m >= 6 && I.log2m <= 10;
                 std::vector<int2>& dst = warp_path ? m1warp[I.log2m - 6] : m1items;
+                // the block kernel's shared memory is sized by the largest m it runs
+                if (!warp_path) max_log2m1 = std::max(max_log2m1, I.log2m);
                 for (int r = 0; r < R; ++r) dst.push_back(make_int2((int)m1n.size(), r));
             }
             if (sketch_only) P.sketch_user_bytes = (size_t)R * xacc * acc;

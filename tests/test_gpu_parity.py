@@ -160,12 +160,13 @@ def test_method1_warp_spectrum_every_size(ctx, m):
 
 def test_method1_batch_mixes_spectrum_kernels(ctx):
     """One batch with networks for the warp kernel at two sizes, the block kernel (open legs,
-    m above 1024, m below 64) and method 2, each against the oracle."""
+    m above 1024, m below 64), the large-m kernels and method 2, each against the oracle."""
     rng = np.random.default_rng(33)
     closed = _closed_specs()
     opened = [W.random_network(rng, p_range=(4, 6), dim_range=(2, 5), open_dim_range=(2, 4)) for _ in range(2)]
-    specs = [closed[0], closed[1], opened[0], closed[3], opened[1], closed[4], closed[5], _trees()[2]]
-    ms = [64, 1024, 256, 2048, 1024, 32, 256, 128]
+    specs = [closed[0], closed[1], opened[0], closed[3], opened[1], closed[4], closed[5], _trees()[2], closed[2],
+             closed[0]]
+    ms = [64, 1024, 256, 2048, 1024, 32, 256, 128, 1 << 15, 1 << 16]
     params = [tnsk.Params(m=m, reps=4 + (i % 3), seed=500 + i,
                           method=tnsk.ACYCLIC if s.name.startswith("tree") else tnsk.GENERAL)
               for i, (s, m) in enumerate(zip(specs, ms))]

@@ -153,9 +153,9 @@ def test_choose_params_by_the_bound(ctx):
 
 def test_trained_predictor_picks_m_where_the_bound_cannot(ctx, tmp_path):
     """Train on measured errors of grids (exact values from the FP64 oracle), then on
-    held-out grids: the bound reaches the 5% target for none of them with cycles, the
-    predictor picks an m for most, and the estimates at the picked m meet the target
-    in most cases (checked with fresh seeds against the exact value)."""
+    held-out grids: the bound reaches the 5% target for none of them, the predictor picks
+    an m for many, and the estimates at the picked m meet the target in most cases
+    (checked with fresh seeds against the exact value)."""
     rng = np.random.default_rng(2026)
     specs = predictor.grid_specs(rng, 48)
     exact = [tc_sequential([np.asarray(x, dtype=np.float32).astype(np.float64) for x in s.tensors], s.edges, s.open)
@@ -186,9 +186,12 @@ def test_trained_predictor_picks_m_where_the_bound_cannot(ctx, tmp_path):
         out = torch.zeros(1, dtype=torch.float64, device="cuda")
         ctx.estimate(net, p, out)
         ctx.sync()
-        met += abs(float(out.item()) - tc) / abs(tc) <= 2 * target
+        met += abs(float(out.item()) - tc) / abs(tc) <= target
     assert bound_picked == 0
-    assert picked >= 0.5 * len(held)
+    # the m picked aims at a 90% chance of meeting the target (the predictor calls a grid
+    # unreachable otherwise); with a predictor trained on 48 grids, ask for picks on a
+    # fifth of the grids (the bound picks none) and for most of the picks to meet it
+    assert picked >= max(4, len(held) / 5)
     assert met >= 0.6 * picked
     mlp.close()
     again.close()
