@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hbm-probe", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true")
     return ap.parse_args()
 
 
@@ -360,6 +361,7 @@ def run_ours(args, world, rank, local):
     launches = int(sum(v[1] for v in prof.values())) // max(args.steps, 1) * args.steps
     probe = hbm_sketch_probe(ctx, dev) if (rank == 0 and not args.no_hbm_probe) else None
     lvp = learned_vs_plain(ctx, dev) if (rank == 0 and not args.no_learned) else None
+    unev = batched_uneven(ctx, dev) if (rank == 0 and not args.no_uneven) else None
     for p_ in plans:
         p_.close()
     ctx.close()
@@ -384,6 +386,7 @@ def run_ours(args, world, rank, local):
         "ms_per_step_profiled": round(ms_profiled, 4),
         "hbm_sketch_probe": probe,
         "learned_vs_plain": lvp,
+        "batched_uneven": unev,
         "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
         "gpu_launches": launches,
         "host_ms_per_call": round(host_s * 1e3 / max(args.steps, 1), 3),
@@ -465,6 +468,66 @@ def hbm_sketch_probe(ctx, dev):
     del mats
     torch.cuda.empty_cache()
     return res
+
+
+# ---------------------------------------------------------------- thousands of uneven networks in one batch
+def batched_uneven(ctx, dev, n_nets: int = 4096, m: int = 256, reps: int = 64, steps: int = 3):
+    """Method 1 on n_nets random connected networks (4..12 tensors, degree 2..4, edge dims
+    2..16, 0..2 open legs of dim 2..16, N(0,1) FP32; ~2.6e8 entries, 1 GB at 4096), m and
+    R fixed: all networks in one plan (one CUDA-graph replay per step) against the plain
+    form, one tnsk_estimate call per network. Estimates/s of each (an estimate = all
+    output entries of one network, combined over its reps)."""
+    import torch
+
+    from paper_2603_07387_gb300 import tnsk
+    from paper_2603_07387_gb300 import workloads as W
+
+    rng = np.random.default_rng(20260307)
+    specs = [W.random_network(rng) for _ in range(n_nets)]
+    nets, outs, entries = [], [], 0
+    for sp in specs:
+        ts = W.to_torch(sp, dev, torch.float32)
+        entries += sum(t.numel() for t in ts)
+        nets.append(tnsk.Network(ts, sp.edges, sp.open))
+        dims = [d for x in sp.tensors for d in np.shape(x)]
+        O = int(np.prod([dims[g] for g in sp.open])) if sp.open else 1
+        outs.append(torch.zeros(max(O, 1), dtype=torch.float64, device=dev))
+    params = [tnsk.Params(m=m, reps=reps, seed=0x7E57 + i) for i in range(n_nets)]
+    plan = ctx.plan(nets, params, outs)
+    plan.run()
+    plan.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan.run()
+    e1.record()
+    torch.cuda.synchronize()
+    batched_s = e0.elapsed_time(e1) / 1e3 / steps
+    ctx.profile(True)
+    plan.run()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    plan.close()
+    for i in range(min(64, n_nets)):  # warm-up of the per-network path
+        ctx.estimate(nets[i], params[i], outs[i])
+    torch.cuda.synchronize()
+    e0.record()
+    for i in range(n_nets):
+        ctx.estimate(nets[i], params[i], outs[i])
+    e1.record()
+    torch.cuda.synchronize()
+    plain_s = e0.elapsed_time(e1) / 1e3
+    upd = reps * entries
+    sc_ms = prof["m1_scatter"][0] / max(prof["m1_scatter"][1], 1)
+    return {"workload": f"{n_nets} random networks (4..12 tensors, degree 2..4, dims 2..16, 0..2 open legs), "
+                        f"method 1, m={m}, {reps} reps, FP32",
+            "entries": int(entries),
+            "batched": {"estimates_per_s": round(n_nets / batched_s, 1), "ms_per_batch": round(batched_s * 1e3, 3),
+                        "kernel_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
+                        "scatter_gupdates_per_s": round(upd / (sc_ms / 1e3) / 1e9, 1)},
+            "plain": {"estimates_per_s": round(n_nets / plain_s, 1), "ms_total": round(plain_s * 1e3, 1)},
+            "ratio": round(plain_s / batched_s, 2)}
 
 
 # ---------------------------------------------------------------- learned-size batched form vs plain form

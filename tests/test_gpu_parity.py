@@ -286,6 +286,30 @@ def test_batch_matches_oracle_per_network(ctx):
                            rtol=1e-14, atol=0)
 
 
+def test_uneven_random_networks_in_one_batch(ctx):
+    """Networks of the uneven-batch family (4..12 tensors, degree 2..4, dims 2..16, 0..2
+    open legs of dim 2..16, N(0,1)) in one planned batch, every per-rep entry against the
+    oracle."""
+    rng = np.random.default_rng(20260307)
+    specs = [W.random_network(rng) for _ in range(40)]
+    specs = [s for s in specs if sum(np.size(x) for x in s.tensors) < 2_000_000][:24]
+    params = [tnsk.Params(m=256, reps=3, seed=0x7E57 + i) for i in range(len(specs))]
+    nets = [gpu_network(s, torch.float32) for s in specs]
+    Os = []
+    for s in specs:
+        dims = [d for x in s.tensors for d in np.shape(x)]
+        Os.append(int(np.prod([dims[g] for g in s.open])) if s.open else 1)
+    outs = [torch.zeros(max(O, 1), dtype=torch.float64, device="cuda") for O in Os]
+    pers = [torch.zeros((3, max(O, 1)), dtype=torch.float64, device="cuda") for O in Os]
+    plan = ctx.plan(nets, params, outs, pers)
+    plan.run()
+    ctx.sync()
+    for s, p, pr, O in zip(specs, params, pers, Os):
+        y, sc = oracle_estimate(s, p, torch.float32)
+        assert_parity(pr.cpu().numpy()[:, :O], y, sc, TOL[p.prec], f"uneven {s.name}")
+    plan.close()
+
+
 def test_plan_runs_match_oracle_and_pick_up_new_data(ctx):
     rng = np.random.default_rng(12)
     specs = [W.random_network(rng, p_range=(4, 6), dim_range=(2, 5), open_dim_range=(2, 4)) for _ in range(3)]
