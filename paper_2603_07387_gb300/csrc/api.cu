@@ -267,10 +267,7 @@ static tnsk_status launch_plan(tnsk_ctx* ctx, const BatchPlan& plan, unsigned ch
     if (plan.m1.n_nets) {
         void* xs = sketch_out ? sketch_out : (void*)(base + plan.m1.xs_off);
         pf.begin(TNSK_K_M1_SCATTER, s);
-        TNSK_CUDA(launch_m1_scatter((const M1Tensor*)(base + plan.m1.tens_off), (const M1Net*)(base + plan.m1.nets_off),
-                                    (const M1Work*)(base + plan.m1.work_off), plan.m1.n_work,
-                                    (const uint32_t*)(base + plan.tabs_off), xs, fp64, plan.m1.scatter_smem,
-                                    plan.m1.max_order, s));
+        TNSK_CUDA(launch_m1_scatters(plan, base, xs, fp64, s));
         pf.end(s);
         if (!sketch_out) {
             pf.begin(TNSK_K_M1_SPECTRUM, s);

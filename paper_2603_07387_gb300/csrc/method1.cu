@@ -476,6 +476,19 @@ cudaError_t launch_m1_spectrum(const M1Tensor* d_tens, const M1Net* d_nets, cons
     return cudaGetLastError();
 }
 
+cudaError_t launch_m1_scatters(const BatchPlan& plan, unsigned char* base, void* xs, bool fp64, cudaStream_t s) {
+    const M1Tensor* tens = (const M1Tensor*)(base + plan.m1.tens_off);
+    const M1Net* nets = (const M1Net*)(base + plan.m1.nets_off);
+    const M1Work* work = (const M1Work*)(base + plan.m1.work_off);
+    const uint32_t* tabs = (const uint32_t*)(base + plan.tabs_off);
+    static const int kClassOrder[M1Plan::kOrderClasses] = {2, 4, 6, TNSK_MAX_ORDER};
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < M1Plan::kOrderClasses && e == cudaSuccess; ++c)
+        e = launch_m1_scatter(tens, nets, work + plan.m1.work_first[c], plan.m1.work_count[c], tabs, xs, fp64,
+                              plan.m1.class_smem[c], kClassOrder[c], s);
+    return e;
+}
+
 cudaError_t launch_m1_spectra(const BatchPlan& plan, unsigned char* base, const void* xs, const void* const* tws,
                               bool fp64, cudaStream_t s) {
     const M1Tensor* tens = (const M1Tensor*)(base + plan.m1.tens_off);

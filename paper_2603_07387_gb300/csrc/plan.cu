@@ -364,8 +364,8 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     std::vector<int4> lfft, lprod;  // large-m method 1: (net, rep, sketch), (net, rep, first bin, bins)
     int64_t ws_x = 0, ws_w = 0, ws_r = 0, ws_v = 0;  // method-2 workspace parts (elements)
     const bool tma = tensor_maps_available();
-    size_t scatter_smem = 16;
-    int max_log2m1 = 0, max_log2m2 = 0, m1_max_order = 0;
+    int max_log2m1 = 0, max_log2m2 = 0;
+    std::vector<M1Work> m1w_cls[M1Plan::kOrderClasses];
     struct PendingItem {
         int h, kind;
         M2Item it;
@@ -426,7 +426,6 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 }
                 T.dtype = N.X[k].dtype;
                 T.order = N.X[k].order;
-                m1_max_order = std::max(m1_max_order, T.order);
                 T.net = (int)m1n.size();
                 int64_t ost = 1;
                 for (int d = T.order - 1; d >= 0; --d) {
@@ -504,7 +503,8 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 // 32x as many entries as bins (a few percent of flush per update)
                 const int64_t CH = priv ? std::max<int64_t>(8192, 32 * T.O * m) : (gtab ? 65536 : 8192);
                 size_t sm = ((size_t)nrep * tab_b + 15) / 16 * 16 + (priv ? (size_t)nrep * bin_b : 0);
-                scatter_smem = std::max(scatter_smem, sm);
+                const int cls = T.order <= 2 ? 0 : (T.order <= 4 ? 1 : (T.order <= 6 ? 2 : 3));
+                P.m1.class_smem[cls] = std::max(P.m1.class_smem[cls], sm);
                 for (int r0 = 0; r0 < R; r0 += nrep)
                     for (int64_t b0 = 0; b0 < T.numel; b0 += CH) {
                         M1Work w{};
@@ -515,7 +515,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                         w.nrep = std::min(nrep, R - r0);
                         w.priv = priv ? ((w.begin == 0 && w.end == T.numel) ? 2 : 1) : 0;
                         w.gtab = gtab ? 1 : 0;
-                        m1w.push_back(w);
+                        m1w_cls[cls].push_back(w);
                     }
             }
             const bool large = I.log2m > max_log2m_for(fp64);
@@ -848,6 +848,11 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
 
     // ---- stage descriptors
     std::vector<unsigned char>& H = P.host_desc;
+    for (int c = 0; c < M1Plan::kOrderClasses; ++c) {
+        P.m1.work_first[c] = (int)m1w.size();
+        P.m1.work_count[c] = (int)m1w_cls[c].size();
+        m1w.insert(m1w.end(), m1w_cls[c].begin(), m1w_cls[c].end());
+    }
     size_t o_reqs = stage(H, reqs), o_m1t = stage(H, m1t), o_m1n = stage(H, m1n), o_m1w = stage(H, m1w);
     const int n_block_items = (int)m1items.size();
     for (int sl = 0; sl < M1Plan::kWarpSlots; ++sl) {
@@ -890,8 +895,6 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     P.m1.n_nets = (int)m1n.size();
     P.m1.n_work = (int)m1w.size();
     P.m1.n_items = n_block_items;
-    P.m1.scatter_smem = scatter_smem;
-    P.m1.max_order = m1_max_order;
     P.m1.max_log2m = max_log2m1;
     P.n_comb = (int)comb.size();
     return TNSK_OK;

@@ -42,8 +42,12 @@ struct M1Plan {
     size_t tens_off = 0, nets_off = 0, work_off = 0, opens_off = 0, items_off = 0;
     size_t xs_off = 0, spec_off = 0, sexp_off = 0;
     int n_work = 0, n_items = 0;
-    size_t scatter_smem = 0;
-    int max_order = 0;  // largest tensor order among method-1 tensors
+    // scatter work items by tensor order class (order <= 2, 4, 6, 12): one launch per
+    // class with its own unrolled width and shared-memory size
+    static constexpr int kOrderClasses = 4;
+    int work_first[kOrderClasses] = {0, 0, 0, 0};
+    int work_count[kOrderClasses] = {0, 0, 0, 0};
+    size_t class_smem[kOrderClasses] = {16, 16, 16, 16};
     int max_log2m = 0;
     // items of the warp-per-item spectrum kernel, by log2 m = 6 + slot, stored after
     // the n_items items of the block kernel
@@ -73,6 +77,8 @@ struct BatchPlan {
 };
 
 // Launches the spectrum kernels of every method-1 item of the plan (rows a3 + a4).
+// Launches the scatter of every method-1 work item (row a2), one launch per order class.
+cudaError_t launch_m1_scatters(const BatchPlan& plan, unsigned char* base, void* xs, bool fp64, cudaStream_t s);
 cudaError_t launch_m1_spectra(const BatchPlan& plan, unsigned char* base, const void* xs, const void* const* tws,
                               bool fp64, cudaStream_t s);
 

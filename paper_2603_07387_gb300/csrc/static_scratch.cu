@@ -129,10 +129,7 @@ extern "C" tnsk_status tnsk_estimate_static(const tnsk_network* net, const tnsk_
         return TNSK_ERR_CUDA;
     if (launch_draw_tables((const TabReq*)(base + plan.reqs_off), plan.n_reqs, plan.n_table_rows,
                            (uint32_t*)(base + plan.tabs_off), s) != cudaSuccess ||
-        launch_m1_scatter((const M1Tensor*)(base + plan.m1.tens_off), (const M1Net*)(base + plan.m1.nets_off),
-                          (const M1Work*)(base + plan.m1.work_off), plan.m1.n_work,
-                          (const uint32_t*)(base + plan.tabs_off), base + plan.m1.xs_off, false,
-                          plan.m1.scatter_smem, plan.m1.max_order, s) != cudaSuccess ||
+        launch_m1_scatters(plan, base, base + plan.m1.xs_off, false, s) != cudaSuccess ||
         launch_m1_spectra(plan, base, base + plan.m1.xs_off, (const void* const*)tws, false, s) != cudaSuccess ||
         launch_combine((const CombineItem*)(base + plan.comb_off), plan.n_comb, (const double*)(base + plan.yrep_off),
                        s) != cudaSuccess) {
