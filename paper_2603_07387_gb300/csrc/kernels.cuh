@@ -72,10 +72,11 @@ cudaError_t launch_m1_spectrum(const M1Tensor* d_tens, const M1Net* d_nets, cons
 cudaError_t launch_m1_large(const M1Tensor* d_tens, const M1Net* d_nets, const int4* d_fft_items, int n_fft,
                             const int4* d_prod_items, int n_prod, const void* d_xs, const void* const* d_tws,
                             void* d_lspec, double* d_yrep, bool fp64, cudaStream_t s);
-// FP32 networks without open legs, 2^6 <= m = 2^log2m <= 2^10: one warp per item
-cudaError_t launch_m1_spectrum_warp(const M1Tensor* d_tens, const M1Net* d_nets, const int2* d_items, int n_items,
-                                    const void* d_xs, const void* const* d_tws, double* d_yrep, int log2m,
-                                    cudaStream_t s);
+// FP32 networks, 2^6 <= m = 2^log2m <= 2^10: one warp per item (open legs: spectra
+// stored to d_spec / d_sexp in the block kernel's layout)
+cudaError_t launch_m1_spectrum_warp(const M1Tensor* d_tens, const M1Net* d_nets, const OpenMode* d_opens,
+                                    const int2* d_items, int n_items, const void* d_xs, const void* const* d_tws,
+                                    void* d_spec, int* d_sexp, double* d_yrep, int log2m, cudaStream_t s);
 cudaError_t launch_combine(const CombineItem* d_items, int n_items, const double* d_yrep, cudaStream_t s);
 // measurement aid: random-bin FP32 shared-memory atomic adds per second (waits for s)
 cudaError_t run_probe_shared_atomics(float* sink, cudaStream_t s, double* updates_per_s);

@@ -1,6 +1,5 @@
-// m1_spectrum_warp.cu -- rows a3 + a4 of the hot path for FP32 networks without
-// open legs and 64 <= m <= 1024: one warp per (network, rep), every FFT held in
-// registers.
+// m1_spectrum_warp.cu -- rows a3 + a4 of the hot path for FP32 networks with
+// 64 <= m <= 1024: one warp per (network, rep), every FFT held in registers.
 //
 // y_r = (1/m) sum_j prod_k (F x_k)(j) (Alg. 1, last line). A real sketch x of
 // length m = 2M is transformed as z[n] = x[2n] + i x[2n+1] (M complex points)
@@ -19,6 +18,10 @@
 // back in order. As in the block kernel, each spectrum is scaled by 2^-e (e
 // from its largest component) before it enters the running product, and the
 // sum sum_j = X[0] + X[M] + 2 Re sum_{0<q<M} X[q] is taken in FP64.
+// Tensors with open legs (one sketch per open index, Corollary "full-to-partial-
+// tc") have their scaled spectra stored, in natural bin order with their
+// exponents (the block kernel's layout); every output entry is then the sum over
+// bins of the running product times one stored spectrum per open tensor.
 #include "fft.cuh"
 #include "kernels.cuh"
 
@@ -97,8 +100,9 @@ constexpr int kWarps = 8;
 template <int LOGJ>
 __global__ void __launch_bounds__(kWarps * 32, 2)
     m1_spectrum_warp_kernel(const M1Tensor* __restrict__ tens, const M1Net* __restrict__ nets,
-                            const int2* __restrict__ items, int n_items, const float* __restrict__ xs,
-                            const C32* const* __restrict__ tws, double* __restrict__ yrep) {
+                            const OpenMode* __restrict__ opens, const int2* __restrict__ items, int n_items,
+                            const float* __restrict__ xs, const C32* const* __restrict__ tws, C32* __restrict__ spec,
+                            int* __restrict__ sexp, double* __restrict__ yrep) {
     constexpr int J = 1 << LOGJ, LOGG = 5 - LOGJ, G = 1 << LOGG;
     constexpr int M = 32 * J, m = 2 * M;
     constexpr int S = 32 + (G & 15);  // row stride of the transpose buffer: conflict-free both ways
@@ -142,82 +146,148 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
     for (int k = 0; k < J; ++k) P[k] = {1.f, 0.f};
     float PM = 1.f;  // bin M (real), kept by lane 0
     int E = 0;       // P holds 2^-E prod_k F x_k
+    C32* Sb = spec + N.spec_off + (int64_t)r * N.spec_per_rep;
+    int* Eb = sexp + N.exp_off + (int64_t)r * N.exp_per_rep;
+    constexpr int K = M + 1;  // stored half spectrum: bins 0 .. M
     for (int t = 0; t < N.p; ++t) {
-        const C32* z = reinterpret_cast<const C32*>(xr + tens[N.t0 + t].xoff);  // 8-byte aligned
-        C32 v[J];
+        const M1Tensor& Tk = tens[N.t0 + t];
+        const int64_t nsk = Tk.soff < 0 ? 1 : Tk.O;
+        for (int64_t os = 0; os < nsk; ++os) {
+            const C32* z = reinterpret_cast<const C32*>(xr + Tk.xoff + os * m);  // 8-byte aligned
+            C32 v[J];
 #pragma unroll
-        for (int j = 0; j < J; ++j) v[j] = z[lane + 32 * j];
-        dft_reg<J>(v);
+            for (int j = 0; j < J; ++j) v[j] = z[lane + 32 * j];
+            dft_reg<J>(v);
 #pragma unroll
-        for (int k = 0; k < J; ++k) wb[k * S + lane] = cmul(v[k], twA[k][lane]);
-        __syncwarp();
+            for (int k = 0; k < J; ++k) wb[k * S + lane] = cmul(v[k], twA[k][lane]);
+            __syncwarp();
 #pragma unroll
-        for (int i = 0; i < J; ++i) v[i] = wb[k1L * S + gL + G * i];
-        __syncwarp();
-        dft_reg<J>(v);
+            for (int i = 0; i < J; ++i) v[i] = wb[k1L * S + gL + G * i];
+            __syncwarp();
+            dft_reg<J>(v);
 #pragma unroll
-        for (int k = 0; k < J; ++k) v[k] = cmul(v[k], twB[k][lane]);
+            for (int k = 0; k < J; ++k) v[k] = cmul(v[k], twB[k][lane]);
 #pragma unroll
-        for (int s = 0; s < LOGG; ++s) {
-            const int h = G >> (s + 1);
-            const bool up = (gL & h) != 0;
+            for (int s = 0; s < LOGG; ++s) {
+                const int h = G >> (s + 1);
+                const bool up = (gL & h) != 0;
+#pragma unroll
+                for (int k = 0; k < J; ++k) {
+                    const C32 o = shfl_xor_c(v[k], h);
+                    v[k] = up ? cmul(csub(o, v[k]), wst[s]) : cadd(v[k], o);
+                }
+            }
+            // real-FFT unpack: X[q] = (Z[q] + conj Z[M-q]) / 2 + W_m^q (Z[q] - conj Z[M-q]) / (2i)
+            C32 X[J];
 #pragma unroll
             for (int k = 0; k < J; ++k) {
-                const C32 o = shfl_xor_c(v[k], h);
-                v[k] = up ? cmul(csub(o, v[k]), wst[s]) : cadd(v[k], o);
+                const C32 send = k1L == 0 ? v[(J - k) & (J - 1)] : v[J - 1 - k];
+                const int src = k1L != 0 ? src_hi : (k != 0 ? G - 1 - gL : src_k0);
+                const C32 zc = cconj(shfl_c(send, src));
+                const C32 zk = v[k];
+                const C32 e = {(zk.x + zc.x) * 0.5f, (zk.y + zc.y) * 0.5f};
+                const C32 d = csub(zk, zc);
+                const C32 o = {d.y * 0.5f, -d.x * 0.5f};
+                X[k] = cadd(e, cmul(o, twC[k][lane]));
+            }
+            const float XM = v[0].x - v[0].y;  // meaningful in lane 0 only (q = 0 there)
+            float mx = lane == 0 ? fabsf(XM) : 0.f;
+#pragma unroll
+            for (int k = 0; k < J; ++k) mx = fmaxf(mx, fmaxf(fabsf(X[k].x), fabsf(X[k].y)));
+            // non-negative floats order like their bit patterns
+            const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+            int e = 0;
+            if (mb != 0u) frexpf(__uint_as_float(mb), &e);
+            const float sc = ldexpf(1.f, -e);
+            if (Tk.soff < 0) {
+#pragma unroll
+                for (int k = 0; k < J; ++k) P[k] = cmul(P[k], C32{X[k].x * sc, X[k].y * sc});
+                PM *= XM * sc;
+                E += e;
+            } else {  // an open index of an open tensor: keep its scaled spectrum
+                C32* dst = Sb + Tk.soff + os * K;
+#pragma unroll
+                for (int k = 0; k < J; ++k) dst[k1L + J * k + J * J * cL] = C32{X[k].x * sc, X[k].y * sc};
+                if (lane == 0) {
+                    dst[M] = C32{XM * sc, 0.f};
+                    Eb[Tk.eoff + os] = e;
+                }
             }
         }
-        // real-FFT unpack: X[q] = (Z[q] + conj Z[M-q]) / 2 + W_m^q (Z[q] - conj Z[M-q]) / (2i)
-        C32 X[J];
+    }
+    double* yr = yrep + N.y_off + (int64_t)r * N.O;
+    if (N.n_ot == 0) {
+        double acc = lane == 0 ? (double)PM : 0.0;
 #pragma unroll
         for (int k = 0; k < J; ++k) {
-            const C32 send = k1L == 0 ? v[(J - k) & (J - 1)] : v[J - 1 - k];
-            const int src = k1L != 0 ? src_hi : (k != 0 ? G - 1 - gL : src_k0);
-            const C32 zc = cconj(shfl_c(send, src));
-            const C32 zk = v[k];
-            const C32 e = {(zk.x + zc.x) * 0.5f, (zk.y + zc.y) * 0.5f};
-            const C32 d = csub(zk, zc);
-            const C32 o = {d.y * 0.5f, -d.x * 0.5f};
-            X[k] = cadd(e, cmul(o, twC[k][lane]));
+            const int q = k1L + J * k + J * J * cL;
+            acc += (q == 0 ? 1.0 : 2.0) * (double)P[k].x;
         }
-        const float XM = v[0].x - v[0].y;  // meaningful in lane 0 only (q = 0 there)
-        float mx = lane == 0 ? fabsf(XM) : 0.f;
 #pragma unroll
-        for (int k = 0; k < J; ++k) mx = fmaxf(mx, fmaxf(fabsf(X[k].x), fabsf(X[k].y)));
-        // non-negative floats order like their bit patterns
-        const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
-        int e = 0;
-        if (mb != 0u) frexpf(__uint_as_float(mb), &e);
-        const float sc = ldexpf(1.f, -e);
-#pragma unroll
-        for (int k = 0; k < J; ++k) P[k] = cmul(P[k], C32{X[k].x * sc, X[k].y * sc});
-        PM *= XM * sc;
-        E += e;
+        for (int sft = 16; sft > 0; sft >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sft);
+        if (lane == 0) yr[0] = ldexp(acc, E) / (double)m;
+        return;
     }
-    double acc = lane == 0 ? (double)PM : 0.0;
+    // open outputs: y(o) = (1/m) sum_j P(j) prod_sl S_sl[o_sl](j), each from the warp's
+    // own stored spectra
+    __threadfence_block();
+    __syncwarp();
+    for (int64_t o = 0; o < N.O; ++o) {
+        int64_t oo[TNSK_MAX_OPEN_TENSORS] = {0, 0, 0, 0};
+        for (int j = 0; j < N.n_open; ++j) {
+            const OpenMode om = opens[N.open0 + j];
+            const int64_t digit = (o / om.ostride) % om.dim;
 #pragma unroll
-    for (int k = 0; k < J; ++k) {
-        const int q = k1L + J * k + J * J * cL;
-        acc += (q == 0 ? 1.0 : 2.0) * (double)P[k].x;
+            for (int sl = 0; sl < TNSK_MAX_OPEN_TENSORS; ++sl)
+                if (sl == om.slot) oo[sl] += digit * om.tstride;
+        }
+        const C32* sp[TNSK_MAX_OPEN_TENSORS];
+        int Eo = E;
+#pragma unroll
+        for (int sl = 0; sl < TNSK_MAX_OPEN_TENSORS; ++sl) {
+            sp[sl] = nullptr;
+            if (sl < N.n_ot) {
+                const M1Tensor& Tt = tens[N.ot[sl]];
+                sp[sl] = Sb + Tt.soff + oo[sl] * K;
+                Eo += Eb[Tt.eoff + oo[sl]];
+            }
+        }
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < J; ++k) {
+            const int q = k1L + J * k + J * J * cL;
+            C32 v = P[k];
+#pragma unroll
+            for (int sl = 0; sl < TNSK_MAX_OPEN_TENSORS; ++sl)
+                if (sl < N.n_ot) v = cmul(v, sp[sl][q]);
+            acc += (q == 0 ? 1.0 : 2.0) * (double)v.x;
+        }
+        if (lane == 0) {
+            float vM = PM;
+#pragma unroll
+            for (int sl = 0; sl < TNSK_MAX_OPEN_TENSORS; ++sl)
+                if (sl < N.n_ot) vM *= sp[sl][M].x;
+            acc += (double)vM;
+        }
+#pragma unroll
+        for (int sft = 16; sft > 0; sft >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sft);
+        if (lane == 0) yr[o] = ldexp(acc, Eo) / (double)m;
     }
-#pragma unroll
-    for (int sft = 16; sft > 0; sft >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sft);
-    if (lane == 0) yrep[N.y_off + r] = ldexp(acc, E) / (double)m;
 }
 
-cudaError_t launch_m1_spectrum_warp(const M1Tensor* d_tens, const M1Net* d_nets, const int2* d_items, int n_items,
-                                    const void* d_xs, const void* const* d_tws, double* d_yrep, int log2m,
-                                    cudaStream_t s) {
+cudaError_t launch_m1_spectrum_warp(const M1Tensor* d_tens, const M1Net* d_nets, const OpenMode* d_opens,
+                                    const int2* d_items, int n_items, const void* d_xs, const void* const* d_tws,
+                                    void* d_spec, int* d_sexp, double* d_yrep, int log2m, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((n_items + kWarps - 1) / kWarps);
     const float* xs = (const float*)d_xs;
     const C32* const* tws = (const C32* const*)d_tws;
     switch (log2m) {
-        case 6: m1_spectrum_warp_kernel<0><<<blocks, kWarps * 32, 0, s>>>(d_tens, d_nets, d_items, n_items, xs, tws, d_yrep); break;
-        case 7: m1_spectrum_warp_kernel<1><<<blocks, kWarps * 32, 0, s>>>(d_tens, d_nets, d_items, n_items, xs, tws, d_yrep); break;
-        case 8: m1_spectrum_warp_kernel<2><<<blocks, kWarps * 32, 0, s>>>(d_tens, d_nets, d_items, n_items, xs, tws, d_yrep); break;
-        case 9: m1_spectrum_warp_kernel<3><<<blocks, kWarps * 32, 0, s>>>(d_tens, d_nets, d_items, n_items, xs, tws, d_yrep); break;
-        case 10: m1_spectrum_warp_kernel<4><<<blocks, kWarps * 32, 0, s>>>(d_tens, d_nets, d_items, n_items, xs, tws, d_yrep); break;
+        case 6: m1_spectrum_warp_kernel<0><<<blocks, kWarps * 32, 0, s>>>(d_tens, d_nets, d_opens, d_items, n_items, xs, tws, (C32*)d_spec, d_sexp, d_yrep); break;
+        case 7: m1_spectrum_warp_kernel<1><<<blocks, kWarps * 32, 0, s>>>(d_tens, d_nets, d_opens, d_items, n_items, xs, tws, (C32*)d_spec, d_sexp, d_yrep); break;
+        case 8: m1_spectrum_warp_kernel<2><<<blocks, kWarps * 32, 0, s>>>(d_tens, d_nets, d_opens, d_items, n_items, xs, tws, (C32*)d_spec, d_sexp, d_yrep); break;
+        case 9: m1_spectrum_warp_kernel<3><<<blocks, kWarps * 32, 0, s>>>(d_tens, d_nets, d_opens, d_items, n_items, xs, tws, (C32*)d_spec, d_sexp, d_yrep); break;
+        case 10: m1_spectrum_warp_kernel<4><<<blocks, kWarps * 32, 0, s>>>(d_tens, d_nets, d_opens, d_items, n_items, xs, tws, (C32*)d_spec, d_sexp, d_yrep); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -499,8 +499,9 @@ cudaError_t launch_m1_spectra(const BatchPlan& plan, unsigned char* base, const 
                                        plan.m1.n_items, xs, tws, base + plan.m1.spec_off,
                                        (int*)(base + plan.m1.sexp_off), yrep, fp64, plan.m1.max_log2m, s);
     for (int sl = 0; sl < M1Plan::kWarpSlots && e == cudaSuccess; ++sl)
-        e = launch_m1_spectrum_warp(tens, nets, items + plan.m1.warp_first[sl], plan.m1.warp_count[sl], xs, tws, yrep,
-                                    6 + sl, s);
+        e = launch_m1_spectrum_warp(tens, nets, (const OpenMode*)(base + plan.m1.opens_off),
+                                    items + plan.m1.warp_first[sl], plan.m1.warp_count[sl], xs, tws,
+                                    base + plan.m1.spec_off, (int*)(base + plan.m1.sexp_off), yrep, 6 + sl, s);
     if (e == cudaSuccess)
         e = launch_m1_large(tens, nets, (const int4*)(base + plan.m1.lfft_off), plan.m1.n_lfft,
                             (const int4*)(base + plan.m1.lprod_off), plan.m1.n_lprod, xs, tws,

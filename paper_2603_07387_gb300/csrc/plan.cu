@@ -533,8 +533,8 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                         lprod.push_back(make_int4((int)m1n.size(), r, (int)j0, (int)std::min<int64_t>(4096, m - j0)));
                 }
             } else if (!sketch_only && I.O > 0) {
-                // FP32, no open legs, 2^6 <= m <= 2^10: the warp-per-item spectrum kernel
-                const bool warp_path = !fp64 && I.O == 1 && nb.n_ot == 0 && I.log2m >= 6 && I.log2m <= 10;
+                // FP32, 2^6 <= m <= 2^10: the warp-per-item spectrum kernel
+                const bool warp_path = !fp64 && I.log2m >= 6 && I.log2m <= 10;
                 std::vector<int2>& dst = warp_path ? m1warp[I.log2m - 6] : m1items;
                 // the block kernel's shared memory is sized by the largest m it runs
                 if (!warp_path) max_log2m1 = std::max(max_log2m1, I.log2m);
