@@ -161,7 +161,8 @@ typedef enum {
     TNSK_K_M2_ROOT = 7,     /* method 2 root inner products (a8) */
     TNSK_K_COMBINE = 8,     /* median of group means (a9) */
     TNSK_K_M2_SCATTER = 9,  /* method 2 count-sketch scatter of the product rows (a7) */
-    TNSK_KERNEL_KINDS = 10
+    TNSK_K_PAIRS = 10,      /* exact pair contractions (tnsk_pairs_run) */
+    TNSK_KERNEL_KINDS = 11
 } tnsk_kernel_kind;
 tnsk_status tnsk_profile(tnsk_ctx* ctx, int32_t enable);
 tnsk_status tnsk_profile_read(tnsk_ctx* ctx, double* ms, int64_t* launches);
@@ -210,6 +211,37 @@ tnsk_status tnsk_estimate_static(const tnsk_network* net, const tnsk_params* par
  * SM over all SMs: full occupancy), the ceiling of privatised scatter-add. Runs on the ctx
  * stream, waits for it, and writes updates per second to *updates_per_s. */
 tnsk_status tnsk_probe_shared_atomics(tnsk_ctx* ctx, double* updates_per_s);
+
+/* ---- Exact contraction of pairs of tensors (the normalisations of Sec. 4.1:
+ * group two tensors into one with their shared contractions summed exactly; a
+ * cyclic ladder of two tensor trains becomes an acyclic chain this way). For each
+ * job: out[i] = sum over the shared indices of A[...] * B[...], where the shared
+ * modes are the pairs (a_modes[j], b_modes[j]), j < n_shared (equal dims); the
+ * other modes of A (in order), then of B (in order), are the free modes
+ * 0 .. n_free - 1, and output mode i is free mode out_perm[i] (out_perm NULL =
+ * identity). out: device FP32, row-major, caller-owned; A, B: device tensors
+ * (FP32 / FP64 / BF16). FP32 products summed in FP32.
+ * tnsk_pairs_create validates the n jobs (n <= 65535) and uploads their
+ * descriptors once (device memory owned by the handle); each tnsk_pairs_run
+ * enqueues one launch for all of them on the ctx stream (new data in the same
+ * buffers is picked up). tnsk_contract_pairs = create + run + wait + destroy.
+ * Errors: TNSK_ERR_INVALID for NULL pointers, bad modes (out of range, repeated,
+ * unequal dims) or a bad permutation; TNSK_ERR_UNSUPPORTED above 2^31 output
+ * entries or 2^20 shared index combinations per job. */
+typedef struct {
+    const tnsk_tensor* A;
+    const tnsk_tensor* B;
+    int32_t n_shared;
+    const int32_t* a_modes;
+    const int32_t* b_modes;
+    const int32_t* out_perm;
+    float* out;
+} tnsk_pair_job;
+typedef struct tnsk_pairs tnsk_pairs;
+tnsk_status tnsk_pairs_create(tnsk_ctx* ctx, int32_t n, const tnsk_pair_job* jobs, tnsk_pairs** pairs);
+tnsk_status tnsk_pairs_run(tnsk_ctx* ctx, tnsk_pairs* pairs);
+tnsk_status tnsk_pairs_destroy(tnsk_pairs* pairs);
+tnsk_status tnsk_contract_pairs(tnsk_ctx* ctx, int32_t n, const tnsk_pair_job* jobs);
 
 /* ---- Learned sketch-size predictor (the paper has no counterpart: it sizes m
  * by its variance bounds). A multilayer perceptron TNSK_MLP_FEATURES -> 128 ->

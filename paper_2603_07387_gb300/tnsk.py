@@ -30,7 +30,7 @@ STATUS = {
 F64, F32, BF16 = 0, 1, 2
 GENERAL, ACYCLIC = 1, 2
 KERNEL_KINDS = ("tables", "m1_scatter", "m1_spectrum", "m2_leaf", "m2_compose", "m2_vbuild", "m2_gemm",
-                "m2_root", "combine", "m2_scatter")
+                "m2_root", "combine", "m2_scatter", "pairs")
 PREC_FP32, PREC_FP64 = 0, 2
 
 # exported symbols declared in include/tnsk.h
@@ -62,6 +62,10 @@ SYMBOLS = (
     "tnsk_mlp_save",
     "tnsk_mlp_load",
     "tnsk_features",
+    "tnsk_pairs_create",
+    "tnsk_pairs_run",
+    "tnsk_pairs_destroy",
+    "tnsk_contract_pairs",
     "tnsk_choose_params",
     "tnsk_status_string",
     "tnsk_last_error",
@@ -162,6 +166,10 @@ def load_library(path: str = LIB_PATH):
         ("tnsk_mlp_save", [vp, ctypes.c_char_p]),
         ("tnsk_mlp_load", [vp, vp, ctypes.c_char_p]),
         ("tnsk_features", [vp, ctypes.POINTER(_Network), ctypes.POINTER(_Params), f32p]),
+        ("tnsk_pairs_create", [vp, i32, vp, ctypes.POINTER(vp)]),
+        ("tnsk_pairs_run", [vp, vp]),
+        ("tnsk_pairs_destroy", [vp]),
+        ("tnsk_contract_pairs", [vp, i32, vp]),
         ("tnsk_choose_params", [vp, ctypes.POINTER(_Network), ctypes.c_double, vp, ctypes.POINTER(_Params), dp]),
     ]:
         getattr(L, name).restype = i32
@@ -284,6 +292,73 @@ class Plan:
 
 
 MLP_FEATURES = 9
+
+
+class _PairJob(ctypes.Structure):
+    _fields_ = [
+        ("A", ctypes.c_void_p),
+        ("B", ctypes.c_void_p),
+        ("n_shared", ctypes.c_int32),
+        ("a_modes", ctypes.POINTER(ctypes.c_int32)),
+        ("b_modes", ctypes.POINTER(ctypes.c_int32)),
+        ("out_perm", ctypes.POINTER(ctypes.c_int32)),
+        ("out", ctypes.c_void_p),
+    ]
+
+
+def _tensor(t):
+    """A one-element tnsk_tensor array for a torch device tensor (keeps its dims alive)."""
+    dims = (ctypes.c_int64 * max(1, t.dim()))(*t.shape)
+    arr = (_Tensor * 1)()
+    arr[0].order = t.dim()
+    arr[0].dims = ctypes.cast(dims, ctypes.POINTER(ctypes.c_int64))
+    arr[0].data = t.data_ptr()
+    arr[0].dtype = _dtype_code(t)
+    arr._dims = dims
+    return arr
+
+
+class _PairJobs:
+    """Owns the ctypes structures behind an array of tnsk_pair_job. A job is
+    (A, B, a_modes, b_modes, out_perm or None, out) with torch device tensors."""
+
+    def __init__(self, jobs):
+        self.keep = []
+        arr = (_PairJob * max(1, len(jobs)))()
+        for i, (A, B, am, bm, perm, out) in enumerate(jobs):
+            ta, tb = _tensor(A), _tensor(B)
+            am_c = (ctypes.c_int32 * max(1, len(am)))(*am)
+            bm_c = (ctypes.c_int32 * max(1, len(bm)))(*bm)
+            pm_c = (ctypes.c_int32 * max(1, len(perm)))(*perm) if perm is not None else None
+            self.keep += [ta, tb, am_c, bm_c, pm_c]
+            arr[i].A = ctypes.addressof(ta[0])
+            arr[i].B = ctypes.addressof(tb[0])
+            arr[i].n_shared = len(am)
+            arr[i].a_modes = ctypes.cast(am_c, ctypes.POINTER(ctypes.c_int32))
+            arr[i].b_modes = ctypes.cast(bm_c, ctypes.POINTER(ctypes.c_int32))
+            arr[i].out_perm = ctypes.cast(pm_c, ctypes.POINTER(ctypes.c_int32)) if pm_c is not None else None
+            arr[i].out = out.data_ptr()
+        self.arr, self.n = arr, len(jobs)
+
+
+class Pairs:
+    """tnsk_pairs: exact pair contractions validated once, one launch per run()."""
+
+    def __init__(self, ctx: "Context", jobs):
+        self.ctx, self.lib = ctx, ctx.lib
+        self._jobs = _PairJobs(jobs)
+        h = ctypes.c_void_p()
+        ctx._check(self.lib.tnsk_pairs_create(ctx.h, self._jobs.n, ctypes.addressof(self._jobs.arr),
+                                              ctypes.byref(h)))
+        self.h = h
+
+    def run(self):
+        self.ctx._check(self.lib.tnsk_pairs_run(self.ctx.h, self.h))
+
+    def close(self):
+        if self.h is not None:
+            self.lib.tnsk_pairs_destroy(self.h)
+            self.h = None
 
 
 class Mlp:
@@ -413,6 +488,15 @@ class Context:
             rarr = (ctypes.c_void_p * max(1, B))(*[(r.data_ptr() if r is not None else None) for r in per_reps])
         self._check(self.lib.tnsk_estimate_batch(self.h, B, carr, parr, oarr, rarr))
         return holders  # callers may keep them alive until the stream completes
+
+    def pairs(self, jobs) -> "Pairs":
+        """tnsk_pairs_create: jobs of (A, B, a_modes, b_modes, out_perm or None, out)."""
+        return Pairs(self, jobs)
+
+    def contract_pairs(self, jobs):
+        """tnsk_contract_pairs: the jobs once (waits for them)."""
+        j = _PairJobs(jobs)
+        self._check(self.lib.tnsk_contract_pairs(self.h, j.n, ctypes.addressof(j.arr)))
 
     def plan(self, nets: Sequence[Network], params: Sequence[Params], outs, per_reps=None) -> "Plan":
         """tnsk_plan_create: plan a batch once; run it with Plan.run()."""

@@ -454,3 +454,45 @@ def test_errors_are_reported(ctx):
         ctx.estimate(net, tnsk.Params(m=8, reps=5, groups=2), out)
     assert e.value.status == -1
     ctx.sync()
+
+
+# ---------------------------------------------------------------- exact pair contractions
+def test_contract_pairs_match_the_exact_oracle(ctx):
+    """tnsk_pairs: the tensor-train rung merge (M[a,b,c,d] = sum_s A[a,s,c] B[b,s,d]) at
+    the bench's shapes, end sites, a pair sharing two modes, permuted outputs, FP64 /
+    BF16 inputs (general path), a long last output mode."""
+    rng = np.random.default_rng(61)
+    cases = []
+    cases.append((rng.standard_normal((32, 8, 32)), rng.standard_normal((32, 8, 32)), [1], [1], [0, 2, 1, 3],
+                  torch.float32))
+    cases.append((rng.standard_normal((6, 3, 5)), rng.standard_normal((4, 3, 7)), [1], [1], [0, 2, 1, 3],
+                  torch.float32))
+    cases.append((rng.standard_normal((3, 6)), rng.standard_normal((3, 4)), [0], [0], None, torch.float32))
+    cases.append((rng.standard_normal((2, 5, 3)), rng.standard_normal((3, 2, 4)), [0, 2], [1, 0], [1, 0],
+                  torch.float64))
+    cases.append((rng.standard_normal((5, 4)), rng.standard_normal((6,)), [], [], [2, 0, 1], torch.bfloat16))
+    cases.append((rng.standard_normal((3, 8, 4)), rng.standard_normal((8, 70)), [1], [0], None, torch.float32))
+    jobs, wants = [], []
+    for A, B, am, bm, perm, dt in cases:
+        Ad = torch.as_tensor(A).to(dt).cuda()
+        Bd = torch.as_tensor(B).to(dt).cuda()
+        Ar, Br = Ad.double().cpu().numpy(), Bd.double().cpu().numpy()
+        na = Ar.ndim
+        edges = [(a, na + b) for a, b in zip(am, bm)]
+        free = [g for g in range(na) if g not in am] + [na + g for g in range(Br.ndim) if g not in bm]
+        order = [free[i] for i in (perm if perm is not None else range(len(free)))]
+        want = np.asarray(oracle.tc_einsum([Ar, Br], edges, order))
+        out = torch.zeros(want.shape, dtype=torch.float32, device="cuda")
+        jobs.append((Ad, Bd, am, bm, perm, out))
+        terms = max(1, int(np.prod([Ar.shape[a] for a in am])))
+        wants.append((want, float(np.abs(Ar).max() * np.abs(Br).max() * terms)))
+    pr = ctx.pairs(jobs)
+    for _ in range(2):  # a second run writes the same values
+        pr.run()
+        ctx.sync()
+        for (A, B, am, bm, perm, out), (want, scale) in zip(jobs, wants):
+            assert out.shape == want.shape
+            assert np.allclose(out.cpu().numpy(), want, rtol=1e-5, atol=1e-6 * scale)
+    pr.close()
+    with pytest.raises(tnsk.TnskError):  # unequal shared dims
+        ctx.contract_pairs([(jobs[1][0], jobs[1][1], [0], [0], None, jobs[1][5])])
