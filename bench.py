@@ -6,10 +6,12 @@ Workload (per GPU, per step): B = 64 pairs of tensor trains (8 sites, bond 32,
 physical 8, N(0, 1/sqrt(32)) entries, FP32). Every pair's inner product is
 estimated by both of the paper's methods at m = 1024 with 64 repetitions:
   * method 2 (Sec. 4.4, acyclic) on the chain obtained by summing each site's
-    physical leg and merging its two bonds (8 tensors: 1024, 6 x 1024x1024, 1024);
-    this is the estimate that meets the 5% error target;
+    physical leg and merging its two bonds (8 tensors: 1024, 6 x 1024x1024, 1024),
+    made on the GPU every step from the cores by exact pair contractions
+    (tnsk_pairs); this is the estimate that meets the 5% error target;
   * method 1 (Sec. 4.2, any network) on the cyclic ladder (16 tensors, t = 22).
-One step = one run of a planned batch (tnsk_plan_run) over the 2B networks: every
+The inputs are the cores (25 MB per GPU). One step = the rung merge (one
+tnsk_pairs_run) and one run of a planned batch (tnsk_plan_run) over the 2B networks: every
 hot-path row (tables, scatter, FFT/product, leaf/compose/V/GEMM/root, combine)
 runs on the GPU each step; only the host-side validation and descriptor upload
 are done once, when the batch is planned. `value` counts
@@ -79,13 +81,23 @@ def dist_setup(args):
 
 
 def make_pairs(B, rank):
+    """B pairs of tensor trains: (cores of train A, cores of train B, their ladder)."""
     from paper_2603_07387_gb300 import workloads as W
 
     pairs = []
     for i in range(B):
         A, Bc = W.tt_cores(seed=W.DATA_SEED + 100003 * rank + i)
-        pairs.append((W.tt_ladder(A, Bc), W.tt_chain(A, Bc)))
+        pairs.append((A, Bc, W.tt_ladder(A, Bc)))
     return pairs
+
+
+def chain_edges(sites: int):
+    """Contractions of the merged chain (vector, sites-2 matrices, vector): the last mode
+    of site k with the first mode of site k+1."""
+    off = [0]
+    for k in range(sites):
+        off.append(off[-1] + (1 if k in (0, sites - 1) else 2))
+    return [(off[k + 1] - 1, off[k + 1]) for k in range(sites - 1)]
 
 
 # ---------------------------------------------------------------- clocks
@@ -177,12 +189,15 @@ def run_ours(args, world, rank, local):
     # every input tensor is a 16-byte aligned view into one flat FP32 buffer, so a
     # step's inputs move host -> device in one copy; two device buffers (and one plan
     # per buffer) let the end-to-end loop copy step k+1 while step k computes
+    # The inputs are the tensor-train cores (the ladders' tensors). The merged chain of
+    # each pair (vector, six 1024 x 1024 matrices, vector) is made on the device every
+    # step by exact pair contractions (tnsk_pairs: M_k[a,b,c,d] = sum_s A_k[a,s,c] B_k[b,s,d]).
+    sites = len(pairs[0][0])
+    bond = pairs[0][0][1].shape[0]
     specs, params, host_ts = [], [], []
-    for ladder, chain in pairs:
-        for spec, method in ((ladder, tnsk.GENERAL), (chain, tnsk.ACYCLIC)):
-            specs.append(spec)
-            params.append(tnsk.Params(m=M, reps=REPS, seed=W.HASH_SEED, method=method))
-            host_ts.append(W.to_torch(spec, "cpu", torch.float32))
+    for A, Bc, ladder in pairs:
+        specs.append(ladder)
+        host_ts.append(W.to_torch(ladder, "cpu", torch.float32))
     offs, total = [], 0
     for ts in host_ts:
         offs.append([])
@@ -197,23 +212,48 @@ def run_ours(args, world, rank, local):
     flat_dev = [torch.empty(total, dtype=torch.float32, device=dev) for _ in range(2)]
     for fd in flat_dev:
         fd.copy_(flat_host)
-    nets_b, outs_b, out_flat = [], [], []
+    ctx = tnsk.Context(local, stream.cuda_stream)
+    cedges = chain_edges(sites)
+    nets_b, outs_b, out_flat, jobs_b = [], [], [], []
     for fd in flat_dev:
-        nb = []
+        nb, jobs = [], []
         for spec, ts, os_ in zip(specs, host_ts, offs):
             views = [fd[o:o + t.numel()].view(t.shape) for t, o in zip(ts, os_)]
             nb.append(tnsk.Network(views, spec.edges, spec.open))
+            mats = []
+            for k in range(sites):
+                Ak, Bk = views[k], views[sites + k]
+                if k == 0:  # [s, a] x [s, b] -> [a, b]
+                    out = torch.empty((bond * bond,), dtype=torch.float32, device=dev)
+                    jobs.append((Ak, Bk, [0], [0], None, out.view(bond, bond)))
+                elif k == sites - 1:  # [a, s] x [b, s] -> [a, b]
+                    out = torch.empty((bond * bond,), dtype=torch.float32, device=dev)
+                    jobs.append((Ak, Bk, [1], [1], None, out.view(bond, bond)))
+                else:  # [a, s, c] x [b, s, d] -> [a, b, c, d]
+                    out = torch.empty((bond * bond, bond * bond), dtype=torch.float32, device=dev)
+                    jobs.append((Ak, Bk, [1], [1], [0, 2, 1, 3], out.view(bond, bond, bond, bond)))
+                mats.append(out)
+            nb.append(tnsk.Network(mats, cedges, []))
         nets_b.append(nb)
-        of = torch.zeros(len(specs), dtype=torch.float64, device=dev)
+        jobs_b.append(jobs)
+        of = torch.zeros(2 * len(specs), dtype=torch.float64, device=dev)
         out_flat.append(of)
-        outs_b.append([of[i:i + 1] for i in range(len(specs))])
+        outs_b.append([of[i:i + 1] for i in range(2 * len(specs))])
+    for _ in specs:
+        params.append(tnsk.Params(m=M, reps=REPS, seed=W.HASH_SEED, method=tnsk.GENERAL))
+        params.append(tnsk.Params(m=M, reps=REPS, seed=W.HASH_SEED, method=tnsk.ACYCLIC))
     nets, outs = nets_b[0], outs_b[0]
-    ctx = tnsk.Context(local, stream.cuda_stream)
-    # plan once per buffer (validation, layout, descriptor upload); a step runs the whole batch
+    # merge jobs and plans once per buffer (validation, layout, descriptor upload); a step
+    # merges the rungs and runs the whole batch
+    merges = [ctx.pairs(j) for j in jobs_b]
+    for mg in merges:
+        mg.run()
+    ctx.sync()
     plans = [ctx.plan(nb, params, ob) for nb, ob in zip(nets_b, outs_b)]
-    plan = plans[0]
+    plan, merge = plans[0], merges[0]
 
     def step():
+        merge.run()
         plan.run()
 
     for _ in range(max(args.warmup, 2)):  # run 1 launches directly, run 2 captures the graph
@@ -274,7 +314,7 @@ def run_ours(args, world, rank, local):
 
     # ---------------- rooflines: the dominant kernel (largest share of device time) first
     total_ms = sum(v[0] for v in prof.values())
-    m1_entries = sum(int(np.prod(np.shape(x))) for sp in specs[0::2] for x in sp.tensors)  # ladders
+    m1_entries = sum(int(np.prod(np.shape(x))) for sp in specs for x in sp.tensors)  # ladders
     units = {
         # one launch per step: every entry of every ladder tensor, once per rep
         "m1_scatter": {"bound": "alu", "per_launch": REPS * m1_entries, "unit": "Gupdates/s",
@@ -287,6 +327,10 @@ def run_ours(args, world, rank, local):
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
                     "what": "bytes of X_k read per launch (each interior matrix once for all 64 reps)"},
         # one launch per step: every ladder sketch (reps x 16 tensors x m FP32) read once
+        # one launch per step: every merged chain written once
+        "pairs": {"bound": "hbm", "per_launch": B * ((sites - 2) * bond ** 4 + 2 * bond ** 2) * 4, "unit": "GB/s",
+                  "peak": hbm_peak(), "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
+                  "what": "bytes of the merged chains written per launch"},
         "m1_spectrum": {"bound": "hbm", "per_launch": B * REPS * 16 * M * 4, "unit": "GB/s", "peak": hbm_peak(),
                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
                         "what": "sketch bytes read per launch"},
@@ -322,7 +366,7 @@ def run_ours(args, world, rank, local):
     # the step that read it has finished.
     e2e = None
     if not args.no_e2e:
-        host_out = [torch.zeros(len(specs), dtype=torch.float64).pin_memory() for _ in range(2)]
+        host_out = [torch.zeros(2 * len(specs), dtype=torch.float64).pin_memory() for _ in range(2)]
         copy_stream = torch.cuda.Stream(dev)
         copied = [torch.cuda.Event() for _ in range(2)]
         done = [torch.cuda.Event() for _ in range(2)]
@@ -336,6 +380,7 @@ def run_ours(args, world, rank, local):
                     flat_dev[b].copy_(flat_host, non_blocking=True)
                     copied[b].record(copy_stream)
                 stream.wait_event(copied[b])
+                merges[b].run()
                 plans[b].run()
                 host_out[b].copy_(out_flat[b], non_blocking=True)
                 done[b].record(stream)
@@ -362,7 +407,7 @@ def run_ours(args, world, rank, local):
     probe = hbm_sketch_probe(ctx, dev) if (rank == 0 and not args.no_hbm_probe) else None
     lvp = learned_vs_plain(ctx, dev) if (rank == 0 and not args.no_learned) else None
     unev = batched_uneven(ctx, dev) if (rank == 0 and not args.no_uneven) else None
-    for p_ in plans:
+    for p_ in plans + merges:
         p_.close()
     ctx.close()
     if rank != 0:
@@ -654,7 +699,10 @@ def cpu_baseline(pair, budget_s: float = 12.0):
     (64 reps of each method)."""
     import oracle
 
-    ladder, chain = pair
+    from paper_2603_07387_gb300 import workloads as W
+
+    A, Bc, ladder = pair
+    chain = W.tt_chain(A, Bc)
     X2 = [np.asarray(x, dtype=np.float32).astype(np.float64) for x in chain.tensors]
     X1 = [np.asarray(x, dtype=np.float32).astype(np.float64) for x in ladder.tensors]
     root = int(np.argmin([x.size for x in X2]))
@@ -679,8 +727,10 @@ def run_reference(args, world, rank):
         return
     import oracle
 
-    pairs = make_pairs(1, 0)
-    ladder, chain = pairs[0]
+    from paper_2603_07387_gb300 import workloads as W
+
+    A, Bc, ladder = make_pairs(1, 0)[0]
+    chain = W.tt_chain(A, Bc)
     X2 = [np.asarray(x, dtype=np.float32).astype(np.float64) for x in chain.tensors]
     X1 = [np.asarray(x, dtype=np.float32).astype(np.float64) for x in ladder.tensors]
     root = int(np.argmin([x.size for x in X2]))
