@@ -113,7 +113,7 @@ __device__ __forceinline__ void rows_same_b_v4(const float* __restrict__ A, cons
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) contract_pairs_kernel(const PairDesc* __restrict__ jobs) {
+__global__ void __launch_bounds__(256, 4) contract_pairs_kernel(const PairDesc* __restrict__ jobs) {
     __shared__ PairDesc d;
     __shared__ int2 tab[kShTable];  // (A, B) offsets of the shared combinations, 32-bit path
     {  // the job's descriptor, copied by the whole block
