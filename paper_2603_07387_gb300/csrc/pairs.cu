@@ -76,43 +76,45 @@ __device__ __forceinline__ void rows_same_b(const float* __restrict__ A, const f
 
 // The same rows when the last output mode runs along B only (la = 0, lb = 1) with
 // 4 <= L <= 32, L % 4 == 0: 8 lanes per row, 4 consecutive columns per lane (16-byte
-// stores), 8 rows per pass of the warp.
+// stores), 4 rows per pass of the warp. The A terms do not depend on the column: lane
+// i loads row base + i's NS terms once, and each row takes them by shuffle, so no
+// load waits inside the row loop.
 template <int NS>
 __device__ __forceinline__ void rows_same_b_v4(const float* __restrict__ A, const float* __restrict__ B,
                                                float* __restrict__ out, const int2* __restrict__ tab, int ra,
                                                int rb, int L, int nr, int base, int lane) {
     const int r4 = lane >> 3, c = (lane & 7) * 4;
     const bool live = c < L;
-    int ta[NS];
+    float av[NS];
     float bv[NS][4];
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
         const int2 t = tab[q];
-        ta[q] = t.x;
+        av[q] = lane < nr ? __ldg(A + ra + t.x) : 0.f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) bv[q][j] = live ? __ldg(B + rb + c + j + t.y) : 0.f;
     }
-    for (int i = 0; i < nr; i += 8) {
+    for (int i = 0; i < nr; i += 4) {
+        const int row = i + r4;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int row = i + 4 * h + r4;
-            const int pa = __shfl_sync(0xffffffffu, ra, min(row, nr - 1));
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int q = 0; q < NS; ++q) {
+            const float a = __shfl_sync(0xffffffffu, av[q], row & 31);
 #pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                const float a = __ldg(A + pa + ta[q]);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[j] += a * bv[q][j];
-            }
-            if (live && row < nr)
-                *reinterpret_cast<float4*>(out + (int64_t)(base + row) * L + c) =
-                    make_float4(acc[0], acc[1], acc[2], acc[3]);
+            for (int j = 0; j < 4; ++j) acc[j] += a * bv[q][j];
         }
+        if (live && row < nr)
+            *reinterpret_cast<float4*>(out + (int64_t)(base + row) * L + c) =
+                make_float4(acc[0], acc[1], acc[2], acc[3]);
     }
 }
 
 }  // namespace
 
+// kFast: the jobs that take the 32-bit FP32 path (fast flag, at most kShTable shared
+// combinations); otherwise the rest. The two are separate kernels so the general
+// path's 64-bit state does not raise the fast path's register count.
+template <bool kFast>
 __global__ void __launch_bounds__(256, 4) contract_pairs_kernel(const PairDesc* __restrict__ jobs) {
     __shared__ PairDesc d;
     __shared__ int2 tab[kShTable];  // (A, B) offsets of the shared combinations, 32-bit path
@@ -124,6 +126,7 @@ __global__ void __launch_bounds__(256, 4) contract_pairs_kernel(const PairDesc* 
     __syncthreads();
     const int64_t nsh = d.sh_numel;
     const bool fast = d.fast && nsh <= kShTable;
+    if (fast != kFast) return;
     auto shared_offsets = [&](int64_t s, int64_t& sa, int64_t& sb) {
         sa = sb = 0;
         for (int j = d.n_sh - 1; j >= 0; --j) {
@@ -134,7 +137,7 @@ __global__ void __launch_bounds__(256, 4) contract_pairs_kernel(const PairDesc* 
             sb += dj * d.b_sh_str[j];
         }
     };
-    if (fast)
+    if (kFast)
         for (int64_t q = threadIdx.x; q < nsh; q += blockDim.x) {
             int64_t sa, sb;
             shared_offsets(q, sa, sb);
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(256, 4) contract_pairs_kernel(const PairDesc* 
     __syncthreads();
     if (d.out_numel == 0) return;
     const int lane = threadIdx.x & 31;
-    if (fast) {
+    if constexpr (kFast) {
         const float* __restrict__ A = static_cast<const float*>(d.A);
         const float* __restrict__ B = static_cast<const float*>(d.B);
         const int last = d.n_out - 1;
@@ -206,8 +209,7 @@ __global__ void __launch_bounds__(256, 4) contract_pairs_kernel(const PairDesc* 
                 }
             }
         }
-        return;
-    }
+    } else {
     // general path: any dtype, 64-bit offsets, the shared combinations decoded per term
     const int last = d.n_out - 1;
     const int64_t L = last >= 0 ? d.out_dim[last] : 1;
@@ -234,6 +236,7 @@ __global__ void __launch_bounds__(256, 4) contract_pairs_kernel(const PairDesc* 
             d.out[row * L + x] = acc;
         }
     }
+    }
 }
 
 }  // namespace tnsk
@@ -242,7 +245,9 @@ using namespace tnsk;
 
 struct tnsk_pairs {
     int device = 0;
+    int sms = 1;
     int n = 0;
+    bool any_fast = false, any_general = false;
     PairDesc* dev = nullptr;
     std::vector<int64_t> sizes;
 };
@@ -336,8 +341,15 @@ tnsk_status tnsk_pairs_create(tnsk_ctx* ctx, int32_t n, const tnsk_pair_job* job
     }
     tnsk_pairs* p = new tnsk_pairs();
     p->device = ctx->device;
+    cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    p->sms = std::max(p->sms, 1);
     p->n = n;
-    for (const PairDesc& d : h) p->sizes.push_back(d.out_numel);
+    for (const PairDesc& d : h) {
+        p->sizes.push_back(d.out_numel);
+        const bool fast = d.fast && d.sh_numel <= kShTable;
+        p->any_fast |= fast;
+        p->any_general |= !fast;
+    }
     if (n > 0) {
         if (cudaMalloc((void**)&p->dev, h.size() * sizeof(PairDesc)) != cudaSuccess ||
             cudaMemcpy(p->dev, h.data(), h.size() * sizeof(PairDesc), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -359,11 +371,14 @@ tnsk_status tnsk_pairs_run(tnsk_ctx* ctx, tnsk_pairs* p) {
     if (p->n == 0) return TNSK_OK;
     int64_t most = 1;
     for (int64_t s : p->sizes) most = std::max(most, s);
-    // blocks of 8 warps, each warp one group of 32 rows: ~8192 outputs per block, so
-    // many blocks are in flight to hide the load latency
-    const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((most + 8191) / 8192, 1024));
+    // blocks of 8 warps, warps striding over groups of 32 rows: about eight waves of
+    // blocks (four per SM) over all jobs, so the per-block setup (descriptor, offset
+    // table) is paid a few times per SM, not once per 8192 outputs
+    const int64_t per_job = (8 * 4 * (int64_t)p->sms + p->n - 1) / p->n;
+    const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>({(most + 8191) / 8192, per_job, 1024}));
     ctx->prof.begin(TNSK_K_PAIRS, ctx->stream);
-    contract_pairs_kernel<<<dim3(gx, (unsigned)p->n), 256, 0, ctx->stream>>>(p->dev);
+    if (p->any_fast) contract_pairs_kernel<true><<<dim3(gx, (unsigned)p->n), 256, 0, ctx->stream>>>(p->dev);
+    if (p->any_general) contract_pairs_kernel<false><<<dim3(gx, (unsigned)p->n), 256, 0, ctx->stream>>>(p->dev);
     ctx->prof.end(ctx->stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "contract_pairs_kernel");

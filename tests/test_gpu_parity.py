@@ -472,6 +472,9 @@ def test_contract_pairs_match_the_exact_oracle(ctx):
                   torch.float64))
     cases.append((rng.standard_normal((5, 4)), rng.standard_normal((6,)), [], [], [2, 0, 1], torch.bfloat16))
     cases.append((rng.standard_normal((3, 8, 4)), rng.standard_normal((8, 70)), [1], [0], None, torch.float32))
+    # 20 rows sharing their B terms: a ragged group of the 16-byte-store path
+    cases.append((rng.standard_normal((1, 4, 20)), rng.standard_normal((1, 4, 8)), [1], [1], [0, 2, 1, 3],
+                  torch.float32))
     jobs, wants = [], []
     for A, B, am, bm, perm, dt in cases:
         Ad = torch.as_tensor(A).to(dt).cuda()
@@ -496,3 +499,24 @@ def test_contract_pairs_match_the_exact_oracle(ctx):
     pr.close()
     with pytest.raises(tnsk.TnskError):  # unequal shared dims
         ctx.contract_pairs([(jobs[1][0], jobs[1][1], [0], [0], None, jobs[1][5])])
+
+
+def test_contract_pairs_many_jobs(ctx):
+    """64 rung merges in one launch: fewer blocks per job than row groups, so every warp
+    strides over several groups of 32 rows (an uneven number of them)."""
+    rng = np.random.default_rng(62)
+    jobs, wants = [], []
+    for k in range(64):
+        bond = 32 if k % 2 == 0 else 24
+        A = rng.standard_normal((bond, 8, bond)).astype(np.float32)
+        B = rng.standard_normal((bond, 8, bond)).astype(np.float32)
+        want = np.einsum("asc,bsd->abcd", A.astype(np.float64), B.astype(np.float64))
+        out = torch.zeros(want.shape, dtype=torch.float32, device="cuda")
+        jobs.append((torch.as_tensor(A).cuda(), torch.as_tensor(B).cuda(), [1], [1], [0, 2, 1, 3], out))
+        wants.append(want)
+    pr = ctx.pairs(jobs)
+    pr.run()
+    ctx.sync()
+    for (A, B, am, bm, perm, out), want in zip(jobs, wants):
+        assert np.allclose(out.cpu().numpy(), want, rtol=1e-5, atol=1e-5 * 8 * np.abs(want).max())
+    pr.close()
