@@ -189,47 +189,65 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
     }
     const uint32_t len = (uint32_t)(it.end - it.begin);  // <= 128
     const uint32_t cnt = len * (uint32_t)R;
-    for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) {
-        const int r = (int)(len == 128 ? q >> 7 : q / len);
-        const int64_t col = it.begin + (q - (uint32_t)r * len);
-        const uint32_t* tabr = tabs + N.tab_off + (int64_t)r * N.Lrep;
-        uint32_t b[QTMAX];
-        uint32_t neg = 0;
-        IdxT rem = (IdxT)col;
-        // children are the non-parent modes in mode order: slot = d, or d - 1 after the parent
+    // Each (rep, column) is a chain of dependent loads (child table word, T-table words,
+    // the child sketch entry): a thread takes kU of them at once, all loads before any
+    // store, so kU chains are in flight per thread.
+    constexpr int kU = 4;
+    for (uint32_t q0 = threadIdx.x; q0 < cnt; q0 += kU * blockDim.x) {
+        T val[kU];
+        int64_t dst[kU];
 #pragma unroll
-        for (int d = MAXD - 1; d >= 0; --d) {
-            if (d < order && d != pmode) {
-                const IdxT qd = rem / dim[d];
-                const IdxT i = rem - qd * dim[d];
-                rem = qd;
-                const uint32_t w = tabr[ctab[d] + (int64_t)i];
-                neg ^= w;
-                if (pmode >= 0 && d > pmode) {
-                    if (d - 1 < QTMAX) b[d > 0 ? d - 1 : 0] = w & mask;
-                } else {
-                    if (d < QTMAX) b[d] = w & mask;
+        for (int u = 0; u < kU; ++u) {
+            const uint32_t q = q0 + (uint32_t)u * blockDim.x;
+            dst[u] = -1;
+            val[u] = (T)0;
+            if (q >= cnt) continue;
+            const int r = (int)(len == 128 ? q >> 7 : q / len);
+            const int64_t col = it.begin + (q - (uint32_t)r * len);
+            const uint32_t* tabr = tabs + N.tab_off + (int64_t)r * N.Lrep;
+            uint32_t b[QTMAX];
+            uint32_t neg = 0;
+            IdxT rem = (IdxT)col;
+            // children are the non-parent modes in mode order: slot = d, or d - 1 after the parent
+#pragma unroll
+            for (int d = MAXD - 1; d >= 0; --d) {
+                if (d < order && d != pmode) {
+                    const IdxT qd = rem / dim[d];
+                    const IdxT i = rem - qd * dim[d];
+                    rem = qd;
+                    const uint32_t w = tabr[ctab[d] + (int64_t)i];
+                    neg ^= w;
+                    if (pmode >= 0 && d > pmode) {
+                        if (d - 1 < QTMAX) b[d > 0 ? d - 1 : 0] = w & mask;
+                    } else {
+                        if (d < QTMAX) b[d] = w & mask;
+                    }
                 }
             }
+#pragma unroll
+            for (int j = 0; j < QTMAX; ++j)
+                if (j >= c && j < qt) {
+                    uint32_t w = tabr[nd.pad_tab + j];
+                    neg ^= w;
+                    b[j] = w & mask;
+                }
+            rsh_reduce<QTMAX>(b, neg, qt, tabr + nd.t_tab, m, mask);
+            const T z = ws[nd.src_off + (int64_t)r * nd.src_stride + b[0]];
+            val[u] = (neg & TNSK_SIGN_BIT) ? -z : z;
+            dst[u] = nd.v_off + (int64_t)r * nd.cols + col;
         }
 #pragma unroll
-        for (int j = 0; j < QTMAX; ++j)
-            if (j >= c && j < qt) {
-                uint32_t w = tabr[nd.pad_tab + j];
-                neg ^= w;
-                b[j] = w & mask;
+        for (int u = 0; u < kU; ++u) {
+            if (dst[u] < 0) continue;
+            if (sizeof(T) == 4 && !nd.is_root) {
+                // operand of the tensor-core product: TF32 hi part, then its lo part R*cols later
+                uint32_t hi, lo;
+                tf32_split((float)val[u], hi, lo);
+                ws[dst[u]] = (T)__uint_as_float(hi);
+                ws[dst[u] + (int64_t)R * nd.cols] = (T)__uint_as_float(lo);
+            } else {
+                ws[dst[u]] = val[u];
             }
-        rsh_reduce<QTMAX>(b, neg, qt, tabr + nd.t_tab, m, mask);
-        const T z = ws[nd.src_off + (int64_t)r * nd.src_stride + b[0]];
-        const T v = (neg & TNSK_SIGN_BIT) ? -z : z;
-        if (sizeof(T) == 4 && !nd.is_root) {
-            // operand of the tensor-core product: TF32 hi part, then its lo part R*cols later
-            uint32_t hi, lo;
-            tf32_split((float)v, hi, lo);
-            ws[nd.v_off + (int64_t)r * nd.cols + col] = (T)__uint_as_float(hi);
-            ws[nd.v_off + ((int64_t)R + r) * nd.cols + col] = (T)__uint_as_float(lo);
-        } else {
-            ws[nd.v_off + (int64_t)r * nd.cols + col] = v;
         }
     }
 }
@@ -354,15 +372,30 @@ __global__ void __launch_bounds__(256) m2_wscatter_kernel(const M2Node* __restri
     const int64_t npar = nd.npar;
     for (int64_t q = threadIdx.x; q < (int64_t)nr * m; q += blockDim.x) bins[q] = 0.f;
     __syncthreads();
-    for (int j = 0; j < nr; ++j) {
-        const int r = r0 + j;
-        const uint32_t* tw = tabs + N.tab_off + (int64_t)r * N.Lrep + nd.ptab;
-        const float* w = ws + nd.w_off + (int64_t)r * npar;
-        for (int64_t i = threadIdx.x; i < npar; i += blockDim.x) {
-            const uint32_t t = tw[i];
-            const float v = w[i];
-            atomicAdd(&bins[(int64_t)j * m + (t & mask)], (t & TNSK_SIGN_BIT) ? -v : v);
+    // (rep, row) pairs flat, kU per thread at once: all table words and W values are
+    // loaded before the shared-memory adds, so the loads of kU pairs overlap
+    constexpr int kU = 8;
+    const int64_t total = (int64_t)nr * npar;
+    for (int64_t q0 = threadIdx.x; q0 < total; q0 += kU * blockDim.x) {
+        uint32_t t[kU];
+        float v[kU];
+        int bj[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t q = q0 + (int64_t)u * blockDim.x;
+            bj[u] = -1;
+            if (q >= total) continue;
+            const int j = (int)(q / npar);
+            const int64_t i = q - (int64_t)j * npar;
+            const int r = r0 + j;
+            t[u] = tabs[N.tab_off + (int64_t)r * N.Lrep + nd.ptab + i];
+            v[u] = ws[nd.w_off + (int64_t)r * npar + i];
+            bj[u] = j;
         }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (bj[u] >= 0)
+                atomicAdd(&bins[(int64_t)bj[u] * m + (t[u] & mask)], (t[u] & TNSK_SIGN_BIT) ? -v[u] : v[u]);
     }
     __syncthreads();
     for (int64_t q = threadIdx.x; q < (int64_t)nr * m; q += blockDim.x)

@@ -19,32 +19,101 @@ __device__ __forceinline__ int find_req(const TabReq* __restrict__ reqs, int nre
     return lo;
 }
 
+// (a + b) mod P and (a - b) mod P for a, b < P.
+__device__ __forceinline__ uint64_t add61(uint64_t a, uint64_t b) {
+    const uint64_t s = a + b;
+    return s >= kP61 ? s - kP61 : s;
+}
+__device__ __forceinline__ uint64_t sub61(uint64_t a, uint64_t b) { return a >= b ? a - b : a + kP61 - b; }
+
+// The sign polynomial c3 x^3 + c2 x^2 + c1 x + c0 mod P at x < 2^32 (Horner).
+__device__ __forceinline__ uint64_t sign_poly_u32(const HashCoef& h, uint32_t x) {
+    uint64_t g = h.c3;
+    g = fold61(mulmod61_u32(g, x) + h.c2);
+    g = fold61(mulmod61_u32(g, x) + h.c1);
+    return fold61(mulmod61_u32(g, x) + h.c0);
+}
+
+// Words of x = x0, x0 + 32, x0 + 64, ... (count of them: steps) by forward differences
+// with step 32, exact in the field mod P: the bin polynomial a1 x + a0 advances by
+// 32 a1; the cubic sign polynomial g by its first three differences at x0 (from g at
+// x0, x0 + 32, x0 + 64) and the constant third difference 6 c3 32^3. Four modular
+// additions per word instead of four products; the words equal hash_packed_u32's.
+// Needs x0 + 64 < 2^32. emit(t, word) stores the word of x0 + 32 t.
+template <typename Emit>
+__device__ __forceinline__ void fd_words(const HashCoef& h, uint32_t x0, int64_t steps, uint32_t mask, Emit emit) {
+    uint64_t g = sign_poly_u32(h, x0);
+    const uint64_t g1 = sign_poly_u32(h, x0 + 32), g2 = sign_poly_u32(h, x0 + 64);
+    uint64_t d1 = sub61(g1, g);
+    uint64_t d2 = sub61(add61(g2, g), add61(g1, g1));
+    const uint64_t d3 = mulmod61_u32(h.c3, 6u * 32u * 32u * 32u);
+    uint64_t b = fold61(mulmod61_u32(h.a1, x0) + h.a0);
+    const uint64_t db = mulmod61_u32(h.a1, 32u);
+    for (int64_t t = 0; t < steps; ++t) {
+        emit(t, (uint32_t)(b & mask) | ((uint32_t)(g & 1) << TNSK_SIGN_SHIFT));
+        b = add61(b, db);
+        g = add61(g, d1);
+        d1 = add61(d1, d2);
+        d2 = add61(d2, d3);
+    }
+}
+
+// Indices [begin, end) of one hash by one warp, lane taking begin + lane + 32 t:
+// forward differences where the range is long and below 2^32, else word by word.
+template <typename Emit>
+__device__ __forceinline__ void warp_words(const HashCoef& h, int64_t begin, int64_t end, uint32_t mask, int lane,
+                                           Emit emit) {
+    const int64_t x0 = begin + lane;
+    if (end - begin >= 256 && x0 + 64 < (1ll << 32)) {
+        const int64_t steps = x0 < end ? (end - x0 + 31) / 32 : 0;
+        const int64_t lim = ((1ll << 32) - x0 + 31) / 32;  // words below 2^32: the 32-bit form
+        fd_words(h, (uint32_t)x0, steps < lim ? steps : lim, mask,
+                 [&](int64_t t, uint32_t w) { emit(x0 + 32 * t, w); });
+        for (int64_t i = x0 + 32 * lim; i < end; i += 32) emit(i, hash_packed(h, (uint64_t)i, mask));
+        return;
+    }
+    for (int64_t i = x0; i < end; i += 32)
+        emit(i, i < (1ll << 32) ? hash_packed_u32(h, (uint32_t)i, mask) : hash_packed(h, (uint64_t)i, mask));
+}
+
 // One warp per table row (request, rep): the SplitMix64 key chain and the six
 // polynomial coefficients once per row, then the lanes over the row's indices
-// (coalesced stores). Warps stride over the rows of all requests.
+// (coalesced stores). Each warp takes a contiguous range of rows, so the request
+// of its first row is found once (binary search) and then advanced in order.
 __global__ void __launch_bounds__(256) draw_tables_kernel(const TabReq* __restrict__ reqs, int nreq, int64_t rows,
                                                           uint32_t* __restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += nwarps) {
-        const TabReq& q = reqs[find_req(reqs, nreq, row, [](const TabReq& r) { return r.crow; })];
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t per = (rows + nwarps - 1) / nwarps;
+    const int64_t r0 = warp * per, r1 = r0 + per < rows ? r0 + per : rows;
+    if (r0 >= r1) return;
+    int k = find_req(reqs, nreq, r0, [](const TabReq& r) { return r.crow; });
+    for (int64_t row = r0; row < r1; ++row) {
+        while (k + 1 < nreq && reqs[k + 1].crow <= row) ++k;
+        const TabReq& q = reqs[k];
         const uint64_t rep = (uint64_t)(row - q.crow);
         const HashCoef h = hash_coef(q.seed, (uint64_t)q.rep_base + rep, q.tid);
         uint32_t* dst = out + q.out_off + (int64_t)rep * q.rep_stride;
-        const int64_t n32 = q.n < (1ll << 32) ? q.n : (1ll << 32);
-        for (int64_t i = lane; i < n32; i += 32) dst[i] = hash_packed_u32(h, (uint32_t)i, q.mask);
-        for (int64_t i = n32 + lane; i < q.n; i += 32) dst[i] = hash_packed(h, (uint64_t)i, q.mask);
+        warp_words(h, 0, q.n, q.mask, lane, [&](int64_t i, uint32_t w) { dst[i] = w; });
     }
 }
 
-__global__ void count_sketch_kernel(uint64_t seed, uint64_t rep, uint64_t tid, int64_t n, uint32_t mask,
-                                    int32_t* __restrict__ bins, int8_t* __restrict__ signs) {
-    HashCoef h = hash_coef(seed, rep, tid);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t w = hash_packed(h, (uint64_t)i, mask);
+// One hash over [0, n): each warp a contiguous range of indices (a multiple of 32).
+__global__ void __launch_bounds__(256) count_sketch_kernel(uint64_t seed, uint64_t rep, uint64_t tid, int64_t n,
+                                                           uint32_t mask, int32_t* __restrict__ bins,
+                                                           int8_t* __restrict__ signs) {
+    const HashCoef h = hash_coef(seed, rep, tid);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t per = ((n + nwarps - 1) / nwarps + 31) & ~(int64_t)31;
+    const int64_t begin = warp * per;
+    if (begin >= n) return;
+    const int64_t end = begin + per < n ? begin + per : n;
+    warp_words(h, begin, end, mask, threadIdx.x & 31, [&](int64_t i, uint32_t w) {
         bins[i] = (int32_t)(w & mask);
         signs[i] = (w & TNSK_SIGN_BIT) ? (int8_t)-1 : (int8_t)1;
-    }
+    });
 }
 
 cudaError_t launch_draw_tables(const TabReq* d_reqs, int nreq, int64_t rows, uint32_t* d_out, cudaStream_t s) {
@@ -58,7 +127,7 @@ cudaError_t launch_draw_tables(const TabReq* d_reqs, int nreq, int64_t rows, uin
 cudaError_t launch_count_sketch(uint64_t seed, uint64_t rep, uint64_t tid, int64_t n, int64_t m, int32_t* bins,
                                 int8_t* signs, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    int64_t blocks = (n + 255) / 256;
+    int64_t blocks = (n + 2047) / 2048;  // 8 warps of at least 256 indices
     if (blocks > 152 * 8) blocks = 152 * 8;
     count_sketch_kernel<<<(unsigned)blocks, 256, 0, s>>>(seed, rep, tid, n, (uint32_t)(m - 1), bins, signs);
     return cudaGetLastError();
