@@ -159,6 +159,15 @@ tnsk_status tnsk_create(tnsk_ctx** out, int device, void* cuda_stream) {
         delete ctx;
         return TNSK_ERR_CUDA;
     }
+    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();  // no second stream: method 1 and 2 then run in sequence
+        if (ctx->side) cudaStreamDestroy(ctx->side);
+        if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+        ctx->side = nullptr;
+        ctx->ev_fork = ctx->ev_join = nullptr;
+    }
     *out = ctx;
     return TNSK_OK;
 }
@@ -173,6 +182,12 @@ tnsk_status tnsk_destroy(tnsk_ctx* ctx) {
     if (ctx->d_tw32) cudaFree(ctx->d_tw32);
     if (ctx->d_tw64) cudaFree(ctx->d_tw64);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->side) {
+        cudaStreamSynchronize(ctx->side);
+        cudaStreamDestroy(ctx->side);
+        cudaEventDestroy(ctx->ev_fork);
+        cudaEventDestroy(ctx->ev_join);
+    }
     delete ctx;
     return TNSK_OK;
 }
@@ -264,25 +279,44 @@ static tnsk_status launch_plan(tnsk_ctx* ctx, const BatchPlan& plan, unsigned ch
                                      (uint32_t*)(base + plan.tabs_off), s));
         pf.end(s);
     }
+    // Methods 1 and 2 share only the tables: with both in the batch (and per-kernel
+    // timing off), method 1 runs on the ctx's second stream while method 2 runs on
+    // the ctx stream, joined before the combine. Inside a stream capture the fork and
+    // join become graph edges.
+    const bool fork = !pf.on && ctx->side && plan.m1.n_nets && plan.m2.n_nets && !sketch_out;
+    cudaStream_t s1 = s;
+    if (fork) {
+        TNSK_CUDA(cudaEventRecord(ctx->ev_fork, s));
+        TNSK_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+        s1 = ctx->side;
+    }
+    tnsk_status st = TNSK_OK;
     if (plan.m1.n_nets) {
         void* xs = sketch_out ? sketch_out : (void*)(base + plan.m1.xs_off);
-        pf.begin(TNSK_K_M1_SCATTER, s);
-        TNSK_CUDA(launch_m1_scatters(plan, base, xs, fp64, s));
-        pf.end(s);
-        if (!sketch_out) {
-            pf.begin(TNSK_K_M1_SPECTRUM, s);
-            TNSK_CUDA(launch_m1_spectra(plan, base, xs,
-                                        fp64 ? (const void* const*)ctx->d_tw64 : (const void* const*)ctx->d_tw32,
-                                        fp64, s));
-            pf.end(s);
+        pf.begin(TNSK_K_M1_SCATTER, s1);
+        cudaError_t e = launch_m1_scatters(plan, base, xs, fp64, s1);
+        pf.end(s1);
+        if (e == cudaSuccess && !sketch_out) {
+            pf.begin(TNSK_K_M1_SPECTRUM, s1);
+            e = launch_m1_spectra(plan, base, xs,
+                                  fp64 ? (const void* const*)ctx->d_tw64 : (const void* const*)ctx->d_tw32, fp64,
+                                  s1);
+            pf.end(s1);
         }
+        if (e != cudaSuccess) st = cuda_fail(ctx, e, "method 1 launch");
     }
-    if (plan.m2.n_nets && !sketch_out) {
-        tnsk_status st =
-            run_method2(plan, base, fp64, fp64 ? (const void* const*)ctx->d_tw64 : (const void* const*)ctx->d_tw32,
-                        s, pf, ctx->d_err, ctx->last_error);
-        if (st != TNSK_OK) return st;
+    if (fork) {  // joined on every path, so a capture never ends with the side stream open
+        const cudaError_t e1 = cudaEventRecord(ctx->ev_join, ctx->side);
+        if (st == TNSK_OK && e1 != cudaSuccess) st = cuda_fail(ctx, e1, "cudaEventRecord");
     }
+    if (st == TNSK_OK && plan.m2.n_nets && !sketch_out)
+        st = run_method2(plan, base, fp64, fp64 ? (const void* const*)ctx->d_tw64 : (const void* const*)ctx->d_tw32, s,
+                         pf, ctx->d_err, ctx->last_error);
+    if (fork) {
+        const cudaError_t e2 = cudaStreamWaitEvent(s, ctx->ev_join, 0);
+        if (st == TNSK_OK && e2 != cudaSuccess) st = cuda_fail(ctx, e2, "cudaStreamWaitEvent");
+    }
+    if (st != TNSK_OK) return st;
     if (!sketch_out && plan.n_comb) {
         pf.begin(TNSK_K_COMBINE, s);
         TNSK_CUDA(launch_combine((const CombineItem*)(base + plan.comb_off), plan.n_comb,

@@ -20,6 +20,10 @@ struct tnsk_ctx {
     const void** d_tw32 = nullptr;  // device arrays of the pointers above
     const void** d_tw64 = nullptr;
     int* d_err = nullptr;  // device error word
+    // second stream for method 1 while method 2 runs on the ctx stream, and the
+    // events that fork it from and join it back into the ctx stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     tnsk::Profiler prof;
 };
 
