@@ -147,16 +147,33 @@ __global__ void __launch_bounds__(kScatterThreads) m1_scatter_kernel(const M1Ten
         constexpr bool kG = decltype(global_tables)::value;
         constexpr int V = decltype(vec)::value;
         constexpr int L = MAXD - 1;  // the tensor's last mode
-        for (int64_t f = w.begin + (int64_t)V * threadIdx.x; f < w.end; f += (int64_t)V * blockDim.x) {
+        // the next step's entries are loaded before this step's adds (one load in flight
+        // per thread while it works, which matters when the tensor streams from HBM)
+        const int64_t fs = (int64_t)V * blockDim.x;
+        int64_t f = w.begin + (int64_t)V * threadIdx.x;
+        float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);
+        AccT vn = AccT(0);
+        if (f < w.end) {
+            if (V == 4)
+                qn = __ldg(reinterpret_cast<const float4*>((const float*)sT.data + f));
+            else
+                vn = load_as<AccT>(sT.data, sT.dtype, f);
+        }
+        for (; f < w.end; f += fs) {
             AccT v[V];
             if (V == 4) {
-                const float4 q = __ldg(reinterpret_cast<const float4*>((const float*)sT.data + f));
-                v[0] = (AccT)q.x;
-                v[V > 1 ? 1 : 0] = (AccT)q.y;
-                v[V > 2 ? 2 : 0] = (AccT)q.z;
-                v[V > 3 ? 3 : 0] = (AccT)q.w;
+                v[0] = (AccT)qn.x;
+                v[V > 1 ? 1 : 0] = (AccT)qn.y;
+                v[V > 2 ? 2 : 0] = (AccT)qn.z;
+                v[V > 3 ? 3 : 0] = (AccT)qn.w;
             } else {
-                v[0] = load_as<AccT>(sT.data, sT.dtype, f);
+                v[0] = vn;
+            }
+            if (f + fs < w.end) {
+                if (V == 4)
+                    qn = __ldg(reinterpret_cast<const float4*>((const float*)sT.data + f + fs));
+                else
+                    vn = load_as<AccT>(sT.data, sT.dtype, f + fs);
             }
             int off[MAXD];
             int64_t o = 0;

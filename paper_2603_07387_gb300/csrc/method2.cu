@@ -165,11 +165,17 @@ __global__ void __launch_bounds__(256) m2_compose_kernel(const M2Node* __restric
 // ---------------------------------------------------------------------------
 // a7: V = sigma_r(col) r_k[r][b_r(col)], and the batched sketched matvec
 // ---------------------------------------------------------------------------
+// Two item forms. Column chunks (it.b == 0): columns [begin, end) x all reps, every
+// table word and child-sketch entry read from global memory (L2). Staged (it.b > 0):
+// reps [a, a + b) x all columns, with those reps' T tables and child sketches copied
+// to shared memory first, so the data-dependent lookups are shared-memory reads; the
+// plan takes this form where they fit (the launch's dynamic shared memory).
 template <typename T, typename IdxT, int QTMAX, int MAXD>
 __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict__ nodes,
                                                         const M2Net* __restrict__ nets,
                                                         const M2Item* __restrict__ items,
                                                         const uint32_t* __restrict__ tabs, T* __restrict__ ws) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const M2Item it = items[blockIdx.x];
     const M2Node& nd = nodes[it.node];
     const M2Net& N = nets[nd.net];
@@ -187,89 +193,137 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
         const int slot = (pmode >= 0 && d > pmode) ? d - 1 : d;
         ctab[d] = child ? nd.ctab[slot < TNSK_MAX_ORDER ? slot : 0] : 0;
     }
-    const uint32_t len = (uint32_t)(it.end - it.begin);  // <= 128
-    const uint32_t cnt = len * (uint32_t)R;
+    // sign word and bin of V(col, r): the child count-sketch words of col's indices, the
+    // padding words, then the T-table levels (ttab: rep r's T tables)
+    auto lookup = [&](const uint32_t* __restrict__ tabr, const uint32_t* ttab, int64_t col, uint32_t& neg) {
+        uint32_t b[QTMAX];
+        neg = 0;
+        IdxT rem = (IdxT)col;
+        // children are the non-parent modes in mode order: slot = d, or d - 1 after the parent
+#pragma unroll
+        for (int d = MAXD - 1; d >= 0; --d) {
+            if (d < order && d != pmode) {
+                const IdxT qd = rem / dim[d];
+                const IdxT i = rem - qd * dim[d];
+                rem = qd;
+                const uint32_t w = tabr[ctab[d] + (int64_t)i];
+                neg ^= w;
+                if (pmode >= 0 && d > pmode) {
+                    if (d - 1 < QTMAX) b[d > 0 ? d - 1 : 0] = w & mask;
+                } else {
+                    if (d < QTMAX) b[d] = w & mask;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < QTMAX; ++j)
+            if (j >= c && j < qt) {
+                uint32_t w = tabr[nd.pad_tab + j];
+                neg ^= w;
+                b[j] = w & mask;
+            }
+        rsh_reduce<QTMAX>(b, neg, qt, ttab, m, mask);
+        return b[0];
+    };
+    auto store = [&](int r, int64_t col, T v) {
+        const int64_t dst = nd.v_off + (int64_t)r * nd.cols + col;
+        if (sizeof(T) == 4 && !nd.is_root) {
+            // operand of the tensor-core product: TF32 hi part, then its lo part R*cols later
+            uint32_t hi, lo;
+            tf32_split((float)v, hi, lo);
+            ws[dst] = (T)__uint_as_float(hi);
+            ws[dst + (int64_t)R * nd.cols] = (T)__uint_as_float(lo);
+        } else {
+            ws[dst] = v;
+        }
+    };
     // Each (rep, column) is a chain of dependent loads (child table word, T-table words,
     // the child sketch entry): a thread takes kU of them at once, all loads before any
     // store, so kU chains are in flight per thread.
     constexpr int kU = 4;
+    if (it.b > 0) {
+        const int G = it.b, r0 = it.a;
+        const int64_t tw = qt >= 2 ? 2 * (int64_t)(qt - 1) * m : 0;  // T-table words of one rep
+        uint32_t* s_t = reinterpret_cast<uint32_t*>(smem_raw);
+        T* s_src = reinterpret_cast<T*>(smem_raw + (((size_t)G * tw * 4 + 15) & ~(size_t)15));
+        for (int g = 0; g < G; ++g) {
+            const uint32_t* src_t = tabs + N.tab_off + (int64_t)(r0 + g) * N.Lrep + nd.t_tab;
+            for (int64_t k = threadIdx.x; k < tw; k += blockDim.x) s_t[g * tw + k] = src_t[k];
+            const T* src_z = ws + nd.src_off + (int64_t)(r0 + g) * nd.src_stride;
+            for (int64_t k = threadIdx.x; k < m; k += blockDim.x) s_src[g * m + k] = src_z[k];
+        }
+        __syncthreads();
+        for (int g = 0; g < G; ++g) {
+            const int r = r0 + g;
+            const uint32_t* tabr = tabs + N.tab_off + (int64_t)r * N.Lrep;
+            for (int64_t c0 = threadIdx.x; c0 < nd.cols; c0 += kU * blockDim.x) {
+                T val[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int64_t col = c0 + (int64_t)u * blockDim.x;
+                    val[u] = (T)0;
+                    if (col >= nd.cols) continue;
+                    uint32_t neg;
+                    const uint32_t b0 = lookup(tabr, s_t + g * tw, col, neg);
+                    const T z = s_src[g * m + b0];
+                    val[u] = (neg & TNSK_SIGN_BIT) ? -z : z;
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int64_t col = c0 + (int64_t)u * blockDim.x;
+                    if (col < nd.cols) store(r, col, val[u]);
+                }
+            }
+        }
+        return;
+    }
+    const uint32_t len = (uint32_t)(it.end - it.begin);  // <= 128
+    const uint32_t cnt = len * (uint32_t)R;
     for (uint32_t q0 = threadIdx.x; q0 < cnt; q0 += kU * blockDim.x) {
         T val[kU];
-        int64_t dst[kU];
+        int rr[kU];
+        int64_t cc[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const uint32_t q = q0 + (uint32_t)u * blockDim.x;
-            dst[u] = -1;
+            rr[u] = -1;
             val[u] = (T)0;
+            cc[u] = 0;
             if (q >= cnt) continue;
             const int r = (int)(len == 128 ? q >> 7 : q / len);
             const int64_t col = it.begin + (q - (uint32_t)r * len);
             const uint32_t* tabr = tabs + N.tab_off + (int64_t)r * N.Lrep;
-            uint32_t b[QTMAX];
-            uint32_t neg = 0;
-            IdxT rem = (IdxT)col;
-            // children are the non-parent modes in mode order: slot = d, or d - 1 after the parent
-#pragma unroll
-            for (int d = MAXD - 1; d >= 0; --d) {
-                if (d < order && d != pmode) {
-                    const IdxT qd = rem / dim[d];
-                    const IdxT i = rem - qd * dim[d];
-                    rem = qd;
-                    const uint32_t w = tabr[ctab[d] + (int64_t)i];
-                    neg ^= w;
-                    if (pmode >= 0 && d > pmode) {
-                        if (d - 1 < QTMAX) b[d > 0 ? d - 1 : 0] = w & mask;
-                    } else {
-                        if (d < QTMAX) b[d] = w & mask;
-                    }
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < QTMAX; ++j)
-                if (j >= c && j < qt) {
-                    uint32_t w = tabr[nd.pad_tab + j];
-                    neg ^= w;
-                    b[j] = w & mask;
-                }
-            rsh_reduce<QTMAX>(b, neg, qt, tabr + nd.t_tab, m, mask);
-            const T z = ws[nd.src_off + (int64_t)r * nd.src_stride + b[0]];
+            uint32_t neg;
+            const uint32_t b0 = lookup(tabr, tabr + nd.t_tab, col, neg);
+            const T z = ws[nd.src_off + (int64_t)r * nd.src_stride + b0];
             val[u] = (neg & TNSK_SIGN_BIT) ? -z : z;
-            dst[u] = nd.v_off + (int64_t)r * nd.cols + col;
+            rr[u] = r;
+            cc[u] = col;
         }
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            if (dst[u] < 0) continue;
-            if (sizeof(T) == 4 && !nd.is_root) {
-                // operand of the tensor-core product: TF32 hi part, then its lo part R*cols later
-                uint32_t hi, lo;
-                tf32_split((float)val[u], hi, lo);
-                ws[dst[u]] = (T)__uint_as_float(hi);
-                ws[dst[u] + (int64_t)R * nd.cols] = (T)__uint_as_float(lo);
-            } else {
-                ws[dst[u]] = val[u];
-            }
-        }
+        for (int u = 0; u < kU; ++u)
+            if (rr[u] >= 0) store(rr[u], cc[u], val[u]);
     }
 }
 
 template <typename T, typename IdxT, int QTMAX>
 static void launch_vbuild_q(int n, const M2Node* nodes, const M2Net* nets, const M2Item* its, const uint32_t* tabs,
-                            T* ws, int max_order, cudaStream_t s) {
+                            T* ws, int max_order, size_t smem, cudaStream_t s) {
     if (max_order <= 4)
-        m2_vbuild_kernel<T, IdxT, QTMAX, 4><<<n, 256, 0, s>>>(nodes, nets, its, tabs, ws);
+        m2_vbuild_kernel<T, IdxT, QTMAX, 4><<<n, 256, smem, s>>>(nodes, nets, its, tabs, ws);
     else
-        m2_vbuild_kernel<T, IdxT, QTMAX, TNSK_MAX_ORDER><<<n, 256, 0, s>>>(nodes, nets, its, tabs, ws);
+        m2_vbuild_kernel<T, IdxT, QTMAX, TNSK_MAX_ORDER><<<n, 256, smem, s>>>(nodes, nets, its, tabs, ws);
 }
 
 template <typename T, typename IdxT>
 static void launch_vbuild(int n, const M2Node* nodes, const M2Net* nets, const M2Item* its, const uint32_t* tabs,
-                          T* ws, int max_qt, int max_order, cudaStream_t s) {
+                          T* ws, int max_qt, int max_order, size_t smem, cudaStream_t s) {
     if (max_qt <= 1)
-        launch_vbuild_q<T, IdxT, 1>(n, nodes, nets, its, tabs, ws, max_order, s);
+        launch_vbuild_q<T, IdxT, 1>(n, nodes, nets, its, tabs, ws, max_order, smem, s);
     else if (max_qt <= 4)
-        launch_vbuild_q<T, IdxT, 4>(n, nodes, nets, its, tabs, ws, max_order, s);
+        launch_vbuild_q<T, IdxT, 4>(n, nodes, nets, its, tabs, ws, max_order, smem, s);
     else
-        launch_vbuild_q<T, IdxT, TNSK_MAX_SLOTS>(n, nodes, nets, its, tabs, ws, max_order, s);
+        launch_vbuild_q<T, IdxT, TNSK_MAX_SLOTS>(n, nodes, nets, its, tabs, ws, max_order, smem, s);
 }
 
 // W = mat(X_k)[rows, :] V[:, reps] for a 64 x 64 tile, then x_k[r][h(i)] += s(i) W[i][r]
@@ -458,9 +512,11 @@ static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void*
                     break;
                 case M2_VBUILD:
                     if (P.m2.idx32)
-                        launch_vbuild<T, uint32_t>(n, nodes, nets, its, tabs, ws, P.m2.max_qt, P.m2.max_order, s);
+                        launch_vbuild<T, uint32_t>(n, nodes, nets, its, tabs, ws, P.m2.max_qt, P.m2.max_order, P.m2.vbuild_smem,
+                                                   s);
                     else
-                        launch_vbuild<T, uint64_t>(n, nodes, nets, its, tabs, ws, P.m2.max_qt, P.m2.max_order, s);
+                        launch_vbuild<T, uint64_t>(n, nodes, nets, its, tabs, ws, P.m2.max_qt, P.m2.max_order, P.m2.vbuild_smem,
+                                                   s);
                     break;
                 case M2_GEMM:
                 case M2_GEMM_STREAM:

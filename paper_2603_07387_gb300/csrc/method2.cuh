@@ -114,6 +114,7 @@ struct M2Plan {
     int max_order = 0;  // largest tensor order
     size_t tmaps_off = 0;  // tensor maps (128 B each) in the descriptor block
     size_t scatter_smem = 0;  // shared-memory bins of the largest row-scatter item
+    size_t vbuild_smem = 0;   // staged T tables + child sketches of the largest staged V-build item
     // tensor maps to encode once the device addresses are fixed: node, 0 = X / 1 = V^T hi / 2 = lo
     std::vector<std::pair<int, int>> tmap_jobs;
     int max_log2m = 0;
