@@ -165,11 +165,11 @@ __global__ void __launch_bounds__(256) m2_compose_kernel(const M2Node* __restric
 // ---------------------------------------------------------------------------
 // a7: V = sigma_r(col) r_k[r][b_r(col)], and the batched sketched matvec
 // ---------------------------------------------------------------------------
-// Two item forms. Column chunks (it.b == 0): columns [begin, end) x all reps, every
-// table word and child-sketch entry read from global memory (L2). Staged (it.b > 0):
-// reps [a, a + b) x all columns, with those reps' T tables and child sketches copied
-// to shared memory first, so the data-dependent lookups are shared-memory reads; the
-// plan takes this form where they fit (the launch's dynamic shared memory).
+// Items: columns [begin, end) x reps [a, a + b). Plain form (pad_ == 0): every table
+// word and child-sketch entry read from global memory (L2). Staged form (pad_ == 1):
+// the reps' T tables and child sketches copied to shared memory first, so the
+// data-dependent lookups are shared-memory reads; the plan takes this form where they
+// fit (the launch's dynamic shared memory).
 template <typename T, typename IdxT, int QTMAX, int MAXD>
 __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict__ nodes,
                                                         const M2Net* __restrict__ nets,
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
     // the child sketch entry): a thread takes kU of them at once, all loads before any
     // store, so kU chains are in flight per thread.
     constexpr int kU = 4;
-    if (it.b > 0) {
+    if (it.pad_ == 1) {
         const int G = it.b, r0 = it.a;
         const int64_t tw = qt >= 2 ? 2 * (int64_t)(qt - 1) * m : 0;  // T-table words of one rep
         uint32_t* s_t = reinterpret_cast<uint32_t*>(smem_raw);
@@ -256,13 +256,13 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
         for (int g = 0; g < G; ++g) {
             const int r = r0 + g;
             const uint32_t* tabr = tabs + N.tab_off + (int64_t)r * N.Lrep;
-            for (int64_t c0 = threadIdx.x; c0 < nd.cols; c0 += kU * blockDim.x) {
+            for (int64_t c0 = it.begin + threadIdx.x; c0 < it.end; c0 += kU * blockDim.x) {
                 T val[kU];
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
                     const int64_t col = c0 + (int64_t)u * blockDim.x;
                     val[u] = (T)0;
-                    if (col >= nd.cols) continue;
+                    if (col >= it.end) continue;
                     uint32_t neg;
                     const uint32_t b0 = lookup(tabr, s_t + g * tw, col, neg);
                     const T z = s_src[g * m + b0];
@@ -271,14 +271,14 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
                     const int64_t col = c0 + (int64_t)u * blockDim.x;
-                    if (col < nd.cols) store(r, col, val[u]);
+                    if (col < it.end) store(r, col, val[u]);
                 }
             }
         }
         return;
     }
     const uint32_t len = (uint32_t)(it.end - it.begin);  // <= 128
-    const uint32_t cnt = len * (uint32_t)R;
+    const uint32_t cnt = len * (uint32_t)it.b;
     for (uint32_t q0 = threadIdx.x; q0 < cnt; q0 += kU * blockDim.x) {
         T val[kU];
         int rr[kU];
@@ -290,8 +290,9 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
             val[u] = (T)0;
             cc[u] = 0;
             if (q >= cnt) continue;
-            const int r = (int)(len == 128 ? q >> 7 : q / len);
-            const int64_t col = it.begin + (q - (uint32_t)r * len);
+            const int rl = (int)(len == 128 ? q >> 7 : q / len);
+            const int r = it.a + rl;
+            const int64_t col = it.begin + (q - (uint32_t)rl * len);
             const uint32_t* tabr = tabs + N.tab_off + (int64_t)r * N.Lrep;
             uint32_t neg;
             const uint32_t b0 = lookup(tabr, tabr + nd.t_tab, col, neg);

@@ -725,25 +725,31 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
             if (nd.qt >= 2)
                 for (int r = 0; r < R; ++r) pend.push_back({h, M2_COMPOSE, M2Item{node_idx, r, 0, 0, 0, 0}});
             if (nd.c >= 1) {
-                // staged form (reps x all columns, a rep's T tables and child sketch in shared
-                // memory) when a rep's share fits 48 KiB and the columns amortise the copy
+                // Items of about 1-4 K outputs (enough CTAs in flight to hide the gathers'
+                // latency). With T tables (qt >= 2) whose share of a rep fits 48 KiB and
+                // enough columns to amortise the copy: staged form (pad_ = 1), a few reps x
+                // 512 columns with the reps' T tables and child sketches in shared memory.
+                // Otherwise 128 columns x 8 reps, every lookup from L2.
                 const int64_t tw = nd.qt >= 2 ? 2 * (int64_t)(nd.qt - 1) * m : 0;
                 const int64_t per_rep = tw * 4 + m * (fp64 ? 8 : 4) + 16;
                 const int64_t budget = 48 * 1024;
-                if (per_rep <= budget && nd.cols >= std::max<int64_t>(256, m / 4)) {
-                    const int G = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)R, budget / per_rep, 8}));
-                    for (int r0 = 0; r0 < R; r0 += G) {
-                        const int g = std::min(G, R - r0);
-                        M2Item it{node_idx, r0, g, 0, 0, nd.cols};
-                        pend.push_back({h, M2_VBUILD, it});
-                        const size_t bytes = (((size_t)g * tw * 4 + 15) & ~(size_t)15) + (size_t)g * m * (fp64 ? 8 : 4);
-                        P.m2.vbuild_smem = std::max(P.m2.vbuild_smem, bytes);
-                    }
+                if (nd.qt >= 2 && per_rep <= budget && nd.cols >= std::max<int64_t>(256, m / 4)) {
+                    const int G = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)R, budget / per_rep, 4}));
+                    for (int r0 = 0; r0 < R; r0 += G)
+                        for (int64_t b0 = 0; b0 < nd.cols; b0 += 512) {
+                            const int g = std::min(G, R - r0);
+                            M2Item it{node_idx, r0, g, 1, b0, std::min(nd.cols, b0 + 512)};
+                            pend.push_back({h, M2_VBUILD, it});
+                            const size_t bytes =
+                                (((size_t)g * tw * 4 + 15) & ~(size_t)15) + (size_t)g * m * (fp64 ? 8 : 4);
+                            P.m2.vbuild_smem = std::max(P.m2.vbuild_smem, bytes);
+                        }
                 } else {
-                    for (int64_t b0 = 0; b0 < nd.cols; b0 += 128) {
-                        M2Item it{node_idx, 0, 0, 0, b0, std::min(nd.cols, b0 + 128)};
-                        pend.push_back({h, M2_VBUILD, it});
-                    }
+                    for (int r0 = 0; r0 < R; r0 += 8)
+                        for (int64_t b0 = 0; b0 < nd.cols; b0 += 128) {
+                            M2Item it{node_idx, r0, std::min(8, R - r0), 0, b0, std::min(nd.cols, b0 + 128)};
+                            pend.push_back({h, M2_VBUILD, it});
+                        }
                 }
             }
             if (!fp64 && nd.c >= 1 && !nd.is_root) {
