@@ -76,10 +76,11 @@ __device__ __forceinline__ void warp_words(const HashCoef& h, int64_t begin, int
         emit(i, i < (1ll << 32) ? hash_packed_u32(h, (uint32_t)i, mask) : hash_packed(h, (uint64_t)i, mask));
 }
 
-// One warp per table row (request, rep): the SplitMix64 key chain and the six
-// polynomial coefficients once per row, then the lanes over the row's indices
-// (coalesced stores). Each warp takes a contiguous range of rows, so the request
-// of its first row is found once (binary search) and then advanced in order.
+// Table rows (request, rep) in contiguous ranges per warp, 32 rows at a time: lane j
+// finds row j's request (advancing from the previous row's) and derives its SplitMix64
+// key chain and six polynomial coefficients, so each lane pays for one row's setup;
+// then the warp writes the rows one after another, the row's coefficients broadcast
+// from its lane, lanes over the row's indices (coalesced stores).
 __global__ void __launch_bounds__(256) draw_tables_kernel(const TabReq* __restrict__ reqs, int nreq, int64_t rows,
                                                           uint32_t* __restrict__ out) {
     const int lane = threadIdx.x & 31;
@@ -89,13 +90,37 @@ __global__ void __launch_bounds__(256) draw_tables_kernel(const TabReq* __restri
     const int64_t r0 = warp * per, r1 = r0 + per < rows ? r0 + per : rows;
     if (r0 >= r1) return;
     int k = find_req(reqs, nreq, r0, [](const TabReq& r) { return r.crow; });
-    for (int64_t row = r0; row < r1; ++row) {
-        while (k + 1 < nreq && reqs[k + 1].crow <= row) ++k;
-        const TabReq& q = reqs[k];
-        const uint64_t rep = (uint64_t)(row - q.crow);
-        const HashCoef h = hash_coef(q.seed, (uint64_t)q.rep_base + rep, q.tid);
-        uint32_t* dst = out + q.out_off + (int64_t)rep * q.rep_stride;
-        warp_words(h, 0, q.n, q.mask, lane, [&](int64_t i, uint32_t w) { dst[i] = w; });
+    for (int64_t g0 = r0; g0 < r1; g0 += 32) {
+        const int64_t row = g0 + lane;
+        int kk = k;
+        while (kk + 1 < nreq && reqs[kk + 1].crow <= row) ++kk;
+        k = __shfl_sync(0xffffffffu, kk, 31);
+        HashCoef hc{0, 0, 0, 0, 0, 0};
+        unsigned long long dst_l = 0;
+        long long n_l = 0;
+        uint32_t mask_l = 0;
+        if (row < r1) {
+            const TabReq& q = reqs[kk];
+            const uint64_t rep = (uint64_t)(row - q.crow);
+            hc = hash_coef(q.seed, (uint64_t)q.rep_base + rep, q.tid);
+            dst_l = (unsigned long long)(uintptr_t)(out + q.out_off + (int64_t)rep * q.rep_stride);
+            n_l = q.n;
+            mask_l = q.mask;
+        }
+        const int cnt = r1 - g0 < 32 ? (int)(r1 - g0) : 32;
+        for (int i = 0; i < cnt; ++i) {
+            HashCoef h;
+            h.a0 = __shfl_sync(0xffffffffu, (unsigned long long)hc.a0, i);
+            h.a1 = __shfl_sync(0xffffffffu, (unsigned long long)hc.a1, i);
+            h.c0 = __shfl_sync(0xffffffffu, (unsigned long long)hc.c0, i);
+            h.c1 = __shfl_sync(0xffffffffu, (unsigned long long)hc.c1, i);
+            h.c2 = __shfl_sync(0xffffffffu, (unsigned long long)hc.c2, i);
+            h.c3 = __shfl_sync(0xffffffffu, (unsigned long long)hc.c3, i);
+            uint32_t* dst = (uint32_t*)(uintptr_t)__shfl_sync(0xffffffffu, dst_l, i);
+            const int64_t n = __shfl_sync(0xffffffffu, n_l, i);
+            const uint32_t mask = __shfl_sync(0xffffffffu, mask_l, i);
+            warp_words(h, 0, n, mask, lane, [&](int64_t x, uint32_t w) { dst[x] = w; });
+        }
     }
 }
 
@@ -118,8 +143,8 @@ __global__ void __launch_bounds__(256) count_sketch_kernel(uint64_t seed, uint64
 
 cudaError_t launch_draw_tables(const TabReq* d_reqs, int nreq, int64_t rows, uint32_t* d_out, cudaStream_t s) {
     if (rows <= 0 || nreq <= 0) return cudaSuccess;
-    int64_t blocks = (rows + 7) / 8;  // 8 warps per block, one row each per pass
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    int64_t blocks = (rows + 255) / 256;  // 8 warps per block, a group of 32 rows each
+    if (blocks > 152 * 12) blocks = 152 * 12;
     draw_tables_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_reqs, nreq, rows, d_out);
     return cudaGetLastError();
 }
