@@ -246,11 +246,30 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
         const int64_t tw = qt >= 2 ? 2 * (int64_t)(qt - 1) * m : 0;  // T-table words of one rep
         uint32_t* s_t = reinterpret_cast<uint32_t*>(smem_raw);
         T* s_src = reinterpret_cast<T*>(smem_raw + (((size_t)G * tw * 4 + 15) & ~(size_t)15));
-        for (int g = 0; g < G; ++g) {
-            const uint32_t* src_t = tabs + N.tab_off + (int64_t)(r0 + g) * N.Lrep + nd.t_tab;
-            for (int64_t k = threadIdx.x; k < tw; k += blockDim.x) s_t[g * tw + k] = src_t[k];
-            const T* src_z = ws + nd.src_off + (int64_t)(r0 + g) * nd.src_stride;
-            for (int64_t k = threadIdx.x; k < m; k += blockDim.x) s_src[g * m + k] = src_z[k];
+        // the copies, kU loads in flight per thread
+        for (int64_t q0 = threadIdx.x; q0 < (int64_t)G * tw; q0 += kU * blockDim.x) {
+            uint32_t v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t q = q0 + (int64_t)u * blockDim.x;
+                const int64_t g = q / tw;
+                v[u] = q < (int64_t)G * tw ? tabs[N.tab_off + (r0 + g) * N.Lrep + nd.t_tab + (q - g * tw)] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (q0 + (int64_t)u * blockDim.x < (int64_t)G * tw) s_t[q0 + (int64_t)u * blockDim.x] = v[u];
+        }
+        for (int64_t q0 = threadIdx.x; q0 < (int64_t)G * m; q0 += kU * blockDim.x) {
+            T v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t q = q0 + (int64_t)u * blockDim.x;
+                const int64_t g = q >> N.log2m;
+                v[u] = q < (int64_t)G * m ? ws[nd.src_off + (r0 + g) * nd.src_stride + (q - g * m)] : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (q0 + (int64_t)u * blockDim.x < (int64_t)G * m) s_src[q0 + (int64_t)u * blockDim.x] = v[u];
         }
         __syncthreads();
         for (int g = 0; g < G; ++g) {

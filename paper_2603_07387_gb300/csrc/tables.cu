@@ -143,8 +143,10 @@ __global__ void __launch_bounds__(256) count_sketch_kernel(uint64_t seed, uint64
 
 cudaError_t launch_draw_tables(const TabReq* d_reqs, int nreq, int64_t rows, uint32_t* d_out, cudaStream_t s) {
     if (rows <= 0 || nreq <= 0) return cudaSuccess;
-    int64_t blocks = (rows + 255) / 256;  // 8 warps per block, a group of 32 rows each
-    if (blocks > 152 * 12) blocks = 152 * 12;
+    // 8 warps per block, a few rows per warp: enough warps to hide the latency of the
+    // word recurrences
+    int64_t blocks = (rows + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
     draw_tables_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_reqs, nreq, rows, d_out);
     return cudaGetLastError();
 }
