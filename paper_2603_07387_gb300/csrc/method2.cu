@@ -183,6 +183,10 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
     const int64_t m = N.m;
     const uint32_t mask = (uint32_t)(m - 1);
     const int order = nd.order, pmode = nd.pmode, c = nd.c, qt = nd.qt;
+    // the node's offsets in registers (one read of the descriptor per block)
+    const int64_t tab_off = N.tab_off, Lrep = N.Lrep, pad_tab = nd.pad_tab, t_tab = nd.t_tab;
+    const int64_t src_off = nd.src_off, src_stride = nd.src_stride, v_off = nd.v_off, cols = nd.cols;
+    const bool split = sizeof(T) == 4 && !nd.is_root;
     // block-uniform per-mode data: dim and child-table offset of each mode
     IdxT dim[MAXD];
     int64_t ctab[MAXD];
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
 #pragma unroll
         for (int j = 0; j < QTMAX; ++j)
             if (j >= c && j < qt) {
-                uint32_t w = tabr[nd.pad_tab + j];
+                uint32_t w = tabr[pad_tab + j];
                 neg ^= w;
                 b[j] = w & mask;
             }
@@ -226,13 +230,13 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
         return b[0];
     };
     auto store = [&](int r, int64_t col, T v) {
-        const int64_t dst = nd.v_off + (int64_t)r * nd.cols + col;
-        if (sizeof(T) == 4 && !nd.is_root) {
+        const int64_t dst = v_off + (int64_t)r * cols + col;
+        if (split) {
             // operand of the tensor-core product: TF32 hi part, then its lo part R*cols later
             uint32_t hi, lo;
             tf32_split((float)v, hi, lo);
             ws[dst] = (T)__uint_as_float(hi);
-            ws[dst + (int64_t)R * nd.cols] = (T)__uint_as_float(lo);
+            ws[dst + (int64_t)R * cols] = (T)__uint_as_float(lo);
         } else {
             ws[dst] = v;
         }
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
             for (int u = 0; u < kU; ++u) {
                 const int64_t q = q0 + (int64_t)u * blockDim.x;
                 const int64_t g = q / tw;
-                v[u] = q < (int64_t)G * tw ? tabs[N.tab_off + (r0 + g) * N.Lrep + nd.t_tab + (q - g * tw)] : 0u;
+                v[u] = q < (int64_t)G * tw ? tabs[tab_off + (r0 + g) * Lrep + t_tab + (q - g * tw)] : 0u;
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u)
@@ -265,7 +269,7 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
             for (int u = 0; u < kU; ++u) {
                 const int64_t q = q0 + (int64_t)u * blockDim.x;
                 const int64_t g = q >> N.log2m;
-                v[u] = q < (int64_t)G * m ? ws[nd.src_off + (r0 + g) * nd.src_stride + (q - g * m)] : (T)0;
+                v[u] = q < (int64_t)G * m ? ws[src_off + (r0 + g) * src_stride + (q - g * m)] : (T)0;
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u)
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
         __syncthreads();
         for (int g = 0; g < G; ++g) {
             const int r = r0 + g;
-            const uint32_t* tabr = tabs + N.tab_off + (int64_t)r * N.Lrep;
+            const uint32_t* tabr = tabs + tab_off + (int64_t)r * Lrep;
             for (int64_t c0 = it.begin + threadIdx.x; c0 < it.end; c0 += kU * blockDim.x) {
                 T val[kU];
 #pragma unroll
@@ -312,10 +316,10 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
             const int rl = (int)(len == 128 ? q >> 7 : q / len);
             const int r = it.a + rl;
             const int64_t col = it.begin + (q - (uint32_t)rl * len);
-            const uint32_t* tabr = tabs + N.tab_off + (int64_t)r * N.Lrep;
+            const uint32_t* tabr = tabs + tab_off + (int64_t)r * Lrep;
             uint32_t neg;
-            const uint32_t b0 = lookup(tabr, tabr + nd.t_tab, col, neg);
-            const T z = ws[nd.src_off + (int64_t)r * nd.src_stride + b0];
+            const uint32_t b0 = lookup(tabr, tabr + t_tab, col, neg);
+            const T z = ws[src_off + (int64_t)r * src_stride + b0];
             val[u] = (neg & TNSK_SIGN_BIT) ? -z : z;
             rr[u] = r;
             cc[u] = col;
@@ -444,6 +448,10 @@ __global__ void __launch_bounds__(256) m2_wscatter_kernel(const M2Node* __restri
     const uint32_t mask = (uint32_t)(m - 1);
     const int r0 = it.a, nr = it.b;
     const int64_t npar = nd.npar;
+    const uint32_t* __restrict__ tw0 = tabs + N.tab_off + nd.ptab;  // + r * Lrep + i
+    const float* __restrict__ w0 = ws + nd.w_off;                   // + r * npar + i
+    float* __restrict__ x0 = ws + nd.x_off + (int64_t)r0 * m;
+    const int64_t Lrep = N.Lrep;
     for (int64_t q = threadIdx.x; q < (int64_t)nr * m; q += blockDim.x) bins[q] = 0.f;
     __syncthreads();
     // (rep, row) pairs flat, kU per thread at once: all table words and W values are
@@ -462,8 +470,8 @@ __global__ void __launch_bounds__(256) m2_wscatter_kernel(const M2Node* __restri
             const int j = (int)(q / npar);
             const int64_t i = q - (int64_t)j * npar;
             const int r = r0 + j;
-            t[u] = tabs[N.tab_off + (int64_t)r * N.Lrep + nd.ptab + i];
-            v[u] = ws[nd.w_off + (int64_t)r * npar + i];
+            t[u] = tw0[(int64_t)r * Lrep + i];
+            v[u] = w0[(int64_t)r * npar + i];
             bj[u] = j;
         }
 #pragma unroll
@@ -472,8 +480,7 @@ __global__ void __launch_bounds__(256) m2_wscatter_kernel(const M2Node* __restri
                 atomicAdd(&bins[(int64_t)bj[u] * m + (t[u] & mask)], (t[u] & TNSK_SIGN_BIT) ? -v[u] : v[u]);
     }
     __syncthreads();
-    for (int64_t q = threadIdx.x; q < (int64_t)nr * m; q += blockDim.x)
-        ws[nd.x_off + (int64_t)r0 * m + q] = bins[q];
+    for (int64_t q = threadIdx.x; q < (int64_t)nr * m; q += blockDim.x) x0[q] = bins[q];
 }
 
 // ---------------------------------------------------------------------------
