@@ -199,9 +199,34 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
     }
     // sign word and bin of V(col, r): the child count-sketch words of col's indices, the
     // padding words, then the T-table levels (ttab: rep r's T tables)
+    // one child mode (the common case of a chain or a binary tree's matrices): its index
+    // is the column itself, no mixed-radix decode
+    int n_child_modes = 0, child_mode = 0;
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d)
+        if (d < order && d != pmode) ++n_child_modes, child_mode = d;
+    const bool one_child = n_child_modes == 1;
+    const int one_slot = (pmode >= 0 && child_mode > pmode) ? child_mode - 1 : child_mode;
+    const int64_t one_ctab = nd.ctab[one_slot < TNSK_MAX_ORDER ? one_slot : 0];
     auto lookup = [&](const uint32_t* __restrict__ tabr, const uint32_t* ttab, int64_t col, uint32_t& neg) {
         uint32_t b[QTMAX];
         neg = 0;
+        if (one_child) {
+            const uint32_t w = tabr[one_ctab + col];
+            neg = w;
+#pragma unroll
+            for (int j = 0; j < QTMAX; ++j)
+                if (j == one_slot) b[j] = w & mask;
+#pragma unroll
+            for (int j = 0; j < QTMAX; ++j)
+                if (j >= c && j < qt) {
+                    uint32_t wp = tabr[pad_tab + j];
+                    neg ^= wp;
+                    b[j] = wp & mask;
+                }
+            rsh_reduce<QTMAX>(b, neg, qt, ttab, m, mask);
+            return b[0];
+        }
         IdxT rem = (IdxT)col;
         // children are the non-parent modes in mode order: slot = d, or d - 1 after the parent
 #pragma unroll
@@ -456,28 +481,27 @@ __global__ void __launch_bounds__(256) m2_wscatter_kernel(const M2Node* __restri
     __syncthreads();
     // (rep, row) pairs flat, kU per thread at once: all table words and W values are
     // loaded before the shared-memory adds, so the loads of kU pairs overlap
-    constexpr int kU = 8;
-    const int64_t total = (int64_t)nr * npar;
-    for (int64_t q0 = threadIdx.x; q0 < total; q0 += kU * blockDim.x) {
-        uint32_t t[kU];
-        float v[kU];
-        int bj[kU];
+    // per rep, rows strided over the threads, kU rows per thread at once: all table
+    // words and W values are loaded before the shared-memory adds, so the loads overlap
+    constexpr int kU = 4;
+    for (int j = 0; j < nr; ++j) {
+        const uint32_t* __restrict__ twr = tw0 + (int64_t)(r0 + j) * Lrep;
+        const float* __restrict__ wr = w0 + (int64_t)(r0 + j) * npar;
+        float* bj = bins + (int64_t)j * m;
+        for (int64_t i0 = threadIdx.x; i0 < npar; i0 += kU * blockDim.x) {
+            uint32_t t[kU];
+            float v[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int64_t q = q0 + (int64_t)u * blockDim.x;
-            bj[u] = -1;
-            if (q >= total) continue;
-            const int j = (int)(q / npar);
-            const int64_t i = q - (int64_t)j * npar;
-            const int r = r0 + j;
-            t[u] = tw0[(int64_t)r * Lrep + i];
-            v[u] = w0[(int64_t)r * npar + i];
-            bj[u] = j;
+            for (int u = 0; u < kU; ++u) {
+                const int64_t i = i0 + (int64_t)u * blockDim.x;
+                t[u] = i < npar ? twr[i] : 0u;
+                v[u] = i < npar ? wr[i] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (i0 + (int64_t)u * blockDim.x < npar)
+                    atomicAdd(&bj[t[u] & mask], (t[u] & TNSK_SIGN_BIT) ? -v[u] : v[u]);
         }
-#pragma unroll
-        for (int u = 0; u < kU; ++u)
-            if (bj[u] >= 0)
-                atomicAdd(&bins[(int64_t)bj[u] * m + (t[u] & mask)], (t[u] & TNSK_SIGN_BIT) ? -v[u] : v[u]);
     }
     __syncthreads();
     for (int64_t q = threadIdx.x; q < (int64_t)nr * m; q += blockDim.x) x0[q] = bins[q];
