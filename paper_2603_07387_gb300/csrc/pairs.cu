@@ -76,44 +76,37 @@ __device__ __forceinline__ void rows_same_b(const float* __restrict__ A, const f
 
 // The same rows when the last output mode runs along B only (la = 0, lb = 1) with
 // 4 <= L <= 32, L % 4 == 0: 8 lanes per row, 4 consecutive columns per lane (16-byte
-// stores), 4 rows per pass of the warp. The A terms do not depend on the column:
-// lane i loads row base + i's NS terms once into the warp's shared-memory slab
-// (8 floats a row), and each row's lanes read them back as two 16-byte broadcasts,
-// so no global load waits inside the row loop. Pairs of columns are updated with
-// packed FP32 FMAs (each half rounds like fmaf).
+// stores), 4 rows per pass of the warp. The A terms do not depend on the column: lane
+// i loads row base + i's NS terms once, and each row takes them by shuffle, so no
+// load waits inside the row loop.
 template <int NS>
 __device__ __forceinline__ void rows_same_b_v4(const float* __restrict__ A, const float* __restrict__ B,
-                                               float* __restrict__ out, const int2* __restrict__ tab,
-                                               float* __restrict__ slab, int ra, int rb, int L, int nr, int base,
-                                               int lane) {
+                                               float* __restrict__ out, const int2* __restrict__ tab, int ra,
+                                               int rb, int L, int nr, int base, int lane) {
     const int r4 = lane >> 3, c = (lane & 7) * 4;
     const bool live = c < L;
-    float2 bv[NS][2];
+    float av[NS];
+    float bv[NS][4];
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
         const int2 t = tab[q];
-        slab[lane * 8 + q] = lane < nr ? __ldg(A + ra + t.x) : 0.f;
-        bv[q][0] = live ? make_float2(__ldg(B + rb + c + t.y), __ldg(B + rb + c + 1 + t.y)) : make_float2(0.f, 0.f);
-        bv[q][1] = live ? make_float2(__ldg(B + rb + c + 2 + t.y), __ldg(B + rb + c + 3 + t.y)) : make_float2(0.f, 0.f);
+        av[q] = lane < nr ? __ldg(A + ra + t.x) : 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[q][j] = live ? __ldg(B + rb + c + j + t.y) : 0.f;
     }
-    __syncwarp();
     for (int i = 0; i < nr; i += 4) {
         const int row = i + r4;
-        const float4* ar = reinterpret_cast<const float4*>(slab + (row & 31) * 8);
-        const float4 a03 = ar[0];
-        const float4 a47 = NS > 4 ? ar[1] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float av[8] = {a03.x, a03.y, a03.z, a03.w, a47.x, a47.y, a47.z, a47.w};
-        float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
-            const float2 a2 = make_float2(av[q], av[q]);
-            acc0 = __ffma2_rn(a2, bv[q][0], acc0);
-            acc1 = __ffma2_rn(a2, bv[q][1], acc1);
+            const float a = __shfl_sync(0xffffffffu, av[q], row & 31);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[j] += a * bv[q][j];
         }
         if (live && row < nr)
-            *reinterpret_cast<float4*>(out + (int64_t)(base + row) * L + c) = make_float4(acc0.x, acc0.y, acc1.x, acc1.y);
+            *reinterpret_cast<float4*>(out + (int64_t)(base + row) * L + c) =
+                make_float4(acc[0], acc[1], acc[2], acc[3]);
     }
-    __syncwarp();  // the slab is rewritten by the warp's next group
 }
 
 }  // namespace
@@ -125,7 +118,6 @@ template <bool kFast>
 __global__ void __launch_bounds__(256, 4) contract_pairs_kernel(const PairDesc* __restrict__ jobs) {
     __shared__ PairDesc d;
     __shared__ int2 tab[kShTable];  // (A, B) offsets of the shared combinations, 32-bit path
-    __shared__ __align__(16) float slabs[kFast ? 8 * 32 * 8 : 1];  // per warp: 32 rows x 8 A terms
     {  // the job's descriptor, copied by the whole block
         const uint64_t* src = reinterpret_cast<const uint64_t*>(jobs + blockIdx.y);
         uint64_t* dst = reinterpret_cast<uint64_t*>(&d);
@@ -182,7 +174,7 @@ __global__ void __launch_bounds__(256, 4) contract_pairs_kernel(const PairDesc* 
             if (same_b && v4 && ns <= 8) {
                 switch (ns) {
 #define TNSK_ROWS(n) \
-    case n: rows_same_b_v4<n>(A, B, d.out, tab, slabs + (threadIdx.x >> 5) * 256, ra, rb, L, nr, base, lane); break;
+    case n: rows_same_b_v4<n>(A, B, d.out, tab, ra, rb, L, nr, base, lane); break;
                     TNSK_ROWS(1) TNSK_ROWS(2) TNSK_ROWS(3) TNSK_ROWS(4) TNSK_ROWS(5) TNSK_ROWS(6) TNSK_ROWS(7)
                     TNSK_ROWS(8)
 #undef TNSK_ROWS
