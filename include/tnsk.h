@@ -63,11 +63,31 @@ typedef enum { TNSK_PREC_FP32 = 0, TNSK_PREC_FP64 = 2 } tnsk_precision;
 
 typedef struct tnsk_ctx tnsk_ctx;
 
+/* A grouped tensor (Sec. 4.1, grouping: two tensors contracted exactly along their
+ * shared mode become one tensor): R((i, j), (k, l)) = sum_s A(i, s, k) B(j, s, l),
+ * an order-2 tensor of dims [a*b, c*d] (first index i*b + j, second k*d + l). The
+ * rung of two tensor trains joined on their physical legs has this form. Entries are
+ * never stored: the method-2 sketch product computes them from A and B (FP32 sums in
+ * the order s = 0, 1, ...: the values contract_pairs would write). */
+typedef struct {
+    const void* A;          /* device FP32 [a][s][c], row-major */
+    const void* B;          /* device FP32 [b][s][d], row-major */
+    int64_t a, s, c, b, d;  /* all >= 1 */
+} tnsk_rung;
+
 typedef struct {
     int32_t order;          /* q_k >= 0 (0 = scalar) */
     const int64_t* dims;    /* [order] host */
-    const void* data;       /* device, row-major, numel = prod dims */
+    const void* data;       /* device, row-major, numel = prod dims; NULL with rung */
     tnsk_dtype dtype;
+    const tnsk_rung* rung;  /* host; NULL for a tensor stored at data. Else the tensor
+                               is the grouped tensor above: order 2, dims
+                               [a*b, c*d], dtype TNSK_F32, data NULL; accepted by
+                               TNSK_ACYCLIC in FP32 where it is an inner node of the
+                               rooted tree (neither a leaf nor the root) and the
+                               column pair's fast index (d, or b when the parent mode
+                               is the second) is a multiple of 32, the staged B factor
+                               within 64 KiB and s <= 16; elsewhere TNSK_ERR_UNSUPPORTED */
 } tnsk_tensor;
 
 typedef struct {

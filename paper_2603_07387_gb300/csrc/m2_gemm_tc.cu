@@ -500,6 +500,238 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
     if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
+// ---------------------------------------------------------------------------
+// Grouped-tensor variant (tnsk_rung, the grouping of Sec. 4.1): X(row, col) =
+// sum_s A(.., s, ..) B(.., s, ..) is never stored. Rows are (i1, i2) (i2 fastest),
+// columns (j1, j2) (j2 fastest, its dim a multiple of 32, so a 32-column chunk has
+// one j1); A's entry (i1, s, j1) is at i1 ai + j1 aj + s as, B's (i2, s, j2) at
+// i2 bi + j2 bj + s bs. The B factor is copied once per CTA into shared memory as
+// [i2][s][j2] rows padded to 4 mod 32 floats (a warp's 32 rows read 16-byte vectors
+// without bank conflicts); the converters form their row's 32 entries of each chunk
+// (FP32 fmaf over s in ascending order: the values contract_pairs writes), split
+// them into TF32 hi / lo and store them to tensor memory as the streaming kernel
+// does; only the V^T tiles arrive by TMA. Same warp roles, barriers and epilogue.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kRungRing = kRawStages * 2 * kRawV;  // V^T hi + lo per stage
+}  // namespace
+
+__global__ void __launch_bounds__(192, 2) m2_gemm_tc_rung_kernel(const M2Node* __restrict__ nodes,
+                                                                 const M2Net* __restrict__ nets,
+                                                                 const M2Item* __restrict__ items,
+                                                                 float* __restrict__ ws,
+                                                                 const unsigned char* __restrict__ tmaps,
+                                                                 int* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t raw_full[kRawStages], raw_empty[kRawStages];
+    __shared__ __align__(8) uint64_t tm_full[kTmStages], tm_empty[kTmStages];
+    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ uint32_t tmem_base;
+    unsigned char* raw = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    float* sB = reinterpret_cast<float*>(raw + kRungRing);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const M2Item it = items[blockIdx.x];
+    const M2Node& nd = nodes[it.node];
+    const M2Net& N = nets[nd.net];
+    const int R = N.R;
+    const int64_t row0 = (int64_t)it.a * kTM;
+    const int rep0 = it.b * kTN;
+    const int64_t npar = nd.npar, cols = nd.cols;
+    const int total_chunks = (int)((cols + kKC - 1) / kKC);
+    const int cbeg = (int)(((int64_t)total_chunks * it.pad_) / it.begin);
+    const int cend = (int)(((int64_t)total_chunks * (it.pad_ + 1)) / it.begin);
+    const int nch = cend - cbeg;
+    const void* tmvh = tmaps + (int64_t)nd.tm_v * 128;
+    const void* tmvl = tmaps + (int64_t)(nd.tm_v + 1) * 128;
+    const int ni2 = nd.rn_i2, nj2 = nd.rn_j2, sn = nd.rs;
+    const int bp = sn * nj2 + 4;  // padded B row (floats)
+
+    // the B factor, all threads: sB[i2 * bp + s * nj2 + j2] = B(i2, s, j2)
+    {
+        const float* __restrict__ Bg = nd.rB;
+        const int per_i2 = sn * nj2;
+        const int total = ni2 * per_i2;
+        for (int q = tid; q < total; q += blockDim.x) {
+            const int i2 = q / per_i2, rem = q - i2 * per_i2;
+            const int sv = rem / nj2, j2 = rem - sv * nj2;
+            sB[i2 * bp + rem] = __ldg(Bg + (int64_t)i2 * nd.r_bi + (int64_t)sv * nd.r_bs + (int64_t)j2 * nd.r_bj);
+        }
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int st = 0; st < kRawStages; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&raw_full[st])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&raw_empty[st])));
+        }
+        for (int t = 0; t < kTmStages; ++t) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(&tm_full[t])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&tm_empty[t])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&done_bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    bool ok = true;
+
+    if (warp == 0) {
+        // ---------------- producer (one thread): the V^T hi / lo tiles of each chunk
+        if (lane == 0) {
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvh) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvl) : "memory");
+            for (int c = 0; c < nch && ok; ++c) {
+                const int st = c % kRawStages;
+                if (c >= kRawStages)
+                    ok = mbar_wait(smem_addr(&raw_empty[st]), (uint32_t)((c / kRawStages - 1) & 1));
+                if (!ok) break;
+                const int k0 = (cbeg + c) * kKC;
+                unsigned char* stp = raw + st * 2 * kRawV;
+                const uint32_t bar = smem_addr(&raw_full[st]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2 * kRawV)
+                             : "memory");
+                tma_load_2d(smem_addr(stp), tmvh, k0, rep0, bar);
+                tma_load_2d(smem_addr(stp + kRawV), tmvl, k0, rep0, bar);
+            }
+        }
+        __syncwarp();
+    } else if (warp <= 4) {
+        // ---------------- converters: thread = row q4 * 32 + lane of the tile (its TMEM lane)
+        const int q4 = warp & 3;
+        const int r = q4 * 32 + lane;
+        const int64_t row = row0 + r;
+        const bool live = row < npar;
+        const int i1 = live ? (int)(row / ni2) : 0, i2 = live ? (int)(row - (int64_t)i1 * ni2) : 0;
+        const float* __restrict__ Arow = nd.rA + (int64_t)i1 * nd.r_ai;
+        const float* Brow = sB + i2 * bp;
+        const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+        for (int c = 0; c < nch && ok; ++c) {
+            const int t = c % kTmStages;
+            if (c >= kTmStages) ok = mbar_wait(smem_addr(&tm_empty[t]), (uint32_t)((c / kTmStages - 1) & 1));
+            if (!ok) break;
+            const int k0 = (cbeg + c) * kKC;
+            const int j1 = k0 / nj2, j20 = k0 - j1 * nj2;
+            float x[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) x[j] = 0.f;
+            if (live) {
+                const float* __restrict__ Aj = Arow + (int64_t)j1 * nd.r_aj;
+                for (int sv = 0; sv < sn; ++sv) {
+                    const float a = __ldg(Aj + (int64_t)sv * nd.r_as);
+                    const float4* bq = reinterpret_cast<const float4*>(Brow + sv * nj2 + j20);
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) {
+                        const float4 b = bq[g];
+                        x[4 * g + 0] = fmaf(a, b.x, x[4 * g + 0]);
+                        x[4 * g + 1] = fmaf(a, b.y, x[4 * g + 1]);
+                        x[4 * g + 2] = fmaf(a, b.z, x[4 * g + 2]);
+                        x[4 * g + 3] = fmaf(a, b.w, x[4 * g + 3]);
+                    }
+                }
+            }
+            uint32_t hi[32], lo[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) tf32_split(x[j], hi[j], lo[j]);
+            const uint32_t col = (uint32_t)(kTN + 64 * t);
+            tmem_store32(tmem + lane_base + col, hi);
+            tmem_store32(tmem + lane_base + col + 32, lo);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_addr(&tm_full[t]));
+        }
+    } else if (lane == 0) {
+        // ---------------- MMA issue (warp 5, one thread)
+        for (int c = 0; c < nch && ok; ++c) {
+            const int st = c % kRawStages, t = c % kTmStages;
+            ok = mbar_wait(smem_addr(&tm_full[t]), (uint32_t)((c / kTmStages) & 1));
+            if (ok) ok = mbar_wait(smem_addr(&raw_full[st]), (uint32_t)((c / kRawStages) & 1));
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned char* stp = raw + st * 2 * kRawV;
+            const uint32_t a_hi = tmem + (uint32_t)(kTN + 64 * t), a_lo = a_hi + 32;
+            const uint32_t aop[3] = {a_hi, a_hi, a_lo};
+            const unsigned char* bop[3] = {stp, stp + kRawV, stp};
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int ks = 0; ks < kKC / 8; ++ks) {
+                    const uint32_t at = aop[p] + ks * 8;
+                    const uint64_t bd = smem_desc_sw128(smem_addr(bop[p]) + ks * 32);
+                    const uint32_t acc = (c > 0 || p > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, q;\n\t}" ::"r"(tmem),
+                        "r"(at), "l"(bd), "r"(kIdesc), "r"(acc));
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_addr(&tm_empty[t])));
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_addr(&raw_empty[st])));
+            if (c == nch - 1)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_addr(&done_bar)));
+        }
+    }
+    if (!ok && (lane == 0)) atomicExch(err, DEVERR_TIMEOUT);
+
+    if (warp >= 1 && warp <= 4 && ok && nch > 0) {
+        // ---------------- epilogue: W^T[rep][row] from TMEM lanes 32 (warp % 4) .. + 31
+        const bool done = mbar_wait(smem_addr(&done_bar), 0u);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!done) {
+            if (lane == 0) atomicExch(err, DEVERR_TIMEOUT);
+        } else {
+            const int q4 = warp & 3;
+            const int64_t row = row0 + q4 * 32 + lane;
+#pragma unroll
+            for (int cc = 0; cc < kTN / 16; ++cc) {
+                uint32_t v[16];
+                const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(cc * 16);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < npar) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int rep = rep0 + cc * 16 + j;
+                        if (rep < R) {
+                            float* dst = &ws[nd.w_off + (int64_t)rep * npar + row];
+                            if (it.begin > 1)
+                                atomicAdd(dst, __uint_as_float(v[j]));  // K split: partial sums
+                            else
+                                *dst = __uint_as_float(v[j]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+size_t m2_gemm_rung_smem(size_t b_bytes) { return 1024 + (size_t)kRungRing + b_bytes; }
+
+cudaError_t launch_m2_gemm_tc_rung(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items, float* ws,
+                                   const unsigned char* tmaps, int* err, size_t smem, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    cudaFuncSetAttribute(m2_gemm_tc_rung_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    m2_gemm_tc_rung_kernel<<<n, 192, smem, s>>>(nodes, nets, items, ws, tmaps, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_m2_gemm_tc(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items,
                               const uint32_t* tabs, float* ws, const unsigned char* tmaps, int* err, bool stream,
                               cudaStream_t s) {

@@ -539,7 +539,7 @@ template <typename T>
 static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void* const* d_tws, cudaStream_t s,
                             Profiler& prof, int* d_err) {
     static const int kKind[M2_NKINDS] = {TNSK_K_M2_LEAF, TNSK_K_M2_COMPOSE, TNSK_K_M2_VBUILD, TNSK_K_M2_GEMM,
-                                         TNSK_K_M2_GEMM, TNSK_K_M2_SCATTER, TNSK_K_M2_ROOT};
+                                         TNSK_K_M2_GEMM, TNSK_K_M2_GEMM,    TNSK_K_M2_SCATTER, TNSK_K_M2_ROOT};
     const M2Node* nodes = (const M2Node*)(base + P.m2.nodes_off);
     const M2Net* nets = (const M2Net*)(base + P.m2.nets_off);
     const M2Item* items = (const M2Item*)(base + P.m2.items_off);
@@ -576,6 +576,11 @@ static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void*
                                           kind == M2_GEMM_STREAM, s);
                     else
                         m2_gemm_kernel<T><<<n, 256, 0, s>>>(nodes, nets, its, tabs, ws);
+                    break;
+                case M2_GEMM_RUNG:  // FP32 plans only (the plan rejects grouped tensors in FP64)
+                    if (sizeof(T) == 4)
+                        launch_m2_gemm_tc_rung(n, nodes, nets, its, (float*)ws, base + P.m2.tmaps_off, d_err,
+                                               P.m2.rung_smem, s);
                     break;
                 case M2_WSCATTER: {
                     const size_t smem = P.m2.scatter_smem;

@@ -69,6 +69,13 @@ struct M2Node {
     int32_t tm_x;     // streaming tensor-core path: tensor-map index of X and of V^T
     int32_t tm_v;
     int32_t pad_;
+    // grouped (rung) tensor, M2_GEMM_RUNG: X(row, col) = sum_s A[i1 ai + j1 aj + s as]
+    // B[i2 bi + j2 bj + s bs] with row = i1 rn_i2 + i2, col = j1 rn_j2 + j2
+    const float* rA;
+    const float* rB;
+    int32_t rn_i1, rn_i2, rn_j1, rn_j2, rs;
+    int32_t r_ai, r_aj, r_as, r_bi, r_bj, r_bs;
+    int32_t rpad_;
 };
 
 struct M2Net {
@@ -99,9 +106,10 @@ enum M2Kind {
     M2_VBUILD = 2,
     M2_GEMM = 3,
     M2_GEMM_STREAM = 4,
-    M2_WSCATTER = 5,
-    M2_ROOT = 6,
-    M2_NKINDS = 7
+    M2_GEMM_RUNG = 5,
+    M2_WSCATTER = 6,
+    M2_ROOT = 7,
+    M2_NKINDS = 8
 };
 
 struct M2Plan {
@@ -115,6 +123,7 @@ struct M2Plan {
     size_t tmaps_off = 0;  // tensor maps (128 B each) in the descriptor block
     size_t scatter_smem = 0;  // shared-memory bins of the largest row-scatter item
     size_t vbuild_smem = 0;   // staged T tables + child sketches of the largest staged V-build item
+    size_t rung_smem = 0;     // dynamic shared memory of the grouped-tensor GEMM (V ring + B)
     // tensor maps to encode once the device addresses are fixed: node, 0 = X / 1 = V^T hi / 2 = lo
     std::vector<std::pair<int, int>> tmap_jobs;
     int max_log2m = 0;
@@ -129,5 +138,9 @@ tnsk_status run_method2(const BatchPlan& plan, unsigned char* base, bool fp64, c
 cudaError_t launch_m2_gemm_tc(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items,
                               const uint32_t* tabs, float* ws, const unsigned char* tmaps, int* err, bool stream,
                               cudaStream_t s);
+// Grouped-tensor tiles (M2_GEMM_RUNG); smem from m2_gemm_rung_smem(bytes of the staged B).
+size_t m2_gemm_rung_smem(size_t b_bytes);
+cudaError_t launch_m2_gemm_tc_rung(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items, float* ws,
+                                   const unsigned char* tmaps, int* err, size_t smem, cudaStream_t s);
 
 }  // namespace tnsk

@@ -573,6 +573,8 @@ tnsk_status network_features(tnsk_ctx* ctx, const tnsk_network& net, const tnsk_
     }
     int comps = 0;
     for (int k = 0; k < I.p; ++k) comps += find(k) == k;
+    for (int k = 0; k < I.p; ++k)
+        if (I.rung[k]) return ctx_fail(ctx, TNSK_ERR_UNSUPPORTED, "features: grouped (rung) tensors have no stored entries");
     // Frobenius norms on the device (FP64 sums of squares)
     double* d = nullptr;
     if (cudaMalloc((void**)&d, std::max(I.p, 1) * sizeof(double)) != cudaSuccess) {

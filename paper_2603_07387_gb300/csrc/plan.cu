@@ -196,6 +196,26 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
             }
         }
         I.numel[k] = n;
+        I.rung.push_back(X.rung);
+        if (X.rung) {  // grouped tensor (Sec. 4.1): R((i,j),(k,l)) = sum_s A(i,s,k) B(j,s,l)
+            const tnsk_rung& g = *X.rung;
+            if (prm.method != TNSK_ACYCLIC || prm.prec != TNSK_PREC_FP32) {
+                why = "tensor " + std::to_string(k) + ": grouped (rung) tensors need method 2 in FP32";
+                return TNSK_ERR_UNSUPPORTED;
+            }
+            if (X.order != 2 || X.dtype != TNSK_F32 || X.data || !g.A || !g.B || g.a < 1 || g.s < 1 || g.c < 1 ||
+                g.b < 1 || g.d < 1 || X.dims[0] != g.a * g.b || X.dims[1] != g.c * g.d) {
+                why = "tensor " + std::to_string(k) +
+                      ": a rung tensor is order 2, FP32, data NULL, dims [a*b, c*d], A and B set, sizes >= 1";
+                return TNSK_ERR_INVALID;
+            }
+            const int64_t lim = (int64_t)1 << 31;
+            if (g.s > 16 || g.a * g.s * g.c >= lim || g.b * g.s * g.d >= lim || n >= lim) {
+                why = "tensor " + std::to_string(k) + ": rung tensor above the kernel's limits (s <= 16, < 2^31 entries)";
+                return TNSK_ERR_UNSUPPORTED;
+            }
+            continue;
+        }
         if (n > 0 && !X.data) {
             why = "null data for a non-empty tensor";
             return TNSK_ERR_INVALID;
@@ -671,6 +691,37 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
             }
             nd.ptab = nd.is_root ? -1 : I.eoff[I.parent_edge[k]];
             nd.c = (int)I.child[k].size();
+            if (I.rung[k]) {
+                // grouped tensor: generated inside the sketch product, so it must be an inner
+                // node (leaves and the root read their entries directly)
+                const tnsk_rung& g = *I.rung[k];
+                if (nd.is_root || nd.c == 0 || nd.order != 2) {
+                    err = "tensor " + std::to_string(k) + ": a rung tensor must be an inner node of the rooted tree";
+                    return TNSK_ERR_UNSUPPORTED;
+                }
+                const bool first = nd.pmode == 0;  // rows (i, j), columns (k, l); else transposed
+                nd.rA = (const float*)g.A;
+                nd.rB = (const float*)g.B;
+                nd.rs = (int32_t)g.s;
+                nd.rn_i1 = (int32_t)(first ? g.a : g.c);
+                nd.rn_i2 = (int32_t)(first ? g.b : g.d);
+                nd.rn_j1 = (int32_t)(first ? g.c : g.a);
+                nd.rn_j2 = (int32_t)(first ? g.d : g.b);
+                // A(i, s, k) at i s c + s c + k; B(j, s, l) at j s d + s d + l
+                nd.r_as = (int32_t)g.c;
+                nd.r_bs = (int32_t)g.d;
+                nd.r_ai = (int32_t)(first ? g.s * g.c : 1);
+                nd.r_aj = (int32_t)(first ? 1 : g.s * g.c);
+                nd.r_bi = (int32_t)(first ? g.s * g.d : 1);
+                nd.r_bj = (int32_t)(first ? 1 : g.s * g.d);
+                const int64_t b_bytes = (int64_t)nd.rn_i2 * (g.s * nd.rn_j2 + 4) * 4;
+                if (nd.rn_j2 % 32 != 0 || b_bytes > 60 * 1024 || !tma) {
+                    err = "tensor " + std::to_string(k) +
+                          ": rung tensor needs its column fast index a multiple of 32 and the B factor within 60 KiB";
+                    return TNSK_ERR_UNSUPPORTED;
+                }
+                P.m2.rung_smem = std::max(P.m2.rung_smem, m2_gemm_rung_smem((size_t)b_bytes));
+            }
             nd.qt = qt[k];
             P.m2.max_qt = std::max(P.m2.max_qt, nd.qt);
             P.m2.max_order = std::max(P.m2.max_order, nd.order);
@@ -763,9 +814,15 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 // row tiles: 128 rows for the tensor-core kernels (FP32), 64 for the FP64 one;
                 // the split of K (tensor-core kernels) is chosen once all tiles are known
                 const int64_t tile = fp64 ? 64 : 128;
-                const bool stream = !fp64 && tma && nd.dtype == TNSK_F32 && nd.A == 1 && (nd.cols % 4) == 0 &&
-                                    ((uintptr_t)nd.data % 16) == 0 && nd.npar < ((int64_t)1 << 31) &&
-                                    nd.cols < ((int64_t)1 << 31);
+                const bool rung = I.rung[k] != nullptr;
+                const bool stream = !rung && !fp64 && tma && nd.dtype == TNSK_F32 && nd.A == 1 &&
+                                    (nd.cols % 4) == 0 && ((uintptr_t)nd.data % 16) == 0 &&
+                                    nd.npar < ((int64_t)1 << 31) && nd.cols < ((int64_t)1 << 31);
+                if (rung) {  // V^T hi / lo maps only: X is generated
+                    m2nodes.back().tm_v = (int32_t)P.m2.tmap_jobs.size();
+                    P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 1});
+                    P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 2});
+                }
                 if (stream) {
                     m2nodes.back().tm_x = (int32_t)P.m2.tmap_jobs.size();
                     P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 0});
@@ -775,7 +832,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 }
                 for (int64_t rt = 0; rt * tile < nd.npar; ++rt)
                     for (int64_t ct = 0; ct * 64 < R; ++ct)
-                        pend.push_back({h, stream ? M2_GEMM_STREAM : M2_GEMM,
+                        pend.push_back({h, rung ? M2_GEMM_RUNG : (stream ? M2_GEMM_STREAM : M2_GEMM),
                                         M2Item{node_idx, (int)rt, (int)ct, 0, 1, 0}});
             }
             if (nd.is_root)  // chunks of 4096 columns x blocks of 8 reps (one warp each)
@@ -816,11 +873,11 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     if (!fp64 && !pend.empty()) {
         std::vector<int64_t> tiles(P.m2.max_height + 1, 0);
         for (const PendingItem& q : pend)
-            if (q.kind == M2_GEMM || q.kind == M2_GEMM_STREAM) tiles[q.h]++;
+            if (q.kind == M2_GEMM || q.kind == M2_GEMM_STREAM || q.kind == M2_GEMM_RUNG) tiles[q.h]++;
         std::vector<PendingItem> out;
         out.reserve(pend.size());
         for (const PendingItem& q : pend) {
-            if (q.kind != M2_GEMM && q.kind != M2_GEMM_STREAM) {
+            if (q.kind != M2_GEMM && q.kind != M2_GEMM_STREAM && q.kind != M2_GEMM_RUNG) {
                 out.push_back(q);
                 continue;
             }

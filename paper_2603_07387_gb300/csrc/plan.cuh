@@ -25,6 +25,7 @@ struct NetInfo {
     int64_t O = 1;                  // output entries
     int log2m = 0;
     bool idx32 = true;
+    std::vector<const tnsk_rung*> rung;  // [p] grouped tensors (NULL: stored)
     // method 2: rooted tree (children in mode order, footnote to Gamma(k))
     int root = -1;
     std::vector<int> parent, parent_mode, parent_edge, height;

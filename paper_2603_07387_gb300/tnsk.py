@@ -78,12 +78,25 @@ class TnskError(RuntimeError):
         self.status = status
 
 
+class _Rung(ctypes.Structure):
+    _fields_ = [
+        ("A", ctypes.c_void_p),
+        ("B", ctypes.c_void_p),
+        ("a", ctypes.c_int64),
+        ("s", ctypes.c_int64),
+        ("c", ctypes.c_int64),
+        ("b", ctypes.c_int64),
+        ("d", ctypes.c_int64),
+    ]
+
+
 class _Tensor(ctypes.Structure):
     _fields_ = [
         ("order", ctypes.c_int32),
         ("dims", ctypes.POINTER(ctypes.c_int64)),
         ("data", ctypes.c_void_p),
         ("dtype", ctypes.c_int32),
+        ("rung", ctypes.POINTER(_Rung)),
     ]
 
 
@@ -220,13 +233,50 @@ def _dtype_code(t):
     raise TypeError(f"unsupported tensor dtype {t.dtype}")
 
 
+class Rung:
+    """A grouped tensor (tnsk_rung): R[(i, j), (k, l)] = sum_s A[i, s, k] B[j, s, l] for
+    contiguous FP32 CUDA tensors A [a, s, c] and B [b, s, d]; an order-2 tensor of
+    shape (a*b, c*d) whose entries the method-2 sketch product forms from A and B."""
+
+    def __init__(self, A, B):
+        if A.dim() != 3 or B.dim() != 3 or A.shape[1] != B.shape[1]:
+            raise ValueError("rung factors are [a, s, c] and [b, s, d] with equal s")
+        self.A, self.B = A, B
+        a, s, c = A.shape
+        b, _, d = B.shape
+        self.shape = (a * b, c * d)
+
+    def dim(self):
+        return 2
+
+    def numel(self):
+        return self.shape[0] * self.shape[1]
+
+
 class _NetHolder:
     """Owns the ctypes arrays behind one tnsk_network."""
 
     def __init__(self, net: Network):
         self.dims = []
+        self.rungs = []
         tens = (_Tensor * max(1, len(net.tensors)))()
         for k, x in enumerate(net.tensors):
+            if isinstance(x, Rung):
+                for f in (x.A, x.B):
+                    if not f.is_contiguous() or _dtype_code(f) != F32:
+                        raise ValueError(f"tensor {k}: rung factors must be contiguous FP32")
+                a, s, c = x.A.shape
+                b, _, dd = x.B.shape
+                g = _Rung(x.A.data_ptr(), x.B.data_ptr(), a, s, c, b, dd)
+                self.rungs.append(g)
+                d = (ctypes.c_int64 * 2)(*x.shape)
+                self.dims.append(d)
+                tens[k].order = 2
+                tens[k].dims = ctypes.cast(d, ctypes.POINTER(ctypes.c_int64))
+                tens[k].data = None
+                tens[k].dtype = F32
+                tens[k].rung = ctypes.pointer(g)
+                continue
             if x.numel() > 0 and not x.is_contiguous():
                 raise ValueError(f"tensor {k} must be contiguous (row-major)")
             d = (ctypes.c_int64 * max(1, x.dim()))(*x.shape)

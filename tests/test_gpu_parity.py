@@ -261,6 +261,68 @@ def test_method2_tt_chain_full_size(ctx):
     assert_parity(per, y, s, TOL[p.prec], "tt_chain")
 
 
+def _rung_chain(sites, bond, phys, seed):
+    """FP32 tensor-train cores, the oracle's dense chain of their rung merges (FP64 sums
+    of the FP32 values), and the same chain for the library with the inner sites as
+    grouped tensors (tnsk.Rung) and the two end vectors stored."""
+    A, B = W.tt_cores(sites=sites, bond=bond, phys=phys, seed=seed)
+    A = [a.astype(np.float32).astype(np.float64) for a in A]
+    B = [b.astype(np.float32).astype(np.float64) for b in B]
+    spec = W.tt_chain(A, B)
+    ts = [torch.as_tensor(spec.tensors[0], dtype=torch.float32, device="cuda")]
+    ts += [tnsk.Rung(torch.as_tensor(A[k], dtype=torch.float32, device="cuda"),
+                     torch.as_tensor(B[k], dtype=torch.float32, device="cuda")) for k in range(1, sites - 1)]
+    ts.append(torch.as_tensor(spec.tensors[-1], dtype=torch.float32, device="cuda"))
+    return spec, tnsk.Network(ts, spec.edges, [])
+
+
+@pytest.mark.parametrize("root", [0, -2])
+def test_method2_grouped_rung_tensors(ctx, root):
+    """Inner sites given as grouped tensors (entries formed inside the tensor-core sketch
+    product, never stored) against the oracle on the dense merged chain, and against the
+    library's own dense path; root 0 puts every parent mode first, the last site as root
+    puts it second (the transposed form)."""
+    sites = 5
+    spec, net = _rung_chain(sites, 32, 8, seed=77)
+    r = 0 if root == 0 else sites - 1
+    p = tnsk.Params(m=1024, reps=16, seed=123, method=tnsk.ACYCLIC, root=r)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    per = torch.zeros((p.reps, 1), dtype=torch.float64, device="cuda")
+    ctx.estimate(net, p, out, per)
+    ctx.sync()
+    y, sc = oracle_estimate(spec, p, torch.float32)
+    assert_parity(per.cpu().numpy(), y, sc, TOL[p.prec], f"rung chain root={r}")
+    _, per_dense = gpu_estimate(ctx, spec, p, torch.float32)
+    assert np.all(np.abs(per.cpu().numpy() - per_dense) <= 1e-6 * sc)
+    # a plan (CUDA-graph replays) gives the same estimates
+    outp = torch.zeros(1, dtype=torch.float64, device="cuda")
+    pl = ctx.plan([net], [p], [outp])
+    for _ in range(3):
+        pl.run()
+    ctx.sync()
+    assert abs(outp.item() - out.item()) <= 1e-6 * float(np.abs(sc).max())
+    pl.close()
+
+
+def test_grouped_rung_tensors_rejected_where_unsupported(ctx):
+    spec, net = _rung_chain(4, 32, 4, seed=5)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(tnsk.TnskError):  # method 1 reads stored entries
+        ctx.estimate(net, tnsk.Params(m=256, reps=4, method=tnsk.GENERAL), out)
+    with pytest.raises(tnsk.TnskError):  # FP64 plans have no grouped-tensor product
+        ctx.estimate(net, tnsk.Params(m=256, reps=4, method=tnsk.ACYCLIC, prec=tnsk.PREC_FP64), out)
+    with pytest.raises(tnsk.TnskError):  # the grouped tensor as the root
+        ctx.estimate(net, tnsk.Params(m=256, reps=4, method=tnsk.ACYCLIC, root=1), out)
+    A, B = W.tt_cores(sites=4, bond=24, phys=4, seed=6)  # column fast index 24: not a multiple of 32
+    spec24 = W.tt_chain(A, B)
+    ts = [torch.as_tensor(spec24.tensors[0], dtype=torch.float32, device="cuda")]
+    ts += [tnsk.Rung(torch.as_tensor(A[k], dtype=torch.float32, device="cuda"),
+                     torch.as_tensor(B[k], dtype=torch.float32, device="cuda")) for k in (1, 2)]
+    ts.append(torch.as_tensor(spec24.tensors[-1], dtype=torch.float32, device="cuda"))
+    with pytest.raises(tnsk.TnskError):
+        ctx.estimate(tnsk.Network(ts, spec24.edges, []), tnsk.Params(m=256, reps=4, method=tnsk.ACYCLIC), out)
+
+
 # ---------------------------------------------------------------- batch, combine, errors
 def test_batch_matches_oracle_per_network(ctx):
     rng = np.random.default_rng(8)
