@@ -6,9 +6,11 @@ Workload (per GPU, per step): B = 64 pairs of tensor trains (8 sites, bond 32,
 physical 8, N(0, 1/sqrt(32)) entries, FP32). Every pair's inner product is
 estimated by both of the paper's methods at m = 1024 with 64 repetitions:
   * method 2 (Sec. 4.4, acyclic) on the chain obtained by summing each site's
-    physical leg and merging its two bonds (8 tensors: 1024, 6 x 1024x1024, 1024),
-    made on the GPU every step from the cores by exact pair contractions
-    (tnsk_pairs); this is the estimate that meets the 5% error target;
+    physical leg and merging its two bonds (8 tensors: 1024, 6 x 1024x1024, 1024):
+    the six inner sites are grouped tensors (tnsk_rung, the grouping of Sec. 4.1)
+    whose entries the tensor-core sketch product forms from the two cores, the
+    end vectors are merged every step by exact pair contractions (tnsk_pairs);
+    --dense-chain materialises every merged site instead;
   * method 1 (Sec. 4.2, any network) on the cyclic ladder (16 tensors, t = 22).
 The inputs are the cores (25 MB per GPU). One step = the rung merge (one
 tnsk_pairs_run) and one run of a planned batch (tnsk_plan_run) over the 2B networks: every
@@ -61,6 +63,8 @@ def parse():
     ap.add_argument("--no-hbm-probe", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--dense-chain", action="store_true",
+                    help="materialise the merged chain every step (tnsk_pairs) instead of grouped tensors")
     return ap.parse_args()
 
 
@@ -194,6 +198,7 @@ def run_ours(args, world, rank, local):
     # step by exact pair contractions (tnsk_pairs: M_k[a,b,c,d] = sum_s A_k[a,s,c] B_k[b,s,d]).
     sites = len(pairs[0][0])
     bond = pairs[0][0][1].shape[0]
+    phys = pairs[0][0][1].shape[1]
     specs, params, host_ts = [], [], []
     for A, Bc, ladder in pairs:
         specs.append(ladder)
@@ -229,9 +234,11 @@ def run_ours(args, world, rank, local):
                 elif k == sites - 1:  # [a, s] x [b, s] -> [a, b]
                     out = torch.empty((bond * bond,), dtype=torch.float32, device=dev)
                     jobs.append((Ak, Bk, [1], [1], None, out.view(bond, bond)))
-                else:  # [a, s, c] x [b, s, d] -> [a, b, c, d]
+                elif args.dense_chain:  # [a, s, c] x [b, s, d] -> [a, b, c, d]
                     out = torch.empty((bond * bond, bond * bond), dtype=torch.float32, device=dev)
                     jobs.append((Ak, Bk, [1], [1], [0, 2, 1, 3], out.view(bond, bond, bond, bond)))
+                else:  # grouped tensor: its entries are formed inside the sketch product
+                    out = tnsk.Rung(Ak, Bk)
                 mats.append(out)
             nb.append(tnsk.Network(mats, cedges, []))
         nets_b.append(nb)
@@ -299,10 +306,28 @@ def run_ours(args, world, rank, local):
     ms_profiled = p0.elapsed_time(p1) / args.steps
 
     # ---------------- accuracy against the exact contraction (input-relative, Def. "ATNC")
+    # the dense merged chains (every site by tnsk_pairs, outside the timed region) give
+    # tc and the input norms
     est = [float(o.item()) for o in outs]
+    dense_jobs, dense = [], []
+    for i in range(B):
+        views = nets[2 * i].tensors
+        chain = []
+        for k in range(sites):
+            Ak, Bk = views[k], views[sites + k]
+            if k in (0, sites - 1):
+                chain.append(nets[2 * i + 1].tensors[k])
+                continue
+            o = torch.empty((bond * bond, bond * bond), dtype=torch.float32, device=dev)
+            dense_jobs.append((Ak, Bk, [1], [1], [0, 2, 1, 3], o.view(bond, bond, bond, bond)))
+            chain.append(o)
+        dense.append(chain)
+    if not args.dense_chain:
+        ctx.contract_pairs(dense_jobs)
+        ctx.sync()
     eps2, eps1, rel2, rel1 = [], [], [], []
     for i in range(B):
-        chain_ts = nets[2 * i + 1].tensors
+        chain_ts = dense[i] if not args.dense_chain else nets[2 * i + 1].tensors
         tc = exact_chain(chain_ts)
         eps2.append((est[2 * i + 1] - tc) / frob(chain_ts))
         eps1.append((est[2 * i] - tc) / frob(nets[2 * i].tensors))
@@ -323,14 +348,25 @@ def run_ours(args, world, rank, local):
                                       "(tnsk_probe_shared_atomics)",
                        "what": "signed scatter-adds (updates) per launch = reps x entries"},
         # one launch per height (6 per step): one 1024 x 1024 FP32 matrix per pair, read once
-        "m2_gemm": {"bound": "hbm", "per_launch": B * 1024 * 1024 * 4, "unit": "GB/s", "peak": hbm_peak(),
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
-                    "what": "bytes of X_k read per launch (each interior matrix once for all 64 reps)"},
+        # one launch per height (6 per step). Dense chain: one 1024 x 1024 FP32 matrix per
+        # pair read once. Grouped tensors: no matrix is read; the converter warps form its
+        # 2^20 entries from the two cores, phys FMAs each (FP32 SIMT work)
+        "m2_gemm": ({"bound": "hbm", "per_launch": B * 1024 * 1024 * 4, "unit": "GB/s", "peak": hbm_peak(),
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
+                     "what": "bytes of X_k read per launch (each interior matrix once for all 64 reps)"}
+                    if args.dense_chain else
+                    {"bound": "alu", "per_launch": B * 1024 * 1024 * phys * 2, "unit": "TFLOP/s",
+                     "scale": 1e12, "peak": FP32_SIMT_PEAK_TFLOPS,
+                     "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (unit counts and clock)",
+                     "what": "FP32 FLOPs forming the grouped tensor's entries per launch (2 x phys per entry); the "
+                             "tensor-core product and V^T loads ride along"}),
+        # one launch per step: the merged sites written once (all sites with --dense-chain,
+        # else the two end vectors only)
+        "pairs": {"bound": "hbm",
+                  "per_launch": B * (((sites - 2) * bond ** 4 if args.dense_chain else 0) + 2 * bond ** 2) * 4,
+                  "unit": "GB/s", "peak": hbm_peak(), "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
+                  "what": "bytes of the merged sites written per launch"},
         # one launch per step: every ladder sketch (reps x 16 tensors x m FP32) read once
-        # one launch per step: every merged chain written once
-        "pairs": {"bound": "hbm", "per_launch": B * ((sites - 2) * bond ** 4 + 2 * bond ** 2) * 4, "unit": "GB/s",
-                  "peak": hbm_peak(), "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
-                  "what": "bytes of the merged chains written per launch"},
         "m1_spectrum": {"bound": "hbm", "per_launch": B * REPS * 16 * M * 4, "unit": "GB/s", "peak": hbm_peak(),
                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
                         "what": "sketch bytes read per launch"},
@@ -345,7 +381,7 @@ def run_ours(args, world, rank, local):
         r = {"kernel": kern, "share": round(k_ms / total_ms, 4) if total_ms else None,
              "launch_ms": round(per_launch_ms, 5), "launches_per_step": k_n / args.steps}
         if d:
-            scale = 1e9
+            scale = d.get("scale", 1e9)
             achieved = d["per_launch"] / (per_launch_ms / 1e3) / scale
             r.update({"bound": d["bound"], "achieved": round(achieved, 1), "peak": round(d["peak"], 1) if d["peak"] else None,
                       "unit": d["unit"], "frac": round(achieved / d["peak"], 4) if d["peak"] else None,
@@ -419,6 +455,9 @@ def run_ours(args, world, rank, local):
         "config": {"workload": f"tt_pair_8x32x8: per GPU per step {B} pairs of tensor trains (8 sites, bond 32, "
                                "physical 8, N(0, 1/sqrt(32))); method 2 on the merged acyclic chain + method 1 on "
                                "the cyclic ladder, m=1024, 64 reps, FP32",
+                   "chain": ("merged sites materialised every step (tnsk_pairs)" if args.dense_chain else
+                             "inner sites as grouped tensors (tnsk_rung: entries formed inside the tensor-core "
+                             "sketch product), end sites merged every step (tnsk_pairs)"),
                    "networks_per_step": 2 * B, "estimate": "method-2 combined estimate of one pair",
                    "m": M, "reps": REPS, "inputs_bytes_per_gpu": in_bytes,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
