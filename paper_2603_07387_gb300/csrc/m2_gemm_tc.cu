@@ -506,8 +506,8 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
 // columns (j1, j2) (j2 fastest, its dim a multiple of 32, so a 32-column chunk has
 // one j1); A's entry (i1, s, j1) is at i1 ai + j1 aj + s as, B's (i2, s, j2) at
 // i2 bi + j2 bj + s bs. The B factor is copied once per CTA into shared memory as
-// [i2][s][j2] rows padded to 4 mod 32 floats (a warp's 32 rows read 16-byte vectors
-// without bank conflicts); the converters form their row's 32 entries of each chunk
+// [i2][s][j2] rows padded to 4 mod 32 floats (the distinct rows of one 16-byte load
+// fall in distinct banks); the converters form their row's 32 entries of each chunk
 // (FP32 fmaf over s in ascending order: the values contract_pairs writes), split
 // them into TF32 hi / lo and store them to tensor memory as the streaming kernel
 // does; only the V^T tiles arrive by TMA. Same warp roles, barriers and epilogue.
@@ -601,10 +601,12 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_rung_kernel(const M2Node* _
         }
         __syncwarp();
     } else if (warp <= 4) {
-        // ---------------- converters: thread = row q4 * 32 + lane of the tile (its TMEM lane)
+        // ---------------- converters: TMEM lane q4 * 32 + lane holds tile row pr, a
+        // permutation that gives each group of 4 lanes one i2 when n_i2 = 32 (4 i1 x 32 i2
+        // per tile), so a warp's B reads hit 8 addresses, each a 4-lane broadcast
         const int q4 = warp & 3;
-        const int r = q4 * 32 + lane;
-        const int64_t row = row0 + r;
+        const int pr = (lane & 3) * 32 + q4 * 8 + (lane >> 2);
+        const int64_t row = row0 + pr;
         const bool live = row < npar;
         const int i1 = live ? (int)(row / ni2) : 0, i2 = live ? (int)(row - (int64_t)i1 * ni2) : 0;
         const float* __restrict__ Arow = nd.rA + (int64_t)i1 * nd.r_ai;
@@ -621,8 +623,13 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_rung_kernel(const M2Node* _
             for (int j = 0; j < 32; ++j) x[j] = 0.f;
             if (live) {
                 const float* __restrict__ Aj = Arow + (int64_t)j1 * nd.r_aj;
-                for (int sv = 0; sv < sn; ++sv) {
-                    const float a = __ldg(Aj + (int64_t)sv * nd.r_as);
+                float av[16];  // the row's A terms of this chunk, loaded together
+#pragma unroll
+                for (int sv = 0; sv < 16; ++sv) av[sv] = sv < sn ? __ldg(Aj + (int64_t)sv * nd.r_as) : 0.f;
+#pragma unroll
+                for (int sv = 0; sv < 16; ++sv) {
+                    if (sv >= sn) break;
+                    const float a = av[sv];
                     const float4* bq = reinterpret_cast<const float4*>(Brow + sv * nj2 + j20);
 #pragma unroll
                     for (int g = 0; g < 8; ++g) {
@@ -688,7 +695,7 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_rung_kernel(const M2Node* _
             if (lane == 0) atomicExch(err, DEVERR_TIMEOUT);
         } else {
             const int q4 = warp & 3;
-            const int64_t row = row0 + q4 * 32 + lane;
+            const int64_t row = row0 + (lane & 3) * 32 + q4 * 8 + (lane >> 2);  // the converters' row map
 #pragma unroll
             for (int cc = 0; cc < kTN / 16; ++cc) {
                 uint32_t v[16];
