@@ -546,15 +546,55 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_rung_kernel(const M2Node* _
     const int ni2 = nd.rn_i2, nj2 = nd.rn_j2, sn = nd.rs;
     const int bp = sn * nj2 + 4;  // padded B row (floats)
 
-    // the B factor, all threads: sB[i2 * bp + s * nj2 + j2] = B(i2, s, j2)
+    // the B factor, all threads: sB[i2 * bp + s * nj2 + j2] = B(i2, s, j2), several loads
+    // in flight per thread
     {
         const float* __restrict__ Bg = nd.rB;
         const int per_i2 = sn * nj2;
-        const int total = ni2 * per_i2;
-        for (int q = tid; q < total; q += blockDim.x) {
-            const int i2 = q / per_i2, rem = q - i2 * per_i2;
-            const int sv = rem / nj2, j2 = rem - sv * nj2;
-            sB[i2 * bp + rem] = __ldg(Bg + (int64_t)i2 * nd.r_bi + (int64_t)sv * nd.r_bs + (int64_t)j2 * nd.r_bj);
+        constexpr int kU = 4;
+        if (nd.r_bj == 1 && nd.r_bs == nj2 && nd.r_bi == per_i2 && ((uintptr_t)Bg & 15) == 0) {
+            // B(i2, s, j2) at i2 per_i2 + s nj2 + j2: contiguous rows, 16-byte copies
+            const int per4 = per_i2 / 4, total4 = ni2 * per4;
+            for (int q0 = tid; q0 < total4; q0 += kU * blockDim.x) {
+                float4 v[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    v[u] = q < total4 ? __ldg(reinterpret_cast<const float4*>(Bg) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    if (q < total4) {
+                        const int i2 = q / per4;
+                        *reinterpret_cast<float4*>(sB + i2 * bp + 4 * (q - i2 * per4)) = v[u];
+                    }
+                }
+            }
+        } else {
+            const int total = ni2 * per_i2;
+            for (int q0 = tid; q0 < total; q0 += kU * blockDim.x) {
+                float v[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    float x = 0.f;
+                    if (q < total) {
+                        const int i2 = q / per_i2, rem = q - i2 * per_i2;
+                        const int sv = rem / nj2, j2 = rem - sv * nj2;
+                        x = __ldg(Bg + (int64_t)i2 * nd.r_bi + (int64_t)sv * nd.r_bs + (int64_t)j2 * nd.r_bj);
+                    }
+                    v[u] = x;
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    if (q < total) {
+                        const int i2 = q / per_i2;
+                        sB[i2 * bp + (q - i2 * per_i2)] = v[u];
+                    }
+                }
+            }
         }
     }
     if (warp == 5) {
