@@ -514,9 +514,19 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int kRungRing = kRawStages * 2 * kRawV;  // V^T hi + lo per stage
+constexpr int kRungMmaWarp = 9;  // warps: 0 producer, 1-8 converters, 9 TMEM and MMA
+
+__device__ __forceinline__ void tmem_store16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
 }  // namespace
 
-__global__ void __launch_bounds__(192, 2) m2_gemm_tc_rung_kernel(const M2Node* __restrict__ nodes,
+__global__ void __launch_bounds__(320, 2) m2_gemm_tc_rung_kernel(const M2Node* __restrict__ nodes,
                                                                  const M2Net* __restrict__ nets,
                                                                  const M2Item* __restrict__ items,
                                                                  float* __restrict__ ws,
@@ -597,7 +607,7 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_rung_kernel(const M2Node* _
             }
         }
     }
-    if (warp == 5) {
+    if (warp == kRungMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -608,7 +618,7 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_rung_kernel(const M2Node* _
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&raw_empty[st])));
         }
         for (int t = 0; t < kTmStages; ++t) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(&tm_full[t])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_addr(&tm_full[t])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&tm_empty[t])));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&done_bar)));
@@ -640,17 +650,19 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_rung_kernel(const M2Node* _
             }
         }
         __syncwarp();
-    } else if (warp <= 4) {
-        // ---------------- converters: TMEM lane q4 * 32 + lane holds tile row pr, a
-        // permutation that gives each group of 4 lanes one i2 when n_i2 = 32 (4 i1 x 32 i2
-        // per tile), so a warp's B reads hit 8 addresses, each a 4-lane broadcast
-        const int q4 = warp & 3;
+    } else if (warp <= 8) {
+        // ---------------- converters, two warps per TMEM lane quarter q4 = warp % 4 (the
+        // quarter a warp may access), each forming 16 of a chunk's 32 columns (half hf).
+        // TMEM lane q4 * 32 + lane holds tile row pr, a permutation that gives each group
+        // of 4 lanes one i2 when n_i2 = 32 (4 i1 x 32 i2 per tile), so a warp's B reads hit
+        // 8 addresses, each a 4-lane broadcast
+        const int q4 = warp & 3, hf = (warp - 1) >> 2;
         const int pr = (lane & 3) * 32 + q4 * 8 + (lane >> 2);
         const int64_t row = row0 + pr;
         const bool live = row < npar;
         const int i1 = live ? (int)(row / ni2) : 0, i2 = live ? (int)(row - (int64_t)i1 * ni2) : 0;
         const float* __restrict__ Arow = nd.rA + (int64_t)i1 * nd.r_ai;
-        const float* Brow = sB + i2 * bp;
+        const float* Brow = sB + i2 * bp + 16 * hf;
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
         for (int c = 0; c < nch && ok; ++c) {
             const int t = c % kTmStages;
@@ -658,9 +670,9 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_rung_kernel(const M2Node* _
             if (!ok) break;
             const int k0 = (cbeg + c) * kKC;
             const int j1 = k0 / nj2, j20 = k0 - j1 * nj2;
-            float x[32];
+            float x[16];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) x[j] = 0.f;
+            for (int j = 0; j < 16; ++j) x[j] = 0.f;
             if (live) {
                 const float* __restrict__ Aj = Arow + (int64_t)j1 * nd.r_aj;
                 float av[16];  // the row's A terms of this chunk, loaded together
@@ -672,7 +684,7 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_rung_kernel(const M2Node* _
                     const float a = av[sv];
                     const float4* bq = reinterpret_cast<const float4*>(Brow + sv * nj2 + j20);
 #pragma unroll
-                    for (int g = 0; g < 8; ++g) {
+                    for (int g = 0; g < 4; ++g) {
                         const float4 b = bq[g];
                         x[4 * g + 0] = fmaf(a, b.x, x[4 * g + 0]);
                         x[4 * g + 1] = fmaf(a, b.y, x[4 * g + 1]);
@@ -681,19 +693,19 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_rung_kernel(const M2Node* _
                     }
                 }
             }
-            uint32_t hi[32], lo[32];
+            uint32_t hi[16], lo[16];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) tf32_split(x[j], hi[j], lo[j]);
-            const uint32_t col = (uint32_t)(kTN + 64 * t);
-            tmem_store32(tmem + lane_base + col, hi);
-            tmem_store32(tmem + lane_base + col + 32, lo);
+            for (int j = 0; j < 16; ++j) tf32_split(x[j], hi[j], lo[j]);
+            const uint32_t col = (uint32_t)(kTN + 64 * t + 16 * hf);
+            tmem_store16(tmem + lane_base + col, hi);
+            tmem_store16(tmem + lane_base + col + 32, lo);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_addr(&tm_full[t]));
         }
     } else if (lane == 0) {
-        // ---------------- MMA issue (warp 5, one thread)
+        // ---------------- MMA issue (warp 9, one thread)
         for (int c = 0; c < nch && ok; ++c) {
             const int st = c % kRawStages, t = c % kTmStages;
             ok = mbar_wait(smem_addr(&tm_full[t]), (uint32_t)((c / kTmStages) & 1));
@@ -727,17 +739,18 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_rung_kernel(const M2Node* _
     }
     if (!ok && (lane == 0)) atomicExch(err, DEVERR_TIMEOUT);
 
-    if (warp >= 1 && warp <= 4 && ok && nch > 0) {
-        // ---------------- epilogue: W^T[rep][row] from TMEM lanes 32 (warp % 4) .. + 31
+    if (warp >= 1 && warp <= 8 && ok && nch > 0) {
+        // ---------------- epilogue: W^T[rep][row] from TMEM lanes 32 (warp % 4) .. + 31,
+        // reps [32 hf, 32 hf + 32) per warp
         const bool done = mbar_wait(smem_addr(&done_bar), 0u);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!done) {
             if (lane == 0) atomicExch(err, DEVERR_TIMEOUT);
         } else {
-            const int q4 = warp & 3;
+            const int q4 = warp & 3, hf = (warp - 1) >> 2;
             const int64_t row = row0 + (lane & 3) * 32 + q4 * 8 + (lane >> 2);  // the converters' row map
 #pragma unroll
-            for (int cc = 0; cc < kTN / 16; ++cc) {
+            for (int cc = 2 * hf; cc < 2 * hf + 2; ++cc) {
                 uint32_t v[16];
                 const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(cc * 16);
                 asm volatile(
@@ -766,7 +779,7 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_rung_kernel(const M2Node* _
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    if (warp == kRungMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 size_t m2_gemm_rung_smem(size_t b_bytes) { return 1024 + (size_t)kRungRing + b_bytes; }
@@ -775,7 +788,7 @@ cudaError_t launch_m2_gemm_tc_rung(int n, const M2Node* nodes, const M2Net* nets
                                    const unsigned char* tmaps, int* err, size_t smem, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     cudaFuncSetAttribute(m2_gemm_tc_rung_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    m2_gemm_tc_rung_kernel<<<n, 192, smem, s>>>(nodes, nets, items, ws, tmaps, err);
+    m2_gemm_tc_rung_kernel<<<n, 320, smem, s>>>(nodes, nets, items, ws, tmaps, err);
     return cudaGetLastError();
 }
 
