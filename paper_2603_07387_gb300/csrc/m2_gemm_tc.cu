@@ -513,7 +513,11 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
 // does; only the V^T tiles arrive by TMA. Same warp roles, barriers and epilogue.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int kRungRing = kRawStages * 2 * kRawV;  // V^T hi + lo per stage
+// deeper rings than the streaming kernel's: 4 V^T stages (its X stages are not needed)
+// and 3 operand stages (64 accumulator + 3 x 64 operand columns = the 256 allocated)
+constexpr int kRungRaw = 4;
+constexpr int kRungTm = 3;
+constexpr int kRungRing = kRungRaw * 2 * kRawV;  // V^T hi + lo per stage
 constexpr int kRungMmaWarp = 9;  // warps: 0 producer, 1-8 converters, 9 TMEM and MMA
 
 __device__ __forceinline__ void tmem_store16(uint32_t taddr, const uint32_t (&r)[16]) {
@@ -533,8 +537,8 @@ __global__ void __launch_bounds__(320, 2) m2_gemm_tc_rung_kernel(const M2Node* _
                                                                  const unsigned char* __restrict__ tmaps,
                                                                  int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t raw_full[kRawStages], raw_empty[kRawStages];
-    __shared__ __align__(8) uint64_t tm_full[kTmStages], tm_empty[kTmStages];
+    __shared__ __align__(8) uint64_t raw_full[kRungRaw], raw_empty[kRungRaw];
+    __shared__ __align__(8) uint64_t tm_full[kRungTm], tm_empty[kRungTm];
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t tmem_base;
     unsigned char* raw = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -613,11 +617,11 @@ __global__ void __launch_bounds__(320, 2) m2_gemm_tc_rung_kernel(const M2Node* _
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int st = 0; st < kRawStages; ++st) {
+        for (int st = 0; st < kRungRaw; ++st) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&raw_full[st])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&raw_empty[st])));
         }
-        for (int t = 0; t < kTmStages; ++t) {
+        for (int t = 0; t < kRungTm; ++t) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_addr(&tm_full[t])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&tm_empty[t])));
         }
@@ -636,9 +640,9 @@ __global__ void __launch_bounds__(320, 2) m2_gemm_tc_rung_kernel(const M2Node* _
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvh) : "memory");
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvl) : "memory");
             for (int c = 0; c < nch && ok; ++c) {
-                const int st = c % kRawStages;
-                if (c >= kRawStages)
-                    ok = mbar_wait(smem_addr(&raw_empty[st]), (uint32_t)((c / kRawStages - 1) & 1));
+                const int st = c % kRungRaw;
+                if (c >= kRungRaw)
+                    ok = mbar_wait(smem_addr(&raw_empty[st]), (uint32_t)((c / kRungRaw - 1) & 1));
                 if (!ok) break;
                 const int k0 = (cbeg + c) * kKC;
                 unsigned char* stp = raw + st * 2 * kRawV;
@@ -665,8 +669,8 @@ __global__ void __launch_bounds__(320, 2) m2_gemm_tc_rung_kernel(const M2Node* _
         const float* Brow = sB + i2 * bp + 16 * hf;
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
         for (int c = 0; c < nch && ok; ++c) {
-            const int t = c % kTmStages;
-            if (c >= kTmStages) ok = mbar_wait(smem_addr(&tm_empty[t]), (uint32_t)((c / kTmStages - 1) & 1));
+            const int t = c % kRungTm;
+            if (c >= kRungTm) ok = mbar_wait(smem_addr(&tm_empty[t]), (uint32_t)((c / kRungTm - 1) & 1));
             if (!ok) break;
             const int k0 = (cbeg + c) * kKC;
             const int j1 = k0 / nj2, j20 = k0 - j1 * nj2;
@@ -707,9 +711,9 @@ __global__ void __launch_bounds__(320, 2) m2_gemm_tc_rung_kernel(const M2Node* _
     } else if (lane == 0) {
         // ---------------- MMA issue (warp 9, one thread)
         for (int c = 0; c < nch && ok; ++c) {
-            const int st = c % kRawStages, t = c % kTmStages;
-            ok = mbar_wait(smem_addr(&tm_full[t]), (uint32_t)((c / kTmStages) & 1));
-            if (ok) ok = mbar_wait(smem_addr(&raw_full[st]), (uint32_t)((c / kRawStages) & 1));
+            const int st = c % kRungRaw, t = c % kRungTm;
+            ok = mbar_wait(smem_addr(&tm_full[t]), (uint32_t)((c / kRungTm) & 1));
+            if (ok) ok = mbar_wait(smem_addr(&raw_full[st]), (uint32_t)((c / kRungRaw) & 1));
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const unsigned char* stp = raw + st * 2 * kRawV;
