@@ -520,6 +520,28 @@ constexpr int kRungTm = 3;
 constexpr int kRungRing = kRungRaw * 2 * kRawV;  // V^T hi + lo per stage
 constexpr int kRungMmaWarp = 9;  // warps: 0 producer, 1-8 converters, 9 TMEM and MMA
 
+// x[j] = sum_{s < SN} A(s) B(s, j) for 16 consecutive columns j (fmaf in ascending s):
+// the A terms at a + s a_s (global), the B row at b + s nj2 (shared, 16-byte aligned).
+template <int SN>
+__device__ __forceinline__ void rung_entries(const float* __restrict__ a, int a_s, const float* b, int nj2,
+                                             float (&x)[16]) {
+    float av[SN];
+#pragma unroll
+    for (int s = 0; s < SN; ++s) av[s] = __ldg(a + (int64_t)s * a_s);
+#pragma unroll
+    for (int s = 0; s < SN; ++s) {
+        const float4* bq = reinterpret_cast<const float4*>(b + s * nj2);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const float4 v = bq[g];
+            x[4 * g + 0] = fmaf(av[s], v.x, x[4 * g + 0]);
+            x[4 * g + 1] = fmaf(av[s], v.y, x[4 * g + 1]);
+            x[4 * g + 2] = fmaf(av[s], v.z, x[4 * g + 2]);
+            x[4 * g + 3] = fmaf(av[s], v.w, x[4 * g + 3]);
+        }
+    }
+}
+
 __device__ __forceinline__ void tmem_store16(uint32_t taddr, const uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
@@ -679,22 +701,15 @@ __global__ void __launch_bounds__(320, 2) m2_gemm_tc_rung_kernel(const M2Node* _
             for (int j = 0; j < 16; ++j) x[j] = 0.f;
             if (live) {
                 const float* __restrict__ Aj = Arow + (int64_t)j1 * nd.r_aj;
-                float av[16];  // the row's A terms of this chunk, loaded together
-#pragma unroll
-                for (int sv = 0; sv < 16; ++sv) av[sv] = sv < sn ? __ldg(Aj + (int64_t)sv * nd.r_as) : 0.f;
-#pragma unroll
-                for (int sv = 0; sv < 16; ++sv) {
-                    if (sv >= sn) break;
-                    const float a = av[sv];
-                    const float4* bq = reinterpret_cast<const float4*>(Brow + sv * nj2 + j20);
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        const float4 b = bq[g];
-                        x[4 * g + 0] = fmaf(a, b.x, x[4 * g + 0]);
-                        x[4 * g + 1] = fmaf(a, b.y, x[4 * g + 1]);
-                        x[4 * g + 2] = fmaf(a, b.z, x[4 * g + 2]);
-                        x[4 * g + 3] = fmaf(a, b.w, x[4 * g + 3]);
-                    }
+                const float* Bj = Brow + j20;
+                switch (sn) {  // the shared dim as a compile-time trip count: loads hoisted
+#define TNSK_RUNG_SN(n) \
+    case n: rung_entries<n>(Aj, nd.r_as, Bj, nj2, x); break;
+                    TNSK_RUNG_SN(1) TNSK_RUNG_SN(2) TNSK_RUNG_SN(3) TNSK_RUNG_SN(4) TNSK_RUNG_SN(5) TNSK_RUNG_SN(6)
+                    TNSK_RUNG_SN(7) TNSK_RUNG_SN(8) TNSK_RUNG_SN(9) TNSK_RUNG_SN(10) TNSK_RUNG_SN(11)
+                    TNSK_RUNG_SN(12) TNSK_RUNG_SN(13) TNSK_RUNG_SN(14) TNSK_RUNG_SN(15) TNSK_RUNG_SN(16)
+#undef TNSK_RUNG_SN
+                    default: break;
                 }
             }
             uint32_t hi[16], lo[16];
