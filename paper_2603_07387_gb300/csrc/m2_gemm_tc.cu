@@ -520,24 +520,24 @@ constexpr int kRungTm = 3;
 constexpr int kRungRing = kRungRaw * 2 * kRawV;  // V^T hi + lo per stage
 constexpr int kRungMmaWarp = 9;  // warps: 0 producer, 1-8 converters, 9 TMEM and MMA
 
-// x[j] = sum_{s < SN} A(s) B(s, j) for 16 consecutive columns j (fmaf in ascending s):
-// the A terms at a + s a_s (global), the B row at b + s nj2 (shared, 16-byte aligned).
-template <int SN>
-__device__ __forceinline__ void rung_entries(const float* __restrict__ a, int a_s, const float* b, int nj2,
-                                             float (&x)[16]) {
+// x[j] = sum_{s < SN} A(s) B(s, j) for 16 consecutive columns j (fma in ascending s, two
+// columns per packed FP32 FMA; each half rounds like fmaf): the A terms at a + s (staged
+// in shared memory, kSA) or a + s a_s (global), the B row at b + s nj2 (shared, 16-byte
+// aligned).
+template <int SN, bool kSA>
+__device__ __forceinline__ void rung_entries(const float* a, int a_s, const float* b, int nj2, float2 (&x)[8]) {
     float av[SN];
 #pragma unroll
-    for (int s = 0; s < SN; ++s) av[s] = __ldg(a + (int64_t)s * a_s);
+    for (int s = 0; s < SN; ++s) av[s] = kSA ? a[s] : __ldg(a + (int64_t)s * a_s);
 #pragma unroll
     for (int s = 0; s < SN; ++s) {
         const float4* bq = reinterpret_cast<const float4*>(b + s * nj2);
+        const float2 aa = make_float2(av[s], av[s]);
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
             const float4 v = bq[g];
-            x[4 * g + 0] = fmaf(av[s], v.x, x[4 * g + 0]);
-            x[4 * g + 1] = fmaf(av[s], v.y, x[4 * g + 1]);
-            x[4 * g + 2] = fmaf(av[s], v.z, x[4 * g + 2]);
-            x[4 * g + 3] = fmaf(av[s], v.w, x[4 * g + 3]);
+            x[2 * g] = __ffma2_rn(aa, make_float2(v.x, v.y), x[2 * g]);
+            x[2 * g + 1] = __ffma2_rn(aa, make_float2(v.z, v.w), x[2 * g + 1]);
         }
     }
 }
@@ -633,6 +633,21 @@ __global__ void __launch_bounds__(320, 2) m2_gemm_tc_rung_kernel(const M2Node* _
             }
         }
     }
+    // the A rows of the tile's i1 range, when the plan staged them: sA[(i1 - i1_lo) sn nj1 +
+    // j1 sn + s] = A(i1, s, j1), so a chunk's terms are sn consecutive floats
+    const int nj1 = nd.rn_j1;
+    const int i1_lo = (int)(row0 / ni2);
+    float* sA = sB + ni2 * bp;
+    if (nd.r_astage) {
+        const int64_t last = (row0 + kTM - 1 < npar ? row0 + kTM - 1 : npar - 1);
+        const int cnt = (int)(last / ni2) - i1_lo + 1;
+        const int per_i1 = sn * nj1, total = cnt * per_i1;
+        for (int q = tid; q < total; q += blockDim.x) {
+            const int di = q / per_i1, rem = q - di * per_i1;
+            const int j1 = rem / sn, sv = rem - j1 * sn;
+            sA[q] = __ldg(nd.rA + (int64_t)(i1_lo + di) * nd.r_ai + (int64_t)j1 * nd.r_aj + (int64_t)sv * nd.r_as);
+        }
+    }
     if (warp == kRungMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
                      "r"(kTmemCols));
@@ -696,15 +711,21 @@ __global__ void __launch_bounds__(320, 2) m2_gemm_tc_rung_kernel(const M2Node* _
             if (!ok) break;
             const int k0 = (cbeg + c) * kKC;
             const int j1 = k0 / nj2, j20 = k0 - j1 * nj2;
-            float x[16];
+            float2 x2[8];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) x[j] = 0.f;
+            for (int j = 0; j < 8; ++j) x2[j] = make_float2(0.f, 0.f);
             if (live) {
-                const float* __restrict__ Aj = Arow + (int64_t)j1 * nd.r_aj;
+                const bool sa = nd.r_astage != 0;
+                const float* Aj = sa ? sA + (i1 - i1_lo) * sn * nj1 + j1 * sn : Arow + (int64_t)j1 * nd.r_aj;
                 const float* Bj = Brow + j20;
                 switch (sn) {  // the shared dim as a compile-time trip count: loads hoisted
-#define TNSK_RUNG_SN(n) \
-    case n: rung_entries<n>(Aj, nd.r_as, Bj, nj2, x); break;
+#define TNSK_RUNG_SN(n)                                                   \
+    case n:                                                               \
+        if (sa)                                                           \
+            rung_entries<n, true>(Aj, 1, Bj, nj2, x2);                    \
+        else                                                              \
+            rung_entries<n, false>(Aj, nd.r_as, Bj, nj2, x2);             \
+        break;
                     TNSK_RUNG_SN(1) TNSK_RUNG_SN(2) TNSK_RUNG_SN(3) TNSK_RUNG_SN(4) TNSK_RUNG_SN(5) TNSK_RUNG_SN(6)
                     TNSK_RUNG_SN(7) TNSK_RUNG_SN(8) TNSK_RUNG_SN(9) TNSK_RUNG_SN(10) TNSK_RUNG_SN(11)
                     TNSK_RUNG_SN(12) TNSK_RUNG_SN(13) TNSK_RUNG_SN(14) TNSK_RUNG_SN(15) TNSK_RUNG_SN(16)
@@ -712,6 +733,9 @@ __global__ void __launch_bounds__(320, 2) m2_gemm_tc_rung_kernel(const M2Node* _
                     default: break;
                 }
             }
+            float x[16];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[2 * j] = x2[j].x, x[2 * j + 1] = x2[j].y;
             uint32_t hi[16], lo[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) tf32_split(x[j], hi[j], lo[j]);

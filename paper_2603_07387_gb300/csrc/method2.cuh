@@ -75,7 +75,7 @@ struct M2Node {
     const float* rB;
     int32_t rn_i1, rn_i2, rn_j1, rn_j2, rs;
     int32_t r_ai, r_aj, r_as, r_bi, r_bj, r_bs;
-    int32_t rpad_;
+    int32_t r_astage;  // 1: the tile's A rows are staged in shared memory after B
 };
 
 struct M2Net {

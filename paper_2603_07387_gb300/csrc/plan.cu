@@ -720,7 +720,13 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                           ": rung tensor needs its column fast index a multiple of 32 and the B factor within 60 KiB";
                     return TNSK_ERR_UNSUPPORTED;
                 }
-                P.m2.rung_smem = std::max(P.m2.rung_smem, m2_gemm_rung_smem((size_t)b_bytes));
+                // A rows of a 128-row tile: at most 127 / n_i2 + 2 values of i1, staged when
+                // they fit 16 KiB
+                const int64_t i1_max = std::min<int64_t>(nd.rn_i1, 127 / nd.rn_i2 + 2);
+                const int64_t a_bytes = i1_max * g.s * nd.rn_j1 * 4;
+                nd.r_astage = a_bytes <= 16 * 1024 ? 1 : 0;
+                P.m2.rung_smem = std::max(P.m2.rung_smem,
+                                          m2_gemm_rung_smem((size_t)(b_bytes + (nd.r_astage ? a_bytes : 0))));
             }
             nd.qt = qt[k];
             P.m2.max_qt = std::max(P.m2.max_qt, nd.qt);
