@@ -739,13 +739,23 @@ __global__ void __launch_bounds__(320, 2) m2_gemm_tc_rung_kernel(const M2Node* _
             uint32_t hi[16], lo[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) tf32_split(x[j], hi[j], lo[j]);
+            // the previous chunk's stores had this chunk's arithmetic to complete: wait for
+            // them and hand that stage to the MMA only now, then store this chunk
+            if (c > 0) {
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&tm_full[(c - 1) % kRungTm]));
+            }
             const uint32_t col = (uint32_t)(kTN + 64 * t + 16 * hf);
             tmem_store16(tmem + lane_base + col, hi);
             tmem_store16(tmem + lane_base + col + 32, lo);
+        }
+        if (ok && nch > 0) {
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_addr(&tm_full[t]));
+            if (lane == 0) mbar_arrive(smem_addr(&tm_full[(nch - 1) % kRungTm]));
         }
     } else if (lane == 0) {
         // ---------------- MMA issue (warp 9, one thread)
