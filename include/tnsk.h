@@ -86,9 +86,8 @@ typedef struct {
                                TNSK_ACYCLIC in FP32 where it is an inner node of the
                                rooted tree (neither a leaf nor the root) and the
                                column pair's fast index (d, or b when the parent mode
-                               is the second) is a multiple of 32, the B factor padded
-                               to rows of s*d + 4 (or s*b + 4) floats within 48 KiB and
-                               s <= 16; elsewhere TNSK_ERR_UNSUPPORTED */
+                               is the second) is a multiple of 32, the staged B factor
+                               within 64 KiB and s <= 16; elsewhere TNSK_ERR_UNSUPPORTED */
 } tnsk_tensor;
 
 typedef struct {

@@ -505,28 +505,20 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
 // sum_s A(.., s, ..) B(.., s, ..) is never stored. Rows are (i1, i2) (i2 fastest),
 // columns (j1, j2) (j2 fastest, its dim a multiple of 32, so a 32-column chunk has
 // one j1); A's entry (i1, s, j1) is at i1 ai + j1 aj + s as, B's (i2, s, j2) at
-// i2 bi + j2 bj + s bs. Per CTA the B factor is copied once into shared memory as
+// i2 bi + j2 bj + s bs. The B factor is copied once per CTA into shared memory as
 // [i2][s][j2] rows padded to 4 mod 32 floats (the distinct rows of one 16-byte load
-// fall in distinct banks), and the tile's A rows too when the plan allows. Two groups
-// of 8 converter warps take alternate chunks; a thread forms 16 of its row's 32
-// entries (FP32 FMAs over s in ascending order: the values contract_pairs writes),
-// splits them into TF32 hi / lo and stores them to a shared-memory operand stage in
-// the K-major no-swizzle layout; the MMA reads both operands from shared memory
-// (V^T by TMA, as in the streaming kernel) and accumulates in tensor memory. One CTA
-// per SM (the operand stages take most of shared memory).
-//   warp 0      producer: V^T hi / lo tiles into a 4-deep ring
-//   warps 1-16  converters (group (warp - 1) / 8 takes chunks of its parity), then
-//               the epilogue (16 accumulator columns per warp)
-//   warp 17     tensor memory (64 columns) and MMA issue
+// fall in distinct banks); the converters form their row's 32 entries of each chunk
+// (FP32 fmaf over s in ascending order: the values contract_pairs writes), split
+// them into TF32 hi / lo and store them to tensor memory as the streaming kernel
+// does; only the V^T tiles arrive by TMA. Same warp roles, barriers and epilogue.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int kRungRaw = 4;                       // V^T stages
-constexpr int kRungAS = 3;                        // A operand stages
-constexpr int kRungRing = kRungRaw * 2 * kRawV;   // V^T hi + lo per stage
-constexpr int kRungAStage = 2 * kABytes;          // A hi + lo, 128 rows x 32 columns each
-constexpr int kRungThreads = 18 * 32;
-constexpr int kRungMmaWarp = 17;
-constexpr uint32_t kRungTmemCols = 64;
+// deeper rings than the streaming kernel's: 4 V^T stages (its X stages are not needed)
+// and 3 operand stages (64 accumulator + 3 x 64 operand columns = the 256 allocated)
+constexpr int kRungRaw = 4;
+constexpr int kRungTm = 3;
+constexpr int kRungRing = kRungRaw * 2 * kRawV;  // V^T hi + lo per stage
+constexpr int kRungMmaWarp = 9;  // warps: 0 producer, 1-8 converters, 9 TMEM and MMA
 
 // x[j] = sum_{s < SN} A(s) B(s, j) for 16 consecutive columns j (fma in ascending s, two
 // columns per packed FP32 FMA; each half rounds like fmaf): the A terms at a + s (staged
@@ -549,22 +541,30 @@ __device__ __forceinline__ void rung_entries(const float* a, int a_s, const floa
         }
     }
 }
+
+__device__ __forceinline__ void tmem_store16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
 }  // namespace
 
-__global__ void __launch_bounds__(kRungThreads, 1) m2_gemm_tc_rung_kernel(const M2Node* __restrict__ nodes,
-                                                                         const M2Net* __restrict__ nets,
-                                                                         const M2Item* __restrict__ items,
-                                                                         float* __restrict__ ws,
-                                                                         const unsigned char* __restrict__ tmaps,
-                                                                         int* __restrict__ err) {
+__global__ void __launch_bounds__(320, 2) m2_gemm_tc_rung_kernel(const M2Node* __restrict__ nodes,
+                                                                 const M2Net* __restrict__ nets,
+                                                                 const M2Item* __restrict__ items,
+                                                                 float* __restrict__ ws,
+                                                                 const unsigned char* __restrict__ tmaps,
+                                                                 int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t raw_full[kRungRaw], raw_empty[kRungRaw];
-    __shared__ __align__(8) uint64_t a_full[kRungAS], a_empty[kRungAS];
+    __shared__ __align__(8) uint64_t tm_full[kRungTm], tm_empty[kRungTm];
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t tmem_base;
     unsigned char* raw = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* aop = raw + kRungRing;
-    float* sB = reinterpret_cast<float*>(aop + kRungAS * kRungAStage);
+    float* sB = reinterpret_cast<float*>(raw + kRungRing);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const M2Item it = items[blockIdx.x];
     const M2Node& nd = nodes[it.node];
@@ -650,7 +650,7 @@ __global__ void __launch_bounds__(kRungThreads, 1) m2_gemm_tc_rung_kernel(const 
     }
     if (warp == kRungMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
-                     "r"(kRungTmemCols));
+                     "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -658,9 +658,9 @@ __global__ void __launch_bounds__(kRungThreads, 1) m2_gemm_tc_rung_kernel(const 
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&raw_full[st])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&raw_empty[st])));
         }
-        for (int t = 0; t < kRungAS; ++t) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_addr(&a_full[t])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&a_empty[t])));
+        for (int t = 0; t < kRungTm; ++t) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_addr(&tm_full[t])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&tm_empty[t])));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&done_bar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -691,22 +691,23 @@ __global__ void __launch_bounds__(kRungThreads, 1) m2_gemm_tc_rung_kernel(const 
             }
         }
         __syncwarp();
-    } else if (warp <= 16) {
-        // ---------------- converters: group gr takes chunks c = gr, gr + 2, ...; in it, warp
-        // q4 + 4 hf forms columns [16 hf, 16 hf + 16) of tile rows pr = 32 (lane / 8) + 8 q4 +
-        // lane % 8: the 8 lanes of a quarter warp hold 8 consecutive rows (conflict-free
-        // 16-byte operand stores) and, when n_i2 = 32, 8 distinct i2 (one 16-byte B load each)
-        const int gr = (warp - 1) >> 3, q = (warp - 1) & 7, q4 = q & 3, hf = q >> 2;
-        const int pr = (lane >> 3) * 32 + q4 * 8 + (lane & 7);
+    } else if (warp <= 8) {
+        // ---------------- converters, two warps per TMEM lane quarter q4 = warp % 4 (the
+        // quarter a warp may access), each forming 16 of a chunk's 32 columns (half hf).
+        // TMEM lane q4 * 32 + lane holds tile row pr, a permutation that gives each group
+        // of 4 lanes one i2 when n_i2 = 32 (4 i1 x 32 i2 per tile), so a warp's B reads hit
+        // 8 addresses, each a 4-lane broadcast
+        const int q4 = warp & 3, hf = (warp - 1) >> 2;
+        const int pr = (lane & 3) * 32 + q4 * 8 + (lane >> 2);
         const int64_t row = row0 + pr;
         const bool live = row < npar;
         const int i1 = live ? (int)(row / ni2) : 0, i2 = live ? (int)(row - (int64_t)i1 * ni2) : 0;
         const float* __restrict__ Arow = nd.rA + (int64_t)i1 * nd.r_ai;
         const float* Brow = sB + i2 * bp + 16 * hf;
-        const bool sa = nd.r_astage != 0;
-        for (int c = gr; c < nch && ok; c += 2) {
-            const int t = c % kRungAS;
-            if (c >= kRungAS) ok = mbar_wait(smem_addr(&a_empty[t]), (uint32_t)((c / kRungAS - 1) & 1));
+        const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+        for (int c = 0; c < nch && ok; ++c) {
+            const int t = c % kRungTm;
+            if (c >= kRungTm) ok = mbar_wait(smem_addr(&tm_empty[t]), (uint32_t)((c / kRungTm - 1) & 1));
             if (!ok) break;
             const int k0 = (cbeg + c) * kKC;
             const int j1 = k0 / nj2, j20 = k0 - j1 * nj2;
@@ -714,6 +715,7 @@ __global__ void __launch_bounds__(kRungThreads, 1) m2_gemm_tc_rung_kernel(const 
 #pragma unroll
             for (int j = 0; j < 8; ++j) x2[j] = make_float2(0.f, 0.f);
             if (live) {
+                const bool sa = nd.r_astage != 0;
                 const float* Aj = sa ? sA + (i1 - i1_lo) * sn * nj1 + j1 * sn : Arow + (int64_t)j1 * nd.r_aj;
                 const float* Bj = Brow + j20;
                 switch (sn) {  // the shared dim as a compile-time trip count: loads hoisted
@@ -731,42 +733,56 @@ __global__ void __launch_bounds__(kRungThreads, 1) m2_gemm_tc_rung_kernel(const 
                     default: break;
                 }
             }
-            unsigned char* a_hi = aop + t * kRungAStage;
-            unsigned char* a_lo = a_hi + kABytes;
+            float x[16];
 #pragma unroll
-            for (int g = 0; g < 4; ++g)
-                store_split(a_hi, a_lo, kmajor_offset(pr, 16 * hf + 4 * g),
-                            make_float4(x2[2 * g].x, x2[2 * g].y, x2[2 * g + 1].x, x2[2 * g + 1].y));
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (int j = 0; j < 8; ++j) x[2 * j] = x2[j].x, x[2 * j + 1] = x2[j].y;
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) tf32_split(x[j], hi[j], lo[j]);
+            // the previous chunk's stores had this chunk's arithmetic to complete: wait for
+            // them and hand that stage to the MMA only now, then store this chunk
+            if (c > 0) {
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&tm_full[(c - 1) % kRungTm]));
+            }
+            const uint32_t col = (uint32_t)(kTN + 64 * t + 16 * hf);
+            tmem_store16(tmem + lane_base + col, hi);
+            tmem_store16(tmem + lane_base + col + 32, lo);
+        }
+        if (ok && nch > 0) {
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_addr(&a_full[t]));
+            if (lane == 0) mbar_arrive(smem_addr(&tm_full[(nch - 1) % kRungTm]));
         }
     } else if (lane == 0) {
-        // ---------------- MMA issue (warp 17, one thread): A and V^T from shared memory
+        // ---------------- MMA issue (warp 9, one thread)
         for (int c = 0; c < nch && ok; ++c) {
-            const int st = c % kRungRaw, t = c % kRungAS;
-            ok = mbar_wait(smem_addr(&a_full[t]), (uint32_t)((c / kRungAS) & 1));
+            const int st = c % kRungRaw, t = c % kRungTm;
+            ok = mbar_wait(smem_addr(&tm_full[t]), (uint32_t)((c / kRungTm) & 1));
             if (ok) ok = mbar_wait(smem_addr(&raw_full[st]), (uint32_t)((c / kRungRaw) & 1));
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const unsigned char* stp = raw + st * 2 * kRawV;
-            const unsigned char* a_hi = aop + t * kRungAStage;
-            const unsigned char* aps[3] = {a_hi, a_hi, a_hi + kABytes};
-            const unsigned char* bps[3] = {stp, stp + kRawV, stp};
+            const uint32_t a_hi = tmem + (uint32_t)(kTN + 64 * t), a_lo = a_hi + 32;
+            const uint32_t aop[3] = {a_hi, a_hi, a_lo};
+            const unsigned char* bop[3] = {stp, stp + kRawV, stp};
 #pragma unroll
             for (int p = 0; p < 3; ++p)
 #pragma unroll
                 for (int ks = 0; ks < kKC / 8; ++ks) {
-                    const uint64_t ad = smem_desc(smem_addr(aps[p]) + ks * 256, 128, 1024);
-                    const uint64_t bd = smem_desc_sw128(smem_addr(bps[p]) + ks * 32);
+                    const uint32_t at = aop[p] + ks * 8;
+                    const uint64_t bd = smem_desc_sw128(smem_addr(bop[p]) + ks * 32);
                     const uint32_t acc = (c > 0 || p > 0 || ks > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, q;\n\t}" ::"r"(tmem),
+                        "r"(at), "l"(bd), "r"(kIdesc), "r"(acc));
                 }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_addr(&a_empty[t])));
+                smem_addr(&tm_empty[t])));
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_addr(&raw_empty[st])));
             if (c == nch - 1)
@@ -776,35 +792,39 @@ __global__ void __launch_bounds__(kRungThreads, 1) m2_gemm_tc_rung_kernel(const 
     }
     if (!ok && (lane == 0)) atomicExch(err, DEVERR_TIMEOUT);
 
-    if (warp >= 1 && warp <= 16 && ok && nch > 0) {
-        // ---------------- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows),
-        // accumulator columns (reps) [16 part, 16 part + 16), part = (w - 1) / 4
+    if (warp >= 1 && warp <= 8 && ok && nch > 0) {
+        // ---------------- epilogue: W^T[rep][row] from TMEM lanes 32 (warp % 4) .. + 31,
+        // reps [32 hf, 32 hf + 32) per warp
         const bool done = mbar_wait(smem_addr(&done_bar), 0u);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!done) {
             if (lane == 0) atomicExch(err, DEVERR_TIMEOUT);
         } else {
-            const int qq = warp & 3, part = (warp - 1) >> 2;
-            const int64_t row = row0 + qq * 32 + lane;
-            uint32_t v[16];
-            const uint32_t ta = tmem + ((uint32_t)(qq * 32) << 16) + (uint32_t)(part * 16);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                "[%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < npar) {
+            const int q4 = warp & 3, hf = (warp - 1) >> 2;
+            const int64_t row = row0 + (lane & 3) * 32 + q4 * 8 + (lane >> 2);  // the converters' row map
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int rep = rep0 + part * 16 + j;
-                    if (rep < R) {
-                        float* dst = &ws[nd.w_off + (int64_t)rep * npar + row];
-                        if (it.begin > 1)
-                            atomicAdd(dst, __uint_as_float(v[j]));  // K split: partial sums
-                        else
-                            *dst = __uint_as_float(v[j]);
+            for (int cc = 2 * hf; cc < 2 * hf + 2; ++cc) {
+                uint32_t v[16];
+                const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(cc * 16);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < npar) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int rep = rep0 + cc * 16 + j;
+                        if (rep < R) {
+                            float* dst = &ws[nd.w_off + (int64_t)rep * npar + row];
+                            if (it.begin > 1)
+                                atomicAdd(dst, __uint_as_float(v[j]));  // K split: partial sums
+                            else
+                                *dst = __uint_as_float(v[j]);
+                        }
                     }
                 }
             }
@@ -812,19 +832,16 @@ __global__ void __launch_bounds__(kRungThreads, 1) m2_gemm_tc_rung_kernel(const 
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == kRungMmaWarp)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kRungTmemCols));
+    if (warp == kRungMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-size_t m2_gemm_rung_smem(size_t b_bytes) {
-    return 1024 + (size_t)kRungRing + (size_t)kRungAS * kRungAStage + b_bytes;
-}
+size_t m2_gemm_rung_smem(size_t b_bytes) { return 1024 + (size_t)kRungRing + b_bytes; }
 
 cudaError_t launch_m2_gemm_tc_rung(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items, float* ws,
                                    const unsigned char* tmaps, int* err, size_t smem, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     cudaFuncSetAttribute(m2_gemm_tc_rung_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    m2_gemm_tc_rung_kernel<<<n, kRungThreads, smem, s>>>(nodes, nets, items, ws, tmaps, err);
+    m2_gemm_tc_rung_kernel<<<n, 320, smem, s>>>(nodes, nets, items, ws, tmaps, err);
     return cudaGetLastError();
 }
 

@@ -715,9 +715,9 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 nd.r_bi = (int32_t)(first ? g.s * g.d : 1);
                 nd.r_bj = (int32_t)(first ? 1 : g.s * g.d);
                 const int64_t b_bytes = (int64_t)nd.rn_i2 * (g.s * nd.rn_j2 + 4) * 4;
-                if (nd.rn_j2 % 32 != 0 || b_bytes > 48 * 1024 || !tma) {
+                if (nd.rn_j2 % 32 != 0 || b_bytes > 60 * 1024 || !tma) {
                     err = "tensor " + std::to_string(k) +
-                          ": rung tensor needs its column fast index a multiple of 32 and the B factor within 48 KiB";
+                          ": rung tensor needs its column fast index a multiple of 32 and the B factor within 60 KiB";
                     return TNSK_ERR_UNSUPPORTED;
                 }
                 // A rows of a 128-row tile: at most 127 / n_i2 + 2 values of i1, staged when
