@@ -6,11 +6,11 @@ Workload (per GPU, per step): B = 64 pairs of tensor trains (8 sites, bond 32,
 physical 8, N(0, 1/sqrt(32)) entries, FP32). Every pair's inner product is
 estimated by both of the paper's methods at m = 1024 with 64 repetitions:
   * method 2 (Sec. 4.4, acyclic) on the chain obtained by summing each site's
-    physical leg and merging its two bonds (8 tensors: 1024, 6 x 1024x1024, 1024):
-    the six inner sites are grouped tensors (tnsk_rung, the grouping of Sec. 4.1)
-    whose entries the tensor-core sketch product forms from the two cores, the
-    end vectors are merged every step by exact pair contractions (tnsk_pairs);
-    --dense-chain materialises every merged site instead;
+    physical leg and merging its two bonds (8 tensors: 1024, 6 x 1024x1024, 1024),
+    made on the GPU every step from the cores by exact pair contractions
+    (tnsk_pairs); with --grouped the six inner sites are grouped tensors
+    (tnsk_rung, the grouping of Sec. 4.1) whose entries the tensor-core sketch
+    product forms from the two cores, and only the end vectors are merged;
   * method 1 (Sec. 4.2, any network) on the cyclic ladder (16 tensors, t = 22).
 The inputs are the cores (25 MB per GPU). One step = the rung merge (one
 tnsk_pairs_run) and one run of a planned batch (tnsk_plan_run) over the 2B networks: every
@@ -63,8 +63,8 @@ def parse():
     ap.add_argument("--no-hbm-probe", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
-    ap.add_argument("--dense-chain", action="store_true",
-                    help="materialise the merged chain every step (tnsk_pairs) instead of grouped tensors")
+    ap.add_argument("--grouped", action="store_true",
+                    help="inner sites as grouped tensors (tnsk_rung) instead of materialising them every step")
     return ap.parse_args()
 
 
@@ -234,7 +234,7 @@ def run_ours(args, world, rank, local):
                 elif k == sites - 1:  # [a, s] x [b, s] -> [a, b]
                     out = torch.empty((bond * bond,), dtype=torch.float32, device=dev)
                     jobs.append((Ak, Bk, [1], [1], None, out.view(bond, bond)))
-                elif args.dense_chain:  # [a, s, c] x [b, s, d] -> [a, b, c, d]
+                elif (not args.grouped):  # [a, s, c] x [b, s, d] -> [a, b, c, d]
                     out = torch.empty((bond * bond, bond * bond), dtype=torch.float32, device=dev)
                     jobs.append((Ak, Bk, [1], [1], [0, 2, 1, 3], out.view(bond, bond, bond, bond)))
                 else:  # grouped tensor: its entries are formed inside the sketch product
@@ -322,12 +322,12 @@ def run_ours(args, world, rank, local):
             dense_jobs.append((Ak, Bk, [1], [1], [0, 2, 1, 3], o.view(bond, bond, bond, bond)))
             chain.append(o)
         dense.append(chain)
-    if not args.dense_chain:
+    if not (not args.grouped):
         ctx.contract_pairs(dense_jobs)
         ctx.sync()
     eps2, eps1, rel2, rel1 = [], [], [], []
     for i in range(B):
-        chain_ts = dense[i] if not args.dense_chain else nets[2 * i + 1].tensors
+        chain_ts = dense[i] if not (not args.grouped) else nets[2 * i + 1].tensors
         tc = exact_chain(chain_ts)
         eps2.append((est[2 * i + 1] - tc) / frob(chain_ts))
         eps1.append((est[2 * i] - tc) / frob(nets[2 * i].tensors))
@@ -354,7 +354,7 @@ def run_ours(args, world, rank, local):
         "m2_gemm": ({"bound": "hbm", "per_launch": B * 1024 * 1024 * 4, "unit": "GB/s", "peak": hbm_peak(),
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
                      "what": "bytes of X_k read per launch (each interior matrix once for all 64 reps)"}
-                    if args.dense_chain else
+                    if (not args.grouped) else
                     {"bound": "alu", "per_launch": B * 1024 * 1024 * phys * 2, "unit": "TFLOP/s",
                      "scale": 1e12, "peak": FP32_SIMT_PEAK_TFLOPS,
                      "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (unit counts and clock)",
@@ -363,7 +363,7 @@ def run_ours(args, world, rank, local):
         # one launch per step: the merged sites written once (all sites with --dense-chain,
         # else the two end vectors only)
         "pairs": {"bound": "hbm",
-                  "per_launch": B * (((sites - 2) * bond ** 4 if args.dense_chain else 0) + 2 * bond ** 2) * 4,
+                  "per_launch": B * (((sites - 2) * bond ** 4 if (not args.grouped) else 0) + 2 * bond ** 2) * 4,
                   "unit": "GB/s", "peak": hbm_peak(), "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
                   "what": "bytes of the merged sites written per launch"},
         # one launch per step: every ladder sketch (reps x 16 tensors x m FP32) read once
@@ -455,7 +455,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": f"tt_pair_8x32x8: per GPU per step {B} pairs of tensor trains (8 sites, bond 32, "
                                "physical 8, N(0, 1/sqrt(32))); method 2 on the merged acyclic chain + method 1 on "
                                "the cyclic ladder, m=1024, 64 reps, FP32",
-                   "chain": ("merged sites materialised every step (tnsk_pairs)" if args.dense_chain else
+                   "chain": ("merged sites materialised every step (tnsk_pairs)" if (not args.grouped) else
                              "inner sites as grouped tensors (tnsk_rung: entries formed inside the tensor-core "
                              "sketch product), end sites merged every step (tnsk_pairs)"),
                    "networks_per_step": 2 * B, "estimate": "method-2 combined estimate of one pair",
