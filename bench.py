@@ -234,7 +234,7 @@ def run_ours(args, world, rank, local):
                 elif k == sites - 1:  # [a, s] x [b, s] -> [a, b]
                     out = torch.empty((bond * bond,), dtype=torch.float32, device=dev)
                     jobs.append((Ak, Bk, [1], [1], None, out.view(bond, bond)))
-                elif (not args.grouped):  # [a, s, c] x [b, s, d] -> [a, b, c, d]
+                elif not args.grouped:  # [a, s, c] x [b, s, d] -> [a, b, c, d]
                     out = torch.empty((bond * bond, bond * bond), dtype=torch.float32, device=dev)
                     jobs.append((Ak, Bk, [1], [1], [0, 2, 1, 3], out.view(bond, bond, bond, bond)))
                 else:  # grouped tensor: its entries are formed inside the sketch product
@@ -322,12 +322,12 @@ def run_ours(args, world, rank, local):
             dense_jobs.append((Ak, Bk, [1], [1], [0, 2, 1, 3], o.view(bond, bond, bond, bond)))
             chain.append(o)
         dense.append(chain)
-    if not (not args.grouped):
+    if args.grouped:
         ctx.contract_pairs(dense_jobs)
         ctx.sync()
     eps2, eps1, rel2, rel1 = [], [], [], []
     for i in range(B):
-        chain_ts = dense[i] if not (not args.grouped) else nets[2 * i + 1].tensors
+        chain_ts = dense[i] if args.grouped else nets[2 * i + 1].tensors
         tc = exact_chain(chain_ts)
         eps2.append((est[2 * i + 1] - tc) / frob(chain_ts))
         eps1.append((est[2 * i] - tc) / frob(nets[2 * i].tensors))
