@@ -309,25 +309,22 @@ def run_ours(args, world, rank, local):
     # the dense merged chains (every site by tnsk_pairs, outside the timed region) give
     # tc and the input norms
     est = [float(o.item()) for o in outs]
-    dense_jobs, dense = [], []
-    for i in range(B):
-        views = nets[2 * i].tensors
-        chain = []
-        for k in range(sites):
-            Ak, Bk = views[k], views[sites + k]
-            if k in (0, sites - 1):
-                chain.append(nets[2 * i + 1].tensors[k])
-                continue
-            o = torch.empty((bond * bond, bond * bond), dtype=torch.float32, device=dev)
-            dense_jobs.append((Ak, Bk, [1], [1], [0, 2, 1, 3], o.view(bond, bond, bond, bond)))
-            chain.append(o)
-        dense.append(chain)
-    if args.grouped:
+    dense = [nets[2 * i + 1].tensors for i in range(B)]
+    if args.grouped:  # the inner sites were never stored: merge them once, untimed
+        dense_jobs = []
+        for i in range(B):
+            views = nets[2 * i].tensors
+            chain = list(dense[i])
+            for k in range(1, sites - 1):
+                o = torch.empty((bond * bond, bond * bond), dtype=torch.float32, device=dev)
+                dense_jobs.append((views[k], views[sites + k], [1], [1], [0, 2, 1, 3], o.view(bond, bond, bond, bond)))
+                chain[k] = o
+            dense[i] = chain
         ctx.contract_pairs(dense_jobs)
         ctx.sync()
     eps2, eps1, rel2, rel1 = [], [], [], []
     for i in range(B):
-        chain_ts = dense[i] if args.grouped else nets[2 * i + 1].tensors
+        chain_ts = dense[i]
         tc = exact_chain(chain_ts)
         eps2.append((est[2 * i + 1] - tc) / frob(chain_ts))
         eps1.append((est[2 * i] - tc) / frob(nets[2 * i].tensors))
