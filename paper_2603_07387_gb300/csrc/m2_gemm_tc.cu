@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(128, 2) m2_gemm_tc_kernel(const M2Node* __rest
 namespace {
 
 constexpr int kRawStages = 3;  // two CTAs per SM: 2 x 97 KiB of shared memory
-constexpr int kTmStages = 4;  // X tail stages of 32 columns after the 64-column accumulator
+constexpr int kTmStages = 2;
 constexpr int kRawX = kTM * 128;   // 128 rows x 128 B
 constexpr int kRawV = kTN * 128;   // 64 rows x 128 B (one of hi / lo)
 constexpr int kRawStage = kRawX + 2 * kRawV;
@@ -408,18 +408,17 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
             if (ok && c >= kTmStages) ok = mbar_wait(smem_addr(&tm_empty[t]), (uint32_t)((c / kTmStages - 1) & 1));
             if (!ok) break;
             const unsigned char* rowp = raw + s * kRawStage + (r >> 3) * 1024 + (r & 7) * 128;
-            // the MMA reads X itself as its TF32 head (the low 13 mantissa bits ignored):
-            // only the remainder x - head, rounded to TF32, goes to tensor memory
-            uint32_t lo[32];
+            uint32_t hi[32], lo[32];
 #pragma unroll
             for (int g = 0; g < 8; ++g) {
                 const float4 v = *reinterpret_cast<const float4*>(rowp + ((g ^ (r & 7)) << 4));
                 const float x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int q = 0; q < 4; ++q) lo[4 * g + q] = tf32_tail(x[q]);
+                for (int q = 0; q < 4; ++q) tf32_split(x[q], hi[4 * g + q], lo[4 * g + q]);
             }
-            const uint32_t col = (uint32_t)(kTN + 32 * t);
-            tmem_store32(tmem + lane_base + col, lo);
+            const uint32_t col = (uint32_t)(kTN + 64 * t);
+            tmem_store32(tmem + lane_base + col, hi);
+            tmem_store32(tmem + lane_base + col + 32, lo);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -433,27 +432,21 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const unsigned char* st = raw + s * kRawStage;
-            const uint32_t a_lo = tmem + (uint32_t)(kTN + 32 * t);
-            // X head x V^T hi, X head x V^T lo (A = the raw X tile in shared memory), then
-            // X tail x V^T hi (A = tensor memory)
+            const uint32_t a_hi = tmem + (uint32_t)(kTN + 64 * t), a_lo = a_hi + 32;
+            const uint32_t aop[3] = {a_hi, a_hi, a_lo};
+            const unsigned char* bop[3] = {st + kRawX, st + kRawX + kRawV, st + kRawX};
 #pragma unroll
-            for (int p = 0; p < 2; ++p)
+            for (int p = 0; p < 3; ++p)
 #pragma unroll
                 for (int ks = 0; ks < kKC / 8; ++ks) {
-                    const uint64_t ad = smem_desc_sw128(smem_addr(st) + ks * 32);
-                    const uint64_t bd = smem_desc_sw128(smem_addr(st + kRawX + p * kRawV) + ks * 32);
+                    const uint32_t at = aop[p] + ks * 8;
+                    const uint64_t bd = smem_desc_sw128(smem_addr(bop[p]) + ks * 32);
                     const uint32_t acc = (c > 0 || p > 0 || ks > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, q;\n\t}" ::"r"(tmem),
+                        "r"(at), "l"(bd), "r"(kIdesc), "r"(acc));
                 }
-#pragma unroll
-            for (int ks = 0; ks < kKC / 8; ++ks) {
-                const uint64_t bd = smem_desc_sw128(smem_addr(st + kRawX) + ks * 32);
-                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;" ::"r"(tmem),
-                             "r"(a_lo + ks * 8), "l"(bd), "r"(kIdesc));
-            }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_addr(&tm_empty[t])));
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(

@@ -31,13 +31,6 @@ namespace tnsk {
 // (a carry into the exponent is the correct rounding up). Integer operations
 // only, so the split of a streamed operand does not queue on the conversion
 // unit. x - hi is exact in FP32 (hi is within a factor of two of x).
-// x - t(x) rounded to TF32, t(x) = x with its low 13 mantissa bits cleared (the TF32 value
-// a tensor core reads from an FP32 word): x = t(x) + tail exactly before the rounding.
-__device__ __forceinline__ uint32_t tf32_tail(float x) {
-    const float head = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-    return (__float_as_uint(x - head) + 0x1000u) & 0xFFFFE000u;
-}
-
 __device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
     hi = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
     lo = (__float_as_uint(x - __uint_as_float(hi)) + 0x1000u) & 0xFFFFE000u;
