@@ -123,6 +123,9 @@ __global__ void __launch_bounds__(kScatterThreads) m1_scatter_kernel(const M1Ten
         gofs[d] = ctr[d] ? sT.tab[md] : 0;
         gcomp[d] = ctr[d] && sT.comp[md];
     }
+    // staged rows of TT words with the last mode's words 16-byte aligned (it is contracted,
+    // TT and its offset are multiples of 4; the vec4 path's index is one too)
+    const bool tab4 = ctr[MAXD - 1] && (TT & 3) == 0 && (base[MAXD - 1] & 3) == 0;
     // one table word of mode d at index off (rep r): staged or global, complement applied
     auto word_of = [&](auto global_tables, int r, int d, int off) -> uint32_t {
         if (decltype(global_tables)::value) {
@@ -190,11 +193,20 @@ __global__ void __launch_bounds__(kScatterThreads) m1_scatter_kernel(const M1Ten
                 if (V == 1) {
                     add(r, o, h, v[0]);
                 } else {
+                    // the last mode's four words: one 16-byte load when the staged row allows
+                    uint32_t wl[V];
+                    if (!kG && tab4) {
+                        const uint4 q = *reinterpret_cast<const uint4*>(s_tab + r * TT + off[L]);
+                        wl[0] = q.x;
+                        wl[V > 1 ? 1 : 0] = q.y;
+                        wl[V > 2 ? 2 : 0] = q.z;
+                        wl[V > 3 ? 3 : 0] = q.w;
+                    } else {
 #pragma unroll
-                    for (int j = 0; j < V; ++j) {
-                        const uint32_t hj = h + (ctr[L] ? word_of(global_tables, r, L, off[L] + j) : 0u);
-                        add(r, has_open ? o + j * ostr[L] : o, hj, v[j]);
+                        for (int j = 0; j < V; ++j) wl[j] = ctr[L] ? word_of(global_tables, r, L, off[L] + j) : 0u;
                     }
+#pragma unroll
+                    for (int j = 0; j < V; ++j) add(r, has_open ? o + j * ostr[L] : o, h + wl[j], v[j]);
                 }
             }
             // advance the multi-index by V * blockDim.x (mixed-radix add with carries)

@@ -96,16 +96,18 @@ __device__ __forceinline__ void rows_same_b_v4(const float* __restrict__ A, cons
     }
     for (int i = 0; i < nr; i += 4) {
         const int row = i + r4;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        // two columns per packed FP32 FMA (each half rounds like fmaf)
+        float2 acc01 = make_float2(0.f, 0.f), acc23 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
             const float a = __shfl_sync(0xffffffffu, av[q], row & 31);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[j] += a * bv[q][j];
+            const float2 aa = make_float2(a, a);
+            acc01 = __ffma2_rn(aa, make_float2(bv[q][0], bv[q][1]), acc01);
+            acc23 = __ffma2_rn(aa, make_float2(bv[q][2], bv[q][3]), acc23);
         }
         if (live && row < nr)
             *reinterpret_cast<float4*>(out + (int64_t)(base + row) * L + c) =
-                make_float4(acc[0], acc[1], acc[2], acc[3]);
+                make_float4(acc01.x, acc01.y, acc23.x, acc23.y);
     }
 }
 
