@@ -327,13 +327,12 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
     }
     const uint32_t len = (uint32_t)(it.end - it.begin);  // <= 128
     const uint32_t cnt = len * (uint32_t)it.b;
-    constexpr int kU2 = 2 * kU;  // 128 x 16 items: 8 chains per thread in one pass
-    for (uint32_t q0 = threadIdx.x; q0 < cnt; q0 += kU2 * blockDim.x) {
-        T val[kU2];
-        int rr[kU2];
-        int64_t cc[kU2];
+    for (uint32_t q0 = threadIdx.x; q0 < cnt; q0 += kU * blockDim.x) {
+        T val[kU];
+        int rr[kU];
+        int64_t cc[kU];
 #pragma unroll
-        for (int u = 0; u < kU2; ++u) {
+        for (int u = 0; u < kU; ++u) {
             const uint32_t q = q0 + (uint32_t)u * blockDim.x;
             rr[u] = -1;
             val[u] = (T)0;
@@ -351,7 +350,7 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
             cc[u] = col;
         }
 #pragma unroll
-        for (int u = 0; u < kU2; ++u)
+        for (int u = 0; u < kU; ++u)
             if (rr[u] >= 0) store(rr[u], cc[u], val[u]);
     }
 }

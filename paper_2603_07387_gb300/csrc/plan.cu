@@ -786,7 +786,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 // latency). With T tables (qt >= 2) whose share of a rep fits 48 KiB and
                 // enough columns to amortise the copy: staged form (pad_ = 1), a few reps x
                 // 512 columns with the reps' T tables and child sketches in shared memory.
-                // Otherwise 128 columns x 16 reps, every lookup from L2.
+                // Otherwise 128 columns x 8 reps, every lookup from L2.
                 const int64_t tw = nd.qt >= 2 ? 2 * (int64_t)(nd.qt - 1) * m : 0;
                 const int64_t per_rep = tw * 4 + m * (fp64 ? 8 : 4) + 16;
                 const int64_t budget = 48 * 1024;
@@ -802,9 +802,9 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                             P.m2.vbuild_smem = std::max(P.m2.vbuild_smem, bytes);
                         }
                 } else {
-                    for (int r0 = 0; r0 < R; r0 += 16)
+                    for (int r0 = 0; r0 < R; r0 += 8)
                         for (int64_t b0 = 0; b0 < nd.cols; b0 += 128) {
-                            M2Item it{node_idx, r0, std::min(16, R - r0), 0, b0, std::min(nd.cols, b0 + 128)};
+                            M2Item it{node_idx, r0, std::min(8, R - r0), 0, b0, std::min(nd.cols, b0 + 128)};
                             pend.push_back({h, M2_VBUILD, it});
                         }
                 }
