@@ -801,16 +801,6 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                                 (((size_t)g * tw * 4 + 15) & ~(size_t)15) + (size_t)g * m * (fp64 ? 8 : 4);
                             P.m2.vbuild_smem = std::max(P.m2.vbuild_smem, bytes);
                         }
-                } else if (nd.qt == 1 && per_rep <= budget && nd.cols >= 512) {
-                    // one child, no T tables: one rep x 1024 columns per CTA with that rep's
-                    // child sketch staged (4 bytes copied per output instead of a 32-byte L2
-                    // sector per gather)
-                    for (int r0 = 0; r0 < R; ++r0)
-                        for (int64_t b0 = 0; b0 < nd.cols; b0 += 1024) {
-                            M2Item it{node_idx, r0, 1, 1, b0, std::min(nd.cols, b0 + 1024)};
-                            pend.push_back({h, M2_VBUILD, it});
-                        }
-                    P.m2.vbuild_smem = std::max(P.m2.vbuild_smem, (size_t)m * (fp64 ? 8 : 4));
                 } else {
                     for (int r0 = 0; r0 < R; r0 += 8)
                         for (int64_t b0 = 0; b0 < nd.cols; b0 += 128) {
