@@ -273,29 +273,24 @@ __global__ void __launch_bounds__(128, 2) m2_gemm_tc_kernel(const M2Node* __rest
 // TMA (2-D boxes from tensor maps made at plan time) in the 128-byte swizzled
 // K-major layout, with zero fill outside the matrices. X's hi / lo parts go to
 // tensor memory, so the MMA reads A from TMEM and only B from shared memory:
-//   warp 0     producers: lane 0 loads the X tiles into a 4-deep ring whose stages
-//              the converters free as soon as they have read them, lane 1 the
-//              V^T hi / lo tiles into a 2-deep ring freed by the MMAs' commits
-//              (expect_tx counts bytes); two CTAs share an SM, so one's prologue
-//              and epilogue overlap the other's streaming
+//   warp 0     producer: three cp.async.bulk.tensor loads per chunk into a
+//              3-deep ring (raw_full counts bytes); two CTAs share an SM, so
+//              one's prologue and epilogue overlap the other's streaming
 //   warps 1-4  converters: one row of X per thread (its TMEM lane), raw FP32 ->
 //              hi / lo TF32 stored with tcgen05.st; then the epilogue
 //   warp 5     tensor memory allocation and MMA issue; tcgen05.commit frees the
-//              V^T stage and the TMEM operand stage
+//              ring stage and the TMEM operand stage
 // Tensor memory: columns [0, 64) accumulator, [64 + 64 t, + 64) operand stage t
 // (hi in the first 32 columns, lo in the next 32).
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int kRawStages = 3;  // stage count of the grouped-tensor kernel's V^T ring
+constexpr int kRawStages = 3;  // two CTAs per SM: 2 x 97 KiB of shared memory
 constexpr int kTmStages = 2;
 constexpr int kRawX = kTM * 128;   // 128 rows x 128 B
 constexpr int kRawV = kTN * 128;   // 64 rows x 128 B (one of hi / lo)
-// streaming kernel: an X ring (stage freed when the converters have read it) deeper than
-// the V^T ring (freed when the MMAs are done); two CTAs per SM: 2 x 97 KiB
-constexpr int kXStages = 4;
-constexpr int kVStages = 2;
-constexpr int kStreamSmem = kXStages * kRawX + kVStages * 2 * kRawV + 1024;
+constexpr int kRawStage = kRawX + 2 * kRawV;
+constexpr int kStreamSmem = kRawStages * kRawStage + 1024;
 constexpr uint32_t kTmemCols = 256;
 
 // K-major, 128-byte swizzle: stride byte offset 1024 (8-row atoms), leading offset unused.
@@ -336,13 +331,11 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
                                                                    const unsigned char* __restrict__ tmaps,
                                                                    int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t x_full[kXStages], x_empty[kXStages];
-    __shared__ __align__(8) uint64_t v_full[kVStages], v_empty[kVStages];
+    __shared__ __align__(8) uint64_t raw_full[kRawStages], raw_empty[kRawStages];
     __shared__ __align__(8) uint64_t tm_full[kTmStages], tm_empty[kTmStages];
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t tmem_base;
-    unsigned char* xring = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* vring = xring + kXStages * kRawX;
+    unsigned char* raw = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const M2Item it = items[blockIdx.x];
     const M2Node& nd = nodes[it.node];
@@ -365,13 +358,9 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int s = 0; s < kXStages; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&x_full[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(&x_empty[s])));
-        }
-        for (int s = 0; s < kVStages; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&v_full[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&v_empty[s])));
+        for (int s = 0; s < kRawStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&raw_full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&raw_empty[s])));
         }
         for (int t = 0; t < kTmStages; ++t) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(&tm_full[t])));
@@ -387,36 +376,24 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
     bool ok = true;
 
     if (warp == 0) {
-        // ---------------- producers: lane 0 the X tiles (a stage is free once the converters
-        // have read it), lane 1 the V^T hi / lo tiles (free once the MMAs using them are done)
-        if (lane < 2) {
-            const bool xl = lane == 0;
-            const int nst = xl ? kXStages : kVStages;
-            uint64_t* full = xl ? x_full : v_full;
-            uint64_t* empty = xl ? x_empty : v_empty;
-            if (xl) {
-                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmx) : "memory");
-            } else {
-                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvh) : "memory");
-                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvl) : "memory");
-            }
+        // ---------------- producer (one thread)
+        if (lane == 0) {
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmx) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvh) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvl) : "memory");
             for (int c = 0; c < nch && ok; ++c) {
-                const int s = c % nst;
-                if (c >= nst) ok = mbar_wait(smem_addr(&empty[s]), (uint32_t)((c / nst - 1) & 1));
+                const int s = c % kRawStages;
+                if (c >= kRawStages)
+                    ok = mbar_wait(smem_addr(&raw_empty[s]), (uint32_t)((c / kRawStages - 1) & 1));
                 if (!ok) break;
                 const int k0 = (cbeg + c) * kKC;
-                const uint32_t bar = smem_addr(&full[s]);
-                if (xl) {
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kRawX)
-                                 : "memory");
-                    tma_load_2d(smem_addr(xring + s * kRawX), tmx, k0, (int)row0, bar);
-                } else {
-                    unsigned char* st = vring + s * 2 * kRawV;
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2 * kRawV)
-                                 : "memory");
-                    tma_load_2d(smem_addr(st), tmvh, k0, rep0, bar);
-                    tma_load_2d(smem_addr(st + kRawV), tmvl, k0, rep0, bar);
-                }
+                unsigned char* st = raw + s * kRawStage;
+                const uint32_t bar = smem_addr(&raw_full[s]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kRawStage)
+                             : "memory");
+                tma_load_2d(smem_addr(st), tmx, k0, (int)row0, bar);
+                tma_load_2d(smem_addr(st + kRawX), tmvh, k0, rep0, bar);
+                tma_load_2d(smem_addr(st + kRawX + kRawV), tmvl, k0, rep0, bar);
             }
         }
         __syncwarp();
@@ -426,11 +403,11 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
         const int r = q4 * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
         for (int c = 0; c < nch && ok; ++c) {
-            const int s = c % kXStages, t = c % kTmStages;
-            ok = mbar_wait(smem_addr(&x_full[s]), (uint32_t)((c / kXStages) & 1));
+            const int s = c % kRawStages, t = c % kTmStages;
+            ok = mbar_wait(smem_addr(&raw_full[s]), (uint32_t)((c / kRawStages) & 1));
             if (ok && c >= kTmStages) ok = mbar_wait(smem_addr(&tm_empty[t]), (uint32_t)((c / kTmStages - 1) & 1));
             if (!ok) break;
-            const unsigned char* rowp = xring + s * kRawX + (r >> 3) * 1024 + (r & 7) * 128;
+            const unsigned char* rowp = raw + s * kRawStage + (r >> 3) * 1024 + (r & 7) * 128;
             uint32_t hi[32], lo[32];
 #pragma unroll
             for (int g = 0; g < 8; ++g) {
@@ -439,8 +416,6 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
 #pragma unroll
                 for (int q = 0; q < 4; ++q) tf32_split(x[q], hi[4 * g + q], lo[4 * g + q]);
             }
-            __syncwarp();  // every lane has read its row: the X stage goes back to the producer
-            if (lane == 0) mbar_arrive(smem_addr(&x_empty[s]));
             const uint32_t col = (uint32_t)(kTN + 64 * t);
             tmem_store32(tmem + lane_base + col, hi);
             tmem_store32(tmem + lane_base + col + 32, lo);
@@ -452,12 +427,11 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
     } else if (lane == 0) {
         // ---------------- MMA issue (warp 5, one thread)
         for (int c = 0; c < nch && ok; ++c) {
-            const int s = c % kVStages, t = c % kTmStages;
+            const int s = c % kRawStages, t = c % kTmStages;
             ok = mbar_wait(smem_addr(&tm_full[t]), (uint32_t)((c / kTmStages) & 1));
-            if (ok) ok = mbar_wait(smem_addr(&v_full[s]), (uint32_t)((c / kVStages) & 1));
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned char* st = vring + s * 2 * kRawV - kRawX;  // V^T hi at st + kRawX
+            const unsigned char* st = raw + s * kRawStage;
             const uint32_t a_hi = tmem + (uint32_t)(kTN + 64 * t), a_lo = a_hi + 32;
             const uint32_t aop[3] = {a_hi, a_hi, a_lo};
             const unsigned char* bop[3] = {st + kRawX, st + kRawX + kRawV, st + kRawX};
@@ -476,7 +450,7 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_addr(&tm_empty[t])));
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_addr(&v_empty[s])));
+                smem_addr(&raw_empty[s])));
             if (c == nch - 1)
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     smem_addr(&done_bar)));
