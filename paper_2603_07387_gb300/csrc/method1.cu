@@ -219,9 +219,79 @@ __global__ void __launch_bounds__(kScatterThreads) m1_scatter_kernel(const M1Ten
             }
         }
     };
+    // Hoisted form of the staged vec4 path: when the stride of a thread's entries leaves
+    // every slot from d0 on unchanged (their step digits are 0, so no carry reaches them),
+    // the last mode among them, and exactly one contracted slot dv below d0 changes, a
+    // thread takes up to 4 of its entries at once and, per rep, reads the unchanged
+    // slots' words once (the last mode's four as one 16-byte load) and one word of dv
+    // per entry, instead of every word per entry.
+    int d0 = MAXD, dv = -1, nvar = 0;
+#pragma unroll
+    for (int d = MAXD - 1; d >= 0; --d)
+        if (step[d] == 0 && d0 == d + 1) d0 = d;
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d)
+        if (d < d0 && ctr[d]) ++nvar, dv = d;
+    const bool hoist = vec4 && !w.gtab && tab4 && d0 <= MAXD - 1 && !has_open && nvar == 1;
+    auto entries_hoisted = [&]() {
+        constexpr int L = MAXD - 1;
+        constexpr int KG = 4;
+        const int64_t S = 4 * (int64_t)blockDim.x;
+        int hb[MAXD];  // offsets of the unchanged slots' words
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) hb[d] = base[d] + dig[d];
+        int64_t f = w.begin + 4 * (int64_t)threadIdx.x;
+        while (f < w.end) {
+            float4 q[KG];
+            int ov[KG];
+            int kn = 0;
+#pragma unroll
+            for (int k = 0; k < KG; ++k) {
+                q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                ov[k] = 0;
+                if (f < w.end) {
+                    q[k] = __ldg(reinterpret_cast<const float4*>((const float*)sT.data + f));
+                    int od = 0;
+#pragma unroll
+                    for (int d = 0; d < MAXD; ++d)
+                        if (d == dv) od = base[d] + dig[d];
+                    ov[k] = od;
+                    ++kn;
+                    f += S;
+                    int carry = 0;  // advance the changing slots (below d0) by the stride
+#pragma unroll
+                    for (int d = MAXD - 1; d >= 0; --d) {
+                        if (d >= d0) continue;
+                        const int t = dig[d] + step[d] + carry;
+                        carry = t >= dim[d];
+                        dig[d] = carry ? t - dim[d] : t;
+                    }
+                }
+            }
+            for (int r = 0; r < nrep; ++r) {
+                const uint32_t* row = s_tab + r * TT;
+                uint32_t hc = 0;
+#pragma unroll
+                for (int d = 0; d < L; ++d)
+                    if (d >= d0 && ctr[d]) hc += row[hb[d]];
+                const uint4 wl = *reinterpret_cast<const uint4*>(row + hb[L]);
+#pragma unroll
+                for (int k = 0; k < KG; ++k) {
+                    if (k >= kn) break;
+                    const uint32_t h = hc + row[ov[k]];
+                    add(r, 0, h + wl.x, (AccT)q[k].x);
+                    add(r, 0, h + wl.y, (AccT)q[k].y);
+                    add(r, 0, h + wl.z, (AccT)q[k].z);
+                    add(r, 0, h + wl.w, (AccT)q[k].w);
+                }
+            }
+        }
+    };
     if (vec4) {
         if (w.gtab)
             entries(std::true_type{}, std::integral_constant<int, 4>{});
+        else if (hoist && sizeof(AccT) == 4)
+            entries_hoisted();
         else
             entries(std::false_type{}, std::integral_constant<int, 4>{});
     } else {
