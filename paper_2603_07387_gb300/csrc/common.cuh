@@ -186,7 +186,8 @@ struct M1Work {
                          // 2: shared-memory bins of a whole tensor, flushed by stores
     int32_t gtab;        // 1: hash-table words read from global memory (large tables),
                          // 0: staged in shared memory
-    int32_t pad_;
+    int32_t ltab;        // staged tables hold only the index range of each mode that
+                         // [begin, end) touches (large tensors sketched in chunks)
 };
 
 template <typename T>

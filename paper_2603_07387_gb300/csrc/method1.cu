@@ -39,15 +39,31 @@ __global__ void __launch_bounds__(kScatterThreads) m1_scatter_kernel(const M1Ten
                                                          const uint32_t* __restrict__ tabs, AccT* __restrict__ xs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ M1Tensor sT;
-    __shared__ int32_t sbase[TNSK_MAX_ORDER];
+    __shared__ int32_t sbase[TNSK_MAX_ORDER], slo[TNSK_MAX_ORDER], scnt[TNSK_MAX_ORDER];
     __shared__ int32_t sTT;
     const M1Work w = work[blockIdx.x];
     if (threadIdx.x == 0) {
         sT = tens[w.tensor];
+        // per contracted mode: the staged index range [lo, lo + cnt) (mod dim); the whole
+        // mode unless the work item's entries touch only part of it (w.ltab)
+        int64_t P = 1;  // product of the dims after mode d
+        for (int d = TNSK_MAX_ORDER - 1; d >= 0; --d) {
+            slo[d] = 0;
+            scnt[d] = d < sT.order ? (int32_t)sT.dims[d] : 0;
+            if (d >= sT.order) continue;
+            if (w.ltab && sT.dims[d] > 0) {
+                const int64_t fb = w.begin / P, span = (w.end - 1) / P - fb + 1;
+                if (span < sT.dims[d]) {
+                    slo[d] = (int32_t)(fb % sT.dims[d]);
+                    scnt[d] = (int32_t)span;
+                }
+            }
+            P *= sT.dims[d];
+        }
         int acc = 0;
         for (int d = 0; d < TNSK_MAX_ORDER; ++d) {
             sbase[d] = acc;
-            if (d < sT.order && sT.tab[d] >= 0) acc += sT.dims[d];
+            if (d < sT.order && sT.tab[d] >= 0) acc += scnt[d];
         }
         sTT = acc;
     }
@@ -71,8 +87,9 @@ __global__ void __launch_bounds__(kScatterThreads) m1_scatter_kernel(const M1Ten
         int loc = q - r * TT;
         int d = 0;
         for (int dd = 0; dd < order; ++dd)
-            if (sT.tab[dd] >= 0 && loc >= sbase[dd] && loc < sbase[dd] + sT.dims[dd]) d = dd;
-        int i = loc - sbase[d];
+            if (sT.tab[dd] >= 0 && loc >= sbase[dd] && loc < sbase[dd] + scnt[dd]) d = dd;
+        int i = slo[d] + (loc - sbase[d]);
+        if (i >= sT.dims[d]) i -= (int)sT.dims[d];
         uint32_t word = tabs[N.tab_off + (int64_t)(w.rep0 + r) * N.L + sT.tab[d] + i];
         if (sT.comp[d]) word = (((uint32_t)m - (word & mask)) & mask) | (word & TNSK_SIGN_BIT);
         s_tab[q] = word;
@@ -84,7 +101,7 @@ __global__ void __launch_bounds__(kScatterThreads) m1_scatter_kernel(const M1Ten
 
     // block-uniform per-mode data in registers. Slot s holds mode s - (MAXD - order): the
     // padding slots (dim 1, not contracted) come first, so the last mode is slot MAXD - 1
-    int dim[MAXD], base[MAXD], dig[MAXD], step[MAXD];
+    int dim[MAXD], base[MAXD], lo[MAXD], dig[MAXD], step[MAXD];
     bool ctr[MAXD];
     int64_t ostr[MAXD];
     const bool has_open = O > 1;
@@ -102,6 +119,7 @@ __global__ void __launch_bounds__(kScatterThreads) m1_scatter_kernel(const M1Ten
             const bool live = md >= 0;
             dim[d] = live ? sT.dims[md] : 1;
             base[d] = live ? sbase[md] : 0;
+            lo[d] = live ? slo[md] : 0;
             ctr[d] = live && sT.tab[md] >= 0;
             ostr[d] = live ? sT.ostride[md] : 0;
             dig[d] = (int)(f0 % dim[d]);
@@ -125,7 +143,12 @@ __global__ void __launch_bounds__(kScatterThreads) m1_scatter_kernel(const M1Ten
     }
     // staged rows of TT words with the last mode's words 16-byte aligned (it is contracted,
     // TT and its offset are multiples of 4; the vec4 path's index is one too)
-    const bool tab4 = ctr[MAXD - 1] && (TT & 3) == 0 && (base[MAXD - 1] & 3) == 0;
+    const bool tab4 = ctr[MAXD - 1] && (TT & 3) == 0 && (base[MAXD - 1] & 3) == 0 && (lo[MAXD - 1] & 3) == 0;
+    // staged word offset of slot d's digit x (the staged range starts at lo, mod dim)
+    auto soff = [&](int d, int x) {
+        int r = x - lo[d];
+        return base[d] + (r < 0 ? r + dim[d] : r);
+    };
     // one table word of mode d at index off (rep r): staged or global, complement applied
     auto word_of = [&](auto global_tables, int r, int d, int off) -> uint32_t {
         if (decltype(global_tables)::value) {
@@ -182,7 +205,7 @@ __global__ void __launch_bounds__(kScatterThreads) m1_scatter_kernel(const M1Ten
             int64_t o = 0;
 #pragma unroll
             for (int d = 0; d < MAXD; ++d) {
-                off[d] = (kG ? gofs[d] : base[d]) + dig[d];
+                off[d] = kG ? gofs[d] + dig[d] : soff(d, dig[d]);
                 if (has_open) o += (int64_t)dig[d] * ostr[d];
             }
             for (int r = 0; r < nrep; ++r) {
@@ -239,7 +262,7 @@ __global__ void __launch_bounds__(kScatterThreads) m1_scatter_kernel(const M1Ten
         const int64_t S = 4 * (int64_t)blockDim.x;
         int hb[MAXD];  // offsets of the unchanged slots' words
 #pragma unroll
-        for (int d = 0; d < MAXD; ++d) hb[d] = base[d] + dig[d];
+        for (int d = 0; d < MAXD; ++d) hb[d] = soff(d, dig[d]);
         int64_t f = w.begin + 4 * (int64_t)threadIdx.x;
         while (f < w.end) {
             float4 q[KG];
@@ -254,7 +277,7 @@ __global__ void __launch_bounds__(kScatterThreads) m1_scatter_kernel(const M1Ten
                     int od = 0;
 #pragma unroll
                     for (int d = 0; d < MAXD; ++d)
-                        if (d == dv) od = base[d] + dig[d];
+                        if (d == dv) od = soff(d, dig[d]);
                     ov[k] = od;
                     ++kn;
                     f += S;

@@ -508,10 +508,26 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 int64_t TT = 0;
                 for (int d = 0; d < T.order; ++d)
                     if (T.tab[d] >= 0) TT += T.dims[d];
-                // tables above 8 KiB per rep are read from global memory (L2)
-                const bool gtab = TT > 2048;
-                const size_t tab_b = gtab ? 0 : (size_t)TT * 4;
+                // tables above 8 KiB per rep: staged per chunk when the index ranges a chunk
+                // of privatised bins touches fit (ltab: a large tensor's leading modes cover
+                // a few indices per chunk), else read from global memory (L2)
                 const size_t bin_b = (size_t)T.O * m * acc;
+                bool gtab = TT > 2048, ltab = false;
+                int64_t TTl = TT;
+                if (gtab && T.numel * 4 >= T.O * m) {
+                    const int64_t CHl = std::max<int64_t>(8192, 32 * T.O * m);
+                    int64_t P = 1, tl = 0;
+                    for (int d = T.order - 1; d >= 0; --d) {
+                        if (T.tab[d] >= 0) tl += std::min<int64_t>(T.dims[d], (CHl - 1) / P + 2);
+                        P *= std::max<int64_t>(T.dims[d], 1);
+                    }
+                    if ((size_t)tl * 4 + bin_b + 16 <= kScatterSmemBudget && tl <= 16384) {
+                        gtab = false;
+                        ltab = true;
+                        TTl = tl;
+                    }
+                }
+                const size_t tab_b = gtab ? 0 : (size_t)TTl * 4;
                 int64_t nrep_priv = (int64_t)(kScatterSmemBudget / (tab_b + bin_b + 16));
                 bool priv = nrep_priv >= 1 && T.numel * 4 >= T.O * m;
                 int nrep;
@@ -535,6 +551,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                         w.nrep = std::min(nrep, R - r0);
                         w.priv = priv ? ((w.begin == 0 && w.end == T.numel) ? 2 : 1) : 0;
                         w.gtab = gtab ? 1 : 0;
+                        w.ltab = ltab ? 1 : 0;
                         m1w_cls[cls].push_back(w);
                     }
             }

@@ -87,15 +87,18 @@ def test_method1_estimate_small(ctx, prec, m):
 
 @pytest.mark.parametrize("prec", [tnsk.PREC_FP32, tnsk.PREC_FP64])
 def test_method1_large_tables_from_global_memory(ctx, prec):
-    """Modes above 2048 indices: the scatter reads table words from global memory
-    (with the complement applied on the fly) and chunks are large; tr(ABC) with long
-    inner modes, and a chain with an open leg, against the oracle."""
+    """Modes above 2048 indices: the scatter stages only the index ranges a chunk touches
+    (tr(ABC) with long inner modes, a chain with an open leg), or, where even those do
+    not fit next to the bins (a 20000-index last mode at m = 2^14), reads the table
+    words from global memory with the complement applied on the fly; against the
+    oracle."""
     rng = np.random.default_rng(17)
     tdt = torch.float64 if prec == tnsk.PREC_FP64 else torch.float32
     A, B, C = rng.standard_normal((3000, 5)), rng.standard_normal((5, 2100)), rng.standard_normal((2100, 3000))
     tri = W.NetSpec([A, B, C], [(1, 2), (3, 4), (5, 0)], [], "long-modes")
     chain = W.NetSpec([rng.standard_normal((2500, 3)), rng.standard_normal((2500, 4))], [(0, 2)], [1, 3], "open")
-    for spec, m in [(tri, 256), (tri, 4096), (chain, 64)]:
+    wide = W.NetSpec([rng.standard_normal((3, 20000)), rng.standard_normal((20000, 3))], [(1, 2), (3, 0)], [], "wide")
+    for spec, m in [(tri, 256), (tri, 4096), (chain, 64), (wide, 1 << 14)]:
         p = tnsk.Params(m=m, reps=9, seed=21, prec=prec)
         out, per = gpu_estimate(ctx, spec, p, tdt)
         y, s = oracle_estimate(spec, p, tdt)
