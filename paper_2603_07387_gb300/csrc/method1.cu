@@ -33,7 +33,7 @@ namespace tnsk {
 constexpr int kScatterThreads = 512;
 
 template <typename AccT, int MAXD>
-__global__ void __launch_bounds__(kScatterThreads) m1_scatter_kernel(const M1Tensor* __restrict__ tens,
+__global__ void __launch_bounds__(kScatterThreads, 2) m1_scatter_kernel(const M1Tensor* __restrict__ tens,
                                                          const M1Net* __restrict__ nets,
                                                          const M1Work* __restrict__ work,
                                                          const uint32_t* __restrict__ tabs, AccT* __restrict__ xs) {
