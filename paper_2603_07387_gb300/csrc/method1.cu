@@ -173,22 +173,17 @@ __global__ void __launch_bounds__(kScatterThreads, 2) m1_scatter_kernel(const M1
         constexpr bool kG = decltype(global_tables)::value;
         constexpr int V = decltype(vec)::value;
         constexpr int L = MAXD - 1;  // the tensor's last mode
-        // the entries of the next two steps (V = 4; the next one for V = 1) are loaded
-        // before this step's adds, so loads stay in flight while the thread works (what
-        // matters when the tensor streams from HBM)
+        // the next step's entries are loaded before this step's adds (one load in flight
+        // per thread while it works, which matters when the tensor streams from HBM)
         const int64_t fs = (int64_t)V * blockDim.x;
         int64_t f = w.begin + (int64_t)V * threadIdx.x;
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4* x4 = reinterpret_cast<const float4*>((const float*)sT.data);
-        float4 qn = z4, qn2 = z4;
+        float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);
         AccT vn = AccT(0);
         if (f < w.end) {
-            if (V == 4) {
-                qn = __ldg(x4 + f / 4);
-                if (f + fs < w.end) qn2 = __ldg(x4 + (f + fs) / 4);
-            } else {
+            if (V == 4)
+                qn = __ldg(reinterpret_cast<const float4*>((const float*)sT.data + f));
+            else
                 vn = load_as<AccT>(sT.data, sT.dtype, f);
-            }
         }
         for (; f < w.end; f += fs) {
             AccT v[V];
@@ -197,11 +192,14 @@ __global__ void __launch_bounds__(kScatterThreads, 2) m1_scatter_kernel(const M1
                 v[V > 1 ? 1 : 0] = (AccT)qn.y;
                 v[V > 2 ? 2 : 0] = (AccT)qn.z;
                 v[V > 3 ? 3 : 0] = (AccT)qn.w;
-                qn = qn2;
-                qn2 = f + 2 * fs < w.end ? __ldg(x4 + (f + 2 * fs) / 4) : z4;
             } else {
                 v[0] = vn;
-                if (f + fs < w.end) vn = load_as<AccT>(sT.data, sT.dtype, f + fs);
+            }
+            if (f + fs < w.end) {
+                if (V == 4)
+                    qn = __ldg(reinterpret_cast<const float4*>((const float*)sT.data + f + fs));
+                else
+                    vn = load_as<AccT>(sT.data, sT.dtype, f + fs);
             }
             int off[MAXD];
             int64_t o = 0;
