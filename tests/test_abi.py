@@ -37,3 +37,43 @@ def test_library_builds_and_exports_every_symbol():
     # status strings need no device
     lib.tnsk_status_string.restype = ctypes.c_char_p
     assert lib.tnsk_status_string(-2) == b"TNSK_ERR_CYCLIC"
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of tnsk_tensor, tnsk_rung, tnsk_network and tnsk_params have
+    the C layout (sizes and field offsets from a program compiled against the header)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    from paper_2603_07387_gb300 import tnsk
+
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "tnsk.h"\n'
+        "int main(void) {\n"
+        '  printf("%zu %zu %zu %zu\\n", sizeof(tnsk_tensor), offsetof(tnsk_tensor, dtype), '
+        "offsetof(tnsk_tensor, rung), sizeof(tnsk_rung));\n"
+        '  printf("%zu %zu %zu\\n", offsetof(tnsk_rung, d), sizeof(tnsk_network), sizeof(tnsk_params));\n'
+        "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(tnsk._Tensor), tnsk._Tensor.dtype.offset, tnsk._Tensor.rung.offset,
+            ctypes.sizeof(tnsk._Rung), tnsk._Rung.d.offset, ctypes.sizeof(tnsk._Network),
+            ctypes.sizeof(tnsk._Params)]
+    assert got == want
+
+
+def test_rung_factors_are_checked_on_the_host():
+    torch = pytest.importorskip("torch")
+    from paper_2603_07387_gb300 import tnsk
+
+    r = tnsk.Rung(torch.zeros(3, 4, 5), torch.zeros(6, 4, 7))
+    assert r.shape == (18, 35) and r.dim() == 2 and r.numel() == 18 * 35
+    with pytest.raises(ValueError):
+        tnsk.Rung(torch.zeros(3, 4, 5), torch.zeros(6, 2, 7))  # unequal shared dims
+    with pytest.raises(ValueError):
+        tnsk.Rung(torch.zeros(3, 4), torch.zeros(6, 4, 7))
