@@ -165,6 +165,29 @@ tnsk_status tnsk_estimate_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* ne
  * dividing R, or a pointer is NULL while O > 0. */
 tnsk_status tnsk_combine(tnsk_ctx* ctx, int32_t R, int64_t O, const double* per_rep, int32_t groups, double* out);
 
+/* Turnstile streams (Sec. 4.2: method 1 stores the sketches x_k, so the general
+ * turnstile model is served by applying each update X_k(i) += delta to every rep's
+ * sketch of X_k, in O(q_k)). tnsk_stream_create sketches the network's tensors as
+ * they are now (one method-1 network, params->method == TNSK_GENERAL, else
+ * TNSK_ERR_UNSUPPORTED), writes the estimate to `out` (device, prod of open dims) and
+ * `per_rep` (device [reps][O] or NULL), and keeps the sketches in memory owned by
+ * the stream; once that work has run, the tensors are not read again.
+ * tnsk_stream_update applies n updates: tensor[u] (0-based tensor of the network),
+ * index[u] (row-major flat entry index), delta[u]; all three device arrays [n],
+ * read by the launch. An update out of range changes nothing and makes the next
+ * tnsk_sync return TNSK_ERR_INVALID. Updates commute (atomic adds; FP32 sketches
+ * add in an order that varies between runs). tnsk_stream_estimate recomputes `out`
+ * and `per_rep` from the current sketches (transform, product, combination). All
+ * three enqueue on the ctx stream. tnsk_stream_destroy waits for the device and
+ * frees the stream. */
+typedef struct tnsk_stream tnsk_stream;
+tnsk_status tnsk_stream_create(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, double* out,
+                               double* per_rep, tnsk_stream** stream);
+tnsk_status tnsk_stream_update(tnsk_ctx* ctx, tnsk_stream* stream, int64_t n, const int32_t* tensor,
+                               const int64_t* index, const double* delta);
+tnsk_status tnsk_stream_estimate(tnsk_ctx* ctx, tnsk_stream* stream);
+tnsk_status tnsk_stream_destroy(tnsk_stream* stream);
+
 /* Per-kernel timing. While enabled, every kernel launch of the ctx is bracketed
  * by CUDA events recorded on the ctx stream. tnsk_profile_read waits for the
  * stream, writes the summed device time (ms) and the launch count of each kernel

@@ -471,6 +471,88 @@ tnsk_status tnsk_plan_destroy(tnsk_plan* plan) {
     return TNSK_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Turnstile streams (Sec. 4.2): one method-1 network whose sketches stay in a plan's
+// memory; updates change them in place, estimates rerun the transform, product and
+// combination on them.
+// ---------------------------------------------------------------------------
+struct tnsk_stream {
+    tnsk_plan* plan = nullptr;
+};
+
+tnsk_status tnsk_stream_create(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, double* out,
+                               double* per_rep, tnsk_stream** out_stream) {
+    if (!out_stream) return TNSK_ERR_INVALID;
+    *out_stream = nullptr;
+    tnsk_status st = check_ctx(ctx);
+    if (st != TNSK_OK) return st;
+    if (!net || !params || !out) return fail(ctx, TNSK_ERR_INVALID, "stream: NULL argument");
+    if (params->method != TNSK_GENERAL)
+        return fail(ctx, TNSK_ERR_UNSUPPORTED, "stream: turnstile updates are method 1 (TNSK_GENERAL) only");
+    double* const outs[1] = {out};
+    double* const pers[1] = {per_rep};
+    tnsk_plan* p = nullptr;
+    st = tnsk_plan_create(ctx, 1, net, params, outs, per_rep ? pers : nullptr, &p);
+    if (st != TNSK_OK) return st;
+    p->no_graph = true;  // runs partial sequences: no graph of the whole plan
+    st = launch_plan(ctx, p->plan, p->dev, p->fp64, nullptr);
+    if (st != TNSK_OK) {
+        tnsk_plan_destroy(p);
+        return st;
+    }
+    tnsk_stream* s = new tnsk_stream();
+    s->plan = p;
+    *out_stream = s;
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_stream_update(tnsk_ctx* ctx, tnsk_stream* s, int64_t n, const int32_t* tensor, const int64_t* index,
+                               const double* delta) {
+    tnsk_status st = check_ctx(ctx);
+    if (st != TNSK_OK) return st;
+    if (!s) return fail(ctx, TNSK_ERR_INVALID, "stream: NULL");
+    if (s->plan->device != ctx->device) return fail(ctx, TNSK_ERR_INVALID, "stream made on another device");
+    if (n < 0 || (n > 0 && (!tensor || !index || !delta))) return fail(ctx, TNSK_ERR_INVALID, "stream: bad update list");
+    if (n == 0) return TNSK_OK;
+    const tnsk_plan* p = s->plan;
+    ctx->prof.begin(TNSK_K_M1_SCATTER, ctx->stream);
+    TNSK_CUDA(launch_m1_updates(p->plan, p->dev, n, tensor, index, delta, p->fp64, ctx->d_err, ctx->stream));
+    ctx->prof.end(ctx->stream);
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_stream_estimate(tnsk_ctx* ctx, tnsk_stream* s) {
+    tnsk_status st = check_ctx(ctx);
+    if (st != TNSK_OK) return st;
+    if (!s) return fail(ctx, TNSK_ERR_INVALID, "stream: NULL");
+    const tnsk_plan* p = s->plan;
+    if (p->device != ctx->device) return fail(ctx, TNSK_ERR_INVALID, "stream made on another device");
+    const BatchPlan& plan = p->plan;
+    unsigned char* base = p->dev;
+    cudaStream_t cs = ctx->stream;
+    // per-rep estimates start from zero (some transform paths accumulate into them);
+    // the sketches, which follow them in the zeroed region, are kept
+    TNSK_CUDA(cudaMemsetAsync(base + plan.yrep_off, 0, plan.m1.xs_off - plan.yrep_off, cs));
+    Profiler& pf = ctx->prof;
+    pf.begin(TNSK_K_M1_SPECTRUM, cs);
+    TNSK_CUDA(launch_m1_spectra(plan, base, base + plan.m1.xs_off,
+                                p->fp64 ? (const void* const*)ctx->d_tw64 : (const void* const*)ctx->d_tw32, p->fp64,
+                                cs));
+    pf.end(cs);
+    pf.begin(TNSK_K_COMBINE, cs);
+    TNSK_CUDA(launch_combine((const CombineItem*)(base + plan.comb_off), plan.n_comb,
+                             (const double*)(base + plan.yrep_off), cs));
+    pf.end(cs);
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_stream_destroy(tnsk_stream* s) {
+    if (!s) return TNSK_ERR_INVALID;
+    tnsk_status st = tnsk_plan_destroy(s->plan);
+    delete s;
+    return st;
+}
+
 tnsk_status tnsk_combine(tnsk_ctx* ctx, int32_t R, int64_t O, const double* per_rep, int32_t groups, double* out) {
     tnsk_status st = check_ctx(ctx);
     if (st != TNSK_OK) return st;

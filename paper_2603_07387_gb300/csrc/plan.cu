@@ -594,6 +594,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 comb.push_back(c);
             }
             yrep_n += (int64_t)R * I.O;
+            if (m1n.empty()) P.m1_reps = R;
             m1n.push_back(nb);
             continue;
         }

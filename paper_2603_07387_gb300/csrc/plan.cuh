@@ -73,6 +73,7 @@ struct BatchPlan {
     size_t yrep_off = 0;
     size_t comb_off = 0;
     int n_comb = 0;
+    int m1_reps = 0;  // repetitions of the first method-1 network (turnstile streams)
     M1Plan m1;
     M2Plan m2;
 };
@@ -80,6 +81,9 @@ struct BatchPlan {
 // Launches the spectrum kernels of every method-1 item of the plan (rows a3 + a4).
 // Launches the scatter of every method-1 work item (row a2), one launch per order class.
 cudaError_t launch_m1_scatters(const BatchPlan& plan, unsigned char* base, void* xs, bool fp64, cudaStream_t s);
+// Turnstile updates of a one-network method-1 plan's stored sketches (every rep).
+cudaError_t launch_m1_updates(const BatchPlan& plan, unsigned char* base, int64_t n, const int32_t* tensor,
+                              const int64_t* index, const double* delta, bool fp64, int* err, cudaStream_t s);
 cudaError_t launch_m1_spectra(const BatchPlan& plan, unsigned char* base, const void* xs, const void* const* tws,
                               bool fp64, cudaStream_t s);
 

@@ -51,6 +51,10 @@ SYMBOLS = (
     "tnsk_sync",
     "tnsk_probe_shared_atomics",
     "tnsk_combine",
+    "tnsk_stream_create",
+    "tnsk_stream_update",
+    "tnsk_stream_estimate",
+    "tnsk_stream_destroy",
     "tnsk_mlp_num_params",
     "tnsk_mlp_create",
     "tnsk_mlp_destroy",
@@ -189,6 +193,14 @@ def load_library(path: str = LIB_PATH):
         getattr(L, name).argtypes = args
     L.tnsk_combine.restype = i32
     L.tnsk_combine.argtypes = [vp, i32, i64, vp, i32, vp]
+    L.tnsk_stream_create.restype = i32
+    L.tnsk_stream_create.argtypes = [vp, ctypes.POINTER(_Network), ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(vp)]
+    L.tnsk_stream_update.restype = i32
+    L.tnsk_stream_update.argtypes = [vp, vp, i64, vp, vp, vp]
+    L.tnsk_stream_estimate.restype = i32
+    L.tnsk_stream_estimate.argtypes = [vp, vp]
+    L.tnsk_stream_destroy.restype = i32
+    L.tnsk_stream_destroy.argtypes = [vp]
     L.tnsk_probe_shared_atomics.restype = i32
     L.tnsk_probe_shared_atomics.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.tnsk_status_string.restype = ctypes.c_char_p
@@ -332,6 +344,43 @@ class Plan:
     def close(self):
         if getattr(self, "h", None):
             self.ctx.lib.tnsk_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Stream:
+    """A turnstile stream (tnsk_stream): method-1 sketches of one network kept on the
+    device; update() adds deltas to tensor entries, estimate() recomputes the outputs."""
+
+    def __init__(self, ctx, handle, tensors, out, per_rep):
+        self.ctx, self.h = ctx, handle
+        self._keep = (tensors, out, per_rep)  # the tensors until the first sketching has run
+
+    def update(self, tensor, index, delta):
+        """Device arrays [n]: tensor (int32, 0-based tensor of the network), index (int64,
+        row-major flat entry index), delta (float64)."""
+        import torch
+
+        assert tensor.dtype == torch.int32 and index.dtype == torch.int64 and delta.dtype == torch.float64
+        assert tensor.is_cuda and index.is_cuda and delta.is_cuda
+        assert tensor.is_contiguous() and index.is_contiguous() and delta.is_contiguous()
+        n = tensor.numel()
+        assert index.numel() == n and delta.numel() == n
+        self._upd = (tensor, index, delta)  # alive until the next update (stream order)
+        self.ctx._check(self.ctx.lib.tnsk_stream_update(self.ctx.h, self.h, n, tensor.data_ptr(), index.data_ptr(),
+                                                        delta.data_ptr()))
+
+    def estimate(self):
+        self.ctx._check(self.ctx.lib.tnsk_stream_estimate(self.ctx.h, self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.tnsk_stream_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -547,6 +596,17 @@ class Context:
         """tnsk_contract_pairs: the jobs once (waits for them)."""
         j = _PairJobs(jobs)
         self._check(self.lib.tnsk_contract_pairs(self.h, j.n, ctypes.addressof(j.arr)))
+
+    def stream(self, net: Network, params: Params, out, per_rep=None) -> "Stream":
+        """tnsk_stream_create: sketch the network's tensors now (method 1), write the
+        estimate to out (and per_rep), keep the sketches for turnstile updates."""
+        nh = _NetHolder(net)
+        pr = _params(params)
+        h = ctypes.c_void_p()
+        self._check(self.lib.tnsk_stream_create(self.h, ctypes.byref(nh.c), ctypes.byref(pr), out.data_ptr(),
+                                                per_rep.data_ptr() if per_rep is not None else None,
+                                                ctypes.byref(h)))
+        return Stream(self, h, list(net.tensors), out, per_rep)
 
     def plan(self, nets: Sequence[Network], params: Sequence[Params], outs, per_reps=None) -> "Plan":
         """tnsk_plan_create: plan a batch once; run it with Plan.run()."""

@@ -326,6 +326,55 @@ def test_grouped_rung_tensors_rejected_where_unsupported(ctx):
         ctx.estimate(tnsk.Network(ts, spec24.edges, []), tnsk.Params(m=256, reps=4, method=tnsk.ACYCLIC), out)
 
 
+@pytest.mark.parametrize("prec", [tnsk.PREC_FP32, tnsk.PREC_FP64])
+def test_turnstile_stream_updates(ctx, prec):
+    """Sec. 4.2's turnstile model: sketch a cyclic network with an open leg, apply
+    batches of entry updates (repeated entries included) to the stored sketches, and
+    re-estimate; each estimate against the oracle on the updated tensors."""
+    rng = np.random.default_rng(31)
+    X0 = [rng.standard_normal((6, 5)), rng.standard_normal((5, 7, 3)), rng.standard_normal((7, 6))]
+    edges, open_ = [(1, 2), (3, 5), (6, 0)], [4]
+    tdt = torch.float64 if prec == tnsk.PREC_FP64 else torch.float32
+    spec0 = W.NetSpec(X0, edges, open_, "turnstile")
+    p = tnsk.Params(m=64, reps=6, groups=2, seed=5, method=tnsk.GENERAL, prec=prec)
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    per = torch.zeros((p.reps, 3), dtype=torch.float64, device="cuda")
+    st = ctx.stream(gpu_network(spec0, tdt), p, out, per)
+    ctx.sync()
+    y, sc = oracle_estimate(spec0, p, tdt)
+    assert_parity(per.cpu().numpy(), y, sc, TOL[prec], "stream initial")
+    X = [x.astype(np.float64) for x in rounded(spec0, tdt)]  # what the sketches hold
+    for batch in range(2):
+        n = 700
+        k = rng.integers(0, 3, n)
+        idx = np.array([rng.integers(0, X[kk].size) for kk in k])
+        idx[: n // 10] = idx[n // 10: 2 * (n // 10)]  # repeated entries
+        k[: n // 10] = k[n // 10: 2 * (n // 10)]
+        delta = rng.standard_normal(n)
+        for kk, ii, dd in zip(k, idx, delta):
+            X[kk].reshape(-1)[ii] += dd
+        st.update(torch.as_tensor(k, dtype=torch.int32, device="cuda"),
+                  torch.as_tensor(idx, dtype=torch.int64, device="cuda"),
+                  torch.as_tensor(delta, dtype=torch.float64, device="cuda"))
+        st.estimate()
+        ctx.sync()
+        y, sc = oracle_estimate(W.NetSpec(X, edges, open_, "turnstile"), p, torch.float64)
+        assert_parity(per.cpu().numpy(), y, sc, TOL[prec], f"stream after batch {batch}")
+        assert np.allclose(out.cpu().numpy(), oracle.combine(per.cpu().numpy(), 2), rtol=1e-14, atol=0)
+    # an update naming a tensor the network does not have is reported and changes nothing
+    before = per.clone()
+    st.update(torch.tensor([3], dtype=torch.int32, device="cuda"), torch.tensor([0], dtype=torch.int64, device="cuda"),
+              torch.tensor([1.0], dtype=torch.float64, device="cuda"))
+    with pytest.raises(tnsk.TnskError):
+        ctx.sync()
+    st.estimate()
+    ctx.sync()
+    assert torch.equal(per, before)
+    st.close()
+    with pytest.raises(tnsk.TnskError):  # method 2 keeps no per-tensor sketches
+        ctx.stream(gpu_network(spec0, tdt), tnsk.Params(m=64, reps=2, method=tnsk.ACYCLIC), out)
+
+
 # ---------------------------------------------------------------- batch, combine, errors
 def test_batch_matches_oracle_per_network(ctx):
     rng = np.random.default_rng(8)
