@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-hbm-probe", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--no-turnstile", action="store_true")
     ap.add_argument("--grouped", action="store_true",
                     help="inner sites as grouped tensors (tnsk_rung) instead of materialising them every step")
     return ap.parse_args()
@@ -440,6 +441,7 @@ def run_ours(args, world, rank, local):
     probe = hbm_sketch_probe(ctx, dev) if (rank == 0 and not args.no_hbm_probe) else None
     lvp = learned_vs_plain(ctx, dev) if (rank == 0 and not args.no_learned) else None
     unev = batched_uneven(ctx, dev) if (rank == 0 and not args.no_uneven) else None
+    turn = turnstile(ctx, dev, pairs[0][2]) if (rank == 0 and not args.no_turnstile) else None
     for p_ in plans + merges:
         p_.close()
     ctx.close()
@@ -468,6 +470,7 @@ def run_ours(args, world, rank, local):
         "hbm_sketch_probe": probe,
         "learned_vs_plain": lvp,
         "batched_uneven": unev,
+        "turnstile": turn,
         "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
         "gpu_launches": launches,
         "host_ms_per_call": round(host_s * 1e3 / max(args.steps, 1), 3),
@@ -549,6 +552,51 @@ def hbm_sketch_probe(ctx, dev):
     del mats
     torch.cuda.empty_cache()
     return res
+
+
+# ---------------------------------------------------------------- turnstile updates (Sec. 4.2)
+def turnstile(ctx, dev, ladder, n_upd: int = 1 << 20, batches: int = 8):
+    """Method 1 in the general turnstile model on one tensor-train ladder (16 tensors,
+    99,328 entries, m = 1024, 64 reps): the stored sketches take batches of 2^20 random
+    entry updates (tnsk_stream_update: one signed atomic add per update and rep), then
+    one re-estimate (transform, product, combination). Updates/s from CUDA events."""
+    import torch
+
+    from paper_2603_07387_gb300 import tnsk
+    from paper_2603_07387_gb300 import workloads as W
+
+    ts = W.to_torch(ladder, dev, torch.float32)
+    sizes = np.array([t.numel() for t in ts], dtype=np.int64)
+    rng = np.random.default_rng(20260307)
+    g = rng.integers(0, int(sizes.sum()), n_upd)  # uniform over all entries
+    starts = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    k = np.searchsorted(starts, g, side="right") - 1
+    k_d = torch.as_tensor(k.astype(np.int32), device=dev)
+    i_d = torch.as_tensor((g - starts[k]).astype(np.int64), device=dev)
+    d_d = torch.as_tensor(rng.standard_normal(n_upd), dtype=torch.float64, device=dev)
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    p = tnsk.Params(m=M, reps=REPS, seed=W.HASH_SEED, method=tnsk.GENERAL)
+    st = ctx.stream(tnsk.Network(ts, ladder.edges, ladder.open), p, out)
+    st.update(k_d, i_d, d_d)  # warm-up
+    st.estimate()
+    ctx.sync()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    for _ in range(batches):
+        st.update(k_d, i_d, d_d)
+    e1.record(stream)
+    st.estimate()
+    e2.record(stream)
+    ctx.sync()
+    upd_ms = e0.elapsed_time(e1) / batches
+    est_ms = e1.elapsed_time(e2)
+    st.close()
+    return {"workload": "tensor-train ladder (16 tensors, 99,328 entries), method 1, m=1024, 64 reps; batches of "
+                        "2^20 uniform random entry updates, N(0,1) deltas",
+            "updates_per_s": round(n_upd / (upd_ms / 1e3), 1),
+            "rep_updates_per_s": round(n_upd * REPS / (upd_ms / 1e3), 1),
+            "ms_per_batch": round(upd_ms, 4), "estimate_ms": round(est_ms, 4)}
 
 
 # ---------------------------------------------------------------- thousands of uneven networks in one batch
