@@ -171,7 +171,9 @@ tnsk_status tnsk_combine(tnsk_ctx* ctx, int32_t R, int64_t O, const double* per_
  * they are now (one method-1 network, params->method == TNSK_GENERAL, else
  * TNSK_ERR_UNSUPPORTED), writes the estimate to `out` (device, prod of open dims) and
  * `per_rep` (device [reps][O] or NULL), and keeps the sketches in memory owned by
- * the stream; once that work has run, the tensors are not read again.
+ * the stream; once that work has run, the tensors are not read again. A tensor
+ * whose data is NULL starts as all zeros: the sparse (COO) input path, where the
+ * nonzeros arrive as updates, each costing O(q_k) per rep instead of a dense pass.
  * tnsk_stream_update applies n updates: tensor[u] (0-based tensor of the network),
  * index[u] (row-major flat entry index), delta[u]; all three device arrays [n],
  * read by the launch. An update out of range changes nothing and makes the next

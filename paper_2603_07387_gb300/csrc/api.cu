@@ -248,12 +248,12 @@ tnsk_status tnsk_count_sketch(tnsk_ctx* ctx, uint64_t seed, uint64_t rep, uint64
 // Host part of a batch: validation and layout of descriptors and scratch.
 static tnsk_status build_plan(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
                               double* const* outs, double* const* per_reps, bool sketch_only, BatchPlan& plan,
-                              bool& fp64) {
+                              bool& fp64, bool zero_ok = false) {
     if (B < 0 || (B > 0 && (!nets || !params))) return fail(ctx, TNSK_ERR_INVALID, "null batch arguments");
     std::vector<NetInfo> infos(B);
     for (int b = 0; b < B; ++b) {
         std::string why;
-        tnsk_status st = validate(nets[b], params[b], infos[b], why);
+        tnsk_status st = validate(nets[b], params[b], infos[b], why, zero_ok);
         if (st != TNSK_OK) return fail(ctx, st, "network " + std::to_string(b) + ": " + why);
         if (!sketch_only && (!outs || !outs[b])) return fail(ctx, TNSK_ERR_INVALID, "null output buffer");
     }
@@ -386,15 +386,15 @@ tnsk_status tnsk_profile_read(tnsk_ctx* ctx, double* ms, int64_t* launches) {
     return TNSK_OK;
 }
 
-tnsk_status tnsk_plan_create(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
-                             double* const* outs, double* const* per_reps, tnsk_plan** out) {
+static tnsk_status create_plan(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
+                               double* const* outs, double* const* per_reps, bool zero_ok, tnsk_plan** out) {
     if (!out) return TNSK_ERR_INVALID;
     *out = nullptr;
     tnsk_status st = check_ctx(ctx);
     if (st != TNSK_OK) return st;
     tnsk_plan* p = new tnsk_plan();
     p->device = ctx->device;
-    st = build_plan(ctx, B, nets, params, outs, per_reps, false, p->plan, p->fp64);
+    st = build_plan(ctx, B, nets, params, outs, per_reps, false, p->plan, p->fp64, zero_ok);
     if (st != TNSK_OK) {
         delete p;
         return st;
@@ -423,6 +423,11 @@ tnsk_status tnsk_plan_create(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets,
     p->plan.host_desc.shrink_to_fit();
     *out = p;
     return TNSK_OK;
+}
+
+tnsk_status tnsk_plan_create(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
+                             double* const* outs, double* const* per_reps, tnsk_plan** out) {
+    return create_plan(ctx, B, nets, params, outs, per_reps, false, out);
 }
 
 tnsk_status tnsk_plan_run(tnsk_ctx* ctx, tnsk_plan* plan) {
@@ -492,7 +497,7 @@ tnsk_status tnsk_stream_create(tnsk_ctx* ctx, const tnsk_network* net, const tns
     double* const outs[1] = {out};
     double* const pers[1] = {per_rep};
     tnsk_plan* p = nullptr;
-    st = tnsk_plan_create(ctx, 1, net, params, outs, per_rep ? pers : nullptr, &p);
+    st = create_plan(ctx, 1, net, params, outs, per_rep ? pers : nullptr, true, &p);
     if (st != TNSK_OK) return st;
     p->no_graph = true;  // runs partial sequences: no graph of the whole plan
     st = launch_plan(ctx, p->plan, p->dev, p->fp64, nullptr);

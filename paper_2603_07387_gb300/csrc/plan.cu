@@ -107,7 +107,7 @@ tnsk_status finalize_plan(BatchPlan& P, unsigned char* base, std::string& err) {
     return TNSK_OK;
 }
 
-tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I, std::string& why) {
+tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I, std::string& why, bool zero_ok) {
     if (net.p < 1 || !net.X) {
         why = "need p >= 1 tensors";
         return TNSK_ERR_INVALID;
@@ -197,7 +197,8 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
         }
         I.numel[k] = n;
         I.rung.push_back(X.rung);
-        if (X.rung) {  // grouped tensor (Sec. 4.1): R((i,j),(k,l)) = sum_s A(i,s,k) B(j,s,l)
+        if (X.rung) {
+            I.zero.push_back(0);  // grouped tensor (Sec. 4.1): R((i,j),(k,l)) = sum_s A(i,s,k) B(j,s,l)
             const tnsk_rung& g = *X.rung;
             if (prm.method != TNSK_ACYCLIC || prm.prec != TNSK_PREC_FP32) {
                 why = "tensor " + std::to_string(k) + ": grouped (rung) tensors need method 2 in FP32";
@@ -216,7 +217,8 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
             }
             continue;
         }
-        if (n > 0 && !X.data) {
+        I.zero.push_back(n > 0 && !X.data && zero_ok ? 1 : 0);
+        if (n > 0 && !X.data && !zero_ok) {
             why = "null data for a non-empty tensor";
             return TNSK_ERR_INVALID;
         }
@@ -504,7 +506,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
             // scatter work: chunks of each tensor x batches of reps
             for (int k = 0; k < I.p; ++k) {
                 const M1Tensor& T = m1t[nb.t0 + k];
-                if (T.numel == 0 || T.O == 0) continue;
+                if (T.numel == 0 || T.O == 0 || I.zero[k]) continue;  // all-zero tensors add nothing
                 int64_t TT = 0;
                 for (int d = 0; d < T.order; ++d)
                     if (T.tab[d] >= 0) TT += T.dims[d];

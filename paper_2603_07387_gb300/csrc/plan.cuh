@@ -26,6 +26,7 @@ struct NetInfo {
     int log2m = 0;
     bool idx32 = true;
     std::vector<const tnsk_rung*> rung;  // [p] grouped tensors (NULL: stored)
+    std::vector<char> zero;              // [p] tensor given as all zeros (data NULL, streams only)
     // method 2: rooted tree (children in mode order, footnote to Gamma(k))
     int root = -1;
     std::vector<int> parent, parent_mode, parent_edge, height;
@@ -87,7 +88,9 @@ cudaError_t launch_m1_updates(const BatchPlan& plan, unsigned char* base, int64_
 cudaError_t launch_m1_spectra(const BatchPlan& plan, unsigned char* base, const void* xs, const void* const* tws,
                               bool fp64, cudaStream_t s);
 
-tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& info, std::string& why);
+// zero_ok: a tensor with data NULL is all zeros (turnstile streams fed by updates)
+tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& info, std::string& why,
+                     bool zero_ok = false);
 // True when the driver's tensor-map encoder is available (streaming tensor-core path).
 bool tensor_maps_available();
 // Encodes the plan's tensor maps into its host descriptor block once the device

@@ -265,6 +265,30 @@ class Rung:
         return self.shape[0] * self.shape[1]
 
 
+class Zeros:
+    """An all-zero tensor of the given shape that is never stored (data NULL): a
+    turnstile stream's sparse input, whose nonzeros arrive as updates."""
+
+    def __init__(self, *shape, dtype=None):
+        self.shape = tuple(int(d) for d in shape)
+        self.dtype = dtype
+
+    def dim(self):
+        return len(self.shape)
+
+    def numel(self):
+        n = 1
+        for d in self.shape:
+            n *= d
+        return n
+
+
+def torch_empty(dtype):
+    import torch
+
+    return torch.empty(0, dtype=dtype)
+
+
 class _NetHolder:
     """Owns the ctypes arrays behind one tnsk_network."""
 
@@ -288,6 +312,14 @@ class _NetHolder:
                 tens[k].data = None
                 tens[k].dtype = F32
                 tens[k].rung = ctypes.pointer(g)
+                continue
+            if isinstance(x, Zeros):  # all zeros, data NULL (turnstile streams only)
+                d = (ctypes.c_int64 * max(1, len(x.shape)))(*x.shape)
+                self.dims.append(d)
+                tens[k].order = len(x.shape)
+                tens[k].dims = ctypes.cast(d, ctypes.POINTER(ctypes.c_int64))
+                tens[k].data = None
+                tens[k].dtype = F32 if x.dtype is None else _dtype_code(torch_empty(x.dtype))
                 continue
             if x.numel() > 0 and not x.is_contiguous():
                 raise ValueError(f"tensor {k} must be contiguous (row-major)")

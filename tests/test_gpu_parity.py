@@ -375,6 +375,32 @@ def test_turnstile_stream_updates(ctx, prec):
         ctx.stream(gpu_network(spec0, tdt), tnsk.Params(m=64, reps=2, method=tnsk.ACYCLIC), out)
 
 
+def test_turnstile_sparse_triangle_count(ctx):
+    """The sparse (COO) input path: tr(A^3) of a random graph's adjacency matrix from
+    three all-zero tensors fed the nonzeros as updates, against the oracle's dense
+    estimate with the same hashes."""
+    rng = np.random.default_rng(33)
+    n = 160
+    Au = np.triu((rng.random((n, n)) < 0.15).astype(np.float64), 1)
+    A = Au + Au.T
+    spec = W.NetSpec([A, A, A], [(1, 2), (3, 4), (5, 0)], [], "triangles")
+    p = tnsk.Params(m=256, reps=16, seed=9, method=tnsk.GENERAL)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    per = torch.zeros((p.reps, 1), dtype=torch.float64, device="cuda")
+    st = ctx.stream(tnsk.Network([tnsk.Zeros(n, n)] * 3, spec.edges, []), p, out, per)
+    rows, cols = np.nonzero(A)
+    flat = (rows * n + cols).astype(np.int64)
+    k = np.repeat(np.arange(3, dtype=np.int32), flat.size)
+    st.update(torch.as_tensor(k, device="cuda"), torch.as_tensor(np.tile(flat, 3), device="cuda"),
+              torch.ones(3 * flat.size, dtype=torch.float64, device="cuda"))
+    st.estimate()
+    ctx.sync()
+    y, sc = oracle_estimate(spec, p, torch.float32)
+    assert_parity(per.cpu().numpy(), y, sc, TOL[p.prec], "sparse triangles")
+    assert np.allclose(out.cpu().numpy(), oracle.combine(per.cpu().numpy(), 1), rtol=1e-14, atol=0)
+    st.close()
+
+
 # ---------------------------------------------------------------- batch, combine, errors
 def test_batch_matches_oracle_per_network(ctx):
     rng = np.random.default_rng(8)
