@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-turnstile", action="store_true")
     ap.add_argument("--no-sparse", action="store_true")
+    ap.add_argument("--no-variance-gap", action="store_true")
     ap.add_argument("--grouped", action="store_true",
                     help="inner sites as grouped tensors (tnsk_rung) instead of materialising them every step")
     return ap.parse_args()
@@ -444,6 +445,7 @@ def run_ours(args, world, rank, local):
     unev = batched_uneven(ctx, dev) if (rank == 0 and not args.no_uneven) else None
     turn = turnstile(ctx, dev, pairs[0][2]) if (rank == 0 and not args.no_turnstile) else None
     sparse = sparse_triangles(ctx, dev) if (rank == 0 and not args.no_sparse) else None
+    vgap = variance_gap(ctx, dev) if (rank == 0 and not args.no_variance_gap) else None
     for p_ in plans + merges:
         p_.close()
     ctx.close()
@@ -474,6 +476,7 @@ def run_ours(args, world, rank, local):
         "batched_uneven": unev,
         "turnstile": turn,
         "sparse_triangles": sparse,
+        "variance_gap": vgap,
         "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
         "gpu_launches": launches,
         "host_ms_per_call": round(host_s * 1e3 / max(args.steps, 1), 3),
@@ -653,6 +656,49 @@ def sparse_triangles(ctx, dev, blocks: int = 256, size: int = 128, p_edge: float
             "estimates_per_s": round(1e3 / ms, 2), "ms_per_estimate": round(ms, 3),
             "rep_updates_per_s": round(3 * nnz * reps / (ms / 1e3), 1),
             "rel_err": [round(r, 4) for r in rel], "triangles_exact": exact / 6}
+
+
+# ---------------------------------------------------------------- exponential vs polynomial variance
+def variance_gap(ctx, dev, n: int = 8, qs=(2, 4, 6, 8, 10, 12, 14, 16), m1: int = 256, reps: int = 16384):
+    """The all-ones chain of Lemma "exponential-dependence" (vectors X_1, X_{q+1} and
+    q - 1 matrices, all entries 1, q contractions): the variance of one repetition,
+    normalised by prod_k ||X_k||_F^2 = n^(2q), measured over `reps` repetitions on the
+    GPU. Method 1 at a fixed m against the lemma's lower bound 3^q / (2 m^2) - 1 (it
+    grows exponentially in q); method 2 with m ~ 16 q against its bound
+    (1 + 8/m)^(2q) - 1 (bounded)."""
+    import torch
+
+    from paper_2603_07387_gb300 import tnsk
+
+    rows = []
+    for q in qs:
+        ts = [torch.ones(n, device=dev)] + [torch.ones(n, n, device=dev) for _ in range(q - 1)] + \
+             [torch.ones(n, device=dev)]
+        off = [0]
+        for t in ts:
+            off.append(off[-1] + t.dim())
+        edges = [(off[k + 1] - 1, off[k + 1]) for k in range(q)]
+        net = tnsk.Network(ts, edges, [])
+        norm = float(n) ** (2 * q)
+        tc = float(n) ** q
+        row = {"q": q}
+        for name, prm in (("m1", tnsk.Params(m=m1, reps=reps, seed=0x7E57, method=tnsk.GENERAL)),
+                          ("m2", tnsk.Params(m=1 << max(4, int(np.ceil(np.log2(16 * q)))), reps=reps, seed=0x7E57,
+                                             method=tnsk.ACYCLIC))):
+            out = torch.zeros(1, dtype=torch.float64, device=dev)
+            per = torch.zeros((reps, 1), dtype=torch.float64, device=dev)
+            ctx.estimate(net, prm, out, per)
+            ctx.sync()
+            y = per.cpu().numpy()[:, 0]
+            row[name + "_m"] = prm.m
+            row[name + "_var_norm"] = float(f"{np.var(y, ddof=1) / norm:.4g}")
+            row[name + "_mean_over_tc"] = round(float(np.mean(y)) / tc, 4)
+        row["m1_lower_bound"] = float(f"{3.0 ** q / (2.0 * m1 * m1) - 1.0:.4g}")
+        row["m2_upper_bound"] = float(f"{(1.0 + 8.0 / row['m2_m']) ** (2 * q) - 1.0:.4g}")
+        rows.append(row)
+    return {"workload": f"all-ones chain, n={n}, q contractions; variance of one repetition / prod ||X_k||_F^2 over "
+                        f"{reps} GPU repetitions; method 1 at m={m1}, method 2 at m = 16q rounded up to a power of two",
+            "rows": rows}
 
 
 # ---------------------------------------------------------------- thousands of uneven networks in one batch
