@@ -283,12 +283,6 @@ class Zeros:
         return n
 
 
-def torch_empty(dtype):
-    import torch
-
-    return torch.empty(0, dtype=dtype)
-
-
 class _NetHolder:
     """Owns the ctypes arrays behind one tnsk_network."""
 
@@ -319,7 +313,7 @@ class _NetHolder:
                 tens[k].order = len(x.shape)
                 tens[k].dims = ctypes.cast(d, ctypes.POINTER(ctypes.c_int64))
                 tens[k].data = None
-                tens[k].dtype = F32 if x.dtype is None else _dtype_code(torch_empty(x.dtype))
+                tens[k].dtype = F32 if x.dtype is None else _dtype_code(x)
                 continue
             if x.numel() > 0 and not x.is_contiguous():
                 raise ValueError(f"tensor {k} must be contiguous (row-major)")
