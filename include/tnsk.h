@@ -147,7 +147,25 @@ tnsk_status tnsk_count_sketch(tnsk_ctx* ctx, uint64_t seed, uint64_t rep, uint64
 tnsk_status tnsk_m1_sketch(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, void* x);
 
 /* Estimate tc(X, E): out = device double[prod of open dims] (1 entry if full);
- * per_rep = device double[R][prod open dims] or NULL. */
+ * per_rep = device double[R][prod open dims] or NULL.
+ * TNSK_ACYCLIC networks are first brought into the form Sec. 4.1 assumes (the
+ * same in tnsk_estimate_batch and tnsk_plan_create):
+ *   WLOG 2: a contraction whose two modes belong to one tensor is summed exactly
+ *           over its diagonal and both modes leave that tensor;
+ *   WLOG 3: the r >= 2 contractions e_1 < ... < e_r (order of `edges`) between
+ *           one pair of tensors become one contraction: in each of the two
+ *           tensors their modes are replaced by a single mode at the place of
+ *           the lowest of them, of size prod_j n_{e_j}, index row-major over
+ *           (i_{e_1}, ..., i_{e_r}) (the paper's example: vec(A) . vec(B)).
+ * Tensors keep their order and count, other modes and contractions their relative
+ * order; the merged contraction stands where e_1 stood, e_1's first endpoint
+ * first. Method 2's hash functions and `root` refer to this rewritten network. A
+ * tensor that needs more than a reshape is written once (FP64 stays FP64, FP32
+ * and BF16 become FP32; diagonal sums in FP64) into a ctx-owned buffer (a
+ * plan's own buffer for tnsk_plan_create), by a kernel the call enqueues before
+ * the method's kernels. A cycle through three or more tensors still returns
+ * TNSK_ERR_CYCLIC; a grouped (rung) tensor that would need the rewrite, or a
+ * merged mode above 2^31 - 1, TNSK_ERR_UNSUPPORTED. */
 tnsk_status tnsk_estimate(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, double* out,
                           double* per_rep);
 
@@ -207,7 +225,8 @@ typedef enum {
     TNSK_K_COMBINE = 8,     /* median of group means (a9) */
     TNSK_K_M2_SCATTER = 9,  /* method 2 count-sketch scatter of the product rows (a7) */
     TNSK_K_PAIRS = 10,      /* exact pair contractions (tnsk_pairs_run) */
-    TNSK_KERNEL_KINDS = 11
+    TNSK_K_NORMALIZE = 11,  /* WLOG 2 / 3 rewrite of acyclic networks (Sec. 4.1) */
+    TNSK_KERNEL_KINDS = 12
 } tnsk_kernel_kind;
 tnsk_status tnsk_profile(tnsk_ctx* ctx, int32_t enable);
 tnsk_status tnsk_profile_read(tnsk_ctx* ctx, double* ms, int64_t* launches);

@@ -11,6 +11,7 @@
 #include "ctx.cuh"
 #include "kernels.cuh"
 #include "method2.cuh"
+#include "normalize.cuh"
 #include "plan.cuh"
 
 using namespace tnsk;
@@ -32,25 +33,30 @@ tnsk_status cuda_fail(tnsk_ctx* ctx, cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
     } while (0)
 
-tnsk_status ensure_scratch(tnsk_ctx* ctx, size_t bytes) {
-    if (bytes <= ctx->scratch_bytes) return TNSK_OK;
-    size_t want = std::max(bytes, ctx->scratch_bytes + ctx->scratch_bytes / 2);
+// Grows a ctx-owned device buffer to at least `bytes` (earlier work on the stream
+// may still read the old one, so it is freed after a stream synchronisation).
+tnsk_status ensure_buffer(tnsk_ctx* ctx, unsigned char*& buf, size_t& have, size_t bytes, const char* what) {
+    if (bytes <= have) return TNSK_OK;
+    size_t want = std::max(bytes, have + have / 2);
     want = (want + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
-    if (ctx->scratch) {
-        // earlier work on the stream may still read the old arena
+    if (buf) {
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
-        cudaFree(ctx->scratch);
-        ctx->scratch = nullptr;
-        ctx->scratch_bytes = 0;
+        cudaFree(buf);
+        buf = nullptr;
+        have = 0;
     }
-    cudaError_t e = cudaMalloc((void**)&ctx->scratch, want);
+    cudaError_t e = cudaMalloc((void**)&buf, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(ctx, TNSK_ERR_OOM, "scratch allocation of " + std::to_string(want) + " bytes failed");
+        return fail(ctx, TNSK_ERR_OOM, std::string(what) + " allocation of " + std::to_string(want) + " bytes failed");
     }
-    ctx->scratch_bytes = want;
+    have = want;
     return TNSK_OK;
+}
+
+tnsk_status ensure_scratch(tnsk_ctx* ctx, size_t bytes) {
+    return ensure_buffer(ctx, ctx->scratch, ctx->scratch_bytes, bytes, "scratch");
 }
 
 tnsk_status ensure_twiddles(tnsk_ctx* ctx) {
@@ -177,6 +183,7 @@ tnsk_status tnsk_destroy(tnsk_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->norm) cudaFree(ctx->norm);
     if (ctx->tw32[0]) cudaFree(ctx->tw32[0]);
     if (ctx->tw64[0]) cudaFree(ctx->tw64[0]);
     if (ctx->d_tw32) cudaFree(ctx->d_tw32);
@@ -267,9 +274,21 @@ static tnsk_status build_plan(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets
 
 // Device part: the launch sequence of a planned batch whose descriptors are
 // already at base + plan.desc_off.
+// The normalisation launch of a batch (WLOG 2 / 3 rewrite of acyclic networks), if any.
+struct NormRun {
+    const NormJob* d_jobs = nullptr;
+    int n = 0;
+    int64_t most = 0;
+};
+
 static tnsk_status launch_plan(tnsk_ctx* ctx, const BatchPlan& plan, unsigned char* base, bool fp64,
-                               void* sketch_out) {
+                               void* sketch_out, const NormRun& nr = NormRun{}) {
     cudaStream_t s = ctx->stream;
+    if (nr.n) {  // the rewritten tensors first: method 2 reads them
+        ctx->prof.begin(TNSK_K_NORMALIZE, s);
+        TNSK_CUDA(launch_normalize(nr.d_jobs, nr.n, nr.most, s));
+        ctx->prof.end(s);
+    }
     if (plan.zero_bytes) TNSK_CUDA(cudaMemsetAsync(base + plan.zero_off, 0, plan.zero_bytes, s));
     if (sketch_out && plan.sketch_user_bytes) TNSK_CUDA(cudaMemsetAsync(sketch_out, 0, plan.sketch_user_bytes, s));
     Profiler& pf = ctx->prof;
@@ -332,9 +351,20 @@ static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets,
     tnsk_status st = check_ctx(ctx);
     if (st != TNSK_OK) return st;
     if (B == 0) return TNSK_OK;
+    // acyclic networks with traces or repeated contractions are rewritten first
+    NormBatch nb;
+    std::string why;
+    st = normalize_batch(B, nets, params, nb, why);
+    if (st != TNSK_OK) return fail(ctx, st, why);
+    if (!nb.jobs.empty()) {
+        st = ensure_buffer(ctx, ctx->norm, ctx->norm_bytes, nb.bytes, "normalisation buffer");
+        if (st != TNSK_OK) return st;
+        normalize_bind(nb, ctx->norm);
+    }
     BatchPlan plan;
     bool fp64 = false;
-    st = build_plan(ctx, B, nets, params, outs, per_reps, sketch_out != nullptr, plan, fp64);
+    st = build_plan(ctx, B, nb.used ? nb.view.data() : nets, params, outs, per_reps, sketch_out != nullptr, plan,
+                    fp64);
     if (st != TNSK_OK) return st;
     st = ensure_scratch(ctx, plan.arena.used);
     if (st != TNSK_OK) return st;
@@ -344,7 +374,13 @@ static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets,
     if (!plan.host_desc.empty())
         TNSK_CUDA(cudaMemcpyAsync(ctx->scratch + plan.desc_off, plan.host_desc.data(), plan.host_desc.size(),
                                   cudaMemcpyHostToDevice, ctx->stream));
-    return launch_plan(ctx, plan, ctx->scratch, fp64, sketch_out);
+    NormRun nr;
+    if (!nb.jobs.empty()) {
+        TNSK_CUDA(cudaMemcpyAsync(ctx->norm + nb.desc_off, nb.jobs.data(), nb.jobs.size() * sizeof(NormJob),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+        nr = NormRun{(const NormJob*)(ctx->norm + nb.desc_off), (int)nb.jobs.size(), nb.most};
+    }
+    return launch_plan(ctx, plan, ctx->scratch, fp64, sketch_out, nr);
 }
 
 struct tnsk_plan {
@@ -352,6 +388,9 @@ struct tnsk_plan {
     bool fp64 = false;
     int device = 0;
     unsigned char* dev = nullptr;  // descriptors + scratch of this plan
+    NormBatch norm;                   // rewritten acyclic networks (WLOG 2 / 3), if any
+    unsigned char* norm_dev = nullptr;  // their tensors and descriptors
+    NormRun nr;
     int64_t runs = 0;
     cudaGraphExec_t graph = nullptr;  // the launch sequence, captured on the second run
     bool no_graph = false;            // capture failed or is not possible: launch directly
@@ -394,29 +433,56 @@ static tnsk_status create_plan(tnsk_ctx* ctx, int32_t B, const tnsk_network* net
     if (st != TNSK_OK) return st;
     tnsk_plan* p = new tnsk_plan();
     p->device = ctx->device;
-    st = build_plan(ctx, B, nets, params, outs, per_reps, false, p->plan, p->fp64, zero_ok);
-    if (st != TNSK_OK) {
+    auto drop = [&]() {
+        cudaFree(p->dev);
+        cudaFree(p->norm_dev);
         delete p;
+    };
+    std::string why;
+    st = normalize_batch(B, nets, params, p->norm, why);
+    if (st != TNSK_OK) {
+        drop();
+        return fail(ctx, st, why);
+    }
+    cudaError_t e = cudaSuccess;
+    if (!p->norm.jobs.empty()) {
+        if (cudaMalloc((void**)&p->norm_dev, p->norm.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p->norm_dev = nullptr;
+            drop();
+            return fail(ctx, TNSK_ERR_OOM, "plan normalisation buffer allocation failed");
+        }
+        normalize_bind(p->norm, p->norm_dev);
+        e = cudaMemcpy(p->norm_dev + p->norm.desc_off, p->norm.jobs.data(), p->norm.jobs.size() * sizeof(NormJob),
+                       cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            drop();
+            return cuda_fail(ctx, e, "cudaMemcpy(normalisation descriptors)");
+        }
+        p->nr = NormRun{(const NormJob*)(p->norm_dev + p->norm.desc_off), (int)p->norm.jobs.size(), p->norm.most};
+    }
+    st = build_plan(ctx, B, p->norm.used ? p->norm.view.data() : nets, params, outs, per_reps, false, p->plan,
+                    p->fp64, zero_ok);
+    if (st != TNSK_OK) {
+        drop();
         return st;
     }
     if (cudaMalloc((void**)&p->dev, std::max<size_t>(p->plan.arena.used, 256)) != cudaSuccess) {
         cudaGetLastError();
-        delete p;
+        p->dev = nullptr;
+        drop();
         return fail(ctx, TNSK_ERR_OOM, "plan scratch allocation failed");
     }
     st = finalize_plan(p->plan, p->dev, ctx->last_error);
     if (st != TNSK_OK) {
-        cudaFree(p->dev);
-        delete p;
+        drop();
         return st;
     }
-    cudaError_t e = cudaSuccess;
     if (!p->plan.host_desc.empty())
         e = cudaMemcpy(p->dev + p->plan.desc_off, p->plan.host_desc.data(), p->plan.host_desc.size(),
                        cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(p->dev);
-        delete p;
+        drop();
         return cuda_fail(ctx, e, "cudaMemcpy(plan descriptors)");
     }
     p->plan.host_desc.clear();
@@ -445,7 +511,7 @@ tnsk_status tnsk_plan_run(tnsk_ctx* ctx, tnsk_plan* plan) {
             cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
             tnsk_status st = TNSK_ERR_CUDA;
             if (e == cudaSuccess) {
-                st = launch_plan(ctx, plan->plan, plan->dev, plan->fp64, nullptr);
+                st = launch_plan(ctx, plan->plan, plan->dev, plan->fp64, nullptr, plan->nr);
                 e = cudaStreamEndCapture(s, &g);
             }
             if (e == cudaSuccess && st == TNSK_OK && g) e = cudaGraphInstantiate(&plan->graph, g, 0);
@@ -463,7 +529,7 @@ tnsk_status tnsk_plan_run(tnsk_ctx* ctx, tnsk_plan* plan) {
             return TNSK_OK;
         }
     }
-    return launch_plan(ctx, plan->plan, plan->dev, plan->fp64, nullptr);
+    return launch_plan(ctx, plan->plan, plan->dev, plan->fp64, nullptr, plan->nr);
 }
 
 tnsk_status tnsk_plan_destroy(tnsk_plan* plan) {
@@ -472,6 +538,7 @@ tnsk_status tnsk_plan_destroy(tnsk_plan* plan) {
     cudaDeviceSynchronize();
     if (plan->graph) cudaGraphExecDestroy(plan->graph);
     cudaFree(plan->dev);
+    cudaFree(plan->norm_dev);
     delete plan;
     return TNSK_OK;
 }

@@ -14,6 +14,9 @@ struct tnsk_ctx {
     // scratch arena, grown on demand, reused by every call (stream ordered)
     unsigned char* scratch = nullptr;
     size_t scratch_bytes = 0;
+    // tensors rewritten for the acyclic method (WLOG 2 / 3), grown on demand, stream ordered
+    unsigned char* norm = nullptr;
+    size_t norm_bytes = 0;
     // twiddles tw[k] = exp(-2 pi i k/m), k < m/2, for m = 2^l, l = 0..16
     void* tw32[17] = {};
     void* tw64[17] = {};
