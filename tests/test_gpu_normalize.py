@@ -58,8 +58,6 @@ def test_traces_and_merged_contractions(ctx, prec, dtype, root):
     out, per = gpu_estimate(ctx, spec, p, tdt)
     y, s = _oracle_normalized(spec, p, tdt)
     assert_parity(per, y[:, None], s[:, None], TOL[prec], f"wlog mixed {dtype} root={root}")
-    # the rewrite keeps tc: the mean over many reps approaches the exact value
-    assert np.isfinite(out).all()
 
 
 def test_rewrite_at_tile_sizes(ctx):
@@ -120,7 +118,7 @@ def test_rewrite_errors(ctx):
     """A cycle through three tensors stays a cycle after merging (TNSK_ERR_CYCLIC); a
     grouped (rung) tensor that would need a trace is refused (TNSK_ERR_UNSUPPORTED)."""
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
-    A = [np.ones((3, 3, 3)), np.ones((3, 3)), np.ones((3, 3))]
+    A = [np.ones((3, 3, 3)), np.ones((3, 3, 3)), np.ones((3, 3))]  # modes 0-2, 3-5, 6-7
     # A-B twice, B-C, C-A: after the merge a triangle
     spec = W.NetSpec(A, [(0, 3), (1, 4), (5, 6), (7, 2)], [])
     with pytest.raises(tnsk.TnskError) as e:
