@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--no-turnstile", action="store_true")
     ap.add_argument("--no-sparse", action="store_true")
     ap.add_argument("--no-variance-gap", action="store_true")
+    ap.add_argument("--no-prior-bias", action="store_true")
     ap.add_argument("--no-joins", action="store_true")
     ap.add_argument("--grouped", action="store_true",
                     help="inner sites as grouped tensors (tnsk_rung) instead of materialising them every step")
@@ -447,6 +448,7 @@ def run_ours(args, world, rank, local):
     turn = turnstile(ctx, dev, pairs[0][2]) if (rank == 0 and not args.no_turnstile) else None
     sparse = sparse_triangles(ctx, dev) if (rank == 0 and not args.no_sparse) else None
     vgap = variance_gap(ctx, dev) if (rank == 0 and not args.no_variance_gap) else None
+    pbias = prior_bias(ctx, dev) if (rank == 0 and not args.no_prior_bias) else None
     jsz = join_sizes(ctx, dev) if (rank == 0 and not args.no_joins) else None
     for p_ in plans + merges:
         p_.close()
@@ -479,6 +481,7 @@ def run_ours(args, world, rank, local):
         "turnstile": turn,
         "sparse_triangles": sparse,
         "variance_gap": vgap,
+        "prior_bias": pbias,
         "join_sizes": jsz,
         "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
         "gpu_launches": launches,
@@ -756,6 +759,41 @@ def variance_gap(ctx, dev, n: int = 8, qs=(2, 4, 6, 8, 10, 12, 14, 16), m1: int 
     return {"workload": f"all-ones chain, n={n}, q contractions; variance of one repetition / prod ||X_k||_F^2 over "
                         f"{reps} GPU repetitions; method 1 at m={m1}, method 2 at m = 16q rounded up to a power of two",
             "rows": rows}
+
+
+def prior_bias(ctx, dev, n: int = 16, ps=(3, 4, 5), m: int = 64, reps: int = 16384):
+    """Rings of p matrices (U(0,1), n x n; tc = tr(X_1 ... X_p)): the mean of the per-rep
+    estimates over `reps` GPU repetitions, relative to tc (exact, FP64 on the GPU), for
+    method 1 and for the earlier cross-correlation estimator. The chain conjugates every
+    other tensor, so on an odd ring one contraction joins two unconjugated tensors and
+    the cross-correlation mean falls to about 2 tc / m; on an even ring both agree."""
+    import torch
+
+    from paper_2603_07387_gb300 import tnsk
+
+    g = torch.Generator(device="cpu").manual_seed(20260307)
+    rows = []
+    for p in ps:
+        mats = [torch.rand(n, n, generator=g, dtype=torch.float64) for _ in range(p)]
+        prod = mats[0]
+        for x in mats[1:]:
+            prod = prod @ x
+        tc = float(torch.trace(prod))
+        ts = [x.to(device=dev, dtype=torch.float32) for x in mats]
+        edges = [(2 * k + 1, (2 * k + 2) % (2 * p)) for k in range(p)]
+        net = tnsk.Network(ts, edges, [])
+        row = {"p": p, "tc": float(f"{tc:.6g}")}
+        for name, method in (("m1", tnsk.GENERAL), ("crosscorr", tnsk.CROSSCORR)):
+            out = torch.zeros(1, dtype=torch.float64, device=dev)
+            per = torch.zeros((reps, 1), dtype=torch.float64, device=dev)
+            ctx.estimate(net, tnsk.Params(m=m, reps=reps, seed=0xB1A5, method=method), out, per)
+            ctx.sync()
+            y = per.cpu().numpy()[:, 0]
+            row[name + "_mean_over_tc"] = round(float(np.mean(y)) / tc, 4)
+            row[name + "_stderr_over_tc"] = float(f"{np.std(y, ddof=1) / np.sqrt(reps) / tc:.3g}")
+        rows.append(row)
+    return {"workload": f"rings of p U(0,1) {n}x{n} matrices, m={m}, {reps} GPU repetitions each; "
+                        f"2/m = {2 / m:.4g}", "rows": rows}
 
 
 # ---------------------------------------------------------------- thousands of uneven networks in one batch

@@ -55,7 +55,19 @@ typedef enum {
 } tnsk_status;
 
 typedef enum { TNSK_F64 = 0, TNSK_F32 = 1, TNSK_BF16 = 2 } tnsk_dtype;
-typedef enum { TNSK_GENERAL = 1, TNSK_ACYCLIC = 2 } tnsk_method;
+/* TNSK_CROSSCORR: the earlier estimator Sec. 4.2 contrasts with method 1 (its two
+ * examples), kept for comparison: every contraction gets one plain count sketch,
+ * every tensor its tensor sketch, and the sketches are combined by the circular
+ * cross-correlation x_1 * x_2 * ... * x_p taken left to right, whose first
+ * component is the estimate. In the Fourier domain the chain conjugates tensor k's
+ * spectrum when p - 1 - k is odd, which the library computes as method 1 with the
+ * complement count sketch on every contracted mode of those tensors (and the plain
+ * one on all others), edge tables as method 1's. Unbiased when every contraction
+ * joins a conjugated and an unconjugated tensor (e.g. a chain); otherwise biased
+ * (on the triangle tr(XYZ) the expectation is about 2 tc / m). Same limits, layout
+ * and calls as TNSK_GENERAL (tnsk_estimate, batches, plans, tnsk_m1_sketch,
+ * streams); tnsk_choose_params and tnsk_estimate_static refuse it. */
+typedef enum { TNSK_GENERAL = 1, TNSK_ACYCLIC = 2, TNSK_CROSSCORR = 3 } tnsk_method;
 /* Arithmetic of the sketches and transforms. FP32: sketches, FFTs and products in
  * FP32 (per-tensor power-of-two scaling), per-rep estimates and combination in
  * FP64. FP64: everything in FP64 (for high-dynamic-range sketches). */

@@ -21,9 +21,12 @@ import numpy as np
 from . import count_sketch, tid
 
 
-def _sketch(x, k, off, edges, tabs, m):
-    """Plain tensor sketch of tensor k: [O_k, m] (open index row-major in mode order)."""
+def _sketch(x, k, off, edges, tabs, m, abs_mode=False):
+    """Plain tensor sketch of tensor k: [O_k, m] (open index row-major in mode order);
+    abs_mode: |X| with every sign +1 (the magnitudes the estimate is built from)."""
     x = np.asarray(x, dtype=np.float64)
+    if abs_mode:
+        x = np.abs(x)
     q = x.ndim
     edge_of = {}
     for e, (u, v) in enumerate(edges):
@@ -39,7 +42,7 @@ def _sketch(x, k, off, edges, tabs, m):
             if g in edge_of:
                 bins, signs = tabs[edge_of[g]]
                 b += int(bins[idx[d]])
-                s *= int(signs[idx[d]])
+                s *= 1 if abs_mode else int(signs[idx[d]])
             else:
                 o = o * x.shape[d] + idx[d]
         out[o, b % m] += s * float(x[idx])
@@ -51,9 +54,11 @@ def _xcorr(a, b):
     return np.array([sum(a[j] * b[(j + k) % m] for j in range(m)) for k in range(m)])
 
 
-def estimate(tensors, edges, open_modes, m: int, reps: int, seed: int):
+def estimate(tensors, edges, open_modes, m: int, reps: int, seed: int, abs_mode: bool = False):
     """Per-rep estimates y[R, O] of the cross-correlation estimator (O = product of
-    the open dims in open_modes order; 1 for a full network)."""
+    the open dims in open_modes order; 1 for a full network). abs_mode: the same
+    chain on magnitude sketches, a bound on the sum of the magnitudes of the terms
+    (the scale of a rounding-error tolerance)."""
     off = [0]
     for x in tensors:
         off.append(off[-1] + np.ndim(x))
@@ -62,7 +67,7 @@ def estimate(tensors, edges, open_modes, m: int, reps: int, seed: int):
     y = np.zeros((reps, O))
     for r in range(reps):
         tabs = [count_sketch(seed, r, tid(1, e), dims[u], m) for e, (u, v) in enumerate(edges)]
-        sk = [_sketch(x, k, off, edges, tabs, m) for k, x in enumerate(tensors)]
+        sk = [_sketch(x, k, off, edges, tabs, m, abs_mode) for k, x in enumerate(tensors)]
         for o, oidx in enumerate(np.ndindex(*[dims[g] for g in open_modes]) if open_modes else [()]):
             # each tensor's open index from the output multi-index, row-major in its mode order
             at = dict(zip(open_modes, oidx))

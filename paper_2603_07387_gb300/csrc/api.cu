@@ -559,8 +559,9 @@ tnsk_status tnsk_stream_create(tnsk_ctx* ctx, const tnsk_network* net, const tns
     tnsk_status st = check_ctx(ctx);
     if (st != TNSK_OK) return st;
     if (!net || !params || !out) return fail(ctx, TNSK_ERR_INVALID, "stream: NULL argument");
-    if (params->method != TNSK_GENERAL)
-        return fail(ctx, TNSK_ERR_UNSUPPORTED, "stream: turnstile updates are method 1 (TNSK_GENERAL) only");
+    if (!is_m1(params->method))
+        return fail(ctx, TNSK_ERR_UNSUPPORTED,
+                    "stream: turnstile updates need stored sketches (TNSK_GENERAL or TNSK_CROSSCORR)");
     double* const outs[1] = {out};
     double* const pers[1] = {per_rep};
     tnsk_plan* p = nullptr;
@@ -675,7 +676,8 @@ tnsk_status tnsk_estimate_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* ne
 
 tnsk_status tnsk_m1_sketch(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, void* x) {
     if (!ctx || !net || !params) return TNSK_ERR_INVALID;
-    if (params->method != TNSK_GENERAL) return fail(ctx, TNSK_ERR_INVALID, "m1_sketch needs TNSK_GENERAL");
+    if (!is_m1(params->method))
+        return fail(ctx, TNSK_ERR_INVALID, "m1_sketch needs TNSK_GENERAL or TNSK_CROSSCORR");
     if (!x) return fail(ctx, TNSK_ERR_INVALID, "null sketch buffer");
     return run_batch(ctx, 1, net, params, nullptr, nullptr, x);
 }

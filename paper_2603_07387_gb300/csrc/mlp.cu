@@ -631,6 +631,9 @@ tnsk_status tnsk_choose_params(tnsk_ctx* ctx, const tnsk_network* net, double ta
     if (!net || !inout || !(target_err > 0.0)) return ctx_fail(ctx, TNSK_ERR_INVALID, "choose_params: arguments");
     constexpr int kLo = 6, kHi = 16;  // candidate m = 2^6 .. 2^16
     const double R = std::max(inout->reps, 1);
+    if (inout->method == TNSK_CROSSCORR)
+        return ctx_fail(ctx, TNSK_ERR_UNSUPPORTED,
+                        "choose_params: the cross-correlation estimator has no variance bound (biased on cycles)");
     if (!mlp || inout->method != TNSK_GENERAL) {
         // the variance bound with delta = 0.1: m R >= 3^t / (eps^2 delta) (general), 32 t / (eps^2 delta) (acyclic)
         NetInfo I;

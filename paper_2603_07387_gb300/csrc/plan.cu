@@ -117,7 +117,7 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
         why = "unknown precision";
         return TNSK_ERR_INVALID;
     }
-    if (prm.method != TNSK_GENERAL && prm.method != TNSK_ACYCLIC) {
+    if (prm.method != TNSK_GENERAL && prm.method != TNSK_ACYCLIC && prm.method != TNSK_CROSSCORR) {
         why = "unknown method";
         return TNSK_ERR_INVALID;
     }
@@ -126,8 +126,8 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
         return TNSK_ERR_UNSUPPORTED;
     }
     I.log2m = ilog2(prm.m);
-    if (I.log2m > (prm.method == TNSK_GENERAL ? kMaxLog2mLarge : max_log2m_for(fp64))) {
-        why = prm.method == TNSK_GENERAL ? "sketch size m above 2^16"
+    if (I.log2m > (is_m1(prm.method) ? kMaxLog2mLarge : max_log2m_for(fp64))) {
+        why = is_m1(prm.method) ? "sketch size m above 2^16"
                                          : "method 2: sketch size m above the single-CTA FFT limit (2^14 FP32, 2^13 FP64)";
         return TNSK_ERR_UNSUPPORTED;
     }
@@ -284,7 +284,7 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
         I.open_tot[k] = o;
         if (o > 1) ++n_ot;
     }
-    if (prm.method == TNSK_GENERAL) {
+    if (is_m1(prm.method)) {
         if (n_ot > TNSK_MAX_OPEN_TENSORS) {
             why = "open legs on more than 4 tensors";
             return TNSK_ERR_UNSUPPORTED;
@@ -409,7 +409,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
         const int64_t m = pr.m;
         const uint32_t mask = (uint32_t)(m - 1);
         const int R = pr.reps;
-        if (pr.method == TNSK_GENERAL) {
+        if (is_m1(pr.method)) {
             M1Net nb{};
             nb.m = m;
             nb.log2m = I.log2m;
@@ -455,7 +455,9 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                     T.dims[d] = (int32_t)I.dims[g];
                     if (I.edge_of[g] >= 0) {
                         T.tab[d] = (int32_t)I.eoff[I.edge_of[g]];
-                        T.comp[d] = I.side_of[g];
+                        // method 1: the second mode of each contraction takes C'; the
+                        // cross-correlation chain: every mode of a conjugated tensor
+                        T.comp[d] = pr.method == TNSK_CROSSCORR ? ((I.p - 1 - k) & 1) : I.side_of[g];
                         T.ostride[d] = 0;
                         T.n_ctr++;
                     } else {

@@ -9,6 +9,10 @@
 
 namespace tnsk {
 
+// Methods that run on the method-1 kernels: method 1 and the cross-correlation
+// estimator (the same sketches with another choice of complemented modes).
+inline bool is_m1(int method) { return method == TNSK_GENERAL || method == TNSK_CROSSCORR; }
+
 // A validated network (Def. "Tensor contraction", Def. "TNC"), 0-based modes.
 struct NetInfo {
     int p = 0, q = 0, t = 0;
