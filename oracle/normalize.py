@@ -1,5 +1,9 @@
-"""WLOG 2 and WLOG 3 of Sec. 4.1 in FP64 numpy (test infrastructure only: the
+"""WLOG 1, WLOG 2 and WLOG 3 of Sec. 4.1 in FP64 numpy (test infrastructure only: the
 tests, the smoke check and the benchmark's CPU-baseline leg are the only callers).
+
+``copy_tensors`` (WLOG 1) replaces each class of three or more modes that
+contractions force equal (a mode in several contractions) by a diagonal copy tensor
+joined to every member; it is the form the general method takes such networks in.
 
 The acyclic method (Sec. 4.4) assumes that every contraction joins two different
 tensors and that at most one contraction joins any two tensors. A network that
@@ -26,6 +30,52 @@ from __future__ import annotations
 import string
 
 import numpy as np
+
+
+def copy_tensors(tensors, edges, open_modes=()):
+    """WLOG 1 of Sec. 4.1: a mode in several contractions gets virtual copies. The modes
+    linked by contractions fall into classes whose indices must all agree; a class of
+    three or more modes becomes a diagonal copy tensor delta(i, ..., i) of order d
+    (one mode per class member) joined to each member. Returns (tensors', edges',
+    open') with: the original tensors, then one copy tensor per such class (classes
+    ordered by their lowest mode id); first the contractions of two-mode classes in
+    their original order (a repeated pair kept once), then per copy tensor the
+    contractions (g_j, c_j) for the class's modes g_1 < ... < g_d and the copy
+    tensor's modes c_j in order. Mode ids of the original tensors do not change."""
+    tensors = [np.asarray(x, dtype=np.float64) for x in tensors]
+    dims = [d for x in tensors for d in x.shape]
+    q = len(dims)
+    parent = list(range(q))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    for u, v in edges:
+        parent[find(u)] = find(v)
+    members = {}
+    for u, v in edges:
+        for g in (u, v):
+            members.setdefault(find(g), set()).add(g)
+    out_t, out_e, seen = list(tensors), [], set()
+    for u, v in edges:
+        cl = members[find(u)]
+        if len(cl) == 2 and frozenset(cl) not in seen:
+            seen.add(frozenset(cl))
+            out_e.append((u, v))
+    nxt = q
+    for cl in sorted((sorted(c) for c in members.values() if len(c) >= 3), key=lambda c: c[0]):
+        d, n = len(cl), dims[cl[0]]
+        delta = np.zeros((n,) * d)
+        for i in range(n):
+            delta[(i,) * d] = 1.0
+        out_t.append(delta)
+        for j, g in enumerate(cl):
+            out_e.append((g, nxt + j))
+        nxt += d
+    return out_t, out_e, list(open_modes)
 
 
 def needs_normalize(tensors, edges) -> bool:

@@ -103,3 +103,44 @@ def test_needs_normalize():
     assert not needs_normalize([A, B, C], [(1, 2), (3, 4)])
     assert needs_normalize([A, B, C], [(0, 1)])                 # trace
     assert needs_normalize([A, B, C], [(0, 2), (1, 3)])         # double contraction
+
+
+def test_wlog1_paper_example_and_copy_tensor_layout():
+    """a, b, c vectors with b's mode in two contractions: sum_i a(i) b(i) c(i); the
+    rewrite appends one order-3 copy tensor joined to modes 0, 1, 2 in order."""
+    from oracle.normalize import copy_tensors
+    rng = np.random.default_rng(8)
+    a, b, c = (rng.standard_normal(5) for _ in range(3))
+    T, E, O = copy_tensors([a, b, c], [(0, 1), (1, 2)])
+    assert len(T) == 4 and T[3].shape == (5, 5, 5) and E == [(0, 3), (1, 4), (2, 5)] and O == []
+    assert T[3].sum() == 5 and all(T[3][i, i, i] == 1 for i in range(5))
+    assert np.isclose(oracle.tc_definition(T, E, []), np.sum(a * b * c))
+    assert np.isclose(oracle.tc_definition([a, b, c], [(0, 1), (1, 2)], []), np.sum(a * b * c))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_wlog1_random_hyperedges_keep_tc(seed):
+    """Random networks where modes join two or three contractions (classes of 3-4 modes,
+    repeated pairs, two-mode classes mixed in, open modes): tc (brute-force definition,
+    which reads every bracket) is unchanged and no mode is left in two contractions."""
+    from oracle.normalize import copy_tensors
+    rng = np.random.default_rng(300 + seed)
+    shapes = [(2, 3), (3, 2), (3,), (2, 2)]
+    tensors = [rng.standard_normal(s) for s in shapes]  # modes 0,1 | 2,3 | 4 | 5,6
+    dims = [2, 3, 3, 2, 3, 2, 2]
+    classes = [[1, 2, 4], [0, 3, 5]] if seed % 2 else [[1, 2, 4], [0, 5]]
+    edges = []
+    for cl in classes:
+        order = list(rng.permutation(cl))
+        edges += [(int(order[i]), int(order[i + 1])) for i in range(len(order) - 1)]
+        if len(cl) >= 3 and seed % 3 == 0:
+            edges.append((int(order[-1]), int(order[0])))  # a redundant cycle of brackets
+    if seed % 2 == 0:
+        edges.append(edges[-1])  # a repeated pair
+    assert all(dims[u] == dims[v] for u, v in edges)
+    open_modes = [g for g in range(7) if all(g not in e for e in edges)]
+    T, E, O = copy_tensors(tensors, edges, open_modes)
+    used = [g for e in E for g in e]
+    assert len(used) == len(set(used))
+    want = oracle.tc_definition(tensors, edges, open_modes)
+    assert np.allclose(oracle.tc_definition(T, E, O), want)
