@@ -160,6 +160,19 @@ tnsk_status tnsk_m1_sketch(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_pa
 
 /* Estimate tc(X, E): out = device double[prod of open dims] (1 entry if full);
  * per_rep = device double[R][prod open dims] or NULL.
+ * TNSK_GENERAL and TNSK_CROSSCORR networks may have hyperedges (a mode in two or
+ * more contractions); the library applies WLOG 1 of Sec. 4.1 (the same in batches,
+ * plans, streams and tnsk_m1_sketch): the modes that contractions force equal form
+ * classes, and a class of three or more modes g_1 < ... < g_d becomes a diagonal
+ * copy tensor delta(i, ..., i) of order d (dims n) joined to each g_j. The network
+ * planned is: the caller's tensors, then one copy tensor per such class (classes by
+ * lowest mode id); contractions: those of the two-mode classes in the caller's order
+ * (a repeated pair kept once), then (g_j, c_j), j = 1..d, per copy tensor (c_j its
+ * j-th mode). Hash tables follow that contraction list; the copy tensors are never
+ * stored (their n nonzeros are sketched directly) and tnsk_m1_sketch writes their
+ * sketches after the caller's tensors. At most TNSK_MAX_ORDER modes per class
+ * (TNSK_ERR_UNSUPPORTED beyond); TNSK_ACYCLIC refuses hyperedges
+ * (TNSK_ERR_UNSUPPORTED).
  * TNSK_ACYCLIC networks are first brought into the form Sec. 4.1 assumes (the
  * same in tnsk_estimate_batch and tnsk_plan_create):
  *   WLOG 2: a contraction whose two modes belong to one tensor is summed exactly
@@ -227,7 +240,7 @@ tnsk_status tnsk_stream_destroy(tnsk_stream* stream);
  * clears the records. Timing adds no synchronisation to the launch sequence. */
 typedef enum {
     TNSK_K_TABLES = 0,      /* hash tables of all reps (a1) */
-    TNSK_K_M1_SCATTER = 1,  /* method 1 signed scatter-add (a2) */
+    TNSK_K_M1_SCATTER = 1,  /* method 1 signed scatter-add (a2), copy tensors included */
     TNSK_K_M1_SPECTRUM = 2, /* method 1 FFT, Hadamard product, bin sum (a3, a4) */
     TNSK_K_M2_LEAF = 3,     /* method 2 leaf count sketches (a5) */
     TNSK_K_M2_COMPOSE = 4,  /* method 2 Q_k composition (a6) */

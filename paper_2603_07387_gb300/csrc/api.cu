@@ -255,12 +255,13 @@ tnsk_status tnsk_count_sketch(tnsk_ctx* ctx, uint64_t seed, uint64_t rep, uint64
 // Host part of a batch: validation and layout of descriptors and scratch.
 static tnsk_status build_plan(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
                               double* const* outs, double* const* per_reps, bool sketch_only, BatchPlan& plan,
-                              bool& fp64, bool zero_ok = false) {
+                              bool& fp64, bool zero_ok = false, const NormBatch* nb = nullptr) {
     if (B < 0 || (B > 0 && (!nets || !params))) return fail(ctx, TNSK_ERR_INVALID, "null batch arguments");
     std::vector<NetInfo> infos(B);
     for (int b = 0; b < B; ++b) {
         std::string why;
-        tnsk_status st = validate(nets[b], params[b], infos[b], why, zero_ok);
+        const char* diag = nb && !nb->diag.empty() && !nb->diag[b].empty() ? nb->diag[b].data() : nullptr;
+        tnsk_status st = validate(nets[b], params[b], infos[b], why, zero_ok, diag);
         if (st != TNSK_OK) return fail(ctx, st, "network " + std::to_string(b) + ": " + why);
         if (!sketch_only && (!outs || !outs[b])) return fail(ctx, TNSK_ERR_INVALID, "null output buffer");
     }
@@ -314,6 +315,7 @@ static tnsk_status launch_plan(tnsk_ctx* ctx, const BatchPlan& plan, unsigned ch
         void* xs = sketch_out ? sketch_out : (void*)(base + plan.m1.xs_off);
         pf.begin(TNSK_K_M1_SCATTER, s1);
         cudaError_t e = launch_m1_scatters(plan, base, xs, fp64, s1);
+        if (e == cudaSuccess) e = launch_m1_diag(plan, base, xs, fp64, s1);  // WLOG 1 copy tensors
         pf.end(s1);
         if (e == cudaSuccess && !sketch_out) {
             pf.begin(TNSK_K_M1_SPECTRUM, s1);
@@ -364,7 +366,7 @@ static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets,
     BatchPlan plan;
     bool fp64 = false;
     st = build_plan(ctx, B, nb.used ? nb.view.data() : nets, params, outs, per_reps, sketch_out != nullptr, plan,
-                    fp64);
+                    fp64, false, &nb);
     if (st != TNSK_OK) return st;
     st = ensure_scratch(ctx, plan.arena.used);
     if (st != TNSK_OK) return st;
@@ -462,7 +464,7 @@ static tnsk_status create_plan(tnsk_ctx* ctx, int32_t B, const tnsk_network* net
         p->nr = NormRun{(const NormJob*)(p->norm_dev + p->norm.desc_off), (int)p->norm.jobs.size(), p->norm.most};
     }
     st = build_plan(ctx, B, p->norm.used ? p->norm.view.data() : nets, params, outs, per_reps, false, p->plan,
-                    p->fp64, zero_ok);
+                    p->fp64, zero_ok, &p->norm);
     if (st != TNSK_OK) {
         drop();
         return st;

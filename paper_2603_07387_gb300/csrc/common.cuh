@@ -144,6 +144,14 @@ struct M1Tensor {
 
 #define TNSK_MAX_OPEN_TENSORS 4
 
+// A diagonal copy tensor delta(i, ..., i) of WLOG 1 (Sec. 4.1), never stored: its n
+// nonzeros are sketched directly (every mode contracted, all at index i).
+struct M1Diag {
+    int32_t tensor;  // index into the method-1 tensor descriptors
+    int32_t net;     // index into the method-1 network descriptors
+    int64_t n;
+};
+
 struct M1Net {
     int64_t m;
     int64_t L;        // table words per rep

@@ -1,11 +1,13 @@
-// normalize.cu -- the WLOG 2 / WLOG 3 rewrite of Sec. 4.1 for the acyclic method
-// (host bookkeeping and the one kernel that writes the rewritten tensors).
+// normalize.cu -- the WLOG rewrites of Sec. 4.1: copy tensors for hyperedges (WLOG 1,
+// method-1 kernels) and the WLOG 2 / WLOG 3 rewrite for the acyclic method (host
+// bookkeeping and the one kernel that writes the rewritten tensors).
 #include <algorithm>
 #include <limits>
 #include <map>
 #include <utility>
 
 #include "normalize.cuh"
+#include "plan.cuh"
 
 namespace tnsk {
 
@@ -99,6 +101,82 @@ bool needs_rewrite(const tnsk_network& N, std::vector<int>& owner, std::vector<i
     return need;
 }
 
+// WLOG 1: copy tensors for the classes of three or more modes. Leaves `nn` and
+// `diag` empty when the network needs none or fails the basic checks.
+tnsk_status copy_tensors(const tnsk_network& N, int b, NormNet& nn, std::vector<char>& diag, std::string& why) {
+    if (N.p < 1 || !N.X || N.t < 0 || (N.t > 0 && !N.edges)) return TNSK_OK;
+    std::vector<int64_t> dimg;
+    for (int k = 0; k < N.p; ++k) {
+        const tnsk_tensor& X = N.X[k];
+        if (X.order < 0 || X.order > TNSK_MAX_ORDER || (X.order > 0 && !X.dims)) return TNSK_OK;
+        for (int d = 0; d < X.order; ++d) dimg.push_back(X.dims[d]);
+    }
+    const int q = (int)dimg.size();
+    std::vector<int> uses(q, 0), parent(q);
+    for (int g = 0; g < q; ++g) parent[g] = g;
+    auto find = [&](int a) {
+        while (parent[a] != a) a = parent[a] = parent[parent[a]];
+        return a;
+    };
+    bool hyper = false;
+    for (int e = 0; e < N.t; ++e) {
+        const int u = N.edges[2 * e], v = N.edges[2 * e + 1];
+        if (u < 0 || v < 0 || u >= q || v >= q || u == v || dimg[u] != dimg[v]) return TNSK_OK;
+        hyper |= ++uses[u] > 1;
+        hyper |= ++uses[v] > 1;
+        parent[find(u)] = find(v);
+    }
+    if (!hyper) return TNSK_OK;
+    std::map<int, std::vector<int>> members;  // class root -> its modes, ascending
+    for (int g = 0; g < q; ++g)
+        if (uses[g]) members[find(g)].push_back(g);
+    nn.X.assign(N.X, N.X + N.p);
+    nn.dims.assign(N.p, {});
+    for (int e = 0; e < N.t; ++e) {  // two-mode classes: their first pair
+        const int u = N.edges[2 * e], v = N.edges[2 * e + 1];
+        std::vector<int>& cl = members[find(u)];
+        if (cl.size() == 2 && cl[0] >= 0) {
+            nn.edges.push_back(u);
+            nn.edges.push_back(v);
+            cl[0] = -1;  // taken
+        }
+    }
+    std::vector<std::vector<int>> copies;
+    for (auto& kv : members)
+        if (kv.second.size() >= 3) copies.push_back(kv.second);
+    std::sort(copies.begin(), copies.end(), [](const std::vector<int>& a, const std::vector<int>& c) {
+        return a[0] < c[0];
+    });
+    int next = q;
+    for (const std::vector<int>& cl : copies) {
+        if ((int)cl.size() > TNSK_MAX_ORDER) {
+            why = "network " + std::to_string(b) + ": a hyperedge joins " + std::to_string(cl.size()) +
+                  " modes (its WLOG 1 copy tensor would exceed order 12)";
+            return TNSK_ERR_UNSUPPORTED;
+        }
+        nn.dims.push_back(std::vector<int64_t>(cl.size(), dimg[cl[0]]));
+        tnsk_tensor c{};
+        c.order = (int32_t)cl.size();
+        c.dtype = TNSK_F32;
+        nn.X.push_back(c);
+        for (size_t j = 0; j < cl.size(); ++j) {
+            nn.edges.push_back(cl[j]);
+            nn.edges.push_back(next + (int)j);
+        }
+        next += (int)cl.size();
+    }
+    for (size_t k = (size_t)N.p; k < nn.X.size(); ++k) nn.X[k].dims = nn.dims[k].data();
+    nn.job.assign(nn.X.size(), -1);
+    diag.assign(nn.X.size(), 0);
+    for (size_t k = (size_t)N.p; k < nn.X.size(); ++k) diag[k] = 1;
+    nn.net = N;
+    nn.net.p = (int32_t)nn.X.size();
+    nn.net.X = nn.X.data();
+    nn.net.t = (int32_t)(nn.edges.size() / 2);
+    nn.net.edges = nn.edges.empty() ? nullptr : nn.edges.data();
+    return TNSK_OK;
+}
+
 }  // namespace
 
 tnsk_status normalize_batch(int B, const tnsk_network* nets, const tnsk_params* params, NormBatch& nb,
@@ -106,12 +184,22 @@ tnsk_status normalize_batch(int B, const tnsk_network* nets, const tnsk_params* 
     nb = NormBatch{};
     if (B <= 0 || !nets || !params) return TNSK_OK;
     nb.nets.resize(B);
+    nb.diag.resize(B);
     nb.view.assign(nets, nets + B);
     size_t off = 0;
     std::vector<int> owner, moff;
     std::vector<int64_t> dimg;
     for (int b = 0; b < B; ++b) {
         const tnsk_network& N = nets[b];
+        if (is_m1(params[b].method)) {
+            tnsk_status st = copy_tensors(N, b, nb.nets[b], nb.diag[b], why);
+            if (st != TNSK_OK) return st;
+            if (!nb.diag[b].empty()) {
+                nb.view[b] = nb.nets[b].net;
+                nb.used = true;
+            }
+            continue;
+        }
         if (params[b].method != TNSK_ACYCLIC || !needs_rewrite(N, owner, dimg, moff)) continue;
         const int p = N.p, q = moff[p], t = N.t;
         // WLOG 3 groups: the first edge of each pair of tensors joined more than once

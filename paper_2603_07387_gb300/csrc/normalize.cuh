@@ -1,4 +1,12 @@
-// normalize.cuh -- WLOG 2 and WLOG 3 of Sec. 4.1 for the acyclic method.
+// normalize.cuh -- the WLOG rewrites of Sec. 4.1 done by the library.
+//
+// WLOG 1 (TNSK_GENERAL, TNSK_CROSSCORR): the modes that contractions force equal
+// fall into classes; a class of three or more modes (some mode in two or more
+// contractions) becomes a diagonal copy tensor delta(i, ..., i) of order d joined to
+// each member g_1 < ... < g_d. Copy tensors are appended after the p tensors (classes
+// by lowest mode id); the contractions are those of the two-mode classes in their
+// order (a repeated pair once), then (g_j, c_j) per copy tensor. Copy tensors are not
+// stored: their n nonzeros are sketched directly (m1_diag_kernel).
 //
 // Method 2 (Sec. 4.4) needs every contraction to join two different tensors and
 // at most one contraction between any two tensors. A TNSK_ACYCLIC network that
@@ -47,6 +55,7 @@ struct NormBatch {
     bool used = false;                // some network was rewritten
     std::vector<NormNet> nets;        // per batch network (empty net.X: not rewritten)
     std::vector<tnsk_network> view;   // the networks to plan: rewritten or the caller's
+    std::vector<std::vector<char>> diag;  // per network: [p'] 1 = WLOG 1 copy tensor (empty: none)
     std::vector<NormJob> jobs;        // host descriptors (dst set by normalize_bind)
     std::vector<size_t> dst_off;      // per job: its output's offset in the buffer
     size_t desc_off = 0;              // descriptors after the outputs
@@ -54,9 +63,11 @@ struct NormBatch {
     int64_t most = 0;                 // largest job output
 };
 
-// Host: rewrites the TNSK_ACYCLIC networks that need it. Networks that fail the
+// Host: rewrites the TNSK_ACYCLIC networks that need WLOG 2 / 3 and the method-1
+// networks (TNSK_GENERAL, TNSK_CROSSCORR) that need WLOG 1. Networks that fail the
 // basic checks of tnsk_estimate are left as they are (planning reports them).
-// TNSK_ERR_UNSUPPORTED when a grouped (rung) tensor would have to be rewritten.
+// TNSK_ERR_UNSUPPORTED when a grouped (rung) tensor would have to be rewritten or a
+// copy tensor would have more than TNSK_MAX_ORDER modes.
 tnsk_status normalize_batch(int B, const tnsk_network* nets, const tnsk_params* params, NormBatch& nb,
                             std::string& why);
 // Points the rewritten tensors and the jobs' outputs into base (>= nb.bytes, 256-byte aligned).

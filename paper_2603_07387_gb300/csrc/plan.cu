@@ -107,7 +107,8 @@ tnsk_status finalize_plan(BatchPlan& P, unsigned char* base, std::string& err) {
     return TNSK_OK;
 }
 
-tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I, std::string& why, bool zero_ok) {
+tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I, std::string& why, bool zero_ok,
+                     const char* diag) {
     if (net.p < 1 || !net.X) {
         why = "need p >= 1 tensors";
         return TNSK_ERR_INVALID;
@@ -172,6 +173,8 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
     I.idx32 = true;
     for (int k = 0; k < I.p; ++k) {
         const tnsk_tensor& X = net.X[k];
+        const bool is_diag = diag && diag[k];  // never stored: only its n nonzeros are read
+        const int64_t max_numel = is_diag ? ((int64_t)1 << 62) : kMaxNumel;
         int64_t n = 1;
         for (int d = 0; d < X.order; ++d) {
             int64_t v = X.dims[d];
@@ -188,7 +191,7 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
             if (v == 0)
                 n = 0;
             else if (n > 0) {
-                if (n > kMaxNumel / v) {
+                if (n > max_numel / v) {
                     why = "tensor above 2^40 entries";
                     return TNSK_ERR_UNSUPPORTED;
                 }
@@ -197,6 +200,7 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
         }
         I.numel[k] = n;
         I.rung.push_back(X.rung);
+        I.diag.push_back(is_diag ? 1 : 0);
         if (X.rung) {
             I.zero.push_back(0);  // grouped tensor (Sec. 4.1): R((i,j),(k,l)) = sum_s A(i,s,k) B(j,s,l)
             const tnsk_rung& g = *X.rung;
@@ -217,12 +221,12 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
             }
             continue;
         }
-        I.zero.push_back(n > 0 && !X.data && zero_ok ? 1 : 0);
-        if (n > 0 && !X.data && !zero_ok) {
+        I.zero.push_back(n > 0 && !X.data && (zero_ok || is_diag) ? 1 : 0);
+        if (n > 0 && !X.data && !zero_ok && !is_diag) {
             why = "null data for a non-empty tensor";
             return TNSK_ERR_INVALID;
         }
-        if (n >= ((int64_t)1 << 32)) I.idx32 = false;
+        if (n >= ((int64_t)1 << 32) && !is_diag) I.idx32 = false;
     }
     I.t = net.t;
     if (I.t < 0 || (I.t > 0 && !net.edges)) {
@@ -244,7 +248,8 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
             return TNSK_ERR_INVALID;
         }
         if (I.edge_of[u] >= 0 || I.edge_of[v] >= 0) {
-            why = "a mode in two contractions (a hyperedge; WLOG 1 copies are not built in)";
+            why = "a mode in two contractions (a hyperedge: WLOG 1 copy tensors are built for TNSK_GENERAL and "
+                  "TNSK_CROSSCORR only)";
             return TNSK_ERR_UNSUPPORTED;
         }
         I.edge_of[u] = e;
@@ -384,6 +389,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     std::vector<M2Net> m2n;
     int64_t tab_words = 0, yrep_n = 0, xs_n = 0, spec_n = 0, sexp_n = 0, lspec_n = 0;
     std::vector<int4> lfft, lprod;  // large-m method 1: (net, rep, sketch), (net, rep, first bin, bins)
+    std::vector<M1Diag> diags;      // diagonal copy tensors (WLOG 1)
     int64_t ws_x = 0, ws_w = 0, ws_r = 0, ws_v = 0;  // method-2 workspace parts (elements)
     const bool tma = tensor_maps_available();
     int max_log2m1 = 0, max_log2m2 = 0;
@@ -508,6 +514,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
             // scatter work: chunks of each tensor x batches of reps
             for (int k = 0; k < I.p; ++k) {
                 const M1Tensor& T = m1t[nb.t0 + k];
+                if (I.diag[k] && T.numel > 0) diags.push_back(M1Diag{nb.t0 + k, (int)m1n.size(), I.dims[I.mode_off[k]]});
                 if (T.numel == 0 || T.O == 0 || I.zero[k]) continue;  // all-zero tensors add nothing
                 int64_t TT = 0;
                 for (int d = 0; d < T.order; ++d)
@@ -969,7 +976,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
         m1items.insert(m1items.end(), m1warp[sl].begin(), m1warp[sl].end());
     }
     size_t o_open = stage(H, opens), o_items = stage(H, m1items), o_comb = stage(H, comb);
-    size_t o_lfft = stage(H, lfft), o_lprod = stage(H, lprod);
+    size_t o_lfft = stage(H, lfft), o_lprod = stage(H, lprod), o_diag = stage(H, diags);
     size_t o_m2nodes = stage(H, m2nodes), o_m2n = stage(H, m2n), o_m2items = stage(H, m2items);
     std::vector<unsigned char> tmap_space(P.m2.tmap_jobs.size() * 128, 0);
     size_t o_tmaps = stage(H, tmap_space);
@@ -984,6 +991,9 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     P.m1.lprod_off = P.desc_off + o_lprod;
     P.m1.n_lfft = (int)lfft.size();
     P.m1.n_lprod = (int)lprod.size();
+    P.m1.diag_off = P.desc_off + o_diag;
+    P.m1.n_diag = (int)diags.size();
+    for (const M1Diag& d : diags) P.m1.diag_most = std::max(P.m1.diag_most, d.n * (int64_t)m1n[d.net].R);
     P.comb_off = P.desc_off + o_comb;
     P.m2.nodes_off = P.desc_off + o_m2nodes;
     P.m2.nets_off = P.desc_off + o_m2n;

@@ -31,6 +31,7 @@ struct NetInfo {
     bool idx32 = true;
     std::vector<const tnsk_rung*> rung;  // [p] grouped tensors (NULL: stored)
     std::vector<char> zero;              // [p] tensor given as all zeros (data NULL, streams only)
+    std::vector<char> diag;              // [p] diagonal copy tensor of WLOG 1 (not stored)
     // method 2: rooted tree (children in mode order, footnote to Gamma(k))
     int root = -1;
     std::vector<int> parent, parent_mode, parent_edge, height;
@@ -63,6 +64,10 @@ struct M1Plan {
     // large-m items (two-pass FFT, then the product over bin blocks) and their spectra
     size_t lfft_off = 0, lprod_off = 0, lspec_off = 0;
     int n_lfft = 0, n_lprod = 0;
+    // diagonal copy tensors (WLOG 1): one item each
+    size_t diag_off = 0;
+    int n_diag = 0;
+    int64_t diag_most = 0;  // largest n * R
 };
 
 struct BatchPlan {
@@ -91,10 +96,13 @@ cudaError_t launch_m1_updates(const BatchPlan& plan, unsigned char* base, int64_
                               const int64_t* index, const double* delta, bool fp64, int* err, cudaStream_t s);
 cudaError_t launch_m1_spectra(const BatchPlan& plan, unsigned char* base, const void* xs, const void* const* tws,
                               bool fp64, cudaStream_t s);
+// Sketches of the plan's diagonal copy tensors (WLOG 1) added into xs (every rep).
+cudaError_t launch_m1_diag(const BatchPlan& plan, unsigned char* base, void* xs, bool fp64, cudaStream_t s);
 
-// zero_ok: a tensor with data NULL is all zeros (turnstile streams fed by updates)
+// zero_ok: a tensor with data NULL is all zeros (turnstile streams fed by updates);
+// diag (NULL or [p]): tensors that are diagonal copy tensors of WLOG 1 (data NULL)
 tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& info, std::string& why,
-                     bool zero_ok = false);
+                     bool zero_ok = false, const char* diag = nullptr);
 // True when the driver's tensor-map encoder is available (streaming tensor-core path).
 bool tensor_maps_available();
 // Encodes the plan's tensor maps into its host descriptor block once the device

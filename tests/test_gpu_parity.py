@@ -587,8 +587,9 @@ def test_errors_are_reported(ctx):
         xy = [torch.ones(3, device="cuda"), torch.ones(4, device="cuda")]
         ctx.estimate(tnsk.Network(xy, [(0, 1)], []), tnsk.Params(m=8, reps=2), out)
     assert e.value.status == -1
-    with pytest.raises(tnsk.TnskError) as e:  # hyperedge: mode 1 in two contractions
-        ctx.estimate(tnsk.Network(net.tensors, [(1, 2), (1, 4), (3, 5)], [0]), tnsk.Params(m=8, reps=2), out)
+    with pytest.raises(tnsk.TnskError) as e:  # hyperedge (mode 1 in two contractions): not for method 2
+        ctx.estimate(tnsk.Network(net.tensors, [(1, 2), (1, 4), (3, 5)], []),
+                     tnsk.Params(m=8, reps=2, method=tnsk.ACYCLIC), out)
     assert e.value.status == -3
     with pytest.raises(tnsk.TnskError) as e:  # groups must divide reps
         ctx.estimate(net, tnsk.Params(m=8, reps=5, groups=2), out)
