@@ -668,8 +668,8 @@ def sparse_triangles(ctx, dev, blocks: int = 256, size: int = 128, p_edge: float
 def join_sizes(ctx, dev, m: int = 1 << 14, reps: int = 64, runs: int = 3):
     """COUNT(*) of the paper's example query R1.1 = R2.2, R3.4 = R2.2, R4.5 = R2.3 on
     synthetic relations (Zipf(1.3) values; join domains 8192 and 4096; 1M, 2M, 1M and
-    0.5M tuples): four frequency tensors and the copy tensor of the three-way class fed
-    to a turnstile stream as 4.5M tuple updates plus 8192 diagonal entries, method 1.
+    0.5M tuples): four frequency tensors fed to a turnstile stream as 4.5M tuple
+    updates, the three-way class a hyperedge (the library's copy tensor, WLOG 1), method 1.
     Estimates/s count the whole estimate (stream planning and table draw, updates,
     transform and combination)."""
     import torch
@@ -711,7 +711,8 @@ def join_sizes(ctx, dev, m: int = 1 << 14, reps: int = 64, runs: int = 3):
             rel.append(abs(float(out.item()) - exact) / exact)
         st.close()
     ms = float(np.median(times))
-    return {"workload": "COUNT(*) of R1.1 = R2.2 = R3.4, R4.5 = R2.3 (three-way class as a copy tensor); Zipf(1.3) "
+    return {"workload": "COUNT(*) of R1.1 = R2.2 = R3.4, R4.5 = R2.3 (three-way class a hyperedge: the library's "
+                        "copy tensor); Zipf(1.3) "
                         "relations of 1M, 2M, 1M, 0.5M tuples, domains 8192 / 4096; method 1 on the sparse input path, "
                         f"m={m}, {reps} reps",
             "estimates_per_s": round(1e3 / ms, 2), "ms_per_estimate": round(ms, 3),

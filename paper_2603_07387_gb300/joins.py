@@ -1,10 +1,11 @@
 """Join-size estimation as tensor network contraction (Sec. 5.1, Corollary
 "multi-join-card-est"): the frequency tensor of each relation over its join columns is
-a tensor of the network, every equi-join class of two columns is a contraction, and a
-class of three or more columns (a hyperedge) becomes a diagonal copy tensor joined to
-each of them (WLOG 1). Frequency and copy tensors are never stored: they start as all
-zeros in a turnstile stream and receive their nonzeros (one +1 per tuple, one 1 per
-diagonal entry) as updates, so sketching costs O(tuples) per repetition.
+a tensor of the network and every equi-join condition is a contraction between two
+of their modes. A join class of three or more columns makes some mode part of two
+contractions (a hyperedge); the library turns such classes into diagonal copy tensors
+itself (WLOG 1). Frequency tensors are never stored: they start as all zeros in a
+turnstile stream and receive one +1 per tuple as an update, so sketching costs
+O(tuples) per repetition.
 
 This module only lays out the network and the update lists (host bookkeeping); the
 sketching, transform, product and combination run in libtnsk's kernels.
@@ -18,18 +19,18 @@ import numpy as np
 
 @dataclass
 class JoinNetwork:
-    shapes: list          # per tensor: its dims (relations' join columns, then copy tensors)
-    edges: list           # contractions, pairs of global mode ids
-    updates: list         # per tensor: int64 flat entry indices of its nonzeros (value 1 each)
+    shapes: list          # per relation: the dims of its joined columns (column order)
+    edges: list           # contractions, pairs of global mode ids (hyperedges allowed)
+    updates: list         # per relation: int64 flat entry indices of its tuples (value 1 each)
     n_relations: int
 
 
 def join_network(relations, equalities, domains=None) -> JoinNetwork:
     """relations: list of int arrays [N_k, c_k] (tuples, values >= 0); equalities: list
-    of ((k1, col1), (k2, col2)) equi-join conditions. Columns that join nothing are
-    summed out (dropped from the frequency tensor). domains: optional {(k, col): size}
-    (else the largest value in the class + 1)."""
-    # union-find over (relation, column)
+    of ((k1, col1), (k2, col2)) equi-join conditions, each one contraction. Columns that
+    join nothing are summed out (dropped from the frequency tensor). domains: optional
+    {(k, col): size} (else the largest value in the class + 1)."""
+    # union-find over (relation, column): a class shares one domain size
     parent = {}
 
     def find(x):
@@ -44,9 +45,8 @@ def join_network(relations, equalities, domains=None) -> JoinNetwork:
     classes = {}
     for x in list(parent):
         classes.setdefault(find(x), []).append(x)
-    classes = [sorted(v) for v in classes.values() if len(v) >= 2]
     size = {}
-    for cl in classes:
+    for cl in classes.values():
         n = 0
         for k, c in cl:
             col = np.asarray(relations[k])[:, c]
@@ -55,38 +55,26 @@ def join_network(relations, equalities, domains=None) -> JoinNetwork:
                 n = max(n, int(domains[(k, c)]))
         for x in cl:
             size[x] = n
-    # tensors: each relation over its joined columns (in column order), then copy tensors
+    # tensors: each relation over its joined columns, in column order
     cols = [sorted(c for (k, c) in size if k == kk) for kk in range(len(relations))]
     shapes = [[size[(k, c)] for c in cols[k]] for k in range(len(relations))]
     off = [0]
     for sh in shapes:
         off.append(off[-1] + len(sh))
     mode = {(k, c): off[k] + cols[k].index(c) for k in range(len(relations)) for c in cols[k]}
-    edges, updates = [], []
+    edges = [(mode[tuple(a)], mode[tuple(b)]) for a, b in equalities]
+    updates = []
     for k, rel in enumerate(relations):
         rel = np.asarray(rel, dtype=np.int64)
         flat = np.zeros(rel.shape[0], dtype=np.int64)
         for c in cols[k]:
             flat = flat * size[(k, c)] + rel[:, c]
         updates.append(flat)
-    next_mode = off[-1]
-    for cl in classes:
-        if len(cl) == 2:
-            edges.append((mode[cl[0]], mode[cl[1]]))
-            continue
-        n, d = size[cl[0]], len(cl)  # copy tensor delta(i, ..., i), order d
-        shapes.append([n] * d)
-        for j, x in enumerate(cl):
-            edges.append((mode[x], next_mode + j))
-        next_mode += d
-        diag = np.arange(n, dtype=np.int64)
-        stride = sum(n ** j for j in range(d))  # flat index of (i, ..., i) = i * (1 + n + ... + n^(d-1))
-        updates.append(diag * stride)
     return JoinNetwork(shapes, edges, updates, len(relations))
 
 
 def exact_dense_tensors(jn: JoinNetwork):
-    """The frequency and copy tensors as dense FP64 arrays (small cases: tests, oracle)."""
+    """The frequency tensors as dense FP64 arrays (small cases: tests, oracle)."""
     out = []
     for sh, flat in zip(jn.shapes, jn.updates):
         t = np.zeros(int(np.prod(sh)) if sh else 1)
