@@ -538,8 +538,9 @@ __global__ void __launch_bounds__(256) m2_root_kernel(const M2Node* __restrict__
 template <typename T>
 static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void* const* d_tws, cudaStream_t s,
                             Profiler& prof, int* d_err) {
-    static const int kKind[M2_NKINDS] = {TNSK_K_M2_LEAF, TNSK_K_M2_COMPOSE, TNSK_K_M2_VBUILD, TNSK_K_M2_GEMM,
-                                         TNSK_K_M2_GEMM, TNSK_K_M2_GEMM,    TNSK_K_M2_SCATTER, TNSK_K_M2_ROOT};
+    static const int kKind[M2_NKINDS] = {TNSK_K_M2_LEAF, TNSK_K_M2_COMPOSE, TNSK_K_M2_VBUILD,
+                                         TNSK_K_M2_GEMM, TNSK_K_M2_GEMM,    TNSK_K_M2_GEMM,
+                                         TNSK_K_M2_GEMM, TNSK_K_M2_SCATTER, TNSK_K_M2_ROOT};
     const M2Node* nodes = (const M2Node*)(base + P.m2.nodes_off);
     const M2Net* nets = (const M2Net*)(base + P.m2.nets_off);
     const M2Item* items = (const M2Item*)(base + P.m2.items_off);
@@ -581,6 +582,12 @@ static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void*
                     if (sizeof(T) == 4)
                         launch_m2_gemm_tc_rung(n, nodes, nets, its, (float*)ws, base + P.m2.tmaps_off, d_err,
                                                P.m2.rung_smem, s);
+                    break;
+                case M2_GEMM_RUNGF:  // FP32 plans only
+                    if (sizeof(T) == 4) {
+                        const cudaError_t e = launch_m2_rung_fact(n, nodes, nets, its, (float*)ws, P.m2.rungf_smem, s);
+                        if (e != cudaSuccess) return e;
+                    }
                     break;
                 case M2_WSCATTER: {
                     const size_t smem = P.m2.scatter_smem;

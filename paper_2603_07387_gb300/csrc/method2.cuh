@@ -107,9 +107,10 @@ enum M2Kind {
     M2_GEMM = 3,
     M2_GEMM_STREAM = 4,
     M2_GEMM_RUNG = 5,
-    M2_WSCATTER = 6,
-    M2_ROOT = 7,
-    M2_NKINDS = 8
+    M2_GEMM_RUNGF = 6,  // grouped tensor in factored form (dims <= 32): it.a first rep, it.b reps
+    M2_WSCATTER = 7,
+    M2_ROOT = 8,
+    M2_NKINDS = 9
 };
 
 struct M2Plan {
@@ -124,6 +125,7 @@ struct M2Plan {
     size_t scatter_smem = 0;  // shared-memory bins of the largest row-scatter item
     size_t vbuild_smem = 0;   // staged T tables + child sketches of the largest staged V-build item
     size_t rung_smem = 0;     // dynamic shared memory of the grouped-tensor GEMM (V ring + B)
+    size_t rungf_smem = 0;    // dynamic shared memory of the factored grouped-tensor product
     // tensor maps to encode once the device addresses are fixed: node, 0 = X / 1 = V^T hi / 2 = lo
     std::vector<std::pair<int, int>> tmap_jobs;
     int max_log2m = 0;
@@ -142,5 +144,10 @@ cudaError_t launch_m2_gemm_tc(int n, const M2Node* nodes, const M2Net* nets, con
 size_t m2_gemm_rung_smem(size_t b_bytes);
 cudaError_t launch_m2_gemm_tc_rung(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items, float* ws,
                                    const unsigned char* tmaps, int* err, size_t smem, cudaStream_t s);
+// Grouped tensors with every factor dim <= 32 (M2_GEMM_RUNGF): the product in factored
+// form, SIMT FP32; smem from m2_rung_fact_smem(s).
+size_t m2_rung_fact_smem(int s);
+cudaError_t launch_m2_rung_fact(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items, float* ws,
+                                size_t smem, cudaStream_t s);
 
 }  // namespace tnsk

@@ -107,6 +107,10 @@ tnsk_status finalize_plan(BatchPlan& P, unsigned char* base, std::string& err) {
     return TNSK_OK;
 }
 
+// A grouped tensor whose four factor dims are at most 32 runs the factored product
+// (m2_rung_fact.cu); larger ones the tensor-core kernel that forms the entries.
+static bool rung_factored(const tnsk_rung& g) { return g.a <= 32 && g.b <= 32 && g.c <= 32 && g.d <= 32 && g.s <= 16; }
+
 tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I, std::string& why, bool zero_ok,
                      const char* diag) {
     if (net.p < 1 || !net.X) {
@@ -744,7 +748,9 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 nd.r_bi = (int32_t)(first ? g.s * g.d : 1);
                 nd.r_bj = (int32_t)(first ? 1 : g.s * g.d);
                 const int64_t b_bytes = (int64_t)nd.rn_i2 * (g.s * nd.rn_j2 + 4) * 4;
-                if (nd.rn_j2 % 32 != 0 || b_bytes > 60 * 1024 || !tma) {
+                if (rung_factored(g)) {
+                    P.m2.rungf_smem = std::max(P.m2.rungf_smem, m2_rung_fact_smem((int)g.s));
+                } else if (nd.rn_j2 % 32 != 0 || b_bytes > 60 * 1024 || !tma) {
                     err = "tensor " + std::to_string(k) +
                           ": rung tensor needs its column fast index a multiple of 32 and the B factor within 60 KiB";
                     return TNSK_ERR_UNSUPPORTED;
@@ -754,8 +760,9 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 const int64_t i1_max = std::min<int64_t>(nd.rn_i1, 127 / nd.rn_i2 + 2);
                 const int64_t a_bytes = i1_max * g.s * nd.rn_j1 * 4;
                 nd.r_astage = a_bytes <= 16 * 1024 ? 1 : 0;
-                P.m2.rung_smem = std::max(P.m2.rung_smem,
-                                          m2_gemm_rung_smem((size_t)(b_bytes + (nd.r_astage ? a_bytes : 0))));
+                if (!rung_factored(g))
+                    P.m2.rung_smem = std::max(P.m2.rung_smem,
+                                              m2_gemm_rung_smem((size_t)(b_bytes + (nd.r_astage ? a_bytes : 0))));
             }
             nd.qt = qt[k];
             P.m2.max_qt = std::max(P.m2.max_qt, nd.qt);
@@ -850,25 +857,30 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 // the split of K (tensor-core kernels) is chosen once all tiles are known
                 const int64_t tile = fp64 ? 64 : 128;
                 const bool rung = I.rung[k] != nullptr;
-                const bool stream = !rung && !fp64 && tma && nd.dtype == TNSK_F32 && nd.A == 1 &&
-                                    (nd.cols % 4) == 0 && ((uintptr_t)nd.data % 16) == 0 &&
-                                    nd.npar < ((int64_t)1 << 31) && nd.cols < ((int64_t)1 << 31);
-                if (rung) {  // V^T hi / lo maps only: X is generated
-                    m2nodes.back().tm_v = (int32_t)P.m2.tmap_jobs.size();
-                    P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 1});
-                    P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 2});
+                if (rung && rung_factored(*I.rung[k])) {  // blocks of 8 reps, no tiles or K split
+                    for (int r0 = 0; r0 < R; r0 += 8)
+                        pend.push_back({h, M2_GEMM_RUNGF, M2Item{node_idx, r0, std::min(8, R - r0), 0, 0, 0}});
+                } else {
+                    const bool stream = !rung && !fp64 && tma && nd.dtype == TNSK_F32 && nd.A == 1 &&
+                                        (nd.cols % 4) == 0 && ((uintptr_t)nd.data % 16) == 0 &&
+                                        nd.npar < ((int64_t)1 << 31) && nd.cols < ((int64_t)1 << 31);
+                    if (rung) {  // V^T hi / lo maps only: X is generated
+                        m2nodes.back().tm_v = (int32_t)P.m2.tmap_jobs.size();
+                        P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 1});
+                        P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 2});
+                    }
+                    if (stream) {
+                        m2nodes.back().tm_x = (int32_t)P.m2.tmap_jobs.size();
+                        P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 0});
+                        m2nodes.back().tm_v = (int32_t)P.m2.tmap_jobs.size();  // hi, then lo at tm_v + 1
+                        P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 1});
+                        P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 2});
+                    }
+                    for (int64_t rt = 0; rt * tile < nd.npar; ++rt)
+                        for (int64_t ct = 0; ct * 64 < R; ++ct)
+                            pend.push_back({h, rung ? M2_GEMM_RUNG : (stream ? M2_GEMM_STREAM : M2_GEMM),
+                                            M2Item{node_idx, (int)rt, (int)ct, 0, 1, 0}});
                 }
-                if (stream) {
-                    m2nodes.back().tm_x = (int32_t)P.m2.tmap_jobs.size();
-                    P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 0});
-                    m2nodes.back().tm_v = (int32_t)P.m2.tmap_jobs.size();  // hi, then lo at tm_v + 1
-                    P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 1});
-                    P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 2});
-                }
-                for (int64_t rt = 0; rt * tile < nd.npar; ++rt)
-                    for (int64_t ct = 0; ct * 64 < R; ++ct)
-                        pend.push_back({h, rung ? M2_GEMM_RUNG : (stream ? M2_GEMM_STREAM : M2_GEMM),
-                                        M2Item{node_idx, (int)rt, (int)ct, 0, 1, 0}});
             }
             if (nd.is_root)  // chunks of 4096 columns x blocks of 8 reps (one warp each)
                 for (int64_t b0 = 0; b0 < std::max<int64_t>(nd.cols, 1); b0 += 4096)

@@ -307,6 +307,42 @@ def test_method2_grouped_rung_tensors(ctx, root):
     pl.close()
 
 
+@pytest.mark.parametrize("root", [0, 2])
+def test_grouped_rung_factored_small_dims(ctx, root):
+    """Grouped tensor with factor dims below 32 and unequal (a, s, c) = (5, 3, 7),
+    (b, s, d) = (6, 3, 4): the factored product (zero-padded tiles) against the oracle
+    on the dense tensor; root 0 makes the row split (i, j), root 2 the transposed one."""
+    rng = np.random.default_rng(91)
+    A = rng.standard_normal((5, 3, 7)).astype(np.float32)
+    B = rng.standard_normal((6, 3, 4)).astype(np.float32)
+    X = np.einsum("isk,jsl->ijkl", A.astype(np.float64), B.astype(np.float64)).reshape(30, 28)
+    x, y = rng.standard_normal(30), rng.standard_normal(28)
+    spec = W.NetSpec([x, X, y], [(0, 1), (2, 3)], [], "rung-small")
+    net = tnsk.Network([torch.as_tensor(x, dtype=torch.float32, device="cuda"),
+                        tnsk.Rung(torch.as_tensor(A, device="cuda"), torch.as_tensor(B, device="cuda")),
+                        torch.as_tensor(y, dtype=torch.float32, device="cuda")], spec.edges, [])
+    p = tnsk.Params(m=64, reps=11, seed=8, method=tnsk.ACYCLIC, root=root)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    per = torch.zeros((p.reps, 1), dtype=torch.float64, device="cuda")
+    ctx.estimate(net, p, out, per)
+    ctx.sync()
+    y_o, sc = oracle_estimate(spec, p, torch.float32)
+    assert_parity(per.cpu().numpy(), y_o, sc, TOL[p.prec], f"rung small root={root}")
+
+
+def test_grouped_rung_tensor_core_path(ctx):
+    """Factor dims above 32 (bond 64, physical 2) take the tensor-core kernel that forms
+    the entries: against the oracle on the dense merged chain."""
+    spec, net = _rung_chain(4, 64, 2, seed=13)
+    p = tnsk.Params(m=256, reps=8, seed=21, method=tnsk.ACYCLIC, root=0)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    per = torch.zeros((p.reps, 1), dtype=torch.float64, device="cuda")
+    ctx.estimate(net, p, out, per)
+    ctx.sync()
+    y, sc = oracle_estimate(spec, p, torch.float32)
+    assert_parity(per.cpu().numpy(), y, sc, TOL[p.prec], "rung chain bond 64")
+
+
 def test_grouped_rung_tensors_rejected_where_unsupported(ctx):
     spec, net = _rung_chain(4, 32, 4, seed=5)
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -316,14 +352,14 @@ def test_grouped_rung_tensors_rejected_where_unsupported(ctx):
         ctx.estimate(net, tnsk.Params(m=256, reps=4, method=tnsk.ACYCLIC, prec=tnsk.PREC_FP64), out)
     with pytest.raises(tnsk.TnskError):  # the grouped tensor as the root
         ctx.estimate(net, tnsk.Params(m=256, reps=4, method=tnsk.ACYCLIC, root=1), out)
-    A, B = W.tt_cores(sites=4, bond=24, phys=4, seed=6)  # column fast index 24: not a multiple of 32
-    spec24 = W.tt_chain(A, B)
-    ts = [torch.as_tensor(spec24.tensors[0], dtype=torch.float32, device="cuda")]
+    A, B = W.tt_cores(sites=4, bond=40, phys=4, seed=6)  # above 32 (tensor cores), 40: not a multiple of 32
+    spec40 = W.tt_chain(A, B)
+    ts = [torch.as_tensor(spec40.tensors[0], dtype=torch.float32, device="cuda")]
     ts += [tnsk.Rung(torch.as_tensor(A[k], dtype=torch.float32, device="cuda"),
                      torch.as_tensor(B[k], dtype=torch.float32, device="cuda")) for k in (1, 2)]
-    ts.append(torch.as_tensor(spec24.tensors[-1], dtype=torch.float32, device="cuda"))
+    ts.append(torch.as_tensor(spec40.tensors[-1], dtype=torch.float32, device="cuda"))
     with pytest.raises(tnsk.TnskError):
-        ctx.estimate(tnsk.Network(ts, spec24.edges, []), tnsk.Params(m=256, reps=4, method=tnsk.ACYCLIC), out)
+        ctx.estimate(tnsk.Network(ts, spec40.edges, []), tnsk.Params(m=256, reps=4, method=tnsk.ACYCLIC), out)
 
 
 @pytest.mark.parametrize("prec", [tnsk.PREC_FP32, tnsk.PREC_FP64])
