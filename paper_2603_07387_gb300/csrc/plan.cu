@@ -857,9 +857,9 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 // the split of K (tensor-core kernels) is chosen once all tiles are known
                 const int64_t tile = fp64 ? 64 : 128;
                 const bool rung = I.rung[k] != nullptr;
-                if (rung && rung_factored(*I.rung[k])) {  // blocks of 8 reps, no tiles or K split
-                    for (int r0 = 0; r0 < R; r0 += 8)
-                        pend.push_back({h, M2_GEMM_RUNGF, M2Item{node_idx, r0, std::min(8, R - r0), 0, 0, 0}});
+                if (rung && rung_factored(*I.rung[k])) {  // blocks of 4 reps, no tiles or K split
+                    for (int r0 = 0; r0 < R; r0 += 4)
+                        pend.push_back({h, M2_GEMM_RUNGF, M2Item{node_idx, r0, std::min(4, R - r0), 0, 0, 0}});
                 } else {
                     const bool stream = !rung && !fp64 && tma && nd.dtype == TNSK_F32 && nd.A == 1 &&
                                         (nd.cols % 4) == 0 && ((uintptr_t)nd.data % 16) == 0 &&
