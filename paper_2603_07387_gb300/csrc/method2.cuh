@@ -68,7 +68,7 @@ struct M2Node {
     int32_t is_root;
     int32_t tm_x;     // streaming tensor-core path: tensor-map index of X and of V^T
     int32_t tm_v;
-    int32_t pad_;
+    int32_t r_fact;   // grouped tensor on the factored product (M2_GEMM_RUNGF)
     // grouped (rung) tensor, M2_GEMM_RUNG: X(row, col) = sum_s A[i1 ai + j1 aj + s as]
     // B[i2 bi + j2 bj + s bs] with row = i1 rn_i2 + i2, col = j1 rn_j2 + j2
     const float* rA;

@@ -107,9 +107,11 @@ tnsk_status finalize_plan(BatchPlan& P, unsigned char* base, std::string& err) {
     return TNSK_OK;
 }
 
-// A grouped tensor whose four factor dims are at most 32 runs the factored product
-// (m2_rung_fact.cu); larger ones the tensor-core kernel that forms the entries.
-static bool rung_factored(const tnsk_rung& g) { return g.a <= 32 && g.b <= 32 && g.c <= 32 && g.d <= 32 && g.s <= 16; }
+// Grouped tensors run the tensor-core kernel that forms their entries where its layout
+// rules hold (column fast index a multiple of 32, B factor within 60 KiB, tensor maps);
+// otherwise, with all four factor dims at most 32, the factored SIMT product
+// (m2_rung_fact.cu), measured slower than the tensor-core kernel at dims 32.
+static bool rung_small(const tnsk_rung& g) { return g.a <= 32 && g.b <= 32 && g.c <= 32 && g.d <= 32; }
 
 tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I, std::string& why, bool zero_ok,
                      const char* diag) {
@@ -748,11 +750,14 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 nd.r_bi = (int32_t)(first ? g.s * g.d : 1);
                 nd.r_bj = (int32_t)(first ? 1 : g.s * g.d);
                 const int64_t b_bytes = (int64_t)nd.rn_i2 * (g.s * nd.rn_j2 + 4) * 4;
-                if (rung_factored(g)) {
+                const bool tc_ok = nd.rn_j2 % 32 == 0 && b_bytes <= 60 * 1024 && tma;
+                nd.r_fact = !tc_ok && rung_small(g) ? 1 : 0;
+                if (nd.r_fact) {
                     P.m2.rungf_smem = std::max(P.m2.rungf_smem, m2_rung_fact_smem((int)g.s));
-                } else if (nd.rn_j2 % 32 != 0 || b_bytes > 60 * 1024 || !tma) {
+                } else if (!tc_ok) {
                     err = "tensor " + std::to_string(k) +
-                          ": rung tensor needs its column fast index a multiple of 32 and the B factor within 60 KiB";
+                          ": rung tensor needs factor dims <= 32, or its column fast index a multiple of 32 and the "
+                          "B factor within 60 KiB";
                     return TNSK_ERR_UNSUPPORTED;
                 }
                 // A rows of a 128-row tile: at most 127 / n_i2 + 2 values of i1, staged when
@@ -760,7 +765,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 const int64_t i1_max = std::min<int64_t>(nd.rn_i1, 127 / nd.rn_i2 + 2);
                 const int64_t a_bytes = i1_max * g.s * nd.rn_j1 * 4;
                 nd.r_astage = a_bytes <= 16 * 1024 ? 1 : 0;
-                if (!rung_factored(g))
+                if (!nd.r_fact)
                     P.m2.rung_smem = std::max(P.m2.rung_smem,
                                               m2_gemm_rung_smem((size_t)(b_bytes + (nd.r_astage ? a_bytes : 0))));
             }
@@ -857,7 +862,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 // the split of K (tensor-core kernels) is chosen once all tiles are known
                 const int64_t tile = fp64 ? 64 : 128;
                 const bool rung = I.rung[k] != nullptr;
-                if (rung && rung_factored(*I.rung[k])) {  // blocks of 4 reps, no tiles or K split
+                if (rung && m2nodes.back().r_fact) {  // blocks of 4 reps, no tiles or K split
                     for (int r0 = 0; r0 < R; r0 += 4)
                         pend.push_back({h, M2_GEMM_RUNGF, M2Item{node_idx, r0, std::min(4, R - r0), 0, 0, 0}});
                 } else {

@@ -330,6 +330,22 @@ def test_grouped_rung_factored_small_dims(ctx, root):
     assert_parity(per.cpu().numpy(), y_o, sc, TOL[p.prec], f"rung small root={root}")
 
 
+@pytest.mark.parametrize("root", [0, -2])
+def test_grouped_rung_factored_chain(ctx, root):
+    """A chain of grouped tensors with bond 24 (below 32, not a multiple of 32: the
+    factored product) against the oracle on the dense merged chain, both orientations."""
+    sites = 5
+    spec, net = _rung_chain(sites, 24, 4, seed=17)
+    r = 0 if root == 0 else sites - 1
+    p = tnsk.Params(m=512, reps=10, seed=33, method=tnsk.ACYCLIC, root=r)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    per = torch.zeros((p.reps, 1), dtype=torch.float64, device="cuda")
+    ctx.estimate(net, p, out, per)
+    ctx.sync()
+    y, sc = oracle_estimate(spec, p, torch.float32)
+    assert_parity(per.cpu().numpy(), y, sc, TOL[p.prec], f"rung chain bond 24 root={r}")
+
+
 def test_grouped_rung_tensor_core_path(ctx):
     """Factor dims above 32 (bond 64, physical 2) take the tensor-core kernel that forms
     the entries: against the oracle on the dense merged chain."""
