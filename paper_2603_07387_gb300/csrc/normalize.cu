@@ -66,8 +66,9 @@ cudaError_t launch_normalize(const NormJob* d_jobs, int n, int64_t most, cudaStr
 
 namespace {
 
-// The rewrite of one network, or false when it is not needed or the network fails
-// the basic checks (left to planning).
+// True when an acyclic network needs the WLOG 2 / 3 rewrite (a contraction inside one
+// tensor, or two between one pair); false when it needs none or fails the basic
+// checks (left to planning). Fills the mode owners, dims and per-tensor mode offsets.
 bool needs_rewrite(const tnsk_network& N, std::vector<int>& owner, std::vector<int64_t>& dimg,
                    std::vector<int>& moff) {
     if (N.p < 1 || !N.X || N.t < 0 || (N.t > 0 && !N.edges) || N.n_open != 0) return false;
