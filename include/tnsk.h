@@ -231,6 +231,16 @@ tnsk_status tnsk_stream_create(tnsk_ctx* ctx, const tnsk_network* net, const tns
 tnsk_status tnsk_stream_update(tnsk_ctx* ctx, tnsk_stream* stream, int64_t n, const int32_t* tensor,
                                const int64_t* index, const double* delta);
 tnsk_status tnsk_stream_estimate(tnsk_ctx* ctx, tnsk_stream* stream);
+/* The stream's stored sketches (sketches are linear in the tensors, Sec. 4.2): *x =
+ * device pointer (owned by the stream) to *count FP32 or FP64 entries (params->prec),
+ * laid out as tnsk_m1_sketch's output ([reps][sum_k O_k m], copy tensors of WLOG 1
+ * after the caller's tensors; the count may include up to 3 entries of padding).
+ * Several processes that each stream a part of the same tensors' entries, with the
+ * same network and params, can sum these buffers (e.g. an all-reduce) and then call
+ * tnsk_stream_estimate to estimate the whole: the sketch of a sum is the sum of the
+ * sketches. Order the reduction after the stream's work on the ctx stream.
+ * TNSK_ERR_INVALID for NULL arguments. */
+tnsk_status tnsk_stream_sketches(tnsk_stream* stream, void** x, int64_t* count);
 tnsk_status tnsk_stream_destroy(tnsk_stream* stream);
 
 /* Per-kernel timing. While enabled, every kernel launch of the ctx is bracketed

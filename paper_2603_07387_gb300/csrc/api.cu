@@ -621,6 +621,14 @@ tnsk_status tnsk_stream_estimate(tnsk_ctx* ctx, tnsk_stream* s) {
     return TNSK_OK;
 }
 
+tnsk_status tnsk_stream_sketches(tnsk_stream* s, void** x, int64_t* count) {
+    if (!s || !x || !count) return TNSK_ERR_INVALID;
+    const tnsk_plan* p = s->plan;
+    *x = p->dev + p->plan.m1.xs_off;
+    *count = p->plan.m1.xs_count;
+    return TNSK_OK;
+}
+
 tnsk_status tnsk_stream_destroy(tnsk_stream* s) {
     if (!s) return TNSK_ERR_INVALID;
     tnsk_status st = tnsk_plan_destroy(s->plan);

@@ -1020,6 +1020,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     P.zero_off = P.arena.take(0);
     P.yrep_off = P.arena.take((size_t)yrep_n * sizeof(double));
     P.m1.xs_off = P.arena.take((size_t)xs_n * acc);
+    P.m1.xs_count = xs_n;
     P.m2.ws_off = P.arena.take((size_t)(ws_x + ws_w + ws_r + ws_v) * acc);
     P.zero_bytes = P.m2.ws_off + (size_t)(ws_x + ws_w) * acc - P.zero_off;
     // ---- the rest

@@ -48,6 +48,7 @@ struct M1Plan {
     int n_nets = 0;
     size_t tens_off = 0, nets_off = 0, work_off = 0, opens_off = 0, items_off = 0;
     size_t xs_off = 0, spec_off = 0, sexp_off = 0;
+    int64_t xs_count = 0;  // sketch entries of all networks (FP32 or FP64)
     int n_work = 0, n_items = 0;
     // scatter work items by tensor order class (order <= 2, 4, 6, 12): one launch per
     // class with its own unrolled width and shared-memory size

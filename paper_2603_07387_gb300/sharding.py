@@ -8,6 +8,12 @@ median of group means (Theorem 1) then runs on the gathered array exactly as in 
 single-GPU call (``Context.combine``), so the sharded result equals the unsharded
 one. Batches of independent networks need no exchange at all: each rank takes
 its own networks.
+
+A tensor too large for one GPU is split by entries instead: sketches are linear in
+the tensors (Sec. 4.2), so ranks that sketch disjoint parts of the same tensors'
+entries (turnstile streams with the same network and params) hold sketches that sum
+to those of the whole; one all-reduce of the sketch buffers (reps x sum_k O_k m
+values) precedes the transform, product and combination (``allreduce_sketches``).
 """
 from __future__ import annotations
 
@@ -44,6 +50,26 @@ def gather_reps(local, reps: int, group=None):
         r0, r1 = rep_shard(reps, world, k)
         blocks.append(parts[k][: r1 - r0])
     return torch.cat(blocks, dim=0).contiguous()
+
+
+def allreduce_sketches(x, group=None):
+    """Sums the sketch buffer ``x`` (a torch tensor: ``Stream.sketches()`` on the GPU,
+    or any tensor the collective's backend takes) over the ranks of ``group`` in place.
+    On the GPU the stream's work must be ordered before it: the library's ctx runs on
+    torch's current stream, or the caller synchronises first."""
+    import torch.distributed as dist
+
+    if dist.is_initialized() and dist.get_world_size(group) > 1:
+        dist.all_reduce(x, op=dist.ReduceOp.SUM, group=group)
+    return x
+
+
+def estimate_entry_sharded(stream, group=None):
+    """The estimate of the whole from this rank's turnstile stream over its part of the
+    entries: all-reduce of the sketches, then ``stream.estimate()`` (outputs as the
+    stream was created with, the same on every rank)."""
+    allreduce_sketches(stream.sketches(), group)
+    stream.estimate()
 
 
 def estimate_sharded(ctx, net, params, out, group=None):

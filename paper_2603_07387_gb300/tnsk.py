@@ -54,6 +54,7 @@ SYMBOLS = (
     "tnsk_stream_create",
     "tnsk_stream_update",
     "tnsk_stream_estimate",
+    "tnsk_stream_sketches",
     "tnsk_stream_destroy",
     "tnsk_mlp_num_params",
     "tnsk_mlp_create",
@@ -199,6 +200,8 @@ def load_library(path: str = LIB_PATH):
     L.tnsk_stream_update.argtypes = [vp, vp, i64, vp, vp, vp]
     L.tnsk_stream_estimate.restype = i32
     L.tnsk_stream_estimate.argtypes = [vp, vp]
+    L.tnsk_stream_sketches.restype = i32
+    L.tnsk_stream_sketches.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64)]
     L.tnsk_stream_destroy.restype = i32
     L.tnsk_stream_destroy.argtypes = [vp]
     L.tnsk_probe_shared_atomics.restype = i32
@@ -383,8 +386,9 @@ class Stream:
     """A turnstile stream (tnsk_stream): method-1 sketches of one network kept on the
     device; update() adds deltas to tensor entries, estimate() recomputes the outputs."""
 
-    def __init__(self, ctx, handle, tensors, out, per_rep):
+    def __init__(self, ctx, handle, tensors, out, per_rep, prec=0):
         self.ctx, self.h = ctx, handle
+        self.prec = prec
         self._keep = (tensors, out, per_rep)  # the tensors until the first sketching has run
 
     def update(self, tensor, index, delta):
@@ -403,6 +407,23 @@ class Stream:
 
     def estimate(self):
         self.ctx._check(self.ctx.lib.tnsk_stream_estimate(self.ctx.h, self.h))
+
+    def sketches(self):
+        """tnsk_stream_sketches: a torch view (no copy) of the stored sketches, FP32 or
+        FP64 by the stream's precision, to be summed across processes that stream parts
+        of the same tensors before estimate()."""
+        import torch
+
+        x = ctypes.c_void_p()
+        n = ctypes.c_int64()
+        self.ctx._check(self.ctx.lib.tnsk_stream_sketches(self.h, ctypes.byref(x), ctypes.byref(n)))
+        typestr = "<f8" if self.prec == PREC_FP64 else "<f4"
+
+        class _View:  # CUDA array interface over the stream's buffer
+            __cuda_array_interface__ = {"shape": (int(n.value),), "typestr": typestr,
+                                        "data": (int(x.value or 0), False), "version": 3}
+
+        return torch.as_tensor(_View(), device="cuda")
 
     def close(self):
         if getattr(self, "h", None):
@@ -632,7 +653,7 @@ class Context:
         self._check(self.lib.tnsk_stream_create(self.h, ctypes.byref(nh.c), ctypes.byref(pr), out.data_ptr(),
                                                 per_rep.data_ptr() if per_rep is not None else None,
                                                 ctypes.byref(h)))
-        return Stream(self, h, list(net.tensors), out, per_rep)
+        return Stream(self, h, list(net.tensors), out, per_rep, params.prec)
 
     def plan(self, nets: Sequence[Network], params: Sequence[Params], outs, per_reps=None) -> "Plan":
         """tnsk_plan_create: plan a batch once; run it with Plan.run()."""

@@ -379,6 +379,52 @@ def test_grouped_rung_tensors_rejected_where_unsupported(ctx):
 
 
 @pytest.mark.parametrize("prec", [tnsk.PREC_FP32, tnsk.PREC_FP64])
+def test_entry_sharded_streams_sum_to_the_whole(ctx, prec):
+    """The entries of a cyclic network with an open leg split between two streams (as
+    two ranks would hold them): the streams' sketch buffers (tnsk_stream_sketches)
+    match the oracle's sketches of each part, their sum estimates the whole, per rep,
+    against the oracle on the full tensors."""
+    rng = np.random.default_rng(52)
+    X = [rng.standard_normal((6, 5)), rng.standard_normal((5, 7, 3)), rng.standard_normal((7, 6))]
+    edges, open_ = [(1, 2), (3, 5), (6, 0)], [4]
+    tdt = torch.float64 if prec == tnsk.PREC_FP64 else torch.float32
+    spec = W.NetSpec(X, edges, open_, "entry-shards")
+    Xr = rounded(spec, tdt)
+    p = tnsk.Params(m=64, reps=6, seed=12, method=tnsk.GENERAL, prec=prec)
+    bins, signs = oracle.m1_tables(Xr, edges, open_, seed=p.seed, reps=p.reps, m=p.m)
+    streams, outs, pers = [], [], []
+    for part in range(2):
+        zeros = tnsk.Network([tnsk.Zeros(*x.shape, dtype=tdt) for x in Xr], edges, open_)
+        out = torch.zeros(3, dtype=torch.float64, device="cuda")
+        per = torch.zeros((p.reps, 3), dtype=torch.float64, device="cuda")
+        st = ctx.stream(zeros, p, out, per)
+        idx = [np.arange(x.size)[np.arange(x.size) % 2 == part] for x in Xr]
+        tk = np.concatenate([np.full(i.size, k, np.int32) for k, i in enumerate(idx)])
+        ti = np.concatenate(idx).astype(np.int64)
+        dv = np.concatenate([x.reshape(-1)[i] for x, i in zip(Xr, idx)])
+        st.update(torch.as_tensor(tk, device="cuda"), torch.as_tensor(ti, device="cuda"),
+                  torch.as_tensor(dv, dtype=torch.float64, device="cuda"))
+        ctx.sync()
+        mine = [np.where(np.arange(x.size).reshape(x.shape) % 2 == part, x, 0.0) for x in Xr]
+        want = oracle.m1_sketch(mine, edges, open_, p.m, bins, signs)
+        scale = oracle.m1_sketch(Xr, edges, open_, p.m, bins, signs, abs_mode=True)
+        got = st.sketches().double().cpu().numpy()[: want.size].reshape(want.shape)
+        tol = 1e-12 if prec == tnsk.PREC_FP64 else 1e-6
+        assert np.all(np.abs(got - want) <= tol * np.maximum(scale, 1e-300)), f"part {part}"
+        streams.append(st)
+        outs.append(out)
+        pers.append(per)
+    xa, xb = streams[0].sketches(), streams[1].sketches()
+    xa += xb  # the all-reduce of two ranks, on one GPU
+    streams[0].estimate()
+    ctx.sync()
+    y, sc = oracle_estimate(spec, p, tdt)
+    assert_parity(pers[0].cpu().numpy(), y, sc, TOL[prec], "entry-sharded sum")
+    for st in streams:
+        st.close()
+
+
+@pytest.mark.parametrize("prec", [tnsk.PREC_FP32, tnsk.PREC_FP64])
 def test_turnstile_stream_updates(ctx, prec):
     """Sec. 4.2's turnstile model: sketch a cyclic network with an open leg, apply
     batches of entry updates (repeated entries included) to the stored sketches, and
