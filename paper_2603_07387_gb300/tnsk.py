@@ -411,7 +411,7 @@ class Stream:
     def sketches(self):
         """tnsk_stream_sketches: a torch view (no copy) of the stored sketches, FP32 or
         FP64 by the stream's precision, to be summed across processes that stream parts
-        of the same tensors before estimate()."""
+        of the same tensors before estimate(). Valid while the stream is open."""
         import torch
 
         x = ctypes.c_void_p()
