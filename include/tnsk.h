@@ -194,6 +194,19 @@ tnsk_status tnsk_m1_sketch(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_pa
 tnsk_status tnsk_estimate(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, double* out,
                           double* per_rep);
 
+/* The network tnsk_estimate plans for `net` under `params` after the WLOG rewrites
+ * above, computed on the host only (no ctx, no device work): *p_out tensors, tensor
+ * k of order order_out[k] with its dims next in dims_out (concatenated in tensor
+ * order), copy_out[k] = 1 for a WLOG 1 copy tensor; *t_out contractions as pairs in
+ * edges_out. Capacities: cap_tensors entries of order_out and copy_out, cap_dims of
+ * dims_out, cap_edges pairs of edges_out. A network that needs no rewrite (or fails
+ * the basic checks, which tnsk_estimate then reports) is returned as given.
+ * Errors: TNSK_ERR_INVALID for NULL pointers or a capacity too small; the rewrite's
+ * own TNSK_ERR_UNSUPPORTED cases as in tnsk_estimate. */
+tnsk_status tnsk_rewrite(const tnsk_network* net, const tnsk_params* params, int32_t cap_tensors, int32_t* p_out,
+                         int32_t* order_out, int32_t* copy_out, int64_t cap_dims, int64_t* dims_out, int32_t cap_edges,
+                         int32_t* t_out, int32_t* edges_out);
+
 /* B networks in one batch (one launch sequence for all). params[b], outs[b],
  * per_reps[b] (may be NULL, or hold NULL entries) as in tnsk_estimate. */
 tnsk_status tnsk_estimate_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,

@@ -320,6 +320,37 @@ tnsk_status normalize_batch(int B, const tnsk_network* nets, const tnsk_params* 
     return TNSK_OK;
 }
 
+}  // namespace tnsk
+
+extern "C" tnsk_status tnsk_rewrite(const tnsk_network* net, const tnsk_params* params, int32_t cap_tensors,
+                                    int32_t* p_out, int32_t* order_out, int32_t* copy_out, int64_t cap_dims,
+                                    int64_t* dims_out, int32_t cap_edges, int32_t* t_out, int32_t* edges_out) {
+    if (!net || !params || !p_out || !t_out || (cap_tensors > 0 && (!order_out || !copy_out)) ||
+        (cap_dims > 0 && !dims_out) || (cap_edges > 0 && !edges_out))
+        return TNSK_ERR_INVALID;
+    tnsk::NormBatch nb;
+    std::string why;
+    const tnsk_status st = tnsk::normalize_batch(1, net, params, nb, why);
+    if (st != TNSK_OK) return st;
+    const tnsk_network& V = nb.view.empty() ? *net : nb.view[0];
+    if (V.p < 0 || V.t < 0 || (V.p > 0 && !V.X) || (V.t > 0 && !V.edges)) return TNSK_ERR_INVALID;
+    if (V.p > cap_tensors || V.t > cap_edges) return TNSK_ERR_INVALID;
+    int64_t o = 0;
+    for (int k = 0; k < V.p; ++k) {
+        const tnsk_tensor& X = V.X[k];
+        if (X.order < 0 || (X.order > 0 && !X.dims) || o + X.order > cap_dims) return TNSK_ERR_INVALID;
+        order_out[k] = X.order;
+        copy_out[k] = !nb.diag.empty() && !nb.diag[0].empty() ? nb.diag[0][(size_t)k] : 0;
+        for (int d = 0; d < X.order; ++d) dims_out[o++] = X.dims[d];
+    }
+    for (int e = 0; e < 2 * V.t; ++e) edges_out[e] = V.edges[e];
+    *p_out = V.p;
+    *t_out = V.t;
+    return TNSK_OK;
+}
+
+namespace tnsk {
+
 void normalize_bind(NormBatch& nb, unsigned char* base) {
     for (size_t j = 0; j < nb.jobs.size(); ++j) nb.jobs[j].dst = base + nb.dst_off[j];
     for (size_t b = 0; b < nb.nets.size(); ++b) {

@@ -43,6 +43,7 @@ SYMBOLS = (
     "tnsk_estimate",
     "tnsk_estimate_batch",
     "tnsk_estimate_static",
+    "tnsk_rewrite",
     "tnsk_plan_create",
     "tnsk_plan_run",
     "tnsk_plan_destroy",
@@ -143,6 +144,9 @@ def load_library(path: str = LIB_PATH):
     vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
     L.tnsk_create.restype = i32
     L.tnsk_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp]
+    pi32, pi64 = ctypes.POINTER(i32), ctypes.POINTER(i64)
+    L.tnsk_rewrite.restype = i32
+    L.tnsk_rewrite.argtypes = [vp, vp, i32, pi32, pi32, pi32, i64, pi64, i32, pi32, pi32]
     L.tnsk_destroy.restype = i32
     L.tnsk_destroy.argtypes = [vp]
     L.tnsk_set_stream.restype = i32
@@ -357,6 +361,33 @@ def estimate_static(net: Network, params: Params, out, per_rep=None, stream=None
                                 ctypes.c_void_p(int(stream)) if stream else None)
     if st != TNSK_OK:
         raise TnskError(st, "tnsk_estimate_static")
+
+
+def rewrite(net: Network, params: Params):
+    """tnsk_rewrite: the network the library plans after the WLOG rewrites of Sec. 4.1,
+    computed on the host (no device work; tensors may be CPU tensors): (shapes, edges,
+    copy) with copy[k] True for a WLOG 1 copy tensor."""
+    L = load_library()
+    nh = _NetHolder(net)
+    pr = _params(params)
+    q = sum(len(x.shape) for x in net.tensors)
+    cap_t, cap_e = len(net.tensors) + max(1, len(net.edges)), max(1, 2 * len(net.edges))
+    cap_d = q + 2 * len(net.edges) + 1
+    p_out, t_out = ctypes.c_int32(), ctypes.c_int32()
+    order = (ctypes.c_int32 * cap_t)()
+    copy = (ctypes.c_int32 * cap_t)()
+    dims = (ctypes.c_int64 * cap_d)()
+    edges = (ctypes.c_int32 * (2 * cap_e))()
+    st = L.tnsk_rewrite(ctypes.byref(nh.c), ctypes.byref(pr), cap_t, ctypes.byref(p_out), order, copy, cap_d, dims,
+                        cap_e, ctypes.byref(t_out), edges)
+    if st != TNSK_OK:
+        raise TnskError(st, "tnsk_rewrite")
+    shapes, o = [], 0
+    for k in range(p_out.value):
+        shapes.append(tuple(int(dims[o + j]) for j in range(order[k])))
+        o += order[k]
+    E = [(int(edges[2 * e]), int(edges[2 * e + 1])) for e in range(t_out.value)]
+    return shapes, E, [bool(copy[k]) for k in range(p_out.value)]
 
 
 class Plan:
