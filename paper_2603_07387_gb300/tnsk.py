@@ -644,6 +644,9 @@ class Context:
                                                bins.data_ptr() if n else None, signs.data_ptr() if n else None))
 
     def m1_sketch(self, net: Network, params: Params, x):
+        """tnsk_m1_sketch: method-1 sketches of every tensor into x (device, [reps][sum_k
+        O_k m]); for a network with hyperedges the WLOG 1 copy tensors' sketches follow
+        the caller's tensors (``rewrite`` gives the planned network)."""
         nh = _NetHolder(net)
         pr = _params(params)
         self._check(self.lib.tnsk_m1_sketch(self.h, ctypes.byref(nh.c), ctypes.byref(pr), x.data_ptr()))
