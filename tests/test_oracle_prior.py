@@ -91,3 +91,16 @@ def test_open_legs_per_output_entry(open_modes):
         at = dict(zip(open_modes, idx))
         want = prior.estimate([A[at[0]], B[:, at[3]]], [(0, 1)], [], m, 2, seed)[:, 0]
         assert np.allclose(got[:, o], want)
+
+
+def test_even_ring_is_unbiased():
+    """A ring of four matrices: the chain conjugates tensors 0 and 2, so every
+    contraction joins a conjugated and an unconjugated tensor and the mean over seeds
+    approaches tc (the odd ring above does not)."""
+    rng = np.random.default_rng(9)
+    Ms = [rng.uniform(0, 1, (3, 3)) for _ in range(4)]
+    edges = [(1, 2), (3, 4), (5, 6), (7, 0)]
+    tc = np.trace(Ms[0] @ Ms[1] @ Ms[2] @ Ms[3])
+    ys = np.concatenate([prior.estimate(Ms, edges, [], 8, 50, seed)[:, 0] for seed in range(30)])
+    se = ys.std(ddof=1) / np.sqrt(ys.size)
+    assert abs(ys.mean() - tc) <= 5 * se
