@@ -144,3 +144,19 @@ def test_wlog1_random_hyperedges_keep_tc(seed):
     assert len(used) == len(set(used))
     want = oracle.tc_definition(tensors, edges, open_modes)
     assert np.allclose(oracle.tc_definition(T, E, O), want)
+
+
+def test_method2_on_the_rewrite_estimates_the_original():
+    """Method 2 on the rewritten network (a trace and a double contraction removed) is
+    unbiased for the original network's tc: mean over many reps within 5 standard
+    errors."""
+    rng = np.random.default_rng(12)
+    A = rng.uniform(0, 1, (3, 2, 4, 4))  # modes 0-3: (2, 3) traced
+    B = rng.uniform(0, 1, (2, 3, 5))     # modes 4-6: joins A twice
+    C = rng.uniform(0, 1, (5,))          # mode 7
+    edges = [(1, 4), (0, 5), (2, 3), (6, 7)]
+    tc = float(oracle.tc_definition([A, B, C], edges, []))
+    T, E, _ = normalize([A, B, C], edges)
+    y, _ = oracle.m2_estimate(T, E, m=16, reps=4000, seed=3, root=2)
+    se = y.std(ddof=1) / np.sqrt(y.size)
+    assert abs(y.mean() - tc) <= 5 * se
