@@ -160,3 +160,17 @@ def test_method2_on_the_rewrite_estimates_the_original():
     y, _ = oracle.m2_estimate(T, E, m=16, reps=4000, seed=3, root=2)
     se = y.std(ddof=1) / np.sqrt(y.size)
     assert abs(y.mean() - tc) <= 5 * se
+
+
+def test_method1_on_copy_tensors_estimates_the_hyperedge_network():
+    """Method 1 on the WLOG 1 rewrite (one copy tensor of order 3) is unbiased for the
+    original network's tc (the brute-force definition reads the hyperedge's brackets)."""
+    from oracle.normalize import copy_tensors
+    rng = np.random.default_rng(13)
+    X = [rng.uniform(0, 1, (4, 3)), rng.uniform(0, 1, (3, 4)), rng.uniform(0, 1, (4,))]  # modes 0,1 | 2,3 | 4
+    edges = [(0, 3), (3, 4), (1, 2)]  # mode 3 in two contractions: class {0, 3, 4}
+    tc = float(oracle.tc_definition(X, edges, []))
+    T, E, _ = copy_tensors(X, edges)
+    y, _ = oracle.m1_estimate(T, E, [], m=16, reps=4000, seed=4)
+    se = y.std(ddof=1) / np.sqrt(y.size)
+    assert abs(y.mean() - tc) <= 5 * se
