@@ -47,7 +47,7 @@ typedef enum {
     TNSK_OK = 0,
     TNSK_ERR_INVALID = -1,      /* malformed network or parameters */
     TNSK_ERR_CYCLIC = -2,       /* TNSK_ACYCLIC on a network with a cycle */
-    TNSK_ERR_UNSUPPORTED = -3,  /* valid, but outside this build's limits */
+    TNSK_ERR_UNSUPPORTED = -3,  /* valid, but outside the library's limits */
     TNSK_ERR_CUDA = -4,         /* a CUDA runtime call failed */
     TNSK_ERR_OOM = -5,          /* scratch allocation failed */
     TNSK_ERR_TIMEOUT = -6,      /* a device-side bounded wait gave up */

@@ -304,7 +304,7 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
     }
     // ---- method 2: acyclic, connected, full (Sec. 4.4) ----
     if (net.n_open != 0) {
-        why = "the acyclic method takes full networks (no open legs) in this build";
+        why = "the acyclic method takes full networks (no open legs) in this library";
         return TNSK_ERR_UNSUPPORTED;
     }
     for (int e = 0; e < I.t; ++e)
