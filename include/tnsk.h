@@ -299,22 +299,23 @@ tnsk_status tnsk_plan_destroy(tnsk_plan* plan);
 
 /* Method-1 estimate that allocates no device memory (the paper has no
  * counterpart; this is a deployment variant of tnsk_estimate).
- * For callers that cannot call cudaMalloc: code running inside a stream capture
- * it does not own, plugins whose host application owns every allocation, or
- * uses that must not grow device memory after start-up. Needs no ctx. Runs the
- * same kernels as tnsk_estimate with TNSK_GENERAL and TNSK_PREC_FP32 on
- * `cuda_stream` (NULL = legacy default stream) of the current device, with all
- * scratch in one fixed 16 MiB device array inside the library (held by every
- * GPU that loads the library until the process exits).
- * net, params: as for tnsk_estimate; params->method must be TNSK_GENERAL and
- * params->prec TNSK_PREC_FP32 (else TNSK_ERR_UNSUPPORTED). out, per_rep: device
- * buffers as for tnsk_estimate (per_rep may be NULL).
+ * For callers that cannot call cudaMalloc: plugins whose host application owns
+ * every allocation, or uses that must not grow device memory after start-up.
+ * Needs no ctx. Runs the same kernels as tnsk_estimate with TNSK_GENERAL and
+ * TNSK_PREC_FP32 on `cuda_stream` (NULL = legacy default stream) of the current
+ * device, with all scratch in one fixed 16 MiB device array inside the library
+ * (held by every GPU that loads the library until the process exits).
+ * net, params: as for tnsk_estimate (hyperedges get WLOG 1's copy tensors, which
+ * are not stored); params->method must be TNSK_GENERAL and params->prec
+ * TNSK_PREC_FP32 (else TNSK_ERR_UNSUPPORTED). out, per_rep: device buffers as for
+ * tnsk_estimate (per_rep may be NULL).
  * Errors: TNSK_ERR_INVALID / _UNSUPPORTED as tnsk_estimate; TNSK_ERR_UNSUPPORTED
  * also when the call would need more than the 16 MiB of scratch; TNSK_ERR_CUDA
  * when a launch or copy fails. There is no error text.
  * The first call on a device looks up the array and fills its FFT twiddles with
- * a synchronous copy: make it before any stream capture. Every call reuses the
- * same array, so calls whose GPU work overlaps race; order them on one stream. */
+ * a synchronous copy. Every call reuses the same array (each device has its own),
+ * so calls on one device whose GPU work overlaps, from two streams or two host
+ * threads, race: order them on one stream. */
 tnsk_status tnsk_estimate_static(const tnsk_network* net, const tnsk_params* params, double* out, double* per_rep,
                                  void* cuda_stream);
 

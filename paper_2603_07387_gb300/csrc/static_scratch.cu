@@ -1,8 +1,7 @@
 // static_scratch.cu -- tnsk_estimate_static: the method-1 estimate for callers
 // that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA stream
-// capture they do not control, plugins whose host application owns every
+// Some callers cannot call cudaMalloc: plugins whose host application owns every
 // allocation (a fixed memory pool or an allocator that forbids side
 // allocations), or embedded uses that must not grow device memory after
 // start-up. For them this entry point runs the same kernels as tnsk_estimate
@@ -14,18 +13,22 @@
 // Costs and rules:
 //  - The array (kStaticBytes = 16 MiB) is part of the library's device image:
 //    every GPU that loads libtnsk holds it until the process exits.
-//  - All calls share the array, which keeps the last call's contents. Calls
-//    whose GPU work overlaps (two streams, two host threads, two devices
-//    sharing nothing else are fine) race on it: order them on one stream.
+//  - All calls share the array, which keeps the last call's contents. Calls on
+//    different devices are independent (each device has its own copy of the
+//    array). Calls on one device whose GPU work overlaps, from two streams or two
+//    host threads, race on the array: order them on one stream.
 //  - The first call on a device looks up the array's device address
 //    (cudaGetSymbolAddress) and writes the twiddle tables with a synchronous
-//    copy; make that first call before any stream capture.
+//    copy.
+//  - Hyperedges (a mode in several contractions) get WLOG 1's copy tensors as in
+//    tnsk_estimate; the copy tensors are never stored, so this needs no buffer.
 #include <cmath>
 #include <mutex>
 #include <vector>
 
 #include "kernels.cuh"
 #include "method2.cuh"
+#include "normalize.cuh"
 #include "plan.cuh"
 
 namespace tnsk {
@@ -103,9 +106,17 @@ extern "C" tnsk_status tnsk_estimate_static(const tnsk_network* net, const tnsk_
         cudaGetLastError();
         return TNSK_ERR_CUDA;
     }
-    std::vector<NetInfo> infos(1);
+    // WLOG 1 (Sec. 4.1) for hyperedges: a host-side view of the network with copy
+    // tensors appended; method-1 networks never need a rewritten tensor buffer
+    NormBatch nb;
     std::string why;
-    tnsk_status st = validate(*net, *params, infos[0], why);
+    tnsk_status st = normalize_batch(1, net, params, nb, why);
+    if (st != TNSK_OK) return st;
+    if (!nb.jobs.empty()) return TNSK_ERR_UNSUPPORTED;
+    const tnsk_network* view = nb.used ? nb.view.data() : net;
+    const char* diag = !nb.diag.empty() && !nb.diag[0].empty() ? nb.diag[0].data() : nullptr;
+    std::vector<NetInfo> infos(1);
+    st = validate(*view, *params, infos[0], why, false, diag);
     if (st != TNSK_OK) return st;
     StaticDevice* sd = nullptr;
     st = setup_device(dev, sd);
@@ -114,7 +125,7 @@ extern "C" tnsk_status tnsk_estimate_static(const tnsk_network* net, const tnsk_
     plan.arena.used = sd->arena_off;  // per-call regions start after the twiddles
     double* outs[1] = {out};
     double* pers[1] = {per_rep};
-    st = plan_batch(infos, net, params, outs, pers, false, false, plan, why);
+    st = plan_batch(infos, view, params, outs, pers, false, false, plan, why);
     if (st != TNSK_OK) return st;
     if (plan.arena.used > kStaticBytes) return TNSK_ERR_UNSUPPORTED;  // beyond the fixed 16 MiB
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -130,6 +141,7 @@ extern "C" tnsk_status tnsk_estimate_static(const tnsk_network* net, const tnsk_
     if (launch_draw_tables((const TabReq*)(base + plan.reqs_off), plan.n_reqs, plan.n_table_rows,
                            (uint32_t*)(base + plan.tabs_off), s) != cudaSuccess ||
         launch_m1_scatters(plan, base, base + plan.m1.xs_off, false, s) != cudaSuccess ||
+        launch_m1_diag(plan, base, base + plan.m1.xs_off, false, s) != cudaSuccess ||
         launch_m1_spectra(plan, base, base + plan.m1.xs_off, (const void* const*)tws, false, s) != cudaSuccess ||
         launch_combine((const CombineItem*)(base + plan.comb_off), plan.n_comb, (const double*)(base + plan.yrep_off),
                        s) != cudaSuccess) {
