@@ -68,10 +68,19 @@ typedef enum { TNSK_F64 = 0, TNSK_F32 = 1, TNSK_BF16 = 2 } tnsk_dtype;
  * and calls as TNSK_GENERAL (tnsk_estimate, batches, plans, tnsk_m1_sketch,
  * streams); tnsk_choose_params and tnsk_estimate_static refuse it. */
 typedef enum { TNSK_GENERAL = 1, TNSK_ACYCLIC = 2, TNSK_CROSSCORR = 3 } tnsk_method;
-/* Arithmetic of the sketches and transforms. FP32: sketches, FFTs and products in
- * FP32 (per-tensor power-of-two scaling), per-rep estimates and combination in
- * FP64. FP64: everything in FP64 (for high-dynamic-range sketches). */
-typedef enum { TNSK_PREC_FP32 = 0, TNSK_PREC_FP64 = 2 } tnsk_precision;
+/* Arithmetic of the sketches and transforms (the paper fixes none).
+ * FP32: sketches accumulated exactly in integers per batch of entries and rounded to
+ *   FP32 (method 1: every entry quantised to 2^-30 of its batch's sum |x|), FFTs and
+ *   products in FP32 (per-tensor power-of-two scaling), method 2's sketched product
+ *   mat(X_k) V on the tensor cores with a 3-pass TF32 split (FP32 accuracy),
+ *   per-rep estimates and combination in FP64.
+ * BF16: tensors stored as TNSK_BF16 (a stored tensor of another dtype returns
+ *   TNSK_ERR_UNSUPPORTED; grouped tensors are FP32 and unsupported), read as they
+ *   are; method 2's sketched product on BF16 tensor cores (tcgen05 kind::f16) with
+ *   X as stored and V as the sum of three BF16 parts, FP32 accumulation, so the
+ *   result is that of FP32 arithmetic on the BF16 values; everything else as FP32.
+ * FP64: everything in FP64 (for high-dynamic-range sketches). */
+typedef enum { TNSK_PREC_FP32 = 0, TNSK_PREC_BF16 = 1, TNSK_PREC_FP64 = 2 } tnsk_precision;
 
 typedef struct tnsk_ctx tnsk_ctx;
 

@@ -63,6 +63,13 @@ cudaError_t launch_count_sketch(uint64_t seed, uint64_t rep, uint64_t tid, int64
 cudaError_t launch_m1_scatter(const M1Tensor* d_tens, const M1Net* d_nets, const M1Work* d_work, int n_work,
                               const uint32_t* d_tabs, void* d_xs, bool fp64, size_t smem, int max_order,
                               cudaStream_t s);
+// FP32 sketches, privatised bins in fixed point (m1_scatter_fx.cu); vec4: every item's
+// tensor is FP32, 16-byte aligned, last dim a multiple of 4
+cudaError_t launch_m1_scatter_fx(const M1Tensor* d_tens, const M1Net* d_nets, const M1Work* d_work, int n_work,
+                                 const uint32_t* d_tabs, float* d_xs, size_t smem, int max_order, bool vec4,
+                                 cudaStream_t s);
+// entries per CTA batch of the fixed-point kernel for tensors of order <= max_order
+int m1_fx_batch(int max_order, bool vec4 = true);
 cudaError_t launch_m1_spectrum(const M1Tensor* d_tens, const M1Net* d_nets, const OpenMode* d_opens,
                                const int2* d_items, int n_items, const void* d_xs, const void* const* d_tws,
                                void* d_spec, int* d_sexp, double* d_yrep, bool fp64, int max_log2m,

@@ -845,6 +845,178 @@ cudaError_t launch_m2_gemm_tc_rung(int n, const M2Node* nodes, const M2Net* nets
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// BF16 variant (TNSK_PREC_BF16, tensors stored as BF16): the same product with
+// BF16 operands and FP32 accumulation in tensor memory (tcgen05.mma kind::f16).
+// X (row-major BF16, parent mode first, cols a multiple of 8) arrives by TMA as it
+// is stored: per K-chunk of 64 columns a 128 x 64 tile (128-byte rows, 128-byte
+// swizzle). V^T is stored by the V build as three BF16 parts V = Vh + Vm + Vl
+// (each the BF16 rounding of what the previous parts leave; together within
+// 2^-24 of V), so W = X Vh + X Vm + X Vl is the product with V at FP32 precision and
+// X exactly as stored: three MMA passes per chunk, both operands read from shared
+// memory, no conversion of X at all. Half the bytes of X of the FP32 path.
+//   warp 0     producer: four TMA loads per chunk (X, Vh, Vm, Vl) into a ring
+//   warp 1     tensor memory allocation and MMA issue
+//   warps 2-5  epilogue (each the TMEM lane quarter warp % 4)
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kBfKC = 64;                                // columns per chunk (4 MMAs of K = 16)
+constexpr int kBfStages = 2;                             // two CTAs per SM
+constexpr int kBfX = kTM * 128;                          // 128 rows x 128 B
+constexpr int kBfV = kTN * 128;                          // 64 rows x 128 B, one part
+constexpr int kBfStage = kBfX + 3 * kBfV;                // 40 KiB
+constexpr int kBfSmem = kBfStages * kBfStage + 1024;
+// Instruction descriptor: D = F32, A = B = BF16, both K-major, N = 64, M = 128.
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
+                                ((uint32_t)(kTM >> 4) << 24);
+}  // namespace
+
+__global__ void __launch_bounds__(192, 2) m2_gemm_bf16_kernel(const M2Node* __restrict__ nodes,
+                                                              const M2Net* __restrict__ nets,
+                                                              const M2Item* __restrict__ items,
+                                                              float* __restrict__ ws,
+                                                              const unsigned char* __restrict__ tmaps,
+                                                              int* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kBfStages], empty[kBfStages];
+    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ uint32_t tmem_base;
+    unsigned char* ring = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const M2Item it = items[blockIdx.x];
+    const M2Node& nd = nodes[it.node];
+    const M2Net& N = nets[nd.net];
+    const int R = N.R;
+    const int64_t row0 = (int64_t)it.a * kTM;
+    const int rep0 = it.b * kTN;
+    const int64_t npar = nd.npar, cols = nd.cols;
+    const int total_chunks = (int)((cols + kBfKC - 1) / kBfKC);
+    const int cbeg = (int)(((int64_t)total_chunks * it.pad_) / it.begin);
+    const int cend = (int)(((int64_t)total_chunks * (it.pad_ + 1)) / it.begin);
+    const int nch = cend - cbeg;
+    const void* tmx = tmaps + (int64_t)nd.tm_x * 128;
+    const void* tmv[3] = {tmaps + (int64_t)nd.tm_v * 128, tmaps + (int64_t)(nd.tm_v + 1) * 128,
+                          tmaps + (int64_t)(nd.tm_v + 2) * 128};
+
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(kTN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kBfStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&empty[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&done_bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmx) : "memory");
+            for (int p = 0; p < 3; ++p)
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmv[p]) : "memory");
+            for (int c = 0; c < nch && ok; ++c) {
+                const int s = c % kBfStages;
+                if (c >= kBfStages) ok = mbar_wait(smem_addr(&empty[s]), (uint32_t)((c / kBfStages - 1) & 1));
+                if (!ok) break;
+                const int k0 = (cbeg + c) * kBfKC;
+                unsigned char* st = ring + s * kBfStage;
+                const uint32_t bar = smem_addr(&full[s]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBfStage)
+                             : "memory");
+                tma_load_2d(smem_addr(st), tmx, k0, (int)row0, bar);
+                for (int p = 0; p < 3; ++p) tma_load_2d(smem_addr(st + kBfX + p * kBfV), tmv[p], k0, rep0, bar);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            for (int c = 0; c < nch && ok; ++c) {
+                const int s = c % kBfStages;
+                ok = mbar_wait(smem_addr(&full[s]), (uint32_t)((c / kBfStages) & 1));
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned char* st = ring + s * kBfStage;
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int ks = 0; ks < kBfKC / 16; ++ks) {
+                        const uint64_t ad = smem_desc_sw128(smem_addr(st) + ks * 32);
+                        const uint64_t bd = smem_desc_sw128(smem_addr(st + kBfX + p * kBfV) + ks * 32);
+                        const uint32_t acc = (c > 0 || p > 0 || ks > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem),
+                            "l"(ad), "l"(bd), "r"(kIdescBf16), "r"(acc));
+                    }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_addr(&empty[s])));
+                if (c == nch - 1)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_addr(&done_bar)));
+            }
+        }
+        __syncwarp();
+    }
+    if (!ok && lane == 0) atomicExch(err, DEVERR_TIMEOUT);
+
+    if (warp >= 2 && nch > 0) {
+        // epilogue: W^T[rep][row] from TMEM lanes 32 (warp % 4) .. + 31
+        const bool done = mbar_wait(smem_addr(&done_bar), 0u);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!done) {
+            if (lane == 0) atomicExch(err, DEVERR_TIMEOUT);
+        } else {
+            const int q4 = warp & 3;
+            const int64_t row = row0 + q4 * 32 + lane;
+#pragma unroll
+            for (int cc = 0; cc < kTN / 16; ++cc) {
+                uint32_t v[16];
+                const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(cc * 16);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < npar) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int rep = rep0 + cc * 16 + j;
+                        if (rep < R) {
+                            float* dst = &ws[nd.w_off + (int64_t)rep * npar + row];
+                            if (it.begin > 1)
+                                atomicAdd(dst, __uint_as_float(v[j]));  // K split: partial sums
+                            else
+                                *dst = __uint_as_float(v[j]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTN));
+}
+
+cudaError_t launch_m2_gemm_bf16(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items, float* ws,
+                                const unsigned char* tmaps, int* err, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    cudaFuncSetAttribute(m2_gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBfSmem);
+    m2_gemm_bf16_kernel<<<n, 192, kBfSmem, s>>>(nodes, nets, items, ws, tmaps, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_m2_gemm_tc(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items,
                               const uint32_t* tabs, float* ws, const unsigned char* tmaps, int* err, bool stream,
                               cudaStream_t s) {

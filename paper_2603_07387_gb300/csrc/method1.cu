@@ -608,6 +608,13 @@ cudaError_t launch_m1_scatters(const BatchPlan& plan, unsigned char* base, void*
     for (int c = 0; c < M1Plan::kOrderClasses && e == cudaSuccess; ++c)
         e = launch_m1_scatter(tens, nets, work + plan.m1.work_first[c], plan.m1.work_count[c], tabs, xs, fp64,
                               plan.m1.class_smem[c], kClassOrder[c], s);
+    // FP32 privatised items: the fixed-point kernel (four-entry loads, then one-entry)
+    for (int k = 1; k <= 2 && !fp64; ++k)
+        for (int c = 0; c < M1Plan::kOrderClasses && e == cudaSuccess; ++c) {
+            const int l = c + M1Plan::kOrderClasses * k;
+            e = launch_m1_scatter_fx(tens, nets, work + plan.m1.work_first[l], plan.m1.work_count[l], tabs,
+                                     (float*)xs, plan.m1.class_smem[l], kClassOrder[c], k == 1, s);
+        }
     return e;
 }
 

@@ -254,9 +254,23 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
         rsh_reduce<QTMAX>(b, neg, qt, ttab, m, mask);
         return b[0];
     };
+    const bool vbf16 = sizeof(T) == 4 && nd.vbf16;
     auto store = [&](int r, int64_t col, T v) {
         const int64_t dst = v_off + (int64_t)r * cols + col;
-        if (split) {
+        if (vbf16) {
+            // operand of the BF16 product: three BF16 parts, each the rounding of what the
+            // previous ones leave (the differences are exact in FP32)
+            __nv_bfloat16* vb = reinterpret_cast<__nv_bfloat16*>(ws + v_off) + (int64_t)r * cols + col;
+            const float x = (float)v;
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            const float x1 = x - __bfloat162float(h);
+            const __nv_bfloat16 mm = __float2bfloat16_rn(x1);
+            const __nv_bfloat16 l = __float2bfloat16_rn(x1 - __bfloat162float(mm));
+            const int64_t part = (int64_t)R * cols;
+            vb[0] = h;
+            vb[part] = mm;
+            vb[2 * part] = l;
+        } else if (split) {
             // operand of the tensor-core product: TF32 hi part, then its lo part R*cols later
             uint32_t hi, lo;
             tf32_split((float)v, hi, lo);
@@ -538,9 +552,9 @@ __global__ void __launch_bounds__(256) m2_root_kernel(const M2Node* __restrict__
 template <typename T>
 static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void* const* d_tws, cudaStream_t s,
                             Profiler& prof, int* d_err) {
-    static const int kKind[M2_NKINDS] = {TNSK_K_M2_LEAF, TNSK_K_M2_COMPOSE, TNSK_K_M2_VBUILD,
-                                         TNSK_K_M2_GEMM, TNSK_K_M2_GEMM,    TNSK_K_M2_GEMM,
-                                         TNSK_K_M2_GEMM, TNSK_K_M2_SCATTER, TNSK_K_M2_ROOT};
+    static const int kKind[M2_NKINDS] = {TNSK_K_M2_LEAF, TNSK_K_M2_COMPOSE, TNSK_K_M2_VBUILD, TNSK_K_M2_GEMM,
+                                         TNSK_K_M2_GEMM, TNSK_K_M2_GEMM,    TNSK_K_M2_GEMM,   TNSK_K_M2_GEMM,
+                                         TNSK_K_M2_SCATTER, TNSK_K_M2_ROOT};
     const M2Node* nodes = (const M2Node*)(base + P.m2.nodes_off);
     const M2Net* nets = (const M2Net*)(base + P.m2.nets_off);
     const M2Item* items = (const M2Item*)(base + P.m2.items_off);
@@ -582,6 +596,10 @@ static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void*
                     if (sizeof(T) == 4)
                         launch_m2_gemm_tc_rung(n, nodes, nets, its, (float*)ws, base + P.m2.tmaps_off, d_err,
                                                P.m2.rung_smem, s);
+                    break;
+                case M2_GEMM_BF16:  // BF16 nodes of FP32-accumulating plans
+                    if (sizeof(T) == 4)
+                        launch_m2_gemm_bf16(n, nodes, nets, its, (float*)ws, base + P.m2.tmaps_off, d_err, s);
                     break;
                 case M2_GEMM_RUNGF:  // FP32 plans only
                     if (sizeof(T) == 4) {

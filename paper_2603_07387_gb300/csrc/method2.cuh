@@ -69,6 +69,8 @@ struct M2Node {
     int32_t tm_x;     // streaming tensor-core path: tensor-map index of X and of V^T
     int32_t tm_v;
     int32_t r_fact;   // grouped tensor on the factored product (M2_GEMM_RUNGF)
+    int32_t vbf16;    // BF16 product (M2_GEMM_BF16): V^T stored as three BF16 parts
+                      // [3][R][cols] at byte offset 4 v_off, X maps tm_x, parts tm_v .. + 2
     // grouped (rung) tensor, M2_GEMM_RUNG: X(row, col) = sum_s A[i1 ai + j1 aj + s as]
     // B[i2 bi + j2 bj + s bs] with row = i1 rn_i2 + i2, col = j1 rn_j2 + j2
     const float* rA;
@@ -108,9 +110,10 @@ enum M2Kind {
     M2_GEMM_STREAM = 4,
     M2_GEMM_RUNG = 5,
     M2_GEMM_RUNGF = 6,  // grouped tensor in factored form (dims <= 32): it.a first rep, it.b reps
-    M2_WSCATTER = 7,
-    M2_ROOT = 8,
-    M2_NKINDS = 9
+    M2_GEMM_BF16 = 7,   // TNSK_PREC_BF16: BF16 tensors on the kind::f16 tensor-core kernel
+    M2_WSCATTER = 8,
+    M2_ROOT = 9,
+    M2_NKINDS = 10
 };
 
 struct M2Plan {
@@ -140,6 +143,9 @@ tnsk_status run_method2(const BatchPlan& plan, unsigned char* base, bool fp64, c
 cudaError_t launch_m2_gemm_tc(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items,
                               const uint32_t* tabs, float* ws, const unsigned char* tmaps, int* err, bool stream,
                               cudaStream_t s);
+// BF16 tiles (M2_GEMM_BF16): X and the three BF16 parts of V^T by TMA, kind::f16.
+cudaError_t launch_m2_gemm_bf16(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items, float* ws,
+                                const unsigned char* tmaps, int* err, cudaStream_t s);
 // Grouped-tensor tiles (M2_GEMM_RUNG); smem from m2_gemm_rung_smem(bytes of the staged B).
 size_t m2_gemm_rung_smem(size_t b_bytes);
 cudaError_t launch_m2_gemm_tc_rung(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items, float* ws,

@@ -69,16 +69,19 @@ EncodeTiledFn encoder() {
 bool tensor_maps_available() { return encoder() != nullptr; }
 
 // Row-major FP32 matrix [rows][cols] (cols % 4 == 0, 16-byte aligned) as 2-D
-// TMA boxes of 32 columns x box_rows rows, 128-byte swizzle, zero fill outside.
-static bool encode_rowmajor(void* out, const void* base, int64_t rows, int64_t cols, int box_rows) {
+// TMA boxes of 32 columns x box_rows rows, 128-byte swizzle, zero fill outside; with
+// bf16, a BF16 matrix (cols % 8 == 0) in boxes of 64 columns (128-byte rows).
+static bool encode_rowmajor(void* out, const void* base, int64_t rows, int64_t cols, int box_rows,
+                            bool bf16 = false) {
     EncodeTiledFn fn = encoder();
     if (!fn) return false;
     CUtensorMap tm;
     cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t gstride[1] = {(cuuint64_t)cols * 4};
-    cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    cuuint64_t gstride[1] = {(cuuint64_t)cols * (bf16 ? 2 : 4)};
+    cuuint32_t box[2] = {bf16 ? 64u : 32u, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), gdim, gstride, box, estr,
+    CUresult r = fn(&tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                    const_cast<void*>(base), gdim, gstride, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return false;
@@ -94,11 +97,19 @@ tnsk_status finalize_plan(BatchPlan& P, unsigned char* base, std::string& err) {
     const float* ws = (const float*)(base + P.m2.ws_off);
     for (size_t i = 0; i < P.m2.tmap_jobs.size(); ++i) {
         const M2Node& nd = nodes[P.m2.tmap_jobs[i].first];
-        const int what = P.m2.tmap_jobs[i].second;  // 0: X, 1: V^T hi, 2: V^T lo
+        // 0: X, 1: V^T hi, 2: V^T lo (FP32); 3: X, 4 .. 6: the three parts of V^T (BF16)
+        const int what = P.m2.tmap_jobs[i].second;
         const int64_t R = nets[nd.net].R;
-        const bool ok = what == 0 ? encode_rowmajor(maps + i * 128, nd.data, nd.npar, nd.cols, 128)
-                                  : encode_rowmajor(maps + i * 128, ws + nd.v_off + (what - 1) * R * nd.cols, R,
-                                                    nd.cols, 64);
+        bool ok;
+        if (what == 0)
+            ok = encode_rowmajor(maps + i * 128, nd.data, nd.npar, nd.cols, 128);
+        else if (what <= 2)
+            ok = encode_rowmajor(maps + i * 128, ws + nd.v_off + (what - 1) * R * nd.cols, R, nd.cols, 64);
+        else if (what == 3)
+            ok = encode_rowmajor(maps + i * 128, nd.data, nd.npar, nd.cols, 128, true);
+        else
+            ok = encode_rowmajor(maps + i * 128, (const unsigned char*)(ws + nd.v_off) + (what - 4) * R * nd.cols * 2,
+                                 R, nd.cols, 64, true);
         if (!ok) {
             err = "tensor-map encoding failed";
             return TNSK_ERR_CUDA;
@@ -120,7 +131,7 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
         return TNSK_ERR_INVALID;
     }
     const bool fp64 = prm.prec == TNSK_PREC_FP64;
-    if (prm.prec != TNSK_PREC_FP32 && prm.prec != TNSK_PREC_FP64) {
+    if (prm.prec != TNSK_PREC_FP32 && prm.prec != TNSK_PREC_BF16 && prm.prec != TNSK_PREC_FP64) {
         why = "unknown precision";
         return TNSK_ERR_INVALID;
     }
@@ -210,7 +221,7 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
         if (X.rung) {
             I.zero.push_back(0);  // grouped tensor (Sec. 4.1): R((i,j),(k,l)) = sum_s A(i,s,k) B(j,s,l)
             const tnsk_rung& g = *X.rung;
-            if (prm.method != TNSK_ACYCLIC || prm.prec != TNSK_PREC_FP32) {
+            if (prm.method != TNSK_ACYCLIC || prm.prec == TNSK_PREC_FP64) {
                 why = "tensor " + std::to_string(k) + ": grouped (rung) tensors need method 2 in FP32";
                 return TNSK_ERR_UNSUPPORTED;
             }
@@ -399,7 +410,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     int64_t ws_x = 0, ws_w = 0, ws_r = 0, ws_v = 0;  // method-2 workspace parts (elements)
     const bool tma = tensor_maps_available();
     int max_log2m1 = 0, max_log2m2 = 0;
-    std::vector<M1Work> m1w_cls[M1Plan::kOrderClasses];
+    std::vector<M1Work> m1w_cls[M1Plan::kScatterLists];
     struct PendingItem {
         int h, kind;
         M2Item it;
@@ -545,7 +556,17 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                     }
                 }
                 const size_t tab_b = gtab ? 0 : (size_t)TTl * 4;
-                int64_t nrep_priv = (int64_t)(kScatterSmemBudget / (tab_b + bin_b + 16));
+                const int cls = T.order <= 2 ? 0 : (T.order <= 4 ? 1 : (T.order <= 6 ? 2 : 3));
+                static const int kClassOrder[M1Plan::kOrderClasses] = {2, 4, 6, TNSK_MAX_ORDER};
+                // FP32 sketches with privatised bins: the fixed-point kernel, 4-byte integer
+                // bins plus an FP32 accumulator when an item spans more than one batch
+                const int64_t CHp = std::max<int64_t>(8192, 32 * T.O * m);
+                const bool fx_multi = std::min<int64_t>(T.numel, CHp) > m1_fx_batch(kClassOrder[cls]);
+                const size_t bin_fx = (size_t)T.O * m * 4 * (fx_multi ? 2 : 1);
+                // (bins that fit only as FP32 words keep the atomic kernel)
+                const bool fx = !fp64 && tab_b + bin_fx + 16 <= kScatterSmemBudget;
+                const size_t bin_p = fx ? bin_fx : bin_b;
+                int64_t nrep_priv = (int64_t)(kScatterSmemBudget / (tab_b + bin_p + 16));
                 bool priv = nrep_priv >= 1 && T.numel * 4 >= T.O * m;
                 int nrep;
                 if (priv)
@@ -554,10 +575,14 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                     nrep = (int)std::min<int64_t>({(int64_t)R, std::max<int64_t>(1, (int64_t)(kScatterSmemBudget / (tab_b + 16))), 16});
                 // chunks: privatised bins are flushed once per chunk, so a chunk has at least
                 // 32x as many entries as bins (a few percent of flush per update)
-                const int64_t CH = priv ? std::max<int64_t>(8192, 32 * T.O * m) : (gtab ? 65536 : 8192);
-                size_t sm = ((size_t)nrep * tab_b + 15) / 16 * 16 + (priv ? (size_t)nrep * bin_b : 0);
-                const int cls = T.order <= 2 ? 0 : (T.order <= 4 ? 1 : (T.order <= 6 ? 2 : 3));
-                P.m1.class_smem[cls] = std::max(P.m1.class_smem[cls], sm);
+                const int64_t CH = priv ? CHp : (gtab ? 65536 : 8192);
+                size_t sm = ((size_t)nrep * tab_b + 15) / 16 * 16 + (priv ? (size_t)nrep * bin_p : 0);
+                // the fixed-point kernel's four-entry loads: FP32 data, 16-byte aligned, last
+                // dim a multiple of 4 (so are the chunk bounds)
+                const bool vec4 = T.dtype == TNSK_F32 && T.order >= 1 && (T.dims[T.order - 1] & 3) == 0 &&
+                                  ((uintptr_t)T.data & 15) == 0;
+                const int list = cls + M1Plan::kOrderClasses * ((fx && priv) ? (vec4 ? 1 : 2) : 0);
+                P.m1.class_smem[list] = std::max(P.m1.class_smem[list], sm);
                 for (int r0 = 0; r0 < R; r0 += nrep)
                     for (int64_t b0 = 0; b0 < T.numel; b0 += CH) {
                         M1Work w{};
@@ -569,7 +594,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                         w.priv = priv ? ((w.begin == 0 && w.end == T.numel) ? 2 : 1) : 0;
                         w.gtab = gtab ? 1 : 0;
                         w.ltab = ltab ? 1 : 0;
-                        m1w_cls[cls].push_back(w);
+                        m1w_cls[list].push_back(w);
                     }
             }
             const bool large = I.log2m > max_log2m_for(fp64);
@@ -869,12 +894,26 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                     const bool stream = !rung && !fp64 && tma && nd.dtype == TNSK_F32 && nd.A == 1 &&
                                         (nd.cols % 4) == 0 && ((uintptr_t)nd.data % 16) == 0 &&
                                         nd.npar < ((int64_t)1 << 31) && nd.cols < ((int64_t)1 << 31);
+                    // TNSK_PREC_BF16: BF16 tensors in the same layout on the kind::f16 kernel
+                    const bool bf16k = !rung && !fp64 && tma && pr.prec == TNSK_PREC_BF16 &&
+                                       nd.dtype == TNSK_BF16 && nd.A == 1 && (nd.cols % 8) == 0 &&
+                                       ((uintptr_t)nd.data % 16) == 0 && nd.npar < ((int64_t)1 << 31) &&
+                                       nd.cols < ((int64_t)1 << 31);
+                    if (bf16k) {
+                        M2Node& bn = m2nodes.back();
+                        bn.vbf16 = 1;
+                        bn.tm_x = (int32_t)P.m2.tmap_jobs.size();
+                        P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 3});
+                        bn.tm_v = (int32_t)P.m2.tmap_jobs.size();  // parts at tm_v, tm_v + 1, tm_v + 2
+                        for (int part = 0; part < 3; ++part)
+                            P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 4 + part});
+                    }
                     if (rung) {  // V^T hi / lo maps only: X is generated
                         m2nodes.back().tm_v = (int32_t)P.m2.tmap_jobs.size();
                         P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 1});
                         P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 2});
                     }
-                    if (stream) {
+                    if (stream && !bf16k) {
                         m2nodes.back().tm_x = (int32_t)P.m2.tmap_jobs.size();
                         P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 0});
                         m2nodes.back().tm_v = (int32_t)P.m2.tmap_jobs.size();  // hi, then lo at tm_v + 1
@@ -883,7 +922,8 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                     }
                     for (int64_t rt = 0; rt * tile < nd.npar; ++rt)
                         for (int64_t ct = 0; ct * 64 < R; ++ct)
-                            pend.push_back({h, rung ? M2_GEMM_RUNG : (stream ? M2_GEMM_STREAM : M2_GEMM),
+                            pend.push_back({h, rung ? M2_GEMM_RUNG
+                                                    : (bf16k ? M2_GEMM_BF16 : (stream ? M2_GEMM_STREAM : M2_GEMM)),
                                             M2Item{node_idx, (int)rt, (int)ct, 0, 1, 0}});
                 }
             }
@@ -925,15 +965,17 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     if (!fp64 && !pend.empty()) {
         std::vector<int64_t> tiles(P.m2.max_height + 1, 0);
         for (const PendingItem& q : pend)
-            if (q.kind == M2_GEMM || q.kind == M2_GEMM_STREAM || q.kind == M2_GEMM_RUNG) tiles[q.h]++;
+            if (q.kind == M2_GEMM || q.kind == M2_GEMM_STREAM || q.kind == M2_GEMM_RUNG || q.kind == M2_GEMM_BF16)
+                tiles[q.h]++;
         std::vector<PendingItem> out;
         out.reserve(pend.size());
         for (const PendingItem& q : pend) {
-            if (q.kind != M2_GEMM && q.kind != M2_GEMM_STREAM && q.kind != M2_GEMM_RUNG) {
+            if (q.kind != M2_GEMM && q.kind != M2_GEMM_STREAM && q.kind != M2_GEMM_RUNG && q.kind != M2_GEMM_BF16) {
                 out.push_back(q);
                 continue;
             }
-            const int64_t chunks = (m2nodes[q.it.node].cols + 31) / 32;
+            const int64_t kc = q.kind == M2_GEMM_BF16 ? 64 : 32;  // columns per chunk of the kernel
+            const int64_t chunks = (m2nodes[q.it.node].cols + kc - 1) / kc;
             const int64_t slots = 2 * 152, fixed = 6;
             int64_t split = 1, best = -1;
             for (int64_t sp = 1; sp <= std::max<int64_t>(1, std::min<int64_t>(chunks / 4, 64)); ++sp) {
@@ -980,7 +1022,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
 
     // ---- stage descriptors
     std::vector<unsigned char>& H = P.host_desc;
-    for (int c = 0; c < M1Plan::kOrderClasses; ++c) {
+    for (int c = 0; c < M1Plan::kScatterLists; ++c) {
         P.m1.work_first[c] = (int)m1w.size();
         P.m1.work_count[c] = (int)m1w_cls[c].size();
         m1w.insert(m1w.end(), m1w_cls[c].begin(), m1w_cls[c].end());

@@ -50,12 +50,16 @@ struct M1Plan {
     size_t xs_off = 0, spec_off = 0, sexp_off = 0;
     int64_t xs_count = 0;  // sketch entries of all networks (FP32 or FP64)
     int n_work = 0, n_items = 0;
-    // scatter work items by tensor order class (order <= 2, 4, 6, 12): one launch per
-    // class with its own unrolled width and shared-memory size
+    // scatter work items by tensor order class (order <= 2, 4, 6, 12) and kernel: one
+    // launch per list with its own unrolled width and shared-memory size. List
+    // c + kOrderClasses * k: k = 0 the FP32 / FP64 atomic kernel (FP64 sketches, and
+    // items whose bins go straight to global memory), k = 1 / 2 the fixed-point kernel
+    // (FP32 sketches with privatised bins; 1: four entries per 16-byte load, 2: one)
     static constexpr int kOrderClasses = 4;
-    int work_first[kOrderClasses] = {0, 0, 0, 0};
-    int work_count[kOrderClasses] = {0, 0, 0, 0};
-    size_t class_smem[kOrderClasses] = {16, 16, 16, 16};
+    static constexpr int kScatterLists = 3 * kOrderClasses;
+    int work_first[kScatterLists] = {};
+    int work_count[kScatterLists] = {};
+    size_t class_smem[kScatterLists] = {16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16};
     int max_log2m = 0;
     // items of the warp-per-item spectrum kernel, by log2 m = 6 + slot, stored after
     // the n_items items of the block kernel

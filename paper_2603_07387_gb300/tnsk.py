@@ -31,7 +31,7 @@ F64, F32, BF16 = 0, 1, 2
 GENERAL, ACYCLIC, CROSSCORR = 1, 2, 3  # tnsk_method (CROSSCORR: the earlier cross-correlation estimator)
 KERNEL_KINDS = ("tables", "m1_scatter", "m1_spectrum", "m2_leaf", "m2_compose", "m2_vbuild", "m2_gemm",
                 "m2_root", "combine", "m2_scatter", "pairs", "normalize")
-PREC_FP32, PREC_FP64 = 0, 2
+PREC_FP32, PREC_BF16, PREC_FP64 = 0, 1, 2
 
 # exported symbols declared in include/tnsk.h
 SYMBOLS = (

@@ -46,6 +46,31 @@ def oracle_estimate(spec, params, torch_dtype):
     return y, s
 
 
+def sketch_tol(X, edges, open_modes, m, bins, signs, prec):
+    """Per-bin bound on |GPU sketch - oracle sketch| for tnsk_m1_sketch's layout.
+    FP64: 1e-12 of the sum of the bin's |entries|. FP32: 1e-6 of that sum (rounding of
+    FP32 sums) plus the fixed-point quantisation of the privatised bins: every entry
+    is rounded to a multiple of 2^-S with sum|x| 2^S <= 2^30 over its batch, an error
+    of at most 2^-30 sum|x| of the batch, bounded here by 2^-30 ||X_k||_1 of its
+    tensor, times the number of entries the bin receives."""
+    scale = oracle.m1_sketch(X, edges, open_modes, m, bins, signs, abs_mode=True)
+    if prec == tnsk.PREC_FP64:
+        return 1e-12 * np.maximum(scale, 1e-300)
+    ones = [np.ones_like(np.asarray(x, dtype=np.float64)) for x in X]
+    counts = oracle.m1_sketch(ones, edges, open_modes, m, bins, signs, abs_mode=True)
+    quant = np.zeros_like(scale)
+    off = 0
+    dims = [d for x in X for d in np.shape(x)]
+    mode0 = 0
+    for x in X:
+        q = np.ndim(x)
+        O = int(np.prod([dims[g] for g in open_modes if mode0 <= g < mode0 + q])) if q else 1
+        quant[:, off:off + O * m] = 2.0**-30 * np.abs(np.asarray(x, dtype=np.float64)).sum()
+        off += O * m
+        mode0 += q
+    return 1e-6 * np.maximum(scale, 1e-300) + counts * quant
+
+
 def assert_parity(gpu_per_rep, orc_y, orc_s, tol, what=""):
     """|y_gpu - y_oracle| <= tol * S per rep and entry, S the oracle's cancellation-aware
     scale (sum of the magnitudes the estimate is built from)."""

@@ -11,7 +11,7 @@ import oracle
 from paper_2603_07387_gb300 import tnsk
 from paper_2603_07387_gb300 import workloads as W
 
-from gpu_common import TOL, assert_parity, gpu_estimate, gpu_network, oracle_estimate, rounded
+from gpu_common import sketch_tol, TOL, assert_parity, gpu_estimate, gpu_network, oracle_estimate, rounded
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -68,8 +68,8 @@ def test_method1_sketch_per_bin(ctx, prec, m):
         ctx.m1_sketch(net, tnsk.Params(m=m, reps=R, seed=seed, prec=prec), x)
         ctx.sync()
         got = x.double().cpu().numpy()
-        tol = 1e-12 if prec == tnsk.PREC_FP64 else 1e-6
-        assert np.all(np.abs(got - want) <= tol * np.maximum(scale, 1e-300)), spec.name
+        bound = sketch_tol(X, spec.edges, spec.open, m, bins, signs, prec)
+        assert np.all(np.abs(got - want) <= bound), spec.name
 
 
 # ---------------------------------------------------------------- a3 + a4 method 1
@@ -409,8 +409,8 @@ def test_entry_sharded_streams_sum_to_the_whole(ctx, prec):
         want = oracle.m1_sketch(mine, edges, open_, p.m, bins, signs)
         scale = oracle.m1_sketch(Xr, edges, open_, p.m, bins, signs, abs_mode=True)
         got = st.sketches().double().cpu().numpy()[: want.size].reshape(want.shape)
-        tol = 1e-12 if prec == tnsk.PREC_FP64 else 1e-6
-        assert np.all(np.abs(got - want) <= tol * np.maximum(scale, 1e-300)), f"part {part}"
+        bound = sketch_tol(Xr, edges, open_, p.m, bins, signs, prec)
+        assert np.all(np.abs(got - want) <= bound), f"part {part}"
         streams.append(st)
         outs.append(out)
         pers.append(per)
