@@ -333,6 +333,9 @@ tnsk_status tnsk_estimate_static(const tnsk_network* net, const tnsk_params* par
  * SM over all SMs: full occupancy), the ceiling of privatised scatter-add. Runs on the ctx
  * stream, waits for it, and writes updates per second to *updates_per_s. */
 tnsk_status tnsk_probe_shared_atomics(tnsk_ctx* ctx, double* updates_per_s);
+/* The same for 32-bit integer shared-memory adds whose result is unused (the update
+ * of the fixed-point method-1 scatter, TNSK_PREC_FP32): updates per second. */
+tnsk_status tnsk_probe_shared_int_adds(tnsk_ctx* ctx, double* updates_per_s);
 
 /* ---- Exact contraction of pairs of tensors (the normalisations of Sec. 4.1:
  * group two tensors into one with their shared contractions summed exactly; a
@@ -416,6 +419,16 @@ tnsk_status tnsk_features(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_par
  * candidate's) when no candidate meets the target. */
 tnsk_status tnsk_choose_params(tnsk_ctx* ctx, const tnsk_network* net, double target_err, tnsk_mlp* mlp,
                                tnsk_params* inout, double* predicted_err);
+
+/* Fault injection for tests (the paper has no counterpart): what = 1 makes the next
+ * launch sequence of this ctx run method 2's TMA-fed tensor-core products (the FP32
+ * streaming kernel and the BF16 kernel) with producers that issue no loads, so every
+ * consumer's bounded wait (at most about 2^31 SM clock cycles) runs out and records
+ * TNSK_ERR_TIMEOUT for tnsk_sync; no copy or MMA is left in flight and the ctx stays
+ * usable. One-shot (cleared by that launch sequence); what = 0 clears it. Plans
+ * replayed from a CUDA graph keep the setting they were captured with. Errors:
+ * TNSK_ERR_INVALID for a NULL ctx or another value. */
+tnsk_status tnsk_debug_inject(tnsk_ctx* ctx, int32_t what);
 
 /* Wait for the ctx's stream; returns the first deferred device error, if any. */
 tnsk_status tnsk_sync(tnsk_ctx* ctx);

@@ -330,9 +330,11 @@ static tnsk_status launch_plan(tnsk_ctx* ctx, const BatchPlan& plan, unsigned ch
         const cudaError_t e1 = cudaEventRecord(ctx->ev_join, ctx->side);
         if (st == TNSK_OK && e1 != cudaSuccess) st = cuda_fail(ctx, e1, "cudaEventRecord");
     }
-    if (st == TNSK_OK && plan.m2.n_nets && !sketch_out)
+    if (st == TNSK_OK && plan.m2.n_nets && !sketch_out) {
         st = run_method2(plan, base, fp64, fp64 ? (const void* const*)ctx->d_tw64 : (const void* const*)ctx->d_tw32, s,
-                         pf, ctx->d_err, ctx->last_error);
+                         pf, ctx->d_err, ctx->last_error, ctx->inject);
+        ctx->inject = 0;  // one-shot
+    }
     if (fork) {
         const cudaError_t e2 = cudaStreamWaitEvent(s, ctx->ev_join, 0);
         if (st == TNSK_OK && e2 != cudaSuccess) st = cuda_fail(ctx, e2, "cudaStreamWaitEvent");
@@ -397,6 +399,12 @@ struct tnsk_plan {
     cudaGraphExec_t graph = nullptr;  // the launch sequence, captured on the second run
     bool no_graph = false;            // capture failed or is not possible: launch directly
 };
+
+tnsk_status tnsk_debug_inject(tnsk_ctx* ctx, int32_t what) {
+    if (!ctx || what < 0 || what > 1) return TNSK_ERR_INVALID;
+    ctx->inject = what;
+    return TNSK_OK;
+}
 
 tnsk_status tnsk_profile(tnsk_ctx* ctx, int32_t enable) {
     if (!ctx) return TNSK_ERR_INVALID;
@@ -669,6 +677,22 @@ tnsk_status tnsk_probe_shared_atomics(tnsk_ctx* ctx, double* updates_per_s) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(sink);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "shared-atomic probe");
+    return TNSK_OK;
+}
+
+tnsk_status tnsk_probe_shared_int_adds(tnsk_ctx* ctx, double* updates_per_s) {
+    if (!updates_per_s) return TNSK_ERR_INVALID;
+    tnsk_status st = check_ctx(ctx);
+    if (st != TNSK_OK) return st;
+    float* sink = nullptr;
+    if (cudaMalloc((void**)&sink, sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, TNSK_ERR_OOM, "probe allocation failed");
+    }
+    cudaError_t e = run_probe_shared_int_adds(sink, ctx->stream, updates_per_s);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(sink);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "shared integer-add probe");
     return TNSK_OK;
 }
 

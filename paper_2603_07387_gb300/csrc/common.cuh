@@ -152,6 +152,23 @@ struct M1Diag {
     int64_t n;
 };
 
+// Row-sorted sketch of one (tensor, rep) (m1_rowsort.cu): the tensor's rows in the order
+// of their leading-mode bins, packed row << 15 | negative << 14 | bin, at order_off
+// (words) in the plan's scratch.
+struct M1RowSort {
+    int32_t tensor;  // index into the method-1 tensor descriptors
+    int32_t net;     // index into the method-1 network descriptors
+    int32_t rep;     // repetition within the call
+    int32_t pad_;
+    int64_t order_off;
+};
+
+// One CTA of the row-sorted sketch: columns [512 strip, 512 strip + 512) of the rows at
+// sorted positions [k_lo, k_hi) of M1RowSort rs.
+struct M1RowItem {
+    int32_t rs, strip, k_lo, k_hi;
+};
+
 struct M1Net {
     int64_t m;
     int64_t L;        // table words per rep

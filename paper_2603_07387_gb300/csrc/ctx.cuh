@@ -28,6 +28,8 @@ struct tnsk_ctx {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     tnsk::Profiler prof;
+    // fault injection for tests (tnsk_debug_inject): consumed by the next launch sequence
+    int inject = 0;
 };
 
 namespace tnsk {

@@ -87,5 +87,7 @@ cudaError_t launch_m1_spectrum_warp(const M1Tensor* d_tens, const M1Net* d_nets,
 cudaError_t launch_combine(const CombineItem* d_items, int n_items, const double* d_yrep, cudaStream_t s);
 // measurement aid: random-bin FP32 shared-memory atomic adds per second (waits for s)
 cudaError_t run_probe_shared_atomics(float* sink, cudaStream_t s, double* updates_per_s);
+// measurement aid: random-bin 32-bit integer shared-memory adds per second (waits for s)
+cudaError_t run_probe_shared_int_adds(float* sink, cudaStream_t s, double* updates_per_s);
 
 }  // namespace tnsk

@@ -32,7 +32,8 @@ constexpr int kABytes = kTM * kKC * 4;                   // 16 KiB
 constexpr int kBBytes = kTN * kKC * 4;                   // 8 KiB
 constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;   // hi + lo of both
 constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
-constexpr uint32_t kWaitLimit = 1u << 22;                // bounded mbarrier waits
+constexpr uint32_t kWaitLimit = 1u << 22;                // bounded mbarrier waits: polls
+constexpr long long kWaitCycles = 1ll << 31;             // and SM clock cycles (~1 s at 2 GHz)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -53,7 +54,9 @@ constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTN
                             ((uint32_t)(kTM >> 4) << 24);
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
     for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        if ((it & 1023u) == 1023u && clock64() - t0 > kWaitCycles) return false;
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -329,7 +332,7 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
                                                                    const M2Item* __restrict__ items,
                                                                    float* __restrict__ ws,
                                                                    const unsigned char* __restrict__ tmaps,
-                                                                   int* __restrict__ err) {
+                                                                   int* __restrict__ err, int inject) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t raw_full[kRawStages], raw_empty[kRawStages];
     __shared__ __align__(8) uint64_t tm_full[kTmStages], tm_empty[kTmStages];
@@ -376,8 +379,9 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
     bool ok = true;
 
     if (warp == 0) {
-        // ---------------- producer (one thread)
-        if (lane == 0) {
+        // ---------------- producer (one thread); with a test's injected fault it issues no
+        // loads, so the consumers' bounded waits run out (nothing is left in flight)
+        if (lane == 0 && !inject) {
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmx) : "memory");
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvh) : "memory");
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvl) : "memory");
@@ -876,7 +880,7 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_bf16_kernel(const M2Node* __re
                                                               const M2Item* __restrict__ items,
                                                               float* __restrict__ ws,
                                                               const unsigned char* __restrict__ tmaps,
-                                                              int* __restrict__ err) {
+                                                              int* __restrict__ err, int inject) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kBfStages], empty[kBfStages];
     __shared__ __align__(8) uint64_t done_bar;
@@ -918,7 +922,7 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_bf16_kernel(const M2Node* __re
     bool ok = true;
 
     if (warp == 0) {
-        if (lane == 0) {
+        if (lane == 0 && !inject) {  // a test's injected fault: no loads (the waits below run out)
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmx) : "memory");
             for (int p = 0; p < 3; ++p)
                 asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmv[p]) : "memory");
@@ -1010,20 +1014,20 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_bf16_kernel(const M2Node* __re
 }
 
 cudaError_t launch_m2_gemm_bf16(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items, float* ws,
-                                const unsigned char* tmaps, int* err, cudaStream_t s) {
+                                const unsigned char* tmaps, int* err, int inject, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     cudaFuncSetAttribute(m2_gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBfSmem);
-    m2_gemm_bf16_kernel<<<n, 192, kBfSmem, s>>>(nodes, nets, items, ws, tmaps, err);
+    m2_gemm_bf16_kernel<<<n, 192, kBfSmem, s>>>(nodes, nets, items, ws, tmaps, err, inject);
     return cudaGetLastError();
 }
 
 cudaError_t launch_m2_gemm_tc(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items,
                               const uint32_t* tabs, float* ws, const unsigned char* tmaps, int* err, bool stream,
-                              cudaStream_t s) {
+                              int inject, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     if (stream) {
         cudaFuncSetAttribute(m2_gemm_tc_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem);
-        m2_gemm_tc_stream_kernel<<<n, 192, kStreamSmem, s>>>(nodes, nets, items, ws, tmaps, err);
+        m2_gemm_tc_stream_kernel<<<n, 192, kStreamSmem, s>>>(nodes, nets, items, ws, tmaps, err, inject);
     } else {
         cudaFuncSetAttribute(m2_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
         m2_gemm_tc_kernel<<<n, 128, kSmemBytes, s>>>(nodes, nets, items, tabs, ws, err);

@@ -615,6 +615,8 @@ cudaError_t launch_m1_scatters(const BatchPlan& plan, unsigned char* base, void*
             e = launch_m1_scatter_fx(tens, nets, work + plan.m1.work_first[l], plan.m1.work_count[l], tabs,
                                      (float*)xs, plan.m1.class_smem[l], kClassOrder[c], k == 1, s);
         }
+    // large FP32 tensors streamed from HBM: the row-sorted form
+    if (e == cudaSuccess && !fp64) e = launch_m1_rowsort(plan, base, (float*)xs, s);
     return e;
 }
 

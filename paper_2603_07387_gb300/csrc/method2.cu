@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(256) m2_root_kernel(const M2Node* __restrict__
 // ---------------------------------------------------------------------------
 template <typename T>
 static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void* const* d_tws, cudaStream_t s,
-                            Profiler& prof, int* d_err) {
+                            Profiler& prof, int* d_err, int inject) {
     static const int kKind[M2_NKINDS] = {TNSK_K_M2_LEAF, TNSK_K_M2_COMPOSE, TNSK_K_M2_VBUILD, TNSK_K_M2_GEMM,
                                          TNSK_K_M2_GEMM, TNSK_K_M2_GEMM,    TNSK_K_M2_GEMM,   TNSK_K_M2_GEMM,
                                          TNSK_K_M2_SCATTER, TNSK_K_M2_ROOT};
@@ -588,7 +588,7 @@ static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void*
                 case M2_GEMM_STREAM:
                     if (sizeof(T) == 4)  // FP32: tensor cores (3-pass TF32 split)
                         launch_m2_gemm_tc(n, nodes, nets, its, tabs, (float*)ws, base + P.m2.tmaps_off, d_err,
-                                          kind == M2_GEMM_STREAM, s);
+                                          kind == M2_GEMM_STREAM, inject, s);
                     else
                         m2_gemm_kernel<T><<<n, 256, 0, s>>>(nodes, nets, its, tabs, ws);
                     break;
@@ -599,7 +599,8 @@ static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void*
                     break;
                 case M2_GEMM_BF16:  // BF16 nodes of FP32-accumulating plans
                     if (sizeof(T) == 4)
-                        launch_m2_gemm_bf16(n, nodes, nets, its, (float*)ws, base + P.m2.tmaps_off, d_err, s);
+                        launch_m2_gemm_bf16(n, nodes, nets, its, (float*)ws, base + P.m2.tmaps_off, d_err, inject,
+                                            s);
                     break;
                 case M2_GEMM_RUNGF:  // FP32 plans only
                     if (sizeof(T) == 4) {
@@ -624,9 +625,9 @@ static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void*
 }
 
 tnsk_status run_method2(const BatchPlan& plan, unsigned char* base, bool fp64, const void* const* d_tws,
-                        cudaStream_t s, Profiler& prof, int* d_err, std::string& err) {
-    cudaError_t e = fp64 ? run_m2_t<double>(plan, base, d_tws, s, prof, d_err)
-                         : run_m2_t<float>(plan, base, d_tws, s, prof, d_err);
+                        cudaStream_t s, Profiler& prof, int* d_err, std::string& err, int inject) {
+    cudaError_t e = fp64 ? run_m2_t<double>(plan, base, d_tws, s, prof, d_err, inject)
+                         : run_m2_t<float>(plan, base, d_tws, s, prof, d_err, inject);
     if (e != cudaSuccess) {
         err = std::string("method 2 launch: ") + cudaGetErrorString(e);
         return TNSK_ERR_CUDA;

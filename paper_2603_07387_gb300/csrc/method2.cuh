@@ -138,14 +138,16 @@ struct M2Plan {
 
 struct BatchPlan;
 struct Profiler;
+// inject (tests only, tnsk_debug_inject): the tensor-core products' TMA producers issue
+// no loads, so their consumers' bounded waits run out and report DEVERR_TIMEOUT
 tnsk_status run_method2(const BatchPlan& plan, unsigned char* base, bool fp64, const void* const* d_tws,
-                        cudaStream_t s, Profiler& prof, int* d_err, std::string& err);
+                        cudaStream_t s, Profiler& prof, int* d_err, std::string& err, int inject = 0);
 cudaError_t launch_m2_gemm_tc(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items,
                               const uint32_t* tabs, float* ws, const unsigned char* tmaps, int* err, bool stream,
-                              cudaStream_t s);
+                              int inject, cudaStream_t s);
 // BF16 tiles (M2_GEMM_BF16): X and the three BF16 parts of V^T by TMA, kind::f16.
 cudaError_t launch_m2_gemm_bf16(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items, float* ws,
-                                const unsigned char* tmaps, int* err, cudaStream_t s);
+                                const unsigned char* tmaps, int* err, int inject, cudaStream_t s);
 // Grouped-tensor tiles (M2_GEMM_RUNG); smem from m2_gemm_rung_smem(bytes of the staged B).
 size_t m2_gemm_rung_smem(size_t b_bytes);
 cudaError_t launch_m2_gemm_tc_rung(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items, float* ws,

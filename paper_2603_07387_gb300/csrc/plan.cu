@@ -407,6 +407,9 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     int64_t tab_words = 0, yrep_n = 0, xs_n = 0, spec_n = 0, sexp_n = 0, lspec_n = 0;
     std::vector<int4> lfft, lprod;  // large-m method 1: (net, rep, sketch), (net, rep, first bin, bins)
     std::vector<M1Diag> diags;      // diagonal copy tensors (WLOG 1)
+    std::vector<M1RowSort> rsorts;  // row-sorted sketches of large tensors
+    std::vector<M1RowItem> ritems;
+    int64_t rs_words = 0;           // their sorted-row scratch (uint32 words)
     int64_t ws_x = 0, ws_w = 0, ws_r = 0, ws_v = 0;  // method-2 workspace parts (elements)
     const bool tma = tensor_maps_available();
     int max_log2m1 = 0, max_log2m2 = 0;
@@ -533,6 +536,30 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 const M1Tensor& T = m1t[nb.t0 + k];
                 if (I.diag[k] && T.numel > 0) diags.push_back(M1Diag{nb.t0 + k, (int)m1n.size(), I.dims[I.mode_off[k]]});
                 if (T.numel == 0 || T.O == 0 || I.zero[k]) continue;  // all-zero tensors add nothing
+                // Large FP32 tensors (far beyond L2) with a contracted leading mode: the
+                // row-sorted form, one pass over the tensor per rep (m1_rowsort.cu)
+                if (!fp64 && !I.diag[k] && T.dtype == TNSK_F32 && T.O == 1 && T.order >= 2 && T.tab[0] >= 0 &&
+                    T.numel >= ((int64_t)1 << 24) && T.dims[0] >= 1024 && T.dims[0] <= (1 << 17) &&
+                    m <= (1 << 14) && R <= 64) {
+                    bool all_ctr = true;
+                    for (int d = 1; d < T.order; ++d) all_ctr = all_ctr && (T.tab[d] >= 0 || T.dims[d] == 1);
+                    const int64_t rl = T.numel / T.dims[0];
+                    if (all_ctr && rl >= 512) {
+                        const int64_t strips = (rl + 511) / 512, rows = 1024;
+                        for (int r = 0; r < R; ++r) {
+                            const int id = (int)rsorts.size();
+                            rsorts.push_back(M1RowSort{nb.t0 + k, (int)m1n.size(), r, 0, rs_words});
+                            rs_words += (T.dims[0] + 63) / 64 * 64;
+                            for (int64_t st = 0; st < strips; ++st)
+                                for (int64_t k0 = 0; k0 < T.dims[0]; k0 += rows)
+                                    ritems.push_back(M1RowItem{id, (int)st, (int)k0,
+                                                               (int)std::min<int64_t>(T.dims[0], k0 + rows)});
+                        }
+                        P.m1.rs_max_m = std::max<int64_t>(P.m1.rs_max_m, m);
+                        P.m1.rs_max_rows = std::max<int>(P.m1.rs_max_rows, (int)std::min<int64_t>(rows, T.dims[0]));
+                        continue;
+                    }
+                }
                 int64_t TT = 0;
                 for (int d = 0; d < T.order; ++d)
                     if (T.tab[d] >= 0) TT += T.dims[d];
@@ -1036,6 +1063,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     }
     size_t o_open = stage(H, opens), o_items = stage(H, m1items), o_comb = stage(H, comb);
     size_t o_lfft = stage(H, lfft), o_lprod = stage(H, lprod), o_diag = stage(H, diags);
+    size_t o_rs = stage(H, rsorts), o_ritems = stage(H, ritems);
     size_t o_m2nodes = stage(H, m2nodes), o_m2n = stage(H, m2n), o_m2items = stage(H, m2items);
     std::vector<unsigned char> tmap_space(P.m2.tmap_jobs.size() * 128, 0);
     size_t o_tmaps = stage(H, tmap_space);
@@ -1050,6 +1078,10 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     P.m1.lprod_off = P.desc_off + o_lprod;
     P.m1.n_lfft = (int)lfft.size();
     P.m1.n_lprod = (int)lprod.size();
+    P.m1.rs_off = P.desc_off + o_rs;
+    P.m1.rs_items_off = P.desc_off + o_ritems;
+    P.m1.n_rs = (int)rsorts.size();
+    P.m1.n_rs_items = (int)ritems.size();
     P.m1.diag_off = P.desc_off + o_diag;
     P.m1.n_diag = (int)diags.size();
     for (const M1Diag& d : diags) P.m1.diag_most = std::max(P.m1.diag_most, d.n * (int64_t)m1n[d.net].R);
@@ -1070,6 +1102,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     P.m1.spec_off = P.arena.take((size_t)spec_n * 2 * acc);
     P.m1.lspec_off = P.arena.take((size_t)lspec_n * 2 * acc);
     P.m1.sexp_off = P.arena.take((size_t)sexp_n * sizeof(int));
+    P.m1.rs_scratch_off = P.arena.take((size_t)rs_words * sizeof(uint32_t));
     P.m1.n_nets = (int)m1n.size();
     P.m1.n_work = (int)m1w.size();
     P.m1.n_items = n_block_items;

@@ -69,6 +69,12 @@ struct M1Plan {
     // large-m items (two-pass FFT, then the product over bin blocks) and their spectra
     size_t lfft_off = 0, lprod_off = 0, lspec_off = 0;
     int n_lfft = 0, n_lprod = 0;
+    // row-sorted sketches of large tensors (m1_rowsort.cu): per (tensor, rep) descriptors,
+    // CTA items and the sorted-row scratch; shared memory of m floats
+    size_t rs_off = 0, rs_items_off = 0, rs_scratch_off = 0;
+    int n_rs = 0, n_rs_items = 0;
+    int64_t rs_max_m = 0;
+    int rs_max_rows = 0;  // largest item's row count
     // diagonal copy tensors (WLOG 1): one item each
     size_t diag_off = 0;
     int n_diag = 0;
@@ -101,6 +107,8 @@ cudaError_t launch_m1_updates(const BatchPlan& plan, unsigned char* base, int64_
                               const int64_t* index, const double* delta, bool fp64, int* err, cudaStream_t s);
 cudaError_t launch_m1_spectra(const BatchPlan& plan, unsigned char* base, const void* xs, const void* const* tws,
                               bool fp64, cudaStream_t s);
+// Row-sorted sketches of the plan's large FP32 tensors added into xs (m1_rowsort.cu).
+cudaError_t launch_m1_rowsort(const BatchPlan& plan, unsigned char* base, float* xs, cudaStream_t s);
 // Sketches of the plan's diagonal copy tensors (WLOG 1) added into xs (every rep).
 cudaError_t launch_m1_diag(const BatchPlan& plan, unsigned char* base, void* xs, bool fp64, cudaStream_t s);
 

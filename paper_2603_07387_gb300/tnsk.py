@@ -49,8 +49,10 @@ SYMBOLS = (
     "tnsk_plan_destroy",
     "tnsk_profile",
     "tnsk_profile_read",
+    "tnsk_debug_inject",
     "tnsk_sync",
     "tnsk_probe_shared_atomics",
+    "tnsk_probe_shared_int_adds",
     "tnsk_combine",
     "tnsk_stream_create",
     "tnsk_stream_update",
@@ -173,6 +175,8 @@ def load_library(path: str = LIB_PATH):
     L.tnsk_profile.argtypes = [vp, i32]
     L.tnsk_profile_read.restype = i32
     L.tnsk_profile_read.argtypes = [vp, vp, vp]
+    L.tnsk_debug_inject.restype = i32
+    L.tnsk_debug_inject.argtypes = [vp, i32]
     L.tnsk_sync.restype = i32
     L.tnsk_sync.argtypes = [vp]
     f32p, dp = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)
@@ -210,6 +214,8 @@ def load_library(path: str = LIB_PATH):
     L.tnsk_stream_destroy.argtypes = [vp]
     L.tnsk_probe_shared_atomics.restype = i32
     L.tnsk_probe_shared_atomics.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.tnsk_probe_shared_int_adds.restype = i32
+    L.tnsk_probe_shared_int_adds.argtypes = [vp, vp]
     L.tnsk_status_string.restype = ctypes.c_char_p
     L.tnsk_status_string.argtypes = [i32]
     L.tnsk_last_error.restype = ctypes.c_char_p
@@ -706,6 +712,11 @@ class Context:
     def profile(self, enable: bool = True):
         self._check(self.lib.tnsk_profile(self.h, 1 if enable else 0))
 
+    def debug_inject(self, what: int = 1):
+        """Tests only: the next launch sequence's TMA-fed tensor-core products issue no
+        loads, so their bounded waits run out (tnsk_sync then reports TNSK_ERR_TIMEOUT)."""
+        self._check(self.lib.tnsk_debug_inject(self.h, int(what)))
+
     def profile_read(self):
         """{kernel kind: (total ms, launches)} since the last read (waits for the stream)."""
         ms = (ctypes.c_double * len(KERNEL_KINDS))()
@@ -752,6 +763,12 @@ class Context:
         r = ctypes.c_double(0.0)
         self._check(self.lib.tnsk_probe_shared_atomics(self.h, ctypes.byref(r)))
         return r.value
+
+    def probe_shared_int_adds(self) -> float:
+        """Random-bin 32-bit integer shared-memory adds per second (measurement aid)."""
+        v = ctypes.c_double(0.0)
+        self._check(self.lib.tnsk_probe_shared_int_adds(self.h, ctypes.byref(v)))
+        return v.value
 
     def sync(self):
         self._check(self.lib.tnsk_sync(self.h))
