@@ -159,14 +159,18 @@ struct M1RowSort {
     int32_t tensor;  // index into the method-1 tensor descriptors
     int32_t net;     // index into the method-1 network descriptors
     int32_t rep;     // repetition within the call
-    int32_t pad_;
+    int32_t strips;  // column strips of 512
     int64_t order_off;
 };
 
-// One CTA of the row-sorted sketch: columns [512 strip, 512 strip + 512) of the rows at
-// sorted positions [k_lo, k_hi) of M1RowSort rs.
+// One CTA of the row-sorted sketch: `count` consecutive (strip, sorted row) positions of
+// the concatenation over all M1RowSort entries (strips in order, sorted rows within a
+// strip), starting at row k of strip `strip` of entry rs. The planner splits the whole
+// concatenation into one equal part per CTA slot.
 struct M1RowItem {
-    int32_t rs, strip, k_lo, k_hi;
+    int32_t rs, strip, k;
+    int32_t pad_;
+    int64_t count;
 };
 
 struct M1Net {

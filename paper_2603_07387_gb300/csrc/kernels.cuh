@@ -68,6 +68,8 @@ cudaError_t launch_m1_scatter(const M1Tensor* d_tens, const M1Net* d_nets, const
 cudaError_t launch_m1_scatter_fx(const M1Tensor* d_tens, const M1Net* d_nets, const M1Work* d_work, int n_work,
                                  const uint32_t* d_tabs, float* d_xs, size_t smem, int max_order, bool vec4,
                                  cudaStream_t s);
+// CTA slots of the row-sorted sketch kernel on the current device (SMs x CTAs per SM)
+int64_t m1_rowsort_slots();
 // entries per CTA batch of the fixed-point kernel for tensors of order <= max_order
 int m1_fx_batch(int max_order, bool vec4 = true);
 cudaError_t launch_m1_spectrum(const M1Tensor* d_tens, const M1Net* d_nets, const OpenMode* d_opens,

@@ -92,77 +92,117 @@ __global__ void __launch_bounds__(1024) m1_rowsort_order_kernel(const M1Tensor* 
     }
 }
 
-// One item: a strip of 512 columns of one (tensor, rep), sorted rows [k_lo, k_hi).
-__global__ void __launch_bounds__(kRsThreads) m1_rowsort_kernel(const M1Tensor* __restrict__ tens,
-                                                                const M1Net* __restrict__ nets,
-                                                                const M1RowSort* __restrict__ rs,
-                                                                const M1RowItem* __restrict__ items,
-                                                                const uint32_t* __restrict__ tabs,
-                                                                const uint32_t* __restrict__ scratch,
-                                                                float* __restrict__ xs) {
-    extern __shared__ float x_sh[];  // [m]
+// One CTA slot: `count` consecutive (strip, sorted row) positions of the concatenation
+// over the entries (see M1RowItem). The 16 warps of the CTA cover the 512 columns of one
+// strip and walk the same rows, whose order words are staged in shared memory in
+// chunks of kChunk; a lane's register sum is added to the shared sketch when the row
+// bin changes and at the end of a chunk; the shared sketch goes to the entry's global
+// sketch when the walk leaves the entry.
+constexpr int kChunk = 512;
+
+__global__ void __launch_bounds__(kRsThreads, 2) m1_rowsort_kernel(const M1Tensor* __restrict__ tens,
+                                                                   const M1Net* __restrict__ nets,
+                                                                   const M1RowSort* __restrict__ rs,
+                                                                   const M1RowItem* __restrict__ items,
+                                                                   const uint32_t* __restrict__ tabs,
+                                                                   const uint32_t* __restrict__ scratch,
+                                                                   float* __restrict__ xs) {
+    extern __shared__ float x_sh[];  // [max m], then kChunk order words
+    uint32_t* s_ord = nullptr;  // after the entry's m floats
     const M1RowItem it = items[blockIdx.x];
-    const M1RowSort R = rs[it.rs];
-    const M1Tensor& T = tens[R.tensor];
-    const M1Net& N = nets[R.net];
-    const int m = (int)N.m;
-    const uint32_t mask = (uint32_t)(m - 1);
-    for (int b = threadIdx.x; b < m; b += blockDim.x) x_sh[b] = 0.f;
-    // this lane's column and its combined word over modes 1 .. order-1 (bins add, the
-    // sign bits' sum carries the product of signs in bit 24)
-    const int64_t rl = T.numel / T.dims[0];
-    const int64_t c = (int64_t)it.strip * kRsThreads + threadIdx.x;
-    const bool live = c < rl;
-    uint32_t wc = 0;
-    if (live) {
-        const uint32_t* tab = tabs + N.tab_off + (int64_t)R.rep * N.L;
-        int64_t rem = c;
-        for (int d = T.order - 1; d >= 1; --d) {
-            const int64_t dim = T.dims[d];
-            const int64_t q = rem / dim;
-            const int x = (int)(rem - q * dim);
-            rem = q;
-            if (T.tab[d] < 0) continue;  // dim 1 (the planner admits no other open mode)
-            uint32_t w = tab[T.tab[d] + x];
-            if (T.comp[d]) w = (((uint32_t)m - (w & mask)) & mask) | (w & TNSK_SIGN_BIT);
-            wc += w;
-        }
-    }
-    const uint32_t hc = wc & mask;
-    const bool neg_c = (wc & TNSK_SIGN_BIT) != 0;
-    __syncthreads();
-    const float* X = (const float*)T.data;
-    // the item's sorted rows in shared memory (uniform reads), one sentinel after them
-    uint32_t* s_ord = reinterpret_cast<uint32_t*>(x_sh + m);
-    const int nk = it.k_hi - it.k_lo;
-    for (int k = threadIdx.x; k <= nk; k += blockDim.x)
-        s_ord[k] = k < nk ? __ldg(scratch + R.order_off + it.k_lo + k) : 0xFFFFFFFFu;
-    __syncthreads();
-    float z = 0.f;
-    constexpr int kU = 16;  // rows per step: their loads in flight together
-    for (int k0 = 0; k0 < nk; k0 += kU) {
-        float v[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u)
-            v[u] = (live && k0 + u < nk) ? __ldg(X + (int64_t)(s_ord[k0 + u] >> 15) * rl + c) : 0.f;
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            if (k0 + u >= nk) break;
-            const uint32_t w = s_ord[k0 + u], wn = s_ord[k0 + u + 1];
-            z += (w & (1u << 14)) ? -v[u] : v[u];
-            // the next row's bin differs, or this is the item's last row: add the column's sum
-            if ((w ^ wn) & mask || k0 + u + 1 >= nk) {
-                if (live) atomicAdd(&x_sh[((w & mask) + hc) & mask], neg_c ? -z : z);
-                z = 0.f;
+    int e = it.rs, strip = it.strip;
+    int64_t k = it.k, left = it.count;
+    while (left > 0) {
+        // ---- entry e: its sketch in shared memory
+        const M1RowSort R = rs[e];
+        const M1Tensor& T = tens[R.tensor];
+        const M1Net& N = nets[R.net];
+        const int m = (int)N.m;
+        const uint32_t mask = (uint32_t)(m - 1);
+        const int64_t n0 = T.dims[0];
+        const int64_t rl = T.numel / n0;
+        const float* X = (const float*)T.data;
+        const uint32_t* order = scratch + R.order_off;
+        s_ord = reinterpret_cast<uint32_t*>(x_sh + m);
+        __syncthreads();  // the previous entry's flush has read x_sh
+        for (int b = threadIdx.x; b < m; b += blockDim.x) x_sh[b] = 0.f;
+        while (left > 0) {
+            // ---- strip `strip`: this lane's column and its combined word over modes
+            // 1 .. order-1 (bins add; the sign bits' sum carries the sign product in bit 24)
+            const int64_t c = (int64_t)strip * kRsThreads + threadIdx.x;
+            const bool live = c < rl;
+            uint32_t wc = 0;
+            if (live) {
+                const uint32_t* tab = tabs + N.tab_off + (int64_t)R.rep * N.L;
+                int64_t rem = c;
+                for (int d = T.order - 1; d >= 1; --d) {
+                    const int64_t dim = T.dims[d];
+                    const int64_t q = rem / dim;
+                    const int x = (int)(rem - q * dim);
+                    rem = q;
+                    if (T.tab[d] < 0) continue;  // dim 1 (the planner admits no other open mode)
+                    uint32_t w = tab[T.tab[d] + x];
+                    if (T.comp[d]) w = (((uint32_t)m - (w & mask)) & mask) | (w & TNSK_SIGN_BIT);
+                    wc += w;
+                }
             }
+            const uint32_t hc = wc & mask;
+            const bool neg_c = (wc & TNSK_SIGN_BIT) != 0;
+            const int64_t seg = min(left, n0 - k);  // rows of this strip in the slot
+            for (int64_t k1 = k; k1 < k + seg; k1 += kChunk) {
+                const int nk = (int)min((int64_t)kChunk, k + seg - k1);
+                __syncthreads();  // the previous chunk's words are consumed
+                for (int i = threadIdx.x; i < nk; i += blockDim.x) s_ord[i] = __ldg(order + k1 + i);
+                __syncthreads();
+                float z = 0.f;
+                constexpr int kU = 16;  // rows per step: their loads in flight together
+                for (int k0 = 0; k0 < nk; k0 += kU) {
+                    uint32_t w[kU + 1];
+                    float v[kU];
+#pragma unroll
+                    for (int u = 0; u <= kU; ++u) w[u] = k0 + u < nk ? s_ord[k0 + u] : 0u;
+#pragma unroll
+                    for (int u = 0; u < kU; ++u)
+                        v[u] = (live && k0 + u < nk) ? __ldg(X + (int64_t)(w[u] >> 15) * rl + c) : 0.f;
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        if (k0 + u >= nk) break;
+                        z += (w[u] & (1u << 14)) ? -v[u] : v[u];
+                        // the next row's bin differs, or this is the chunk's last row
+                        if (((w[u] ^ w[u + 1]) & mask) || k0 + u + 1 >= nk) {
+                            if (live) atomicAdd(&x_sh[((w[u] & mask) + hc) & mask], neg_c ? -z : z);
+                            z = 0.f;
+                        }
+                    }
+                }
+            }
+            left -= seg;
+            k = 0;
+            if (++strip == R.strips) break;  // the entry is done
         }
+        __syncthreads();
+        float* gx = xs + N.x_off + (int64_t)R.rep * N.X + T.xoff;
+        for (int b = threadIdx.x; b < m; b += blockDim.x) {
+            const float val = x_sh[b];
+            if (val != 0.f) atomicAdd(&gx[b], val);
+        }
+        ++e;
+        strip = 0;
     }
-    __syncthreads();
-    float* gx = xs + N.x_off + (int64_t)R.rep * N.X + T.xoff;
-    for (int b = threadIdx.x; b < m; b += blockDim.x) {
-        const float val = x_sh[b];
-        if (val != 0.f) atomicAdd(&gx[b], val);
+}
+
+int64_t m1_rowsort_slots() {
+    static int64_t slots = 0;
+    if (!slots) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+            cudaGetLastError();
+            sms = 152;
+        }
+        slots = 2 * (int64_t)sms;  // two 512-thread CTAs per SM (launch bounds)
     }
+    return slots;
 }
 
 cudaError_t launch_m1_rowsort(const BatchPlan& plan, unsigned char* base, float* xs, cudaStream_t s) {
@@ -176,8 +216,8 @@ cudaError_t launch_m1_rowsort(const BatchPlan& plan, unsigned char* base, float*
     const size_t smem = (size_t)plan.m1.rs_max_m * 4;
     cudaFuncSetAttribute(m1_rowsort_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     m1_rowsort_order_kernel<<<plan.m1.n_rs, 1024, smem, s>>>(tens, nets, rs, tabs, scratch);
-    // the shared sketch, then the item's sorted rows and a sentinel
-    const size_t smem2 = smem + (size_t)(plan.m1.rs_max_rows + 1) * 4;
+    // the shared sketch, then one chunk of order words
+    const size_t smem2 = smem + (size_t)kChunk * 4;
     cudaFuncSetAttribute(m1_rowsort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     m1_rowsort_kernel<<<plan.m1.n_rs_items, kRsThreads, smem2, s>>>(tens, nets, rs, items, tabs, scratch, xs);
     return cudaGetLastError();

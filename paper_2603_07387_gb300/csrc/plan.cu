@@ -545,18 +545,12 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                     for (int d = 1; d < T.order; ++d) all_ctr = all_ctr && (T.tab[d] >= 0 || T.dims[d] == 1);
                     const int64_t rl = T.numel / T.dims[0];
                     if (all_ctr && rl >= 512) {
-                        const int64_t strips = (rl + 511) / 512, rows = 1024;
+                        const int64_t strips = (rl + 511) / 512;
                         for (int r = 0; r < R; ++r) {
-                            const int id = (int)rsorts.size();
-                            rsorts.push_back(M1RowSort{nb.t0 + k, (int)m1n.size(), r, 0, rs_words});
+                            rsorts.push_back(M1RowSort{nb.t0 + k, (int)m1n.size(), r, (int)strips, rs_words});
                             rs_words += (T.dims[0] + 63) / 64 * 64;
-                            for (int64_t st = 0; st < strips; ++st)
-                                for (int64_t k0 = 0; k0 < T.dims[0]; k0 += rows)
-                                    ritems.push_back(M1RowItem{id, (int)st, (int)k0,
-                                                               (int)std::min<int64_t>(T.dims[0], k0 + rows)});
                         }
                         P.m1.rs_max_m = std::max<int64_t>(P.m1.rs_max_m, m);
-                        P.m1.rs_max_rows = std::max<int>(P.m1.rs_max_rows, (int)std::min<int64_t>(rows, T.dims[0]));
                         continue;
                     }
                 }
@@ -1046,6 +1040,30 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     }
     P.n_reqs = (int)reqs.size();
     P.n_table_rows = crow;
+
+    // ---- row-sorted sketches: the concatenation of every entry's (strip, sorted row)
+    // positions split into one equal contiguous part per CTA slot (m1_rowsort_slots)
+    if (!rsorts.empty()) {
+        std::vector<int64_t> start(rsorts.size() + 1, 0);
+        for (size_t i = 0; i < rsorts.size(); ++i) {
+            const M1Tensor& T = m1t[rsorts[i].tensor];
+            start[i + 1] = start[i] + (int64_t)rsorts[i].strips * T.dims[0];
+        }
+        const int64_t total = start.back();
+        const int64_t G = std::max<int64_t>(1, std::min<int64_t>(m1_rowsort_slots(), total / 64));
+        size_t e = 0;
+        for (int64_t g = 0; g < G; ++g) {
+            const int64_t a = total * g / G, b = total * (g + 1) / G;
+            if (b <= a) continue;
+            while (start[e + 1] <= a) ++e;
+            const int64_t n0 = m1t[rsorts[e].tensor].dims[0];
+            const int64_t off = a - start[e];
+            ritems.push_back(M1RowItem{(int)e, (int)(off / n0), (int)(off % n0), 0, b - a});
+        }
+        int64_t most_n0 = 0;
+        for (const M1RowSort& r : rsorts) most_n0 = std::max<int64_t>(most_n0, m1t[r.tensor].dims[0]);
+        P.m1.rs_max_rows = (int)most_n0;
+    }
 
     // ---- stage descriptors
     std::vector<unsigned char>& H = P.host_desc;
