@@ -430,6 +430,28 @@ tnsk_status tnsk_choose_params(tnsk_ctx* ctx, const tnsk_network* net, double ta
  * TNSK_ERR_INVALID for a NULL ctx or another value. */
 tnsk_status tnsk_debug_inject(tnsk_ctx* ctx, int32_t what);
 
+/* Parameters for B networks at once (the library's sizing policy; the paper sizes m
+ * by its variance bounds only). For every network, the cheapest (m, R) with m in
+ * 2^6 .. 2^16 and R in {16, 32, 64} (the normal quantile of a mean of fewer, heavy-
+ * tailed repetitions is not trusted), the cost being Theorem 1's work per
+ * repetition times R, R (sum_k q_k N_k + p m log2 m), whose predicted relative error
+ * |y - tc| / |tc| (90% quantile) is at most target_err:
+ *   1. from the learned predictor (TNSK_GENERAL networks, mlp not NULL; how[b] = 0);
+ *   2. else, with pilot_reps >= 2, from a pilot: pilot_reps repetitions at m = 2^12
+ *      of all such networks in one batch (repetitions rep0 = 2^20 on, apart from the
+ *      estimate's), whose sample variance s^2, taken one standard error up
+ *      (s^2 (1 + sqrt(2 / (pilot_reps - 1)))), scales as 1/m per repetition (both
+ *      variance lemmas) and 1/R for the mean: 1.6449 sqrt(s^2 2^12 / (m R)) / |mean|
+ *      (how[b] = 1);
+ *   3. else m = 2^16, R = 64 (how[b] = 2; predicted_err[b] = the best candidate's).
+ * inout[b]: m, reps and groups (1) are set, other fields kept. predicted_err, how: host
+ * arrays [B]. Runs the pilot on the ctx stream and waits for it. Errors: as
+ * tnsk_estimate for a network; TNSK_ERR_INVALID for bad arguments (pilot_reps 1 or
+ * above 4096); TNSK_ERR_UNSUPPORTED for TNSK_CROSSCORR. */
+tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, double target_err,
+                                     tnsk_mlp* mlp, int32_t pilot_reps, tnsk_params* inout, double* predicted_err,
+                                     int32_t* how);
+
 /* Wait for the ctx's stream; returns the first deferred device error, if any. */
 tnsk_status tnsk_sync(tnsk_ctx* ctx);
 

@@ -159,7 +159,7 @@ struct M1RowSort {
     int32_t tensor;  // index into the method-1 tensor descriptors
     int32_t net;     // index into the method-1 network descriptors
     int32_t rep;     // repetition within the call
-    int32_t strips;  // column strips of 512
+    int32_t strips;  // column strips of 2048
     int64_t order_off;
 };
 

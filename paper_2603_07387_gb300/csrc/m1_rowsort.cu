@@ -22,11 +22,12 @@
 namespace tnsk {
 
 namespace {
-constexpr int kRsThreads = 512;  // 16 warps: a strip of 512 columns
+constexpr int kRsThreads = 512;  // 16 warps: a strip of 2048 columns
 }
 
-// Sorted rows of one (tensor, rep): packed words row << 15 | negative << 14 | bin, in
-// the order of the bins. Counting sort in shared memory (m <= 2^14 counters).
+// Sorted rows of one (tensor, rep): packed words row << 16 | run end << 15 | negative << 14
+// | bin, in the order of the bins (run end: the next row's bin differs, or the last row).
+// Counting sort in shared memory (m <= 2^14 counters, n0 <= 2^16 rows).
 __global__ void __launch_bounds__(1024) m1_rowsort_order_kernel(const M1Tensor* __restrict__ tens,
                                                                 const M1Net* __restrict__ nets,
                                                                 const M1RowSort* __restrict__ rs,
@@ -87,18 +88,28 @@ __global__ void __launch_bounds__(1024) m1_rowsort_order_kernel(const M1Tensor* 
     uint32_t* out = scratch + R.order_off;
     for (int i = threadIdx.x; i < n0; i += blockDim.x) {
         const uint32_t w = word(i);
-        const int pos = atomicAdd(&cnt[w & mask], 1);
-        out[pos] = ((uint32_t)i << 15) | ((w & TNSK_SIGN_BIT) ? (1u << 14) : 0u) | (w & mask);
+        const uint32_t b = w & mask;
+        const int pos = atomicAdd(&cnt[b], 1);
+        out[pos] = ((uint32_t)i << 16) | ((w & TNSK_SIGN_BIT) ? (1u << 14) : 0u) | b;
+    }
+    __syncthreads();
+    // run ends: once every row is placed, cnt[b] is the end of bin b's rows, so the row
+    // at position k ends its run when k + 1 == cnt[its bin]
+    for (int k = threadIdx.x; k < n0; k += blockDim.x) {
+        const uint32_t w = out[k];
+        if (k + 1 == cnt[w & mask]) out[k] = w | (1u << 15);
     }
 }
 
 // One CTA slot: `count` consecutive (strip, sorted row) positions of the concatenation
-// over the entries (see M1RowItem). The 16 warps of the CTA cover the 512 columns of one
-// strip and walk the same rows, whose order words are staged in shared memory in
-// chunks of kChunk; a lane's register sum is added to the shared sketch when the row
-// bin changes and at the end of a chunk; the shared sketch goes to the entry's global
-// sketch when the walk leaves the entry.
+// over the entries (see M1RowItem). A strip is 2048 columns: each of the 512 lanes owns
+// four consecutive columns (one 16-byte load per row; the CTA reads 8 KiB of a row);
+// the CTA's warps walk the same rows, whose order words are staged in shared memory
+// in chunks of kChunk. A lane's four register sums are added to the shared sketch when
+// the row bin changes (the run-end bit of the order word) and at the end of a chunk;
+// the shared sketch goes to the entry's global sketch when the walk leaves the entry.
 constexpr int kChunk = 512;
+constexpr int kCols = 4 * kRsThreads;  // columns of a strip
 
 __global__ void __launch_bounds__(kRsThreads, 2) m1_rowsort_kernel(const M1Tensor* __restrict__ tens,
                                                                    const M1Net* __restrict__ nets,
@@ -107,8 +118,7 @@ __global__ void __launch_bounds__(kRsThreads, 2) m1_rowsort_kernel(const M1Tenso
                                                                    const uint32_t* __restrict__ tabs,
                                                                    const uint32_t* __restrict__ scratch,
                                                                    float* __restrict__ xs) {
-    extern __shared__ float x_sh[];  // [max m], then kChunk order words
-    uint32_t* s_ord = nullptr;  // after the entry's m floats
+    extern __shared__ __align__(16) float x_sh[];  // [max m], then kChunk order words
     const M1RowItem it = items[blockIdx.x];
     int e = it.rs, strip = it.strip;
     int64_t k = it.k, left = it.count;
@@ -120,60 +130,86 @@ __global__ void __launch_bounds__(kRsThreads, 2) m1_rowsort_kernel(const M1Tenso
         const int m = (int)N.m;
         const uint32_t mask = (uint32_t)(m - 1);
         const int64_t n0 = T.dims[0];
-        const int64_t rl = T.numel / n0;
+        const int64_t rl = T.numel / n0;  // a multiple of 4 (the planner's condition)
         const float* X = (const float*)T.data;
         const uint32_t* order = scratch + R.order_off;
-        s_ord = reinterpret_cast<uint32_t*>(x_sh + m);
+        uint32_t* s_ord = reinterpret_cast<uint32_t*>(x_sh + ((m + 3) & ~3));
         __syncthreads();  // the previous entry's flush has read x_sh
         for (int b = threadIdx.x; b < m; b += blockDim.x) x_sh[b] = 0.f;
         while (left > 0) {
-            // ---- strip `strip`: this lane's column and its combined word over modes
-            // 1 .. order-1 (bins add; the sign bits' sum carries the sign product in bit 24)
-            const int64_t c = (int64_t)strip * kRsThreads + threadIdx.x;
-            const bool live = c < rl;
-            uint32_t wc = 0;
-            if (live) {
-                const uint32_t* tab = tabs + N.tab_off + (int64_t)R.rep * N.L;
-                int64_t rem = c;
-                for (int d = T.order - 1; d >= 1; --d) {
-                    const int64_t dim = T.dims[d];
-                    const int64_t q = rem / dim;
-                    const int x = (int)(rem - q * dim);
-                    rem = q;
-                    if (T.tab[d] < 0) continue;  // dim 1 (the planner admits no other open mode)
-                    uint32_t w = tab[T.tab[d] + x];
-                    if (T.comp[d]) w = (((uint32_t)m - (w & mask)) & mask) | (w & TNSK_SIGN_BIT);
-                    wc += w;
+            // ---- strip `strip`: this lane's four columns, each with its combined word over
+            // modes 1 .. order-1 (bins add; the sign bits' sum carries the sign product in bit 24)
+            const int64_t c0 = (int64_t)strip * kCols + 4 * threadIdx.x;
+            const bool live = c0 < rl;  // all four or none (rl % 4 == 0)
+            uint32_t hc[4], cs[4];
+            const uint32_t* tab = tabs + N.tab_off + (int64_t)R.rep * N.L;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint32_t wc = 0;
+                if (live) {
+                    int64_t rem = c0 + j;
+                    for (int d = T.order - 1; d >= 1; --d) {
+                        const int64_t dim = T.dims[d];
+                        const int64_t q = rem / dim;
+                        const int x = (int)(rem - q * dim);
+                        rem = q;
+                        if (T.tab[d] < 0) continue;  // dim 1 (the planner admits no other open mode)
+                        uint32_t w = tab[T.tab[d] + x];
+                        if (T.comp[d]) w = (((uint32_t)m - (w & mask)) & mask) | (w & TNSK_SIGN_BIT);
+                        wc += w;
+                    }
                 }
+                hc[j] = wc & mask;
+                cs[j] = (wc & TNSK_SIGN_BIT) ? 0x80000000u : 0u;  // the column's sign, as an FP32 sign bit
             }
-            const uint32_t hc = wc & mask;
-            const bool neg_c = (wc & TNSK_SIGN_BIT) != 0;
             const int64_t seg = min(left, n0 - k);  // rows of this strip in the slot
+            const float4* Xc = reinterpret_cast<const float4*>(X + c0);
             for (int64_t k1 = k; k1 < k + seg; k1 += kChunk) {
                 const int nk = (int)min((int64_t)kChunk, k + seg - k1);
                 __syncthreads();  // the previous chunk's words are consumed
-                for (int i = threadIdx.x; i < nk; i += blockDim.x) s_ord[i] = __ldg(order + k1 + i);
+                for (int i = threadIdx.x; i < kChunk; i += blockDim.x)
+                    s_ord[i] = i < nk ? __ldg(order + k1 + i) : 0u;  // zero words past the end add 0
                 __syncthreads();
-                float z = 0.f;
-                constexpr int kU = 16;  // rows per step: their loads in flight together
+                float z[4] = {0.f, 0.f, 0.f, 0.f};
+                constexpr int kU = 8;  // rows per step: their loads in flight together
                 for (int k0 = 0; k0 < nk; k0 += kU) {
-                    uint32_t w[kU + 1];
-                    float v[kU];
+                    uint32_t w[kU];
 #pragma unroll
-                    for (int u = 0; u <= kU; ++u) w[u] = k0 + u < nk ? s_ord[k0 + u] : 0u;
+                    for (int u = 0; u < kU; u += 4) {
+                        const uint4 q = *reinterpret_cast<const uint4*>(s_ord + k0 + u);
+                        w[u] = q.x;
+                        w[u + 1] = q.y;
+                        w[u + 2] = q.z;
+                        w[u + 3] = q.w;
+                    }
+                    float4 v[kU];
 #pragma unroll
                     for (int u = 0; u < kU; ++u)
-                        v[u] = (live && k0 + u < nk) ? __ldg(X + (int64_t)(w[u] >> 15) * rl + c) : 0.f;
+                        v[u] = (live && k0 + u < nk) ? __ldg(Xc + (int64_t)(w[u] >> 16) * (rl >> 2))
+                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                     for (int u = 0; u < kU; ++u) {
-                        if (k0 + u >= nk) break;
-                        z += (w[u] & (1u << 14)) ? -v[u] : v[u];
-                        // the next row's bin differs, or this is the chunk's last row
-                        if (((w[u] ^ w[u + 1]) & mask) || k0 + u + 1 >= nk) {
-                            if (live) atomicAdd(&x_sh[((w[u] & mask) + hc) & mask], neg_c ? -z : z);
-                            z = 0.f;
+                        const uint32_t rsg = (w[u] << 17) & 0x80000000u;  // the row's sign
+                        z[0] += __uint_as_float(__float_as_uint(v[u].x) ^ rsg ^ cs[0]);
+                        z[1] += __uint_as_float(__float_as_uint(v[u].y) ^ rsg ^ cs[1]);
+                        z[2] += __uint_as_float(__float_as_uint(v[u].z) ^ rsg ^ cs[2]);
+                        z[3] += __uint_as_float(__float_as_uint(v[u].w) ^ rsg ^ cs[3]);
+                        if (w[u] & (1u << 15)) {  // the bin's run ends here: add the columns' sums
+                            if (live) {
+                                const uint32_t b = w[u] & mask;
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) atomicAdd(&x_sh[(b + hc[j]) & mask], z[j]);
+                            }
+                            z[0] = z[1] = z[2] = z[3] = 0.f;
                         }
                     }
+                }
+                // a run that continues past the chunk: add its part (the last word read)
+                if (live) {
+                    const uint32_t b = s_ord[nk - 1] & mask;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (z[j] != 0.f) atomicAdd(&x_sh[(b + hc[j]) & mask], z[j]);
                 }
             }
             left -= seg;
@@ -216,8 +252,8 @@ cudaError_t launch_m1_rowsort(const BatchPlan& plan, unsigned char* base, float*
     const size_t smem = (size_t)plan.m1.rs_max_m * 4;
     cudaFuncSetAttribute(m1_rowsort_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     m1_rowsort_order_kernel<<<plan.m1.n_rs, 1024, smem, s>>>(tens, nets, rs, tabs, scratch);
-    // the shared sketch, then one chunk of order words
-    const size_t smem2 = smem + (size_t)kChunk * 4;
+    // the shared sketch (rounded up to 16 bytes), then one chunk of order words
+    const size_t smem2 = (size_t)((plan.m1.rs_max_m + 3) & ~3) * 4 + (size_t)kChunk * 4;
     cudaFuncSetAttribute(m1_rowsort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     m1_rowsort_kernel<<<plan.m1.n_rs_items, kRsThreads, smem2, s>>>(tens, nets, rs, items, tabs, scratch, xs);
     return cudaGetLastError();

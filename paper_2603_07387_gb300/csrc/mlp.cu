@@ -699,4 +699,185 @@ tnsk_status tnsk_choose_params(tnsk_ctx* ctx, const tnsk_network* net, double ta
     return ctx_fail(ctx, TNSK_ERR_UNREACHABLE, "choose_params: no m <= 2^16 meets the target");
 }
 
+// Sizing for a batch (tnsk.h): the learned predictor first, a batched pilot second.
+// Candidates m = 2^6 .. 2^16, R in {16, 32, 64}; the cost of a candidate is
+// Theorem 1's work per repetition times R: R (sum_k q_k N_k + p m log2 m).
+tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, double target_err,
+                                     tnsk_mlp* mlp, int32_t pilot_reps, tnsk_params* inout, double* predicted_err,
+                                     int32_t* how) {
+    tnsk_status st = ctx_check(ctx);
+    if (st != TNSK_OK) return st;
+    if (B < 0 || (B > 0 && (!nets || !inout || !predicted_err || !how)) || !(target_err > 0.0) || pilot_reps < 0 ||
+        pilot_reps == 1 || pilot_reps > 4096)
+        return ctx_fail(ctx, TNSK_ERR_INVALID, "choose_params_batch: arguments");
+    constexpr int kLo = 6, kHi = 16, kPilotLog2m = 12;
+    // R from 16 up: the normal quantile of the mean is not trusted below (heavy tails)
+    static const int kReps[] = {16, 32, 64};
+    constexpr int nR = 3, nL = kHi - kLo + 1;
+    constexpr double kQuantile90 = 1.0 / 0.3224;  // as tnsk_choose_params: 10^pred / 0.3224
+    constexpr double kZ90 = 1.6449;               // P(|Z| <= 1.6449) = 0.9
+    std::vector<double> work(B, 0.0);  // sum_k q_k N_k
+    std::vector<int> pterms(B, 0);
+    std::vector<char> done(B, 0);
+    // ---- the learned predictor (method 1 networks)
+    std::vector<float> hx;
+    std::vector<int> rows_of;  // network of each block of nL * nR rows
+    for (int b = 0; b < B; ++b) {
+        if (inout[b].method == TNSK_CROSSCORR)
+            return ctx_fail(ctx, TNSK_ERR_UNSUPPORTED, "choose_params_batch: the cross-correlation estimator");
+        NetInfo I;
+        float base[kFeatures];
+        tnsk_params q = inout[b];
+        q.reps = 16;
+        if (mlp && inout[b].method == TNSK_GENERAL) {
+            st = network_features(ctx, nets[b], q, I, base);
+            if (st != TNSK_OK) return st;
+        } else {
+            std::string why;
+            q.m = 1;
+            st = validate(nets[b], q, I, why);
+            if (st != TNSK_OK) return ctx_fail(ctx, st, "network " + std::to_string(b) + ": " + why);
+        }
+        for (int k = 0; k < I.p; ++k)
+            work[b] += (double)(I.mode_off[k + 1] - I.mode_off[k]) * (double)I.numel[k];
+        pterms[b] = I.p;
+        if (mlp && inout[b].method == TNSK_GENERAL) {
+            rows_of.push_back(b);
+            for (int l = kLo; l <= kHi; ++l)
+                for (int j = 0; j < nR; ++j) {
+                    const size_t at = hx.size();
+                    hx.insert(hx.end(), base, base + kFeatures);
+                    hx[at + 7] = (float)l;
+                    hx[at + 8] = (float)std::log2((double)kReps[j]);
+                }
+        }
+    }
+    auto cost = [&](int b, int l, int R) {
+        return (double)R * (work[b] + (double)pterms[b] * std::ldexp(1.0, l) * (double)l);
+    };
+    for (int b = 0; b < B; ++b) {
+        how[b] = 2;
+        predicted_err[b] = 1e300;
+    }
+    if (!rows_of.empty()) {
+        const size_t n = hx.size() / kFeatures;
+        float* d = nullptr;
+        if (cudaMalloc((void**)&d, (hx.size() + n) * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return ctx_fail(ctx, TNSK_ERR_OOM, "choose_params_batch: buffer");
+        }
+        std::vector<float> hy(n);
+        cudaMemcpyAsync(d, hx.data(), hx.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+        st = tnsk_mlp_predict(ctx, mlp, d, (int64_t)n, d + hx.size(), 1);
+        if (st == TNSK_OK) {
+            cudaMemcpyAsync(hy.data(), d + hx.size(), n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+            const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) st = ctx_cuda_fail(ctx, e, "choose_params_batch");
+        }
+        cudaFree(d);
+        if (st != TNSK_OK) return st;
+        for (size_t i = 0; i < rows_of.size(); ++i) {
+            const int b = rows_of[i];
+            double best_cost = 1e300, best_err = 1e300;
+            int bl = -1, bR = 0;
+            for (int l = kLo; l <= kHi; ++l)
+                for (int j = 0; j < nR; ++j) {
+                    const double err = std::pow(10.0, (double)hy[i * nL * nR + (l - kLo) * nR + j]) * kQuantile90;
+                    predicted_err[b] = std::min(predicted_err[b], err);
+                    if (err <= target_err && cost(b, l, kReps[j]) < best_cost) {
+                        best_cost = cost(b, l, kReps[j]);
+                        best_err = err;
+                        bl = l;
+                        bR = kReps[j];
+                    }
+                }
+            if (bl >= 0) {
+                inout[b].m = (int64_t)1 << bl;
+                inout[b].reps = bR;
+                inout[b].groups = 1;
+                predicted_err[b] = best_err;
+                how[b] = 0;
+                done[b] = 1;
+            }
+        }
+    }
+    // ---- the pilot: pilot_reps repetitions at m = 2^12 of the rest, in one batch; the
+    // per-rep variance scales as 1/m (both variance lemmas), the mean of R reps as 1/R
+    std::vector<int> pil;
+    for (int b = 0; b < B; ++b)
+        if (!done[b] && pilot_reps > 0) pil.push_back(b);
+    if (!pil.empty()) {
+        const int P = (int)pil.size();
+        double* d = nullptr;
+        const size_t nd = (size_t)P * (pilot_reps + 1);
+        if (cudaMalloc((void**)&d, nd * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return ctx_fail(ctx, TNSK_ERR_OOM, "choose_params_batch: pilot buffer");
+        }
+        std::vector<tnsk_network> pn(P);
+        std::vector<tnsk_params> pp(P);
+        std::vector<double*> po(P), pr(P);
+        for (int i = 0; i < P; ++i) {
+            pn[i] = nets[pil[i]];
+            pp[i] = inout[pil[i]];
+            pp[i].m = (int64_t)1 << kPilotLog2m;
+            pp[i].reps = pilot_reps;
+            pp[i].groups = 1;
+            pp[i].rep0 = 1 << 20;  // repetitions apart from those of the estimate itself
+            po[i] = d + (size_t)i * (pilot_reps + 1);
+            pr[i] = po[i] + 1;
+        }
+        st = tnsk_estimate_batch(ctx, P, pn.data(), pp.data(), po.data(), pr.data());
+        std::vector<double> h(nd);
+        if (st == TNSK_OK) {
+            cudaMemcpyAsync(h.data(), d, nd * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+            const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) st = ctx_cuda_fail(ctx, e, "choose_params_batch: pilot");
+        }
+        cudaFree(d);
+        if (st != TNSK_OK) return st;
+        for (int i = 0; i < P; ++i) {
+            const int b = pil[i];
+            const double* y = h.data() + (size_t)i * (pilot_reps + 1) + 1;
+            double mean = 0.0, var = 0.0;
+            for (int r = 0; r < pilot_reps; ++r) mean += y[r];
+            mean /= pilot_reps;
+            for (int r = 0; r < pilot_reps; ++r) var += (y[r] - mean) * (y[r] - mean);
+            var /= (pilot_reps - 1);
+            // one standard error up (a normal sample variance has relative error sqrt(2/(n-1))),
+            // so a pilot that happens to see a small spread does not undersize
+            var *= 1.0 + std::sqrt(2.0 / (pilot_reps - 1));
+            double best_cost = 1e300, best_err = 1e300;
+            int bl = -1, bR = 0;
+            for (int l = kLo; l <= kHi; ++l)
+                for (int j = 0; j < nR; ++j) {
+                    const double sd = std::sqrt(var * std::ldexp(1.0, kPilotLog2m - l) / kReps[j]);
+                    const double err = mean != 0.0 ? kZ90 * sd / std::fabs(mean) : 1e300;
+                    predicted_err[b] = std::min(predicted_err[b], err);
+                    if (err <= target_err && cost(b, l, kReps[j]) < best_cost) {
+                        best_cost = cost(b, l, kReps[j]);
+                        best_err = err;
+                        bl = l;
+                        bR = kReps[j];
+                    }
+                }
+            if (bl >= 0) {
+                inout[b].m = (int64_t)1 << bl;
+                inout[b].reps = bR;
+                inout[b].groups = 1;
+                predicted_err[b] = best_err;
+                how[b] = 1;
+                done[b] = 1;
+            }
+        }
+    }
+    for (int b = 0; b < B; ++b)
+        if (!done[b]) {  // beyond every candidate: the largest one
+            inout[b].m = (int64_t)1 << kHi;
+            inout[b].reps = kReps[nR - 1];
+            inout[b].groups = 1;
+        }
+    return TNSK_OK;
+}
+
 }  // extern "C"

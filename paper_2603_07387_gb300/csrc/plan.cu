@@ -539,13 +539,14 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 // Large FP32 tensors (far beyond L2) with a contracted leading mode: the
                 // row-sorted form, one pass over the tensor per rep (m1_rowsort.cu)
                 if (!fp64 && !I.diag[k] && T.dtype == TNSK_F32 && T.O == 1 && T.order >= 2 && T.tab[0] >= 0 &&
-                    T.numel >= ((int64_t)1 << 24) && T.dims[0] >= 1024 && T.dims[0] <= (1 << 17) &&
+                    T.numel >= ((int64_t)1 << 24) && T.dims[0] >= 1024 && T.dims[0] <= (1 << 16) &&
                     m <= (1 << 14) && R <= 64) {
                     bool all_ctr = true;
                     for (int d = 1; d < T.order; ++d) all_ctr = all_ctr && (T.tab[d] >= 0 || T.dims[d] == 1);
                     const int64_t rl = T.numel / T.dims[0];
-                    if (all_ctr && rl >= 512) {
-                        const int64_t strips = (rl + 511) / 512;
+                    // four columns per lane: 16-byte loads of every row
+                    if (all_ctr && rl >= 2048 && (rl & 3) == 0 && ((uintptr_t)T.data & 15) == 0) {
+                        const int64_t strips = (rl + 2047) / 2048;
                         for (int r = 0; r < R; ++r) {
                             rsorts.push_back(M1RowSort{nb.t0 + k, (int)m1n.size(), r, (int)strips, rs_words});
                             rs_words += (T.dims[0] + 63) / 64 * 64;

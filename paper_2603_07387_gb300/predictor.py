@@ -31,23 +31,30 @@ def grid_specs(rng, count: int):
     return specs
 
 
-def measure(ctx, specs, exact, log2ms=LOG2M, reps=(4, 16), seeds=(1, 2), device="cuda"):
+def measure(ctx, specs, exact, log2ms=LOG2M, reps=(4, 16), seeds=(1, 2), device="cuda",
+            max_bytes: float = 4e9):
     """Samples (X [n][9] float32, y [n] float32) for every spec x m x R x seed: one
-    libtnsk estimate per sample against exact[i] = tc of specs[i]."""
+    libtnsk estimate per sample against exact[i] = tc of specs[i]. Networks run in
+    batches whose sketches and spectra stay below about max_bytes."""
     import torch
 
     nets = [tnsk.Network(W.to_torch(s, device, torch.float32), s.edges, s.open) for s in specs]
     base = [ctx.features(n, tnsk.Params(m=1, reps=1)) for n in nets]
     exact = np.asarray(exact, dtype=np.float64)
+    pmax = max(len(s.tensors) for s in specs)
     X, y = [], []
     for l in log2ms:
         for R in reps:
+            # sketch + spectra per network: about 12 bytes per bin, rep and tensor
+            chunk = int(max(1, max_bytes // (12.0 * R * pmax * (1 << l))))
             for sd in seeds:
                 params = [tnsk.Params(m=1 << l, reps=R, seed=int(sd) * 1000003 + i) for i in range(len(nets))]
-                outs = [torch.zeros(1, dtype=torch.float64, device=device) for _ in nets]
-                ctx.estimate_batch(nets, params, outs)
+                outd = torch.zeros(len(nets), dtype=torch.float64, device=device)
+                outs = [outd[i:i + 1] for i in range(len(nets))]
+                for c0 in range(0, len(nets), chunk):
+                    ctx.estimate_batch(nets[c0:c0 + chunk], params[c0:c0 + chunk], outs[c0:c0 + chunk])
                 ctx.sync()
-                est = np.array([float(o.item()) for o in outs])
+                est = outd.cpu().numpy()
                 rel = np.abs(est - exact) / np.abs(exact)
                 for i, b in enumerate(base):
                     f = b.copy()

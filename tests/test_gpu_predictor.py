@@ -195,3 +195,46 @@ def test_trained_predictor_picks_m_where_the_bound_cannot(ctx, tmp_path):
     assert met >= 0.6 * picked
     mlp.close()
     again.close()
+
+
+def test_choose_params_batch_pilot_meets_the_target(ctx):
+    """tnsk_choose_params_batch without a predictor: the pilot (16 reps at m = 2^12 of
+    every network in one batch) sizes (m, R) by the sample variance; on held-out grids,
+    of the networks the pilot sizes (at least half), the estimates at the chosen (m, R)
+    with fresh repetitions meet the 5% target for at least 80% (the choice aims at 90%);
+    the others get the largest candidate and are flagged; and the cheapest candidate
+    wins (a network needing less gets a smaller m R)."""
+    held = [s for s in predictor.grid_specs(np.random.default_rng(11), 30) if len(s.edges) >= 4]
+    nets = [tnsk.Network(W.to_torch(s, "cuda", torch.float32), s.edges, s.open) for s in held]
+    params = [tnsk.Params(m=1, reps=16, seed=900 + i) for i in range(len(nets))]
+    chosen, errs, how = ctx.choose_params_batch(nets, 0.05, params, None, pilot_reps=16)
+    assert all(h in (1, 2) for h in how) and sum(h == 1 for h in how) >= 0.5 * len(how)
+    met = sized = 0
+    for s, n, p, h, e in zip(held, nets, chosen, how, errs):
+        assert p.reps in (16, 32, 64) and p.m in [1 << l for l in range(6, 17)]
+        if h == 2:  # no candidate reaches the target by the pilot: the largest one, flagged
+            assert p.m == 1 << 16 and p.reps == 64 and e > 0.05
+            continue
+        sized += 1
+        assert e <= 0.05
+        tc = tc_sequential([np.asarray(x, dtype=np.float32).astype(np.float64) for x in s.tensors], s.edges, s.open)
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ctx.estimate(n, p, out)
+        ctx.sync()
+        met += abs(float(out.item()) - tc) / abs(tc) <= 0.05
+    assert met >= 0.8 * sized
+    # an easy network (a single contraction of two U(0,1) vectors) gets the smallest cost
+    easy = W.NetSpec([np.random.default_rng(1).uniform(0, 1, 64), np.random.default_rng(2).uniform(0, 1, 64)],
+                     [(0, 1)], [], "dot")
+    ne = tnsk.Network(W.to_torch(easy, "cuda", torch.float32), easy.edges, easy.open)
+    (pe,), _, (he,) = ctx.choose_params_batch([ne], 0.05, [tnsk.Params(m=1, reps=16, seed=3)], None, pilot_reps=16)
+    assert he == 1 and pe.m * pe.reps <= 1 << 14
+
+
+def test_choose_params_batch_rejects_bad_arguments(ctx):
+    spec = W.grid(1, 2, 4, seed=1)
+    net = tnsk.Network(W.to_torch(spec, "cuda", torch.float32), spec.edges, spec.open)
+    with pytest.raises(tnsk.TnskError):
+        ctx.choose_params_batch([net], 0.05, [tnsk.Params(m=1, reps=16)], None, pilot_reps=1)
+    with pytest.raises(tnsk.TnskError):
+        ctx.choose_params_batch([net], 0.05, [tnsk.Params(m=1, reps=16, method=tnsk.CROSSCORR)], None)
