@@ -443,7 +443,9 @@ tnsk_status tnsk_debug_inject(tnsk_ctx* ctx, int32_t what);
  *      (s^2 (1 + sqrt(2 / (pilot_reps - 1)))), scales as 1/m per repetition (both
  *      variance lemmas) and 1/R for the mean: 1.6449 sqrt(s^2 2^12 / (m R)) / |mean|
  *      (how[b] = 1);
- *   3. else m = 2^16, R = 64 (how[b] = 2; predicted_err[b] = the best candidate's).
+ *   3. else the cheapest candidate, m = 2^6 and R = 16, flagged how[b] = 2 with
+ *      predicted_err[b] the best candidate's (no affordable work meets the target; the
+ *      caller decides whether a larger estimate is worth it).
  * inout[b]: m, reps and groups (1) are set, other fields kept. predicted_err, how: host
  * arrays [B]. Runs the pilot on the ctx stream and waits for it. Errors: as
  * tnsk_estimate for a network; TNSK_ERR_INVALID for bad arguments (pilot_reps 1 or

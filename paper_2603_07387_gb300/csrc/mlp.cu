@@ -154,16 +154,48 @@ __global__ void mlp_adam_kernel(float* __restrict__ theta, const float* __restri
     }
 }
 
-// sum of squares of a tensor in FP64 (features: Frobenius norms)
-__global__ void sumsq_kernel(const void* __restrict__ data, int dtype, int64_t n, double* __restrict__ out) {
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double x = load_as<double>(data, dtype, i);
-        s += x * x;
-    }
+// Sums of squares of many tensors in FP64 (features: Frobenius norms), one launch:
+// each tensor is cut into chunks of kSqChunk entries numbered from jobs[j].chunk0; a
+// block takes chunks round-robin, finds a chunk's tensor by binary search over chunk0
+// and adds its chunk's sum into out[j].
+struct SqJob {
+    const void* data;
+    int64_t n;
+    int64_t chunk0;
+    int32_t dtype;
+    int32_t pad_;
+};
+constexpr int kSqChunk = 8192;
+
+__global__ void __launch_bounds__(256) sumsq_batch_kernel(const SqJob* __restrict__ jobs, int nj, int64_t nchunks,
+                                                          double* __restrict__ out) {
+    __shared__ double red[8];
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        int lo = 0, hi = nj - 1;  // the last job whose first chunk is <= c
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].chunk0 <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const SqJob J = jobs[lo];
+        const int64_t i0 = (c - J.chunk0) * kSqChunk;
+        const int64_t i1 = J.n < i0 + kSqChunk ? J.n : i0 + kSqChunk;
+        double s = 0.0;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const double x = load_as<double>(J.data, J.dtype, i);
+            s += x * x;
+        }
 #pragma unroll
-    for (int sh = 16; sh > 0; sh >>= 1) s += __shfl_xor_sync(0xffffffffu, s, sh);
-    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+        for (int sh = 16; sh > 0; sh >>= 1) s += __shfl_xor_sync(0xffffffffu, s, sh);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+            atomicAdd(out + lo, t);
+        }
+        __syncthreads();
+    }
 }
 
 }  // namespace tnsk
@@ -549,13 +581,15 @@ namespace {
 // Features of a network at sketch size m and R reps (the predictor's inputs):
 // p, t, cycle rank t - p + components, log2 of the largest and mean log2 of the
 // contraction dims, mean and standard deviation of ln ||X_k||_F, log2 m, log2 R.
-tnsk_status network_features(tnsk_ctx* ctx, const tnsk_network& net, const tnsk_params& prm, NetInfo& I,
-                             float* feat) {
+// net_structure fills all but the two norm features (5, 6) and validates the network.
+tnsk_status net_structure(tnsk_ctx* ctx, const tnsk_network& net, const tnsk_params& prm, NetInfo& I, float* feat) {
     std::string why;
     tnsk_params q = prm;
     q.m = 1;  // the features take log2 m from prm; validation needs any valid m
     tnsk_status st = validate(net, q, I, why);
     if (st != TNSK_OK) return ctx_fail(ctx, st, why);
+    for (int k = 0; k < I.p; ++k)
+        if (I.rung[k]) return ctx_fail(ctx, TNSK_ERR_UNSUPPORTED, "features: grouped (rung) tensors have no stored entries");
     // connected components of the tensors joined by contractions
     std::vector<int> parent(I.p);
     for (int k = 0; k < I.p; ++k) parent[k] = k;
@@ -573,42 +607,75 @@ tnsk_status network_features(tnsk_ctx* ctx, const tnsk_network& net, const tnsk_
     }
     int comps = 0;
     for (int k = 0; k < I.p; ++k) comps += find(k) == k;
-    for (int k = 0; k < I.p; ++k)
-        if (I.rung[k]) return ctx_fail(ctx, TNSK_ERR_UNSUPPORTED, "features: grouped (rung) tensors have no stored entries");
-    // Frobenius norms on the device (FP64 sums of squares)
-    double* d = nullptr;
-    if (cudaMalloc((void**)&d, std::max(I.p, 1) * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        return ctx_fail(ctx, TNSK_ERR_OOM, "features: buffer");
-    }
-    cudaMemsetAsync(d, 0, std::max(I.p, 1) * sizeof(double), ctx->stream);
-    for (int k = 0; k < I.p; ++k)
-        if (I.numel[k] > 0)
-            sumsq_kernel<<<grid_for(I.numel[k]), 256, 0, ctx->stream>>>(net.X[k].data, net.X[k].dtype, I.numel[k],
-                                                                      d + k);
-    std::vector<double> ss(std::max(I.p, 1));
-    cudaMemcpyAsync(ss.data(), d, ss.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    cudaFree(d);
-    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "features");
-    double mean = 0.0, var = 0.0;
-    std::vector<double> ln(I.p);
-    for (int k = 0; k < I.p; ++k) {
-        ln[k] = 0.5 * std::log(std::max(ss[k], 1e-300));
-        mean += ln[k];
-    }
-    mean /= std::max(I.p, 1);
-    for (int k = 0; k < I.p; ++k) var += (ln[k] - mean) * (ln[k] - mean);
-    var /= std::max(I.p, 1);
     feat[0] = (float)I.p;
     feat[1] = (float)I.t;
     feat[2] = (float)(I.t - I.p + comps);
     feat[3] = (float)lmax;
     feat[4] = I.t > 0 ? (float)(lsum / I.t) : 0.f;
-    feat[5] = (float)mean;
-    feat[6] = (float)std::sqrt(var);
+    feat[5] = feat[6] = 0.f;
     feat[7] = (float)std::log2((double)std::max<int64_t>(prm.m, 1));
     feat[8] = (float)std::log2((double)std::max(prm.reps, 1));
+    return TNSK_OK;
+}
+
+// Features 5 and 6 from the sums of squares ss[k] of the network's p tensors.
+void norm_features(int p, const double* ss, float* feat) {
+    double mean = 0.0, var = 0.0;
+    std::vector<double> ln(p);
+    for (int k = 0; k < p; ++k) {
+        ln[k] = 0.5 * std::log(std::max(ss[k], 1e-300));
+        mean += ln[k];
+    }
+    mean /= std::max(p, 1);
+    for (int k = 0; k < p; ++k) var += (ln[k] - mean) * (ln[k] - mean);
+    var /= std::max(p, 1);
+    feat[5] = (float)mean;
+    feat[6] = (float)std::sqrt(var);
+}
+
+// One sum of squares per job (FP64), in one launch and one synchronisation.
+tnsk_status batch_sumsq(tnsk_ctx* ctx, std::vector<SqJob>& jobs, std::vector<double>& ss) {
+    ss.assign(jobs.size(), 0.0);
+    if (jobs.empty()) return TNSK_OK;
+    int64_t nchunks = 0;
+    for (auto& j : jobs) {
+        j.chunk0 = nchunks;
+        nchunks += (j.n + kSqChunk - 1) / kSqChunk;
+    }
+    const size_t jb = (jobs.size() * sizeof(SqJob) + 15) / 16 * 16;
+    unsigned char* d = nullptr;
+    if (cudaMalloc((void**)&d, jb + jobs.size() * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return ctx_fail(ctx, TNSK_ERR_OOM, "features: buffer");
+    }
+    double* dout = (double*)(d + jb);
+    cudaMemcpyAsync(d, jobs.data(), jobs.size() * sizeof(SqJob), cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemsetAsync(dout, 0, jobs.size() * sizeof(double), ctx->stream);
+    if (nchunks > 0) {
+        const int grid = (int)std::min<int64_t>(nchunks, 4096);
+        sumsq_batch_kernel<<<grid, 256, 0, ctx->stream>>>((const SqJob*)d, (int)jobs.size(), nchunks, dout);
+    }
+    cudaMemcpyAsync(ss.data(), dout, jobs.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "features");
+    return TNSK_OK;
+}
+
+void push_jobs(const tnsk_network& net, const NetInfo& I, std::vector<SqJob>& jobs) {
+    for (int k = 0; k < I.p; ++k) jobs.push_back(SqJob{net.X[k].data, I.numel[k], 0, net.X[k].dtype, 0});
+}
+
+tnsk_status network_features(tnsk_ctx* ctx, const tnsk_network& net, const tnsk_params& prm, NetInfo& I,
+                             float* feat) {
+    tnsk_status st = net_structure(ctx, net, prm, I, feat);
+    if (st != TNSK_OK) return st;
+    std::vector<SqJob> jobs;
+    push_jobs(net, I, jobs);
+    std::vector<double> ss;
+    st = batch_sumsq(ctx, jobs, ss);
+    if (st != TNSK_OK) return st;
+    norm_features(I.p, ss.data(), feat);
     return TNSK_OK;
 }
 
@@ -722,6 +789,8 @@ tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_networ
     // ---- the learned predictor (method 1 networks)
     std::vector<float> hx;
     std::vector<int> rows_of;  // network of each block of nL * nR rows
+    std::vector<float> bases;  // features of those networks (norm features filled below)
+    std::vector<SqJob> jobs;   // their tensors, for one batched norm pass
     for (int b = 0; b < B; ++b) {
         if (inout[b].method == TNSK_CROSSCORR)
             return ctx_fail(ctx, TNSK_ERR_UNSUPPORTED, "choose_params_batch: the cross-correlation estimator");
@@ -730,8 +799,11 @@ tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_networ
         tnsk_params q = inout[b];
         q.reps = 16;
         if (mlp && inout[b].method == TNSK_GENERAL) {
-            st = network_features(ctx, nets[b], q, I, base);
+            st = net_structure(ctx, nets[b], q, I, base);
             if (st != TNSK_OK) return st;
+            rows_of.push_back(b);
+            bases.insert(bases.end(), base, base + kFeatures);
+            push_jobs(nets[b], I, jobs);
         } else {
             std::string why;
             q.m = 1;
@@ -741,8 +813,16 @@ tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_networ
         for (int k = 0; k < I.p; ++k)
             work[b] += (double)(I.mode_off[k + 1] - I.mode_off[k]) * (double)I.numel[k];
         pterms[b] = I.p;
-        if (mlp && inout[b].method == TNSK_GENERAL) {
-            rows_of.push_back(b);
+    }
+    if (!rows_of.empty()) {
+        std::vector<double> ss;
+        st = batch_sumsq(ctx, jobs, ss);
+        if (st != TNSK_OK) return st;
+        size_t at_ss = 0;
+        for (size_t i = 0; i < rows_of.size(); ++i) {
+            float* base = &bases[i * kFeatures];
+            norm_features(pterms[rows_of[i]], ss.data() + at_ss, base);
+            at_ss += pterms[rows_of[i]];
             for (int l = kLo; l <= kHi; ++l)
                 for (int j = 0; j < nR; ++j) {
                     const size_t at = hx.size();
@@ -872,9 +952,9 @@ tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_networ
         }
     }
     for (int b = 0; b < B; ++b)
-        if (!done[b]) {  // beyond every candidate: the largest one
-            inout[b].m = (int64_t)1 << kHi;
-            inout[b].reps = kReps[nR - 1];
+        if (!done[b]) {  // no candidate reaches the target: the cheapest one, flagged (how = 2)
+            inout[b].m = (int64_t)1 << kLo;
+            inout[b].reps = kReps[0];
             inout[b].groups = 1;
         }
     return TNSK_OK;

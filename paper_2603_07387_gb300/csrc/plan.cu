@@ -536,11 +536,12 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 const M1Tensor& T = m1t[nb.t0 + k];
                 if (I.diag[k] && T.numel > 0) diags.push_back(M1Diag{nb.t0 + k, (int)m1n.size(), I.dims[I.mode_off[k]]});
                 if (T.numel == 0 || T.O == 0 || I.zero[k]) continue;  // all-zero tensors add nothing
-                // Large FP32 tensors (far beyond L2) with a contracted leading mode: the
-                // row-sorted form, one pass over the tensor per rep (m1_rowsort.cu)
+                // Large FP32 tensors (far beyond L2) with a contracted leading mode, at most
+                // two reps: the row-sorted form, one pass over the tensor per rep
+                // (m1_rowsort.cu); more reps share one pass of the entry scatter
                 if (!fp64 && !I.diag[k] && T.dtype == TNSK_F32 && T.O == 1 && T.order >= 2 && T.tab[0] >= 0 &&
                     T.numel >= ((int64_t)1 << 24) && T.dims[0] >= 1024 && T.dims[0] <= (1 << 16) &&
-                    m <= (1 << 14) && R <= 64) {
+                    m <= (1 << 14) && R <= 2) {
                     bool all_ctr = true;
                     for (int d = 1; d < T.order; ++d) all_ctr = all_ctr && (T.tab[d] >= 0 || T.dims[d] == 1);
                     const int64_t rl = T.numel / T.dims[0];

@@ -59,7 +59,7 @@ def test_rowsort_sketch_per_bin(ctx, m):
 
 def test_rowsort_estimates(ctx):
     for spec in _specs():
-        p = tnsk.Params(m=1024, reps=3, seed=5)
+        p = tnsk.Params(m=1024, reps=2, seed=5)
         _, per = gpu_estimate(ctx, spec, p, torch.float32)
         X = rounded(spec, torch.float32)
         y, s = oracle.m1_estimate(X, spec.edges, spec.open, m=p.m, reps=p.reps, seed=p.seed)
