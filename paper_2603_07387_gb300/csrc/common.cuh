@@ -185,7 +185,7 @@ struct M1Net {
     int64_t spec_per_rep;
     int64_t exp_off;  // their exponents (ints) of rep 0
     int64_t exp_per_rep;
-    int64_t lspec_off;  // large-m spectra [R][p][m] (complex entries) of rep 0
+    int64_t lspec_off;  // spectra of rep 0: [R][p][m] (large m) or [R][p][m/2 + 1] (mid m), complex entries
     int32_t log2m;
     int32_t R;
     int32_t t0;       // first tensor

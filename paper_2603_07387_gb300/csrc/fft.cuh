@@ -100,6 +100,84 @@ __device__ void block_fft_dif_interleaved(Cplx<T>* z, int log2nb, int log2M, con
     }
 }
 
+// Padded shared-memory layout for the fused transform below: element i at
+// i + i / 32, so that the strided accesses of its last passes spread over the banks.
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 5); }
+
+// A consecutive radix-2 DIF stages s .. s + A - 1 of a length-M transform (padded
+// layout) in one pass: each thread loads the 2^A points i = base + sum_t b_t h_t
+// (h_t = M >> (s + 1 + t), base free of those bits), applies the A stages' butterflies
+// in registers with the same twiddles as block_fft_dif (stage s + t: W at index
+// (i mod h_t) << (s + t + 1) of the length-2M table) and stores them back, so the
+// result equals A separate radix-2 stages. Ends with __syncthreads().
+template <typename T, int A>
+__device__ __forceinline__ void fft_pass(Cplx<T>* z, int log2M, int s, const Cplx<T>* __restrict__ tw) {
+    constexpr int P = 1 << A;
+    const int lh0 = log2M - s - 1;  // log2 h_0
+    const int lhl = lh0 - (A - 1);  // log2 h_{A-1}
+    const int ngroups = 1 << (log2M - A);
+    for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
+        const int jl = g & ((1 << lhl) - 1);
+        const int base = ((g >> lhl) << (lh0 + 1)) + jl;
+        int at[P];
+        Cplx<T> v[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            int off = 0;
+#pragma unroll
+            for (int t = 0; t < A; ++t)
+                if ((q >> (A - 1 - t)) & 1) off += 1 << (lh0 - t);
+            at[q] = pidx(base + off);
+            v[q] = z[at[q]];
+        }
+#pragma unroll
+        for (int t = 0; t < A; ++t) {
+            const int bit = 1 << (A - 1 - t);
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                if (q & bit) continue;
+                int j = jl;  // the pair's index within its half-group at stage s + t
+#pragma unroll
+                for (int u = t + 1; u < A; ++u)
+                    if ((q >> (A - 1 - u)) & 1) j += 1 << (lh0 - u);
+                const Cplx<T> a = v[q], c = v[q | bit];
+                v[q] = cadd(a, c);
+                v[q | bit] = cmul(csub(a, c), tw[j << (s + t + 1)]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < P; ++q) z[at[q]] = v[q];
+    }
+    __syncthreads();
+}
+
+// The DIF FFT of one length-M array in the padded layout, three stages per pass
+// (then a pass of two or one): natural order in, bit-reversed order out, the same
+// values as block_fft_dif. tw as there (may point to global memory).
+template <typename T>
+__device__ void block_fft_dif_fused(Cplx<T>* z, int log2M, const Cplx<T>* __restrict__ tw) {
+    int s = 0;
+    for (; log2M - s >= 3; s += 3) fft_pass<T, 3>(z, log2M, s, tw);
+    if (log2M - s == 2) fft_pass<T, 2>(z, log2M, s, tw);
+    else if (log2M - s == 1) fft_pass<T, 1>(z, log2M, s, tw);
+    else __syncthreads();
+}
+
+// Half-spectrum bin k (0..M) of the real sequence whose packed transform Z sits
+// bit-reversed in z in the padded layout.
+template <typename T>
+__device__ __forceinline__ Cplx<T> unpack_bin_padded(const Cplx<T>* z, int k, int log2M,
+                                                     const Cplx<T>* __restrict__ tw) {
+    const int M = 1 << log2M;
+    Cplx<T> zk = z[pidx(bitrev(k & (M - 1), log2M))];
+    Cplx<T> zc = cconj(z[pidx(bitrev((M - k) & (M - 1), log2M))]);
+    Cplx<T> e = {(zk.x + zc.x) * T(0.5), (zk.y + zc.y) * T(0.5)};
+    Cplx<T> d = csub(zk, zc);
+    Cplx<T> o = {d.y * T(0.5), -d.x * T(0.5)};  // (Zk - conj Z_{M-k}) / (2i)
+    Cplx<T> w = (k < M) ? tw[k] : Cplx<T>{T(-1), T(0)};
+    return cadd(e, cmul(w, o));
+}
+
 // Half-spectrum bin k (0..M) of the real sequence whose packed transform Z sits
 // bit-reversed in z (one array of length M).
 template <typename T>

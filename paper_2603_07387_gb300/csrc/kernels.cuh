@@ -81,6 +81,11 @@ cudaError_t launch_m1_spectrum(const M1Tensor* d_tens, const M1Net* d_nets, cons
 cudaError_t launch_m1_large(const M1Tensor* d_tens, const M1Net* d_nets, const int4* d_fft_items, int n_fft,
                             const int4* d_prod_items, int n_prod, const void* d_xs, const void* const* d_tws,
                             void* d_lspec, double* d_yrep, bool fp64, cudaStream_t s);
+// closed networks at 2^11 <= m <= 2^14: one CTA per (net, rep, sketch) transform into
+// the half spectra in d_lspec, then the product and bin sum per (net, rep, bin block)
+cudaError_t launch_m1_mid(const M1Tensor* d_tens, const M1Net* d_nets, const int4* d_fft_items, int n_fft,
+                          const int4* d_prod_items, int n_prod, int max_log2m, const void* d_xs,
+                          const void* const* d_tws, void* d_lspec, double* d_yrep, bool fp64, cudaStream_t s);
 // FP32 networks, 2^6 <= m = 2^log2m <= 2^10: one warp per item (open legs: spectra
 // stored to d_spec / d_sexp in the block kernel's layout)
 cudaError_t launch_m1_spectrum_warp(const M1Tensor* d_tens, const M1Net* d_nets, const OpenMode* d_opens,

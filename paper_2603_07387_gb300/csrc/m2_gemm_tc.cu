@@ -271,29 +271,35 @@ __global__ void __launch_bounds__(128, 2) m2_gemm_tc_kernel(const M2Node* __rest
 // ---------------------------------------------------------------------------
 // Streaming variant for row-major FP32 tensors whose parent mode is the first
 // mode (mat(X_k) is the row-major matrix itself) and whose column count is a
-// multiple of 4. Warp-specialised; per K-chunk of 32 columns the tiles of X and
-// of the pre-split V^T (hi and lo TF32 parts, written by the V build) arrive by
-// TMA (2-D boxes from tensor maps made at plan time) in the 128-byte swizzled
+// multiple of 4. Warp-specialised; per K-chunk of 32 columns the tile of X and the
+// tiles of the pre-split V^T (hi and lo TF32 parts, written by the V build) arrive
+// by TMA (2-D boxes from tensor maps made at plan time) in the 128-byte swizzled
 // K-major layout, with zero fill outside the matrices. X's hi / lo parts go to
-// tensor memory, so the MMA reads A from TMEM and only B from shared memory:
-//   warp 0     producer: three cp.async.bulk.tensor loads per chunk into a
-//              3-deep ring (raw_full counts bytes); two CTAs share an SM, so
-//              one's prologue and epilogue overlap the other's streaming
+// tensor memory, so the MMA reads A from TMEM and only B from shared memory. X and
+// V^T have rings of their own (3 deep each): an X stage is free again as soon as the
+// converters have read it, a V^T stage once the MMA that reads it completes; three
+// TMEM operand stages let the conversion of a chunk overlap the MMAs of the two
+// before it. X loads are marked evict-first in L2, V^T loads evict-last:
+//   warp 0     X producer: one cp.async.bulk.tensor load per chunk
 //   warps 1-4  converters: one row of X per thread (its TMEM lane), raw FP32 ->
 //              hi / lo TF32 stored with tcgen05.st; then the epilogue
 //   warp 5     tensor memory allocation and MMA issue; tcgen05.commit frees the
-//              ring stage and the TMEM operand stage
+//              V^T stage and the TMEM operand stage
+//   warp 6     V^T producer: the hi and lo tiles of each chunk (L2-resident: the
+//              row tiles of one matrix share them)
+// Two CTAs share an SM, so one's prologue and epilogue overlap the other's streaming.
 // Tensor memory: columns [0, 64) accumulator, [64 + 64 t, + 64) operand stage t
 // (hi in the first 32 columns, lo in the next 32).
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int kRawStages = 3;  // two CTAs per SM: 2 x 97 KiB of shared memory
-constexpr int kTmStages = 2;
+constexpr int kXStages = 3;    // X ring; two CTAs per SM: 2 x 97 KiB of shared memory
+constexpr int kVStages = 3;    // V^T ring
+constexpr int kTmStages = 3;   // TMEM operand stages: columns 64 + 64 t, t < 3, of 256
 constexpr int kRawX = kTM * 128;   // 128 rows x 128 B
 constexpr int kRawV = kTN * 128;   // 64 rows x 128 B (one of hi / lo)
-constexpr int kRawStage = kRawX + 2 * kRawV;
-constexpr int kStreamSmem = kRawStages * kRawStage + 1024;
+constexpr int kStreamThreads = 224;
+constexpr int kStreamSmem = kXStages * kRawX + kVStages * 2 * kRawV + 1024;
 constexpr uint32_t kTmemCols = 256;
 
 // K-major, 128-byte swizzle: stride byte offset 1024 (8-row atoms), leading offset unused.
@@ -314,6 +320,18 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int 
         : "memory");
 }
 
+// The same load with an L2 cache policy (from createpolicy): the streamed X tiles are
+// marked evict-first and the V^T tiles, which every row tile of a matrix re-reads,
+// evict-last, so that streaming X does not push V^T out of L2.
+__device__ __forceinline__ void tma_load_2d_hint(uint32_t dst, const void* tmap, int x, int y, uint32_t bar,
+                                                 uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], "
+        "[%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+        "l"(tmap), "r"(x), "r"(y), "r"(bar), "l"(policy)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_store32(uint32_t taddr, const uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
@@ -327,18 +345,20 @@ __device__ __forceinline__ void tmem_store32(uint32_t taddr, const uint32_t (&r)
 
 }  // namespace
 
-__global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node* __restrict__ nodes,
-                                                                   const M2Net* __restrict__ nets,
-                                                                   const M2Item* __restrict__ items,
-                                                                   float* __restrict__ ws,
-                                                                   const unsigned char* __restrict__ tmaps,
-                                                                   int* __restrict__ err, int inject) {
+__global__ void __launch_bounds__(kStreamThreads, 2) m2_gemm_tc_stream_kernel(const M2Node* __restrict__ nodes,
+                                                                               const M2Net* __restrict__ nets,
+                                                                               const M2Item* __restrict__ items,
+                                                                               float* __restrict__ ws,
+                                                                               const unsigned char* __restrict__ tmaps,
+                                                                               int* __restrict__ err, int inject) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t raw_full[kRawStages], raw_empty[kRawStages];
+    __shared__ __align__(8) uint64_t x_full[kXStages], x_empty[kXStages];
+    __shared__ __align__(8) uint64_t v_full[kVStages], v_empty[kVStages];
     __shared__ __align__(8) uint64_t tm_full[kTmStages], tm_empty[kTmStages];
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t tmem_base;
-    unsigned char* raw = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* xring = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* vring = xring + kXStages * kRawX;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const M2Item it = items[blockIdx.x];
     const M2Node& nd = nodes[it.node];
@@ -361,9 +381,13 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int s = 0; s < kRawStages; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&raw_full[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&raw_empty[s])));
+        for (int s = 0; s < kXStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&x_full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_addr(&x_empty[s])));
+        }
+        for (int s = 0; s < kVStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&v_full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&v_empty[s])));
         }
         for (int t = 0; t < kTmStages; ++t) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(&tm_full[t])));
@@ -378,27 +402,47 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
     const uint32_t tmem = tmem_base;
     bool ok = true;
 
-    if (warp == 0) {
-        // ---------------- producer (one thread); with a test's injected fault it issues no
-        // loads, so the consumers' bounded waits run out (nothing is left in flight)
+    if (warp == 0 || warp == 6) {
+        // ---------------- producers (one thread each): X (warp 0) and V^T (warp 6). With a
+        // test's injected fault they issue no loads, so the consumers' bounded waits run out.
+        // Before leaving, each waits (bounded) for its last loads to land, so no copy is in
+        // flight when the CTA exits, whatever happened to the consumers.
         if (lane == 0 && !inject) {
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmx) : "memory");
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvh) : "memory");
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvl) : "memory");
+            const bool isx = warp == 0;
+            const int S = isx ? kXStages : kVStages;
+            uint64_t* full = isx ? x_full : v_full;
+            uint64_t* empty = isx ? x_empty : v_empty;
+            if (isx) {
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmx) : "memory");
+            } else {
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvh) : "memory");
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmvl) : "memory");
+            }
+            uint64_t policy;
+            if (isx) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+            else asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(policy));
+            int issued = 0;
             for (int c = 0; c < nch && ok; ++c) {
-                const int s = c % kRawStages;
-                if (c >= kRawStages)
-                    ok = mbar_wait(smem_addr(&raw_empty[s]), (uint32_t)((c / kRawStages - 1) & 1));
+                const int s = c % S;
+                if (c >= S) ok = mbar_wait(smem_addr(&empty[s]), (uint32_t)((c / S - 1) & 1));
                 if (!ok) break;
                 const int k0 = (cbeg + c) * kKC;
-                unsigned char* st = raw + s * kRawStage;
-                const uint32_t bar = smem_addr(&raw_full[s]);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kRawStage)
-                             : "memory");
-                tma_load_2d(smem_addr(st), tmx, k0, (int)row0, bar);
-                tma_load_2d(smem_addr(st + kRawX), tmvh, k0, rep0, bar);
-                tma_load_2d(smem_addr(st + kRawX + kRawV), tmvl, k0, rep0, bar);
+                const uint32_t bar = smem_addr(&full[s]);
+                if (isx) {
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kRawX)
+                                 : "memory");
+                    tma_load_2d_hint(smem_addr(xring + s * kRawX), tmx, k0, (int)row0, bar, policy);
+                } else {
+                    unsigned char* st = vring + s * 2 * kRawV;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2 * kRawV)
+                                 : "memory");
+                    tma_load_2d_hint(smem_addr(st), tmvh, k0, rep0, bar, policy);
+                    tma_load_2d_hint(smem_addr(st + kRawV), tmvl, k0, rep0, bar, policy);
+                }
+                issued = c + 1;
             }
+            for (int c = issued > S ? issued - S : 0; c < issued; ++c)
+                if (!mbar_wait(smem_addr(&full[c % S]), (uint32_t)((c / S) & 1))) ok = false;
         }
         __syncwarp();
     } else if (warp <= 4) {
@@ -407,16 +451,20 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
         const int r = q4 * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
         for (int c = 0; c < nch && ok; ++c) {
-            const int s = c % kRawStages, t = c % kTmStages;
-            ok = mbar_wait(smem_addr(&raw_full[s]), (uint32_t)((c / kRawStages) & 1));
+            const int s = c % kXStages, t = c % kTmStages;
+            ok = mbar_wait(smem_addr(&x_full[s]), (uint32_t)((c / kXStages) & 1));
             if (ok && c >= kTmStages) ok = mbar_wait(smem_addr(&tm_empty[t]), (uint32_t)((c / kTmStages - 1) & 1));
             if (!ok) break;
-            const unsigned char* rowp = raw + s * kRawStage + (r >> 3) * 1024 + (r & 7) * 128;
+            const unsigned char* rowp = xring + s * kRawX + (r >> 3) * 1024 + (r & 7) * 128;
+            float4 v[8];
+#pragma unroll
+            for (int g = 0; g < 8; ++g) v[g] = *reinterpret_cast<const float4*>(rowp + ((g ^ (r & 7)) << 4));
+            // this thread's reads of the stage are done (arrive releases them)
+            mbar_arrive(smem_addr(&x_empty[s]));
             uint32_t hi[32], lo[32];
 #pragma unroll
             for (int g = 0; g < 8; ++g) {
-                const float4 v = *reinterpret_cast<const float4*>(rowp + ((g ^ (r & 7)) << 4));
-                const float x[4] = {v.x, v.y, v.z, v.w};
+                const float x[4] = {v[g].x, v[g].y, v[g].z, v[g].w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) tf32_split(x[q], hi[4 * g + q], lo[4 * g + q]);
             }
@@ -431,14 +479,15 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
     } else if (lane == 0) {
         // ---------------- MMA issue (warp 5, one thread)
         for (int c = 0; c < nch && ok; ++c) {
-            const int s = c % kRawStages, t = c % kTmStages;
+            const int t = c % kTmStages, sv = c % kVStages;
             ok = mbar_wait(smem_addr(&tm_full[t]), (uint32_t)((c / kTmStages) & 1));
+            if (ok) ok = mbar_wait(smem_addr(&v_full[sv]), (uint32_t)((c / kVStages) & 1));
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned char* st = raw + s * kRawStage;
+            const unsigned char* st = vring + sv * 2 * kRawV;
             const uint32_t a_hi = tmem + (uint32_t)(kTN + 64 * t), a_lo = a_hi + 32;
             const uint32_t aop[3] = {a_hi, a_hi, a_lo};
-            const unsigned char* bop[3] = {st + kRawX, st + kRawX + kRawV, st + kRawX};
+            const unsigned char* bop[3] = {st, st + kRawV, st};
 #pragma unroll
             for (int p = 0; p < 3; ++p)
 #pragma unroll
@@ -454,7 +503,7 @@ __global__ void __launch_bounds__(192, 2) m2_gemm_tc_stream_kernel(const M2Node*
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_addr(&tm_empty[t])));
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_addr(&raw_empty[s])));
+                smem_addr(&v_empty[sv])));
             if (c == nch - 1)
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     smem_addr(&done_bar)));
@@ -1027,7 +1076,7 @@ cudaError_t launch_m2_gemm_tc(int n, const M2Node* nodes, const M2Net* nets, con
     if (n <= 0) return cudaSuccess;
     if (stream) {
         cudaFuncSetAttribute(m2_gemm_tc_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem);
-        m2_gemm_tc_stream_kernel<<<n, 192, kStreamSmem, s>>>(nodes, nets, items, ws, tmaps, err, inject);
+        m2_gemm_tc_stream_kernel<<<n, kStreamThreads, kStreamSmem, s>>>(nodes, nets, items, ws, tmaps, err, inject);
     } else {
         cudaFuncSetAttribute(m2_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
         m2_gemm_tc_kernel<<<n, 128, kSmemBytes, s>>>(nodes, nets, items, tabs, ws, err);

@@ -634,6 +634,10 @@ cudaError_t launch_m1_spectra(const BatchPlan& plan, unsigned char* base, const 
                                     items + plan.m1.warp_first[sl], plan.m1.warp_count[sl], xs, tws,
                                     base + plan.m1.spec_off, (int*)(base + plan.m1.sexp_off), yrep, 6 + sl, s);
     if (e == cudaSuccess)
+        e = launch_m1_mid(tens, nets, (const int4*)(base + plan.m1.mfft_off), plan.m1.n_mfft,
+                          (const int4*)(base + plan.m1.mprod_off), plan.m1.n_mprod, plan.m1.mid_max_log2m, xs, tws,
+                          base + plan.m1.lspec_off, yrep, fp64, s);
+    if (e == cudaSuccess)
         e = launch_m1_large(tens, nets, (const int4*)(base + plan.m1.lfft_off), plan.m1.n_lfft,
                             (const int4*)(base + plan.m1.lprod_off), plan.m1.n_lprod, xs, tws,
                             base + plan.m1.lspec_off, yrep, fp64, s);

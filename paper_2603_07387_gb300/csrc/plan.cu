@@ -406,6 +406,8 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     std::vector<M2Net> m2n;
     int64_t tab_words = 0, yrep_n = 0, xs_n = 0, spec_n = 0, sexp_n = 0, lspec_n = 0;
     std::vector<int4> lfft, lprod;  // large-m method 1: (net, rep, sketch), (net, rep, first bin, bins)
+    std::vector<int4> mfft, mprod;  // mid-m closed networks: the same item forms
+    int mid_max_log2m = 0;
     std::vector<M1Diag> diags;      // diagonal copy tensors (WLOG 1)
     std::vector<M1RowSort> rsorts;  // row-sorted sketches of large tensors
     std::vector<M1RowItem> ritems;
@@ -633,6 +635,18 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                     for (int k = 0; k < I.p; ++k) lfft.push_back(make_int4((int)m1n.size(), r, k, 0));
                     for (int64_t j0 = 0; j0 < m; j0 += 4096)
                         lprod.push_back(make_int4((int)m1n.size(), r, (int)j0, (int)std::min<int64_t>(4096, m - j0)));
+                }
+            } else if (!sketch_only && I.O == 1 && nb.n_ot == 0 && I.log2m >= 11) {
+                // closed networks at 2^11 <= m <= 2^14 (2^13 FP64): one CTA per sketch for
+                // the transforms, half spectra [R][p][m/2 + 1] through a global scratch
+                const int64_t K = (m >> 1) + 1;
+                nb.lspec_off = lspec_n;
+                lspec_n += (int64_t)R * I.p * K;
+                mid_max_log2m = std::max(mid_max_log2m, I.log2m);
+                for (int r = 0; r < R; ++r) {
+                    for (int k = 0; k < I.p; ++k) mfft.push_back(make_int4((int)m1n.size(), r, k, 0));
+                    for (int64_t j0 = 0; j0 < K; j0 += 4096)
+                        mprod.push_back(make_int4((int)m1n.size(), r, (int)j0, (int)std::min<int64_t>(4096, K - j0)));
                 }
             } else if (!sketch_only && I.O > 0) {
                 // FP32, 2^6 <= m <= 2^10: the warp-per-item spectrum kernel
@@ -1083,6 +1097,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     }
     size_t o_open = stage(H, opens), o_items = stage(H, m1items), o_comb = stage(H, comb);
     size_t o_lfft = stage(H, lfft), o_lprod = stage(H, lprod), o_diag = stage(H, diags);
+    size_t o_mfft = stage(H, mfft), o_mprod = stage(H, mprod);
     size_t o_rs = stage(H, rsorts), o_ritems = stage(H, ritems);
     size_t o_m2nodes = stage(H, m2nodes), o_m2n = stage(H, m2n), o_m2items = stage(H, m2items);
     std::vector<unsigned char> tmap_space(P.m2.tmap_jobs.size() * 128, 0);
@@ -1098,6 +1113,11 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     P.m1.lprod_off = P.desc_off + o_lprod;
     P.m1.n_lfft = (int)lfft.size();
     P.m1.n_lprod = (int)lprod.size();
+    P.m1.mfft_off = P.desc_off + o_mfft;
+    P.m1.mprod_off = P.desc_off + o_mprod;
+    P.m1.n_mfft = (int)mfft.size();
+    P.m1.n_mprod = (int)mprod.size();
+    P.m1.mid_max_log2m = mid_max_log2m;
     P.m1.rs_off = P.desc_off + o_rs;
     P.m1.rs_items_off = P.desc_off + o_ritems;
     P.m1.n_rs = (int)rsorts.size();

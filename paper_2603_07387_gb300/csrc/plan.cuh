@@ -69,6 +69,11 @@ struct M1Plan {
     // large-m items (two-pass FFT, then the product over bin blocks) and their spectra
     size_t lfft_off = 0, lprod_off = 0, lspec_off = 0;
     int n_lfft = 0, n_lprod = 0;
+    // mid-m closed networks (m1_spectrum_mid.cu): the same two item lists, spectra in
+    // the same scratch; shared memory sized by the largest m
+    size_t mfft_off = 0, mprod_off = 0;
+    int n_mfft = 0, n_mprod = 0;
+    int mid_max_log2m = 0;
     // row-sorted sketches of large tensors (m1_rowsort.cu): per (tensor, rep) descriptors,
     // CTA items and the sorted-row scratch; shared memory of m floats
     size_t rs_off = 0, rs_items_off = 0, rs_scratch_off = 0;

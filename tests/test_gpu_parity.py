@@ -161,9 +161,25 @@ def test_method1_warp_spectrum_every_size(ctx, m):
         assert_parity(per, y, s, TOL[p.prec], f"{spec.name} m={m}")
 
 
+@pytest.mark.parametrize("prec", [tnsk.PREC_FP32, tnsk.PREC_FP64])
+def test_method1_mid_m_every_size(ctx, prec):
+    """Closed networks at 2^11 <= m <= 2^14 (2^13 in FP64) take one CTA per sketch for the
+    transforms and the product over blocks of the half spectra (more than one block of
+    4096 bins from m = 2^13 on); every size against the oracle."""
+    tdt = torch.float64 if prec == tnsk.PREC_FP64 else torch.float32
+    top = 14 if prec == tnsk.PREC_FP32 else 13
+    for l in range(11, top + 1):
+        for spec in (W.grid(3, 3, 4, seed=11), _closed_specs()[3]):
+            p = tnsk.Params(m=1 << l, reps=3, seed=90 + l, prec=prec)
+            out, per = gpu_estimate(ctx, spec, p, tdt)
+            y, s = oracle_estimate(spec, p, tdt)
+            assert_parity(per, y, s, TOL[prec], f"{spec.name} m=2^{l}")
+
+
 def test_method1_batch_mixes_spectrum_kernels(ctx):
-    """One batch with networks for the warp kernel at two sizes, the block kernel (open legs,
-    m above 1024, m below 64), the large-m kernels and method 2, each against the oracle."""
+    """One batch with networks for the warp kernel at two sizes, the per-sketch mid-m
+    kernels (m = 2048, closed), the block kernel (open legs, m above 1024, m below 64), the
+    large-m kernels and method 2, each against the oracle."""
     rng = np.random.default_rng(33)
     closed = _closed_specs()
     opened = [W.random_network(rng, p_range=(4, 6), dim_range=(2, 5), open_dim_range=(2, 4)) for _ in range(2)]
