@@ -76,6 +76,7 @@ def parse():
     ap.add_argument("--no-joins", action="store_true")
     ap.add_argument("--no-grid", action="store_true", help="skip the 4x4 grid precision leg")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16 method-2 leg")
+    ap.add_argument("--no-triangle", action="store_true", help="skip the 64 x 64 triangle leg")
     ap.add_argument("--grouped", action="store_true",
                     help="inner sites as grouped tensors (tnsk_rung) instead of materialising them every step")
     return ap.parse_args()
@@ -498,6 +499,7 @@ def run_ours(args, world, rank, local):
     pbias = prior_bias(ctx, dev) if (rank == 0 and not args.no_prior_bias) else None
     jsz = join_sizes(ctx, dev) if (rank == 0 and not args.no_joins) else None
     gridp = grid_precision(ctx, dev) if (rank == 0 and not args.no_grid) else None
+    tri = triangle_leg(ctx, dev) if (rank == 0 and not args.no_triangle) else None
     bf16c = (bf16_chains(ctx, dev, dense, cedges) if (rank == 0 and not args.no_bf16 and not args.grouped)
              else None)
     for p_ in plans + merges:
@@ -534,6 +536,7 @@ def run_ours(args, world, rank, local):
         "ms_per_step_profiled": round(ms_profiled, 4),
         "hbm_sketch_probe": probe,
         "learned_vs_plain": lvp,
+        "triangle": tri,
         "batched_uneven": unev,
         "turnstile": turn,
         "sparse_triangles": sparse,
@@ -1146,6 +1149,56 @@ def learned_vs_plain(ctx, dev, steps: int = 5, n_train: int = 800):
                          "train_s": round(t_train, 1)}}
     mlp.close()
     return out
+
+
+# ---------------------------------------------------------------- the triangle (tr(ABC), 64 x 64)
+def triangle_leg(ctx, dev, copies: int = 1024, steps: int = 10):
+    """tr(ABC) of three 64 x 64 N(0,1) matrices (FP64 inputs), method 1, m = 256, 16 reps:
+    one tnsk_estimate call (its latency, host planning included), and `copies` triangles
+    (different seeds) as one planned batch (device time of a graph replay); FP64 and FP32
+    paths. Error: the relative error of each estimate against the exact trace, and the
+    deviation of the FP32 path from the FP64 path on the same hash functions."""
+    import torch
+
+    from paper_2603_07387_gb300 import tnsk
+    from paper_2603_07387_gb300 import workloads as W
+
+    spec = W.triangle(64)
+    tc = float(np.trace(spec.tensors[0] @ spec.tensors[1] @ spec.tensors[2]))
+    ts = W.to_torch(spec, dev, torch.float64)
+    net = tnsk.Network(ts, spec.edges, spec.open)
+    res = {"workload": "tr(ABC), three 64 x 64 N(0,1) FP64 matrices, method 1, m = 256, 16 reps", "tc": tc}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, prec in (("fp64", tnsk.PREC_FP64), ("fp32", tnsk.PREC_FP32)):
+        out = torch.zeros(1, dtype=torch.float64, device=dev)
+        p = tnsk.Params(m=256, reps=16, seed=W.HASH_SEED, prec=prec)
+        ctx.estimate(net, p, out)
+        ctx.sync()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            ctx.estimate(net, p, out)
+        ctx.sync()
+        one_ms = (time.perf_counter() - t0) / steps * 1e3
+        est = float(out.item())
+        outs = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in range(copies)]
+        plan = ctx.plan([net] * copies, [tnsk.Params(m=256, reps=16, seed=W.HASH_SEED + i, prec=prec)
+                                         for i in range(copies)], outs)
+        plan.run()
+        plan.run()
+        ctx.sync()
+        e0.record()
+        for _ in range(steps):
+            plan.run()
+        e1.record()
+        ctx.sync()
+        ms = e0.elapsed_time(e1) / steps
+        rel = np.abs(np.array([float(o.item()) for o in outs]) - tc) / abs(tc)
+        plan.close()
+        res[name] = {"one_call_ms": round(one_ms, 4), "estimate": est, "rel_err": float(f"{abs(est - tc) / abs(tc):.3g}"),
+                     "batch_estimates_per_s": round(copies * 1e3 / ms, 1), "batch_ms": round(ms, 4),
+                     "batch_median_rel_err": float(f"{np.median(rel):.3g}")}
+    res["fp32_vs_fp64"] = float(f"{abs(res['fp32']['estimate'] - res['fp64']['estimate']) / abs(res['fp64']['estimate']):.3g}")
+    return res
 
 
 # ---------------------------------------------------------------- precision (the cyclic 4 x 4 grid)

@@ -80,7 +80,18 @@ typedef enum { TNSK_GENERAL = 1, TNSK_ACYCLIC = 2, TNSK_CROSSCORR = 3 } tnsk_met
  *   X as stored and V as the sum of three BF16 parts, FP32 accumulation, so the
  *   result is that of FP32 arithmetic on the BF16 values; everything else as FP32.
  * FP64: everything in FP64 (for high-dynamic-range sketches). */
-typedef enum { TNSK_PREC_FP32 = 0, TNSK_PREC_BF16 = 1, TNSK_PREC_FP64 = 2 } tnsk_precision;
+/* AUTO (tnsk_estimate only; method 1, no open legs): the FP32 path, then the FP64 path
+ *   for the reps whose FP32 transforms may be inexact. Every spectral kernel also
+ *   returns the rep's magnitude sum A_r = (1/m) sum_j |prod_k F x_k(j)|; the FP32
+ *   rounding of the transforms and of the products is at most about
+ *   c32 A_r, c32 = (p + 2 log2 m + 8) 2^-24 (p as given), so a rep with c32 A_r > 2^-17 |y_r| (a
+ *   sketch whose spectrum has a high dynamic range and cancels in the sum) is flagged.
+ *   The smallest range of reps holding every flagged rep is recomputed by the FP64
+ *   path (same hash functions: FP64 sketches from the same inputs, FP64 transforms),
+ *   and the estimate is the combination of the resulting per-rep values.
+ *   tnsk_auto_report gives the number of reps taken in FP64 and the largest remaining
+ *   relative bound, c A_r / |y_r| over the reps (c = c32 or its FP64 counterpart). */
+typedef enum { TNSK_PREC_FP32 = 0, TNSK_PREC_BF16 = 1, TNSK_PREC_FP64 = 2, TNSK_PREC_AUTO = 3 } tnsk_precision;
 
 typedef struct tnsk_ctx tnsk_ctx;
 
@@ -325,6 +336,11 @@ tnsk_status tnsk_plan_destroy(tnsk_plan* plan);
  * a synchronous copy. Every call reuses the same array (each device has its own),
  * so calls on one device whose GPU work overlaps, from two streams or two host
  * threads, race: order them on one stream. */
+/* The last TNSK_PREC_AUTO estimate on this ctx: reps recomputed in FP64 and the
+ * largest relative rounding bound of a per-rep value (see TNSK_PREC_AUTO); 0 and 0
+ * before the first. Either pointer may be NULL. */
+tnsk_status tnsk_auto_report(tnsk_ctx* ctx, int32_t* fp64_reps, double* max_rel_bound);
+
 tnsk_status tnsk_estimate_static(const tnsk_network* net, const tnsk_params* params, double* out, double* per_rep,
                                  void* cuda_stream);
 

@@ -15,6 +15,10 @@ second.
     python -m paper_2603_07387_gb300.cases ladders [--count 8]
         method 1 on `count` tensor-train ladders (two chains of 8 cores, bond 32,
         physical 8), m = 1024, 64 reps: the fixed-point scatter (m1_scatter_fx_kernel).
+    python -m paper_2603_07387_gb300.cases grid [--log2m 14] [--reps 256]
+        method 1 on the cyclic 4 x 4 grid of bond 8 (U(0,1), FP32): the transforms and
+        the product of the spectra (m1_fft_mid_kernel at 2^11 <= m <= 2^14,
+        m1_fft_large_kernel above).
 """
 from __future__ import annotations
 
@@ -87,21 +91,36 @@ def ladders(ctx, count: int):
     _run(ctx, nets, params, outs, "m1_scatter", nbytes)
 
 
+def grid(ctx, log2m: int, reps: int):
+    import torch
+
+    spec = W.grid(4, 4, 8)
+    ts = W.to_torch(spec, "cuda", torch.float32)
+    net = tnsk.Network(ts, spec.edges, spec.open)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    # the transforms read every sketch once (4 bytes per bin, 16 sketches per rep)
+    _run(ctx, [net], [tnsk.Params(m=1 << log2m, reps=reps, seed=W.HASH_SEED)], [out], "m1_spectrum",
+         16 * reps * (1 << log2m) * 4)
+
+
 def main(argv=None):
     import torch
 
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("case", choices=("chains", "trace4", "ladders"))
+    ap.add_argument("case", choices=("chains", "trace4", "ladders", "grid"))
+    ap.add_argument("--log2m", type=int, default=14)
     ap.add_argument("--count", type=int, default=None)
     ap.add_argument("--prec", choices=("fp32", "bf16"), default="fp32")
     ap.add_argument("--n", type=int, default=4096)
-    ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=None)
     a = ap.parse_args(argv)
     ctx = tnsk.Context(0, torch.cuda.current_stream().cuda_stream)
     if a.case == "chains":
         chains(ctx, a.count or 16, a.prec)
     elif a.case == "trace4":
-        trace4(ctx, a.n, a.reps)
+        trace4(ctx, a.n, a.reps or 1)
+    elif a.case == "grid":
+        grid(ctx, a.log2m, a.reps or 256)
     else:
         ladders(ctx, a.count or 8)
     ctx.close()

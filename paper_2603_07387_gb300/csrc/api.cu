@@ -189,6 +189,7 @@ tnsk_status tnsk_destroy(tnsk_ctx* ctx) {
     if (ctx->d_tw32) cudaFree(ctx->d_tw32);
     if (ctx->d_tw64) cudaFree(ctx->d_tw64);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->aux) cudaFree(ctx->aux);
     if (ctx->side) {
         cudaStreamSynchronize(ctx->side);
         cudaStreamDestroy(ctx->side);
@@ -351,7 +352,8 @@ static tnsk_status launch_plan(tnsk_ctx* ctx, const BatchPlan& plan, unsigned ch
 
 // Batch driver shared by tnsk_estimate, tnsk_estimate_batch and tnsk_m1_sketch.
 static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
-                             double* const* outs, double* const* per_reps, void* sketch_out) {
+                             double* const* outs, double* const* per_reps, void* sketch_out,
+                             size_t* yrep_off = nullptr, int64_t* yrep_n = nullptr) {
     tnsk_status st = check_ctx(ctx);
     if (st != TNSK_OK) return st;
     if (B == 0) return TNSK_OK;
@@ -384,7 +386,79 @@ static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets,
                                   cudaMemcpyHostToDevice, ctx->stream));
         nr = NormRun{(const NormJob*)(ctx->norm + nb.desc_off), (int)nb.jobs.size(), nb.most};
     }
+    if (yrep_off) *yrep_off = plan.yrep_off;
+    if (yrep_n) *yrep_n = plan.yrep_n;
     return launch_plan(ctx, plan, ctx->scratch, fp64, sketch_out, nr);
+}
+
+// TNSK_PREC_AUTO (tnsk.h): the FP32 path with the per-rep magnitude sums, the FP64 path
+// for the smallest range of reps holding every flagged one, then the combination.
+static tnsk_status estimate_auto(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, double* out,
+                                 double* per_rep) {
+    tnsk_status st = check_ctx(ctx);
+    if (st != TNSK_OK) return st;
+    if (params->method != TNSK_GENERAL || net->n_open != 0)
+        return fail(ctx, TNSK_ERR_UNSUPPORTED, "TNSK_PREC_AUTO: method 1 (TNSK_GENERAL) without open legs only");
+    if (!out) return fail(ctx, TNSK_ERR_INVALID, "null output buffer");
+    const int32_t R = params->reps;
+    if (R < 1 || R > 65536) return fail(ctx, TNSK_ERR_INVALID, "reps must be in [1, 65536]");
+    // per-rep values: the caller's buffer, else the ctx's; one more double for the FP64
+    // pass's combined value, which is not used
+    const size_t need = (size_t)(R + 1) * sizeof(double);
+    unsigned char* auxb = (unsigned char*)ctx->aux;
+    st = ensure_buffer(ctx, auxb, ctx->aux_bytes, need, "TNSK_PREC_AUTO buffer");
+    ctx->aux = (double*)auxb;
+    if (st != TNSK_OK) return st;
+    double* yr = per_rep ? per_rep : ctx->aux + 1;
+    tnsk_params q = *params;
+    q.prec = TNSK_PREC_FP32;
+    size_t yoff = 0;
+    int64_t yn = 0;
+    st = run_batch(ctx, 1, net, &q, &out, &yr, nullptr, &yoff, &yn);
+    if (st != TNSK_OK) return st;
+    // a one-network plan: its estimates are yrep[0 .. R), the magnitude sums yrep[yn ..)
+    std::vector<double> y(R), a(R);
+    TNSK_CUDA(cudaMemcpyAsync(y.data(), ctx->scratch + yoff, R * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    TNSK_CUDA(cudaMemcpyAsync(a.data(), ctx->scratch + yoff + (size_t)yn * sizeof(double), R * sizeof(double),
+                              cudaMemcpyDeviceToHost, ctx->stream));
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "TNSK_PREC_AUTO");
+    const double lg = std::log2((double)std::max<int64_t>(params->m, 1));
+    const double c32 = (net->p + 2.0 * lg + 8.0) * std::ldexp(1.0, -24);
+    const double c64 = (net->p + 2.0 * lg + 8.0) * std::ldexp(1.0, -53);
+    const double tau = std::ldexp(1.0, -17);  // ~7.6e-6 of the rep's own value
+    int32_t lo = R, hi = -1;
+    for (int32_t r = 0; r < R; ++r)
+        if (c32 * a[r] > tau * std::fabs(y[r])) {
+            lo = std::min(lo, r);
+            hi = r;
+        }
+    if (hi >= lo) {
+        tnsk_params q64 = *params;
+        q64.prec = TNSK_PREC_FP64;
+        q64.rep0 = params->rep0 + lo;
+        q64.reps = hi - lo + 1;
+        q64.groups = 1;
+        double* o64 = ctx->aux;
+        double* p64 = yr + lo;
+        st = run_batch(ctx, 1, net, &q64, &o64, &p64, nullptr);
+        if (st != TNSK_OK) return st;
+        TNSK_CUDA(cudaMemcpyAsync(y.data() + lo, p64, (size_t)(hi - lo + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+        e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "TNSK_PREC_AUTO");
+        st = tnsk_combine(ctx, R, 1, yr, params->groups, out);
+        if (st != TNSK_OK) return st;
+    }
+    double worst = 0.0;
+    for (int32_t r = 0; r < R; ++r) {
+        const double c = (r >= lo && r <= hi) ? c64 : c32;
+        const double b = a[r] > 0.0 ? c * a[r] / std::fabs(y[r]) : 0.0;  // +inf when y_r = 0 < A_r
+        worst = std::max(worst, b);
+    }
+    ctx->auto_fp64_reps = hi >= lo ? hi - lo + 1 : 0;
+    ctx->auto_max_bound = worst;
+    return TNSK_OK;
 }
 
 struct tnsk_plan {
@@ -699,7 +773,15 @@ tnsk_status tnsk_probe_shared_int_adds(tnsk_ctx* ctx, double* updates_per_s) {
 tnsk_status tnsk_estimate(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, double* out,
                           double* per_rep) {
     if (!ctx || !net || !params) return TNSK_ERR_INVALID;
+    if (params->prec == TNSK_PREC_AUTO) return estimate_auto(ctx, net, params, out, per_rep);
     return run_batch(ctx, 1, net, params, &out, &per_rep, nullptr);
+}
+
+tnsk_status tnsk_auto_report(tnsk_ctx* ctx, int32_t* fp64_reps, double* max_rel_bound) {
+    if (!ctx) return TNSK_ERR_INVALID;
+    if (fp64_reps) *fp64_reps = ctx->auto_fp64_reps;
+    if (max_rel_bound) *max_rel_bound = ctx->auto_max_bound;
+    return TNSK_OK;
 }
 
 tnsk_status tnsk_estimate_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,

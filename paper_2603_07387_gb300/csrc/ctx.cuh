@@ -30,6 +30,12 @@ struct tnsk_ctx {
     tnsk::Profiler prof;
     // fault injection for tests (tnsk_debug_inject): consumed by the next launch sequence
     int inject = 0;
+    // the last TNSK_PREC_AUTO estimate: reps taken in FP64, largest relative bound
+    int32_t auto_fp64_reps = 0;
+    double auto_max_bound = 0.0;
+    // per-rep buffer of TNSK_PREC_AUTO calls made without one (grown on demand)
+    double* aux = nullptr;
+    size_t aux_bytes = 0;
 };
 
 namespace tnsk {

@@ -85,12 +85,12 @@ __global__ void __launch_bounds__(256) m1_spec_product_kernel(const M1Net* __res
                                                               const int4* __restrict__ items,
                                                               const Cplx<T>* __restrict__ lspec,
                                                               double* __restrict__ yrep) {
-    __shared__ double red[32];
+    __shared__ double red[32], rab[32];
     const int4 it = items[blockIdx.x];  // (network, rep, first bin, bins)
     const M1Net& N = nets[it.x];
     const int64_t m = N.m;
     const Cplx<T>* base = lspec + N.lspec_off + (int64_t)it.y * N.p * m;
-    double acc = 0.0;
+    double acc = 0.0, aab = 0.0;  // the sum and the magnitude sum (for the FP64 criterion)
     for (int64_t j = it.z + threadIdx.x; j < (int64_t)it.z + it.w; j += blockDim.x) {
         Cplx<T> P = {T(1), T(0)};
         int E = 0;  // the product is P 2^E
@@ -106,16 +106,27 @@ __global__ void __launch_bounds__(256) m1_spec_product_kernel(const M1Net* __res
             }
         }
         acc += ldexp((double)P.x, E);
+        aab += ldexp(hypot((double)P.x, (double)P.y), E);
     }
 #pragma unroll
-    for (int sft = 16; sft > 0; sft >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sft);
+    for (int sft = 16; sft > 0; sft >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, sft);
+        aab += __shfl_xor_sync(0xffffffffu, aab, sft);
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) red[warp] = acc;
+    if (lane == 0) {
+        red[warp] = acc;
+        rab[warp] = aab;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        double t = 0.0, ta = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t += red[w];
+            ta += rab[w];
+        }
         atomicAdd(&yrep[N.y_off + it.y], t / (double)m);
+        atomicAdd(&yrep[N.yabs_off + it.y], ta / (double)m);
     }
 }
 

@@ -53,18 +53,23 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTN >> 3) << 17) |
                             ((uint32_t)(kTM >> 4) << 24);
 
+// Bounded wait for the phase of parity `parity` of an mbarrier. Each try_wait suspends
+// the thread until the phase completes or kSuspendNs pass (so waiting warps take no
+// issue slots from the working ones); after about kWaitCycles SM cycles in all, or
+// kWaitLimit polls, it gives up and returns false.
+constexpr uint32_t kSuspendNs = 100000;  // 0.1 ms per poll
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     const long long t0 = clock64();
     for (uint32_t it = 0; it < kWaitLimit; ++it) {
-        if ((it & 1023u) == 1023u && clock64() - t0 > kWaitCycles) return false;
         uint32_t done;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
-            : "r"(bar), "r"(parity)
+            : "r"(bar), "r"(parity), "r"(kSuspendNs)
             : "memory");
         if (done) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
     }
     return false;
 }
@@ -283,8 +288,9 @@ __global__ void __launch_bounds__(128, 2) m2_gemm_tc_kernel(const M2Node* __rest
 //   warp 0     X producer: one cp.async.bulk.tensor load per chunk
 //   warps 1-4  converters: one row of X per thread (its TMEM lane), raw FP32 ->
 //              hi / lo TF32 stored with tcgen05.st; then the epilogue
-//   warp 5     tensor memory allocation and MMA issue; tcgen05.commit frees the
-//              V^T stage and the TMEM operand stage
+//   warp 5     tensor memory allocation and MMA issue: one wait (tm_full: the
+//              converters' TMEM stores, and the V^T tiles, checked by one converter) and
+//              one tcgen05.commit (freeing the V^T stage and the TMEM stage) per chunk
 //   warp 6     V^T producer: the hi and lo tiles of each chunk (L2-resident: the
 //              row tiles of one matrix share them)
 // Two CTAs share an SM, so one's prologue and epilogue overlap the other's streaming.
@@ -296,6 +302,7 @@ namespace {
 constexpr int kXStages = 3;    // X ring; two CTAs per SM: 2 x 97 KiB of shared memory
 constexpr int kVStages = 3;    // V^T ring
 constexpr int kTmStages = 3;   // TMEM operand stages: columns 64 + 64 t, t < 3, of 256
+static_assert(kVStages == kTmStages, "chunk c uses V^T stage and TMEM stage c % 3: one barrier frees both");
 constexpr int kRawX = kTM * 128;   // 128 rows x 128 B
 constexpr int kRawV = kTN * 128;   // 64 rows x 128 B (one of hi / lo)
 constexpr int kStreamThreads = 224;
@@ -353,8 +360,10 @@ __global__ void __launch_bounds__(kStreamThreads, 2) m2_gemm_tc_stream_kernel(co
                                                                                int* __restrict__ err, int inject) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t x_full[kXStages], x_empty[kXStages];
-    __shared__ __align__(8) uint64_t v_full[kVStages], v_empty[kVStages];
-    __shared__ __align__(8) uint64_t tm_full[kTmStages], tm_empty[kTmStages];
+    __shared__ __align__(8) uint64_t v_full[kVStages];
+    // tm_full[t]: TMEM operand stage t written and V^T stage t landed (one wait for the
+    // MMA thread); freed[t]: the MMAs of stage t done (one commit frees both stages)
+    __shared__ __align__(8) uint64_t tm_full[kTmStages], freed[kTmStages];
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t tmem_base;
     unsigned char* xring = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -385,13 +394,11 @@ __global__ void __launch_bounds__(kStreamThreads, 2) m2_gemm_tc_stream_kernel(co
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&x_full[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_addr(&x_empty[s])));
         }
-        for (int s = 0; s < kVStages; ++s) {
+        for (int s = 0; s < kVStages; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&v_full[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&v_empty[s])));
-        }
         for (int t = 0; t < kTmStages; ++t) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(&tm_full[t])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&tm_empty[t])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&freed[t])));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&done_bar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -411,7 +418,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) m2_gemm_tc_stream_kernel(co
             const bool isx = warp == 0;
             const int S = isx ? kXStages : kVStages;
             uint64_t* full = isx ? x_full : v_full;
-            uint64_t* empty = isx ? x_empty : v_empty;
+            uint64_t* empty = isx ? x_empty : freed;
             if (isx) {
                 asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmx) : "memory");
             } else {
@@ -453,7 +460,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) m2_gemm_tc_stream_kernel(co
         for (int c = 0; c < nch && ok; ++c) {
             const int s = c % kXStages, t = c % kTmStages;
             ok = mbar_wait(smem_addr(&x_full[s]), (uint32_t)((c / kXStages) & 1));
-            if (ok && c >= kTmStages) ok = mbar_wait(smem_addr(&tm_empty[t]), (uint32_t)((c / kTmStages - 1) & 1));
+            if (ok && c >= kTmStages) ok = mbar_wait(smem_addr(&freed[t]), (uint32_t)((c / kTmStages - 1) & 1));
             if (!ok) break;
             const unsigned char* rowp = xring + s * kRawX + (r >> 3) * 1024 + (r & 7) * 128;
             float4 v[8];
@@ -473,15 +480,16 @@ __global__ void __launch_bounds__(kStreamThreads, 2) m2_gemm_tc_stream_kernel(co
             tmem_store32(tmem + lane_base + col + 32, lo);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_addr(&tm_full[t]));
+            // one converter also waits for the chunk's V^T tiles, so that tm_full covers them
+            if (warp == 1 && lane == 0) ok = mbar_wait(smem_addr(&v_full[t]), (uint32_t)((c / kTmStages) & 1));
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (ok && lane == 0) mbar_arrive(smem_addr(&tm_full[t]));
         }
     } else if (lane == 0) {
         // ---------------- MMA issue (warp 5, one thread)
         for (int c = 0; c < nch && ok; ++c) {
-            const int t = c % kTmStages, sv = c % kVStages;
+            const int t = c % kTmStages, sv = t;
             ok = mbar_wait(smem_addr(&tm_full[t]), (uint32_t)((c / kTmStages) & 1));
-            if (ok) ok = mbar_wait(smem_addr(&v_full[sv]), (uint32_t)((c / kVStages) & 1));
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const unsigned char* st = vring + sv * 2 * kRawV;
@@ -501,9 +509,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) m2_gemm_tc_stream_kernel(co
                         "r"(at), "l"(bd), "r"(kIdesc), "r"(acc));
                 }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_addr(&tm_empty[t])));
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_addr(&v_empty[sv])));
+                smem_addr(&freed[t])));
             if (c == nch - 1)
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     smem_addr(&done_bar)));

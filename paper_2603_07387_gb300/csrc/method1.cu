@@ -462,19 +462,30 @@ __global__ void __launch_bounds__(256) m1_spectrum_kernel(const M1Tensor* __rest
     // so sum_j = P[0] + P[M] + 2 Re sum_{0<k<M} P[k] (m >= 2).
     double* yr = yrep + N.y_off + (int64_t)r * O;
     if (N.n_ot == 0) {
-        double acc = 0;
+        double acc = 0, aab = 0;  // the sum and the magnitude sum (for the FP64 criterion)
         for (int k = threadIdx.x; k < K; k += blockDim.x) {
             double wgt = (m == 1 || k == 0 || k == M) ? 1.0 : 2.0;
             acc += wgt * (double)P[k].x;
+            aab += wgt * hypot((double)P[k].x, (double)P[k].y);
         }
 #pragma unroll
-        for (int sft = 16; sft > 0; sft >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sft);
-        if (lane == 0) dred[warp] = acc;
+        for (int sft = 16; sft > 0; sft >>= 1) {
+            acc += __shfl_xor_sync(0xffffffffu, acc, sft);
+            aab += __shfl_xor_sync(0xffffffffu, aab, sft);
+        }
+        if (lane == 0) {
+            dred[warp] = acc;
+            dred[16 + warp] = aab;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double t = 0;
-            for (int q = 0; q < nw; ++q) t += dred[q];
+            double t = 0, ta = 0;
+            for (int q = 0; q < nw; ++q) {
+                t += dred[q];
+                ta += dred[16 + q];
+            }
             yr[0] = ldexp(t, E) / (double)m;
+            yrep[N.yabs_off + r] = ldexp(ta, E) / (double)m;
         }
         return;
     }

@@ -131,6 +131,10 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
         return TNSK_ERR_INVALID;
     }
     const bool fp64 = prm.prec == TNSK_PREC_FP64;
+    if (prm.prec == TNSK_PREC_AUTO) {
+        why = "TNSK_PREC_AUTO is taken by tnsk_estimate only (one network, method 1, no open legs)";
+        return TNSK_ERR_UNSUPPORTED;
+    }
     if (prm.prec != TNSK_PREC_FP32 && prm.prec != TNSK_PREC_BF16 && prm.prec != TNSK_PREC_FP64) {
         why = "unknown precision";
         return TNSK_ERR_INVALID;
@@ -1088,6 +1092,8 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
         P.m1.work_count[c] = (int)m1w_cls[c].size();
         m1w.insert(m1w.end(), m1w_cls[c].begin(), m1w_cls[c].end());
     }
+    // the per-rep magnitude sums of method-1 networks follow all per-rep estimates
+    for (M1Net& nb : m1n) nb.yabs_off = nb.y_off + yrep_n;
     size_t o_reqs = stage(H, reqs), o_m1t = stage(H, m1t), o_m1n = stage(H, m1n), o_m1w = stage(H, m1w);
     const int n_block_items = (int)m1items.size();
     for (int sl = 0; sl < M1Plan::kWarpSlots; ++sl) {
@@ -1132,7 +1138,8 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     P.m2.tmaps_off = P.desc_off + o_tmaps;
     // ---- zeroed region: per-rep estimates, method-1 sketches, method-2 x accumulators
     P.zero_off = P.arena.take(0);
-    P.yrep_off = P.arena.take((size_t)yrep_n * sizeof(double));
+    P.yrep_off = P.arena.take((size_t)2 * yrep_n * sizeof(double));  // estimates, then magnitude sums
+    P.yrep_n = yrep_n;
     P.m1.xs_off = P.arena.take((size_t)xs_n * acc);
     P.m1.xs_count = xs_n;
     P.m2.ws_off = P.arena.take((size_t)(ws_x + ws_w + ws_r + ws_v) * acc);

@@ -97,6 +97,7 @@ struct BatchPlan {
     int64_t n_table_rows = 0;  // (request, rep) rows
     size_t tabs_off = 0;
     size_t yrep_off = 0;
+    int64_t yrep_n = 0;  // per-rep estimates at yrep_off; the magnitude sums follow them
     size_t comb_off = 0;
     int n_comb = 0;
     int m1_reps = 0;  // repetitions of the first method-1 network (turnstile streams)

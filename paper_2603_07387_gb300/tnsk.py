@@ -31,7 +31,7 @@ F64, F32, BF16 = 0, 1, 2
 GENERAL, ACYCLIC, CROSSCORR = 1, 2, 3  # tnsk_method (CROSSCORR: the earlier cross-correlation estimator)
 KERNEL_KINDS = ("tables", "m1_scatter", "m1_spectrum", "m2_leaf", "m2_compose", "m2_vbuild", "m2_gemm",
                 "m2_root", "combine", "m2_scatter", "pairs", "normalize")
-PREC_FP32, PREC_BF16, PREC_FP64 = 0, 1, 2
+PREC_FP32, PREC_BF16, PREC_FP64, PREC_AUTO = 0, 1, 2, 3
 
 # exported symbols declared in include/tnsk.h
 SYMBOLS = (
@@ -53,6 +53,7 @@ SYMBOLS = (
     "tnsk_sync",
     "tnsk_probe_shared_atomics",
     "tnsk_probe_shared_int_adds",
+    "tnsk_auto_report",
     "tnsk_combine",
     "tnsk_stream_create",
     "tnsk_stream_update",
@@ -218,6 +219,8 @@ def load_library(path: str = LIB_PATH):
     L.tnsk_probe_shared_atomics.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.tnsk_probe_shared_int_adds.restype = i32
     L.tnsk_probe_shared_int_adds.argtypes = [vp, vp]
+    L.tnsk_auto_report.restype = i32
+    L.tnsk_auto_report.argtypes = [vp, vp, vp]
     L.tnsk_status_string.restype = ctypes.c_char_p
     L.tnsk_status_string.argtypes = [i32]
     L.tnsk_last_error.restype = ctypes.c_char_p
@@ -790,6 +793,13 @@ class Context:
         v = ctypes.c_double(0.0)
         self._check(self.lib.tnsk_probe_shared_int_adds(self.h, ctypes.byref(v)))
         return v.value
+
+    def auto_report(self):
+        """(reps recomputed in FP64, largest relative rounding bound of a per-rep value)
+        of the last TNSK_PREC_AUTO estimate on this context."""
+        n, b = ctypes.c_int32(0), ctypes.c_double(0.0)
+        self._check(self.lib.tnsk_auto_report(self.h, ctypes.byref(n), ctypes.byref(b)))
+        return int(n.value), float(b.value)
 
     def sync(self):
         self._check(self.lib.tnsk_sync(self.h))
