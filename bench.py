@@ -888,9 +888,11 @@ def prior_bias(ctx, dev, n: int = 16, ps=(3, 4, 5), m: int = 64, reps: int = 163
 def batched_uneven(ctx, dev, n_nets: int = 4096, m: int = 256, reps: int = 64, steps: int = 3):
     """Method 1 on n_nets random connected networks (4..12 tensors, degree 2..4, edge dims
     2..16, 0..2 open legs of dim 2..16, N(0,1) FP32; ~2.6e8 entries, 1 GB at 4096), m and
-    R fixed: all networks in one plan (one CUDA-graph replay per step) against the plain
-    form, one tnsk_estimate call per network. Estimates/s of each (an estimate = all
-    output entries of one network, combined over its reps)."""
+    R fixed: all networks in one plan (one CUDA-graph replay per step), the same plan
+    under the scatter schedule tnsk_autotune picks for it, and the plain form, one
+    tnsk_estimate call per network. Estimates/s of each (an estimate = all output
+    entries of one network, combined over its reps); `ratio` = plain time over the
+    faster batched form's."""
     import torch
 
     from paper_2603_07387_gb300 import tnsk
@@ -923,6 +925,25 @@ def batched_uneven(ctx, dev, n_nets: int = 4096, m: int = 256, reps: int = 64, s
     prof = ctx.profile_read()
     ctx.profile(False)
     plan.close()
+    # the scatter schedule picked by the autotuner, then the same batch planned with it
+    t0 = time.perf_counter()
+    sched, ms_def, ms_tuned = ctx.autotune(nets, params, trials=2)
+    tune_s = time.perf_counter() - t0
+    plan = ctx.plan(nets, params, outs, schedule=sched)
+    plan.run()
+    plan.run()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        plan.run()
+    e1.record()
+    torch.cuda.synchronize()
+    tuned_s = e0.elapsed_time(e1) / 1e3 / steps
+    ctx.profile(True)
+    plan.run()
+    tprof = ctx.profile_read()
+    ctx.profile(False)
+    plan.close()
     for i in range(min(64, n_nets)):  # warm-up of the per-network path
         ctx.estimate(nets[i], params[i], outs[i])
     torch.cuda.synchronize()
@@ -940,8 +961,12 @@ def batched_uneven(ctx, dev, n_nets: int = 4096, m: int = 256, reps: int = 64, s
             "batched": {"estimates_per_s": round(n_nets / batched_s, 1), "ms_per_batch": round(batched_s * 1e3, 3),
                         "kernel_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
                         "scatter_gupdates_per_s": round(upd / (sc_ms / 1e3) / 1e9, 1)},
+            "tuned": {"estimates_per_s": round(n_nets / tuned_s, 1), "ms_per_batch": round(tuned_s * 1e3, 3),
+                      "scatter_ms": round(tprof["m1_scatter"][0], 3),
+                      "autotune": {"seconds": round(tune_s, 2), "scatter_ms_default": round(ms_def, 3),
+                                   "scatter_ms_tuned": round(ms_tuned, 3), "schedule": sched.as_dict()}},
             "plain": {"estimates_per_s": round(n_nets / plain_s, 1), "ms_total": round(plain_s * 1e3, 1)},
-            "ratio": round(plain_s / batched_s, 2)}
+            "ratio": round(plain_s / min(batched_s, tuned_s), 2)}
 
 
 # ---------------------------------------------------------------- learned-size batched form vs plain form

@@ -336,6 +336,39 @@ tnsk_status tnsk_plan_destroy(tnsk_plan* plan);
  * a synchronous copy. Every call reuses the same array (each device has its own),
  * so calls on one device whose GPU work overlaps, from two streams or two host
  * threads, race: order them on one stream. */
+/* Scatter schedule of a plan (row a2's work items: chunks of a tensor's entries x
+ * batches of its reps, one CTA each), per scatter list l = c + 4 k, c the tensor's
+ * order class (order <= 2, <= 4, <= 6, above) and k its kernel (0: the FP32 / FP64
+ * atomic kernel, 1: the fixed-point kernel with 16-byte loads, 2: the fixed-point
+ * kernel with single loads):
+ *   rep_cap[l]     most reps one work item sketches in one pass over its entries
+ *                  (0 = default: 32 with privatised bins, 16 without; values above
+ *                  those are clamped to them and to what fits in shared memory);
+ *   chunk_scale[l] entries per work item as a multiple of the default chunk (0 or 1 =
+ *                  default; tensors whose tables are staged per chunk keep 1).
+ * Any schedule gives the same estimates up to FP32 rounding order. */
+#define TNSK_SCATTER_LISTS 12
+typedef struct {
+    int32_t rep_cap[TNSK_SCATTER_LISTS];
+    int32_t chunk_scale[TNSK_SCATTER_LISTS];
+} tnsk_schedule;
+
+/* Autotuner of the scatter schedule of a batch (the arguments of tnsk_estimate_batch
+ * without outputs): plans the batch under each candidate (rep_cap in {8, 16, 32} x
+ * chunk_scale in {1, 2, 4}, applied to every list), runs each list's scatter launch
+ * `trials` times (1..64) on the ctx stream inside the ctx's scratch (CUDA events;
+ * the scratch's contents are overwritten), and writes to *sched, per list, the
+ * candidate with the least mean time. ms_default / ms_tuned (may be NULL) receive the
+ * summed per-launch scatter time of the default schedule and of the chosen one.
+ * Synchronous. Errors as tnsk_estimate_batch; TNSK_ERR_INVALID for trials outside
+ * 1..64 or a NULL sched. */
+tnsk_status tnsk_autotune(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
+                          int32_t trials, tnsk_schedule* sched, double* ms_default, double* ms_tuned);
+/* tnsk_plan_create with a scatter schedule (sched NULL: the default one). */
+tnsk_status tnsk_plan_create_scheduled(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets,
+                                       const tnsk_params* params, double* const* outs, double* const* per_reps,
+                                       const tnsk_schedule* sched, tnsk_plan** plan);
+
 /* The last TNSK_PREC_AUTO estimate on this ctx: reps recomputed in FP64 and the
  * largest relative rounding bound of a per-rep value (see TNSK_PREC_AUTO); 0 and 0
  * before the first. Either pointer may be NULL. */

@@ -256,7 +256,8 @@ tnsk_status tnsk_count_sketch(tnsk_ctx* ctx, uint64_t seed, uint64_t rep, uint64
 // Host part of a batch: validation and layout of descriptors and scratch.
 static tnsk_status build_plan(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
                               double* const* outs, double* const* per_reps, bool sketch_only, BatchPlan& plan,
-                              bool& fp64, bool zero_ok = false, const NormBatch* nb = nullptr) {
+                              bool& fp64, bool zero_ok = false, const NormBatch* nb = nullptr,
+                              const tnsk_schedule* sched = nullptr) {
     if (B < 0 || (B > 0 && (!nets || !params))) return fail(ctx, TNSK_ERR_INVALID, "null batch arguments");
     std::vector<NetInfo> infos(B);
     for (int b = 0; b < B; ++b) {
@@ -271,7 +272,7 @@ static tnsk_status build_plan(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets
     for (int b = 1; b < B; ++b)
         if ((params[b].prec == TNSK_PREC_FP64) != fp64)
             return fail(ctx, TNSK_ERR_UNSUPPORTED, "mixed precisions in one batch");
-    return plan_batch(infos, nets, params, outs, per_reps, fp64, sketch_only, plan, ctx->last_error);
+    return plan_batch(infos, nets, params, outs, per_reps, fp64, sketch_only, plan, ctx->last_error, sched);
 }
 
 // Device part: the launch sequence of a planned batch whose descriptors are
@@ -510,7 +511,8 @@ tnsk_status tnsk_profile_read(tnsk_ctx* ctx, double* ms, int64_t* launches) {
 }
 
 static tnsk_status create_plan(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
-                               double* const* outs, double* const* per_reps, bool zero_ok, tnsk_plan** out) {
+                               double* const* outs, double* const* per_reps, bool zero_ok, tnsk_plan** out,
+                               const tnsk_schedule* sched = nullptr) {
     if (!out) return TNSK_ERR_INVALID;
     *out = nullptr;
     tnsk_status st = check_ctx(ctx);
@@ -546,7 +548,7 @@ static tnsk_status create_plan(tnsk_ctx* ctx, int32_t B, const tnsk_network* net
         p->nr = NormRun{(const NormJob*)(p->norm_dev + p->norm.desc_off), (int)p->norm.jobs.size(), p->norm.most};
     }
     st = build_plan(ctx, B, p->norm.used ? p->norm.view.data() : nets, params, outs, per_reps, false, p->plan,
-                    p->fp64, zero_ok, &p->norm);
+                    p->fp64, zero_ok, &p->norm, sched);
     if (st != TNSK_OK) {
         drop();
         return st;
@@ -578,6 +580,117 @@ static tnsk_status create_plan(tnsk_ctx* ctx, int32_t B, const tnsk_network* net
 tnsk_status tnsk_plan_create(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
                              double* const* outs, double* const* per_reps, tnsk_plan** out) {
     return create_plan(ctx, B, nets, params, outs, per_reps, false, out);
+}
+
+tnsk_status tnsk_plan_create_scheduled(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets,
+                                       const tnsk_params* params, double* const* outs, double* const* per_reps,
+                                       const tnsk_schedule* sched, tnsk_plan** out) {
+    return create_plan(ctx, B, nets, params, outs, per_reps, false, out, sched);
+}
+
+// The scatter autotuner (tnsk.h): every candidate schedule planned on the host and
+// laid out in the ctx scratch; per scatter list the launch is timed alone.
+tnsk_status tnsk_autotune(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
+                          int32_t trials, tnsk_schedule* sched, double* ms_default, double* ms_tuned) {
+    tnsk_status st = check_ctx(ctx);
+    if (st != TNSK_OK) return st;
+    if (!sched || trials < 1 || trials > 64) return fail(ctx, TNSK_ERR_INVALID, "autotune: arguments");
+    constexpr int L = TNSK_SCATTER_LISTS;
+    static const int kCaps[] = {8, 16, 32}, kScales[] = {1, 2, 4};
+    struct Cand {
+        int cap, scale;
+    };
+    std::vector<Cand> cands;
+    for (int c : kCaps)
+        for (int s : kScales) cands.push_back({c, s});
+    NormBatch nb;
+    std::string why;
+    st = normalize_batch(B, nets, params, nb, why);
+    if (st != TNSK_OK) return fail(ctx, st, why);
+    if (!nb.jobs.empty()) {
+        st = ensure_buffer(ctx, ctx->norm, ctx->norm_bytes, nb.bytes, "normalisation buffer");
+        if (st != TNSK_OK) return st;
+        normalize_bind(nb, ctx->norm);
+    }
+    const tnsk_network* view = nb.used ? nb.view.data() : nets;
+    // outputs are not written (only the scatter runs); the planner wants non-null ones
+    std::vector<double*> outs(B, nullptr);
+    double dummy = 0.0;
+    for (int b = 0; b < B; ++b) outs[b] = &dummy;
+    std::vector<std::vector<double>> ms(cands.size() + 1, std::vector<double>(L, 0.0));
+    std::vector<std::vector<int>> cnt(cands.size() + 1, std::vector<int>(L, 0));
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return cuda_fail(ctx, cudaGetLastError(), "autotune events");
+    auto done = [&](tnsk_status s) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return s;
+    };
+    for (size_t ci = 0; ci <= cands.size(); ++ci) {  // the last entry: the default schedule
+        tnsk_schedule cs{};
+        if (ci < cands.size())
+            for (int l = 0; l < L; ++l) {
+                cs.rep_cap[l] = cands[ci].cap;
+                cs.chunk_scale[l] = cands[ci].scale;
+            }
+        BatchPlan plan;
+        bool fp64 = false;
+        st = build_plan(ctx, B, view, params, outs.data(), nullptr, false, plan, fp64, false, &nb,
+                        ci < cands.size() ? &cs : nullptr);
+        if (st != TNSK_OK) return done(st);
+        st = ensure_scratch(ctx, plan.arena.used);
+        if (st != TNSK_OK) return done(st);
+        unsigned char* base = ctx->scratch;
+        st = finalize_plan(plan, base, ctx->last_error);
+        if (st != TNSK_OK) return done(st);
+        if (!plan.host_desc.empty() &&
+            cudaMemcpyAsync(base + plan.desc_off, plan.host_desc.data(), plan.host_desc.size(), cudaMemcpyHostToDevice,
+                            ctx->stream) != cudaSuccess)
+            return done(cuda_fail(ctx, cudaGetLastError(), "autotune descriptors"));
+        if (plan.zero_bytes && cudaMemsetAsync(base + plan.zero_off, 0, plan.zero_bytes, ctx->stream) != cudaSuccess)
+            return done(cuda_fail(ctx, cudaGetLastError(), "autotune memset"));
+        if (plan.n_reqs &&
+            launch_draw_tables((const TabReq*)(base + plan.reqs_off), plan.n_reqs, plan.n_table_rows,
+                               (uint32_t*)(base + plan.tabs_off), ctx->stream) != cudaSuccess)
+            return done(cuda_fail(ctx, cudaGetLastError(), "autotune tables"));
+        void* xs = base + plan.m1.xs_off;
+        for (int l = 0; l < L; ++l) {
+            cnt[ci][l] = plan.m1.work_count[l];
+            if (!plan.m1.work_count[l]) continue;
+            // one untimed launch, then `trials` timed ones
+            cudaError_t e = launch_m1_scatter_list(plan, base, xs, fp64, l, ctx->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+            for (int t = 0; t < trials && e == cudaSuccess; ++t)
+                e = launch_m1_scatter_list(plan, base, xs, fp64, l, ctx->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e != cudaSuccess) return done(cuda_fail(ctx, e, "autotune launch"));
+            ms[ci][l] = (double)t / trials;
+        }
+    }
+    // per list, the fastest candidate (a list a candidate leaves empty moved its work to
+    // another list, so such candidates are compared on the list sums of every list)
+    *sched = tnsk_schedule{};
+    const size_t def = cands.size();
+    double tot_def = 0.0, tot_best = 0.0;
+    for (int l = 0; l < L; ++l) tot_def += ms[def][l];
+    for (int l = 0; l < L; ++l) {
+        if (!cnt[def][l]) continue;
+        size_t best = def;
+        for (size_t ci = 0; ci < cands.size(); ++ci)
+            if (cnt[ci][l] && ms[ci][l] < ms[best][l]) best = ci;
+        tot_best += ms[best][l];
+        if (best != def) {
+            sched->rep_cap[l] = cands[best].cap;
+            sched->chunk_scale[l] = cands[best].scale;
+        }
+    }
+    if (ms_default) *ms_default = tot_def;
+    if (ms_tuned) *ms_tuned = tot_best;
+    return done(TNSK_OK);
 }
 
 tnsk_status tnsk_plan_run(tnsk_ctx* ctx, tnsk_plan* plan) {

@@ -609,6 +609,22 @@ cudaError_t launch_m1_spectrum(const M1Tensor* d_tens, const M1Net* d_nets, cons
     return cudaGetLastError();
 }
 
+cudaError_t launch_m1_scatter_list(const BatchPlan& plan, unsigned char* base, void* xs, bool fp64, int list,
+                                   cudaStream_t s) {
+    static const int kClassOrder[M1Plan::kOrderClasses] = {2, 4, 6, TNSK_MAX_ORDER};
+    const M1Tensor* tens = (const M1Tensor*)(base + plan.m1.tens_off);
+    const M1Net* nets = (const M1Net*)(base + plan.m1.nets_off);
+    const M1Work* work = (const M1Work*)(base + plan.m1.work_off);
+    const uint32_t* tabs = (const uint32_t*)(base + plan.tabs_off);
+    const int c = list % M1Plan::kOrderClasses, k = list / M1Plan::kOrderClasses;
+    if (k == 0)
+        return launch_m1_scatter(tens, nets, work + plan.m1.work_first[list], plan.m1.work_count[list], tabs, xs, fp64,
+                                 plan.m1.class_smem[list], kClassOrder[c], s);
+    if (fp64) return cudaSuccess;
+    return launch_m1_scatter_fx(tens, nets, work + plan.m1.work_first[list], plan.m1.work_count[list], tabs,
+                                (float*)xs, plan.m1.class_smem[list], kClassOrder[c], k == 1, s);
+}
+
 cudaError_t launch_m1_scatters(const BatchPlan& plan, unsigned char* base, void* xs, bool fp64, cudaStream_t s) {
     const M1Tensor* tens = (const M1Tensor*)(base + plan.m1.tens_off);
     const M1Net* nets = (const M1Net*)(base + plan.m1.nets_off);

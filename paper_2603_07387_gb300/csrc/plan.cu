@@ -395,7 +395,7 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
 
 tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* nets, const tnsk_params* params,
                        double* const* outs, double* const* per_reps, bool fp64, bool sketch_only, BatchPlan& P,
-                       std::string& err) {
+                       std::string& err, const tnsk_schedule* sched) {
     const int B = (int)infos.size();
     const size_t acc = fp64 ? sizeof(double) : sizeof(float);
     std::vector<TabReq> reqs;
@@ -589,28 +589,46 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 static const int kClassOrder[M1Plan::kOrderClasses] = {2, 4, 6, TNSK_MAX_ORDER};
                 // FP32 sketches with privatised bins: the fixed-point kernel, 4-byte integer
                 // bins plus an FP32 accumulator when an item spans more than one batch
-                const int64_t CHp = std::max<int64_t>(8192, 32 * T.O * m);
-                const bool fx_multi = std::min<int64_t>(T.numel, CHp) > m1_fx_batch(kClassOrder[cls]);
-                const size_t bin_fx = (size_t)T.O * m * 4 * (fx_multi ? 2 : 1);
-                // (bins that fit only as FP32 words keep the atomic kernel)
-                const bool fx = !fp64 && tab_b + bin_fx + 16 <= kScatterSmemBudget;
-                const size_t bin_p = fx ? bin_fx : bin_b;
-                int64_t nrep_priv = (int64_t)(kScatterSmemBudget / (tab_b + bin_p + 16));
-                bool priv = nrep_priv >= 1 && T.numel * 4 >= T.O * m;
-                int nrep;
-                if (priv)
-                    nrep = (int)std::min<int64_t>({(int64_t)R, nrep_priv, 32});
-                else
-                    nrep = (int)std::min<int64_t>({(int64_t)R, std::max<int64_t>(1, (int64_t)(kScatterSmemBudget / (tab_b + 16))), 16});
-                // chunks: privatised bins are flushed once per chunk, so a chunk has at least
-                // 32x as many entries as bins (a few percent of flush per update)
-                const int64_t CH = priv ? CHp : (gtab ? 65536 : 8192);
-                size_t sm = ((size_t)nrep * tab_b + 15) / 16 * 16 + (priv ? (size_t)nrep * bin_p : 0);
                 // the fixed-point kernel's four-entry loads: FP32 data, 16-byte aligned, last
                 // dim a multiple of 4 (so are the chunk bounds)
                 const bool vec4 = T.dtype == TNSK_F32 && T.order >= 1 && (T.dims[T.order - 1] & 3) == 0 &&
                                   ((uintptr_t)T.data & 15) == 0;
-                const int list = cls + M1Plan::kOrderClasses * ((fx && priv) ? (vec4 ? 1 : 2) : 0);
+                // the item sizes: the default chunk, then the schedule's multiple of it for
+                // the tensor's scatter list (kept only where the bins still fit)
+                int list = 0, nrep = 1;
+                int64_t CH = 8192;
+                size_t bin_p = 0;
+                bool priv = false;
+                for (int pass = 0; pass < 2; ++pass) {
+                    int scale = 1;
+                    if (pass == 1 && sched && !gtab && !ltab)
+                        scale = std::max(1, std::min(64, (int)sched->chunk_scale[list]));
+                    if (pass == 1 && scale == 1) break;
+                    const int64_t CHp = std::max<int64_t>(8192, 32 * T.O * m) * scale;
+                    const bool fx_multi = std::min<int64_t>(T.numel, CHp) > m1_fx_batch(kClassOrder[cls]);
+                    const size_t bin_fx = (size_t)T.O * m * 4 * (fx_multi ? 2 : 1);
+                    // (bins that fit only as FP32 words keep the atomic kernel)
+                    const bool fx = !fp64 && tab_b + bin_fx + 16 <= kScatterSmemBudget;
+                    const size_t bp = fx ? bin_fx : bin_b;
+                    const int64_t nrep_priv = (int64_t)(kScatterSmemBudget / (tab_b + bp + 16));
+                    const bool pv = nrep_priv >= 1 && T.numel * 4 >= T.O * m;
+                    const int l = cls + M1Plan::kOrderClasses * ((fx && pv) ? (vec4 ? 1 : 2) : 0);
+                    if (pass == 1 && l != list) break;  // the larger chunk would change the kernel
+                    list = l;
+                    priv = pv;
+                    bin_p = bp;
+                    const int cap = sched && sched->rep_cap[l] > 0 ? (int)sched->rep_cap[l] : (pv ? 32 : 16);
+                    if (pv)
+                        nrep = (int)std::min<int64_t>({(int64_t)R, nrep_priv, std::min(cap, 32)});
+                    else
+                        nrep = (int)std::min<int64_t>(
+                            {(int64_t)R, std::max<int64_t>(1, (int64_t)(kScatterSmemBudget / (tab_b + 16))),
+                             std::min(cap, 16)});
+                    // chunks: privatised bins are flushed once per chunk, so a chunk has at
+                    // least 32x as many entries as bins (a few percent of flush per update)
+                    CH = pv ? CHp : (gtab ? 65536 : 8192) * scale;
+                }
+                size_t sm = ((size_t)nrep * tab_b + 15) / 16 * 16 + (priv ? (size_t)nrep * bin_p : 0);
                 P.m1.class_smem[list] = std::max(P.m1.class_smem[list], sm);
                 for (int r0 = 0; r0 < R; r0 += nrep)
                     for (int64_t b0 = 0; b0 < T.numel; b0 += CH) {

@@ -57,6 +57,7 @@ struct M1Plan {
     // (FP32 sketches with privatised bins; 1: four entries per 16-byte load, 2: one)
     static constexpr int kOrderClasses = 4;
     static constexpr int kScatterLists = 3 * kOrderClasses;
+    static_assert(kScatterLists == TNSK_SCATTER_LISTS, "tnsk_schedule covers every scatter list");
     int work_first[kScatterLists] = {};
     int work_count[kScatterLists] = {};
     size_t class_smem[kScatterLists] = {16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16};
@@ -108,6 +109,9 @@ struct BatchPlan {
 // Launches the spectrum kernels of every method-1 item of the plan (rows a3 + a4).
 // Launches the scatter of every method-1 work item (row a2), one launch per order class.
 cudaError_t launch_m1_scatters(const BatchPlan& plan, unsigned char* base, void* xs, bool fp64, cudaStream_t s);
+// The scatter launch of one list (class + kOrderClasses x kernel kind) alone.
+cudaError_t launch_m1_scatter_list(const BatchPlan& plan, unsigned char* base, void* xs, bool fp64, int list,
+                                   cudaStream_t s);
 // Turnstile updates of a one-network method-1 plan's stored sketches (every rep).
 cudaError_t launch_m1_updates(const BatchPlan& plan, unsigned char* base, int64_t n, const int32_t* tensor,
                               const int64_t* index, const double* delta, bool fp64, int* err, cudaStream_t s);
@@ -127,8 +131,9 @@ bool tensor_maps_available();
 // Encodes the plan's tensor maps into its host descriptor block once the device
 // base address of the plan's scratch is fixed (before the descriptor upload).
 tnsk_status finalize_plan(BatchPlan& plan, unsigned char* base, std::string& err);
+// sched: the scatter schedule (tnsk.h), NULL = the default one.
 tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* nets, const tnsk_params* params,
                        double* const* outs, double* const* per_reps, bool fp64, bool sketch_only, BatchPlan& plan,
-                       std::string& err);
+                       std::string& err, const tnsk_schedule* sched = nullptr);
 
 }  // namespace tnsk

@@ -45,6 +45,8 @@ SYMBOLS = (
     "tnsk_estimate_static",
     "tnsk_rewrite",
     "tnsk_plan_create",
+    "tnsk_plan_create_scheduled",
+    "tnsk_autotune",
     "tnsk_plan_run",
     "tnsk_plan_destroy",
     "tnsk_profile",
@@ -121,6 +123,18 @@ class _Network(ctypes.Structure):
     ]
 
 
+SCATTER_LISTS = 12
+
+
+class Schedule(ctypes.Structure):
+    """tnsk_schedule: per scatter list (order class c + 4 x kernel kind) the most reps
+    per work item and the chunk multiple; zeros are the defaults."""
+    _fields_ = [("rep_cap", ctypes.c_int32 * SCATTER_LISTS), ("chunk_scale", ctypes.c_int32 * SCATTER_LISTS)]
+
+    def as_dict(self):
+        return {"rep_cap": list(self.rep_cap), "chunk_scale": list(self.chunk_scale)}
+
+
 class _Params(ctypes.Structure):
     _fields_ = [
         ("m", ctypes.c_int64),
@@ -169,6 +183,14 @@ def load_library(path: str = LIB_PATH):
     L.tnsk_plan_create.restype = i32
     L.tnsk_plan_create.argtypes = [vp, i32, ctypes.POINTER(_Network), ctypes.POINTER(_Params), ctypes.POINTER(vp),
                                    ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.tnsk_plan_create_scheduled.restype = i32
+    L.tnsk_plan_create_scheduled.argtypes = [vp, i32, ctypes.POINTER(_Network), ctypes.POINTER(_Params),
+                                             ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(Schedule),
+                                             ctypes.POINTER(vp)]
+    L.tnsk_autotune.restype = i32
+    L.tnsk_autotune.argtypes = [vp, i32, ctypes.POINTER(_Network), ctypes.POINTER(_Params), i32,
+                                ctypes.POINTER(Schedule), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double)]
     L.tnsk_plan_run.restype = i32
     L.tnsk_plan_run.argtypes = [vp, vp]
     L.tnsk_plan_destroy.restype = i32
@@ -700,8 +722,22 @@ class Context:
                                                 ctypes.byref(h)))
         return Stream(self, h, list(net.tensors), out, per_rep, params.prec)
 
-    def plan(self, nets: Sequence[Network], params: Sequence[Params], outs, per_reps=None) -> "Plan":
-        """tnsk_plan_create: plan a batch once; run it with Plan.run()."""
+    def autotune(self, nets: Sequence[Network], params: Sequence[Params], trials: int = 3):
+        """tnsk_autotune: (Schedule, default scatter ms, tuned scatter ms) for the batch."""
+        B = len(nets)
+        holders = [_NetHolder(n) for n in nets]
+        carr = (_Network * max(1, B))(*[h.c for h in holders])
+        parr = (_Params * max(1, B))(*[_params(p) for p in params])
+        sched = Schedule()
+        d, t = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        self._check(self.lib.tnsk_autotune(self.h, B, carr, parr, trials, ctypes.byref(sched), ctypes.byref(d),
+                                           ctypes.byref(t)))
+        return sched, d.value, t.value
+
+    def plan(self, nets: Sequence[Network], params: Sequence[Params], outs, per_reps=None,
+             schedule: "Schedule | None" = None) -> "Plan":
+        """tnsk_plan_create (tnsk_plan_create_scheduled with a schedule): plan a batch
+        once; run it with Plan.run()."""
         B = len(nets)
         holders = [_NetHolder(n) for n in nets]
         carr = (_Network * max(1, B))(*[h.c for h in holders])
@@ -711,7 +747,11 @@ class Context:
         if per_reps is not None:
             rarr = (ctypes.c_void_p * max(1, B))(*[(r.data_ptr() if r is not None else None) for r in per_reps])
         h = ctypes.c_void_p()
-        self._check(self.lib.tnsk_plan_create(self.h, B, carr, parr, oarr, rarr, ctypes.byref(h)))
+        if schedule is None:
+            self._check(self.lib.tnsk_plan_create(self.h, B, carr, parr, oarr, rarr, ctypes.byref(h)))
+        else:
+            self._check(self.lib.tnsk_plan_create_scheduled(self.h, B, carr, parr, oarr, rarr, ctypes.byref(schedule),
+                                                            ctypes.byref(h)))
         return Plan(self, h, [n.tensors for n in nets], list(outs), per_reps)
 
     def profile(self, enable: bool = True):
