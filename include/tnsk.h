@@ -82,7 +82,8 @@ typedef enum { TNSK_GENERAL = 1, TNSK_ACYCLIC = 2, TNSK_CROSSCORR = 3 } tnsk_met
  * FP64: everything in FP64 (for high-dynamic-range sketches). */
 /* AUTO (tnsk_estimate only; method 1, no open legs): the FP32 path, then the FP64 path
  *   for the reps whose FP32 transforms may be inexact. Every spectral kernel also
- *   returns the rep's magnitude sum A_r = (1/m) sum_j |prod_k F x_k(j)|; the FP32
+ *   returns the rep's magnitude sum A_r = (1/m) sum_j (|Re| + |Im|)(prod_k F x_k(j))
+ *   (at most sqrt 2 times the sum of the moduli); the FP32
  *   rounding of the transforms and of the products is at most about
  *   c32 A_r, c32 = (p + 2 log2 m + 8) 2^-24 (p as given), so a rep with c32 A_r > 2^-17 |y_r| (a
  *   sketch whose spectrum has a high dynamic range and cancels in the sum) is flagged.

@@ -186,7 +186,7 @@ struct M1Net {
     int64_t exp_off;  // their exponents (ints) of rep 0
     int64_t exp_per_rep;
     int64_t lspec_off;  // spectra of rep 0: [R][p][m] (large m) or [R][p][m/2 + 1] (mid m), complex entries
-    int64_t yabs_off;   // per-rep magnitude sums (1/m) sum_j |prod_k F x_k(j)| [R] (networks without
+    int64_t yabs_off;   // per-rep magnitude sums (1/m) sum_j (|Re| + |Im|)(prod_k F x_k(j)) [R] (networks without
                         // open legs), in the per-rep estimate buffer after all estimates
     int32_t log2m;
     int32_t R;

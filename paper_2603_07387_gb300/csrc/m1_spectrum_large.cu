@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256) m1_spec_product_kernel(const M1Net* __res
     const M1Net& N = nets[it.x];
     const int64_t m = N.m;
     const Cplx<T>* base = lspec + N.lspec_off + (int64_t)it.y * N.p * m;
-    double acc = 0.0, aab = 0.0;  // the sum and the magnitude sum (for the FP64 criterion)
+    double acc = 0.0, aab = 0.0;  // the sum and the magnitude sum, as sum (|Re| + |Im|) (FP64 criterion)
     for (int64_t j = it.z + threadIdx.x; j < (int64_t)it.z + it.w; j += blockDim.x) {
         Cplx<T> P = {T(1), T(0)};
         int E = 0;  // the product is P 2^E
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(256) m1_spec_product_kernel(const M1Net* __res
             }
         }
         acc += ldexp((double)P.x, E);
-        aab += ldexp(hypot((double)P.x, (double)P.y), E);
+        aab += ldexp((double)(fabs(P.x) + fabs(P.y)), E);
     }
 #pragma unroll
     for (int sft = 16; sft > 0; sft >>= 1) {

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) m1_spec_product_half_kernel(const M1Net* 
     const M1Net& N = nets[it.x];
     const int64_t M = N.m >> 1, K = M + 1;
     const Cplx<T>* base = lspec + N.lspec_off + (int64_t)it.y * N.p * K;
-    double acc = 0.0, aab = 0.0;  // the sum and the magnitude sum (for the FP64 criterion)
+    double acc = 0.0, aab = 0.0;  // the sum and the magnitude sum, as sum (|Re| + |Im|) (FP64 criterion)
     for (int64_t j = it.z + threadIdx.x; j < (int64_t)it.z + it.w; j += blockDim.x) {
         Cplx<T> P = {T(1), T(0)};
         int E = 0;  // the product is P 2^E
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256) m1_spec_product_half_kernel(const M1Net* 
         }
         const double w = (j == 0 || j == M) ? 1.0 : 2.0;
         acc += w * ldexp((double)P.x, E);
-        aab += w * ldexp(hypot((double)P.x, (double)P.y), E);
+        aab += w * ldexp((double)(fabs(P.x) + fabs(P.y)), E);
     }
 #pragma unroll
     for (int sft = 16; sft > 0; sft >>= 1) {

@@ -218,12 +218,13 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
     double* yr = yrep + N.y_off + (int64_t)r * N.O;
     if (N.n_ot == 0) {
         double acc = lane == 0 ? (double)PM : 0.0;
-        double aab = lane == 0 ? fabs((double)PM) : 0.0;  // the magnitude sum, for the FP64 criterion
+        // the magnitude sum for the FP64 criterion, as sum (|Re| + |Im|): FP32 suffices
+        float aab = lane == 0 ? fabsf(PM) : 0.f;
 #pragma unroll
         for (int k = 0; k < J; ++k) {
             const int q = k1L + J * k + J * J * cL;
             acc += (q == 0 ? 1.0 : 2.0) * (double)P[k].x;
-            aab += (q == 0 ? 1.0 : 2.0) * hypot((double)P[k].x, (double)P[k].y);
+            aab += (q == 0 ? 1.f : 2.f) * (fabsf(P[k].x) + fabsf(P[k].y));
         }
 #pragma unroll
         for (int sft = 16; sft > 0; sft >>= 1) {
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
         }
         if (lane == 0) {
             yr[0] = ldexp(acc, E) / (double)m;
-            yrep[N.yabs_off + r] = ldexp(aab, E) / (double)m;
+            yrep[N.yabs_off + r] = ldexp((double)aab, E) / (double)m;
         }
         return;
     }

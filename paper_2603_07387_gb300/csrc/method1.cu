@@ -462,11 +462,12 @@ __global__ void __launch_bounds__(256) m1_spectrum_kernel(const M1Tensor* __rest
     // so sum_j = P[0] + P[M] + 2 Re sum_{0<k<M} P[k] (m >= 2).
     double* yr = yrep + N.y_off + (int64_t)r * O;
     if (N.n_ot == 0) {
-        double acc = 0, aab = 0;  // the sum and the magnitude sum (for the FP64 criterion)
+        double acc = 0;  // the sum, and the magnitude sum as sum (|Re| + |Im|) (FP64 criterion)
+        T aab = T(0);
         for (int k = threadIdx.x; k < K; k += blockDim.x) {
             double wgt = (m == 1 || k == 0 || k == M) ? 1.0 : 2.0;
             acc += wgt * (double)P[k].x;
-            aab += wgt * hypot((double)P[k].x, (double)P[k].y);
+            aab += T(wgt) * (fabs(P[k].x) + fabs(P[k].y));
         }
 #pragma unroll
         for (int sft = 16; sft > 0; sft >>= 1) {
@@ -475,7 +476,7 @@ __global__ void __launch_bounds__(256) m1_spectrum_kernel(const M1Tensor* __rest
         }
         if (lane == 0) {
             dred[warp] = acc;
-            dred[16 + warp] = aab;
+            dred[16 + warp] = (double)aab;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
