@@ -341,14 +341,15 @@ tnsk_status tnsk_plan_destroy(tnsk_plan* plan);
  * batches of its reps, one CTA each), per scatter list l = c + 4 k, c the tensor's
  * order class (order <= 2, <= 4, <= 6, above) and k its kernel (0: the FP32 / FP64
  * atomic kernel, 1: the fixed-point kernel with 16-byte loads, 2: the fixed-point
- * kernel with single loads):
+ * kernel with single loads, 3: the fixed-point kernel over whole fibers of a short
+ * contracted last mode):
  *   rep_cap[l]     most reps one work item sketches in one pass over its entries
  *                  (0 = default: 32 with privatised bins, 16 without; values above
  *                  those are clamped to them and to what fits in shared memory);
  *   chunk_scale[l] entries per work item as a multiple of the default chunk (0 or 1 =
  *                  default; tensors whose tables are staged per chunk keep 1).
  * Any schedule gives the same estimates up to FP32 rounding order. */
-#define TNSK_SCATTER_LISTS 12
+#define TNSK_SCATTER_LISTS 16
 typedef struct {
     int32_t rep_cap[TNSK_SCATTER_LISTS];
     int32_t chunk_scale[TNSK_SCATTER_LISTS];

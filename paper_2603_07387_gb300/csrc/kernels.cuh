@@ -72,6 +72,12 @@ cudaError_t launch_m1_scatter_fx(const M1Tensor* d_tens, const M1Net* d_nets, co
 int64_t m1_rowsort_slots();
 // entries per CTA batch of the fixed-point kernel for tensors of order <= max_order
 int m1_fx_batch(int max_order, bool vec4 = true);
+// the fiber kernel (FP32 sketches, a contracted last mode of L <= 16 indices): whole
+// fibers per thread, entries per CTA batch
+cudaError_t launch_m1_scatter_fiber(const M1Tensor* d_tens, const M1Net* d_nets, const M1Work* d_work, int n_work,
+                                    const uint32_t* d_tabs, float* d_xs, size_t smem, int max_order,
+                                    cudaStream_t s);
+int64_t m1_fiber_batch(int L);
 cudaError_t launch_m1_spectrum(const M1Tensor* d_tens, const M1Net* d_nets, const OpenMode* d_opens,
                                const int2* d_items, int n_items, const void* d_xs, const void* const* d_tws,
                                void* d_spec, int* d_sexp, double* d_yrep, bool fp64, int max_log2m,

@@ -622,6 +622,9 @@ cudaError_t launch_m1_scatter_list(const BatchPlan& plan, unsigned char* base, v
         return launch_m1_scatter(tens, nets, work + plan.m1.work_first[list], plan.m1.work_count[list], tabs, xs, fp64,
                                  plan.m1.class_smem[list], kClassOrder[c], s);
     if (fp64) return cudaSuccess;
+    if (k == 3)
+        return launch_m1_scatter_fiber(tens, nets, work + plan.m1.work_first[list], plan.m1.work_count[list], tabs,
+                                       (float*)xs, plan.m1.class_smem[list], kClassOrder[c], s);
     return launch_m1_scatter_fx(tens, nets, work + plan.m1.work_first[list], plan.m1.work_count[list], tabs,
                                 (float*)xs, plan.m1.class_smem[list], kClassOrder[c], k == 1, s);
 }
@@ -636,12 +639,15 @@ cudaError_t launch_m1_scatters(const BatchPlan& plan, unsigned char* base, void*
     for (int c = 0; c < M1Plan::kOrderClasses && e == cudaSuccess; ++c)
         e = launch_m1_scatter(tens, nets, work + plan.m1.work_first[c], plan.m1.work_count[c], tabs, xs, fp64,
                               plan.m1.class_smem[c], kClassOrder[c], s);
-    // FP32 privatised items: the fixed-point kernel (four-entry loads, then one-entry)
-    for (int k = 1; k <= 2 && !fp64; ++k)
+    // FP32 privatised items: the fixed-point kernel (four-entry loads, then one-entry),
+    // then the fiber kernel
+    for (int k = 1; k <= 3 && !fp64; ++k)
         for (int c = 0; c < M1Plan::kOrderClasses && e == cudaSuccess; ++c) {
             const int l = c + M1Plan::kOrderClasses * k;
-            e = launch_m1_scatter_fx(tens, nets, work + plan.m1.work_first[l], plan.m1.work_count[l], tabs,
-                                     (float*)xs, plan.m1.class_smem[l], kClassOrder[c], k == 1, s);
+            e = k == 3 ? launch_m1_scatter_fiber(tens, nets, work + plan.m1.work_first[l], plan.m1.work_count[l], tabs,
+                                                 (float*)xs, plan.m1.class_smem[l], kClassOrder[c], s)
+                       : launch_m1_scatter_fx(tens, nets, work + plan.m1.work_first[l], plan.m1.work_count[l], tabs,
+                                              (float*)xs, plan.m1.class_smem[l], kClassOrder[c], k == 1, s);
         }
     // large FP32 tensors streamed from HBM: the row-sorted form
     if (e == cudaSuccess && !fp64) e = launch_m1_rowsort(plan, base, (float*)xs, s);

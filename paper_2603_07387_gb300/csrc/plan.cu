@@ -605,14 +605,23 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                         scale = std::max(1, std::min(64, (int)sched->chunk_scale[list]));
                     if (pass == 1 && scale == 1) break;
                     const int64_t CHp = std::max<int64_t>(8192, 32 * T.O * m) * scale;
-                    const bool fx_multi = std::min<int64_t>(T.numel, CHp) > m1_fx_batch(kClassOrder[cls]);
+                    // FP32 tensors with a short contracted last mode whose entries cannot be
+                    // read four at a time take the fiber kernel (m1_scatter_fiber.cu): its
+                    // batches are whole fibers, so the bins allow for either kernel's batch
+                    const int Ld = T.dims[T.order - 1];
+                    const bool fib_shape = !fp64 && !vec4 && !gtab && T.dtype == TNSK_F32 && T.order >= 2 && Ld >= 2 &&
+                                           Ld <= 16;
+                    const int64_t batch = fib_shape ? std::min<int64_t>(m1_fx_batch(kClassOrder[cls]), m1_fiber_batch(Ld))
+                                                    : m1_fx_batch(kClassOrder[cls]);
+                    const bool fx_multi = std::min<int64_t>(T.numel, CHp) > batch;
                     const size_t bin_fx = (size_t)T.O * m * 4 * (fx_multi ? 2 : 1);
                     // (bins that fit only as FP32 words keep the atomic kernel)
                     const bool fx = !fp64 && tab_b + bin_fx + 16 <= kScatterSmemBudget;
                     const size_t bp = fx ? bin_fx : bin_b;
                     const int64_t nrep_priv = (int64_t)(kScatterSmemBudget / (tab_b + bp + 16));
                     const bool pv = nrep_priv >= 1 && T.numel * 4 >= T.O * m;
-                    const int l = cls + M1Plan::kOrderClasses * ((fx && pv) ? (vec4 ? 1 : 2) : 0);
+                    const int kind = (fx && pv) ? (vec4 ? 1 : (fib_shape ? 3 : 2)) : 0;
+                    const int l = cls + M1Plan::kOrderClasses * kind;
                     if (pass == 1 && l != list) break;  // the larger chunk would change the kernel
                     list = l;
                     priv = pv;
@@ -627,6 +636,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                     // chunks: privatised bins are flushed once per chunk, so a chunk has at
                     // least 32x as many entries as bins (a few percent of flush per update)
                     CH = pv ? CHp : (gtab ? 65536 : 8192) * scale;
+                    if (kind == 3) CH = CHp / Ld * Ld;  // whole fibers per item
                 }
                 size_t sm = ((size_t)nrep * tab_b + 15) / 16 * 16 + (priv ? (size_t)nrep * bin_p : 0);
                 P.m1.class_smem[list] = std::max(P.m1.class_smem[list], sm);

@@ -54,13 +54,14 @@ struct M1Plan {
     // launch per list with its own unrolled width and shared-memory size. List
     // c + kOrderClasses * k: k = 0 the FP32 / FP64 atomic kernel (FP64 sketches, and
     // items whose bins go straight to global memory), k = 1 / 2 the fixed-point kernel
-    // (FP32 sketches with privatised bins; 1: four entries per 16-byte load, 2: one)
+    // (FP32 sketches with privatised bins; 1: four entries per 16-byte load, 2: one),
+    // k = 3 the fixed-point fiber kernel (whole fibers of a short contracted last mode)
     static constexpr int kOrderClasses = 4;
-    static constexpr int kScatterLists = 3 * kOrderClasses;
+    static constexpr int kScatterLists = 4 * kOrderClasses;
     static_assert(kScatterLists == TNSK_SCATTER_LISTS, "tnsk_schedule covers every scatter list");
     int work_first[kScatterLists] = {};
     int work_count[kScatterLists] = {};
-    size_t class_smem[kScatterLists] = {16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16};
+    size_t class_smem[kScatterLists] = {16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16};
     int max_log2m = 0;
     // items of the warp-per-item spectrum kernel, by log2 m = 6 + slot, stored after
     // the n_items items of the block kernel

@@ -123,7 +123,7 @@ class _Network(ctypes.Structure):
     ]
 
 
-SCATTER_LISTS = 12
+SCATTER_LISTS = 16
 
 
 class Schedule(ctypes.Structure):

@@ -161,6 +161,35 @@ def test_method1_warp_spectrum_every_size(ctx, m):
         assert_parity(per, y, s, TOL[p.prec], f"{spec.name} m={m}")
 
 
+def test_method1_fiber_kernel(ctx):
+    """FP32 tensors with a short last mode whose dim is not a multiple of 4 take the
+    fiber kernel (whole fibers per thread): random networks of orders 2..7 with open
+    legs (open last modes among them); an order-4 tensor with an open mode whose one
+    item spans 19 batches of fibers (the FP32 accumulator between batches); the same
+    network with its last mode on the complement side of the edge; a tensor of several
+    chunks (items flushed by atomics); a 3000 x 7 tensor whose long mode's table is
+    staged per chunk; an open last mode of dim 3; each against the oracle."""
+    rng = np.random.default_rng(77)
+    specs = [W.random_network(rng, p_range=(4, 8), dim_range=(2, 11), open_dim_range=(2, 5)) for _ in range(6)]
+    big = rng.standard_normal((8, 40, 60, 9))
+    A, Bm, v = rng.standard_normal((40, 5)), rng.standard_normal((60, 5)), rng.standard_normal(9)
+    specs.append(W.NetSpec([big, A, Bm, v], [(1, 4), (2, 6), (5, 7), (3, 8)], [0], "fiber-multibatch"))
+    specs.append(W.NetSpec([big, A, Bm, v], [(1, 4), (2, 6), (5, 7), (8, 3)], [0], "fiber-complement"))
+    wide = rng.standard_normal((30, 20, 25, 9))
+    specs.append(W.NetSpec([wide, rng.standard_normal((30, 20, 25)), rng.standard_normal(9)],
+                           [(0, 4), (1, 5), (2, 6), (3, 7)], [], "fiber-chunks"))
+    tall = rng.standard_normal((3000, 7))
+    specs.append(W.NetSpec([tall, rng.standard_normal(3000), rng.standard_normal(7)], [(0, 2), (1, 3)], [],
+                           "fiber-staged-ranges"))
+    specs.append(W.NetSpec([rng.standard_normal((6, 5, 3)), rng.standard_normal((6, 5))], [(0, 3), (1, 4)], [2],
+                           "fiber-open-last"))
+    for i, spec in enumerate(specs):
+        p = tnsk.Params(m=1024 if 6 <= i <= 8 else 256, reps=3, seed=70 + i)
+        out, per = gpu_estimate(ctx, spec, p, torch.float32)
+        y, sc = oracle_estimate(spec, p, torch.float32)
+        assert_parity(per, y, sc, TOL[p.prec], f"{spec.name} m={p.m}")
+
+
 @pytest.mark.parametrize("prec", [tnsk.PREC_FP32, tnsk.PREC_FP64])
 def test_method1_mid_m_every_size(ctx, prec):
     """Closed networks at 2^11 <= m <= 2^14 (2^13 in FP64) take one CTA per sketch for the
