@@ -185,7 +185,7 @@ struct M1Net {
     int64_t spec_per_rep;
     int64_t exp_off;  // their exponents (ints) of rep 0
     int64_t exp_per_rep;
-    int64_t lspec_off;  // spectra of rep 0: [R][p][m] (large m) or [R][p][m/2 + 1] (mid m), complex entries
+    int64_t lspec_off;  // spectra of rep 0: [R][p][m/2] (large m, pass-1 output) or [R][p][m/2 + 1] (mid m), complex
     int64_t yabs_off;   // per-rep magnitude sums (1/m) sum_j (|Re| + |Im|)(prod_k F x_k(j)) [R] (networks without
                         // open legs), in the per-rep estimate buffer after all estimates
     int32_t log2m;

@@ -82,11 +82,16 @@ cudaError_t launch_m1_spectrum(const M1Tensor* d_tens, const M1Net* d_nets, cons
                                const int2* d_items, int n_items, const void* d_xs, const void* const* d_tws,
                                void* d_spec, int* d_sexp, double* d_yrep, bool fp64, int max_log2m,
                                cudaStream_t s);
-// m above one CTA's shared memory, no open legs: two-pass FFT per (net, rep, sketch)
-// into d_lspec, then the product and bin sum per (net, rep, bin block)
+// m above one CTA's shared memory, no open legs: pass 1 of the packed four-step FFT
+// per (net, rep, sketch) into d_lspec, then pass 2 with the product and bin sum per
+// (net, rep, pair of rows)
 cudaError_t launch_m1_large(const M1Tensor* d_tens, const M1Net* d_nets, const int4* d_fft_items, int n_fft,
-                            const int4* d_prod_items, int n_prod, const void* d_xs, const void* const* d_tws,
-                            void* d_lspec, double* d_yrep, bool fp64, cudaStream_t s);
+                            const int4* d_prod_items, int n_prod, size_t rows_smem, const void* d_xs,
+                            const void* const* d_tws, void* d_lspec, double* d_yrep, bool fp64, cudaStream_t s);
+// the large path's pass 2: shared memory for G sketches' pairs of rows, and the G
+// that fits (at most p)
+size_t m1_large_rows_smem(int log2m, int G, bool fp64);
+int m1_large_rows_group(int log2m, int p, bool fp64);
 // closed networks at 2^11 <= m <= 2^14: one CTA per (net, rep, sketch) transform into
 // the half spectra in d_lspec, then the product and bin sum per (net, rep, bin block)
 cudaError_t launch_m1_mid(const M1Tensor* d_tens, const M1Net* d_nets, const int4* d_fft_items, int n_fft,

@@ -673,7 +673,7 @@ cudaError_t launch_m1_spectra(const BatchPlan& plan, unsigned char* base, const 
                           base + plan.m1.lspec_off, yrep, fp64, s);
     if (e == cudaSuccess)
         e = launch_m1_large(tens, nets, (const int4*)(base + plan.m1.lfft_off), plan.m1.n_lfft,
-                            (const int4*)(base + plan.m1.lprod_off), plan.m1.n_lprod, xs, tws,
+                            (const int4*)(base + plan.m1.lprod_off), plan.m1.n_lprod, plan.m1.lrows_smem, xs, tws,
                             base + plan.m1.lspec_off, yrep, fp64, s);
     return e;
 }

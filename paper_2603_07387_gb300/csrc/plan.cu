@@ -660,13 +660,17 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 return TNSK_ERR_UNSUPPORTED;
             }
             if (!sketch_only && I.O > 0 && large) {
-                // two-pass FFT per (rep, sketch) through a global spectrum scratch
+                // packed transforms (M = m/2 complex values per sketch) through a global
+                // scratch: pass 1 per (rep, sketch), pass 2 and the product per (rep,
+                // pair of rows {k1, N1 - k1}, k1 <= N1/2), G sketches of a rep at a time
                 nb.lspec_off = lspec_n;
-                lspec_n += (int64_t)R * I.p * m;
+                lspec_n += (int64_t)R * I.p * (m / 2);
+                const int LM = I.log2m - 1, N1 = 1 << (LM / 2);
+                const int G = m1_large_rows_group(I.log2m, I.p, fp64);
+                P.m1.lrows_smem = std::max(P.m1.lrows_smem, m1_large_rows_smem(I.log2m, G, fp64));
                 for (int r = 0; r < R; ++r) {
                     for (int k = 0; k < I.p; ++k) lfft.push_back(make_int4((int)m1n.size(), r, k, 0));
-                    for (int64_t j0 = 0; j0 < m; j0 += 4096)
-                        lprod.push_back(make_int4((int)m1n.size(), r, (int)j0, (int)std::min<int64_t>(4096, m - j0)));
+                    for (int k1 = 0; k1 <= N1 / 2; ++k1) lprod.push_back(make_int4((int)m1n.size(), r, k1, G));
                 }
             } else if (!sketch_only && I.O == 1 && nb.n_ot == 0 && I.log2m >= 11) {
                 // closed networks at 2^11 <= m <= 2^14 (2^13 FP64): one CTA per sketch for

@@ -71,6 +71,7 @@ struct M1Plan {
     // large-m items (two-pass FFT, then the product over bin blocks) and their spectra
     size_t lfft_off = 0, lprod_off = 0, lspec_off = 0;
     int n_lfft = 0, n_lprod = 0;
+    size_t lrows_smem = 16;  // shared memory of the pass-2 kernel (largest group of rows)
     // mid-m closed networks (m1_spectrum_mid.cu): the same two item lists, spectra in
     // the same scratch; shared memory sized by the largest m
     size_t mfft_off = 0, mprod_off = 0;
