@@ -922,19 +922,22 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 for (int r = 0; r < R; ++r) pend.push_back({h, M2_COMPOSE, M2Item{node_idx, r, 0, 0, 0, 0}});
             if (nd.c >= 1) {
                 // Items of about 1-4 K outputs (enough CTAs in flight to hide the gathers'
-                // latency). With T tables (qt >= 2) whose share of a rep fits 48 KiB and
-                // enough columns to amortise the copy: staged form (pad_ = 1), a few reps x
-                // 512 columns with the reps' T tables and child sketches in shared memory.
-                // Otherwise 128 columns x 8 reps, every lookup from L2.
+                // latency). Where a rep's T tables (qt >= 2) and child sketch fit 48 KiB and
+                // there are enough columns to amortise the copy: staged form (pad_ = 1), a
+                // few reps x 512 columns with the reps' T tables and child sketches in
+                // shared memory (the gathers from the child sketch are random: from L2 each
+                // would move a 32-byte sector for 4 bytes). Otherwise 128 columns x 8 reps,
+                // every lookup from L2.
                 const int64_t tw = nd.qt >= 2 ? 2 * (int64_t)(nd.qt - 1) * m : 0;
                 const int64_t per_rep = tw * 4 + m * (fp64 ? 8 : 4) + 16;
                 const int64_t budget = 48 * 1024;
-                if (nd.qt >= 2 && per_rep <= budget && nd.cols >= std::max<int64_t>(256, m / 4)) {
-                    const int G = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)R, budget / per_rep, 4}));
+                if (per_rep <= budget && nd.cols >= std::max<int64_t>(256, m / 4)) {
+                    const int G = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)R, budget / per_rep, nd.qt >= 2 ? 4 : 2}));
+                    const int64_t cb = nd.qt >= 2 ? 512 : 2048;
                     for (int r0 = 0; r0 < R; r0 += G)
-                        for (int64_t b0 = 0; b0 < nd.cols; b0 += 512) {
+                        for (int64_t b0 = 0; b0 < nd.cols; b0 += cb) {
                             const int g = std::min(G, R - r0);
-                            M2Item it{node_idx, r0, g, 1, b0, std::min(nd.cols, b0 + 512)};
+                            M2Item it{node_idx, r0, g, 1, b0, std::min(nd.cols, b0 + cb)};
                             pend.push_back({h, M2_VBUILD, it});
                             const size_t bytes =
                                 (((size_t)g * tw * 4 + 15) & ~(size_t)15) + (size_t)g * m * (fp64 ? 8 : 4);
