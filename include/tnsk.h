@@ -417,6 +417,14 @@ typedef struct tnsk_pairs tnsk_pairs;
 tnsk_status tnsk_pairs_create(tnsk_ctx* ctx, int32_t n, const tnsk_pair_job* jobs, tnsk_pairs** pairs);
 tnsk_status tnsk_pairs_run(tnsk_ctx* ctx, tnsk_pairs* pairs);
 tnsk_status tnsk_pairs_destroy(tnsk_pairs* pairs);
+/* Makes every later tnsk_plan_run of `plan` run `pairs` (as tnsk_pairs_run) on the ctx
+ * stream ahead of the plan's method-2 work, while the plan's method-1 work runs on the
+ * ctx's second stream: pair contractions that produce method-2 tensors (a merged
+ * chain) then overlap the method-1 sketches instead of preceding the whole run. The
+ * pairs' outputs must not be read by the plan's method-1 networks. NULL detaches. The
+ * handle must stay alive while the plan runs it; a captured run sequence is captured
+ * again on the next run. */
+tnsk_status tnsk_plan_set_prelude(tnsk_ctx* ctx, tnsk_plan* plan, tnsk_pairs* pairs);
 tnsk_status tnsk_contract_pairs(tnsk_ctx* ctx, int32_t n, const tnsk_pair_job* jobs);
 
 /* ---- Learned sketch-size predictor (the paper has no counterpart: it sizes m

@@ -285,7 +285,7 @@ struct NormRun {
 };
 
 static tnsk_status launch_plan(tnsk_ctx* ctx, const BatchPlan& plan, unsigned char* base, bool fp64,
-                               void* sketch_out, const NormRun& nr = NormRun{}) {
+                               void* sketch_out, const NormRun& nr = NormRun{}, tnsk_pairs* prelude = nullptr) {
     cudaStream_t s = ctx->stream;
     if (nr.n) {  // the rewritten tensors first: method 2 reads them
         ctx->prof.begin(TNSK_K_NORMALIZE, s);
@@ -332,6 +332,9 @@ static tnsk_status launch_plan(tnsk_ctx* ctx, const BatchPlan& plan, unsigned ch
         const cudaError_t e1 = cudaEventRecord(ctx->ev_join, ctx->side);
         if (st == TNSK_OK && e1 != cudaSuccess) st = cuda_fail(ctx, e1, "cudaEventRecord");
     }
+    // the plan's prelude (tnsk_plan_set_prelude): pair contractions that feed method 2,
+    // on the ctx stream, so they overlap method 1 on the second stream
+    if (st == TNSK_OK && prelude && !sketch_out) st = tnsk_pairs_run(ctx, prelude);
     if (st == TNSK_OK && plan.m2.n_nets && !sketch_out) {
         st = run_method2(plan, base, fp64, fp64 ? (const void* const*)ctx->d_tw64 : (const void* const*)ctx->d_tw32, s,
                          pf, ctx->d_err, ctx->last_error, ctx->inject);
@@ -464,6 +467,7 @@ static tnsk_status estimate_auto(tnsk_ctx* ctx, const tnsk_network* net, const t
 
 struct tnsk_plan {
     BatchPlan plan;
+    tnsk_pairs* prelude = nullptr;  // run ahead of method 2 in every run (tnsk_plan_set_prelude)
     bool fp64 = false;
     int device = 0;
     unsigned char* dev = nullptr;  // descriptors + scratch of this plan
@@ -708,7 +712,7 @@ tnsk_status tnsk_plan_run(tnsk_ctx* ctx, tnsk_plan* plan) {
             cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
             tnsk_status st = TNSK_ERR_CUDA;
             if (e == cudaSuccess) {
-                st = launch_plan(ctx, plan->plan, plan->dev, plan->fp64, nullptr, plan->nr);
+                st = launch_plan(ctx, plan->plan, plan->dev, plan->fp64, nullptr, plan->nr, plan->prelude);
                 e = cudaStreamEndCapture(s, &g);
             }
             if (e == cudaSuccess && st == TNSK_OK && g) e = cudaGraphInstantiate(&plan->graph, g, 0);
@@ -726,7 +730,22 @@ tnsk_status tnsk_plan_run(tnsk_ctx* ctx, tnsk_plan* plan) {
             return TNSK_OK;
         }
     }
-    return launch_plan(ctx, plan->plan, plan->dev, plan->fp64, nullptr, plan->nr);
+    return launch_plan(ctx, plan->plan, plan->dev, plan->fp64, nullptr, plan->nr, plan->prelude);
+}
+
+tnsk_status tnsk_plan_set_prelude(tnsk_ctx* ctx, tnsk_plan* plan, tnsk_pairs* pairs) {
+    if (!plan) return TNSK_ERR_INVALID;
+    tnsk_status st = check_ctx(ctx);
+    if (st != TNSK_OK) return st;
+    if (ctx->device != plan->device) return fail(ctx, TNSK_ERR_INVALID, "plan made on another device");
+    plan->prelude = pairs;
+    if (plan->graph) {  // the captured sequence changes: capture again on the next run
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+        cudaGraphExecDestroy(plan->graph);
+        plan->graph = nullptr;
+    }
+    return TNSK_OK;
 }
 
 tnsk_status tnsk_plan_destroy(tnsk_plan* plan) {

@@ -49,6 +49,7 @@ SYMBOLS = (
     "tnsk_autotune",
     "tnsk_plan_run",
     "tnsk_plan_destroy",
+    "tnsk_plan_set_prelude",
     "tnsk_profile",
     "tnsk_profile_read",
     "tnsk_debug_inject",
@@ -195,6 +196,8 @@ def load_library(path: str = LIB_PATH):
     L.tnsk_plan_run.argtypes = [vp, vp]
     L.tnsk_plan_destroy.restype = i32
     L.tnsk_plan_destroy.argtypes = [vp]
+    L.tnsk_plan_set_prelude.restype = i32
+    L.tnsk_plan_set_prelude.argtypes = [vp, vp, vp]
     L.tnsk_profile.restype = i32
     L.tnsk_profile.argtypes = [vp, i32]
     L.tnsk_profile_read.restype = i32
@@ -433,6 +436,12 @@ class Plan:
 
     def run(self):
         self.ctx._check(self.ctx.lib.tnsk_plan_run(self.ctx.h, self.h))
+
+    def set_prelude(self, pairs: "Pairs | None"):
+        """Run `pairs` ahead of the plan's method-2 work in every run(), beside its
+        method-1 work (tnsk_plan_set_prelude); None detaches."""
+        self.ctx._check(self.ctx.lib.tnsk_plan_set_prelude(self.ctx.h, self.h, pairs.h if pairs else None))
+        self._prelude = pairs  # kept alive while attached
 
     def close(self):
         if getattr(self, "h", None):

@@ -804,3 +804,63 @@ def test_contract_pairs_many_jobs(ctx):
     for (A, B, am, bm, perm, out), want in zip(jobs, wants):
         assert np.allclose(out.cpu().numpy(), want, rtol=1e-5, atol=1e-5 * 8 * np.abs(want).max())
     pr.close()
+
+
+def test_plan_prelude_feeds_method2_beside_method1():
+    """tnsk_plan_set_prelude: the rung merge attached to a plan runs ahead of method 2
+    (the merged tensor is method 2's input) while method 1 sketches another network on
+    the second stream; direct runs and graph replays match the oracle on the merged
+    values, and new core values reach the estimate through the prelude."""
+    stream = torch.cuda.Stream()
+    c = tnsk.Context(0, stream.cuda_stream)
+    rng = np.random.default_rng(47)
+    A = rng.standard_normal((4, 3, 5))
+    B = rng.standard_normal((6, 3, 7))
+    vecs = [rng.standard_normal(n) for n in (4, 6, 5, 7)]
+    m1_spec = W.random_network(rng, p_range=(4, 5), dim_range=(2, 5), open_dim_range=(2, 3))
+    with torch.cuda.stream(stream):
+        Ad = torch.as_tensor(A, dtype=torch.float32, device="cuda")
+        Bd = torch.as_tensor(B, dtype=torch.float32, device="cuda")
+        Md = torch.zeros((4, 6, 5, 7), dtype=torch.float32, device="cuda")
+        vd = [torch.as_tensor(v, dtype=torch.float32, device="cuda") for v in vecs]
+        # M[a, b, c, d] = sum_s A[a, s, c] B[b, s, d], contracted with one vector per mode
+        star = tnsk.Network([Md] + vd, [(0, 4), (1, 5), (2, 6), (3, 7)], [])
+        gen = gpu_network(m1_spec, torch.float32)
+        dims = [d for x in m1_spec.tensors for d in np.shape(x)]
+        O = int(np.prod([dims[g] for g in m1_spec.open])) if m1_spec.open else 1
+        outs = [torch.zeros(1, dtype=torch.float64, device="cuda"), torch.zeros(max(O, 1), dtype=torch.float64,
+                                                                               device="cuda")]
+        pers = [torch.zeros((6, 1), dtype=torch.float64, device="cuda"),
+                torch.zeros((6, max(O, 1)), dtype=torch.float64, device="cuda")]
+    stream.synchronize()
+    params = [tnsk.Params(m=64, reps=6, seed=31, method=tnsk.ACYCLIC),
+              tnsk.Params(m=128, reps=6, seed=32, method=tnsk.GENERAL)]
+    merge = c.pairs([(Ad, Bd, [1], [1], [0, 2, 1, 3], Md)])
+    plan = c.plan([star, gen], params, outs, pers)
+    plan.set_prelude(merge)
+    for run in range(4):
+        if run == 2:  # new core values: only the prelude carries them into M
+            A = -0.5 * A
+            with torch.cuda.stream(stream):
+                Ad.copy_(torch.as_tensor(A, dtype=torch.float32, device="cuda"))
+        plan.run()
+        c.sync()
+        M = Md.double().cpu().numpy()
+        want = np.einsum("asc,bsd->abcd", np.float32(A).astype(np.float64), np.float32(B).astype(np.float64))
+        assert np.allclose(M, want, rtol=1e-5, atol=1e-6 * np.abs(want).max()), f"run {run}: merged tensor"
+        star_spec = W.NetSpec([M] + [np.float32(v).astype(np.float64) for v in vecs],
+                              [(0, 4), (1, 5), (2, 6), (3, 7)], [], "star")
+        y, sc = oracle_estimate(star_spec, params[0], torch.float64)
+        assert_parity(pers[0].cpu().numpy(), y, sc, TOL[tnsk.PREC_FP32], f"prelude run {run}: method 2")
+        y, sc = oracle_estimate(m1_spec, params[1], torch.float32)
+        assert_parity(pers[1].cpu().numpy()[:, :O], y, sc, TOL[tnsk.PREC_FP32], f"prelude run {run}: method 1")
+    plan.set_prelude(None)  # detached: M keeps its last values
+    A2 = 3.0 * A
+    with torch.cuda.stream(stream):
+        Ad.copy_(torch.as_tensor(A2, dtype=torch.float32, device="cuda"))
+    plan.run()
+    c.sync()
+    assert np.allclose(Md.double().cpu().numpy(), M)
+    plan.close()
+    merge.close()
+    c.close()
