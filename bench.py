@@ -6,14 +6,15 @@ Workload (per GPU, per step): B = 64 pairs of tensor trains (8 sites, bond 32,
 physical 8, N(0, 1/sqrt(32)) entries, FP32). Every pair's inner product is
 estimated by both of the paper's methods at m = 1024 with 64 repetitions:
   * method 2 (Sec. 4.4, acyclic) on the chain obtained by summing each site's
-    physical leg and merging its two bonds (8 tensors: 1024, 6 x 1024x1024, 1024),
-    made on the GPU every step from the cores by exact pair contractions
-    (tnsk_pairs); with --grouped the six inner sites are grouped tensors
-    (tnsk_rung, the grouping of Sec. 4.1) whose entries the tensor-core sketch
-    product forms from the two cores, and only the end vectors are merged;
+    physical leg and merging its two bonds (8 tensors: 1024, 6 x 1024x1024, 1024):
+    the six inner sites are grouped tensors (tnsk_rung, the grouping of Sec. 4.1),
+    whose sketched product the tensor cores take in factored form from the two
+    cores, and the two end vectors are merged every step by exact pair
+    contractions (tnsk_pairs); with --materialise every merged site is stored by
+    tnsk_pairs each step and method 2 reads the 1024 x 1024 matrices;
   * method 1 (Sec. 4.2, any network) on the cyclic ladder (16 tensors, t = 22).
-The inputs are the cores (25 MB per GPU). One step = the rung merge (one
-tnsk_pairs_run) and one run of a planned batch (tnsk_plan_run) over the 2B networks: every
+The inputs are the cores (25 MB per GPU). One step = one run of a planned batch
+(tnsk_plan_run, the merge attached as its prelude) over the 2B networks: every
 hot-path row (tables, scatter, FFT/product, leaf/compose/V/GEMM/root, combine)
 runs on the GPU each step; only the host-side validation and descriptor upload
 are done once, when the batch is planned. `value` counts
@@ -48,7 +49,6 @@ METRIC = "estimates/s at <=5% rel. err (chosen vs plain form, same GB300); HBM r
 UNIT = "estimates/s"
 M, REPS = 1024, 64
 # FP32 SIMT peak of GB300: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz
-FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # instruction issue of GB300: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz
 ISSUE_PER_S = 152 * 4 * 32 * 2.070e9
 # shared memory: 152 SMs x 32 banks x 2070 MHz words per second when conflict-free; 32
@@ -77,9 +77,11 @@ def parse():
     ap.add_argument("--no-grid", action="store_true", help="skip the 4x4 grid precision leg")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16 method-2 leg")
     ap.add_argument("--no-triangle", action="store_true", help="skip the 64 x 64 triangle leg")
-    ap.add_argument("--grouped", action="store_true",
-                    help="inner sites as grouped tensors (tnsk_rung) instead of materialising them every step")
-    return ap.parse_args()
+    ap.add_argument("--materialise", action="store_true",
+                    help="store the merged inner sites every step (tnsk_pairs) instead of grouped tensors (tnsk_rung)")
+    args = ap.parse_args()
+    args.grouped = not args.materialise
+    return args
 
 
 def dist_setup(args):
@@ -396,19 +398,20 @@ def run_ours(args, world, rank, local):
                        "peak_source": "measured in this run: random-bin FP32 shared-memory atomic adds "
                                       "(tnsk_probe_shared_atomics)",
                        "what": "entries of W^T scattered per launch (64 reps x 1024 rows per pair)"},
-        # one launch per height (6 per step): one 1024 x 1024 FP32 matrix per pair, read once
         # one launch per height (6 per step). Dense chain: one 1024 x 1024 FP32 matrix per
-        # pair read once. Grouped tensors: no matrix is read; the converter warps form its
-        # 2^20 entries from the two cores, phys FMAs each (FP32 SIMT work)
+        # pair read once. Grouped tensors: no matrix is read; the two contractions of the
+        # factored product, 2 phys 32^3 multiply-adds each per rep and pair, on the tensor
+        # cores (three TF32 passes each)
         "m2_gemm": ({"bound": "hbm", "per_launch": B * 1024 * 1024 * 4, "unit": "GB/s", "peak": hbm_peak(),
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
                      "what": "bytes of X_k read per launch (each interior matrix once for all 64 reps)"}
                     if (not args.grouped) else
-                    {"bound": "alu", "per_launch": B * 1024 * 1024 * phys * 2, "unit": "TFLOP/s",
-                     "scale": 1e12, "peak": FP32_SIMT_PEAK_TFLOPS,
-                     "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (unit counts and clock)",
-                     "what": "FP32 FLOPs forming the grouped tensor's entries per launch (2 x phys per entry); the "
-                             "tensor-core product and V^T loads ride along"}),
+                    {"bound": "tensor", "per_launch": B * REPS * 2 * 2 * phys * bond ** 3, "unit": "TFLOP/s",
+                     "scale": 1e12, "peak": tf32_peak(),
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained x 1.1 / 2.25 (nominal dense TF32 / "
+                                    "BF16 ratio): TF32 peak of measured",
+                     "what": "FLOPs of one pass of the factored product per launch (2 contractions x 2 phys bond^3 "
+                             "multiply-adds x 64 reps per pair); the tensor cores run three TF32 passes of it"}),
         # one launch per step: the merged sites written once (all sites with --dense-chain,
         # else the two end vectors only)
         "pairs": {"bound": "hbm",
@@ -440,7 +443,8 @@ def run_ours(args, world, rank, local):
                           "probe_source": d["probe_source"]})
         else:
             r.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None})
-        r["traffic"] = read_traffic(kern)
+        # the committed counters of the method-2 product are those of the dense-chain kernel
+        r["traffic"] = read_traffic(kern) if (kern != "m2_gemm" or not args.grouped) else None
         rooflines.append(r)
     roof = rooflines[0] if rooflines else None
     if roof is not None:
@@ -501,8 +505,8 @@ def run_ours(args, world, rank, local):
     jsz = join_sizes(ctx, dev) if (rank == 0 and not args.no_joins) else None
     gridp = grid_precision(ctx, dev) if (rank == 0 and not args.no_grid) else None
     tri = triangle_leg(ctx, dev) if (rank == 0 and not args.no_triangle) else None
-    bf16c = (bf16_chains(ctx, dev, dense, cedges) if (rank == 0 and not args.no_bf16 and not args.grouped)
-             else None)
+    # the dense merged chains exist in both modes (merged once, untimed, for grouped tensors)
+    bf16c = bf16_chains(ctx, dev, dense, cedges) if (rank == 0 and not args.no_bf16) else None
     for p_ in plans + merges:
         p_.close()
     ctx.close()
@@ -516,8 +520,9 @@ def run_ours(args, world, rank, local):
                                "physical 8, N(0, 1/sqrt(32))); method 2 on the merged acyclic chain + method 1 on "
                                "the cyclic ladder, m=1024, 64 reps, FP32",
                    "chain": ("merged sites materialised every step (tnsk_pairs)" if (not args.grouped) else
-                             "inner sites as grouped tensors (tnsk_rung: entries formed inside the tensor-core "
-                             "sketch product), end sites merged every step (tnsk_pairs)"),
+                             "inner sites as grouped tensors (tnsk_rung: the sketched product in factored form on "
+                             "the tensor cores, no merged site stored), end sites merged every step (tnsk_pairs, "
+                             "the plan's prelude)"),
                    "networks_per_step": 2 * B, "estimate": "method-2 combined estimate of one pair",
                    "m": M, "reps": REPS, "inputs_bytes_per_gpu": in_bytes,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
@@ -562,6 +567,17 @@ def hbm_peak():
             return float(json.load(f)["hbm_gbs"])
     except Exception:
         return 6800.0
+
+
+def tf32_peak():
+    """Dense TF32 tensor peak: the measured sustained BF16 GEMM rate x the nominal TF32 / BF16
+    ratio (1.1 / 2.25 PFLOP/s dense); the recipe's fallback if the file is missing."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops_sustained"])
+    except Exception:
+        bf16 = 1700.0
+    return bf16 * 1.1 / 2.25
 
 
 def read_traffic(kernel):

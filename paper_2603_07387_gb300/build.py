@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtnsk.so")
-SOURCES = ["api.cu", "plan.cu", "tables.cu", "method1.cu", "method2.cu", "m2_gemm_tc.cu", "m1_spectrum_warp.cu", "m1_spectrum_large.cu", "probe.cu", "mlp.cu", "pairs.cu", "streams.cu", "normalize.cu", "m2_rung_fact.cu", "static_scratch.cu", "m1_scatter_fx.cu", "m1_rowsort.cu", "m1_spectrum_mid.cu", "m1_scatter_fiber.cu"]
+SOURCES = ["api.cu", "plan.cu", "tables.cu", "method1.cu", "method2.cu", "m2_gemm_tc.cu", "m1_spectrum_warp.cu", "m1_spectrum_large.cu", "probe.cu", "mlp.cu", "pairs.cu", "streams.cu", "normalize.cu", "m2_rung_fact.cu", "m2_rung_tc.cu", "static_scratch.cu", "m1_scatter_fx.cu", "m1_rowsort.cu", "m1_spectrum_mid.cu", "m1_scatter_fiber.cu"]
 NVCC_FLAGS = [
     "-std=c++17",
     "-O3",

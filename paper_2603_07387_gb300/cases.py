@@ -8,6 +8,11 @@ second.
         method 2 (Algorithm 4) on `count` merged tensor-train chains (vector, six
         1024 x 1024 matrices, vector), m = 1024, 64 reps: the sketched product
         (m2_gemm_tc_stream_kernel, or m2_gemm_bf16_kernel for BF16 storage).
+    python -m paper_2603_07387_gb300.cases rungs   [--count 64]
+        method 2 on `count` tensor-train pair chains (8 sites, bond 32, physical 8)
+        with the six inner sites as grouped tensors (tnsk.Rung), m = 1024, 64 reps:
+        the factored product on the tensor cores (m2_rung_tc_kernel after
+        m2_rung_prep_kernel); rate in TFLOP/s of one pass of the two contractions.
     python -m paper_2603_07387_gb300.cases trace4  [--n 4096] [--reps 1]
         method 1 (Algorithm 3) on tr(ABCD) of four n x n FP32 N(0,1) matrices,
         m = 4096: the row-sorted sketch (m1_rowsort_kernel) when reps <= 2, the
@@ -28,7 +33,7 @@ from . import tnsk
 from . import workloads as W
 
 
-def _run(ctx, nets, params, outs, key, nbytes):
+def _run(ctx, nets, params, outs, key, nbytes, flops=None):
     plan = ctx.plan(nets, params, outs)
     for _ in range(3):
         plan.run()
@@ -41,8 +46,12 @@ def _run(ctx, nets, params, outs, key, nbytes):
     plan.close()
     ms, launches = prof[key]
     per_run = ms / 3
-    print(f"{key}: {per_run:.4f} ms per run ({launches // 3} launches), "
-          f"{nbytes / (per_run / 1e3) / 1e9:.1f} GB/s of algorithmic bytes")
+    if flops is not None:
+        print(f"{key}: {per_run:.4f} ms per run ({launches // 3} launches), "
+              f"{flops / (per_run / 1e3) / 1e12:.2f} TFLOP/s")
+    else:
+        print(f"{key}: {per_run:.4f} ms per run ({launches // 3} launches), "
+              f"{nbytes / (per_run / 1e3) / 1e9:.1f} GB/s of algorithmic bytes")
 
 
 def chains(ctx, count: int, prec: str):
@@ -63,6 +72,24 @@ def chains(ctx, count: int, prec: str):
     params = [tnsk.Params(m=1024, reps=64, seed=7, method=tnsk.ACYCLIC, prec=p) for _ in nets]
     # X of every interior matrix is read once per launch (one height per launch)
     _run(ctx, nets, params, outs, "m2_gemm", 6 * count * 1024 * 1024 * dt.itemsize)
+
+
+def rungs(ctx, count: int):
+    import torch
+
+    nets, outs = [], []
+    for i in range(count):
+        A, B = W.tt_cores(seed=20260307 + i)
+        spec = W.tt_chain(A, B)
+        ts = [torch.as_tensor(spec.tensors[0], dtype=torch.float32, device="cuda")]
+        ts += [tnsk.Rung(torch.as_tensor(A[k], dtype=torch.float32, device="cuda"),
+                         torch.as_tensor(B[k], dtype=torch.float32, device="cuda")) for k in range(1, 7)]
+        ts.append(torch.as_tensor(spec.tensors[-1], dtype=torch.float32, device="cuda"))
+        nets.append(tnsk.Network(ts, spec.edges, []))
+        outs.append(torch.zeros(1, dtype=torch.float64, device="cuda"))
+    params = [tnsk.Params(m=1024, reps=64, seed=7, method=tnsk.ACYCLIC, root=0) for _ in nets]
+    # per grouped site and rep: two contractions of 2 s n^3 = 2 x 8 x 32^3 FLOPs each
+    _run(ctx, nets, params, outs, "m2_gemm", 0, flops=6 * count * 64 * 2 * 2 * 8 * 32 ** 3)
 
 
 def trace4(ctx, n: int, reps: int):
@@ -107,7 +134,7 @@ def main(argv=None):
     import torch
 
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("case", choices=("chains", "trace4", "ladders", "grid"))
+    ap.add_argument("case", choices=("chains", "rungs", "trace4", "ladders", "grid"))
     ap.add_argument("--log2m", type=int, default=14)
     ap.add_argument("--count", type=int, default=None)
     ap.add_argument("--prec", choices=("fp32", "bf16"), default="fp32")
@@ -117,6 +144,8 @@ def main(argv=None):
     ctx = tnsk.Context(0, torch.cuda.current_stream().cuda_stream)
     if a.case == "chains":
         chains(ctx, a.count or 16, a.prec)
+    elif a.case == "rungs":
+        rungs(ctx, a.count or 64)
     elif a.case == "trace4":
         trace4(ctx, a.n, a.reps or 1)
     elif a.case == "grid":

@@ -20,6 +20,7 @@
 // frees a stage. The streaming kernel further below serves the common case.
 #include "common.cuh"
 #include "method2.cuh"
+#include "tcgen05.cuh"
 
 namespace tnsk {
 namespace {
@@ -32,10 +33,6 @@ constexpr int kABytes = kTM * kKC * 4;                   // 16 KiB
 constexpr int kBBytes = kTN * kKC * 4;                   // 8 KiB
 constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;   // hi + lo of both
 constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
-constexpr uint32_t kWaitLimit = 1u << 22;                // bounded mbarrier waits: polls
-constexpr long long kWaitCycles = 1ll << 31;             // and SM clock cycles (~1 s at 2 GHz)
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Byte offset of (row, k) in a K-major no-swizzle operand tile (k < 32).
 __device__ __forceinline__ int kmajor_offset(int row, int k) {
@@ -52,27 +49,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 // Instruction descriptor: D = F32, A = B = TF32, both K-major, N = 64, M = 128.
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTN >> 3) << 17) |
                             ((uint32_t)(kTM >> 4) << 24);
-
-// Bounded wait for the phase of parity `parity` of an mbarrier. Each try_wait suspends
-// the thread until the phase completes or kSuspendNs pass (so waiting warps take no
-// issue slots from the working ones); after about kWaitCycles SM cycles in all, or
-// kWaitLimit polls, it gives up and returns false.
-constexpr uint32_t kSuspendNs = 100000;  // 0.1 ms per poll
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const long long t0 = clock64();
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity), "r"(kSuspendNs)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
-    }
-    return false;
-}
 
 __device__ __forceinline__ void store_split(unsigned char* hi, unsigned char* lo, int off, float4 v) {
     uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
@@ -308,47 +284,6 @@ constexpr int kRawV = kTN * 128;   // 64 rows x 128 B (one of hi / lo)
 constexpr int kStreamThreads = 224;
 constexpr int kStreamSmem = kXStages * kRawX + kVStages * 2 * kRawV + 1024;
 constexpr uint32_t kTmemCols = 256;
-
-// K-major, 128-byte swizzle: stride byte offset 1024 (8-row atoms), leading offset unused.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
-    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
-           (2ull << 61);
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(dst),
-        "l"(tmap), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-// The same load with an L2 cache policy (from createpolicy): the streamed X tiles are
-// marked evict-first and the V^T tiles, which every row tile of a matrix re-reads,
-// evict-last, so that streaming X does not push V^T out of L2.
-__device__ __forceinline__ void tma_load_2d_hint(uint32_t dst, const void* tmap, int x, int y, uint32_t bar,
-                                                 uint64_t policy) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], "
-        "[%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-        "l"(tmap), "r"(x), "r"(y), "r"(bar), "l"(policy)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_store32(uint32_t taddr, const uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
-        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
-        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
-        "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
-        "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
-        : "memory");
-}
 
 }  // namespace
 
@@ -601,14 +536,6 @@ __device__ __forceinline__ void rung_entries(const float* a, int a_s, const floa
     }
 }
 
-__device__ __forceinline__ void tmem_store16(uint32_t taddr, const uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-            taddr),
-        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
-        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
-        : "memory");
-}
 }  // namespace
 
 __global__ void __launch_bounds__(320, 2) m2_gemm_tc_rung_kernel(const M2Node* __restrict__ nodes,

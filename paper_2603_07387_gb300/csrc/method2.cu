@@ -554,7 +554,7 @@ static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void*
                             Profiler& prof, int* d_err, int inject) {
     static const int kKind[M2_NKINDS] = {TNSK_K_M2_LEAF, TNSK_K_M2_COMPOSE, TNSK_K_M2_VBUILD, TNSK_K_M2_GEMM,
                                          TNSK_K_M2_GEMM, TNSK_K_M2_GEMM,    TNSK_K_M2_GEMM,   TNSK_K_M2_GEMM,
-                                         TNSK_K_M2_SCATTER, TNSK_K_M2_ROOT};
+                                         TNSK_K_M2_GEMM, TNSK_K_M2_SCATTER, TNSK_K_M2_ROOT,   TNSK_K_M2_GEMM};
     const M2Node* nodes = (const M2Node*)(base + P.m2.nodes_off);
     const M2Net* nets = (const M2Net*)(base + P.m2.nets_off);
     const M2Item* items = (const M2Item*)(base + P.m2.items_off);
@@ -605,6 +605,19 @@ static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void*
                 case M2_GEMM_RUNGF:  // FP32 plans only
                     if (sizeof(T) == 4) {
                         const cudaError_t e = launch_m2_rung_fact(n, nodes, nets, its, (float*)ws, P.m2.rungf_smem, s);
+                        if (e != cudaSuccess) return e;
+                    }
+                    break;
+                case M2_GEMM_RUNGT:  // FP32 plans only
+                    if (sizeof(T) == 4) {
+                        const cudaError_t e = launch_m2_rung_tc(n, nodes, its, (float*)ws,
+                                                                base + P.m2.tmaps_off, d_err, inject, s);
+                        if (e != cudaSuccess) return e;
+                    }
+                    break;
+                case M2_RUNG_PREP:  // FP32 plans only
+                    if (sizeof(T) == 4) {
+                        const cudaError_t e = launch_m2_rung_prep(n, nodes, its, (float*)ws, s);
                         if (e != cudaSuccess) return e;
                     }
                     break;

@@ -68,7 +68,8 @@ struct M2Node {
     int32_t is_root;
     int32_t tm_x;     // streaming tensor-core path: tensor-map index of X and of V^T
     int32_t tm_v;
-    int32_t r_fact;   // grouped tensor on the factored product (M2_GEMM_RUNGF)
+    int32_t r_fact;   // grouped tensor in factored form: 1 SIMT (M2_GEMM_RUNGF), 2 tensor
+                      // cores (M2_GEMM_RUNGT, factors prepared at rc_off)
     int32_t vbf16;    // BF16 product (M2_GEMM_BF16): V^T stored as three BF16 parts
                       // [3][R][cols] at byte offset 4 v_off, X maps tm_x, parts tm_v .. + 2
     // grouped (rung) tensor, M2_GEMM_RUNG: X(row, col) = sum_s A[i1 ai + j1 aj + s as]
@@ -78,6 +79,8 @@ struct M2Node {
     int32_t rn_i1, rn_i2, rn_j1, rn_j2, rs;
     int32_t r_ai, r_aj, r_as, r_bi, r_bj, r_bs;
     int32_t r_astage;  // 1: the tile's A rows are staged in shared memory after B
+    int64_t rc_off;    // M2_GEMM_RUNGT: TF32 hi / lo parts of B and A, [Bh | Bl | Ah | Al] of
+                       // rs 1024 floats each (m2_rung_prep_kernel), -1 otherwise
 };
 
 struct M2Net {
@@ -111,9 +114,12 @@ enum M2Kind {
     M2_GEMM_RUNG = 5,
     M2_GEMM_RUNGF = 6,  // grouped tensor in factored form (dims <= 32): it.a first rep, it.b reps
     M2_GEMM_BF16 = 7,   // TNSK_PREC_BF16: BF16 tensors on the kind::f16 tensor-core kernel
-    M2_WSCATTER = 8,
-    M2_ROOT = 9,
-    M2_NKINDS = 10
+    M2_GEMM_RUNGT = 8,  // grouped tensor in factored form on the tensor cores (factor dims 32,
+                        // s <= 8): it.a first rep, it.b reps (<= 4); one persistent launch
+    M2_WSCATTER = 9,
+    M2_ROOT = 10,
+    M2_RUNG_PREP = 11,  // the prepared factors of every M2_GEMM_RUNGT node (height 0)
+    M2_NKINDS = 12
 };
 
 struct M2Plan {
@@ -157,5 +163,11 @@ cudaError_t launch_m2_gemm_tc_rung(int n, const M2Node* nodes, const M2Net* nets
 size_t m2_rung_fact_smem(int s);
 cudaError_t launch_m2_rung_fact(int n, const M2Node* nodes, const M2Net* nets, const M2Item* items, float* ws,
                                 size_t smem, cudaStream_t s);
+// Grouped tensors with all four factor dims 32 and s <= 8 (M2_GEMM_RUNGT): the factored
+// product on the tensor cores, one persistent CTA per SM over the n blocks; the factors'
+// TF32 parts first by launch_m2_rung_prep (one block per item of M2_RUNG_PREP).
+cudaError_t launch_m2_rung_prep(int n, const M2Node* nodes, const M2Item* items, float* ws, cudaStream_t s);
+cudaError_t launch_m2_rung_tc(int n, const M2Node* nodes, const M2Item* items, float* ws, const unsigned char* tmaps,
+                              int* err, int inject, cudaStream_t s);
 
 }  // namespace tnsk

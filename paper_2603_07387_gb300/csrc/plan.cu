@@ -97,7 +97,8 @@ tnsk_status finalize_plan(BatchPlan& P, unsigned char* base, std::string& err) {
     const float* ws = (const float*)(base + P.m2.ws_off);
     for (size_t i = 0; i < P.m2.tmap_jobs.size(); ++i) {
         const M2Node& nd = nodes[P.m2.tmap_jobs[i].first];
-        // 0: X, 1: V^T hi, 2: V^T lo (FP32); 3: X, 4 .. 6: the three parts of V^T (BF16)
+        // 0: X, 1: V^T hi, 2: V^T lo (FP32); 3: X, 4 .. 6: the three parts of V^T (BF16);
+        // 7, 8: V^T hi, lo of a grouped node viewed as [R cols / 32][32], boxes of 128 rows
         const int what = P.m2.tmap_jobs[i].second;
         const int64_t R = nets[nd.net].R;
         bool ok;
@@ -107,6 +108,8 @@ tnsk_status finalize_plan(BatchPlan& P, unsigned char* base, std::string& err) {
             ok = encode_rowmajor(maps + i * 128, ws + nd.v_off + (what - 1) * R * nd.cols, R, nd.cols, 64);
         else if (what == 3)
             ok = encode_rowmajor(maps + i * 128, nd.data, nd.npar, nd.cols, 128, true);
+        else if (what >= 7)
+            ok = encode_rowmajor(maps + i * 128, ws + nd.v_off + (what - 7) * R * nd.cols, R * nd.cols / 32, 32, 128);
         else
             ok = encode_rowmajor(maps + i * 128, (const unsigned char*)(ws + nd.v_off) + (what - 4) * R * nd.cols * 2,
                                  R, nd.cols, 64, true);
@@ -417,6 +420,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     std::vector<M1RowItem> ritems;
     int64_t rs_words = 0;           // their sorted-row scratch (uint32 words)
     int64_t ws_x = 0, ws_w = 0, ws_r = 0, ws_v = 0;  // method-2 workspace parts (elements)
+    int64_t ws_c = 0;  // prepared factors of grouped tensors on the factored tensor-core product
     const bool tma = tensor_maps_available();
     int max_log2m1 = 0, max_log2m2 = 0;
     std::vector<M1Work> m1w_cls[M1Plan::kScatterLists];
@@ -429,6 +433,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     struct M2Fix {
         size_t node;
         int64_t x, w, r, v, src;
+        int64_t c;     // prepared factors (M2_GEMM_RUNGT), -1 none
         int src_kind;  // 0 none, 1 r part, 2 x part
         int64_t child_x[TNSK_MAX_SLOTS];
     };
@@ -849,10 +854,14 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 nd.r_bj = (int32_t)(first ? 1 : g.s * g.d);
                 const int64_t b_bytes = (int64_t)nd.rn_i2 * (g.s * nd.rn_j2 + 4) * 4;
                 const bool tc_ok = nd.rn_j2 % 32 == 0 && b_bytes <= 60 * 1024 && tma;
-                nd.r_fact = !tc_ok && rung_small(g) ? 1 : 0;
-                if (nd.r_fact) {
+                // all four factor dims 32 and s <= 8: the factored product on the tensor
+                // cores (m2_rung_tc.cu), which neither forms X's entries nor reads them
+                const bool tc_fact = tma && nd.rn_i1 == 32 && nd.rn_i2 == 32 && nd.rn_j1 == 32 &&
+                                     nd.rn_j2 == 32 && g.s >= 1 && g.s <= 8;
+                nd.r_fact = tc_fact ? 2 : (!tc_ok && rung_small(g) ? 1 : 0);
+                if (nd.r_fact == 1) {
                     P.m2.rungf_smem = std::max(P.m2.rungf_smem, m2_rung_fact_smem((int)g.s));
-                } else if (!tc_ok) {
+                } else if (!tc_ok && !tc_fact) {
                     err = "tensor " + std::to_string(k) +
                           ": rung tensor needs factor dims <= 32, or its column fast index a multiple of 32 and the "
                           "B factor within 60 KiB";
@@ -878,11 +887,17 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
             nd.t_tab = t_tab[k];
             nd.tm_x = -1;
             nd.tm_v = -1;
+            nd.rc_off = -1;
             M2Fix fx{};
             fx.node = m2nodes.size();
             fx.x = xo[k];
             fx.r = -1;
             fx.v = -1;
+            fx.c = -1;
+            if (nd.r_fact == 2) {
+                fx.c = ws_c;
+                ws_c = up16(ws_c + 4 * (int64_t)nd.rs * 1024);
+            }
             fx.src_kind = 0;
             for (int j = 0; j < nd.c; ++j) fx.child_x[j] = xo[I.child[k][j]];
             if (nd.qt >= 2) {
@@ -963,9 +978,18 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 // the split of K (tensor-core kernels) is chosen once all tiles are known
                 const int64_t tile = fp64 ? 64 : 128;
                 const bool rung = I.rung[k] != nullptr;
-                if (rung && m2nodes.back().r_fact) {  // blocks of 4 reps, no tiles or K split
+                if (rung && m2nodes.back().r_fact == 1) {  // blocks of 4 reps, no tiles or K split
                     for (int r0 = 0; r0 < R; r0 += 4)
                         pend.push_back({h, M2_GEMM_RUNGF, M2Item{node_idx, r0, std::min(4, R - r0), 0, 0, 0}});
+                } else if (rung && m2nodes.back().r_fact == 2) {
+                    // blocks of 4 reps for the persistent kernel; V^T viewed as [R 32][32] in
+                    // boxes of 128 rows (hi, lo); the factors prepared once at height 0
+                    m2nodes.back().tm_v = (int32_t)P.m2.tmap_jobs.size();
+                    P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 7});
+                    P.m2.tmap_jobs.push_back({(int)(m2nodes.size() - 1), 8});
+                    pend.push_back({0, M2_RUNG_PREP, M2Item{node_idx, 0, 0, 0, 0, 0}});
+                    for (int r0 = 0; r0 < R; r0 += 4)
+                        pend.push_back({h, M2_GEMM_RUNGT, M2Item{node_idx, r0, std::min(4, R - r0), 0, 0, 0}});
                 } else {
                     const bool stream = !rung && !fp64 && tma && nd.dtype == TNSK_F32 && nd.A == 1 &&
                                         (nd.cols % 4) == 0 && ((uintptr_t)nd.data % 16) == 0 &&
@@ -1031,6 +1055,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
         nd.w_off = fx.w >= 0 ? ws_x + fx.w : -1;
         nd.r_off = fx.r >= 0 ? ws_x + ws_w + fx.r : -1;
         nd.v_off = fx.v >= 0 ? ws_x + ws_w + ws_r + fx.v : -1;
+        nd.rc_off = fx.c >= 0 ? ws_x + ws_w + ws_r + ws_v + fx.c : -1;
         nd.src_off = fx.src_kind == 1 ? ws_x + ws_w + fx.src : (fx.src_kind == 2 ? fx.src : -1);
         for (int j = 0; j < nd.c; ++j) nd.child_x[j] = fx.child_x[j];
     }
@@ -1177,7 +1202,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     P.yrep_n = yrep_n;
     P.m1.xs_off = P.arena.take((size_t)xs_n * acc);
     P.m1.xs_count = xs_n;
-    P.m2.ws_off = P.arena.take((size_t)(ws_x + ws_w + ws_r + ws_v) * acc);
+    P.m2.ws_off = P.arena.take((size_t)(ws_x + ws_w + ws_r + ws_v + ws_c) * acc);
     P.zero_bytes = P.m2.ws_off + (size_t)(ws_x + ws_w) * acc - P.zero_off;
     // ---- the rest
     P.tabs_off = P.arena.take((size_t)tab_words * sizeof(uint32_t));

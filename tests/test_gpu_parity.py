@@ -352,6 +352,33 @@ def test_method2_grouped_rung_tensors(ctx, root):
     pl.close()
 
 
+@pytest.mark.parametrize("root", [0, -2])
+def test_grouped_rung_factored_tensor_cores_batch(ctx, root):
+    """All factor dims 32 (the factored product on the tensor cores, one persistent CTA
+    per SM): three chains with s = 8, 3 and 1 in one plan, 254 reps (a last block of 2
+    reps), so that per height 192 blocks of 4 reps share 152 CTAs and CTAs cross from
+    one node (and one s) to the next; both orientations, against the oracle on the
+    dense merged chains, direct run and graph replays."""
+    sites, R = 4, 254
+    specs, nets = [], []
+    for i, phys in enumerate((8, 3, 1)):
+        spec, net = _rung_chain(sites, 32, phys, seed=300 + i)
+        specs.append(spec)
+        nets.append(net)
+    r = 0 if root == 0 else sites - 1
+    params = [tnsk.Params(m=256, reps=R, seed=40 + i, method=tnsk.ACYCLIC, root=r) for i in range(3)]
+    outs = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in nets]
+    pers = [torch.zeros((R, 1), dtype=torch.float64, device="cuda") for _ in nets]
+    pl = ctx.plan(nets, params, outs, pers)
+    want = [oracle_estimate(s, p, torch.float32) for s, p in zip(specs, params)]
+    for run in range(3):
+        pl.run()
+        ctx.sync()
+        for (y, sc), pr, s in zip(want, pers, specs):
+            assert_parity(pr.cpu().numpy(), y, sc, TOL[tnsk.PREC_FP32], f"run {run} {s.name} root={r}")
+    pl.close()
+
+
 @pytest.mark.parametrize("root", [0, 2])
 def test_grouped_rung_factored_small_dims(ctx, root):
     """Grouped tensor with factor dims below 32 and unequal (a, s, c) = (5, 3, 7),
