@@ -127,6 +127,9 @@ tnsk_status ctx_fail(tnsk_ctx* ctx, tnsk_status st, const std::string& msg) { re
 tnsk_status ctx_cuda_fail(tnsk_ctx* ctx, cudaError_t e, const char* where) { return cuda_fail(ctx, e, where); }
 tnsk_status ctx_check(tnsk_ctx* ctx) { return check_ctx(ctx); }
 tnsk_status ctx_ensure_scratch(tnsk_ctx* ctx, size_t bytes) { return ensure_scratch(ctx, bytes); }
+tnsk_status ctx_ensure_work(tnsk_ctx* ctx, size_t bytes) {
+    return ensure_buffer(ctx, ctx->work, ctx->work_bytes, bytes, "work buffer");
+}
 }  // namespace tnsk
 
 // ---------------------------------------------------------------------------
@@ -190,6 +193,7 @@ tnsk_status tnsk_destroy(tnsk_ctx* ctx) {
     if (ctx->d_tw64) cudaFree(ctx->d_tw64);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->aux) cudaFree(ctx->aux);
+    if (ctx->work) cudaFree(ctx->work);
     if (ctx->side) {
         cudaStreamSynchronize(ctx->side);
         cudaStreamDestroy(ctx->side);
@@ -384,6 +388,7 @@ static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets,
     if (!plan.host_desc.empty())
         TNSK_CUDA(cudaMemcpyAsync(ctx->scratch + plan.desc_off, plan.host_desc.data(), plan.host_desc.size(),
                                   cudaMemcpyHostToDevice, ctx->stream));
+    recycle_host_desc(plan.host_desc);  // a pageable source is consumed when the call returns
     NormRun nr;
     if (!nb.jobs.empty()) {
         TNSK_CUDA(cudaMemcpyAsync(ctx->norm + nb.desc_off, nb.jobs.data(), nb.jobs.size() * sizeof(NormJob),
@@ -575,8 +580,7 @@ static tnsk_status create_plan(tnsk_ctx* ctx, int32_t B, const tnsk_network* net
         drop();
         return cuda_fail(ctx, e, "cudaMemcpy(plan descriptors)");
     }
-    p->plan.host_desc.clear();
-    p->plan.host_desc.shrink_to_fit();
+    recycle_host_desc(p->plan.host_desc);
     *out = p;
     return TNSK_OK;
 }

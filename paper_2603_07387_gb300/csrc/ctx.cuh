@@ -36,6 +36,10 @@ struct tnsk_ctx {
     // per-rep buffer of TNSK_PREC_AUTO calls made without one (grown on demand)
     double* aux = nullptr;
     size_t aux_bytes = 0;
+    // the predictor's small device buffers (features, inputs and outputs, pilot
+    // estimates), grown on demand and reused, so a parameter choice allocates nothing
+    unsigned char* work = nullptr;
+    size_t work_bytes = 0;
 };
 
 namespace tnsk {
@@ -46,4 +50,6 @@ tnsk_status ctx_cuda_fail(tnsk_ctx* ctx, cudaError_t e, const char* where);
 tnsk_status ctx_check(tnsk_ctx* ctx);
 // the ctx scratch arena holds at least `bytes` (stream-ordered reuse)
 tnsk_status ctx_ensure_scratch(tnsk_ctx* ctx, size_t bytes);
+// the ctx work buffer (ctx->work) holds at least `bytes` (stream-ordered reuse)
+tnsk_status ctx_ensure_work(tnsk_ctx* ctx, size_t bytes);
 }  // namespace tnsk

@@ -643,11 +643,9 @@ tnsk_status batch_sumsq(tnsk_ctx* ctx, std::vector<SqJob>& jobs, std::vector<dou
         nchunks += (j.n + kSqChunk - 1) / kSqChunk;
     }
     const size_t jb = (jobs.size() * sizeof(SqJob) + 15) / 16 * 16;
-    unsigned char* d = nullptr;
-    if (cudaMalloc((void**)&d, jb + jobs.size() * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        return ctx_fail(ctx, TNSK_ERR_OOM, "features: buffer");
-    }
+    tnsk_status st = ctx_ensure_work(ctx, jb + jobs.size() * sizeof(double));
+    if (st != TNSK_OK) return st;
+    unsigned char* d = ctx->work;
     double* dout = (double*)(d + jb);
     cudaMemcpyAsync(d, jobs.data(), jobs.size() * sizeof(SqJob), cudaMemcpyHostToDevice, ctx->stream);
     cudaMemsetAsync(dout, 0, jobs.size() * sizeof(double), ctx->stream);
@@ -657,7 +655,6 @@ tnsk_status batch_sumsq(tnsk_ctx* ctx, std::vector<SqJob>& jobs, std::vector<dou
     }
     cudaMemcpyAsync(ss.data(), dout, jobs.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     const cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    cudaFree(d);
     if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "features");
     return TNSK_OK;
 }
@@ -732,11 +729,9 @@ tnsk_status tnsk_choose_params(tnsk_ctx* ctx, const tnsk_network* net, double ta
         std::memcpy(&hx[(size_t)c * kFeatures], base, sizeof(base));
         hx[(size_t)c * kFeatures + 7] = (float)(kLo + c);
     }
-    float* d = nullptr;
-    if (cudaMalloc((void**)&d, (hx.size() + hy.size()) * sizeof(float)) != cudaSuccess) {
-        cudaGetLastError();
-        return ctx_fail(ctx, TNSK_ERR_OOM, "choose_params: buffer");
-    }
+    st = ctx_ensure_work(ctx, (hx.size() + hy.size()) * sizeof(float));
+    if (st != TNSK_OK) return st;
+    float* d = (float*)ctx->work;
     cudaMemcpyAsync(d, hx.data(), hx.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
     st = tnsk_mlp_predict(ctx, mlp, d, nc, d + hx.size(), 1);
     if (st == TNSK_OK) {
@@ -744,7 +739,6 @@ tnsk_status tnsk_choose_params(tnsk_ctx* ctx, const tnsk_network* net, double ta
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) st = ctx_cuda_fail(ctx, e, "choose_params");
     }
-    cudaFree(d);
     if (st != TNSK_OK) return st;
     // The predictor gives the expected log10 of one estimate's relative error. With
     // the estimate's error ~ sigma Z (a mean of reps; Z standard normal),
@@ -841,11 +835,9 @@ tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_networ
     }
     if (!rows_of.empty()) {
         const size_t n = hx.size() / kFeatures;
-        float* d = nullptr;
-        if (cudaMalloc((void**)&d, (hx.size() + n) * sizeof(float)) != cudaSuccess) {
-            cudaGetLastError();
-            return ctx_fail(ctx, TNSK_ERR_OOM, "choose_params_batch: buffer");
-        }
+        st = ctx_ensure_work(ctx, (hx.size() + n) * sizeof(float));
+        if (st != TNSK_OK) return st;
+        float* d = (float*)ctx->work;
         std::vector<float> hy(n);
         cudaMemcpyAsync(d, hx.data(), hx.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
         st = tnsk_mlp_predict(ctx, mlp, d, (int64_t)n, d + hx.size(), 1);
@@ -854,7 +846,6 @@ tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_networ
             const cudaError_t e = cudaStreamSynchronize(ctx->stream);
             if (e != cudaSuccess) st = ctx_cuda_fail(ctx, e, "choose_params_batch");
         }
-        cudaFree(d);
         if (st != TNSK_OK) return st;
         for (size_t i = 0; i < rows_of.size(); ++i) {
             const int b = rows_of[i];
@@ -888,12 +879,10 @@ tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_networ
         if (!done[b] && pilot_reps > 0) pil.push_back(b);
     if (!pil.empty()) {
         const int P = (int)pil.size();
-        double* d = nullptr;
         const size_t nd = (size_t)P * (pilot_reps + 1);
-        if (cudaMalloc((void**)&d, nd * sizeof(double)) != cudaSuccess) {
-            cudaGetLastError();
-            return ctx_fail(ctx, TNSK_ERR_OOM, "choose_params_batch: pilot buffer");
-        }
+        st = ctx_ensure_work(ctx, nd * sizeof(double));
+        if (st != TNSK_OK) return st;
+        double* d = (double*)ctx->work;
         std::vector<tnsk_network> pn(P);
         std::vector<tnsk_params> pp(P);
         std::vector<double*> po(P), pr(P);
@@ -914,7 +903,6 @@ tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_networ
             const cudaError_t e = cudaStreamSynchronize(ctx->stream);
             if (e != cudaSuccess) st = ctx_cuda_fail(ctx, e, "choose_params_batch: pilot");
         }
-        cudaFree(d);
         if (st != TNSK_OK) return st;
         for (int i = 0; i < P; ++i) {
             const int b = pil[i];

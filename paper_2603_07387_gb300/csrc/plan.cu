@@ -396,11 +396,8 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
     return TNSK_OK;
 }
 
-tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* nets, const tnsk_params* params,
-                       double* const* outs, double* const* per_reps, bool fp64, bool sketch_only, BatchPlan& P,
-                       std::string& err, const tnsk_schedule* sched) {
-    const int B = (int)infos.size();
-    const size_t acc = fp64 ? sizeof(double) : sizeof(float);
+namespace {
+struct PlanLists {
     std::vector<TabReq> reqs;
     std::vector<M1Tensor> m1t;
     std::vector<M1Net> m1n;
@@ -411,19 +408,88 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     std::vector<CombineItem> comb;
     std::vector<M2Node> m2nodes;
     std::vector<M2Net> m2n;
-    int64_t tab_words = 0, yrep_n = 0, xs_n = 0, spec_n = 0, sexp_n = 0, lspec_n = 0;
-    std::vector<int4> lfft, lprod;  // large-m method 1: (net, rep, sketch), (net, rep, first bin, bins)
-    std::vector<int4> mfft, mprod;  // mid-m closed networks: the same item forms
-    int mid_max_log2m = 0;
-    std::vector<M1Diag> diags;      // diagonal copy tensors (WLOG 1)
-    std::vector<M1RowSort> rsorts;  // row-sorted sketches of large tensors
+    std::vector<int4> lfft, lprod, mfft, mprod;
+    std::vector<M1Diag> diags;
+    std::vector<M1RowSort> rsorts;
     std::vector<M1RowItem> ritems;
+    std::vector<M1Work> m1w_cls[M1Plan::kScatterLists];
+    std::vector<M2Item> m2items;
+};
+
+// This thread's lists, emptied (capacity kept).
+PlanLists& plan_lists() {
+    static thread_local PlanLists L;
+    L.reqs.clear();
+    L.m1items.clear();
+    L.m1t.clear();
+    L.m1n.clear();
+    L.m1w.clear();
+    L.opens.clear();
+    for (auto& v : L.m1warp) v.clear();
+    L.comb.clear();
+    L.m2nodes.clear();
+    L.m2n.clear();
+    for (auto* v : {&L.lfft, &L.lprod, &L.mfft, &L.mprod}) v->clear();
+    L.diags.clear();
+    L.rsorts.clear();
+    L.ritems.clear();
+    for (auto& v : L.m1w_cls) v.clear();
+    L.m2items.clear();
+    return L;
+}
+
+// A staged descriptor block that has been uploaded, kept for the thread's next plan.
+thread_local std::vector<unsigned char> g_desc_pool;
+
+void take_desc_buffer(std::vector<unsigned char>& H) {
+    if (H.capacity() < g_desc_pool.capacity()) H.swap(g_desc_pool);
+    H.clear();
+}
+}  // namespace
+
+void recycle_host_desc(std::vector<unsigned char>& H) {
+    if (H.capacity() > g_desc_pool.capacity()) {
+        H.clear();
+        g_desc_pool.swap(H);
+    }
+}
+
+tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* nets, const tnsk_params* params,
+                       double* const* outs, double* const* per_reps, bool fp64, bool sketch_only, BatchPlan& P,
+                       std::string& err, const tnsk_schedule* sched) {
+    const int B = (int)infos.size();
+    const size_t acc = fp64 ? sizeof(double) : sizeof(float);
+    // The descriptor lists live in per-thread vectors that keep their capacity from one
+    // plan to the next: a batch of large-m networks stages megabytes of items, and fresh
+    // vectors grown by doubling spent most of the planning time in page faults.
+    PlanLists& L = plan_lists();
+    std::vector<TabReq>& reqs = L.reqs;
+    std::vector<M1Tensor>& m1t = L.m1t;
+    std::vector<M1Net>& m1n = L.m1n;
+    std::vector<M1Work>& m1w = L.m1w;
+    std::vector<OpenMode>& opens = L.opens;
+    std::vector<int2>& m1items = L.m1items;
+    std::vector<int2>* m1warp = L.m1warp;
+    std::vector<CombineItem>& comb = L.comb;
+    std::vector<M2Node>& m2nodes = L.m2nodes;
+    std::vector<M2Net>& m2n = L.m2n;
+    int64_t tab_words = 0, yrep_n = 0, xs_n = 0, spec_n = 0, sexp_n = 0, lspec_n = 0;
+    // large-m method 1: (net, rep, sketch), (net, rep, first bin, bins)
+    std::vector<int4>& lfft = L.lfft;
+    std::vector<int4>& lprod = L.lprod;
+    // mid-m closed networks: the same item forms
+    std::vector<int4>& mfft = L.mfft;
+    std::vector<int4>& mprod = L.mprod;
+    int mid_max_log2m = 0;
+    std::vector<M1Diag>& diags = L.diags;      // diagonal copy tensors (WLOG 1)
+    std::vector<M1RowSort>& rsorts = L.rsorts;  // row-sorted sketches of large tensors
+    std::vector<M1RowItem>& ritems = L.ritems;
     int64_t rs_words = 0;           // their sorted-row scratch (uint32 words)
     int64_t ws_x = 0, ws_w = 0, ws_r = 0, ws_v = 0;  // method-2 workspace parts (elements)
     int64_t ws_c = 0;  // prepared factors of grouped tensors on the factored tensor-core product
     const bool tma = tensor_maps_available();
     int max_log2m1 = 0, max_log2m2 = 0;
-    std::vector<M1Work> m1w_cls[M1Plan::kScatterLists];
+    std::vector<M1Work>* m1w_cls = L.m1w_cls;
     struct PendingItem {
         int h, kind;
         M2Item it;
@@ -1094,7 +1160,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
         pend.swap(out);
     }
     // ---- method-2 item order: by height, then kind
-    std::vector<M2Item> m2items;
+    std::vector<M2Item>& m2items = L.m2items;
     if (!m2n.empty()) {
         const int H = P.m2.max_height + 1;
         P.m2.first.assign(H * M2_NKINDS, 0);
@@ -1154,6 +1220,31 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
     }
     // the per-rep magnitude sums of method-1 networks follow all per-rep estimates
     for (M1Net& nb : m1n) nb.yabs_off = nb.y_off + yrep_n;
+    {
+        // one allocation for the staged block (a recycled one where the thread has it)
+        size_t total = 0;
+        auto add = [&](size_t bytes) { total = ((total + 255) & ~(size_t)255) + bytes; };
+        add(reqs.size() * sizeof(TabReq));
+        add(m1t.size() * sizeof(M1Tensor));
+        add(m1n.size() * sizeof(M1Net));
+        add(m1w.size() * sizeof(M1Work));
+        size_t n_items = m1items.size();
+        for (int sl = 0; sl < M1Plan::kWarpSlots; ++sl) n_items += m1warp[sl].size();
+        add(opens.size() * sizeof(OpenMode));
+        add(n_items * sizeof(int2));
+        add(comb.size() * sizeof(CombineItem));
+        for (size_t n : {lfft.size(), lprod.size()}) add(n * sizeof(int4));
+        add(diags.size() * sizeof(M1Diag));
+        for (size_t n : {mfft.size(), mprod.size()}) add(n * sizeof(int4));
+        add(rsorts.size() * sizeof(M1RowSort));
+        add(ritems.size() * sizeof(M1RowItem));
+        add(m2nodes.size() * sizeof(M2Node));
+        add(m2n.size() * sizeof(M2Net));
+        add(m2items.size() * sizeof(M2Item));
+        add(P.m2.tmap_jobs.size() * 128);
+        take_desc_buffer(H);
+        H.reserve(total);
+    }
     size_t o_reqs = stage(H, reqs), o_m1t = stage(H, m1t), o_m1n = stage(H, m1n), o_m1w = stage(H, m1w);
     const int n_block_items = (int)m1items.size();
     for (int sl = 0; sl < M1Plan::kWarpSlots; ++sl) {

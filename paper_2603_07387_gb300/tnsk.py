@@ -263,6 +263,11 @@ class Network:
     edges: Sequence[tuple[int, int]]
     open: Sequence[int] = ()
 
+    def __getstate__(self):  # the cached marshalled form (ctypes) stays behind
+        d = dict(self.__dict__)
+        d.pop("_holder", None)
+        return d
+
 
 @dataclass
 class Params:
@@ -381,6 +386,33 @@ class _NetHolder:
         self.keep = list(net.tensors)
 
 
+def _storage_key(x):
+    if isinstance(x, Rung):
+        return (x.A.data_ptr(), x.B.data_ptr())
+    if isinstance(x, Zeros):
+        return None
+    return x.data_ptr()
+
+
+def _holder(net: Network) -> _NetHolder:
+    """The network's marshalled form (_NetHolder), built on first use and kept on the
+    Network while it holds the same tensor objects over the same storage, the same
+    edges and the same open modes; a batch of many networks then costs one check per
+    network instead of a rebuild."""
+    h = net.__dict__.get("_holder")
+    ts = net.tensors
+    if (h is not None and len(h.keep) == len(ts) and all(a is b for a, b in zip(h.keep, ts))
+            and h.storage == [_storage_key(x) for x in ts] and h.edge_list == list(net.edges)
+            and h.open_ == list(net.open)):
+        return h
+    h = _NetHolder(net)
+    h.storage = [_storage_key(x) for x in ts]
+    h.edge_list = list(net.edges)
+    h.open_ = list(net.open)
+    net.__dict__["_holder"] = h
+    return h
+
+
 def _params(p: Params) -> _Params:
     return _Params(int(p.m), int(p.reps), int(p.groups), int(p.seed) & ((1 << 64) - 1), int(p.method),
                    int(p.root), int(p.prec), int(p.rep0))
@@ -390,7 +422,7 @@ def estimate_static(net: Network, params: Params, out, per_rep=None, stream=None
     """tnsk_estimate_static: method-1 estimate with no device allocation (all scratch
     in the library's fixed 16 MiB device array). Needs no Context."""
     L = load_library()
-    nh = _NetHolder(net)
+    nh = _holder(net)
     pr = _params(params)
     st = L.tnsk_estimate_static(ctypes.byref(nh.c), ctypes.byref(pr), out.data_ptr(),
                                 per_rep.data_ptr() if per_rep is not None else None,
@@ -404,7 +436,7 @@ def rewrite(net: Network, params: Params):
     computed on the host (no device work; tensors may be CPU tensors): (shapes, edges,
     copy) with copy[k] True for a WLOG 1 copy tensor."""
     L = load_library()
-    nh = _NetHolder(net)
+    nh = _holder(net)
     pr = _params(params)
     q = sum(len(x.shape) for x in net.tensors)
     cap_t, cap_e = len(net.tensors) + max(1, len(net.edges)), max(1, 2 * len(net.edges))
@@ -689,19 +721,19 @@ class Context:
         """tnsk_m1_sketch: method-1 sketches of every tensor into x (device, [reps][sum_k
         O_k m]); for a network with hyperedges the WLOG 1 copy tensors' sketches follow
         the caller's tensors (``rewrite`` gives the planned network)."""
-        nh = _NetHolder(net)
+        nh = _holder(net)
         pr = _params(params)
         self._check(self.lib.tnsk_m1_sketch(self.h, ctypes.byref(nh.c), ctypes.byref(pr), x.data_ptr()))
 
     def estimate(self, net: Network, params: Params, out, per_rep=None):
-        nh = _NetHolder(net)
+        nh = _holder(net)
         pr = _params(params)
         self._check(self.lib.tnsk_estimate(self.h, ctypes.byref(nh.c), ctypes.byref(pr), out.data_ptr(),
                                            per_rep.data_ptr() if per_rep is not None else None))
 
     def estimate_batch(self, nets: Sequence[Network], params: Sequence[Params], outs, per_reps=None):
         B = len(nets)
-        holders = [_NetHolder(n) for n in nets]
+        holders = [_holder(n) for n in nets]
         carr = (_Network * max(1, B))(*[h.c for h in holders])
         parr = (_Params * max(1, B))(*[_params(p) for p in params])
         oarr = (ctypes.c_void_p * max(1, B))(*[o.data_ptr() for o in outs])
@@ -723,7 +755,7 @@ class Context:
     def stream(self, net: Network, params: Params, out, per_rep=None) -> "Stream":
         """tnsk_stream_create: sketch the network's tensors now (method 1), write the
         estimate to out (and per_rep), keep the sketches for turnstile updates."""
-        nh = _NetHolder(net)
+        nh = _holder(net)
         pr = _params(params)
         h = ctypes.c_void_p()
         self._check(self.lib.tnsk_stream_create(self.h, ctypes.byref(nh.c), ctypes.byref(pr), out.data_ptr(),
@@ -734,7 +766,7 @@ class Context:
     def autotune(self, nets: Sequence[Network], params: Sequence[Params], trials: int = 3):
         """tnsk_autotune: (Schedule, default scatter ms, tuned scatter ms) for the batch."""
         B = len(nets)
-        holders = [_NetHolder(n) for n in nets]
+        holders = [_holder(n) for n in nets]
         carr = (_Network * max(1, B))(*[h.c for h in holders])
         parr = (_Params * max(1, B))(*[_params(p) for p in params])
         sched = Schedule()
@@ -748,7 +780,7 @@ class Context:
         """tnsk_plan_create (tnsk_plan_create_scheduled with a schedule): plan a batch
         once; run it with Plan.run()."""
         B = len(nets)
-        holders = [_NetHolder(n) for n in nets]
+        holders = [_holder(n) for n in nets]
         carr = (_Network * max(1, B))(*[h.c for h in holders])
         parr = (_Params * max(1, B))(*[_params(p) for p in params])
         oarr = (ctypes.c_void_p * max(1, B))(*[o.data_ptr() for o in outs])
@@ -790,7 +822,7 @@ class Context:
         """tnsk_features: the predictor's inputs for a network at params.m, params.reps."""
         import numpy as np
 
-        nh = _NetHolder(net)
+        nh = _holder(net)
         pr = _params(params)
         f = (ctypes.c_float * MLP_FEATURES)()
         self._check(self.lib.tnsk_features(self.h, ctypes.byref(nh.c), ctypes.byref(pr), f))
@@ -802,7 +834,7 @@ class Context:
         (TNSK_ERR_UNREACHABLE); other errors raise."""
         import dataclasses
 
-        nh = _NetHolder(net)
+        nh = _holder(net)
         pr = _params(params)
         err = ctypes.c_double(0.0)
         st = self.lib.tnsk_choose_params(self.h, ctypes.byref(nh.c), float(target_err),
@@ -819,7 +851,7 @@ class Context:
         import dataclasses
 
         B = len(nets)
-        holders = [_NetHolder(n) for n in nets]
+        holders = [_holder(n) for n in nets]
         carr = (_Network * max(1, B))(*[h.c for h in holders])
         parr = (_Params * max(1, B))(*[_params(p) for p in params])
         err = (ctypes.c_double * max(1, B))()

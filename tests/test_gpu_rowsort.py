@@ -3,7 +3,7 @@ contracted leading mode of 1024 .. 2^17 indices, m <= 2^14): rows visited in the
 order of their leading-mode bins, one register sum per column and bin. Against the
 oracle per bin (tnsk_m1_sketch) and per repetition (tnsk_estimate), including a
 leading mode and rows that are not multiples of the CTA's sizes, an order-3 tensor,
-and complemented leading modes."""
+and complemented leading modes, from m = 256 up to the form's largest m, 2^14."""
 import numpy as np
 import pytest
 
@@ -42,7 +42,7 @@ def _specs():
     return [trab, order3]
 
 
-@pytest.mark.parametrize("m", [256, 4096])
+@pytest.mark.parametrize("m", [256, 4096, 16384])
 def test_rowsort_sketch_per_bin(ctx, m):
     R, seed = 2, 0x7E57
     for spec in _specs():
