@@ -293,17 +293,21 @@ def run_ours(args, world, rank, local):
     clocks = ClockSampler(gpu_uuid(local))
     clocks.start()
     time.sleep(0.3)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    # The step's inputs (25 MB of cores) fit in L2, so L2 is flushed between timed steps:
+    # a 256 MiB buffer written after each step, outside that step's event pair
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    flush_buf.zero_()
     host_s = 0.0
-    for _ in range(args.steps):
+    for a, b in ev:
         h0 = time.perf_counter()
+        a.record(stream)
         step()
+        b.record(stream)
         host_s += time.perf_counter() - h0
-    e1.record(stream)
+        flush_buf.zero_()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     clk = clocks.stop()
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -319,10 +323,18 @@ def run_ours(args, world, rank, local):
     p0.record(stream)
     for _ in range(args.steps):
         step()
+        flush_buf.zero_()
     p1.record(stream)
     prof = ctx.profile_read()
     ctx.profile(False)
-    ms_profiled = p0.elapsed_time(p1) / args.steps
+    # (less the flushes between the steps, timed alone)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        flush_buf.zero_()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_profiled = (p0.elapsed_time(p1) - f0.elapsed_time(f1)) / args.steps
 
     # ---------------- accuracy against the exact contraction (input-relative, Def. "ATNC")
     # the dense merged chains (every site by tnsk_pairs, outside the timed region) give
@@ -525,7 +537,8 @@ def run_ours(args, world, rank, local):
                              "the plan's prelude)"),
                    "networks_per_step": 2 * B, "estimate": "method-2 combined estimate of one pair",
                    "m": M, "reps": REPS, "inputs_bytes_per_gpu": in_bytes,
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+                   "l2": "L2 flushed between timed steps (256 MiB written after each step, outside its CUDA-event "
+                         "pair; the 25 MB of inputs fit in L2)", "parallelism": f"replicas x{world}"},
         "accuracy": {"method2_eps_rms": float(f"{rms(eps2):.3e}"), "method1_eps_rms": float(f"{rms(eps1):.3e}"),
                      "method2_eps_bound": float(f"{bound2:.3e}"), "method1_eps_bound": float(f"{bound1:.3e}"),
                      "method2_rel_err_rms": float(f"{rms(rel2):.3e}"), "method1_rel_err_rms": float(f"{rms(rel1):.3e}"),
@@ -1029,6 +1042,10 @@ def learned_vs_plain(ctx, dev, steps: int = 5, n_train: int = 800):
                 tnsk_estimate_batch call. Its time per step is the choice plus that call,
                 host time included; `estimates_per_s_plan_only` is the device time of
                 the same batch replayed from a plan (CUDA graph).
+      chosen_rate = tnsk_choose_params_rate: the same predictor and pilot, the (m, R)
+                that maximise the batch's expected within-5% estimates per unit of
+                work (a network whose chosen chance is below 1/2 is flagged), then the
+                batch in one call, timed like the chosen arm.
     Throughput counts every estimate produced; `within_5pct` is the fraction of them
     within 5% of the exact value; `miss_rate` = 1 - within_5pct. `by_flag` splits both
     arms' within-5% fractions by the chosen arm's verdict (sized or flagged).
@@ -1135,9 +1152,37 @@ def learned_vs_plain(ctx, dev, steps: int = 5, n_train: int = 800):
         good_plain = n * plain["within_5pct"] / plain_s
         good_chosen = n * chosen["within_5pct"] / chosen_s
         ratio = good_chosen / good_plain if good_plain else None
-        res = {"plain": plain, "chosen": chosen, "by_flag": by_flag,
+        # the rate policy (tnsk_choose_params_rate): the same predictor and pilot, the (m, R)
+        # that maximise the batch's expected within-5% estimates per unit of work; timed
+        # like the chosen arm (choice, then the batch in one call)
+        routs = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in nets]
+        rate_p, _, rhow = ctx.choose_params_batch(nets, target, base, mlp, pilot_reps=16, rate=True)  # warm-up
+        ctx.estimate_batch(nets, rate_p, routs)
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        for _ in range(steps):
+            rate_p, _, rhow = ctx.choose_params_batch(nets, target, base, mlp, pilot_reps=16, rate=True)
+            ctx.estimate_batch(nets, rate_p, routs)
+            torch.cuda.synchronize()
+        rate_s = (time.perf_counter() - c0) / steps
+        rate_err = rel(routs)
+        rhow = np.asarray(rhow)
+        runits = np.array([p.m * p.reps for p in rate_p], dtype=np.float64)
+        rate = {"estimates_per_s": round(n / rate_s, 1), "networks": n,
+                "within_5pct": round(float(np.mean(rate_err <= target)), 3),
+                "median_m": int(np.median([p.m for p in rate_p])),
+                "median_reps": int(np.median([p.reps for p in rate_p])),
+                "sum_mR_over_plain": float(f"{runits.sum() / punits.sum():.3g}"),
+                "sized_by": {"predictor": int(np.sum(rhow == 0)), "pilot": int(np.sum(rhow == 1)),
+                             "flagged": int(np.sum(rhow == 2))},
+                "sized_within_5pct": round(float(np.mean(rate_err[rhow != 2] <= target)), 3) if (rhow != 2).any()
+                else None}
+        good_rate = n * rate["within_5pct"] / rate_s
+        res = {"plain": plain, "chosen": chosen, "chosen_rate": rate, "by_flag": by_flag,
                "within_5pct_estimates_per_s": {"plain": round(good_plain, 1), "chosen": round(good_chosen, 1),
-                                               "ratio": round(ratio, 2) if ratio else None}}
+                                               "ratio": round(ratio, 2) if ratio else None,
+                                               "chosen_rate": round(good_rate, 1),
+                                               "ratio_rate": round(good_rate / good_plain, 2) if good_plain else None}}
         if ceiling:
             # The best any sizing rule can do on these networks: each network's errors
             # measured at every candidate (m, R) over 8 other seeds; the cheapest

@@ -513,6 +513,27 @@ tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_networ
                                      tnsk_mlp* mlp, int32_t pilot_reps, tnsk_params* inout, double* predicted_err,
                                      int32_t* how);
 
+/* Parameters for B networks for the most estimates within target_err per unit of work
+ * over the batch (a throughput policy of the library; the paper sizes m by its variance
+ * bounds only). The candidates, their cost R (sum_k q_k N_k + p m log2 m) and the
+ * sources of prediction are those of tnsk_choose_params_batch; both policies model one
+ * estimate's relative error as sigma |Z| (Z standard normal; from the predictor,
+ * log10 sigma = prediction + 0.2757, since E log10 |Z| = -0.2757; from the pilot,
+ * sigma = s / |mean| with s^2 as there), so a candidate meets the target with chance
+ * P = erf(target_err / (sigma sqrt 2)). The choice maximises sum_b P_b / sum_b cost_b:
+ * Dinkelbach's iteration, each network taking the candidate that maximises
+ * P - lambda cost with lambda the batch's current ratio, until lambda stops rising.
+ * A network is sized where the predictor covers it (how[b] = 0), else by the pilot when
+ * pilot_reps >= 2 (how[b] = 1; networks with a prediction are not piloted); where its
+ * chosen chance is below 1/2 it is flagged how[b] = 2 (meeting the target costs more
+ * than it returns at the batch's rate), its candidate still the one chosen.
+ * predicted_err[b]: the chosen candidate's 90% quantile, 1.6449 sigma (1e300 where
+ * nothing predicts it). inout, predicted_err, how, waits and errors: as
+ * tnsk_choose_params_batch. */
+tnsk_status tnsk_choose_params_rate(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, double target_err,
+                                    tnsk_mlp* mlp, int32_t pilot_reps, tnsk_params* inout, double* predicted_err,
+                                    int32_t* how);
+
 /* Wait for the ctx's stream; returns the first deferred device error, if any. */
 tnsk_status tnsk_sync(tnsk_ctx* ctx);
 

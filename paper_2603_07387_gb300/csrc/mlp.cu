@@ -760,26 +760,42 @@ tnsk_status tnsk_choose_params(tnsk_ctx* ctx, const tnsk_network* net, double ta
     return ctx_fail(ctx, TNSK_ERR_UNREACHABLE, "choose_params: no m <= 2^16 meets the target");
 }
 
-// Sizing for a batch (tnsk.h): the learned predictor first, a batched pilot second.
-// Candidates m = 2^6 .. 2^16, R in {16, 32, 64}; the cost of a candidate is
-// Theorem 1's work per repetition times R: R (sum_k q_k N_k + p m log2 m).
-tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, double target_err,
-                                     tnsk_mlp* mlp, int32_t pilot_reps, tnsk_params* inout, double* predicted_err,
-                                     int32_t* how) {
+}  // extern "C"
+
+namespace {
+
+// The sizing policies of a batch (tnsk_choose_params_batch, tnsk_choose_params_rate).
+// Both see every candidate (m, R), m = 2^6 .. 2^16 and R in {16, 32, 64}, through the
+// same normal model of one estimate's relative error, sigma |Z|: from the learned
+// predictor (log10 sigma = prediction + 0.2757, since E log10 |Z| = -0.2757), or from a
+// pilot (sigma = s / |mean|, s^2 the pilot's per-rep variance taken one standard error
+// up and scaled by 2^12 / (m R)). Its 90% quantile is 1.6449 sigma. The cost of a
+// candidate is R (sum_k q_k N_k + p m log2 m).
+// quantile policy (rate = false): the cheapest candidate whose 90% quantile meets the
+//   target; predictor first, the pilot for the networks it leaves, else flagged;
+// rate policy (rate = true): the candidates that maximise the batch's expected number
+//   of estimates within the target per unit of cost, sum_b P_b / sum_b cost_b with
+//   P = erf(target / (sigma sqrt 2)) (Dinkelbach's iteration); the pilot only for
+//   networks without a prediction; flagged where the chosen chance is below 1/2.
+tnsk_status choose_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, double target_err, tnsk_mlp* mlp,
+                         int32_t pilot_reps, tnsk_params* inout, double* predicted_err, int32_t* how, bool rate) {
     tnsk_status st = ctx_check(ctx);
     if (st != TNSK_OK) return st;
+    const char* who = rate ? "choose_params_rate" : "choose_params_batch";
     if (B < 0 || (B > 0 && (!nets || !inout || !predicted_err || !how)) || !(target_err > 0.0) || pilot_reps < 0 ||
         pilot_reps == 1 || pilot_reps > 4096)
-        return ctx_fail(ctx, TNSK_ERR_INVALID, "choose_params_batch: arguments");
+        return ctx_fail(ctx, TNSK_ERR_INVALID, std::string(who) + ": arguments");
     constexpr int kLo = 6, kHi = 16, kPilotLog2m = 12;
     // R from 16 up: the normal quantile of the mean is not trusted below (heavy tails)
     static const int kReps[] = {16, 32, 64};
-    constexpr int nR = 3, nL = kHi - kLo + 1;
-    constexpr double kQuantile90 = 1.0 / 0.3224;  // as tnsk_choose_params: 10^pred / 0.3224
-    constexpr double kZ90 = 1.6449;               // P(|Z| <= 1.6449) = 0.9
+    constexpr int nR = 3, nL = kHi - kLo + 1, nO = nL * nR;
+    constexpr double kZ90 = 1.6449;         // P(|Z| <= 1.6449) = 0.9
+    constexpr double kGeoZ = 0.2757;        // -E log10 |Z|
     std::vector<double> work(B, 0.0);  // sum_k q_k N_k
     std::vector<int> pterms(B, 0);
-    std::vector<char> done(B, 0);
+    // sigma of every candidate (o = (l - kLo) nR + j), +inf where nothing predicts it
+    std::vector<double> sig((size_t)B * nO, HUGE_VAL);
+    std::vector<char> predicted(B, 0);
     // ---- the learned predictor (method 1 networks)
     std::vector<float> hx;
     std::vector<int> rows_of;  // network of each block of nL * nR rows
@@ -787,7 +803,7 @@ tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_networ
     std::vector<SqJob> jobs;   // their tensors, for one batched norm pass
     for (int b = 0; b < B; ++b) {
         if (inout[b].method == TNSK_CROSSCORR)
-            return ctx_fail(ctx, TNSK_ERR_UNSUPPORTED, "choose_params_batch: the cross-correlation estimator");
+            return ctx_fail(ctx, TNSK_ERR_UNSUPPORTED, std::string(who) + ": the cross-correlation estimator");
         NetInfo I;
         float base[kFeatures];
         tnsk_params q = inout[b];
@@ -825,15 +841,6 @@ tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_networ
                     hx[at + 8] = (float)std::log2((double)kReps[j]);
                 }
         }
-    }
-    auto cost = [&](int b, int l, int R) {
-        return (double)R * (work[b] + (double)pterms[b] * std::ldexp(1.0, l) * (double)l);
-    };
-    for (int b = 0; b < B; ++b) {
-        how[b] = 2;
-        predicted_err[b] = 1e300;
-    }
-    if (!rows_of.empty()) {
         const size_t n = hx.size() / kFeatures;
         st = ctx_ensure_work(ctx, (hx.size() + n) * sizeof(float));
         if (st != TNSK_OK) return st;
@@ -844,39 +851,35 @@ tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_networ
         if (st == TNSK_OK) {
             cudaMemcpyAsync(hy.data(), d + hx.size(), n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
             const cudaError_t e = cudaStreamSynchronize(ctx->stream);
-            if (e != cudaSuccess) st = ctx_cuda_fail(ctx, e, "choose_params_batch");
+            if (e != cudaSuccess) st = ctx_cuda_fail(ctx, e, who);
         }
         if (st != TNSK_OK) return st;
         for (size_t i = 0; i < rows_of.size(); ++i) {
             const int b = rows_of[i];
-            double best_cost = 1e300, best_err = 1e300;
-            int bl = -1, bR = 0;
-            for (int l = kLo; l <= kHi; ++l)
-                for (int j = 0; j < nR; ++j) {
-                    const double err = std::pow(10.0, (double)hy[i * nL * nR + (l - kLo) * nR + j]) * kQuantile90;
-                    predicted_err[b] = std::min(predicted_err[b], err);
-                    if (err <= target_err && cost(b, l, kReps[j]) < best_cost) {
-                        best_cost = cost(b, l, kReps[j]);
-                        best_err = err;
-                        bl = l;
-                        bR = kReps[j];
-                    }
-                }
-            if (bl >= 0) {
-                inout[b].m = (int64_t)1 << bl;
-                inout[b].reps = bR;
-                inout[b].groups = 1;
-                predicted_err[b] = best_err;
-                how[b] = 0;
-                done[b] = 1;
-            }
+            predicted[b] = 1;
+            for (int o = 0; o < nO; ++o) sig[(size_t)b * nO + o] = std::pow(10.0, (double)hy[i * nO + o] + kGeoZ);
         }
     }
-    // ---- the pilot: pilot_reps repetitions at m = 2^12 of the rest, in one batch; the
-    // per-rep variance scales as 1/m (both variance lemmas), the mean of R reps as 1/R
+    auto cost = [&](int b, int o) {
+        const int l = kLo + o / nR, R = kReps[o % nR];
+        return (double)R * (work[b] + (double)pterms[b] * std::ldexp(1.0, l) * (double)l);
+    };
+    // the cheapest candidate whose 90% quantile meets the target, -1 if none
+    auto cheapest_meeting = [&](int b) {
+        int best = -1;
+        for (int o = 0; o < nO; ++o)
+            if (kZ90 * sig[(size_t)b * nO + o] <= target_err && (best < 0 || cost(b, o) < cost(b, best))) best = o;
+        return best;
+    };
+    for (int b = 0; b < B; ++b) how[b] = 2;
+    // ---- the pilot: pilot_reps repetitions at m = 2^12 of the networks the predictor
+    // leaves (no prediction; for the quantile policy also no candidate meeting the
+    // target), in one batch; the per-rep variance scales as 1/m (both variance
+    // lemmas), the mean of R reps as 1/R
     std::vector<int> pil;
     for (int b = 0; b < B; ++b)
-        if (!done[b] && pilot_reps > 0) pil.push_back(b);
+        if (pilot_reps > 0 && (!predicted[b] || (!rate && cheapest_meeting(b) < 0))) pil.push_back(b);
+    std::vector<char> piloted(B, 0);
     if (!pil.empty()) {
         const int P = (int)pil.size();
         const size_t nd = (size_t)P * (pilot_reps + 1);
@@ -901,7 +904,7 @@ tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_networ
         if (st == TNSK_OK) {
             cudaMemcpyAsync(h.data(), d, nd * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
             const cudaError_t e = cudaStreamSynchronize(ctx->stream);
-            if (e != cudaSuccess) st = ctx_cuda_fail(ctx, e, "choose_params_batch: pilot");
+            if (e != cudaSuccess) st = ctx_cuda_fail(ctx, e, who);
         }
         if (st != TNSK_OK) return st;
         for (int i = 0; i < P; ++i) {
@@ -915,37 +918,82 @@ tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_networ
             // one standard error up (a normal sample variance has relative error sqrt(2/(n-1))),
             // so a pilot that happens to see a small spread does not undersize
             var *= 1.0 + std::sqrt(2.0 / (pilot_reps - 1));
-            double best_cost = 1e300, best_err = 1e300;
-            int bl = -1, bR = 0;
-            for (int l = kLo; l <= kHi; ++l)
-                for (int j = 0; j < nR; ++j) {
-                    const double sd = std::sqrt(var * std::ldexp(1.0, kPilotLog2m - l) / kReps[j]);
-                    const double err = mean != 0.0 ? kZ90 * sd / std::fabs(mean) : 1e300;
-                    predicted_err[b] = std::min(predicted_err[b], err);
-                    if (err <= target_err && cost(b, l, kReps[j]) < best_cost) {
-                        best_cost = cost(b, l, kReps[j]);
-                        best_err = err;
-                        bl = l;
-                        bR = kReps[j];
-                    }
-                }
-            if (bl >= 0) {
-                inout[b].m = (int64_t)1 << bl;
-                inout[b].reps = bR;
-                inout[b].groups = 1;
-                predicted_err[b] = best_err;
-                how[b] = 1;
-                done[b] = 1;
+            piloted[b] = 1;
+            for (int o = 0; o < nO; ++o) {
+                const int l = kLo + o / nR;
+                const double sd = std::sqrt(var * std::ldexp(1.0, kPilotLog2m - l) / kReps[o % nR]);
+                sig[(size_t)b * nO + o] = mean != 0.0 ? sd / std::fabs(mean) : HUGE_VAL;
             }
         }
     }
-    for (int b = 0; b < B; ++b)
-        if (!done[b]) {  // no candidate reaches the target: the cheapest one, flagged (how = 2)
-            inout[b].m = (int64_t)1 << kLo;
-            inout[b].reps = kReps[0];
-            inout[b].groups = 1;
+    std::vector<int> pick(B, 0);  // candidate per network (0: the cheapest, m = 2^6, R = 16)
+    if (!rate) {
+        for (int b = 0; b < B; ++b) {
+            const int o = cheapest_meeting(b);
+            if (o >= 0) {
+                pick[b] = o;
+                how[b] = piloted[b] ? 1 : 0;
+            }
         }
+    } else {
+        // Dinkelbach's iteration for max sum P / sum cost: with lambda the current ratio,
+        // each network takes the candidate maximising P - lambda cost; the new ratio is at
+        // least the old one, and a repeat of it ends the iteration
+        std::vector<double> chance((size_t)B * nO);
+        for (size_t i = 0; i < chance.size(); ++i)
+            chance[i] = std::isfinite(sig[i]) ? std::erf(target_err / (sig[i] * std::sqrt(2.0))) : 0.0;
+        double lambda = 0.0;
+        for (int it = 0; it < 64; ++it) {
+            double num = 0.0, den = 0.0;
+            for (int b = 0; b < B; ++b) {
+                int best = 0;
+                double bv = -HUGE_VAL;
+                for (int o = 0; o < nO; ++o) {
+                    const double v = chance[(size_t)b * nO + o] - lambda * cost(b, o);
+                    if (v > bv || (v == bv && cost(b, o) < cost(b, best))) bv = v, best = o;
+                }
+                pick[b] = best;
+                num += chance[(size_t)b * nO + best];
+                den += cost(b, best);
+            }
+            const double next = den > 0.0 ? num / den : 0.0;
+            if (!(next > lambda * (1.0 + 1e-12))) break;
+            lambda = next;
+        }
+        for (int b = 0; b < B; ++b)
+            if (chance[(size_t)b * nO + pick[b]] >= 0.5) how[b] = piloted[b] ? 1 : 0;
+    }
+    for (int b = 0; b < B; ++b) {
+        const int o = how[b] == 2 && !rate ? 0 : pick[b];
+        inout[b].m = (int64_t)1 << (kLo + o / nR);
+        inout[b].reps = kReps[o % nR];
+        inout[b].groups = 1;
+        if (how[b] != 2 || rate) {
+            const double e = kZ90 * sig[(size_t)b * nO + o];
+            predicted_err[b] = std::isfinite(e) ? e : 1e300;
+        } else {  // flagged: the best candidate's 90% quantile
+            double best = HUGE_VAL;
+            for (int q = 0; q < nO; ++q) best = std::min(best, kZ90 * sig[(size_t)b * nO + q]);
+            predicted_err[b] = std::isfinite(best) ? best : 1e300;
+        }
+    }
     return TNSK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tnsk_status tnsk_choose_params_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, double target_err,
+                                     tnsk_mlp* mlp, int32_t pilot_reps, tnsk_params* inout, double* predicted_err,
+                                     int32_t* how) {
+    return choose_batch(ctx, B, nets, target_err, mlp, pilot_reps, inout, predicted_err, how, false);
+}
+
+tnsk_status tnsk_choose_params_rate(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, double target_err,
+                                    tnsk_mlp* mlp, int32_t pilot_reps, tnsk_params* inout, double* predicted_err,
+                                    int32_t* how) {
+    return choose_batch(ctx, B, nets, target_err, mlp, pilot_reps, inout, predicted_err, how, true);
 }
 
 }  // extern "C"

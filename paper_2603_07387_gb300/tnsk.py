@@ -80,6 +80,7 @@ SYMBOLS = (
     "tnsk_contract_pairs",
     "tnsk_choose_params",
     "tnsk_choose_params_batch",
+    "tnsk_choose_params_rate",
     "tnsk_status_string",
     "tnsk_last_error",
 )
@@ -225,6 +226,7 @@ def load_library(path: str = LIB_PATH):
         ("tnsk_contract_pairs", [vp, i32, vp]),
         ("tnsk_choose_params", [vp, ctypes.POINTER(_Network), ctypes.c_double, vp, ctypes.POINTER(_Params), dp]),
         ("tnsk_choose_params_batch", [vp, i32, vp, ctypes.c_double, vp, i32, vp, vp, vp]),
+        ("tnsk_choose_params_rate", [vp, i32, vp, ctypes.c_double, vp, i32, vp, vp, vp]),
     ]:
         getattr(L, name).restype = i32
         getattr(L, name).argtypes = args
@@ -845,20 +847,21 @@ class Context:
         return dataclasses.replace(params, m=int(pr.m)), err.value
 
     def choose_params_batch(self, nets: Sequence[Network], target_err: float, params: Sequence[Params], mlp=None,
-                            pilot_reps: int = 16):
-        """tnsk_choose_params_batch: ([params with m and reps chosen], [predicted error],
-        [how: 0 predictor, 1 pilot, 2 neither reached the target])."""
+                            pilot_reps: int = 16, rate: bool = False):
+        """tnsk_choose_params_batch (tnsk_choose_params_rate with rate=True): ([params with
+        m and reps chosen], [predicted error], [how: 0 predictor, 1 pilot, 2 flagged: not
+        sized to the target])."""
         import dataclasses
 
+        fn = self.lib.tnsk_choose_params_rate if rate else self.lib.tnsk_choose_params_batch
         B = len(nets)
         holders = [_holder(n) for n in nets]
         carr = (_Network * max(1, B))(*[h.c for h in holders])
         parr = (_Params * max(1, B))(*[_params(p) for p in params])
         err = (ctypes.c_double * max(1, B))()
         how = (ctypes.c_int32 * max(1, B))()
-        self._check(self.lib.tnsk_choose_params_batch(self.h, B, carr, float(target_err),
-                                                      mlp.h if mlp is not None else None, int(pilot_reps), parr,
-                                                      err, how))
+        self._check(fn(self.h, B, carr, float(target_err), mlp.h if mlp is not None else None, int(pilot_reps), parr,
+                       err, how))
         out = [dataclasses.replace(p, m=int(parr[i].m), reps=int(parr[i].reps), groups=int(parr[i].groups))
                for i, p in enumerate(params)]
         return out, [err[i] for i in range(B)], [how[i] for i in range(B)]

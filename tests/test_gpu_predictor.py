@@ -231,6 +231,44 @@ def test_choose_params_batch_pilot_meets_the_target(ctx):
     assert he == 1 and pe.m * pe.reps <= 1 << 14
 
 
+def test_choose_params_rate_pilot(ctx):
+    """tnsk_choose_params_rate without a predictor: every network is piloted; the choice
+    maximises the batch's expected within-target estimates per unit of work, so a sized
+    network (how 1) has a chance of at least 1/2 by the model (90% quantile at most
+    1.6449 / 0.6745 times the target), a flagged one (how 2) less; the sized estimates,
+    checked with fresh repetitions against the exact value, meet the target about as
+    often as the model says (at least 40% here); and an easy network is sized cheaply."""
+    held = [s for s in predictor.grid_specs(np.random.default_rng(11), 30) if len(s.edges) >= 4]
+    nets = [tnsk.Network(W.to_torch(s, "cuda", torch.float32), s.edges, s.open) for s in held]
+    params = [tnsk.Params(m=1, reps=16, seed=900 + i) for i in range(len(nets))]
+    target = 0.05
+    chosen, errs, how = ctx.choose_params_batch(nets, target, params, None, pilot_reps=16, rate=True)
+    assert all(h in (1, 2) for h in how)
+    lim = 1.6449 / 0.6745 * target
+    met = sized = 0
+    for s, n, p, h, e in zip(held, nets, chosen, how, errs):
+        assert p.reps in (16, 32, 64) and p.m in [1 << l for l in range(6, 17)] and p.groups == 1
+        if h == 2:
+            assert e > lim * (1 - 1e-9)
+            continue
+        assert e <= lim * (1 + 1e-9)
+        sized += 1
+        tc = tc_sequential([np.asarray(x, dtype=np.float32).astype(np.float64) for x in s.tensors], s.edges, s.open)
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ctx.estimate(n, p, out)
+        ctx.sync()
+        met += abs(float(out.item()) - tc) / abs(tc) <= target
+    assert sized >= 4 and met >= 0.4 * sized
+    easy = W.NetSpec([np.random.default_rng(1).uniform(0, 1, 64), np.random.default_rng(2).uniform(0, 1, 64)],
+                     [(0, 1)], [], "dot")
+    ne = tnsk.Network(W.to_torch(easy, "cuda", torch.float32), easy.edges, easy.open)
+    (pe,), _, (he,) = ctx.choose_params_batch([ne], target, [tnsk.Params(m=1, reps=16, seed=3)], None, pilot_reps=16,
+                                              rate=True)
+    assert he == 1 and pe.m * pe.reps <= 1 << 14
+    with pytest.raises(tnsk.TnskError):
+        ctx.choose_params_batch([ne], target, [tnsk.Params(m=1, reps=16)], None, pilot_reps=1, rate=True)
+
+
 def test_choose_params_batch_rejects_bad_arguments(ctx):
     spec = W.grid(1, 2, 4, seed=1)
     net = tnsk.Network(W.to_torch(spec, "cuda", torch.float32), spec.edges, spec.open)
