@@ -284,6 +284,50 @@ __global__ void __launch_bounds__(256) m2_vbuild_kernel(const M2Node* __restrict
     // the child sketch entry): a thread takes kU of them at once, all loads before any
     // store, so kU chains are in flight per thread.
     constexpr int kU = 4;
+    if (it.pad_ == 1 && one_child && qt <= 1 && it.b <= 2 && it.end - it.begin <= 4 * (int64_t)blockDim.x &&
+        (int64_t)it.b * m <= 8 * (int64_t)blockDim.x) {
+        // One child mode, no padding words or T tables (chains): every global load of the
+        // item, the column words of all its reps and their child sketches, is issued at
+        // once, then one barrier, the gathers from shared memory and the stores
+        const int G = it.b, r0 = it.a;
+        const int bd = (int)blockDim.x;
+        T* s_src = reinterpret_cast<T*>(smem_raw);
+        uint32_t wv[2][4];
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            const uint32_t* tabr = tabs + tab_off + (int64_t)(r0 + (g < G ? g : 0)) * Lrep + one_ctab;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t col = it.begin + threadIdx.x + (int64_t)u * bd;
+                wv[g][u] = (g < G && col < it.end) ? __ldg(tabr + col) : 0u;
+            }
+        }
+        const int64_t nsrc = (int64_t)G * m;
+        T cv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int64_t q = threadIdx.x + (int64_t)i * bd;
+            const int64_t g = q >> N.log2m;
+            cv[i] = q < nsrc ? ws[src_off + (r0 + g) * src_stride + (q - (g << N.log2m))] : (T)0;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int64_t q = threadIdx.x + (int64_t)i * bd;
+            if (q < nsrc) s_src[q] = cv[i];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t col = it.begin + threadIdx.x + (int64_t)u * bd;
+                if (g < G && col < it.end) {
+                    const T z = s_src[g * m + (wv[g][u] & mask)];
+                    store(r0 + g, col, (wv[g][u] & TNSK_SIGN_BIT) ? -z : z);
+                }
+            }
+        return;
+    }
     if (it.pad_ == 1) {
         const int G = it.b, r0 = it.a;
         const int64_t tw = qt >= 2 ? 2 * (int64_t)(qt - 1) * m : 0;  // T-table words of one rep
