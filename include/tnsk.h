@@ -211,7 +211,17 @@ tnsk_status tnsk_m1_sketch(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_pa
  * plan's own buffer for tnsk_plan_create), by a kernel the call enqueues before
  * the method's kernels. A cycle through three or more tensors still returns
  * TNSK_ERR_CYCLIC; a grouped (rung) tensor that would need the rewrite, or a
- * merged mode above 2^31 - 1, TNSK_ERR_UNSUPPORTED. */
+ * merged mode above 2^31 - 1, TNSK_ERR_UNSUPPORTED.
+ * TNSK_ACYCLIC networks with open legs (tnsk_estimate and tnsk_estimate_batch; plans
+ * refuse them): each output entry o, row-major over `open`, is the full estimate of
+ * the network whose tensors are sliced at o's open indices (Corollary
+ * "full-to-partial-tc"), all entries with the same hash functions. Every tensor with
+ * open modes is first written once, open modes first, into a ctx-owned buffer (FP64
+ * stays FP64, FP32 and BF16 become FP32); the entries then run in one batch, the
+ * slices being the networks planned (WLOG 2 / 3 apply to them, `root` refers to their
+ * tensors, the default root taking the smallest slice). per_rep, if given, receives
+ * [R][O] as for method 1. At most 2^16 output entries per call (TNSK_ERR_UNSUPPORTED
+ * beyond, and for an empty output or a grouped tensor with open modes). */
 tnsk_status tnsk_estimate(tnsk_ctx* ctx, const tnsk_network* net, const tnsk_params* params, double* out,
                           double* per_rep);
 

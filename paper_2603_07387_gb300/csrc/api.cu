@@ -194,6 +194,7 @@ tnsk_status tnsk_destroy(tnsk_ctx* ctx) {
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->aux) cudaFree(ctx->aux);
     if (ctx->work) cudaFree(ctx->work);
+    if (ctx->open_buf) cudaFree(ctx->open_buf);
     if (ctx->side) {
         cudaStreamSynchronize(ctx->side);
         cudaStreamDestroy(ctx->side);
@@ -261,7 +262,7 @@ tnsk_status tnsk_count_sketch(tnsk_ctx* ctx, uint64_t seed, uint64_t rep, uint64
 static tnsk_status build_plan(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
                               double* const* outs, double* const* per_reps, bool sketch_only, BatchPlan& plan,
                               bool& fp64, bool zero_ok = false, const NormBatch* nb = nullptr,
-                              const tnsk_schedule* sched = nullptr) {
+                              const tnsk_schedule* sched = nullptr, const int64_t* rep_stride = nullptr) {
     if (B < 0 || (B > 0 && (!nets || !params))) return fail(ctx, TNSK_ERR_INVALID, "null batch arguments");
     std::vector<NetInfo> infos(B);
     for (int b = 0; b < B; ++b) {
@@ -276,7 +277,8 @@ static tnsk_status build_plan(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets
     for (int b = 1; b < B; ++b)
         if ((params[b].prec == TNSK_PREC_FP64) != fp64)
             return fail(ctx, TNSK_ERR_UNSUPPORTED, "mixed precisions in one batch");
-    return plan_batch(infos, nets, params, outs, per_reps, fp64, sketch_only, plan, ctx->last_error, sched);
+    return plan_batch(infos, nets, params, outs, per_reps, fp64, sketch_only, plan, ctx->last_error, sched,
+                      rep_stride);
 }
 
 // Device part: the launch sequence of a planned batch whose descriptors are
@@ -359,9 +361,10 @@ static tnsk_status launch_plan(tnsk_ctx* ctx, const BatchPlan& plan, unsigned ch
 }
 
 // Batch driver shared by tnsk_estimate, tnsk_estimate_batch and tnsk_m1_sketch.
-static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
-                             double* const* outs, double* const* per_reps, void* sketch_out,
-                             size_t* yrep_off = nullptr, int64_t* yrep_n = nullptr) {
+static tnsk_status run_batch_core(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
+                                  double* const* outs, double* const* per_reps, void* sketch_out,
+                                  size_t* yrep_off = nullptr, int64_t* yrep_n = nullptr,
+                                  const int64_t* rep_stride = nullptr) {
     tnsk_status st = check_ctx(ctx);
     if (st != TNSK_OK) return st;
     if (B == 0) return TNSK_OK;
@@ -378,7 +381,7 @@ static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets,
     BatchPlan plan;
     bool fp64 = false;
     st = build_plan(ctx, B, nb.used ? nb.view.data() : nets, params, outs, per_reps, sketch_out != nullptr, plan,
-                    fp64, false, &nb);
+                    fp64, false, &nb, nullptr, rep_stride);
     if (st != TNSK_OK) return st;
     st = ensure_scratch(ctx, plan.arena.used);
     if (st != TNSK_OK) return st;
@@ -398,6 +401,232 @@ static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets,
     if (yrep_off) *yrep_off = plan.yrep_off;
     if (yrep_n) *yrep_n = plan.yrep_n;
     return launch_plan(ctx, plan, ctx->scratch, fp64, sketch_out, nr);
+}
+
+// Method 2 with open legs (Corollary "full-to-partial-tc"): every output entry of a
+// TNSK_ACYCLIC network with open modes is the full estimate of the network whose
+// tensors are sliced at that entry's open indices. Each tensor with open modes is
+// written once, its open modes first (in the output order) and its other modes after
+// them in their order, so that every slice is a contiguous block; the entries then run
+// as networks of their own in one batch, with the same hash functions (the edges keep
+// their order) and the per-rep values of entry o at per_rep[r O + o]. Other networks
+// of the batch pass through. Networks whose structure does not check out here pass
+// through unchanged and are reported by the planner.
+namespace {
+struct OpenExpansion {
+    std::vector<tnsk_network> nets;
+    std::vector<tnsk_params> params;
+    std::vector<double*> outs, reps;
+    std::vector<int64_t> stride;
+    std::vector<std::vector<tnsk_tensor>> X;            // per expanded entry
+    std::vector<std::vector<std::vector<int64_t>>> dims;  // per source network: sliced dims per tensor
+    std::vector<std::vector<int32_t>> edges;             // per source network: renumbered edges
+    std::vector<NormJob> jobs;
+    std::vector<size_t> off;  // per job: output offset in the buffer
+    std::vector<std::pair<size_t, int>> sliced;  // (entry, tensor) whose data is an offset into the buffer
+    size_t bytes = 0;
+    int64_t most = 0;
+};
+constexpr int64_t kMaxOpenEntries = 1 << 16;  // expanded entries per call
+}  // namespace
+
+static tnsk_status expand_open_m2(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
+                                  double* const* outs, double* const* per_reps, OpenExpansion& E) {
+    int64_t entries = 0;
+    E.dims.resize(B);
+    E.edges.resize(B);
+    // first pass: which networks expand, their jobs and buffer size
+    struct Src {
+        bool expand = false;
+        int64_t O = 1;
+        std::vector<int> mode_off, open_pos, new_id, job;
+        std::vector<int64_t> slice;  // per tensor: entries per slice (its non-open modes)
+        std::vector<std::vector<int>> opens;  // per tensor: its open modes in output order
+    };
+    std::vector<Src> src(B);
+    for (int b = 0; b < B; ++b) {
+        const tnsk_network& N = nets[b];
+        Src& S = src[b];
+        if (params[b].method != TNSK_ACYCLIC || N.n_open <= 0 || N.p < 1 || !N.X || !N.open || N.t < 0 ||
+            (N.t > 0 && !N.edges))
+            continue;
+        // structure: modes, contracted modes, the open list a permutation of the rest
+        S.mode_off.assign(N.p + 1, 0);
+        bool ok = true;
+        for (int k = 0; k < N.p && ok; ++k) {
+            const tnsk_tensor& T = N.X[k];
+            ok = T.order >= 0 && T.order <= TNSK_MAX_ORDER && (T.order == 0 || T.dims) && (T.rung || T.data);
+            S.mode_off[k + 1] = S.mode_off[k] + (ok ? T.order : 0);
+        }
+        const int q = S.mode_off[N.p];
+        std::vector<int> tensor_of(q), used(q, 0);
+        for (int k = 0; k < N.p && ok; ++k)
+            for (int g = S.mode_off[k]; g < S.mode_off[k + 1]; ++g) tensor_of[g] = k;
+        for (int e = 0; e < N.t && ok; ++e)
+            for (int side = 0; side < 2 && ok; ++side) {
+                const int g = N.edges[2 * e + side];
+                ok = g >= 0 && g < q && !used[g];
+                if (ok) used[g] = 1;
+            }
+        S.open_pos.assign(q, -1);
+        for (int j = 0; j < N.n_open && ok; ++j) {
+            const int g = N.open[j];
+            ok = g >= 0 && g < q && !used[g] && S.open_pos[g] < 0;
+            if (ok) S.open_pos[g] = j;
+        }
+        for (int g = 0; g < q && ok; ++g) ok = used[g] || S.open_pos[g] >= 0;
+        if (!ok) continue;
+        auto dim_of = [&](int g) { return N.X[tensor_of[g]].dims[g - S.mode_off[tensor_of[g]]]; };
+        for (int j = 0; j < N.n_open; ++j) S.O *= std::max<int64_t>(dim_of(N.open[j]), 0);
+        entries += S.O;
+        if (S.O == 0 || entries > kMaxOpenEntries)
+            return fail(ctx, TNSK_ERR_UNSUPPORTED,
+                        "network " + std::to_string(b) + ": method 2 with open legs takes up to 2^16 output entries "
+                        "per call (one full estimate each), and none of an empty output");
+        S.expand = true;
+        // renumbered contracted modes and edges; per tensor its open modes (output order)
+        S.new_id.assign(q, -1);
+        int nid = 0;
+        for (int g = 0; g < q; ++g)
+            if (S.open_pos[g] < 0) S.new_id[g] = nid++;
+        E.edges[b].resize(2 * (size_t)N.t);
+        for (int e = 0; e < 2 * N.t; ++e) E.edges[b][e] = S.new_id[N.edges[e]];
+        S.opens.assign(N.p, {});
+        S.slice.assign(N.p, 1);
+        S.job.assign(N.p, -1);
+        E.dims[b].assign(N.p, {});
+        for (int j = 0; j < N.n_open; ++j) S.opens[tensor_of[N.open[j]]].push_back(N.open[j]);
+        for (int k = 0; k < N.p; ++k)
+            if (N.X[k].rung && !S.opens[k].empty())
+                return fail(ctx, TNSK_ERR_UNSUPPORTED,
+                            "network " + std::to_string(b) + ": a grouped tensor with open modes (method 2)");
+        for (int k = 0; k < N.p; ++k) {
+            const tnsk_tensor& T = N.X[k];
+            for (int d = 0; d < T.order; ++d)
+                if (S.open_pos[S.mode_off[k] + d] < 0) {
+                    E.dims[b][k].push_back(T.dims[d]);
+                    S.slice[k] *= T.dims[d];
+                }
+            if (S.opens[k].empty()) continue;
+            // the tensor with its open modes first: a strided gather (normalize_kernel)
+            NormJob J{};
+            J.src = T.data;
+            J.src_dtype = T.dtype;
+            J.dst_f64 = T.dtype == TNSK_F64;
+            int64_t str[TNSK_MAX_ORDER], st = 1;
+            for (int d = T.order - 1; d >= 0; --d) str[d] = st, st *= T.dims[d];
+            J.numel = st;
+            J.n = 0;
+            for (int g : S.opens[k]) {
+                J.dim[J.n] = dim_of(g);
+                J.str[J.n++] = str[g - S.mode_off[k]];
+            }
+            for (int d = 0; d < T.order; ++d)
+                if (S.open_pos[S.mode_off[k] + d] < 0) {
+                    J.dim[J.n] = T.dims[d];
+                    J.str[J.n++] = str[d];
+                }
+            J.nd = 0;
+            S.job[k] = (int)E.jobs.size();
+            E.bytes = (E.bytes + 255) & ~(size_t)255;
+            E.off.push_back(E.bytes);
+            E.bytes += (size_t)J.numel * (J.dst_f64 ? 8 : 4);
+            E.most = std::max(E.most, J.numel);
+            E.jobs.push_back(J);
+        }
+    }
+    if (E.jobs.empty() && entries == 0) return TNSK_OK;
+    // the expanded batch
+    E.nets.reserve(B + entries);
+    E.X.reserve(entries);
+    for (int b = 0; b < B; ++b) {
+        const Src& S = src[b];
+        if (!S.expand) {
+            E.nets.push_back(nets[b]);
+            E.params.push_back(params[b]);
+            E.outs.push_back(outs ? outs[b] : nullptr);
+            E.reps.push_back(per_reps ? per_reps[b] : nullptr);
+            E.stride.push_back(0);
+            continue;
+        }
+        const tnsk_network& N = nets[b];
+        for (int64_t o = 0; o < S.O; ++o) {
+            E.X.emplace_back(N.X, N.X + N.p);
+            std::vector<tnsk_tensor>& X = E.X.back();
+            for (int k = 0; k < N.p; ++k) {
+                X[k].order = (int32_t)E.dims[b][k].size();
+                X[k].dims = E.dims[b][k].data();
+                if (S.job[k] < 0) continue;
+                // the slice at this entry's indices of the tensor's open modes (row-major
+                // over them in output order, the open list's first mode slowest)
+                int64_t at = 0;
+                for (int g : S.opens[k]) {
+                    int64_t stride_o = 1;
+                    for (int j = S.open_pos[g] + 1; j < N.n_open; ++j) {
+                        const int h = N.open[j];
+                        int kk = 0;
+                        while (S.mode_off[kk + 1] <= h) ++kk;
+                        stride_o *= N.X[kk].dims[h - S.mode_off[kk]];
+                    }
+                    int kk = 0;
+                    while (S.mode_off[kk + 1] <= g) ++kk;
+                    const int64_t dg = N.X[kk].dims[g - S.mode_off[kk]];
+                    at = at * dg + (o / stride_o) % dg;
+                }
+                const NormJob& J = E.jobs[S.job[k]];
+                // an offset into the buffer until its address is known (run_batch)
+                X[k].data = (const void*)(uintptr_t)(E.off[S.job[k]] + (size_t)(at * S.slice[k]) * (J.dst_f64 ? 8 : 4));
+                X[k].dtype = J.dst_f64 ? TNSK_F64 : TNSK_F32;
+                E.sliced.emplace_back(E.X.size() - 1, k);
+            }
+            tnsk_network n{};
+            n.p = N.p;
+            n.X = X.data();
+            n.t = N.t;
+            n.edges = E.edges[b].data();
+            n.n_open = 0;
+            n.open = nullptr;
+            E.nets.push_back(n);
+            E.params.push_back(params[b]);
+            E.outs.push_back(outs && outs[b] ? outs[b] + o : nullptr);
+            E.reps.push_back(per_reps && per_reps[b] ? per_reps[b] + o : nullptr);
+            E.stride.push_back(S.O);
+        }
+    }
+    return TNSK_OK;
+}
+
+// Batch driver shared by tnsk_estimate, tnsk_estimate_batch and tnsk_m1_sketch.
+static tnsk_status run_batch(tnsk_ctx* ctx, int32_t B, const tnsk_network* nets, const tnsk_params* params,
+                             double* const* outs, double* const* per_reps, void* sketch_out,
+                             size_t* yrep_off = nullptr, int64_t* yrep_n = nullptr) {
+    tnsk_status st = check_ctx(ctx);
+    if (st != TNSK_OK) return st;
+    if (B <= 0 || !nets || !params || sketch_out)
+        return run_batch_core(ctx, B, nets, params, outs, per_reps, sketch_out, yrep_off, yrep_n);
+    OpenExpansion E;
+    st = expand_open_m2(ctx, B, nets, params, outs, per_reps, E);
+    if (st != TNSK_OK) return st;
+    if (E.nets.empty()) return run_batch_core(ctx, B, nets, params, outs, per_reps, sketch_out, yrep_off, yrep_n);
+    // the sliced copies, then the expanded batch on the same stream
+    st = ensure_buffer(ctx, ctx->open_buf, ctx->open_bytes,
+                       ((E.bytes + 255) & ~(size_t)255) + E.jobs.size() * sizeof(NormJob), "open-leg buffer");
+    if (st != TNSK_OK) return st;
+    for (size_t j = 0; j < E.jobs.size(); ++j) E.jobs[j].dst = ctx->open_buf + E.off[j];
+    for (const auto& sk : E.sliced) {  // the slices' offsets become addresses
+        tnsk_tensor& T = E.X[sk.first][sk.second];
+        T.data = ctx->open_buf + (uintptr_t)T.data;
+    }
+    const size_t desc = (E.bytes + 255) & ~(size_t)255;
+    if (!E.jobs.empty()) {
+        TNSK_CUDA(cudaMemcpyAsync(ctx->open_buf + desc, E.jobs.data(), E.jobs.size() * sizeof(NormJob),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+        ctx->prof.begin(TNSK_K_NORMALIZE, ctx->stream);
+        TNSK_CUDA(launch_normalize((const NormJob*)(ctx->open_buf + desc), (int)E.jobs.size(), E.most, ctx->stream));
+        ctx->prof.end(ctx->stream);
+    }
+    return run_batch_core(ctx, (int32_t)E.nets.size(), E.nets.data(), E.params.data(), E.outs.data(), E.reps.data(),
+                          nullptr, yrep_off, yrep_n, E.stride.data());
 }
 
 // TNSK_PREC_AUTO (tnsk.h): the FP32 path with the per-rep magnitude sums, the FP64 path

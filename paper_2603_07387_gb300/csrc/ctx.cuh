@@ -40,6 +40,10 @@ struct tnsk_ctx {
     // estimates), grown on demand and reused, so a parameter choice allocates nothing
     unsigned char* work = nullptr;
     size_t work_bytes = 0;
+    // method 2 with open legs: the tensors with open modes rewritten open modes first
+    // (their slices contiguous), then the job descriptors; grown on demand, stream ordered
+    unsigned char* open_buf = nullptr;
+    size_t open_bytes = 0;
 };
 
 namespace tnsk {

@@ -53,7 +53,8 @@ struct CombineItem {  // one output entry of one network
     int32_t R;
     int32_t groups;
     double* out;
-    double* per_rep;  // optional [R][O]
+    double* per_rep;  // optional [R][O]: rep r's value of entry o at r * ps + o
+    int64_t ps;       // per_rep row stride (O, or the caller's for an expanded network)
 };
 
 // One table row per (request, rep); rows = sum of the requests' R (crow prefix).

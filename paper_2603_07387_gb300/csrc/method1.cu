@@ -552,7 +552,7 @@ __global__ void combine_kernel(const CombineItem* __restrict__ items, int n_item
         const int g = c.groups;
         c.out[c.o] = (g & 1) ? med[g / 2] : 0.5 * (med[g / 2 - 1] + med[g / 2]);
         if (c.per_rep)
-            for (int r = 0; r < c.R; ++r) c.per_rep[(int64_t)r * c.O + c.o] = y[(int64_t)r * c.O + c.o];
+            for (int r = 0; r < c.R; ++r) c.per_rep[(int64_t)r * c.ps + c.o] = y[(int64_t)r * c.O + c.o];
     }
 }
 

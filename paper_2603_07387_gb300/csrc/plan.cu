@@ -456,7 +456,7 @@ void recycle_host_desc(std::vector<unsigned char>& H) {
 
 tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* nets, const tnsk_params* params,
                        double* const* outs, double* const* per_reps, bool fp64, bool sketch_only, BatchPlan& P,
-                       std::string& err, const tnsk_schedule* sched) {
+                       std::string& err, const tnsk_schedule* sched, const int64_t* rep_stride) {
     const int B = (int)infos.size();
     const size_t acc = fp64 ? sizeof(double) : sizeof(float);
     // The descriptor lists live in per-thread vectors that keep their capacity from one
@@ -777,6 +777,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
                 c.groups = pr.groups;
                 c.out = nb.out;
                 c.per_rep = nb.per_rep;
+                c.ps = I.O;
                 comb.push_back(c);
             }
             yrep_n += (int64_t)R * I.O;
@@ -1109,6 +1110,7 @@ tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* ne
         c.groups = pr.groups;
         c.out = outs ? outs[b] : nullptr;
         c.per_rep = per_reps ? per_reps[b] : nullptr;
+        c.ps = rep_stride && rep_stride[b] > 0 ? rep_stride[b] : 1;
         comb.push_back(c);
         yrep_n += R;
         m2n.push_back(nb);

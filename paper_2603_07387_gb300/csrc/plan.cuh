@@ -133,12 +133,15 @@ bool tensor_maps_available();
 // Encodes the plan's tensor maps into its host descriptor block once the device
 // base address of the plan's scratch is fixed (before the descriptor upload).
 tnsk_status finalize_plan(BatchPlan& plan, unsigned char* base, std::string& err);
-// sched: the scatter schedule (tnsk.h), NULL = the default one.
 // Hands an uploaded plan's staged descriptor block back for the calling thread's next
 // plan (its memory is reused instead of allocated and faulted in again); H is left empty.
 void recycle_host_desc(std::vector<unsigned char>& H);
+// sched: the scatter schedule (tnsk.h), NULL = the default one. rep_stride: per
+// network, the row stride of its per-rep output for method 2 (NULL or 0: 1; an output
+// entry of a network with open legs estimated as its own full network, see api.cu).
 tnsk_status plan_batch(const std::vector<NetInfo>& infos, const tnsk_network* nets, const tnsk_params* params,
                        double* const* outs, double* const* per_reps, bool fp64, bool sketch_only, BatchPlan& plan,
-                       std::string& err, const tnsk_schedule* sched = nullptr);
+                       std::string& err, const tnsk_schedule* sched = nullptr,
+                       const int64_t* rep_stride = nullptr);
 
 }  // namespace tnsk
