@@ -208,9 +208,6 @@ __global__ void __launch_bounds__(kFxThreads, 2) m1_scatter_fx_kernel(const M1Te
         if ((threadIdx.x & 31) == 0 && part > 0.f) atomicAdd(&s_mass[b % 3], part);
         __syncthreads();
         const float tot = s_mass[b % 3];
-        // prefetch the next batch while this one is scattered
-        float nxt[U][V];
-        if (b + 1 < nbatch) load(nxt, f + (int64_t)U * fs);
         if (tot > 0.f) {  // block-uniform; an all-zero batch adds nothing
             int ex;
             frexpf(tot, &ex);  // tot <= 2^ex
@@ -335,28 +332,24 @@ __global__ void __launch_bounds__(kFxThreads, 2) m1_scatter_fx_kernel(const M1Te
             for (int u = 0; u < U; ++u) advance();
         }
         f += (int64_t)U * fs;
-        if (b + 1 < nbatch) {
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-#pragma unroll
-                for (int j = 0; j < V; ++j) cur[u][j] = nxt[u][j];
-        }
+        if (b + 1 < nbatch) load(cur, f);
     }
     __syncthreads();
     // ---- out: the last batch's integer sums (scale 2^S) plus the accumulator
     const float g1 = pow2f(-(S / 2)), g2 = pow2f(-(S - S / 2));
     float* gx = xs + N.x_off + sT.xoff;
     const int per = (int)(O * m);
-    for (int q = threadIdx.x; q < (int)nbins; q += blockDim.x) {
-        float val = ((float)s_q[q] * g1) * g2;
-        if (multi) val += s_acc[q];
-        const int r = q / per;
-        const int ob = q - r * per;
-        float* dst = &gx[(int64_t)(w.rep0 + r) * N.X + ob];
-        if (w.priv == 2)
-            *dst = val;  // this item owns these bins: no other CTA writes them
-        else if (val != 0.f)
-            atomicAdd(dst, val);
+    for (int r = 0; r < nrep; ++r) {  // rep by rep: no division per bin
+        float* gr = gx + (int64_t)(w.rep0 + r) * N.X;
+        for (int ob = threadIdx.x; ob < per; ob += blockDim.x) {
+            const int q = r * per + ob;
+            float val = ((float)s_q[q] * g1) * g2;
+            if (multi) val += s_acc[q];
+            if (w.priv == 2)
+                gr[ob] = val;  // this item owns these bins: no other CTA writes them
+            else if (val != 0.f)
+                atomicAdd(&gr[ob], val);
+        }
     }
 }
 
