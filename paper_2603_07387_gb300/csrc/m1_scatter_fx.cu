@@ -49,6 +49,12 @@ __global__ void __launch_bounds__(kFxThreads, 2) m1_scatter_fx_kernel(const M1Te
     __shared__ int32_t sbase[TNSK_MAX_ORDER], slo[TNSK_MAX_ORDER], scnt[TNSK_MAX_ORDER];
     __shared__ int32_t sTT;
     __shared__ float s_mass[3];
+    // block-uniform per-slot data (slot s holds mode s - (MAXD - order): padding slots,
+    // dim 1 and not contracted, come first, so the last mode is slot MAXD - 1), read from
+    // shared memory where needed instead of held in every thread's registers
+    __shared__ int32_t u_dim[MAXD], u_base[MAXD], u_lo[MAXD], u_step[MAXD], u_gofs[MAXD];
+    __shared__ int64_t u_ostr[MAXD];
+    __shared__ bool u_ctr[MAXD], u_comp[MAXD];
     const M1Work w = work[blockIdx.x];
     if (threadIdx.x == 0) {
         sT = tens[w.tensor];
@@ -75,6 +81,20 @@ __global__ void __launch_bounds__(kFxThreads, 2) m1_scatter_fx_kernel(const M1Te
         }
         sTT = acc;
         s_mass[0] = s_mass[1] = s_mass[2] = 0.f;
+        int64_t sv = (int64_t)V * blockDim.x;  // the stride between a thread's groups
+        for (int d = MAXD - 1; d >= 0; --d) {
+            const int md = d - (MAXD - sT.order);
+            const bool live = md >= 0;
+            u_dim[d] = live ? (int32_t)sT.dims[md] : 1;
+            u_base[d] = live ? sbase[md] : 0;
+            u_lo[d] = live ? slo[md] : 0;
+            u_ctr[d] = live && sT.tab[md] >= 0;
+            u_comp[d] = u_ctr[d] && sT.comp[md];
+            u_gofs[d] = u_ctr[d] ? sT.tab[md] : 0;
+            u_ostr[d] = live ? sT.ostride[md] : 0;
+            u_step[d] = (int32_t)(sv % u_dim[d]);
+            sv /= u_dim[d];
+        }
     }
     __syncthreads();
     const M1Net& N = nets[sT.net];
@@ -112,30 +132,21 @@ __global__ void __launch_bounds__(kFxThreads, 2) m1_scatter_fx_kernel(const M1Te
         if (multi) s_acc[q] = 0.f;
     }
 
-    // block-uniform per-mode data. Slot s holds mode s - (MAXD - order): padding slots
-    // (dim 1, not contracted) come first, so the last mode is slot MAXD - 1
-    int dim[MAXD], base[MAXD], lo[MAXD], dig[MAXD], step[MAXD];
-    bool ctr[MAXD], comp[MAXD];
-    int64_t ostr[MAXD];
-    int32_t gofs[MAXD];
+    const int32_t* const dim = u_dim;
+    const int32_t* const base = u_base;
+    const int32_t* const lo = u_lo;
+    const int32_t* const step = u_step;
+    const int32_t* const gofs = u_gofs;
+    const int64_t* const ostr = u_ostr;
+    const bool* const ctr = u_ctr;
+    const bool* const comp = u_comp;
+    int dig[MAXD];  // this thread's multi-index (per slot)
     {
         int64_t f0 = w.begin + (int64_t)V * threadIdx.x;
-        int64_t sv = (int64_t)V * blockDim.x;
 #pragma unroll
         for (int d = MAXD - 1; d >= 0; --d) {
-            const int md = d - (MAXD - order);
-            const bool live = md >= 0;
-            dim[d] = live ? sT.dims[md] : 1;
-            base[d] = live ? sbase[md] : 0;
-            lo[d] = live ? slo[md] : 0;
-            ctr[d] = live && sT.tab[md] >= 0;
-            comp[d] = ctr[d] && sT.comp[md];
-            gofs[d] = ctr[d] ? sT.tab[md] : 0;
-            ostr[d] = live ? sT.ostride[md] : 0;
             dig[d] = (int)(f0 % dim[d]);
             f0 /= dim[d];
-            step[d] = (int)(sv % dim[d]);
-            sv /= dim[d];
         }
     }
     const bool has_open = O > 1;
@@ -232,15 +243,17 @@ __global__ void __launch_bounds__(kFxThreads, 2) m1_scatter_fx_kernel(const M1Te
                     ov[u] = fg < w.end ? od : -1;
                     advance();
                 }
+                // word offsets of the fixed slots, -1 where a slot adds no word
                 int hb[MAXD];
 #pragma unroll
-                for (int d = 0; d < MAXD; ++d) hb[d] = soff(d, dig[d]);  // unchanged by the advances
+                for (int d = 0; d < MAXD; ++d)
+                    hb[d] = (d == MAXD - 1 || (d >= d0 && ctr[d])) ? soff(d, dig[d]) : -1;  // unchanged by the advances
                 auto rep_updates = [&](int r) {
                     const uint32_t* row = s_tab + r * TT;
                     uint32_t hc = 0;
 #pragma unroll
                     for (int d = 0; d < MAXD - 1; ++d)
-                        if (d >= d0 && ctr[d]) hc += row[hb[d]];
+                        if (hb[d] >= 0) hc += row[hb[d]];
                     const uint4 wl = *reinterpret_cast<const uint4*>(row + hb[MAXD - 1]);
                     int32_t* qrow = s_q + (int64_t)r * m;
 #pragma unroll
