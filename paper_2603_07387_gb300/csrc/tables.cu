@@ -34,21 +34,22 @@ __device__ __forceinline__ uint64_t sign_poly_u32(const HashCoef& h, uint32_t x)
     return fold61(mulmod61_u32(g, x) + h.c0);
 }
 
-// Words of x = x0, x0 + 32, x0 + 64, ... (count of them: steps) by forward differences
-// with step 32, exact in the field mod P: the bin polynomial a1 x + a0 advances by
-// 32 a1; the cubic sign polynomial g by its first three differences at x0 (from g at
-// x0, x0 + 32, x0 + 64) and the constant third difference 6 c3 32^3. Four modular
-// additions per word instead of four products; the words equal hash_packed_u32's.
-// Needs x0 + 64 < 2^32. emit(t, word) stores the word of x0 + 32 t.
-template <typename Emit>
+// Words of x = x0, x0 + STEP, x0 + 2 STEP, ... (count of them: steps) by forward
+// differences, exact in the field mod P: the bin polynomial a1 x + a0 advances by
+// STEP a1; the cubic sign polynomial g by its first three differences at x0 (from g at
+// x0, x0 + STEP, x0 + 2 STEP) and the constant third difference 6 c3 STEP^3. Four
+// modular additions per word instead of four products; the words equal
+// hash_packed_u32's. Needs x0 + 2 STEP < 2^32. emit(t, word) stores the word of
+// x0 + STEP t.
+template <uint32_t STEP = 32, typename Emit>
 __device__ __forceinline__ void fd_words(const HashCoef& h, uint32_t x0, int64_t steps, uint32_t mask, Emit emit) {
     uint64_t g = sign_poly_u32(h, x0);
-    const uint64_t g1 = sign_poly_u32(h, x0 + 32), g2 = sign_poly_u32(h, x0 + 64);
+    const uint64_t g1 = sign_poly_u32(h, x0 + STEP), g2 = sign_poly_u32(h, x0 + 2 * STEP);
     uint64_t d1 = sub61(g1, g);
     uint64_t d2 = sub61(add61(g2, g), add61(g1, g1));
-    const uint64_t d3 = mulmod61_u32(h.c3, 6u * 32u * 32u * 32u);
+    const uint64_t d3 = mulmod61_u32(h.c3, 6u * STEP * STEP * STEP);
     uint64_t b = fold61(mulmod61_u32(h.a1, x0) + h.a0);
-    const uint64_t db = mulmod61_u32(h.a1, 32u);
+    const uint64_t db = mulmod61_u32(h.a1, STEP);
     for (int64_t t = 0; t < steps; ++t) {
         emit(t, (uint32_t)(b & mask) | ((uint32_t)(g & 1) << TNSK_SIGN_SHIFT));
         b = add61(b, db);
@@ -108,6 +109,19 @@ __global__ void __launch_bounds__(256) draw_tables_kernel(const TabReq* __restri
             mask_l = q.mask;
         }
         const int cnt = r1 - g0 < 32 ? (int)(r1 - g0) : 32;
+        // short rows (at most 32 indices, e.g. the bonds and legs of small networks): each
+        // lane writes its own row by forward differences of step 1, instead of the warp
+        // taking the rows one after another with most lanes idle
+        if (__all_sync(0xffffffffu, row >= r1 || n_l <= 32)) {
+            if (row < r1 && n_l > 0) {
+                uint32_t* dst = (uint32_t*)(uintptr_t)dst_l;
+                if (n_l >= 4)
+                    fd_words<1>(hc, 0u, n_l, mask_l, [&](int64_t t, uint32_t w) { dst[t] = w; });
+                else
+                    for (int x = 0; x < (int)n_l; ++x) dst[x] = hash_packed_u32(hc, (uint32_t)x, mask_l);
+            }
+            continue;
+        }
         for (int i = 0; i < cnt; ++i) {
             HashCoef h;
             h.a0 = __shfl_sync(0xffffffffu, (unsigned long long)hc.a0, i);
