@@ -455,8 +455,9 @@ def run_ours(args, world, rank, local):
                           "probe_source": d["probe_source"]})
         else:
             r.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None})
-        # the committed counters of the method-2 product are those of the dense-chain kernel
-        r["traffic"] = read_traffic(kern) if (kern != "m2_gemm" or not args.grouped) else None
+        # the method-2 product's counters: the streaming kernel (stored chain) or the
+        # grouped-tensor kernel
+        r["traffic"] = read_traffic(kern if (kern != "m2_gemm" or not args.grouped) else "m2_gemm_rung")
         rooflines.append(r)
     roof = rooflines[0] if rooflines else None
     if roof is not None:

@@ -305,7 +305,8 @@ typedef enum {
     TNSK_K_M2_SCATTER = 9,  /* method 2 count-sketch scatter of the product rows (a7) */
     TNSK_K_PAIRS = 10,      /* exact pair contractions (tnsk_pairs_run) */
     TNSK_K_NORMALIZE = 11,  /* WLOG 2 / 3 rewrite of acyclic networks (Sec. 4.1) */
-    TNSK_KERNEL_KINDS = 12
+    TNSK_K_M2_PREP = 12,    /* method 2: TF32 parts of grouped tensors' factors, once per run (a7) */
+    TNSK_KERNEL_KINDS = 13
 } tnsk_kernel_kind;
 tnsk_status tnsk_profile(tnsk_ctx* ctx, int32_t enable);
 tnsk_status tnsk_profile_read(tnsk_ctx* ctx, double* ms, int64_t* launches);

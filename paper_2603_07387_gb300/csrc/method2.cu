@@ -598,7 +598,7 @@ static cudaError_t run_m2_t(const BatchPlan& P, unsigned char* base, const void*
                             Profiler& prof, int* d_err, int inject) {
     static const int kKind[M2_NKINDS] = {TNSK_K_M2_LEAF, TNSK_K_M2_COMPOSE, TNSK_K_M2_VBUILD, TNSK_K_M2_GEMM,
                                          TNSK_K_M2_GEMM, TNSK_K_M2_GEMM,    TNSK_K_M2_GEMM,   TNSK_K_M2_GEMM,
-                                         TNSK_K_M2_GEMM, TNSK_K_M2_SCATTER, TNSK_K_M2_ROOT,   TNSK_K_M2_GEMM};
+                                         TNSK_K_M2_GEMM, TNSK_K_M2_SCATTER, TNSK_K_M2_ROOT,   TNSK_K_M2_PREP};
     const M2Node* nodes = (const M2Node*)(base + P.m2.nodes_off);
     const M2Net* nets = (const M2Net*)(base + P.m2.nets_off);
     const M2Item* items = (const M2Item*)(base + P.m2.items_off);

@@ -30,7 +30,7 @@ STATUS = {
 F64, F32, BF16 = 0, 1, 2
 GENERAL, ACYCLIC, CROSSCORR = 1, 2, 3  # tnsk_method (CROSSCORR: the earlier cross-correlation estimator)
 KERNEL_KINDS = ("tables", "m1_scatter", "m1_spectrum", "m2_leaf", "m2_compose", "m2_vbuild", "m2_gemm",
-                "m2_root", "combine", "m2_scatter", "pairs", "normalize")
+                "m2_root", "combine", "m2_scatter", "pairs", "normalize", "m2_prep")
 PREC_FP32, PREC_BF16, PREC_FP64, PREC_AUTO = 0, 1, 2, 3
 
 # exported symbols declared in include/tnsk.h
