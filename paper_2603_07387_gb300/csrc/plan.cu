@@ -322,7 +322,8 @@ tnsk_status validate(const tnsk_network& net, const tnsk_params& prm, NetInfo& I
     }
     // ---- method 2: acyclic, connected, full (Sec. 4.4) ----
     if (net.n_open != 0) {
-        why = "the acyclic method takes full networks (no open legs) in this library";
+        why = "the acyclic method takes open legs in tnsk_estimate and tnsk_estimate_batch only (one full estimate "
+              "per output entry), not in plans, streams or parameter choices";
         return TNSK_ERR_UNSUPPORTED;
     }
     for (int e = 0; e < I.t; ++e)
