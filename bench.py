@@ -1049,7 +1049,7 @@ def learned_vs_plain(ctx, dev, steps: int = 5, n_train: int = 800):
                 batch in one call, timed like the chosen arm.
     Throughput counts every estimate produced; `within_5pct` is the fraction of them
     within 5% of the exact value; `miss_rate` = 1 - within_5pct. `by_flag` splits both
-    arms' within-5% fractions by the chosen arm's verdict (sized or flagged).
+    arms' within-5% fractions by the chosen arm's decision (sized or flagged).
     `hindsight_sized` (all held-out grids) is the ceiling of any sizing rule on the same
     networks: sizes picked from each network's own measured errors."""
     import torch
