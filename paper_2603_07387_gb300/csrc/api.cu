@@ -456,6 +456,11 @@ static tnsk_status expand_open_m2(tnsk_ctx* ctx, int32_t B, const tnsk_network* 
         for (int k = 0; k < N.p && ok; ++k) {
             const tnsk_tensor& T = N.X[k];
             ok = T.order >= 0 && T.order <= TNSK_MAX_ORDER && (T.order == 0 || T.dims) && (T.rung || T.data);
+            int64_t numel = 1;  // dims non-negative, at most 2^40 entries (else the planner reports it)
+            for (int d = 0; d < T.order && ok; ++d) {
+                ok = T.dims[d] >= 0 && (T.dims[d] == 0 || numel <= ((int64_t)1 << 40) / T.dims[d]);
+                if (ok) numel *= T.dims[d];
+            }
             S.mode_off[k + 1] = S.mode_off[k] + (ok ? T.order : 0);
         }
         const int q = S.mode_off[N.p];
@@ -477,7 +482,8 @@ static tnsk_status expand_open_m2(tnsk_ctx* ctx, int32_t B, const tnsk_network* 
         for (int g = 0; g < q && ok; ++g) ok = used[g] || S.open_pos[g] >= 0;
         if (!ok) continue;
         auto dim_of = [&](int g) { return N.X[tensor_of[g]].dims[g - S.mode_off[tensor_of[g]]]; };
-        for (int j = 0; j < N.n_open; ++j) S.O *= std::max<int64_t>(dim_of(N.open[j]), 0);
+        for (int j = 0; j < N.n_open; ++j)  // (capped just above the limit: no overflow)
+            S.O = std::min<int64_t>(S.O * dim_of(N.open[j]), kMaxOpenEntries + 1);
         entries += S.O;
         if (S.O == 0 || entries > kMaxOpenEntries)
             return fail(ctx, TNSK_ERR_UNSUPPORTED,
