@@ -102,3 +102,19 @@ def test_method2_open_legs_in_a_batch_and_not_in_plans(ctx):
     assert_parity(pers[2].cpu().numpy(), y, s, TOL[tnsk.PREC_FP32], "method 1 beside them")
     with pytest.raises(tnsk.TnskError):
         ctx.plan([nets[0]], [p], [outs[0]])
+
+
+def test_method2_open_legs_limits(ctx):
+    """More than 2^16 output entries in one call, or an empty output, are refused with
+    TNSK_ERR_UNSUPPORTED (each entry is a full estimate of its own)."""
+    rng = np.random.default_rng(3)
+    big = W.NetSpec([rng.standard_normal((300, 5)).astype(np.float32), rng.standard_normal((5, 300)).astype(np.float32)],
+                    [(1, 2)], [0, 3], "90000 entries")
+    empty = W.NetSpec([np.zeros((0, 5), dtype=np.float32), rng.standard_normal((5, 4)).astype(np.float32)],
+                      [(1, 2)], [0, 3], "empty output")
+    p = tnsk.Params(m=64, reps=2, seed=1, method=tnsk.ACYCLIC)
+    for spec in (big, empty):
+        net = gpu_network(spec, torch.float32)
+        out = torch.zeros(max(1, 300 * 300), dtype=torch.float64, device="cuda")
+        with pytest.raises(tnsk.TnskError):
+            ctx.estimate(net, p, out)
