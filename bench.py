@@ -537,6 +537,9 @@ def run_ours(args, world, rank, local):
                              "the tensor cores, no merged site stored), end sites merged every step (tnsk_pairs, "
                              "the plan's prelude)"),
                    "networks_per_step": 2 * B, "estimate": "method-2 combined estimate of one pair",
+                   "error_gate": "the metric's <=5% gate read as the ATNC error |y - tc| / prod_k ||X_k||_F (Def. "
+                                 "ATNC); on these zero-mean trains it is met trivially (see accuracy: eps and the "
+                                 "fraction within 5% of tc)",
                    "m": M, "reps": REPS, "inputs_bytes_per_gpu": in_bytes,
                    "l2": "L2 flushed between timed steps (256 MiB written after each step, outside its CUDA-event "
                          "pair; the 25 MB of inputs fit in L2)", "parallelism": f"replicas x{world}"},
