@@ -77,3 +77,17 @@ def test_rung_factors_are_checked_on_the_host():
         tnsk.Rung(torch.zeros(3, 4, 5), torch.zeros(6, 2, 7))  # unequal shared dims
     with pytest.raises(ValueError):
         tnsk.Rung(torch.zeros(3, 4), torch.zeros(6, 4, 7))
+
+
+def test_binding_kernel_kinds_follow_the_header():
+    """tnsk_profile_read fills one slot per tnsk_kernel_kind: the binding's names are in
+    the header's order and as many as TNSK_KERNEL_KINDS."""
+    from paper_2603_07387_gb300 import tnsk
+
+    with open(os.path.join(ROOT, "include", "tnsk.h")) as f:
+        src = f.read()
+    kinds = {int(v): k for k, v in re.findall(r"TNSK_K_(\w+)\s*=\s*(\d+)", src)}
+    total = int(re.search(r"TNSK_KERNEL_KINDS\s*=\s*(\d+)", src).group(1))
+    assert sorted(kinds) == list(range(total))
+    assert len(tnsk.KERNEL_KINDS) == total
+    assert [kinds[i].lower() for i in range(total)] == list(tnsk.KERNEL_KINDS)
