@@ -136,6 +136,33 @@ class Schedule(ctypes.Structure):
     def as_dict(self):
         return {"rep_cap": list(self.rep_cap), "chunk_scale": list(self.chunk_scale)}
 
+    @classmethod
+    def from_dict(cls, d) -> "Schedule":
+        """The schedule of a table {"rep_cap": [...], "chunk_scale": [...]} (one non-negative
+        integer per scatter list; 0 keeps the default), e.g. one tnsk_autotune found."""
+        s = cls()
+        for key in ("rep_cap", "chunk_scale"):
+            vals = [int(v) for v in d[key]]
+            if len(vals) != SCATTER_LISTS or min(vals) < 0:
+                raise ValueError(f"{key}: {SCATTER_LISTS} non-negative integers expected")
+            getattr(s, key)[:] = vals
+        return s
+
+    def save(self, path: str):
+        """Writes the schedule as a JSON table (as_dict) for later plans."""
+        import json
+
+        with open(path, "w") as f:
+            json.dump(self.as_dict(), f)
+
+    @classmethod
+    def load(cls, path: str) -> "Schedule":
+        """A schedule saved by save(): ctx.plan(..., schedule=Schedule.load(path))."""
+        import json
+
+        with open(path) as f:
+            return cls.from_dict(json.load(f))
+
 
 class _Params(ctypes.Structure):
     _fields_ = [

@@ -56,3 +56,19 @@ def test_marshalled_form_stays_out_of_pickles_and_copies():
         assert m.edges == n.edges
         h = tnsk._holder(m)
         assert h.c.p == 3
+
+
+def test_schedule_json_table_round_trip(tmp_path):
+    """A scatter schedule (what tnsk_autotune finds) saved as a JSON table and loaded for
+    later plans is the same schedule; malformed tables are refused."""
+    s = tnsk.Schedule()
+    s.rep_cap[:] = [(3 * i) % 33 for i in range(tnsk.SCATTER_LISTS)]
+    s.chunk_scale[:] = [1 + i % 4 for i in range(tnsk.SCATTER_LISTS)]
+    path = str(tmp_path / "schedule.json")
+    s.save(path)
+    t = tnsk.Schedule.load(path)
+    assert t.as_dict() == s.as_dict()
+    with pytest.raises(ValueError):
+        tnsk.Schedule.from_dict({"rep_cap": [1, 2], "chunk_scale": [1, 2]})
+    with pytest.raises(ValueError):
+        tnsk.Schedule.from_dict({"rep_cap": [-1] * tnsk.SCATTER_LISTS, "chunk_scale": [1] * tnsk.SCATTER_LISTS})
